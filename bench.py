@@ -1,0 +1,358 @@
+"""Throughput benchmark of the ADER-DG hot path on one GB300 (per rank).
+
+Workload: the rising warm bubble -- degree 5 (order 6), 81 x 81 = 6561 cells
+on [0,1000]^2 m with slip walls, isentropic background theta0 = 300 K,
+g = 9.81, cosine theta' bubble (0.5 K, radius 250 m, centre (500, 350)),
+mu = 0.01, fixed dt from CFL 0.5 on the initial state.  One step = one pass
+of the hot path: space-time predictor, corrector, and the TV refinement
+indicator (per-cell TV of theta, Chan mean/std, flags).
+
+Metric: DOF-updates/s = cells * (N+1)^2 * 4 * steps / seconds (the paper's
+DOF count: spatial nodal values of the 4 conserved variables).
+
+Timing: W untimed warm-up steps, then K steps each bracketed by CUDA events
+on the launching stream; a 256 MB buffer is written before every timed step
+to flush L2 (the state is smaller than L2).  Under torchrun each rank runs an
+independent replica (weak scaling, no data-path collective); the time is the
+max over ranks.
+
+--impl reference times the FP64 CPU oracle on the host cores on a bounded
+sample of the same workload (the tier's reference arm).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ADER-DG DOF-updates/s at order 6: mixed/batched vs FP64 at stated error"
+UNIT = "DOF-updates/s"
+DEGREE, NX, NY = 5, 81, 81
+T_R, T_C = 1.5, -0.5    # AMR thresholds of the 2D cosine bubble (Sec. 4.2)
+
+
+def workload_config(precision):
+    return {
+        "workload": "rising warm bubble, degree 5 (order 6), 81x81=6561 cells on [0,1000]^2 m, "
+                    "slip walls, theta0=300 K, g=9.81, cosine bubble 0.5 K r=250 m at (500,350), "
+                    "mu=0.01, CFL 0.5; step = predictor + corrector + TV indicator",
+        "cells": NX * NY, "degree": DEGREE, "dof_per_step": NX * NY * (DEGREE + 1) ** 2 * 4,
+        "precision": precision, "l2": "flushed before every timed step (256 MB write)",
+    }
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ------------------------------------------------------------------ roofline
+def predictor_flops_per_cell(n):
+    """Algorithmic FP64 flops (FMA = 2) of one predictor launch per cell, as
+    implemented: sweep 1 evaluates one time slice (the iterate is constant in
+    time), sweeps 2..n all n time slices, then one final evaluation, time
+    averages, the weak volume residual and the face extrapolation."""
+    c_pt = 100                     # point-wise NS flux/source per node (counted from ns_flux)
+    grad = 16 * n + 8              # 4 vars x 2 directions x n FMA + scaling
+    evals = n * n + (n - 1) * n ** 3 + n ** 3
+    f = evals * (grad + c_pt)
+    div_slices = n * n + (n - 1) * n ** 3
+    f += div_slices * 4 * (4 * n + 3)            # -dF/dx - dG/dy
+    f += n * n * n * 4 * 3                         # sweep-1 time update
+    f += (n - 1) * n * n * 4 * n * (2 * n + 2)     # sweeps 2..n time contraction
+    f += n ** 3 * 24 * 2                           # time averages
+    f += n * n * 4 * (4 * n + 4)                   # volume residual
+    f += 4 * n * (16 * 2 * n + 20)                 # traces + wave speed
+    return f
+
+
+def measure_fma_peaks():
+    """Run the committed FMA microbenchmark (built by build()); returns
+    {'fp64': TFLOP/s, 'fp32': TFLOP/s} or {}."""
+    exe = os.path.join(ROOT, "paper_1905_05524_gb300", "_build", "fma_peak")
+    if not os.path.exists(exe):
+        return {}
+    try:
+        out = subprocess.run([exe], capture_output=True, text=True, timeout=120).stdout
+    except Exception:
+        return {}
+    res = {}
+    for line in out.splitlines():
+        try:
+            d = json.loads(line)
+            res[d["pipe"].split("_")[0]] = d["tflops"]
+        except Exception:
+            pass
+    return res
+
+
+def measured_peaks_file():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            with open(p) as f:
+                return json.load(f)
+        except Exception:
+            return None
+    return None
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ oracle arm
+def oracle_sample(steps, threads=None):
+    """Time the CPU oracle on the full workload for `steps` steps; returns
+    (DOF-updates/s, seconds, cores)."""
+    import torch
+    if threads:
+        torch.set_num_threads(threads)
+    from paper_1905_05524_gb300.solver import atmosphere_config
+    from tests.oracle_bridge import oracle_for, cosine_field
+    from oracle import indicator as oind
+    cfg = atmosphere_config(degree=DEGREE, nx=NX, ny=NY)
+    o = oracle_for(cfg)
+    u = cosine_field(o)
+    dt = o.stable_dt(u, 0.5)
+    t0 = time.perf_counter()
+    t = 0.0
+    for _ in range(steps):
+        u = o.step(u, dt, t)
+        t += dt
+        oind.tv_indicator(o, u, "theta", T_R, T_C)
+    sec = time.perf_counter() - t0
+    dof = NX * NY * (DEGREE + 1) ** 2 * 4
+    return dof * steps / sec, sec, torch.get_num_threads()
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    for _ in range(args.warmup and 1):
+        oracle_sample(1)
+    steps = max(1, args.steps)
+    val, sec, cores = oracle_sample(steps)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec / steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (analytic initial state)", "config": workload_config("fp64 CPU oracle"),
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{steps} full steps of the 81x81 degree-5 workload on the host cores"},
+        "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_ours(args):
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if ws > 1 else 0)
+    torch.cuda.set_device(dev)
+
+    from paper_1905_05524_gb300 import _lib as L
+    from paper_1905_05524_gb300.solver import Mesh, atmosphere_config
+
+    prec = L.ADG_PREC_FP64 if args.precision == "fp64" else L.ADG_PREC_MIXED
+    cfg = atmosphere_config(degree=DEGREE, nx=NX, ny=NY, precision=prec, device=dev.index)
+    m = Mesh(cfg)
+    m.init_scenario(L.ADG_SCEN_COSINE, A=0.5, a=250.0, xc=500.0, zc=350.0)
+    dt = m.stable_dt(0.5)
+    u_init = m.get_state().clone()
+    cells, n = NX * NY, DEGREE + 1
+    dof = cells * n * n * 4
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    tvbuf = torch.empty(cells, dtype=torch.float64, device=dev)
+    flags = torch.empty(cells, dtype=torch.int8, device=dev)
+    import ctypes
+    sp = ctypes.c_void_p(stream.cuda_stream)
+    lib = L.lib()
+
+    def one_step():
+        L.check(lib.adg_predictor(m.h, dt, sp))
+        ev[1].record(stream)
+        L.check(lib.adg_corrector(m.h, dt, sp))
+        ev[2].record(stream)
+        L.check(lib.adg_tv_indicator(m.h, L.ADG_TV_THETA, T_R, T_C, ctypes.c_void_p(tvbuf.data_ptr()),
+                                     ctypes.c_void_p(flags.data_ptr()), None, sp))
+
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    for _ in range(args.warmup):
+        ev[0].record(stream)
+        one_step()
+        ev[3].record(stream)
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(dev.index)
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    total = pred = corr = tvt = 0.0
+    for _ in range(args.steps):
+        flush.fill_(1.0)  # evict L2 between timed steps
+        ev[0].record(stream)
+        one_step()
+        ev[3].record(stream)
+        ev[3].synchronize()
+        total += ev[0].elapsed_time(ev[3])
+        pred += ev[0].elapsed_time(ev[1])
+        corr += ev[1].elapsed_time(ev[2])
+        tvt += ev[2].elapsed_time(ev[3])
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    t_ms = total
+    if ws > 1:
+        t = torch.tensor([t_ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_ms = float(t.item())
+    value = dof * args.steps * ws / (t_ms * 1e-3)
+
+    # ---- end to end through the public API with host buffers (pinned)
+    host_in = u_init.cpu().pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    stats = (ctypes.c_double * 2)()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2e_steps = max(1, args.steps)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        L.check(lib.adg_set_state(m.h, ctypes.c_void_p(host_in.data_ptr()), m.count, 0, sp))
+        L.check(lib.adg_step(m.h, dt, sp))
+        L.check(lib.adg_tv_indicator(m.h, L.ADG_TV_THETA, T_R, T_C, ctypes.c_void_p(tvbuf.data_ptr()),
+                                     ctypes.c_void_p(flags.data_ptr()), stats, sp))
+        L.check(lib.adg_get_state(m.h, ctypes.c_void_p(host_out.data_ptr()), m.count, 0, sp))
+    torch.cuda.synchronize()
+    e2e_sec = time.perf_counter() - t0
+    if ws > 1:
+        t = torch.tensor([e2e_sec], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_sec = float(t.item())
+    e2e_val = dof * e2e_steps * ws / e2e_sec
+
+    out = None
+    if rank == 0:
+        peaks = measure_fma_peaks()
+        mp = measured_peaks_file()
+        flops_launch = predictor_flops_per_cell(n) * cells
+        pred_avg = pred / args.steps
+        fp64_peak = peaks.get("fp64")
+        achieved = flops_launch / (pred_avg * 1e-3) / 1e12
+        roof = {
+            "kernel": "k_predictor_fp64<5,4>",
+            "bound": "alu", "pipe": "fp64 FMA",
+            "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+            "frac": (achieved / fp64_peak) if fp64_peak else None,
+            "peak_source": "measured by paper_1905_05524_gb300/csrc/fma_peak.cu on this GPU" if fp64_peak
+            else "unavailable",
+            "flops_per_launch": flops_launch, "launch_ms": pred_avg,
+            "traffic": None,
+            "hbm_achieved_gbs": cells * n * n * 4 * 8 * 2 / (pred_avg * 1e-3) / 1e9,
+            "hbm_peak_gbs": (mp or {}).get("hbm_gbs", 6800.0),
+            "hbm_peak_source": "MEASURED_PEAKS.json" if mp else "fallback 6.8 TB/s",
+        }
+        cpu = None
+        if not args.no_cpu_baseline and ws == 1:
+            cval, csec, ccores = oracle_sample(args.cpu_steps)
+            cpu = {"value": cval, "unit": UNIT, "cores": ccores, "kind": "oracle",
+                   "sample": f"{args.cpu_steps} full steps (predictor+corrector+TV) of the same "
+                             f"81x81 degree-5 workload, {csec:.1f} s"}
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+            "data": "synthetic (analytic initial state)", "config": workload_config(args.precision),
+            "phases_ms": {"predictor": pred_avg, "corrector": corr / args.steps, "tv_indicator": tvt / args.steps},
+            "gpu_launches": 4 * args.steps,
+            "clocks": clk,
+            "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": dof * 8,
+                    "d2h_bytes_per_step": dof * 8 + 16},
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "fma_peaks_tflops": peaks,
+        }
+        print(json.dumps(out), flush=True)
+    m.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--cpu-steps", type=int, default=8)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

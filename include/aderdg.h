@@ -1,0 +1,152 @@
+/*
+ * aderdg.h -- C ABI of the GB300 ADER-DG compressible Navier-Stokes hot path.
+ *
+ * Method: Krenz, Rannabauer, Bader, "A High-Order Discontinuous Galerkin
+ * Solver with Dynamic Adaptive Mesh Refinement to Simulate Cloud Formation
+ * Processes" (arXiv 1905.05524).  Sec. 2 (Eqs. 1-7) fixes the PDE: 2D
+ * compressible Navier-Stokes with viscous flux, EOS with geopotential and
+ * the hydrostatic perturbation split; Sec. 3 fixes the scheme family
+ * (ADER-DG predictor/corrector, Rusanov-type viscous flux) and the
+ * total-variation refinement indicator (Eqs. 6-8).
+ *
+ * Conventions (all functions):
+ *   - return an int status, ADG_OK (0) on success; nothing throws or aborts;
+ *   - adg_last_error() returns a thread-local text of the last failure;
+ *   - the library owns each mesh and its device workspace; the caller owns
+ *     every array it passes;
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream); all device work of a call is queued on it; only calls that
+ *     return host data synchronise it;
+ *   - `on_device` != 0 means the pointer is a device pointer on the mesh's
+ *     device, 0 means host memory.
+ *
+ * State layout (set_state / get_state / adjoint vectors): double u[c][v][j][i]
+ * with c = iy*nx + ix (row-major cells), v = rho, rho*u, rho*v, rho*E, and
+ * j, i the y- and x-indices of the (N+1) x (N+1) Gauss-Legendre nodes of the
+ * cell (nodal values).  count = nx*ny*(N+1)^2*4.
+ */
+#ifndef ADERDG_H
+#define ADERDG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define ADG_OK 0
+#define ADG_EINVAL 1      /* bad argument (size, range, NULL)                */
+#define ADG_ENOMEM 2      /* device or host allocation failed                 */
+#define ADG_ECUDA 3       /* a CUDA runtime call failed (text kept)           */
+#define ADG_ENONFINITE 4  /* a NaN/Inf was found in the state                 */
+#define ADG_ETIMEOUT 5    /* a bounded device wait gave up                    */
+#define ADG_ESTATE 6      /* wrong call order (e.g. corrector w/o predictor)  */
+#define ADG_EUNSUPPORTED 7 /* option not built for this configuration         */
+
+/* ---- options ---- */
+#define ADG_BC_PERIODIC 0
+#define ADG_BC_WALL 1       /* slip wall with background ghost (Sec. 4.2, Eq. 10) */
+
+#define ADG_SRC_NONE 0
+#define ADG_SRC_STEADY 1    /* steady manufactured source rho = 1 + a sin(2pi(x+y)/L) */
+
+#define ADG_PREC_FP64 0     /* every operation in FP64                          */
+#define ADG_PREC_MIXED 1    /* FP32 predictor on perturbation variables; FP64
+                               background split, pressure recovery and update   */
+
+#define ADG_TV_RHO 0
+#define ADG_TV_THETA 1      /* potential temperature theta = T (p0/p)^(R/cp)  */
+
+#define ADG_MAX_DEGREE 7
+
+typedef struct adg_mesh adg_mesh;
+
+/* Mesh and physics description.  A uniform nx x ny mesh on
+ * [x0, x0+Lx] x [y0, y0+Ly]; y is the vertical (z) coordinate of Eqs. 2, 6, 7. */
+typedef struct adg_mesh_desc {
+    int degree;            /* polynomial degree N, 1..ADG_MAX_DEGREE             */
+    int nx, ny;            /* cells per direction, >= 1                          */
+    double x0, y0, Lx, Ly; /* domain box                                         */
+    int bc_x, bc_y;        /* ADG_BC_* per direction                             */
+    double gamma, Pr, R, mu; /* Eqs. 2-5: heat-capacity ratio, Prandtl number,
+                                gas constant, viscosity                          */
+    int gravity;           /* 1: gravity source -g rho' and hydrostatic split    */
+    double g, p0, theta0;  /* gravity, reference pressure, background theta      */
+    int source;            /* ADG_SRC_*                                          */
+    double src_a, src_L, src_U, src_p; /* parameters of ADG_SRC_STEADY            */
+    int precision;         /* ADG_PREC_*                                         */
+    int device;            /* CUDA device ordinal                                */
+} adg_mesh_desc;
+
+#define ADG_SCEN_STEADY 0       /* steady manufactured field of the source above */
+#define ADG_SCEN_COSINE 1       /* cosine bubble theta' (Eq. 15, r/a reading)    */
+#define ADG_SCEN_TWO_BUBBLES 2  /* Gaussian-tail warm + cold bubbles (Eqs. 12, 14) */
+#define ADG_SCEN_BACKGROUND 3   /* unperturbed hydrostatic atmosphere (Eq. 6)     */
+
+typedef struct adg_scenario {
+    int kind;              /* ADG_SCEN_*                                         */
+    double A, a, xc, zc;   /* cosine bubble: amplitude, radius, centre           */
+} adg_scenario;
+
+/* Create a mesh: allocates the state and workspace on desc->device and builds
+ * the basis (Gauss-Legendre nodes, derivative, time-stiffness matrices).
+ * Errors: ADG_EINVAL (degree/size/options), ADG_ENOMEM, ADG_ECUDA. */
+int adg_create_mesh(const adg_mesh_desc* desc, adg_mesh** out);
+
+/* Free everything owned by the mesh; NULL-safe.  Synchronises the device. */
+void adg_destroy_mesh(adg_mesh* m);
+
+/* Number of doubles of the state: nx*ny*(N+1)^2*4. */
+size_t adg_state_count(const adg_mesh* m);
+
+/* Copy a state in / out (layout above).  count must equal adg_state_count;
+ * ADG_EINVAL otherwise.  get_state with a host pointer synchronises `stream`. */
+int adg_set_state(adg_mesh* m, const double* u, size_t count, int on_device, void* stream);
+int adg_get_state(adg_mesh* m, double* u, size_t count, int on_device, void* stream);
+
+/* Simulation time carried by the mesh (advanced by adg_step). */
+int adg_set_time(adg_mesh* m, double t);
+double adg_get_time(const adg_mesh* m);
+
+/* Nodal interpolation of a scenario's initial state (Sec. 4.1, 4.2). */
+int adg_init_scenario(adg_mesh* m, const adg_scenario* s, void* stream);
+
+/* Space-time predictor (Sec. 3, ADER-DG): n = N+1 Picard sweeps of the
+ * element-local space-time polynomial, then the time-averaged volume
+ * residual and the boundary-extrapolated face traces into the workspace. */
+int adg_predictor(adg_mesh* m, double dt, void* stream);
+
+/* Corrector: Rusanov-type viscous face flux (Sec. 3), weak-form lift and the
+ * FP64 update u += dt * (volume - faces + source).  ADG_ESTATE unless the
+ * last call on this mesh was adg_predictor with the same dt. */
+int adg_corrector(adg_mesh* m, double dt, void* stream);
+
+/* predictor + corrector; t += dt. */
+int adg_step(adg_mesh* m, double dt, void* stream);
+
+/* Largest stable dt for a CFL number (dt = CFL h / (2 (2N+1) max(|v| + c +
+ * 2 eta lambda_v))).  Synchronises `stream`. */
+int adg_stable_dt(adg_mesh* m, double cfl, double* dt, void* stream);
+
+/* Total-variation refinement indicator of the current state (Sec. 3,
+ * Eqs. 6-8): per-cell TV of `var` (ADG_TV_*), mean and population standard
+ * deviation over all cells (Chan et al. parallel update, fixed combine
+ * order), and flags +1 refine / 0 keep / -1 coarsen.  tv (double[cells]) and
+ * flags (int8_t[cells]) are device pointers, either may be NULL; stats (host,
+ * double[2] = mean, std) may be NULL; when it is not, `stream` is synchronised. */
+int adg_tv_indicator(adg_mesh* m, int var, double T_r, double T_c,
+                     double* tv, int8_t* flags, double* stats, void* stream);
+
+/* Scan the state for NaN/Inf: ADG_ENONFINITE if any.  Synchronises `stream`. */
+int adg_check_finite(adg_mesh* m, void* stream);
+
+/* Text of the last error on the calling thread ("" if none). */
+const char* adg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ADERDG_H */

@@ -1,0 +1,112 @@
+"""ctypes binding of libaderdg.so (include/aderdg.h): argument marshalling only.
+
+Every computation happens in the CUDA library; this module only converts
+Python arguments to C types and C status codes to exceptions.  Loading fails
+loudly if the library has not been built.
+"""
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libaderdg.so")
+
+ADG_OK = 0
+ADG_EINVAL = 1
+ADG_ENOMEM = 2
+ADG_ECUDA = 3
+ADG_ENONFINITE = 4
+ADG_ETIMEOUT = 5
+ADG_ESTATE = 6
+ADG_EUNSUPPORTED = 7
+
+ADG_BC_PERIODIC = 0
+ADG_BC_WALL = 1
+ADG_SRC_NONE = 0
+ADG_SRC_STEADY = 1
+ADG_PREC_FP64 = 0
+ADG_PREC_MIXED = 1
+ADG_TV_RHO = 0
+ADG_TV_THETA = 1
+ADG_SCEN_STEADY = 0
+ADG_SCEN_COSINE = 1
+ADG_SCEN_TWO_BUBBLES = 2
+ADG_SCEN_BACKGROUND = 3
+
+STATUS_NAMES = {1: "ADG_EINVAL", 2: "ADG_ENOMEM", 3: "ADG_ECUDA", 4: "ADG_ENONFINITE",
+                5: "ADG_ETIMEOUT", 6: "ADG_ESTATE", 7: "ADG_EUNSUPPORTED"}
+
+
+class MeshDesc(ctypes.Structure):
+    _fields_ = [("degree", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int),
+                ("x0", ctypes.c_double), ("y0", ctypes.c_double),
+                ("Lx", ctypes.c_double), ("Ly", ctypes.c_double),
+                ("bc_x", ctypes.c_int), ("bc_y", ctypes.c_int),
+                ("gamma", ctypes.c_double), ("Pr", ctypes.c_double),
+                ("R", ctypes.c_double), ("mu", ctypes.c_double),
+                ("gravity", ctypes.c_int), ("g", ctypes.c_double),
+                ("p0", ctypes.c_double), ("theta0", ctypes.c_double),
+                ("source", ctypes.c_int), ("src_a", ctypes.c_double),
+                ("src_L", ctypes.c_double), ("src_U", ctypes.c_double),
+                ("src_p", ctypes.c_double), ("precision", ctypes.c_int),
+                ("device", ctypes.c_int)]
+
+
+class Scenario(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("A", ctypes.c_double), ("a", ctypes.c_double),
+                ("xc", ctypes.c_double), ("zc", ctypes.c_double)]
+
+
+class AdgError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+_P = ctypes.c_void_p
+_D = ctypes.c_double
+_I = ctypes.c_int
+_S = ctypes.c_size_t
+
+# name -> (restype, argtypes); the list of symbols include/aderdg.h declares
+SIGNATURES = {
+    "adg_create_mesh": (_I, [ctypes.POINTER(MeshDesc), ctypes.POINTER(_P)]),
+    "adg_destroy_mesh": (None, [_P]),
+    "adg_state_count": (_S, [_P]),
+    "adg_set_state": (_I, [_P, _P, _S, _I, _P]),
+    "adg_get_state": (_I, [_P, _P, _S, _I, _P]),
+    "adg_set_time": (_I, [_P, _D]),
+    "adg_get_time": (_D, [_P]),
+    "adg_init_scenario": (_I, [_P, ctypes.POINTER(Scenario), _P]),
+    "adg_predictor": (_I, [_P, _D, _P]),
+    "adg_corrector": (_I, [_P, _D, _P]),
+    "adg_step": (_I, [_P, _D, _P]),
+    "adg_stable_dt": (_I, [_P, _D, ctypes.POINTER(_D), _P]),
+    "adg_tv_indicator": (_I, [_P, _I, _D, _D, _P, _P, _P, _P]),
+    "adg_check_finite": (_I, [_P, _P]),
+    "adg_last_error": (ctypes.c_char_p, []),
+}
+
+_lib = None
+
+
+def lib():
+    """Load libaderdg.so once; raise if it is missing (no fallback path)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libaderdg.so not built ({LIB_PATH}); run "
+                               "`python -m paper_1905_05524_gb300.build` first")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def check(code):
+    if code != ADG_OK:
+        msg = lib().adg_last_error().decode(errors="replace")
+        raise AdgError(code, msg)
+    return code

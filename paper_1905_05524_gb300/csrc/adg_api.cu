@@ -1,0 +1,561 @@
+// C ABI of the GB300 ADER-DG library: mesh lifetime, basis construction,
+// state transfer and the host side of every entry point in include/aderdg.h.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "adg_internal.h"
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+    g_err = msg;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+    g_err = std::string(what) + ": " + cudaGetErrorString(e);
+    return ADG_ECUDA;
+}
+
+#define ADG_CK(call, what)                              \
+    do {                                                \
+        cudaError_t e_ = (call);                        \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+// ---------------------------------------------------------------- basis
+// Gauss-Legendre nodes on [-1, 1] by Newton's method on the three-term
+// recurrence of the Legendre polynomials, mapped to [0, 1].
+void gauss_legendre01(int n, double* xi, double* w) {
+    for (int r = 0; r < n; ++r) {
+        double x = std::cos(M_PI * (r + 0.75) / (n + 0.5));
+        double dp = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            double pm = 1.0, p = x;  // P_0, P_1
+            for (int k = 2; k <= n; ++k) {
+                const double pk = ((2.0 * k - 1.0) * x * p - (k - 1.0) * pm) / k;
+                pm = p;
+                p = pk;
+            }
+            if (n == 1) { p = x; pm = 1.0; }
+            dp = n * (x * p - pm) / (x * x - 1.0);
+            const double dx = p / dp;
+            x -= dx;
+            if (std::fabs(dx) < 1e-16) break;
+        }
+        double pm = 1.0, p = x;
+        for (int k = 2; k <= n; ++k) {
+            const double pk = ((2.0 * k - 1.0) * x * p - (k - 1.0) * pm) / k;
+            pm = p;
+            p = pk;
+        }
+        if (n == 1) { p = x; pm = 1.0; }
+        dp = n * (x * p - pm) / (x * x - 1.0);
+        // roots come out in descending x; store ascending
+        xi[n - 1 - r] = 0.5 * (x + 1.0);
+        w[n - 1 - r] = 1.0 / ((1.0 - x * x) * dp * dp);  // = (2/((1-x^2) P'^2)) / 2
+    }
+}
+
+double lagrange(const double* xi, int n, int j, double x) {
+    double v = 1.0;
+    for (int m = 0; m < n; ++m)
+        if (m != j) v *= (x - xi[m]) / (xi[j] - xi[m]);
+    return v;
+}
+
+bool invert(int n, const double* A, double* Ainv) {  // Gauss-Jordan, partial pivoting
+    double M[adg::kMaxN][2 * adg::kMaxN];
+    for (int r = 0; r < n; ++r)
+        for (int c = 0; c < 2 * n; ++c) M[r][c] = c < n ? A[r * n + c] : (c - n == r ? 1.0 : 0.0);
+    for (int c = 0; c < n; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < n; ++r)
+            if (std::fabs(M[r][c]) > std::fabs(M[piv][c])) piv = r;
+        if (std::fabs(M[piv][c]) < 1e-300) return false;
+        if (piv != c)
+            for (int k = 0; k < 2 * n; ++k) std::swap(M[c][k], M[piv][k]);
+        const double d = M[c][c];
+        for (int k = 0; k < 2 * n; ++k) M[c][k] /= d;
+        for (int r = 0; r < n; ++r) {
+            if (r == c) continue;
+            const double f = M[r][c];
+            for (int k = 0; k < 2 * n; ++k) M[r][k] -= f * M[c][k];
+        }
+    }
+    for (int r = 0; r < n; ++r)
+        for (int c = 0; c < n; ++c) Ainv[r * n + c] = M[r][n + c];
+    return true;
+}
+
+bool build_basis(int N, adg::Basis& B) {
+    std::memset(&B, 0, sizeof(B));
+    const int n = N + 1;
+    B.n = n;
+    gauss_legendre01(n, B.xi, B.w);
+    double lam[adg::kMaxN];
+    for (int j = 0; j < n; ++j) {
+        lam[j] = 1.0;
+        for (int m = 0; m < n; ++m)
+            if (m != j) lam[j] /= (B.xi[j] - B.xi[m]);
+    }
+    for (int i = 0; i < n; ++i) {
+        double diag = 0.0;
+        for (int j = 0; j < n; ++j) {
+            if (i == j) continue;
+            B.D[i][j] = (lam[j] / lam[i]) / (B.xi[i] - B.xi[j]);
+            diag -= B.D[i][j];
+        }
+        B.D[i][i] = diag;
+    }
+    for (int j = 0; j < n; ++j) {
+        B.phi0[j] = lagrange(B.xi, n, j, 0.0);
+        B.phi1[j] = lagrange(B.xi, n, j, 1.0);
+        B.lift0[j] = B.phi0[j] / B.w[j];
+        B.lift1[j] = B.phi1[j] / B.w[j];
+    }
+    // K1[l][k] = phi_l(1) phi_k(1) - w_k D[k][l]
+    double K1[adg::kMaxN * adg::kMaxN], K1i[adg::kMaxN * adg::kMaxN];
+    for (int l = 0; l < n; ++l)
+        for (int k = 0; k < n; ++k) K1[l * n + k] = B.phi1[l] * B.phi1[k] - B.w[k] * B.D[k][l];
+    if (!invert(n, K1, K1i)) return false;
+    for (int l = 0; l < n; ++l) {
+        double s = 0.0;
+        for (int k = 0; k < n; ++k) {
+            B.Kw[l][k] = K1i[l * n + k] * B.w[k];
+            s += B.Kw[l][k];
+        }
+        B.Kw1[l] = s;
+    }
+    for (int p = 0; p < n; ++p)
+        for (int i = 0; i < n; ++i) B.Vx[p][i] = B.w[p] * B.D[p][i] / B.w[i];
+    return true;
+}
+
+}  // namespace
+
+struct adg_mesh {
+    adg_mesh_desc d;
+    int N = 0, n = 0, cells = 0;
+    adg::Basis B;
+    adg::Phys P;
+    double* u = nullptr;
+    double* rvol = nullptr;
+    double* trace = nullptr;
+    double* tv = nullptr;
+    double* stats = nullptr;     // device [2]
+    double* speed = nullptr;     // device partial maxima
+    int speed_blocks = 0;
+    int* flag = nullptr;         // device int
+    double* bgbuf = nullptr;     // pbar_node, rhobar_node, pbar_face, rhobar_face
+    adg::Background bg{};
+    // mixed precision
+    adg::BasisF Bf;
+    adg::PhysF Pf;
+    void* mixbuf = nullptr;
+    adg::MixedBg mbg{};
+    double t = 0.0;
+    bool predicted = false;
+    double pred_dt = 0.0;
+};
+
+namespace {
+
+void free_mesh(adg_mesh* m) {
+    if (!m) return;
+    cudaFree(m->u);
+    cudaFree(m->rvol);
+    cudaFree(m->trace);
+    cudaFree(m->tv);
+    cudaFree(m->stats);
+    cudaFree(m->speed);
+    cudaFree(m->flag);
+    cudaFree(m->bgbuf);
+    cudaFree(m->mixbuf);
+    delete m;
+}
+
+// FP32 copies of basis/constants and the FP64/FP32 background tables of the
+// mixed-precision path.
+int build_mixed(adg_mesh* m) {
+    const adg_mesh_desc* d = &m->d;
+    const int n = m->n, ny = d->ny;
+    adg::BasisF& b = m->Bf;
+    std::memset(&b, 0, sizeof(b));
+    for (int a = 0; a < n; ++a) {
+        b.xi[a] = (float)m->B.xi[a];
+        b.w[a] = (float)m->B.w[a];
+        b.phi0[a] = (float)m->B.phi0[a];
+        b.phi1[a] = (float)m->B.phi1[a];
+        b.Kw1[a] = (float)m->B.Kw1[a];
+        b.lift0[a] = (float)m->B.lift0[a];
+        b.lift1[a] = (float)m->B.lift1[a];
+        for (int c = 0; c < n; ++c) {
+            b.D[a][c] = (float)m->B.D[a][c];
+            b.Kw[a][c] = (float)m->B.Kw[a][c];
+            b.Vx[a][c] = (float)m->B.Vx[a][c];
+        }
+    }
+    const adg::Phys& P = m->P;
+    adg::PhysF& f = m->Pf;
+    std::memset(&f, 0, sizeof(f));
+    f.gamma = (float)P.gamma; f.gm1 = (float)P.gm1; f.R = (float)P.R; f.invR = (float)P.invR;
+    f.mu = (float)P.mu; f.kappa = (float)P.kappa; f.g = d->gravity ? (float)P.g : 0.f;
+    f.cp = (float)P.cp; f.lamv = (float)P.lamv; f.eta_x = (float)P.eta_x; f.eta_y = (float)P.eta_y;
+    f.hx = (float)P.hx; f.hy = (float)P.hy; f.inv_hx = (float)P.inv_hx; f.inv_hy = (float)P.inv_hy;
+    f.x0 = (float)P.x0; f.y0 = (float)P.y0;
+    f.sa = (float)P.sa; f.sL = (float)P.sL; f.sU = (float)P.sU; f.sp = (float)P.sp;
+    f.gravity = P.gravity; f.source = P.source; f.nx = P.nx; f.ny = P.ny; f.bc_x = P.bc_x; f.bc_y = P.bc_y;
+    // tables
+    const size_t nn = (size_t)ny * n;
+    std::vector<double> rb(nn, 0.0), Eb(nn, 0.0);
+    std::vector<float> pb(nn, 0.f), dzr(nn, 0.f), dzE(nn, 0.f), face((size_t)ny * 2 * adg::kFaceBg, 0.f);
+    if (d->gravity) {
+        for (int iy = 0; iy < ny; ++iy) {
+            double zn[adg::kMaxN], pn[adg::kMaxN];
+            for (int j = 0; j < n; ++j) {
+                const double z = d->y0 + (iy + m->B.xi[j]) * P.hy;
+                const double ex = 1.0 - d->g * z / (P.cp * d->theta0);
+                const double p = d->p0 * std::pow(ex, P.cp / d->R);
+                const double r = p / (d->R * d->theta0 * ex);
+                zn[j] = z;
+                pn[j] = p;
+                rb[iy * n + j] = r;
+                Eb[iy * n + j] = p / P.gm1 + r * d->g * z;
+                pb[iy * n + j] = (float)p;
+            }
+            for (int j = 0; j < n; ++j) {
+                double sr = 0.0, sE = 0.0;
+                for (int p = 0; p < n; ++p) {
+                    sr += m->B.D[j][p] * rb[iy * n + p];
+                    sE += m->B.D[j][p] * Eb[iy * n + p];
+                }
+                dzr[iy * n + j] = (float)(sr * P.inv_hy);
+                dzE[iy * n + j] = (float)(sE * P.inv_hy);
+            }
+            for (int side = 0; side < 2; ++side) {  // 0: north (phi(1)), 1: south (phi(0))
+                const double* phi = side == 0 ? m->B.phi1 : m->B.phi0;
+                double r = 0.0, E = 0.0;
+                for (int j = 0; j < n; ++j) {
+                    r += phi[j] * rb[iy * n + j];
+                    E += phi[j] * Eb[iy * n + j];
+                }
+                const double zf = d->y0 + (iy + (side == 0 ? 1 : 0)) * P.hy;
+                float* fb = face.data() + ((size_t)iy * 2 + side) * adg::kFaceBg;
+                fb[0] = (float)r;
+                fb[1] = (float)E;
+                fb[2] = (float)(P.gm1 * (E - r * d->g * zf));
+            }
+            (void)zn;
+            (void)pn;
+        }
+    }
+    const size_t bytes = nn * 8 * 2 + nn * 4 * 3 + face.size() * 4;
+    if (cudaMalloc(&m->mixbuf, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ADG_ENOMEM, "create_mesh: mixed tables");
+    }
+    char* p = (char*)m->mixbuf;
+    auto put = [&](const void* src, size_t nb) {
+        void* dst = p;
+        cudaMemcpy(dst, src, nb, cudaMemcpyHostToDevice);
+        p += nb;
+        return dst;
+    };
+    m->mbg.rb = (const double*)put(rb.data(), nn * 8);
+    m->mbg.Eb = (const double*)put(Eb.data(), nn * 8);
+    m->mbg.pb = (const float*)put(pb.data(), nn * 4);
+    m->mbg.dzr = (const float*)put(dzr.data(), nn * 4);
+    m->mbg.dzE = (const float*)put(dzE.data(), nn * 4);
+    m->mbg.face = (const float*)put(face.data(), face.size() * 4);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "create_mesh: mixed tables upload");
+    return ADG_OK;
+}
+
+int set_device(const adg_mesh* m) {
+    ADG_CK(cudaSetDevice(m->d.device), "cudaSetDevice");
+    return ADG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* adg_last_error(void) { return g_err.c_str(); }
+
+int adg_create_mesh(const adg_mesh_desc* d, adg_mesh** out) {
+    if (!d || !out) return fail(ADG_EINVAL, "create_mesh: NULL argument");
+    *out = nullptr;
+    if (d->degree < 1 || d->degree > ADG_MAX_DEGREE)
+        return fail(ADG_EINVAL, "create_mesh: degree must be in [1, 7]");
+    if (d->nx < 1 || d->ny < 1) return fail(ADG_EINVAL, "create_mesh: nx, ny must be >= 1");
+    if ((long long)d->nx * d->ny > (1LL << 26)) return fail(ADG_EINVAL, "create_mesh: too many cells");
+    if (!(d->Lx > 0.0) || !(d->Ly > 0.0)) return fail(ADG_EINVAL, "create_mesh: Lx, Ly must be > 0");
+    if (d->bc_x < 0 || d->bc_x > 1 || d->bc_y < 0 || d->bc_y > 1)
+        return fail(ADG_EINVAL, "create_mesh: unknown boundary condition");
+    if (!(d->gamma > 1.0) || !(d->R > 0.0) || !(d->Pr > 0.0) || !(d->mu >= 0.0))
+        return fail(ADG_EINVAL, "create_mesh: invalid gas constants");
+    if (d->source != ADG_SRC_NONE && d->source != ADG_SRC_STEADY)
+        return fail(ADG_EINVAL, "create_mesh: unknown source");
+    if (d->source == ADG_SRC_STEADY && !(d->src_L > 0.0))
+        return fail(ADG_EINVAL, "create_mesh: steady source needs src_L > 0");
+    if (d->precision != ADG_PREC_FP64 && d->precision != ADG_PREC_MIXED)
+        return fail(ADG_EINVAL, "create_mesh: unknown precision");
+    if (d->gravity && !(d->theta0 > 0.0 && d->p0 > 0.0))
+        return fail(ADG_EINVAL, "create_mesh: gravity needs theta0 > 0 and p0 > 0");
+    int ndev = 0;
+    ADG_CK(cudaGetDeviceCount(&ndev), "cudaGetDeviceCount");
+    if (d->device < 0 || d->device >= ndev) return fail(ADG_EINVAL, "create_mesh: bad device ordinal");
+
+    adg_mesh* m = new adg_mesh();
+    m->d = *d;
+    m->N = d->degree;
+    m->n = d->degree + 1;
+    m->cells = d->nx * d->ny;
+    if (!build_basis(m->N, m->B)) {
+        delete m;
+        return fail(ADG_EINVAL, "create_mesh: singular time-stiffness matrix");
+    }
+    adg::Phys& P = m->P;
+    std::memset(&P, 0, sizeof(P));
+    P.gamma = d->gamma;
+    P.gm1 = d->gamma - 1.0;
+    P.R = d->R;
+    P.invR = 1.0 / d->R;
+    P.mu = d->mu;
+    P.cp = d->gamma * d->R / (d->gamma - 1.0);
+    P.kappa = d->mu * P.cp / d->Pr;
+    P.g = d->g;
+    P.p0 = d->p0;
+    P.theta0 = d->theta0;
+    P.Rcp = d->R / P.cp;
+    P.lamv = std::fmax(4.0 / 3.0, d->gamma / d->Pr) * d->mu;
+    P.hx = d->Lx / d->nx;
+    P.hy = d->Ly / d->ny;
+    P.inv_hx = 1.0 / P.hx;
+    P.inv_hy = 1.0 / P.hy;
+    P.x0 = d->x0;
+    P.y0 = d->y0;
+    P.eta_x = (2.0 * m->N + 1.0) / (P.hx * std::sqrt(M_PI / 2.0));
+    P.eta_y = (2.0 * m->N + 1.0) / (P.hy * std::sqrt(M_PI / 2.0));
+    P.gravity = d->gravity ? 1 : 0;
+    P.source = d->source;
+    P.sa = d->src_a;
+    P.sL = d->src_L;
+    P.sU = d->src_U;
+    P.sp = d->src_p;
+    P.nx = d->nx;
+    P.ny = d->ny;
+    P.bc_x = d->bc_x;
+    P.bc_y = d->bc_y;
+
+    int rc = set_device(m);
+    if (rc) { delete m; return rc; }
+    const size_t cnt = (size_t)m->cells * m->n * m->n * 4;
+    const size_t tr = (size_t)m->cells * 4 * adg::kTraceComps * m->n;
+    int nb = 0;
+    adg::launch_max_speed(m->N, nullptr, nullptr, m->cells, m->B, m->P, &nb, nullptr);
+    m->speed_blocks = nb;
+    const size_t nbg = 2 * (size_t)d->ny * m->n + 2 * (size_t)(d->ny + 1);
+    if (cudaMalloc(&m->u, cnt * 8) != cudaSuccess || cudaMalloc(&m->rvol, cnt * 8) != cudaSuccess ||
+        cudaMalloc(&m->trace, tr * 8) != cudaSuccess || cudaMalloc(&m->tv, (size_t)m->cells * 8) != cudaSuccess ||
+        cudaMalloc(&m->stats, 2 * 8) != cudaSuccess || cudaMalloc(&m->speed, (size_t)nb * 8) != cudaSuccess ||
+        cudaMalloc(&m->flag, sizeof(int)) != cudaSuccess || cudaMalloc(&m->bgbuf, nbg * 8) != cudaSuccess) {
+        cudaGetLastError();
+        free_mesh(m);
+        return fail(ADG_ENOMEM, "create_mesh: device allocation failed");
+    }
+    // hydrostatic background tables (Eq. 6, isentropic reading): zero without gravity
+    std::vector<double> h(nbg, 0.0);
+    double* pn = h.data();
+    double* rn = pn + (size_t)d->ny * m->n;
+    double* pf = rn + (size_t)d->ny * m->n;
+    double* rf = pf + (d->ny + 1);
+    if (d->gravity) {
+        auto bgp = [&](double z, double& pb, double& rb) {
+            const double ex = 1.0 - d->g * z / (P.cp * d->theta0);
+            pb = d->p0 * std::pow(ex, P.cp / d->R);
+            rb = pb / (d->R * d->theta0 * ex);
+        };
+        for (int iy = 0; iy < d->ny; ++iy)
+            for (int j = 0; j < m->n; ++j)
+                bgp(d->y0 + (iy + m->B.xi[j]) * P.hy, pn[iy * m->n + j], rn[iy * m->n + j]);
+        for (int f = 0; f <= d->ny; ++f) bgp(d->y0 + f * P.hy, pf[f], rf[f]);
+    }
+    if (cudaMemcpy(m->bgbuf, h.data(), nbg * 8, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(m->u, 0, cnt * 8) != cudaSuccess) {
+        cudaError_t e = cudaGetLastError();
+        free_mesh(m);
+        return cuda_fail(e, "create_mesh: upload");
+    }
+    if (d->precision == ADG_PREC_MIXED) {
+        int rc2 = build_mixed(m);
+        if (rc2) {
+            free_mesh(m);
+            return rc2;
+        }
+    }
+    m->bg.pbar_node = m->bgbuf;
+    m->bg.rhobar_node = m->bgbuf + (size_t)d->ny * m->n;
+    m->bg.pbar_face = m->bgbuf + 2 * (size_t)d->ny * m->n;
+    m->bg.rhobar_face = m->bg.pbar_face + (d->ny + 1);
+    *out = m;
+    return ADG_OK;
+}
+
+void adg_destroy_mesh(adg_mesh* m) {
+    if (!m) return;
+    cudaSetDevice(m->d.device);
+    cudaDeviceSynchronize();
+    free_mesh(m);
+}
+
+size_t adg_state_count(const adg_mesh* m) {
+    return m ? (size_t)m->cells * m->n * m->n * 4 : 0;
+}
+
+int adg_set_state(adg_mesh* m, const double* u, size_t count, int on_device, void* stream) {
+    if (!m || !u) return fail(ADG_EINVAL, "set_state: NULL argument");
+    if (count != adg_state_count(m)) return fail(ADG_EINVAL, "set_state: count != cells*(N+1)^2*4");
+    if (int rc = set_device(m)) return rc;
+    ADG_CK(cudaMemcpyAsync(m->u, u, count * 8, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                           (cudaStream_t)stream), "set_state");
+    m->predicted = false;
+    return ADG_OK;
+}
+
+int adg_get_state(adg_mesh* m, double* u, size_t count, int on_device, void* stream) {
+    if (!m || !u) return fail(ADG_EINVAL, "get_state: NULL argument");
+    if (count != adg_state_count(m)) return fail(ADG_EINVAL, "get_state: count != cells*(N+1)^2*4");
+    if (int rc = set_device(m)) return rc;
+    ADG_CK(cudaMemcpyAsync(u, m->u, count * 8, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                           (cudaStream_t)stream), "get_state");
+    if (!on_device) ADG_CK(cudaStreamSynchronize((cudaStream_t)stream), "get_state sync");
+    return ADG_OK;
+}
+
+int adg_set_time(adg_mesh* m, double t) {
+    if (!m) return fail(ADG_EINVAL, "set_time: NULL mesh");
+    m->t = t;
+    return ADG_OK;
+}
+
+double adg_get_time(const adg_mesh* m) { return m ? m->t : 0.0; }
+
+int adg_init_scenario(adg_mesh* m, const adg_scenario* s, void* stream) {
+    if (!m || !s) return fail(ADG_EINVAL, "init_scenario: NULL argument");
+    if (s->kind < ADG_SCEN_STEADY || s->kind > ADG_SCEN_BACKGROUND)
+        return fail(ADG_EINVAL, "init_scenario: unknown scenario");
+    if (s->kind != ADG_SCEN_STEADY && !m->d.gravity)
+        return fail(ADG_EINVAL, "init_scenario: bubble scenarios need gravity");
+    if (s->kind == ADG_SCEN_STEADY && m->d.source != ADG_SRC_STEADY)
+        return fail(ADG_EINVAL, "init_scenario: steady field needs the steady source");
+    if (s->kind == ADG_SCEN_COSINE && !(s->a > 0.0))
+        return fail(ADG_EINVAL, "init_scenario: cosine bubble radius must be > 0");
+    if (int rc = set_device(m)) return rc;
+    int e = adg::launch_init_scenario(m->N, m->u, m->cells, s->kind, s->A, s->a, s->xc, s->zc, m->B, m->P, stream);
+    if (e) return cuda_fail((cudaError_t)e, "init_scenario");
+    m->predicted = false;
+    m->t = 0.0;
+    return ADG_OK;
+}
+
+int adg_predictor(adg_mesh* m, double dt, void* stream) {
+    if (!m) return fail(ADG_EINVAL, "predictor: NULL mesh");
+    if (!(dt > 0.0) || !std::isfinite(dt)) return fail(ADG_EINVAL, "predictor: dt must be finite and > 0");
+    if (int rc = set_device(m)) return rc;
+    int e;
+    if (m->d.precision == ADG_PREC_FP64)
+        e = adg::launch_predictor_fp64(m->N, m->u, m->rvol, m->trace, m->cells, dt, m->t, m->B, m->P, m->bg, stream);
+    else
+        e = adg::launch_predictor_mixed(m->N, m->u, (float*)m->rvol, (float*)m->trace, m->cells, dt, m->Bf,
+                                        m->Pf, m->mbg, stream);
+    if (e) return cuda_fail((cudaError_t)e, "predictor launch");
+    m->predicted = true;
+    m->pred_dt = dt;
+    return ADG_OK;
+}
+
+int adg_corrector(adg_mesh* m, double dt, void* stream) {
+    if (!m) return fail(ADG_EINVAL, "corrector: NULL mesh");
+    if (!m->predicted || m->pred_dt != dt)
+        return fail(ADG_ESTATE, "corrector: needs a preceding predictor with the same dt");
+    if (int rc = set_device(m)) return rc;
+    int e = m->d.precision == ADG_PREC_FP64
+                ? adg::launch_corrector_fp64(m->N, m->u, m->rvol, m->trace, m->cells, dt, m->B, m->P, m->bg, stream)
+                : adg::launch_corrector_mixed(m->N, m->u, (const float*)m->rvol, (const float*)m->trace, m->cells,
+                                              dt, m->Bf, m->Pf, m->mbg, stream);
+    if (e) return cuda_fail((cudaError_t)e, "corrector launch");
+    m->predicted = false;
+    return ADG_OK;
+}
+
+int adg_step(adg_mesh* m, double dt, void* stream) {
+    int rc = adg_predictor(m, dt, stream);
+    if (rc) return rc;
+    rc = adg_corrector(m, dt, stream);
+    if (rc) return rc;
+    m->t += dt;
+    return ADG_OK;
+}
+
+int adg_stable_dt(adg_mesh* m, double cfl, double* dt, void* stream) {
+    if (!m || !dt) return fail(ADG_EINVAL, "stable_dt: NULL argument");
+    if (!(cfl > 0.0)) return fail(ADG_EINVAL, "stable_dt: cfl must be > 0");
+    if (int rc = set_device(m)) return rc;
+    int nb = 0;
+    int e = adg::launch_max_speed(m->N, m->u, m->speed, m->cells, m->B, m->P, &nb, stream);
+    if (e) return cuda_fail((cudaError_t)e, "stable_dt launch");
+    std::vector<double> h(nb);
+    ADG_CK(cudaMemcpyAsync(h.data(), m->speed, nb * 8, cudaMemcpyDeviceToHost, (cudaStream_t)stream), "stable_dt copy");
+    ADG_CK(cudaStreamSynchronize((cudaStream_t)stream), "stable_dt sync");
+    double lam = 0.0;
+    for (double v : h) lam = std::fmax(lam, v);
+    if (!(lam > 0.0) || !std::isfinite(lam) || lam >= 1e300)
+        return fail(ADG_ENONFINITE, "stable_dt: non-finite or non-positive wave speed");
+    const double hmin = std::fmin(m->P.hx, m->P.hy);
+    *dt = cfl * hmin / (2.0 * (2.0 * m->N + 1.0) * lam);
+    return ADG_OK;
+}
+
+int adg_tv_indicator(adg_mesh* m, int var, double T_r, double T_c, double* tv, int8_t* flags,
+                     double* stats, void* stream) {
+    if (!m) return fail(ADG_EINVAL, "tv_indicator: NULL mesh");
+    if (var != ADG_TV_RHO && var != ADG_TV_THETA) return fail(ADG_EINVAL, "tv_indicator: unknown variable");
+    if (var == ADG_TV_THETA && !m->d.gravity)
+        return fail(ADG_EINVAL, "tv_indicator: theta needs the atmosphere constants (gravity on)");
+    if (!(T_r > T_c)) return fail(ADG_EINVAL, "tv_indicator: needs T_r > T_c");
+    if (int rc = set_device(m)) return rc;
+    double* tvbuf = tv ? tv : m->tv;
+    int e = adg::launch_tv_cells(m->N, m->u, tvbuf, m->cells, var, m->B, m->P, stream);
+    if (e) return cuda_fail((cudaError_t)e, "tv_indicator cells");
+    e = adg::launch_tv_stats(tvbuf, m->cells, T_r, T_c, m->stats, flags, stream);
+    if (e) return cuda_fail((cudaError_t)e, "tv_indicator stats");
+    if (stats) {
+        ADG_CK(cudaMemcpyAsync(stats, m->stats, 16, cudaMemcpyDeviceToHost, (cudaStream_t)stream), "tv stats copy");
+        ADG_CK(cudaStreamSynchronize((cudaStream_t)stream), "tv stats sync");
+    }
+    return ADG_OK;
+}
+
+int adg_check_finite(adg_mesh* m, void* stream) {
+    if (!m) return fail(ADG_EINVAL, "check_finite: NULL mesh");
+    if (int rc = set_device(m)) return rc;
+    ADG_CK(cudaMemsetAsync(m->flag, 0, sizeof(int), (cudaStream_t)stream), "check_finite memset");
+    int e = adg::launch_check_finite(m->u, adg_state_count(m), m->flag, stream);
+    if (e) return cuda_fail((cudaError_t)e, "check_finite launch");
+    int h = 0;
+    ADG_CK(cudaMemcpyAsync(&h, m->flag, sizeof(int), cudaMemcpyDeviceToHost, (cudaStream_t)stream), "check_finite copy");
+    ADG_CK(cudaStreamSynchronize((cudaStream_t)stream), "check_finite sync");
+    return h ? fail(ADG_ENONFINITE, "state contains NaN or Inf") : ADG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,101 @@
+// Internal declarations shared by the translation units of libaderdg
+// (not part of the C ABI).
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <string>
+
+#include "../../include/aderdg.h"
+
+namespace adg {
+
+constexpr int kMaxN = ADG_MAX_DEGREE + 1;  // nodes per direction
+
+// One-dimensional operators of the degree-N nodal Gauss-Legendre basis on
+// [0, 1], passed to kernels by value (lands in the constant bank).
+struct Basis {
+    int n;
+    double xi[kMaxN];         // nodes
+    double w[kMaxN];          // weights, sum 1
+    double phi0[kMaxN];       // phi_j(0)
+    double phi1[kMaxN];       // phi_j(1)
+    double D[kMaxN][kMaxN];   // D[i][j] = phi_j'(xi_i)
+    double Kw[kMaxN][kMaxN];  // (K1^{-1})[l][k] * w_k  (time update of the predictor)
+    double Kw1[kMaxN];        // sum_k Kw[l][k] (first sweep: time-constant residual)
+    double Vx[kMaxN][kMaxN];  // Vx[p][i] = w_p D[p][i] / w_i (weak volume term)
+    double lift0[kMaxN];      // phi_i(0) / w_i
+    double lift1[kMaxN];      // phi_i(1) / w_i
+};
+
+// Physical and mesh constants of one mesh.
+struct Phys {
+    double gamma, gm1, R, invR, mu, kappa, g, cp, p0, theta0, Rcp;
+    double lamv;              // max(4/3, gamma/Pr) * mu  (viscous eigenvalue * rho)
+    double eta_x, eta_y;      // (2N+1) / (h sqrt(pi/2)) per direction
+    double hx, hy, inv_hx, inv_hy, x0, y0;
+    int gravity;
+    int source;
+    double sa, sL, sU, sp;    // steady manufactured source parameters
+    int nx, ny, bc_x, bc_y;
+};
+
+// Per-mesh device tables of the hydrostatic background (zero without gravity).
+struct Background {
+    const double* pbar_node;    // [ny][n]  at node heights y0 + (iy + xi_j) hy
+    const double* rhobar_node;  // [ny][n]
+    const double* pbar_face;    // [ny+1]   at face heights y0 + f hy
+    const double* rhobar_face;  // [ny+1]
+};
+
+// Trace record per face node: q-bar(4), normal flux(4), qx-bar(4), qy-bar(4), s(1)
+constexpr int kTraceComps = 17;
+
+// FP32 copies of the basis and constants for the mixed-precision kernels.
+struct BasisF {
+    float xi[kMaxN], w[kMaxN], phi0[kMaxN], phi1[kMaxN];
+    float D[kMaxN][kMaxN], Kw[kMaxN][kMaxN], Kw1[kMaxN], Vx[kMaxN][kMaxN];
+    float lift0[kMaxN], lift1[kMaxN];
+};
+
+struct PhysF {
+    float gamma, gm1, R, invR, mu, kappa, g, cp, lamv, eta_x, eta_y;
+    float hx, hy, inv_hx, inv_hy, x0, y0;
+    float sa, sL, sU, sp;
+    int gravity, source, nx, ny, bc_x, bc_y;
+};
+
+// Background tables of the mixed path (zero without gravity).  Node tables
+// are indexed [iy * n + j]; face table [iy][0: north, 1: south][kFaceBg].
+constexpr int kFaceBg = 3;  // rhobar, Ebar, pbar at the face (extrapolated nodal background)
+struct MixedBg {
+    const double* rb;   // rhobar at nodes (FP64, for the perturbation split)
+    const double* Eb;   // Ebar = pbar/(gamma-1) + rhobar g z at nodes (FP64)
+    const float* pb;    // pbar at nodes
+    const float* dzr;   // d rhobar/dz of the nodal interpolant
+    const float* dzE;   // d Ebar/dz of the nodal interpolant
+    const float* face;  // [ny][2][kFaceBg]
+};
+
+// Kernel launchers (adg_fp64.cu, adg_mixed.cu, adg_tv.cu).  They return a
+// cudaError_t value as int.
+int launch_predictor_fp64(int N, const double* u, double* rvol, double* trace, int cells,
+                          double dt, double t, const Basis& B, const Phys& P,
+                          const Background& bg, void* stream);
+int launch_corrector_fp64(int N, double* u, const double* rvol, const double* trace, int cells,
+                          double dt, const Basis& B, const Phys& P, const Background& bg,
+                          void* stream);
+int launch_predictor_mixed(int N, const double* u, float* rvol, float* trace, int cells, double dt,
+                           const BasisF& B, const PhysF& P, const MixedBg& bg, void* stream);
+int launch_corrector_mixed(int N, double* u, const float* rvol, const float* trace, int cells,
+                           double dt, const BasisF& B, const PhysF& P, const MixedBg& bg, void* stream);
+int launch_tv_cells(int N, const double* u, double* tv, int cells, int var, const Basis& B,
+                    const Phys& P, void* stream);
+int launch_tv_stats(const double* tv, int cells, double T_r, double T_c, double* stats_dev,
+                    int8_t* flags, void* stream);
+int launch_max_speed(int N, const double* u, double* partial, int cells, const Basis& B,
+                     const Phys& P, int* nblocks_out, void* stream);
+int launch_init_scenario(int N, double* u, int cells, int kind, double A, double a, double xc,
+                         double zc, const Basis& B, const Phys& P, void* stream);
+int launch_check_finite(const double* u, size_t count, int* flag, void* stream);
+
+}  // namespace adg

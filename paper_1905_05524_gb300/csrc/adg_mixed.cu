@@ -1,0 +1,480 @@
+// Mixed-precision ADER-DG predictor and corrector for sm_103a.
+//
+// Same scheme as adg_fp64.cu (Sec. 3: Picard space-time predictor, Rusanov-
+// type viscous corrector), with the arithmetic split by what it needs:
+//
+//  * FP64: the perturbation split against the hydrostatic background,
+//    u' = u - ubar(z) (rho and rhoE: this is where rhoE cancels against the
+//    background energy, Eqs. 2, 6, 7), and the corrector's accumulation
+//    u^{n+1} = u^n + dt * du.
+//  * FP32: everything between -- the Picard sweeps on the perturbation
+//    q' = q - ubar, the contractions (gradients, flux divergence, time
+//    update), the point-wise fluxes and the face traces/Riemann fluxes.
+//    The pressure perturbation is formed directly from perturbations,
+//        p' = (gamma-1) (rhoE' - |rho v|^2 / (2 rho) - g z rho'),
+//    which is exact algebra (pbar = (gamma-1)(Ebar - rhobar g z)), so no FP32
+//    quantity ever carries the large background values through a difference.
+//  * Background gradients: the nodal derivative of the interpolated background
+//    (rhobar, Ebar) is formed once in FP64 on the host and added in FP32.
+//
+// Without gravity the background is zero and q' is the full state.
+#include <cuda_runtime.h>
+
+#include "adg_internal.h"
+
+namespace adg {
+
+struct FluxF {
+    float F[4], G[4], S[4];
+};
+
+// Point-wise flux from perturbation variables qp (rho', m, m, E'), full
+// gradients (gx, gy), background (rb, Eb, pb) at height z.
+__device__ __forceinline__ void ns_flux_pert(const float qp[4], const float gx[4], const float gy[4],
+                                             float z, float rb, float Eb, float pb, const PhysF& P,
+                                             FluxF& o, bool use_heat = false, float hTy = 0.f) {
+    const float rho = rb + qp[0];
+    const float mx = qp[1], my = qp[2];
+    const float rinv = __frcp_rn(rho);
+    const float u = mx * rinv, v = my * rinv;
+    const float gz = P.g * z;
+    const float pp = P.gm1 * (qp[3] - 0.5f * (mx * u + my * v) - gz * qp[0]);
+    const float p = pb + pp;
+    const float E = Eb + qp[3];
+    const float T = p * rinv * P.invR;
+    const float ux = (gx[1] - u * gx[0]) * rinv;
+    const float uy = (gy[1] - u * gy[0]) * rinv;
+    const float vx = (gx[2] - v * gx[0]) * rinv;
+    const float vy = (gy[2] - v * gy[0]) * rinv;
+    const float kin = 0.5f * (u * u + v * v);
+    float Tx, Ty;
+    if (use_heat) {
+        Tx = 0.f;
+        Ty = hTy;
+    } else {
+        const float px = P.gm1 * (gx[3] - (u * gx[1] + v * gx[2]) + kin * gx[0] - gz * gx[0]);
+        const float py = P.gm1 * (gy[3] - (u * gy[1] + v * gy[2]) + kin * gy[0] - gz * gy[0] - rho * P.g);
+        Tx = (px - P.R * T * gx[0]) * rinv * P.invR;
+        Ty = (py - P.R * T * gy[0]) * rinv * P.invR;
+    }
+    const float div = ux + vy;
+    const float sxx = P.mu * ((2.f / 3.f) * div - 2.f * ux);
+    const float syy = P.mu * ((2.f / 3.f) * div - 2.f * vy);
+    const float sxy = -P.mu * (uy + vx);
+    const float Ep = E + p;
+    o.F[0] = mx;
+    o.F[1] = mx * u + pp + sxx;
+    o.F[2] = my * u + sxy;
+    o.F[3] = u * Ep + u * sxx + v * sxy - P.kappa * Tx;
+    o.G[0] = my;
+    o.G[1] = mx * v + sxy;
+    o.G[2] = my * v + pp + syy;
+    o.G[3] = v * Ep + u * sxy + v * syy - P.kappa * Ty;
+    o.S[0] = 0.f;
+    o.S[1] = 0.f;
+    o.S[2] = -P.g * qp[0];
+    o.S[3] = 0.f;
+}
+
+__device__ __forceinline__ float wave_speed_f(float rho, float mx, float my, float pp, float pb,
+                                              bool xdir, const PhysF& P) {
+    const float rinv = __frcp_rn(rho);
+    const float c = sqrtf(P.gamma * (pb + pp) * rinv);
+    const float vn = fabsf((xdir ? mx : my) * rinv);
+    return vn + c + 2.f * (xdir ? P.eta_x : P.eta_y) * P.lamv * rinv;
+}
+
+template <int N>
+struct MixCfg {
+    static constexpr int n = N + 1;
+    static constexpr int cpb = N == 1 ? 32 : N == 2 ? 16 : N == 3 ? 8 : N <= 5 ? 4 : 2;
+    static constexpr int threads = cpb * n * n;
+    static constexpr size_t smem_pred = (size_t)cpb * 3 * n * 4 * n * n * sizeof(float);
+};
+
+template <int N, int CPB>
+__global__ void __launch_bounds__(CPB*(N + 1) * (N + 1))
+k_predictor_mixed(const double* __restrict__ u, float* __restrict__ rvol, float* __restrict__ trace,
+                  int cells, float dt, const BasisF B, const PhysF P, const MixedBg bg) {
+    constexpr int n = N + 1, n2 = n * n, SL = 4 * n2;
+    extern __shared__ float smf[];
+    const int cl = threadIdx.x / n2;
+    const int node = threadIdx.x - cl * n2;
+    const int j = node / n, i = node - j * n;
+    const int cell_raw = blockIdx.x * CPB + cl;
+    const bool active = cell_raw < cells;
+    const int cell = active ? cell_raw : cells - 1;
+    float* Q = smf + (size_t)cl * (3 * n * SL);
+    float* Fs = Q + n * SL;
+    float* Gs = Fs + n * SL;
+    const int ix = cell % P.nx, iy = cell / P.nx;
+    const int row = iy * n + j;
+    const float x = P.x0 + (ix + B.xi[i]) * P.hx;
+    const float z = P.y0 + (iy + B.xi[j]) * P.hy;
+    (void)x;
+    const float rb = (float)bg.rb[row], Eb = (float)bg.Eb[row], pb = bg.pb[row];
+    const float dzr = bg.dzr[row], dzE = bg.dzE[row];
+
+    // FP64 perturbation split, then FP32 from here on
+    float up[4];
+    const double* uc = u + (size_t)cell * SL;
+    up[0] = (float)(uc[node] - bg.rb[row]);
+    up[1] = (float)uc[n2 + node];
+    up[2] = (float)uc[2 * n2 + node];
+    up[3] = (float)(uc[3 * n2 + node] - bg.Eb[row]);
+#pragma unroll
+    for (int v = 0; v < 4; ++v) Q[v * n2 + node] = up[v];
+    float Sm[4] = {0.f, 0.f, 0.f, 0.f};
+    if (P.source == ADG_SRC_STEADY) {
+        const float k = 6.283185307179586f / P.sL;
+        float sn, cs;
+        sincosf(k * (x + z), &sn, &cs);
+        const float a = P.sa, U = P.sU;
+        const float rho = 1.f + a * sn;
+        const float c = 2.f * U * a * k * cs;
+        const float lapT = (2.f * P.sp * P.invR) * (a * k * k * sn / (rho * rho) +
+                                                    2.f * a * a * k * k * cs * cs / (rho * rho * rho));
+        Sm[0] = c;
+        Sm[1] = c * U;
+        Sm[2] = c * U;
+        Sm[3] = c * U * U - P.kappa * lapT;
+    }
+    __syncthreads();
+
+    auto eval_node = [&](const float* Qk, float q[4], float gx[4], float gy[4], FluxF& f) {
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const float* Qv = Qk + v * n2;
+            q[v] = Qv[node];
+            float sx = 0.f, sy = 0.f;
+#pragma unroll
+            for (int p = 0; p < n; ++p) {
+                sx = fmaf(B.D[i][p], Qv[j * n + p], sx);
+                sy = fmaf(B.D[j][p], Qv[p * n + i], sy);
+            }
+            gx[v] = sx * P.inv_hx;
+            gy[v] = sy * P.inv_hy;
+        }
+        gy[0] += dzr;
+        gy[3] += dzE;
+        ns_flux_pert(q, gx, gy, z, rb, Eb, pb, P, f);
+    };
+    auto divergence = [&](int k, int v) {
+        const float* Fv = Fs + k * SL + v * n2;
+        const float* Gv = Gs + k * SL + v * n2;
+        float sx = 0.f, sy = 0.f;
+#pragma unroll
+        for (int p = 0; p < n; ++p) {
+            sx = fmaf(B.D[i][p], Fv[j * n + p], sx);
+            sy = fmaf(B.D[j][p], Gv[p * n + i], sy);
+        }
+        return -(sx * P.inv_hx + sy * P.inv_hy);
+    };
+
+    {  // sweep 1: iterate constant in time
+        float q[4], gx[4], gy[4];
+        FluxF f;
+        eval_node(Q, q, gx, gy, f);
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            Fs[v * n2 + node] = f.F[v];
+            Gs[v * n2 + node] = f.G[v];
+        }
+        __syncthreads();
+        float R0[4];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) R0[v] = f.S[v] + Sm[v] + divergence(0, v);
+#pragma unroll
+        for (int l = 0; l < n; ++l) {
+#pragma unroll
+            for (int v = 0; v < 4; ++v) Q[l * SL + v * n2 + node] = fmaf(dt, B.Kw1[l] * R0[v], up[v]);
+        }
+        __syncthreads();
+    }
+#pragma unroll 1
+    for (int r = 1; r < n; ++r) {
+        float R[n][4];
+#pragma unroll
+        for (int k = 0; k < n; ++k) {
+            float q[4], gx[4], gy[4];
+            FluxF f;
+            eval_node(Q + k * SL, q, gx, gy, f);
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                Fs[k * SL + v * n2 + node] = f.F[v];
+                Gs[k * SL + v * n2 + node] = f.G[v];
+                R[k][v] = f.S[v] + Sm[v];
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < n; ++k) {
+#pragma unroll
+            for (int v = 0; v < 4; ++v) R[k][v] += divergence(k, v);
+        }
+#pragma unroll
+        for (int l = 0; l < n; ++l) {
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                float acc = 0.f;
+#pragma unroll
+                for (int k = 0; k < n; ++k) acc = fmaf(B.Kw[l][k], R[k][v], acc);
+                Q[l * SL + v * n2 + node] = fmaf(dt, acc, up[v]);
+            }
+        }
+        __syncthreads();
+    }
+
+    float qb[4], Fb[4], Gb[4], Sb[4], qxb[4], qyb[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) qb[v] = Fb[v] = Gb[v] = Sb[v] = qxb[v] = qyb[v] = 0.f;
+#pragma unroll
+    for (int k = 0; k < n; ++k) {
+        float q[4], gx[4], gy[4];
+        FluxF f;
+        eval_node(Q + k * SL, q, gx, gy, f);
+        const float wk = B.w[k];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            qb[v] = fmaf(wk, q[v], qb[v]);
+            Fb[v] = fmaf(wk, f.F[v], Fb[v]);
+            Gb[v] = fmaf(wk, f.G[v], Gb[v]);
+            Sb[v] = fmaf(wk, f.S[v] + Sm[v], Sb[v]);
+            qxb[v] = fmaf(wk, gx[v], qxb[v]);
+            qyb[v] = fmaf(wk, gy[v], qyb[v]);  // full y-gradient (background included)
+        }
+    }
+    __syncthreads();
+    float* A = Q;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+        A[0 * SL + v * n2 + node] = qb[v];
+        A[1 * SL + v * n2 + node] = Fb[v];
+        A[2 * SL + v * n2 + node] = Gb[v];
+        A[3 * SL + v * n2 + node] = qxb[v];
+        A[4 * SL + v * n2 + node] = qyb[v];
+    }
+    __syncthreads();
+    if (active) {
+        float* rc = rvol + (size_t)cell * SL;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            float sx = 0.f, sy = 0.f;
+#pragma unroll
+            for (int p = 0; p < n; ++p) {
+                sx = fmaf(B.Vx[p][i], A[1 * SL + v * n2 + j * n + p], sx);
+                sy = fmaf(B.Vx[p][j], A[2 * SL + v * n2 + p * n + i], sy);
+            }
+            rc[v * n2 + node] = sx * P.inv_hx + sy * P.inv_hy + Sb[v];
+        }
+    }
+    for (int idx = node; idx < 4 * n; idx += n2) {
+        const int f = idx / n, m = idx - f * n;
+        const bool xface = f < 2;
+        const float* phi = (f == 0 || f == 2) ? B.phi1 : B.phi0;
+        float rec[kTraceComps];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int slot = c == 0 ? 0 : c == 1 ? (xface ? 1 : 2) : (c == 2 ? 3 : 4);
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                const float* S = A + slot * SL + v * n2;
+                float s = 0.f;
+#pragma unroll
+                for (int p = 0; p < n; ++p) s = fmaf(phi[p], xface ? S[m * n + p] : S[p * n + m], s);
+                rec[c * 4 + v] = s;
+            }
+        }
+        // background at the face node: nodal values on x-faces, extrapolated on y-faces
+        float rbf, pbf;
+        if (xface) {
+            rbf = (float)bg.rb[iy * n + m];
+            pbf = bg.pb[iy * n + m];
+        } else {
+            const float* fb = bg.face + ((size_t)iy * 2 + (f == 2 ? 0 : 1)) * kFaceBg;
+            rbf = fb[0];
+            pbf = fb[2];
+        }
+        const float zf = xface ? P.y0 + (iy + B.xi[m]) * P.hy : P.y0 + (iy + (f == 2 ? 1 : 0)) * P.hy;
+        const float rho = rbf + rec[0];
+        const float rinv = __frcp_rn(rho);
+        const float pp = P.gm1 * (rec[3] - 0.5f * (rec[1] * rec[1] + rec[2] * rec[2]) * rinv - P.g * zf * rec[0]);
+        rec[16] = wave_speed_f(rho, rec[1], rec[2], pp, pbf, xface, P);
+        if (active) {
+            float* tr = trace + ((size_t)cell * 4 + f) * kTraceComps * n;
+#pragma unroll
+            for (int c = 0; c < kTraceComps; ++c) tr[c * n + m] = rec[c];
+        }
+    }
+}
+
+// Slip-wall ghost (Eq. 10 reading) in perturbation variables: rho' = rhoE' = 0
+// (the background), momentum reflected, interior gradients, background heat flux.
+__device__ __forceinline__ void wall_ghost_f(const float* rec, int f, float z, float rb, float Eb,
+                                             float pb, float dzr, float dzE, const PhysF& P,
+                                             float qG[4], float fG[4], float& sG) {
+    const float nx = f == 0 ? 1.f : f == 1 ? -1.f : 0.f;
+    const float ny = f == 2 ? 1.f : f == 3 ? -1.f : 0.f;
+    const float mn = rec[1] * nx + rec[2] * ny;
+    qG[0] = P.gravity ? 0.f : rec[0];
+    qG[1] = rec[1] - 2.f * mn * nx;
+    qG[2] = rec[2] - 2.f * mn * ny;
+    qG[3] = P.gravity ? 0.f : rec[3];
+    float gx[4], gy[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+        gx[v] = rec[8 + v];
+        gy[v] = rec[12 + v];
+    }
+    (void)dzr;
+    (void)dzE;
+    FluxF fl;
+    ns_flux_pert(qG, gx, gy, z, rb, Eb, pb, P, fl, true, P.gravity ? -P.g / P.cp : 0.f);
+    const bool xdir = f < 2;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) fG[v] = xdir ? fl.F[v] : fl.G[v];
+    const float rho = rb + qG[0];
+    const float rinv = __frcp_rn(rho);
+    const float pp = P.gm1 * (qG[3] - 0.5f * (qG[1] * qG[1] + qG[2] * qG[2]) * rinv - P.g * z * qG[0]);
+    sG = wave_speed_f(rho, qG[1], qG[2], pp, pb, xdir, P);
+}
+
+__device__ __forceinline__ void rusanov_f(const float qL[4], const float fL[4], float sL,
+                                          const float qR[4], const float fR[4], float sR, float out[4]) {
+    const float hs = __fmul_rn(-0.5f, fmaxf(sL, sR));
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+        const float avg = __fmul_rn(0.5f, __fadd_rn(fL[v], fR[v]));
+        out[v] = __fmaf_rn(hs, __fsub_rn(qR[v], qL[v]), avg);
+    }
+}
+
+template <int N, int CPB>
+__global__ void __launch_bounds__(CPB*(N + 1) * (N + 1))
+k_corrector_mixed(double* __restrict__ u, const float* __restrict__ rvol,
+                  const float* __restrict__ trace, int cells, double dt, const BasisF B,
+                  const PhysF P, const MixedBg bg) {
+    constexpr int n = N + 1, n2 = n * n, SL = 4 * n2, TR = kTraceComps * n;
+    __shared__ float Fst[CPB][4][4][n];
+    const int cl = threadIdx.x / n2;
+    const int node = threadIdx.x - cl * n2;
+    const int j = node / n, i = node - j * n;
+    const int cell_raw = blockIdx.x * CPB + cl;
+    const bool active = cell_raw < cells;
+    const int cell = active ? cell_raw : cells - 1;
+    const int ix = cell % P.nx, iy = cell / P.nx;
+
+    for (int idx = node; idx < 4 * n; idx += n2) {
+        const int f = idx / n, m = idx - f * n;
+        const bool xface = f < 2;
+        const bool wall = xface ? (P.bc_x == ADG_BC_WALL && ((f == 0 && ix == P.nx - 1) || (f == 1 && ix == 0)))
+                                : (P.bc_y == ADG_BC_WALL && ((f == 2 && iy == P.ny - 1) || (f == 3 && iy == 0)));
+        const float* own = trace + ((size_t)cell * 4 + f) * TR;
+        float rec[kTraceComps];
+#pragma unroll
+        for (int c = 0; c < kTraceComps; ++c) rec[c] = own[c * n + m];
+        float qo[4] = {rec[0], rec[1], rec[2], rec[3]};
+        float fo[4] = {rec[4], rec[5], rec[6], rec[7]};
+        const float so = rec[16];
+        float qn[4], fn[4], sn;
+        if (wall) {
+            float z, rb, Eb, pb;
+            if (xface) {
+                z = P.y0 + (iy + B.xi[m]) * P.hy;
+                rb = (float)bg.rb[iy * n + m];
+                Eb = (float)bg.Eb[iy * n + m];
+                pb = bg.pb[iy * n + m];
+            } else {
+                z = P.y0 + (iy + (f == 2 ? 1 : 0)) * P.hy;
+                const float* fb = bg.face + ((size_t)iy * 2 + (f == 2 ? 0 : 1)) * kFaceBg;
+                rb = fb[0];
+                Eb = fb[1];
+                pb = fb[2];
+            }
+            wall_ghost_f(rec, f, z, rb, Eb, pb, 0.f, 0.f, P, qn, fn, sn);
+        } else {
+            int nb, nf;
+            if (f == 0) { nb = iy * P.nx + (ix + 1 == P.nx ? 0 : ix + 1); nf = 1; }
+            else if (f == 1) { nb = iy * P.nx + (ix == 0 ? P.nx - 1 : ix - 1); nf = 0; }
+            else if (f == 2) { nb = (iy + 1 == P.ny ? 0 : iy + 1) * P.nx + ix; nf = 3; }
+            else { nb = (iy == 0 ? P.ny - 1 : iy - 1) * P.nx + ix; nf = 2; }
+            const float* ot = trace + ((size_t)nb * 4 + nf) * TR;
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                qn[v] = ot[v * n + m];
+                fn[v] = ot[(4 + v) * n + m];
+            }
+            sn = ot[16 * n + m];
+        }
+        float out[4];
+        if (f == 0 || f == 2) rusanov_f(qo, fo, so, qn, fn, sn, out);
+        else rusanov_f(qn, fn, sn, qo, fo, so, out);
+#pragma unroll
+        for (int v = 0; v < 4; ++v) Fst[cl][f][v][m] = out[v];
+    }
+    __syncthreads();
+    if (!active) return;
+    double* uc = u + (size_t)cell * SL;
+    const float* rc = rvol + (size_t)cell * SL;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+        const float face = (B.lift1[i] * Fst[cl][0][v][j] - B.lift0[i] * Fst[cl][1][v][j]) * P.inv_hx +
+                           (B.lift1[j] * Fst[cl][2][v][i] - B.lift0[j] * Fst[cl][3][v][i]) * P.inv_hy;
+        const float du = rc[v * n2 + node] - face;
+        uc[v * n2 + node] = fma(dt, (double)du, uc[v * n2 + node]);  // FP64 accumulation
+    }
+}
+
+template <int N>
+static int launch_pred_mixed(const double* u, float* rvol, float* trace, int cells, float dt,
+                             const BasisF& B, const PhysF& P, const MixedBg& bg, cudaStream_t s) {
+    using C = MixCfg<N>;
+    auto kern = k_predictor_mixed<N, C::cpb>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem_pred);
+    if (e != cudaSuccess) return (int)e;
+    const int blocks = (cells + C::cpb - 1) / C::cpb;
+    kern<<<blocks, C::threads, C::smem_pred, s>>>(u, rvol, trace, cells, dt, B, P, bg);
+    return (int)cudaGetLastError();
+}
+
+template <int N>
+static int launch_corr_mixed(double* u, const float* rvol, const float* trace, int cells, double dt,
+                             const BasisF& B, const PhysF& P, const MixedBg& bg, cudaStream_t s) {
+    using C = MixCfg<N>;
+    const int blocks = (cells + C::cpb - 1) / C::cpb;
+    k_corrector_mixed<N, C::cpb><<<blocks, C::threads, 0, s>>>(u, rvol, trace, cells, dt, B, P, bg);
+    return (int)cudaGetLastError();
+}
+
+int launch_predictor_mixed(int N, const double* u, float* rvol, float* trace, int cells, double dt,
+                           const BasisF& B, const PhysF& P, const MixedBg& bg, void* stream) {
+    cudaStream_t s = (cudaStream_t)stream;
+    const float dtf = (float)dt;
+    switch (N) {
+        case 1: return launch_pred_mixed<1>(u, rvol, trace, cells, dtf, B, P, bg, s);
+        case 2: return launch_pred_mixed<2>(u, rvol, trace, cells, dtf, B, P, bg, s);
+        case 3: return launch_pred_mixed<3>(u, rvol, trace, cells, dtf, B, P, bg, s);
+        case 4: return launch_pred_mixed<4>(u, rvol, trace, cells, dtf, B, P, bg, s);
+        case 5: return launch_pred_mixed<5>(u, rvol, trace, cells, dtf, B, P, bg, s);
+        case 6: return launch_pred_mixed<6>(u, rvol, trace, cells, dtf, B, P, bg, s);
+        case 7: return launch_pred_mixed<7>(u, rvol, trace, cells, dtf, B, P, bg, s);
+    }
+    return (int)cudaErrorInvalidValue;
+}
+
+int launch_corrector_mixed(int N, double* u, const float* rvol, const float* trace, int cells,
+                           double dt, const BasisF& B, const PhysF& P, const MixedBg& bg, void* stream) {
+    cudaStream_t s = (cudaStream_t)stream;
+    switch (N) {
+        case 1: return launch_corr_mixed<1>(u, rvol, trace, cells, dt, B, P, bg, s);
+        case 2: return launch_corr_mixed<2>(u, rvol, trace, cells, dt, B, P, bg, s);
+        case 3: return launch_corr_mixed<3>(u, rvol, trace, cells, dt, B, P, bg, s);
+        case 4: return launch_corr_mixed<4>(u, rvol, trace, cells, dt, B, P, bg, s);
+        case 5: return launch_corr_mixed<5>(u, rvol, trace, cells, dt, B, P, bg, s);
+        case 6: return launch_corr_mixed<6>(u, rvol, trace, cells, dt, B, P, bg, s);
+        case 7: return launch_corr_mixed<7>(u, rvol, trace, cells, dt, B, P, bg, s);
+    }
+    return (int)cudaErrorInvalidValue;
+}
+
+}  // namespace adg

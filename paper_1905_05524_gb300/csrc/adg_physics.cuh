@@ -1,0 +1,114 @@
+// Point-wise FP64 physics of the 2D compressible Navier-Stokes system with
+// gravity (Sec. 2 of Krenz, Rannabauer, Bader):
+//   Eq. 1  F = F^h(Q) + F^v(Q, grad Q), Q = (rho, rho u, rho v, rho E)
+//   Eq. 2  p = (gamma-1)(rhoE - 1/2 |rho v|^2 / rho - rho g z)
+//   Eq. 3  T = p / (rho R)
+//   Eq. 4  sigma = mu ((2/3) div v I - (grad v + grad v^T))
+//   Eq. 5  kappa = mu c_p / Pr
+//   Eq. 7  momentum flux with p' = p - pbar(z), source -g rho' in the z row
+// Gradients of v, p, T follow from grad Q by the chain rule.
+#pragma once
+#include "adg_internal.h"
+
+namespace adg {
+
+struct Flux4 {
+    double F[4], G[4], S[4];
+};
+
+// F, G and the physical source S at one point.  heat: if use_heat, (Tx, Ty)
+// replaces grad T in the heat flux (slip-wall ghost, Eq. 10).
+__device__ __forceinline__ void ns_flux(const double q[4], const double qx[4], const double qy[4],
+                                        double z, double pbar, double rhobar, const Phys& P,
+                                        Flux4& o, bool use_heat = false, double hTx = 0.0,
+                                        double hTy = 0.0) {
+    const double rho = q[0], mx = q[1], my = q[2], E = q[3];
+    const double rinv = 1.0 / rho;
+    const double u = mx * rinv, v = my * rinv;
+    const double gz = P.gravity ? P.g * z : 0.0;
+    const double p = P.gm1 * (E - 0.5 * (mx * u + my * v) - rho * gz);
+    const double pp = p - pbar;
+    const double T = p * rinv * P.invR;
+    const double ux = (qx[1] - u * qx[0]) * rinv;
+    const double uy = (qy[1] - u * qy[0]) * rinv;
+    const double vx = (qx[2] - v * qx[0]) * rinv;
+    const double vy = (qy[2] - v * qy[0]) * rinv;
+    const double kin = 0.5 * (u * u + v * v);
+    const double rg = P.gravity ? rho * P.g : 0.0;
+    double Tx, Ty;
+    if (use_heat) {
+        Tx = hTx;
+        Ty = hTy;
+    } else {
+        const double px = P.gm1 * (qx[3] - (u * qx[1] + v * qx[2]) + kin * qx[0] - gz * qx[0]);
+        const double py = P.gm1 * (qy[3] - (u * qy[1] + v * qy[2]) + kin * qy[0] - gz * qy[0] - rg);
+        Tx = (px - P.R * T * qx[0]) * rinv * P.invR;
+        Ty = (py - P.R * T * qy[0]) * rinv * P.invR;
+    }
+    const double div = ux + vy;
+    const double sxx = P.mu * ((2.0 / 3.0) * div - 2.0 * ux);
+    const double syy = P.mu * ((2.0 / 3.0) * div - 2.0 * vy);
+    const double sxy = -P.mu * (uy + vx);
+    const double Ep = E + p;
+    o.F[0] = mx;
+    o.F[1] = mx * u + pp + sxx;
+    o.F[2] = my * u + sxy;
+    o.F[3] = u * Ep + u * sxx + v * sxy - P.kappa * Tx;
+    o.G[0] = my;
+    o.G[1] = mx * v + sxy;
+    o.G[2] = my * v + pp + syy;
+    o.G[3] = v * Ep + u * sxy + v * syy - P.kappa * Ty;
+    o.S[0] = 0.0;
+    o.S[1] = 0.0;
+    o.S[2] = P.gravity ? -P.g * (rho - rhobar) : 0.0;
+    o.S[3] = 0.0;
+}
+
+// Steady manufactured source: rho = 1 + a sin(k s), s = x + y, k = 2 pi / L,
+// u = v = U, p = const.  Closed form of dF/dx + dG/dy for that field
+// (convective part 2 U a k cos(k s) (1, U, U, U^2) and the heat-conduction
+// term -kappa Laplace(T) with T = p / (rho R)).
+__device__ __forceinline__ void steady_source(double x, double y, const Phys& P, double S[4]) {
+    const double k = 2.0 * 3.14159265358979323846 / P.sL;
+    double sn, cs;
+    sincos(k * (x + y), &sn, &cs);
+    const double a = P.sa, U = P.sU;
+    const double rho = 1.0 + a * sn;
+    const double c = 2.0 * U * a * k * cs;
+    const double lapT = (2.0 * P.sp * P.invR) * (a * k * k * sn / (rho * rho) +
+                                                 2.0 * a * a * k * k * cs * cs / (rho * rho * rho));
+    S[0] = c;
+    S[1] = c * U;
+    S[2] = c * U;
+    S[3] = c * U * U - P.kappa * lapT;
+}
+
+// Rusanov speed |v.n| + c + 2 eta lambda_v of a face state (normal along x
+// if xdir, else along y), lambda_v = max(4/3, gamma/Pr) mu / rho.
+__device__ __forceinline__ double wave_speed(const double q[4], double z, bool xdir, const Phys& P) {
+    const double rinv = 1.0 / q[0];
+    const double u = q[1] * rinv, v = q[2] * rinv;
+    const double gz = P.gravity ? P.g * z : 0.0;
+    const double p = P.gm1 * (q[3] - 0.5 * (q[1] * u + q[2] * v) - q[0] * gz);
+    const double c = sqrt(P.gamma * p * rinv);
+    const double vn = xdir ? fabs(u) : fabs(v);
+    const double eta = xdir ? P.eta_x : P.eta_y;
+    return vn + c + 2.0 * eta * P.lamv * rinv;
+}
+
+// Numerical flux (F_L + F_R)/2 - max(s_L, s_R) (q_R - q_L)/2, written with
+// explicit round-to-nearest intrinsics so that both cells sharing a face
+// obtain the bitwise-identical value (exact conservation).
+__device__ __forceinline__ void rusanov(const double qL[4], const double fL[4], double sL,
+                                        const double qR[4], const double fR[4], double sR,
+                                        double out[4]) {
+    const double s = fmax(sL, sR);
+    const double hs = __dmul_rn(-0.5, s);
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+        const double avg = __dmul_rn(0.5, __dadd_rn(fL[v], fR[v]));
+        out[v] = __fma_rn(hs, __dsub_rn(qR[v], qL[v]), avg);
+    }
+}
+
+}  // namespace adg

@@ -1,0 +1,161 @@
+"""Thin Python front end of the C ABI (include/aderdg.h).
+
+PyTorch supplies device memory and the CUDA stream; every step of the method
+runs in libaderdg.so.  The functions here only build the C descriptors, pass
+pointers and turn status codes into exceptions.
+"""
+import ctypes
+import math
+from dataclasses import dataclass
+
+import torch
+
+from . import _lib as L
+
+
+@dataclass
+class MeshConfig:
+    """Python mirror of adg_mesh_desc (defaults: the CFD constants of Sec. 4.1)."""
+    degree: int = 3
+    nx: int = 9
+    ny: int = 9
+    x0: float = 0.0
+    y0: float = 0.0
+    Lx: float = 10.0
+    Ly: float = 10.0
+    bc_x: int = L.ADG_BC_PERIODIC
+    bc_y: int = L.ADG_BC_PERIODIC
+    gamma: float = 1.4
+    Pr: float = 0.7
+    R: float = 0.4
+    mu: float = 0.1
+    gravity: int = 0
+    g: float = 9.81
+    p0: float = 1e5
+    theta0: float = 300.0
+    source: int = L.ADG_SRC_NONE
+    src_a: float = 0.1
+    src_L: float = 10.0
+    src_U: float = 0.5
+    src_p: float = 1.0
+    precision: int = L.ADG_PREC_FP64
+    device: int = 0
+
+    def to_c(self):
+        return L.MeshDesc(**{f: getattr(self, f) for f, _ in L.MeshDesc._fields_})
+
+    @property
+    def n(self):
+        return self.degree + 1
+
+    @property
+    def cells(self):
+        return self.nx * self.ny
+
+
+def steady_manufactured_config(degree=3, nx=9, ny=9, precision=L.ADG_PREC_FP64, device=0):
+    """Periodic [0,10]^2, gamma 1.4, Pr 0.7, c_v 1, mu 0.1, steady manufactured
+    solution rho = 1 + 0.1 sin(2 pi (x+y)/10), u = v = 0.5, p = 1 with its source."""
+    return MeshConfig(degree=degree, nx=nx, ny=ny, source=L.ADG_SRC_STEADY,
+                      precision=precision, device=device)
+
+
+def atmosphere_config(degree=5, nx=81, ny=81, mu=0.01, precision=L.ADG_PREC_FP64, device=0):
+    """[0,1000]^2 m with slip walls, gamma 1.4, Pr 0.71, R 287.058, p0 1e5 Pa,
+    g 9.81, theta0 300 K isentropic background (Sec. 4.2)."""
+    return MeshConfig(degree=degree, nx=nx, ny=ny, Lx=1000.0, Ly=1000.0,
+                      bc_x=L.ADG_BC_WALL, bc_y=L.ADG_BC_WALL, gamma=1.4, Pr=0.71,
+                      R=287.058, mu=mu, gravity=1, g=9.81, p0=1e5, theta0=300.0,
+                      precision=precision, device=device)
+
+
+def _stream_ptr(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class Mesh:
+    """Owns one adg_mesh handle."""
+
+    def __init__(self, cfg: MeshConfig):
+        self.cfg = cfg
+        self._lib = L.lib()
+        h = ctypes.c_void_p()
+        L.check(self._lib.adg_create_mesh(ctypes.byref(cfg.to_c()), ctypes.byref(h)))
+        self.h = h
+        self.count = self._lib.adg_state_count(self.h)
+        self.device = torch.device("cuda", cfg.device)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._lib.adg_destroy_mesh(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def shape(self):
+        n = self.cfg.n
+        return (self.cfg.cells, 4, n, n)
+
+    # --------------------------------------------------------------- state
+    def set_state(self, u: torch.Tensor, stream=None):
+        assert u.dtype == torch.float64 and u.is_contiguous() and u.numel() == self.count
+        on_dev = 1 if u.is_cuda else 0
+        L.check(self._lib.adg_set_state(self.h, ctypes.c_void_p(u.data_ptr()), self.count,
+                                        on_dev, _stream_ptr(stream)))
+
+    def get_state(self, out: torch.Tensor = None, stream=None):
+        if out is None:
+            out = torch.empty(self.shape, dtype=torch.float64, device=self.device)
+        assert out.dtype == torch.float64 and out.is_contiguous() and out.numel() == self.count
+        L.check(self._lib.adg_get_state(self.h, ctypes.c_void_p(out.data_ptr()), self.count,
+                                        1 if out.is_cuda else 0, _stream_ptr(stream)))
+        return out
+
+    @property
+    def time(self):
+        return self._lib.adg_get_time(self.h)
+
+    @time.setter
+    def time(self, t):
+        L.check(self._lib.adg_set_time(self.h, float(t)))
+
+    def init_scenario(self, kind, A=0.5, a=250.0, xc=500.0, zc=350.0, stream=None):
+        sc = L.Scenario(kind=kind, A=A, a=a, xc=xc, zc=zc)
+        L.check(self._lib.adg_init_scenario(self.h, ctypes.byref(sc), _stream_ptr(stream)))
+
+    # --------------------------------------------------------------- method
+    def predictor(self, dt, stream=None):
+        L.check(self._lib.adg_predictor(self.h, float(dt), _stream_ptr(stream)))
+
+    def corrector(self, dt, stream=None):
+        L.check(self._lib.adg_corrector(self.h, float(dt), _stream_ptr(stream)))
+
+    def step(self, dt, nsteps=1, stream=None):
+        sp = _stream_ptr(stream)
+        for _ in range(nsteps):
+            L.check(self._lib.adg_step(self.h, float(dt), sp))
+
+    def stable_dt(self, cfl, stream=None):
+        dt = ctypes.c_double()
+        L.check(self._lib.adg_stable_dt(self.h, float(cfl), ctypes.byref(dt), _stream_ptr(stream)))
+        return dt.value
+
+    def tv_indicator(self, var, T_r, T_c, want_stats=True, stream=None):
+        C = self.cfg.cells
+        tv = torch.empty(C, dtype=torch.float64, device=self.device)
+        flags = torch.empty(C, dtype=torch.int8, device=self.device)
+        stats = (ctypes.c_double * 2)()
+        L.check(self._lib.adg_tv_indicator(
+            self.h, int(var), float(T_r), float(T_c), ctypes.c_void_p(tv.data_ptr()),
+            ctypes.c_void_p(flags.data_ptr()), stats if want_stats else None,
+            _stream_ptr(stream)))
+        return tv, flags, (stats[0], stats[1])
+
+    def check_finite(self, stream=None):
+        L.check(self._lib.adg_check_finite(self.h, _stream_ptr(stream)))

@@ -1,0 +1,90 @@
+"""Mixed-precision path (FP32 predictor/corrector arithmetic on perturbation
+variables, FP64 background split and update) against the FP64 oracle and
+the FP64 GPU path.
+
+Stated bound: relative L2 error of theta' <= 1e-6 (and per conserved
+variable errors reported) on the warm-bubble configuration."""
+import pytest
+import torch
+
+from paper_1905_05524_gb300 import _lib as L
+from paper_1905_05524_gb300.solver import Mesh, atmosphere_config, steady_manufactured_config
+from tests.oracle_bridge import oracle_for, cosine_field, steady_field
+from oracle import physics as ph
+
+pytestmark = pytest.mark.gpu
+
+THETA_TOL = 1e-6
+
+
+def theta_prime(o, u):
+    return ph.theta(u.unbind(1), o.Y, o.P) - o.P.theta0
+
+
+def rel_theta_err(o, a, b):
+    ta, tb = theta_prime(o, a), theta_prime(o, b)
+    w = o.b.w
+    W = (w[None, :, None] * w[None, None, :])
+    num = torch.sqrt((W * (ta - tb) ** 2).sum())
+    den = torch.sqrt((W * tb ** 2).sum())
+    return (num / den).item()
+
+
+def test_mixed_vs_oracle_bubble_small():
+    """N = 5, 9x9 bubble, 30 steps: mixed vs FP64 oracle."""
+    cfg = atmosphere_config(degree=5, nx=9, ny=9, precision=L.ADG_PREC_MIXED)
+    o = oracle_for(cfg)
+    u0 = cosine_field(o)
+    dt = o.stable_dt(u0, 0.5)
+    m = Mesh(cfg)
+    m.set_state(u0.cuda().contiguous())
+    m.step(dt, 30)
+    uo = u0
+    for _ in range(30):
+        uo = o.step(uo, dt)
+    a = m.get_state().cpu()
+    err = rel_theta_err(o, a, uo)
+    assert err <= THETA_TOL, err
+
+
+def test_mixed_vs_fp64_gpu_config2_400_steps():
+    """Config 2 at full size: 400 steps of the mixed path against 400 steps of
+    the FP64 GPU path (itself parity-checked against the oracle)."""
+    res = {}
+    for prec in (L.ADG_PREC_FP64, L.ADG_PREC_MIXED):
+        cfg = atmosphere_config(degree=5, nx=81, ny=81, precision=prec)
+        m = Mesh(cfg)
+        m.init_scenario(L.ADG_SCEN_COSINE, A=0.5, a=250.0, xc=500.0, zc=350.0)
+        if prec == L.ADG_PREC_FP64:
+            dt = m.stable_dt(0.5)
+        m.step(dt, 400)
+        res[prec] = m.get_state().cpu()
+    o = oracle_for(atmosphere_config(degree=5, nx=81, ny=81))
+    err = rel_theta_err(o, res[L.ADG_PREC_MIXED], res[L.ADG_PREC_FP64])
+    print(f"config2 400 steps: relative theta' L2 error mixed vs fp64 = {err:.3e}")
+    assert err <= THETA_TOL, err
+    # conserved variables: relative L2 per variable, stated
+    for v in range(4):
+        a, b = res[L.ADG_PREC_MIXED][:, v], res[L.ADG_PREC_FP64][:, v]
+        r = (torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b)).item()
+        print(f"  var {v}: rel L2 {r:.3e}")
+        assert r < 1e-5
+
+
+def test_mixed_vs_oracle_manufactured():
+    """Periodic CFD case without gravity (the FP32 path carries the full
+    state): error stays at FP32 level."""
+    cfg = steady_manufactured_config(degree=3, nx=9, ny=9, precision=L.ADG_PREC_MIXED)
+    o = oracle_for(cfg)
+    u0 = steady_field(o, cfg)
+    dt = o.stable_dt(u0, 0.5)
+    m = Mesh(cfg)
+    m.set_state(u0.cuda().contiguous())
+    m.step(dt, 20)
+    uo = u0
+    for k in range(20):
+        uo = o.step(uo, dt, k * dt)
+    a = m.get_state().cpu()
+    for v in range(4):
+        r = (torch.linalg.vector_norm(a[:, v] - uo[:, v]) / torch.linalg.vector_norm(uo[:, v])).item()
+        assert r < 1e-6, (v, r)
