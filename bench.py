@@ -3,7 +3,7 @@
 Workload: the rising warm bubble -- degree 5 (order 6), 81 x 81 = 6561 cells
 on [0,1000]^2 m with slip walls, isentropic background theta0 = 300 K,
 g = 9.81, cosine theta' bubble (0.5 K, radius 250 m, centre (500, 350)),
-mu = 0.01, fixed dt from CFL 0.5 on the initial state.  One step = one pass
+mu = 0.01, fixed dt from CFL 0.25 on the initial state.  One step = one pass
 of the hot path: space-time predictor, corrector, and the TV refinement
 indicator (per-cell TV of theta, Chan mean/std, flags).
 
@@ -34,13 +34,14 @@ METRIC = "ADER-DG DOF-updates/s at order 6: mixed/batched vs FP64 at stated erro
 UNIT = "DOF-updates/s"
 DEGREE, NX, NY = 5, 81, 81
 T_R, T_C = 1.5, -0.5    # AMR thresholds of the 2D cosine bubble (Sec. 4.2)
+CFL = 0.25              # fixed dt from this CFL number on the initial state
 
 
 def workload_config(precision):
     return {
         "workload": "rising warm bubble, degree 5 (order 6), 81x81=6561 cells on [0,1000]^2 m, "
                     "slip walls, theta0=300 K, g=9.81, cosine bubble 0.5 K r=250 m at (500,350), "
-                    "mu=0.01, CFL 0.5; step = predictor + corrector + TV indicator",
+                    "mu=0.01, CFL 0.25; step = predictor + corrector + TV indicator",
         "cells": NX * NY, "degree": DEGREE, "dof_per_step": NX * NY * (DEGREE + 1) ** 2 * 4,
         "precision": precision, "l2": "flushed before every timed step (256 MB write)",
     }
@@ -71,6 +72,12 @@ def predictor_flops_per_cell(n):
     f += n * n * 4 * (4 * n + 4)                   # volume residual
     f += 4 * n * (16 * 2 * n + 20)                 # traces + wave speed
     return f
+
+
+# DRAM bytes (read + write) of one predictor launch on this workload, from one
+# ncu capture of the kernel as it stands (profiles/k_predictor_*_warm_bubble_n5_81x81.md);
+# set to None whenever the kernel changes after the capture.
+PREDICTOR_TRAFFIC = {"fp64": 7810304 + 768, "mixed": None}
 
 
 def measure_fma_peaks():
@@ -163,7 +170,7 @@ def oracle_sample(steps, threads=None):
     cfg = atmosphere_config(degree=DEGREE, nx=NX, ny=NY)
     o = oracle_for(cfg)
     u = cosine_field(o)
-    dt = o.stable_dt(u, 0.5)
+    dt = o.stable_dt(u, CFL)
     t0 = time.perf_counter()
     t = 0.0
     for _ in range(steps):
@@ -214,7 +221,7 @@ def run_ours(args):
     cfg = atmosphere_config(degree=DEGREE, nx=NX, ny=NY, precision=prec, device=dev.index)
     m = Mesh(cfg)
     m.init_scenario(L.ADG_SCEN_COSINE, A=0.5, a=250.0, xc=500.0, zc=350.0)
-    dt = m.stable_dt(0.5)
+    dt = m.stable_dt(CFL)
     u_init = m.get_state().clone()
     cells, n = NX * NY, DEGREE + 1
     dof = cells * n * n * 4
@@ -292,21 +299,23 @@ def run_ours(args):
 
     out = None
     if rank == 0:
-        peaks = measure_fma_peaks()
+        peaks = {} if args.no_peaks else measure_fma_peaks()
         mp = measured_peaks_file()
         flops_launch = predictor_flops_per_cell(n) * cells
         pred_avg = pred / args.steps
-        fp64_peak = peaks.get("fp64")
+        pipe = "fp64" if args.precision == "fp64" else "fp32"
+        pk = peaks.get(pipe)
         achieved = flops_launch / (pred_avg * 1e-3) / 1e12
         roof = {
-            "kernel": "k_predictor_fp64<5,4>",
-            "bound": "alu", "pipe": "fp64 FMA",
-            "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
-            "frac": (achieved / fp64_peak) if fp64_peak else None,
-            "peak_source": "measured by paper_1905_05524_gb300/csrc/fma_peak.cu on this GPU" if fp64_peak
-            else "unavailable",
+            "kernel": f"k_predictor_{'fp64' if pipe == 'fp64' else 'mixed'}<5,4>",
+            "bound": "alu", "pipe": f"{pipe} FMA (CUDA cores)",
+            "achieved": achieved, "peak": pk, "unit": "TFLOP/s",
+            "frac": (achieved / pk) if pk else None,
+            "peak_source": "measured by paper_1905_05524_gb300/csrc/fma_peak.cu on this GPU (FMA-only loop)"
+            if pk else "unavailable",
             "flops_per_launch": flops_launch, "launch_ms": pred_avg,
-            "traffic": None,
+            "traffic": PREDICTOR_TRAFFIC.get(args.precision),
+            "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
             "hbm_achieved_gbs": cells * n * n * 4 * 8 * 2 / (pred_avg * 1e-3) / 1e9,
             "hbm_peak_gbs": (mp or {}).get("hbm_gbs", 6800.0),
             "hbm_peak_source": "MEASURED_PEAKS.json" if mp else "fallback 6.8 TB/s",
@@ -348,6 +357,7 @@ def main():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--cpu-steps", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-peaks", action="store_true", help="skip the FMA peak probe (profiling runs)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
