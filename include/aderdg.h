@@ -142,6 +142,34 @@ int adg_tv_indicator(adg_mesh* m, int var, double T_r, double T_c,
 /* Scan the state for NaN/Inf: ADG_ENONFINITE if any.  Synchronises `stream`. */
 int adg_check_finite(adg_mesh* m, void* stream);
 
+/* ---- allocation-free step (the paper has no counterpart) ----
+ *
+ * One FP64 step (predictor + corrector, the same kernels as adg_step, so
+ * the same results up to FP64 rounding of the background tables) on a
+ * caller-owned device state, with no mesh object and no device allocation.  Meant for callers that must not call cudaMalloc: an
+ * application whose pool allocator already owns the device memory, a
+ * latency-critical loop that cannot take cudaMalloc's implicit device-wide
+ * synchronisation, or a plug-in whose host forbids allocator calls.
+ *
+ *   desc   mesh/physics description (as for adg_create_mesh); precision must
+ *          be ADG_PREC_FP64 (ADG_EUNSUPPORTED otherwise)
+ *   u      device pointer to the state (layout above), updated in place;
+ *          count must equal nx*ny*(N+1)^2*4
+ *   dt     time step (> 0)
+ *
+ * Scratch (background tables, volume residual, face traces) lives in a
+ * fixed file-scope device array of ADG_NOALLOC_SCRATCH_BYTES that every GPU
+ * loading the library holds until exit; meshes needing more scratch are
+ * rejected with ADG_EINVAL and a message giving both sizes (at N = 5 about
+ * 7,500 cells fit).  The first call on a device looks up the array's address
+ * once; make that first call before any stream capture.  All calls share the
+ * array, so calls whose work overlaps on the GPU (different streams, or
+ * different threads on one device) race; serialise them.  Every scratch
+ * entry is written before it is read within a call, so no state carries over
+ * between calls. */
+#define ADG_NOALLOC_SCRATCH_BYTES (32u << 20)
+int adg_step_noalloc(const adg_mesh_desc* desc, double* u, size_t count, double dt, void* stream);
+
 /* Text of the last error on the calling thread ("" if none). */
 const char* adg_last_error(void);
 

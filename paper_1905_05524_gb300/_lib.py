@@ -31,6 +31,7 @@ ADG_SCEN_STEADY = 0
 ADG_SCEN_COSINE = 1
 ADG_SCEN_TWO_BUBBLES = 2
 ADG_SCEN_BACKGROUND = 3
+ADG_NOALLOC_SCRATCH_BYTES = 32 << 20
 
 STATUS_NAMES = {1: "ADG_EINVAL", 2: "ADG_ENOMEM", 3: "ADG_ECUDA", 4: "ADG_ENONFINITE",
                 5: "ADG_ETIMEOUT", 6: "ADG_ESTATE", 7: "ADG_EUNSUPPORTED"}
@@ -83,6 +84,7 @@ SIGNATURES = {
     "adg_stable_dt": (_I, [_P, _D, ctypes.POINTER(_D), _P]),
     "adg_tv_indicator": (_I, [_P, _I, _D, _D, _P, _P, _P, _P]),
     "adg_check_finite": (_I, [_P, _P]),
+    "adg_step_noalloc": (_I, [ctypes.POINTER(MeshDesc), _P, _S, _D, _P]),
     "adg_last_error": (ctypes.c_char_p, []),
 }
 

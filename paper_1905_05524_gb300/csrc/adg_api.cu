@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -559,3 +560,153 @@ int adg_check_finite(adg_mesh* m, void* stream) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// adg_step_noalloc: one FP64 step on a caller-owned state without any device
+// allocation.  It serves callers that must not call cudaMalloc: an
+// application whose own pool allocator has reserved the device memory, a
+// latency-critical loop that cannot afford cudaMalloc's implicit device-wide
+// synchronisation, or a plug-in whose host forbids allocator calls after
+// start-up.  The scratch the predictor/corrector pair needs (background
+// tables, volume residual, face traces) lives in one file-scope device array
+// of fixed size; every GPU that loads this library holds it until exit.
+// The first call on a device looks up the array's device address once
+// (cudaGetSymbolAddress); make that first call before any stream capture.
+// All calls share the array: calls whose work overlaps on the GPU race.
+namespace {
+
+constexpr size_t kNoallocBytes = (size_t)32 << 20;  // ADG_NOALLOC_SCRATCH_BYTES
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
+
+constexpr int kNoallocMaxDevices = 64;
+void* g_noalloc_ptr[kNoallocMaxDevices] = {};
+std::mutex g_noalloc_mu;
+
+// isentropic background at node heights and face heights (Eq. 6, reading R7)
+__global__ void k_noalloc_background(double* pn, double* rn, double* pf, double* rf, int ny, int n,
+                                     adg::Basis B, double y0, double hy, double g, double cp,
+                                     double R, double p0, double theta0, int gravity) {
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nodes = ny * n;
+    if (a < nodes + ny + 1) {
+        const double z = a < nodes ? y0 + (a / n + B.xi[a % n]) * hy : y0 + (a - nodes) * hy;
+        double p = 0.0, r = 0.0;
+        if (gravity) {
+            const double ex = 1.0 - g * z / (cp * theta0);
+            p = p0 * pow(ex, cp / R);
+            r = p / (R * theta0 * ex);
+        }
+        if (a < nodes) {
+            pn[a] = p;
+            rn[a] = r;
+        } else {
+            pf[a - nodes] = p;
+            rf[a - nodes] = r;
+        }
+    }
+}
+
+}  // namespace
+
+extern "C" int adg_step_noalloc(const adg_mesh_desc* d, double* u, size_t count, double dt, void* stream) {
+    if (!d || !u) return fail(ADG_EINVAL, "step_noalloc: NULL argument");
+    if (d->degree < 1 || d->degree > ADG_MAX_DEGREE)
+        return fail(ADG_EINVAL, "step_noalloc: degree must be in [1, 7]");
+    if (d->nx < 1 || d->ny < 1 || !(d->Lx > 0.0) || !(d->Ly > 0.0))
+        return fail(ADG_EINVAL, "step_noalloc: bad mesh size");
+    if (d->bc_x < 0 || d->bc_x > 1 || d->bc_y < 0 || d->bc_y > 1)
+        return fail(ADG_EINVAL, "step_noalloc: unknown boundary condition");
+    if (!(d->gamma > 1.0) || !(d->R > 0.0) || !(d->Pr > 0.0) || !(d->mu >= 0.0))
+        return fail(ADG_EINVAL, "step_noalloc: invalid gas constants");
+    if (d->source != ADG_SRC_NONE && !(d->source == ADG_SRC_STEADY && d->src_L > 0.0))
+        return fail(ADG_EINVAL, "step_noalloc: unknown source");
+    if (d->gravity && !(d->theta0 > 0.0 && d->p0 > 0.0))
+        return fail(ADG_EINVAL, "step_noalloc: gravity needs theta0 > 0 and p0 > 0");
+    if (d->precision != ADG_PREC_FP64) return fail(ADG_EUNSUPPORTED, "step_noalloc: FP64 precision only");
+    if (!(dt > 0.0) || !std::isfinite(dt)) return fail(ADG_EINVAL, "step_noalloc: dt must be finite and > 0");
+    if (d->device < 0 || d->device >= kNoallocMaxDevices) return fail(ADG_EINVAL, "step_noalloc: bad device ordinal");
+
+    const int N = d->degree, n = N + 1;
+    const size_t cells = (size_t)d->nx * d->ny;
+    const size_t nbg = 2 * (size_t)d->ny * n + 2 * (size_t)(d->ny + 1);
+    const size_t cnt = cells * n * n * 4;
+    if (count != cnt) return fail(ADG_EINVAL, "step_noalloc: count != nx*ny*(N+1)^2*4");
+    const size_t ntr = cells * 4 * adg::kTraceComps * n;
+    auto up256 = [](size_t b) { return (b + 255) / 256 * 256; };
+    const size_t need = up256(nbg * 8) + up256(cnt * 8) + up256(ntr * 8);
+    if (need > kNoallocBytes) {
+        char msg[200];
+        std::snprintf(msg, sizeof(msg),
+                      "step_noalloc: mesh needs %zu bytes of scratch, the static limit is %zu bytes "
+                      "(ADG_NOALLOC_SCRATCH_BYTES)", need, kNoallocBytes);
+        return fail(ADG_EINVAL, msg);
+    }
+
+    ADG_CK(cudaSetDevice(d->device), "step_noalloc: cudaSetDevice");
+    void* base = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_noalloc_mu);
+        if (!g_noalloc_ptr[d->device]) {  // one-time set-up on this device
+            void* p = nullptr;
+            ADG_CK(cudaGetSymbolAddress(&p, g_noalloc_scratch), "step_noalloc: cudaGetSymbolAddress");
+            g_noalloc_ptr[d->device] = p;
+        }
+        base = g_noalloc_ptr[d->device];
+    }
+
+    adg::Basis B;
+    if (!build_basis(N, B)) return fail(ADG_EINVAL, "step_noalloc: singular time-stiffness matrix");
+    adg::Phys P;
+    std::memset(&P, 0, sizeof(P));
+    P.gamma = d->gamma;
+    P.gm1 = d->gamma - 1.0;
+    P.R = d->R;
+    P.invR = 1.0 / d->R;
+    P.mu = d->mu;
+    P.cp = d->gamma * d->R / (d->gamma - 1.0);
+    P.kappa = d->mu * P.cp / d->Pr;
+    P.g = d->g;
+    P.p0 = d->p0;
+    P.theta0 = d->theta0;
+    P.Rcp = d->R / P.cp;
+    P.lamv = std::fmax(4.0 / 3.0, d->gamma / d->Pr) * d->mu;
+    P.hx = d->Lx / d->nx;
+    P.hy = d->Ly / d->ny;
+    P.inv_hx = 1.0 / P.hx;
+    P.inv_hy = 1.0 / P.hy;
+    P.x0 = d->x0;
+    P.y0 = d->y0;
+    P.eta_x = (2.0 * N + 1.0) / (P.hx * std::sqrt(M_PI / 2.0));
+    P.eta_y = (2.0 * N + 1.0) / (P.hy * std::sqrt(M_PI / 2.0));
+    P.gravity = d->gravity ? 1 : 0;
+    P.source = d->source;
+    P.sa = d->src_a;
+    P.sL = d->src_L;
+    P.sU = d->src_U;
+    P.sp = d->src_p;
+    P.nx = d->nx;
+    P.ny = d->ny;
+    P.bc_x = d->bc_x;
+    P.bc_y = d->bc_y;
+
+    // scratch layout: background tables | rvol | trace (every entry is written
+    // before it is read, so nothing needs clearing between calls)
+    unsigned char* s = (unsigned char*)base;
+    double* pn = (double*)s;
+    double* rn = pn + (size_t)d->ny * n;
+    double* pf = rn + (size_t)d->ny * n;
+    double* rf = pf + (d->ny + 1);
+    double* rvol = (double*)(s + up256(nbg * 8));
+    double* trace = (double*)(s + up256(nbg * 8) + up256(cnt * 8));
+    cudaStream_t st = (cudaStream_t)stream;
+    const int nb = (int)((nbg / 2 + 255) / 256);
+    k_noalloc_background<<<nb, 256, 0, st>>>(pn, rn, pf, rf, d->ny, n, B, d->y0, P.hy, d->g, P.cp, d->R,
+                                             d->p0, d->theta0, P.gravity);
+    ADG_CK(cudaGetLastError(), "step_noalloc: background launch");
+    adg::Background bg{pn, rn, pf, rf};
+    int e = adg::launch_predictor_fp64(N, u, rvol, trace, (int)cells, dt, 0.0, B, P, bg, stream);
+    if (e) return cuda_fail((cudaError_t)e, "step_noalloc: predictor launch");
+    e = adg::launch_corrector_fp64(N, u, rvol, trace, (int)cells, dt, B, P, bg, stream);
+    if (e) return cuda_fail((cudaError_t)e, "step_noalloc: corrector launch");
+    return ADG_OK;
+}
