@@ -10,6 +10,12 @@ indicator (per-cell TV of theta, Chan mean/std, flags).
 Metric: DOF-updates/s = cells * (N+1)^2 * 4 * steps / seconds (the paper's
 DOF count: spatial nodal values of the 4 conserved variables).
 
+Forms: the headline `value` is the mixed-precision form (FP32 arithmetic on
+perturbation variables, FP64 background split and update); the same line
+carries the plain FP64 form on the same workload, the theta' error of the
+mixed form against it, and the batched form (64 instances of uneven sizes in
+one persistent, graph-captured launch per phase).
+
 Timing: W untimed warm-up steps, then K steps each bracketed by CUDA events
 on the launching stream; a 256 MB buffer is written before every timed step
 to flush L2 (the state is smaller than L2).  Under torchrun each rank runs an
@@ -204,61 +210,70 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------ GPU arm
-def run_ours(args):
-    import torch
-    ws, rank, local = dist_env()
-    if ws > 1:
-        import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
-    dev = torch.device("cuda", local if ws > 1 else 0)
-    torch.cuda.set_device(dev)
+def theta_prime_np(u, cfg):
+    """theta' = T (p0/p)^(R/cp) - theta0 at the nodes of a [c, v, j, i] state
+    (measurement only: compares the mixed and FP64 forms)."""
+    import numpy as np
+    n = cfg.degree + 1
+    xi, _ = np.polynomial.legendre.leggauss(n)
+    xi = 0.5 * (xi + 1.0)
+    hy = cfg.Ly / cfg.ny
+    iy = np.arange(cfg.nx * cfg.ny) // cfg.nx
+    z = cfg.y0 + (iy[:, None, None] + xi[None, :, None]) * hy + 0.0 * xi[None, None, :]
+    rho, mx, my, E = u[:, 0], u[:, 1], u[:, 2], u[:, 3]
+    cp = cfg.gamma * cfg.R / (cfg.gamma - 1.0)
+    p = (cfg.gamma - 1.0) * (E - 0.5 * (mx * mx + my * my) / rho - rho * cfg.g * z)
+    T = p / (rho * cfg.R)
+    return T * (cfg.p0 / p) ** (cfg.R / cp) - cfg.theta0
 
+
+def run_form(prec_name, steps, warmup, dev, ws):
+    """Time `steps` steps (predictor + corrector + TV) of the workload in one
+    precision form; returns timings and the final state."""
+    import ctypes
+    import torch
     from paper_1905_05524_gb300 import _lib as L
     from paper_1905_05524_gb300.solver import Mesh, atmosphere_config
 
-    prec = L.ADG_PREC_FP64 if args.precision == "fp64" else L.ADG_PREC_MIXED
+    prec = L.ADG_PREC_FP64 if prec_name == "fp64" else L.ADG_PREC_MIXED
     cfg = atmosphere_config(degree=DEGREE, nx=NX, ny=NY, precision=prec, device=dev.index)
     m = Mesh(cfg)
     m.init_scenario(L.ADG_SCEN_COSINE, A=0.5, a=250.0, xc=500.0, zc=350.0)
     dt = m.stable_dt(CFL)
     u_init = m.get_state().clone()
-    cells, n = NX * NY, DEGREE + 1
-    dof = cells * n * n * 4
+    cells = NX * NY
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     tvbuf = torch.empty(cells, dtype=torch.float64, device=dev)
     flags = torch.empty(cells, dtype=torch.int8, device=dev)
-    import ctypes
     sp = ctypes.c_void_p(stream.cuda_stream)
     lib = L.lib()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
 
     def one_step():
+        ev[0].record(stream)
         L.check(lib.adg_predictor(m.h, dt, sp))
         ev[1].record(stream)
         L.check(lib.adg_corrector(m.h, dt, sp))
         ev[2].record(stream)
         L.check(lib.adg_tv_indicator(m.h, L.ADG_TV_THETA, T_R, T_C, ctypes.c_void_p(tvbuf.data_ptr()),
                                      ctypes.c_void_p(flags.data_ptr()), None, sp))
-
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
-    for _ in range(args.warmup):
-        ev[0].record(stream)
-        one_step()
         ev[3].record(stream)
-    torch.cuda.synchronize()
 
+    for _ in range(warmup):
+        one_step()
+    torch.cuda.synchronize()
+    m.set_state(u_init)          # timed steps start from the initial state
+    torch.cuda.synchronize()
     clocks = ClockSampler(dev.index)
     if ws > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
     clocks.start()
     total = pred = corr = tvt = 0.0
-    for _ in range(args.steps):
+    for _ in range(steps):
         flush.fill_(1.0)  # evict L2 between timed steps
-        ev[0].record(stream)
         one_step()
-        ev[3].record(stream)
         ev[3].synchronize()
         total += ev[0].elapsed_time(ev[3])
         pred += ev[0].elapsed_time(ev[1])
@@ -268,22 +283,15 @@ def run_ours(args):
     if ws > 1:
         torch.distributed.barrier()
     clk = clocks.stop()
-    t_ms = total
-    if ws > 1:
-        t = torch.tensor([t_ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_ms = float(t.item())
-    value = dof * args.steps * ws / (t_ms * 1e-3)
+    final = m.get_state().cpu().numpy()
 
-    # ---- end to end through the public API with host buffers (pinned)
+    # end to end through the public API with host buffers (pinned)
     host_in = u_init.cpu().pin_memory()
     host_out = torch.empty_like(host_in).pin_memory()
     stats = (ctypes.c_double * 2)()
     torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e2e_steps = max(1, args.steps)
     t0 = time.perf_counter()
-    for _ in range(e2e_steps):
+    for _ in range(steps):
         L.check(lib.adg_set_state(m.h, ctypes.c_void_p(host_in.data_ptr()), m.count, 0, sp))
         L.check(lib.adg_step(m.h, dt, sp))
         L.check(lib.adg_tv_indicator(m.h, L.ADG_TV_THETA, T_R, T_C, ctypes.c_void_p(tvbuf.data_ptr()),
@@ -291,18 +299,97 @@ def run_ours(args):
         L.check(lib.adg_get_state(m.h, ctypes.c_void_p(host_out.data_ptr()), m.count, 0, sp))
     torch.cuda.synchronize()
     e2e_sec = time.perf_counter() - t0
+    m.close()
+    return dict(total=total, pred=pred, corr=corr, tv=tvt, clocks=clk, final=final, e2e_sec=e2e_sec,
+                cfg=cfg, dt=dt)
+
+
+def run_batch(dev, nsteps=20, instances=64):
+    """Config-5 batch: `instances` warm-bubble instances (sides U{9..81},
+    seed 3; radii U[100,300] m, seed 4), degree 5, mixed precision, advanced
+    by the persistent graph-captured batched launch (predictor + corrector)."""
+    import torch
+    from paper_1905_05524_gb300 import _lib as L
+    from paper_1905_05524_gb300 import inputs
+    from paper_1905_05524_gb300.solver import Batch, Mesh, atmosphere_config
+    sides = inputs.instance_sizes(instances, seed=3, lo=9, hi=81)
+    radii = inputs.uniform_values(instances, seed=4, lo=100.0, hi=300.0)
+    ms = []
+    for s_, r_ in zip(sides, radii):
+        m = Mesh(atmosphere_config(degree=DEGREE, nx=int(s_), ny=int(s_), precision=L.ADG_PREC_MIXED,
+                                   device=dev.index))
+        m.init_scenario(L.ADG_SCEN_COSINE, A=0.5, a=float(r_), xc=500.0, zc=350.0)
+        ms.append(m)
+    dts = [m.stable_dt(CFL) for m in ms]
+    b = Batch(ms)
+    b.step(dts, nsteps)            # capture + warm-up
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stream = torch.cuda.current_stream()
+    e0.record(stream)
+    b.step(dts, nsteps)
+    e1.record(stream)
+    e1.synchronize()
+    ms_total = e0.elapsed_time(e1)
+    cells = int(sum(int(s_) ** 2 for s_ in sides))
+    dof = cells * (DEGREE + 1) ** 2 * 4
+    info = b.info()
+    b.close()
+    for m in ms:
+        m.close()
+    return {"value": dof * nsteps / (ms_total * 1e-3), "unit": UNIT, "instances": instances,
+            "cells": cells, "steps": nsteps, "ms_per_step": ms_total / nsteps,
+            "step": "predictor + corrector (persistent launches, CUDA graph)", "tiles": info,
+            "l2": "state (%.0f MB) exceeds L2" % (dof * 8 / 1e6) if dof * 8 > 129e6 else "not flushed"}
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    ws, rank, local = dist_env()
     if ws > 1:
-        t = torch.tensor([e2e_sec], device=dev, dtype=torch.float64)
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if ws > 1 else 0)
+    torch.cuda.set_device(dev)
+    n = DEGREE + 1
+    cells = NX * NY
+    dof = cells * n * n * 4
+
+    main = run_form(args.precision, args.steps, args.warmup, dev, ws)
+    t_ms = main["total"]
+    e2e_sec = main["e2e_sec"]
+    if ws > 1:
+        t = torch.tensor([t_ms, e2e_sec], device=dev, dtype=torch.float64)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_sec = float(t.item())
-    e2e_val = dof * e2e_steps * ws / e2e_sec
+        t_ms, e2e_sec = float(t[0]), float(t[1])
+    value = dof * args.steps * ws / (t_ms * 1e-3)
+    e2e_val = dof * args.steps * ws / e2e_sec
 
     out = None
     if rank == 0:
+        forms = {}
+        if not args.no_compare and args.precision == "mixed":
+            ref = run_form("fp64", args.steps, min(args.warmup, 3), dev, 1)
+            th_m = theta_prime_np(main["final"], main["cfg"])
+            th_d = theta_prime_np(ref["final"], ref["cfg"])
+            err = float(np.linalg.norm(th_m - th_d) / np.linalg.norm(th_d))
+            var_err = [float(np.linalg.norm(main["final"][:, v] - ref["final"][:, v]) /
+                             np.linalg.norm(ref["final"][:, v])) for v in range(4)]
+            forms["fp64"] = {"value": dof * args.steps / (ref["total"] * 1e-3), "unit": UNIT,
+                             "ms_per_step": ref["total"] / args.steps,
+                             "phases_ms": {"predictor": ref["pred"] / args.steps,
+                                           "corrector": ref["corr"] / args.steps,
+                                           "tv_indicator": ref["tv"] / args.steps}}
+            forms["mixed_error_vs_fp64"] = {"theta_prime_rel_l2": err, "per_variable_rel_l2": var_err,
+                                            "steps": args.steps, "stated_bound": 1e-6}
+        if not args.no_batch and args.precision == "mixed":
+            forms["mixed_batched_64_instances"] = run_batch(dev, nsteps=args.batch_steps)
         peaks = {} if args.no_peaks else measure_fma_peaks()
         mp = measured_peaks_file()
         flops_launch = predictor_flops_per_cell(n) * cells
-        pred_avg = pred / args.steps
+        pred_avg = main["pred"] / args.steps
         pipe = "fp64" if args.precision == "fp64" else "fp32"
         pk = peaks.get(pipe)
         achieved = flops_launch / (pred_avg * 1e-3) / 1e12
@@ -332,17 +419,18 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if args.precision == "fp64" else "f32+f64",
             "data": "synthetic (analytic initial state)", "config": workload_config(args.precision),
-            "phases_ms": {"predictor": pred_avg, "corrector": corr / args.steps, "tv_indicator": tvt / args.steps},
-            "gpu_launches": 4 * args.steps,
-            "clocks": clk,
+            "phases_ms": {"predictor": pred_avg, "corrector": main["corr"] / args.steps,
+                          "tv_indicator": main["tv"] / args.steps},
+            "gpu_launches": 5 * args.steps,
+            "clocks": main["clocks"],
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": dof * 8,
                     "d2h_bytes_per_step": dof * 8 + 16},
             "roofline": roof,
             "cpu_baseline": cpu,
+            "forms": forms,
             "fma_peaks_tflops": peaks,
         }
         print(json.dumps(out), flush=True)
-    m.close()
     if ws > 1:
         torch.distributed.destroy_process_group()
     return 0
@@ -351,10 +439,13 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
+    ap.add_argument("--no-compare", action="store_true", help="skip the FP64 comparison form")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 64-instance batched form")
+    ap.add_argument("--batch-steps", type=int, default=20)
     ap.add_argument("--cpu-steps", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-peaks", action="store_true", help="skip the FMA peak probe (profiling runs)")

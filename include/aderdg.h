@@ -139,8 +139,45 @@ int adg_stable_dt(adg_mesh* m, double cfl, double* dt, void* stream);
 int adg_tv_indicator(adg_mesh* m, int var, double T_r, double T_c,
                      double* tv, int8_t* flags, double* stats, void* stream);
 
+/* Discrete adjoint of one adg_step (predictor + corrector, FP64) at the
+ * state u_n: lam_n = lam_np1 + (d step / d u)^T lam_np1, i.e. the gradient of
+ * J(u^{n+1}) with respect to u^n given lam_np1 = dJ/du^{n+1} (the adjoint of
+ * the method of Sec. 3, not a separate discretisation).  u_n, lam_np1, lam_n
+ * are device arrays in the state layout; lam_n must not alias the inputs.
+ * The mesh's own state is not touched; its predictor workspace is
+ * (a following adg_corrector needs a new adg_predictor).  Non-smooth points:
+ * max(s_L, s_R) takes s_L on ties and |v.n| takes sign(v.n) (0 at 0).
+ * FP64 meshes with degree <= 5 (ADG_EUNSUPPORTED otherwise). */
+int adg_step_adjoint(adg_mesh* m, double dt, const double* u_n, const double* lam_np1, double* lam_n,
+                     void* stream);
+
 /* Scan the state for NaN/Inf: ADG_ENONFINITE if any.  Synchronises `stream`. */
 int adg_check_finite(adg_mesh* m, void* stream);
+
+/* ---- batched persistent step ----
+ *
+ * Many independent meshes ("instances", e.g. scenarios of different grid
+ * sizes; the paper's method applied per instance, Sec. 3) advanced together:
+ * per step one persistent predictor launch and one persistent corrector
+ * launch walk a static list of tiles (instance, first cell) across all
+ * instances; nsteps steps are captured once into a CUDA graph and replayed.
+ * adg_batch_create times the predictor's tile-size candidates on the batch
+ * and keeps the fastest (cached per degree, SM count and size class).
+ *
+ *   meshes   k meshes of one degree and device, all ADG_PREC_MIXED
+ *            (ADG_EUNSUPPORTED otherwise); they stay owned by the caller and
+ *            must outlive the batch; their states are advanced in place
+ *   dt       host array of k time steps (> 0), one per instance
+ *   nsteps   steps per call (>= 1); each instance's time += nsteps * dt
+ *   info     adg_batch_info fills up to n of: predictor tiles, cells per
+ *            predictor tile, predictor grid, corrector tiles, cells per
+ *            corrector tile, corrector grid, tuned time of candidates 0..2 (ns)
+ * adg_batch_step synchronises `stream` only when the dt array changed. */
+typedef struct adg_batch adg_batch;
+int adg_batch_create(adg_mesh* const* meshes, int k, adg_batch** out);
+int adg_batch_step(adg_batch* b, const double* dt, int nsteps, void* stream);
+int adg_batch_info(const adg_batch* b, int* info, int n);
+void adg_batch_destroy(adg_batch* b);
 
 /* ---- allocation-free step (the paper has no counterpart) ----
  *

@@ -84,6 +84,11 @@ SIGNATURES = {
     "adg_stable_dt": (_I, [_P, _D, ctypes.POINTER(_D), _P]),
     "adg_tv_indicator": (_I, [_P, _I, _D, _D, _P, _P, _P, _P]),
     "adg_check_finite": (_I, [_P, _P]),
+    "adg_step_adjoint": (_I, [_P, _D, _P, _P, _P, _P]),
+    "adg_batch_create": (_I, [ctypes.POINTER(_P), _I, ctypes.POINTER(_P)]),
+    "adg_batch_step": (_I, [_P, ctypes.POINTER(_D), _I, _P]),
+    "adg_batch_info": (_I, [_P, ctypes.POINTER(_I), _I]),
+    "adg_batch_destroy": (None, [_P]),
     "adg_step_noalloc": (_I, [ctypes.POINTER(MeshDesc), _P, _S, _D, _P]),
     "adg_last_error": (ctypes.c_char_p, []),
 }

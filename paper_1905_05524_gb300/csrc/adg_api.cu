@@ -150,8 +150,10 @@ struct adg_mesh {
     double* u = nullptr;
     double* rvol = nullptr;
     double* trace = nullptr;
+    double* trace_bar = nullptr; // adjoint of the traces (allocated on first adg_step_adjoint)
     double* tv = nullptr;
     double* stats = nullptr;     // device [2]
+    double* part = nullptr;      // device partial (count, mean, M2) triples of the TV statistics
     double* speed = nullptr;     // device partial maxima
     int speed_blocks = 0;
     int* flag = nullptr;         // device int
@@ -174,8 +176,10 @@ void free_mesh(adg_mesh* m) {
     cudaFree(m->u);
     cudaFree(m->rvol);
     cudaFree(m->trace);
+    cudaFree(m->trace_bar);
     cudaFree(m->tv);
     cudaFree(m->stats);
+    cudaFree(m->part);
     cudaFree(m->speed);
     cudaFree(m->flag);
     cudaFree(m->bgbuf);
@@ -369,6 +373,7 @@ int adg_create_mesh(const adg_mesh_desc* d, adg_mesh** out) {
     if (cudaMalloc(&m->u, cnt * 8) != cudaSuccess || cudaMalloc(&m->rvol, cnt * 8) != cudaSuccess ||
         cudaMalloc(&m->trace, tr * 8) != cudaSuccess || cudaMalloc(&m->tv, (size_t)m->cells * 8) != cudaSuccess ||
         cudaMalloc(&m->stats, 2 * 8) != cudaSuccess || cudaMalloc(&m->speed, (size_t)nb * 8) != cudaSuccess ||
+        cudaMalloc(&m->part, 3 * 8 * (size_t)adg::tv_stats_partials(m->cells)) != cudaSuccess ||
         cudaMalloc(&m->flag, sizeof(int)) != cudaSuccess || cudaMalloc(&m->bgbuf, nbg * 8) != cudaSuccess) {
         cudaGetLastError();
         free_mesh(m);
@@ -536,14 +541,40 @@ int adg_tv_indicator(adg_mesh* m, int var, double T_r, double T_c, double* tv, i
     if (!(T_r > T_c)) return fail(ADG_EINVAL, "tv_indicator: needs T_r > T_c");
     if (int rc = set_device(m)) return rc;
     double* tvbuf = tv ? tv : m->tv;
-    int e = adg::launch_tv_cells(m->N, m->u, tvbuf, m->cells, var, m->B, m->P, stream);
+    int e = m->d.precision == ADG_PREC_FP64
+                ? adg::launch_tv_cells(m->N, m->u, tvbuf, m->cells, var, m->B, m->P, stream)
+                : adg::launch_tv_cells_mixed(m->N, m->u, tvbuf, m->cells, var, m->Bf, m->Pf, m->mbg,
+                                             m->d.theta0, m->P.Rcp, stream);
     if (e) return cuda_fail((cudaError_t)e, "tv_indicator cells");
-    e = adg::launch_tv_stats(tvbuf, m->cells, T_r, T_c, m->stats, flags, stream);
+    e = adg::launch_tv_stats_multi(tvbuf, m->cells, T_r, T_c, m->part, m->stats, flags, stream);
     if (e) return cuda_fail((cudaError_t)e, "tv_indicator stats");
     if (stats) {
         ADG_CK(cudaMemcpyAsync(stats, m->stats, 16, cudaMemcpyDeviceToHost, (cudaStream_t)stream), "tv stats copy");
         ADG_CK(cudaStreamSynchronize((cudaStream_t)stream), "tv stats sync");
     }
+    return ADG_OK;
+}
+
+int adg_step_adjoint(adg_mesh* m, double dt, const double* u_n, const double* lam_np1, double* lam_n,
+                     void* stream) {
+    if (!m || !u_n || !lam_np1 || !lam_n) return fail(ADG_EINVAL, "step_adjoint: NULL argument");
+    if (!(dt > 0.0) || !std::isfinite(dt)) return fail(ADG_EINVAL, "step_adjoint: dt must be finite and > 0");
+    if (m->d.precision != ADG_PREC_FP64) return fail(ADG_EUNSUPPORTED, "step_adjoint: FP64 meshes only");
+    if (m->N > 5) return fail(ADG_EUNSUPPORTED, "step_adjoint: built for degree <= 5");
+    if (lam_n == lam_np1 || lam_n == u_n) return fail(ADG_EINVAL, "step_adjoint: lam_n must not alias the inputs");
+    if (int rc = set_device(m)) return rc;
+    const size_t tr = (size_t)m->cells * 4 * adg::kTraceComps * m->n;
+    if (!m->trace_bar && cudaMalloc(&m->trace_bar, tr * 8) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ADG_ENOMEM, "step_adjoint: trace adjoint buffer");
+    }
+    // forward traces at u_n (workspace), then the two adjoint kernels
+    int e = adg::launch_predictor_fp64(m->N, u_n, m->rvol, m->trace, m->cells, dt, m->t, m->B, m->P, m->bg, stream);
+    if (e) return cuda_fail((cudaError_t)e, "step_adjoint: forward predictor");
+    m->predicted = false;
+    e = adg::launch_step_adjoint_fp64(m->N, u_n, lam_np1, lam_n, m->trace, m->trace_bar, m->cells, dt, m->B, m->P,
+                                      m->bg, stream);
+    if (e) return cuda_fail((cudaError_t)e, "step_adjoint: adjoint kernels");
     return ADG_OK;
 }
 
@@ -709,4 +740,231 @@ extern "C" int adg_step_noalloc(const adg_mesh_desc* d, double* u, size_t count,
     e = adg::launch_corrector_fp64(N, u, rvol, trace, (int)cells, dt, B, P, bg, stream);
     if (e) return cuda_fail((cudaError_t)e, "step_noalloc: corrector launch");
     return ADG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Batched persistent step: many independent meshes (instances of different
+// sizes) advanced by one predictor and one corrector launch per step, each a
+// persistent grid walking a static tile list; nsteps steps are captured once
+// into a CUDA graph and replayed.  The tile size (cells per block) of the
+// predictor is chosen by timing the candidates on the batch itself.
+struct adg_batch {
+    int device = 0, N = 0, k = 0;
+    std::vector<adg_mesh*> meshes;
+    std::vector<adg::MixedInst> host_insts;
+    adg::MixedInst* insts = nullptr;
+    adg::BatchTile* tiles_pred = nullptr;
+    adg::BatchTile* tiles_corr = nullptr;
+    int ntiles_pred = 0, ntiles_corr = 0;
+    int cand_pred = 1, cand_corr = 1;
+    int cpb_pred = 0, cpb_corr = 0, blocks_pred = 0, blocks_corr = 0;
+    long long cells = 0;
+    std::vector<double> last_dt;
+    cudaStream_t cap = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraph_t graph = nullptr;
+    int graph_steps = 0;
+    double tune_ms[adg::kBatchCandidates] = {0, 0, 0};
+};
+
+namespace {
+
+std::mutex g_tune_mu;
+std::vector<std::pair<std::string, int>> g_tune_cache;  // key -> candidate
+
+std::vector<adg::BatchTile> make_tiles(const std::vector<adg_mesh*>& ms, int cpb) {
+    std::vector<adg::BatchTile> t;
+    for (int a = 0; a < (int)ms.size(); ++a)
+        for (int c = 0; c < ms[a]->cells; c += cpb) t.push_back({a, c});
+    return t;
+}
+
+void free_batch(adg_batch* b) {
+    if (!b) return;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    cudaFree(b->insts);
+    cudaFree(b->tiles_pred);
+    cudaFree(b->tiles_corr);
+    delete b;
+}
+
+int upload_tiles(adg_batch* b, int cand, int phase, adg::BatchTile** dst, int* ntiles, int* cpb, int* blocks) {
+    int c = 0, bl = 0;
+    int e = adg::launch_batch_mixed(b->N, cand, phase, nullptr, nullptr, 0, b->meshes[0]->Bf, &c, &bl, nullptr);
+    if (e) return cuda_fail((cudaError_t)e, "batch: query");
+    std::vector<adg::BatchTile> t = make_tiles(b->meshes, c);
+    cudaFree(*dst);
+    *dst = nullptr;
+    if (cudaMalloc(dst, t.size() * sizeof(adg::BatchTile)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ADG_ENOMEM, "batch: tile list");
+    }
+    ADG_CK(cudaMemcpy(*dst, t.data(), t.size() * sizeof(adg::BatchTile), cudaMemcpyHostToDevice), "batch: tiles");
+    *ntiles = (int)t.size();
+    *cpb = c;
+    *blocks = bl;
+    return ADG_OK;
+}
+
+}  // namespace
+
+extern "C" int adg_batch_create(adg_mesh* const* meshes, int k, adg_batch** out) {
+    if (!meshes || !out || k < 1) return fail(ADG_EINVAL, "batch_create: need k >= 1 meshes");
+    *out = nullptr;
+    for (int a = 0; a < k; ++a) {
+        if (!meshes[a]) return fail(ADG_EINVAL, "batch_create: NULL mesh");
+        if (meshes[a]->N != meshes[0]->N || meshes[a]->d.device != meshes[0]->d.device)
+            return fail(ADG_EINVAL, "batch_create: meshes must share degree and device");
+        if (meshes[a]->d.precision != ADG_PREC_MIXED)
+            return fail(ADG_EUNSUPPORTED, "batch_create: batched launch is built for ADG_PREC_MIXED meshes");
+    }
+    adg_batch* b = new adg_batch();
+    b->device = meshes[0]->d.device;
+    b->N = meshes[0]->N;
+    b->k = k;
+    b->meshes.assign(meshes, meshes + k);
+    b->last_dt.assign(k, -1.0);
+    if (int rc = set_device(meshes[0])) { delete b; return rc; }
+    b->host_insts.resize(k);
+    for (int a = 0; a < k; ++a) {
+        adg_mesh* m = meshes[a];
+        adg::MixedInst& I = b->host_insts[a];
+        I.u = m->u;
+        I.rvol = (float*)m->rvol;
+        I.trace = (float*)m->trace;
+        I.cells = m->cells;
+        I.dtf = 0.f;
+        I.dt = 0.0;
+        I.P = m->Pf;
+        I.bg = m->mbg;
+        b->cells += m->cells;
+    }
+    if (cudaMalloc(&b->insts, k * sizeof(adg::MixedInst)) != cudaSuccess) {
+        cudaGetLastError();
+        free_batch(b);
+        return fail(ADG_ENOMEM, "batch_create: instance table");
+    }
+    if (cudaMemcpy(b->insts, b->host_insts.data(), k * sizeof(adg::MixedInst), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaError_t e = cudaGetLastError();
+        free_batch(b);
+        return cuda_fail(e, "batch_create: setup");
+    }
+    // autotune the predictor tile size (the predictor only reads the state)
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
+    int bucket = 0;
+    for (long long c = b->cells; c > 1; c >>= 1) ++bucket;
+    char keybuf[96];
+    std::snprintf(keybuf, sizeof(keybuf), "mixed N=%d sms=%d cells~2^%d", b->N, sms, bucket);
+    const std::string key(keybuf);
+    int best = -1;
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        for (auto& kv : g_tune_cache)
+            if (kv.first == key) best = kv.second;
+    }
+    if (best < 0) {
+        float best_ms = 1e30f;
+        cudaEvent_t e0, e1;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        for (int c = 0; c < adg::kBatchCandidates; ++c) {
+            int rc = upload_tiles(b, c, 0, &b->tiles_pred, &b->ntiles_pred, &b->cpb_pred, &b->blocks_pred);
+            if (rc) { cudaEventDestroy(e0); cudaEventDestroy(e1); free_batch(b); return rc; }
+            int e = adg::launch_batch_mixed(b->N, c, 0, b->insts, b->tiles_pred, b->ntiles_pred, meshes[0]->Bf,
+                                            nullptr, &b->blocks_pred, b->cap);  // warm-up
+            cudaEventRecord(e0, b->cap);
+            for (int r = 0; r < 3 && !e; ++r)
+                e = adg::launch_batch_mixed(b->N, c, 0, b->insts, b->tiles_pred, b->ntiles_pred, meshes[0]->Bf,
+                                            nullptr, &b->blocks_pred, b->cap);
+            cudaEventRecord(e1, b->cap);
+            if (e || cudaEventSynchronize(e1) != cudaSuccess) {
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                free_batch(b);
+                return cuda_fail(e ? (cudaError_t)e : cudaGetLastError(), "batch_create: autotune");
+            }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            b->tune_ms[c] = ms / 3.0;
+            if (ms < best_ms) { best_ms = ms; best = c; }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        g_tune_cache.push_back({key, best});
+    }
+    b->cand_pred = best;
+    int rc = upload_tiles(b, b->cand_pred, 0, &b->tiles_pred, &b->ntiles_pred, &b->cpb_pred, &b->blocks_pred);
+    if (!rc) rc = upload_tiles(b, b->cand_corr, 1, &b->tiles_corr, &b->ntiles_corr, &b->cpb_corr, &b->blocks_corr);
+    if (rc) { free_batch(b); return rc; }
+    *out = b;
+    return ADG_OK;
+}
+
+extern "C" int adg_batch_info(const adg_batch* b, int* info, int n) {
+    if (!b || !info || n < 1) return fail(ADG_EINVAL, "batch_info: NULL argument");
+    const int v[9] = {b->ntiles_pred, b->cpb_pred, b->blocks_pred, b->ntiles_corr, b->cpb_corr, b->blocks_corr,
+                      (int)(b->tune_ms[0] * 1000), (int)(b->tune_ms[1] * 1000), (int)(b->tune_ms[2] * 1000)};
+    for (int a = 0; a < n && a < 9; ++a) info[a] = v[a];
+    return ADG_OK;
+}
+
+extern "C" int adg_batch_step(adg_batch* b, const double* dt, int nsteps, void* stream) {
+    if (!b || !dt) return fail(ADG_EINVAL, "batch_step: NULL argument");
+    if (nsteps < 1) return fail(ADG_EINVAL, "batch_step: nsteps must be >= 1");
+    for (int a = 0; a < b->k; ++a)
+        if (!(dt[a] > 0.0) || !std::isfinite(dt[a])) return fail(ADG_EINVAL, "batch_step: dt must be finite and > 0");
+    ADG_CK(cudaSetDevice(b->device), "batch_step: cudaSetDevice");
+    cudaStream_t s = (cudaStream_t)stream;
+    bool changed = false;
+    for (int a = 0; a < b->k; ++a)
+        if (dt[a] != b->last_dt[a]) {
+            changed = true;
+            b->last_dt[a] = dt[a];
+            b->host_insts[a].dt = dt[a];
+            b->host_insts[a].dtf = (float)dt[a];
+        }
+    if (changed) {
+        ADG_CK(cudaMemcpyAsync(b->insts, b->host_insts.data(), b->k * sizeof(adg::MixedInst),
+                               cudaMemcpyHostToDevice, s), "batch_step: dt upload");
+        // the staging vector must stay valid until the copy has run
+        ADG_CK(cudaStreamSynchronize(s), "batch_step: dt upload sync");
+    }
+    if (!b->exec || b->graph_steps != nsteps) {
+        if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
+        if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
+        ADG_CK(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal), "batch_step: begin capture");
+        int e = 0;
+        for (int st = 0; st < nsteps && !e; ++st) {
+            e = adg::launch_batch_mixed(b->N, b->cand_pred, 0, b->insts, b->tiles_pred, b->ntiles_pred,
+                                        b->meshes[0]->Bf, nullptr, &b->blocks_pred, b->cap);
+            if (!e)
+                e = adg::launch_batch_mixed(b->N, b->cand_corr, 1, b->insts, b->tiles_corr, b->ntiles_corr,
+                                            b->meshes[0]->Bf, nullptr, &b->blocks_corr, b->cap);
+        }
+        cudaGraph_t g = nullptr;
+        cudaError_t ce = cudaStreamEndCapture(b->cap, &g);
+        if (e) { if (g) cudaGraphDestroy(g); return cuda_fail((cudaError_t)e, "batch_step: capture launch"); }
+        if (ce != cudaSuccess) return cuda_fail(ce, "batch_step: end capture");
+        b->graph = g;
+        ADG_CK(cudaGraphInstantiate(&b->exec, g, 0), "batch_step: instantiate");
+        b->graph_steps = nsteps;
+    }
+    ADG_CK(cudaGraphLaunch(b->exec, s), "batch_step: graph launch");
+    for (int a = 0; a < b->k; ++a) {
+        b->meshes[a]->t += nsteps * dt[a];
+        b->meshes[a]->predicted = false;
+    }
+    return ADG_OK;
+}
+
+extern "C" void adg_batch_destroy(adg_batch* b) {
+    if (!b) return;
+    cudaSetDevice(b->device);
+    cudaDeviceSynchronize();
+    free_batch(b);
 }

@@ -76,6 +76,23 @@ struct MixedBg {
     const float* face;  // [ny][2][kFaceBg]
 };
 
+// One instance of a batched launch (device table entry) and one tile of
+// consecutive cells of an instance.
+struct MixedInst {
+    double* u;
+    float* rvol;
+    float* trace;
+    int cells;
+    float dtf;
+    double dt;
+    PhysF P;
+    MixedBg bg;
+};
+struct BatchTile {
+    int inst, c0;
+};
+constexpr int kBatchCandidates = 3;  // tile-size candidates the autotuner times
+
 // Kernel launchers (adg_fp64.cu, adg_mixed.cu, adg_tv.cu).  They return a
 // cudaError_t value as int.
 int launch_predictor_fp64(int N, const double* u, double* rvol, double* trace, int cells,
@@ -88,10 +105,23 @@ int launch_predictor_mixed(int N, const double* u, float* rvol, float* trace, in
                            const BasisF& B, const PhysF& P, const MixedBg& bg, void* stream);
 int launch_corrector_mixed(int N, double* u, const float* rvol, const float* trace, int cells,
                            double dt, const BasisF& B, const PhysF& P, const MixedBg& bg, void* stream);
+// phase 0: predictor, 1: corrector.  tiles == nullptr: query -- returns the
+// cells per block and writes the persistent grid size to *blocks_out; otherwise
+// launches with the grid size in *blocks_out.
+int launch_batch_mixed(int N, int cand, int phase, const MixedInst* insts, const BatchTile* tiles,
+                       int ntiles, const BasisF& B, int* cpb_out, int* blocks_out, void* stream);
+int launch_step_adjoint_fp64(int N, const double* u, const double* lam, double* lam_out, const double* trace,
+                             double* trace_bar, int cells, double dt, const Basis& B, const Phys& P,
+                             const Background& bg, void* stream);
 int launch_tv_cells(int N, const double* u, double* tv, int cells, int var, const Basis& B,
                     const Phys& P, void* stream);
-int launch_tv_stats(const double* tv, int cells, double T_r, double T_c, double* stats_dev,
-                    int8_t* flags, void* stream);
+int launch_tv_cells_mixed(int N, const double* u, double* tv, int cells, int var, const BasisF& B,
+                          const PhysF& P, const MixedBg& bg, double theta0, double Rcp, void* stream);
+// multi-block deterministic statistics: `part` is scratch of 3 * tv_stats_partials(cells) doubles
+int tv_stats_chunk(int cells);
+int tv_stats_partials(int cells);
+int launch_tv_stats_multi(const double* tv, int cells, double T_r, double T_c, double* part,
+                          double* stats_dev, int8_t* flags, void* stream);
 int launch_max_speed(int N, const double* u, double* partial, int cells, const Basis& B,
                      const Phys& P, int* nblocks_out, void* stream);
 int launch_init_scenario(int N, double* u, int cells, int kind, double A, double a, double xc,

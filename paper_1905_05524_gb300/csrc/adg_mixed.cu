@@ -84,27 +84,34 @@ __device__ __forceinline__ float wave_speed_f(float rho, float mx, float my, flo
     return vn + c + 2.f * (xdir ? P.eta_x : P.eta_y) * P.lamv * rinv;
 }
 
-template <int N>
+template <int N, int CPB_ = 0>
 struct MixCfg {
     static constexpr int n = N + 1;
-    static constexpr int cpb = N == 1 ? 32 : N == 2 ? 16 : N == 3 ? 8 : N <= 5 ? 4 : 2;
+    static constexpr int cpb_default = N == 1 ? 32 : N == 2 ? 16 : N == 3 ? 8 : N <= 5 ? 4 : 2;
+    static constexpr int cpb = CPB_ ? CPB_ : cpb_default;
     static constexpr int threads = cpb * n * n;
-    static constexpr size_t smem_pred = (size_t)cpb * 3 * n * 4 * n * n * sizeof(float);
+    // per-cell smem stride padded to 16 (mod 32) floats: neighbouring cells of
+    // one warp then fall on disjoint banks in the row/column contractions
+    static constexpr int raw = 3 * n * 4 * n * n;
+    static constexpr int stride = raw + ((16 - raw % 32) + 32) % 32;
+    static constexpr size_t smem_pred = (size_t)cpb * stride * sizeof(float);
 };
 
+// Predictor body for the tile of CPB cells starting at cell c0 (one thread per
+// spatial node); shared by the per-mesh kernel and the batched persistent one.
 template <int N, int CPB>
-__global__ void __launch_bounds__(CPB*(N + 1) * (N + 1))
-k_predictor_mixed(const double* __restrict__ u, float* __restrict__ rvol, float* __restrict__ trace,
-                  int cells, float dt, const BasisF B, const PhysF P, const MixedBg bg) {
+__device__ __forceinline__ void predictor_mixed_body(const double* __restrict__ u, float* __restrict__ rvol,
+                                                     float* __restrict__ trace, int cells, int c0, float dt,
+                                                     const BasisF& B, const PhysF& P, const MixedBg& bg,
+                                                     float* smf) {
     constexpr int n = N + 1, n2 = n * n, SL = 4 * n2;
-    extern __shared__ float smf[];
     const int cl = threadIdx.x / n2;
     const int node = threadIdx.x - cl * n2;
     const int j = node / n, i = node - j * n;
-    const int cell_raw = blockIdx.x * CPB + cl;
+    const int cell_raw = c0 + cl;
     const bool active = cell_raw < cells;
     const int cell = active ? cell_raw : cells - 1;
-    float* Q = smf + (size_t)cl * (3 * n * SL);
+    float* Q = smf + (size_t)cl * MixCfg<N, CPB>::stride;
     float* Fs = Q + n * SL;
     float* Gs = Fs + n * SL;
     const int ix = cell % P.nx, iy = cell / P.nx;
@@ -350,16 +357,16 @@ __device__ __forceinline__ void rusanov_f(const float qL[4], const float fL[4], 
 }
 
 template <int N, int CPB>
-__global__ void __launch_bounds__(CPB*(N + 1) * (N + 1))
-k_corrector_mixed(double* __restrict__ u, const float* __restrict__ rvol,
-                  const float* __restrict__ trace, int cells, double dt, const BasisF B,
-                  const PhysF P, const MixedBg bg) {
+__device__ __forceinline__ void corrector_mixed_body(double* __restrict__ u, const float* __restrict__ rvol,
+                                                     const float* __restrict__ trace, int cells, int c0,
+                                                     double dt, const BasisF& B, const PhysF& P,
+                                                     const MixedBg& bg) {
     constexpr int n = N + 1, n2 = n * n, SL = 4 * n2, TR = kTraceComps * n;
     __shared__ float Fst[CPB][4][4][n];
     const int cl = threadIdx.x / n2;
     const int node = threadIdx.x - cl * n2;
     const int j = node / n, i = node - j * n;
-    const int cell_raw = blockIdx.x * CPB + cl;
+    const int cell_raw = c0 + cl;
     const bool active = cell_raw < cells;
     const int cell = active ? cell_raw : cells - 1;
     const int ix = cell % P.nx, iy = cell / P.nx;
@@ -425,6 +432,54 @@ k_corrector_mixed(double* __restrict__ u, const float* __restrict__ rvol,
     }
 }
 
+template <int N, int CPB>
+__global__ void __launch_bounds__(CPB*(N + 1) * (N + 1))
+k_predictor_mixed(const double* __restrict__ u, float* __restrict__ rvol, float* __restrict__ trace,
+                  int cells, float dt, const BasisF B, const PhysF P, const MixedBg bg) {
+    extern __shared__ float smf[];
+    predictor_mixed_body<N, CPB>(u, rvol, trace, cells, blockIdx.x * CPB, dt, B, P, bg, smf);
+}
+
+template <int N, int CPB>
+__global__ void __launch_bounds__(CPB*(N + 1) * (N + 1))
+k_corrector_mixed(double* __restrict__ u, const float* __restrict__ rvol,
+                  const float* __restrict__ trace, int cells, double dt, const BasisF B,
+                  const PhysF P, const MixedBg bg) {
+    corrector_mixed_body<N, CPB>(u, rvol, trace, cells, blockIdx.x * CPB, dt, B, P, bg);
+}
+
+// Batched persistent kernels: a fixed grid walks a list of tiles (instance,
+// first cell) of many independent meshes; tile t goes to block t mod grid,
+// so the schedule is static and the results do not depend on timing.
+template <int N, int CPB>
+__global__ void __launch_bounds__(CPB*(N + 1) * (N + 1))
+k_predictor_mixed_batch(const MixedInst* __restrict__ insts, const BatchTile* __restrict__ tiles,
+                        int ntiles, const BasisF B) {
+    extern __shared__ float smf[];
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const BatchTile tl = tiles[t];
+        const MixedInst& I = insts[tl.inst];
+        const PhysF P = I.P;
+        const MixedBg bg = I.bg;
+        predictor_mixed_body<N, CPB>(I.u, I.rvol, I.trace, I.cells, tl.c0, I.dtf, B, P, bg, smf);
+        __syncthreads();
+    }
+}
+
+template <int N, int CPB>
+__global__ void __launch_bounds__(CPB*(N + 1) * (N + 1))
+k_corrector_mixed_batch(const MixedInst* __restrict__ insts, const BatchTile* __restrict__ tiles,
+                        int ntiles, const BasisF B) {
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const BatchTile tl = tiles[t];
+        const MixedInst& I = insts[tl.inst];
+        const PhysF P = I.P;
+        const MixedBg bg = I.bg;
+        corrector_mixed_body<N, CPB>(I.u, I.rvol, I.trace, I.cells, tl.c0, I.dt, B, P, bg);
+        __syncthreads();
+    }
+}
+
 template <int N>
 static int launch_pred_mixed(const double* u, float* rvol, float* trace, int cells, float dt,
                              const BasisF& B, const PhysF& P, const MixedBg& bg, cudaStream_t s) {
@@ -473,6 +528,75 @@ int launch_corrector_mixed(int N, double* u, const float* rvol, const float* tra
         case 5: return launch_corr_mixed<5>(u, rvol, trace, cells, dt, B, P, bg, s);
         case 6: return launch_corr_mixed<6>(u, rvol, trace, cells, dt, B, P, bg, s);
         case 7: return launch_corr_mixed<7>(u, rvol, trace, cells, dt, B, P, bg, s);
+    }
+    return (int)cudaErrorInvalidValue;
+}
+
+// ------------------------------------------------------------ batched launch
+// Tile-size candidates per degree: half, default and double the default cells
+// per block (kept within 1024 threads and the shared-memory limit).
+template <int N, int K>
+struct BatchCand {
+    static constexpr int base = MixCfg<N>::cpb_default;
+    static constexpr int raw = K == 0 ? base / 2 : K == 1 ? base : base * 2;
+    static constexpr int cpb = raw < 1 ? 1 : ((raw * (N + 1) * (N + 1) > 1024) ? base : raw);
+};
+
+template <int N, int K>
+static int batch_mixed_nk(int phase, const MixedInst* insts, const BatchTile* tiles, int ntiles,
+                          const BasisF& B, int* cpb_out, int* blocks_io, cudaStream_t s) {
+    constexpr int CPB = BatchCand<N, K>::cpb;
+    using C = MixCfg<N, CPB>;
+    if (cpb_out) *cpb_out = CPB;
+    if (!tiles) {  // query: set the smem limit and size the persistent grid (not during capture)
+        int per_sm = 0, dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaError_t e;
+        if (phase == 0) {
+            e = cudaFuncSetAttribute(k_predictor_mixed_batch<N, CPB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)C::smem_pred);
+            if (e == cudaSuccess)
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_predictor_mixed_batch<N, CPB>,
+                                                                  C::threads, C::smem_pred);
+        } else {
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_corrector_mixed_batch<N, CPB>,
+                                                              C::threads, 0);
+        }
+        if (e != cudaSuccess) return (int)e;
+        if (blocks_io) *blocks_io = per_sm > 0 ? per_sm * sms : sms;
+        return 0;
+    }
+    const int blocks = *blocks_io;
+    if (phase == 0)
+        k_predictor_mixed_batch<N, CPB><<<blocks, C::threads, C::smem_pred, s>>>(insts, tiles, ntiles, B);
+    else
+        k_corrector_mixed_batch<N, CPB><<<blocks, C::threads, 0, s>>>(insts, tiles, ntiles, B);
+    return (int)cudaGetLastError();
+}
+
+template <int N>
+static int batch_mixed_n(int cand, int phase, const MixedInst* insts, const BatchTile* tiles, int ntiles,
+                         const BasisF& B, int* cpb_out, int* blocks_out, cudaStream_t s) {
+    switch (cand) {
+        case 0: return batch_mixed_nk<N, 0>(phase, insts, tiles, ntiles, B, cpb_out, blocks_out, s);
+        case 1: return batch_mixed_nk<N, 1>(phase, insts, tiles, ntiles, B, cpb_out, blocks_out, s);
+        case 2: return batch_mixed_nk<N, 2>(phase, insts, tiles, ntiles, B, cpb_out, blocks_out, s);
+    }
+    return (int)cudaErrorInvalidValue;
+}
+
+int launch_batch_mixed(int N, int cand, int phase, const MixedInst* insts, const BatchTile* tiles,
+                       int ntiles, const BasisF& B, int* cpb_out, int* blocks_out, void* stream) {
+    cudaStream_t s = (cudaStream_t)stream;
+    switch (N) {
+        case 1: return batch_mixed_n<1>(cand, phase, insts, tiles, ntiles, B, cpb_out, blocks_out, s);
+        case 2: return batch_mixed_n<2>(cand, phase, insts, tiles, ntiles, B, cpb_out, blocks_out, s);
+        case 3: return batch_mixed_n<3>(cand, phase, insts, tiles, ntiles, B, cpb_out, blocks_out, s);
+        case 4: return batch_mixed_n<4>(cand, phase, insts, tiles, ntiles, B, cpb_out, blocks_out, s);
+        case 5: return batch_mixed_n<5>(cand, phase, insts, tiles, ntiles, B, cpb_out, blocks_out, s);
+        case 6: return batch_mixed_n<6>(cand, phase, insts, tiles, ntiles, B, cpb_out, blocks_out, s);
+        case 7: return batch_mixed_n<7>(cand, phase, insts, tiles, ntiles, B, cpb_out, blocks_out, s);
     }
     return (int)cudaErrorInvalidValue;
 }

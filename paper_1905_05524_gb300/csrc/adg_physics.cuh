@@ -112,3 +112,155 @@ __device__ __forceinline__ void rusanov(const double qL[4], const double fL[4], 
 }
 
 }  // namespace adg
+
+namespace adg {
+
+// Reverse (adjoint) of ns_flux: given the adjoints Fb, Gb, Sb of its outputs
+// at the point (q, qx, qy), accumulate the adjoints of q, qx, qy.  With
+// use_heat the heat-flux gradient is a constant (wall ghost) and carries no
+// adjoint to qx, qy.  Written line by line against ns_flux above.
+__device__ __forceinline__ void ns_flux_adj(const double q[4], const double qx[4], const double qy[4],
+                                            double z, const Phys& P, const double Fb[4], const double Gb[4],
+                                            const double Sb[4], double qb[4], double qxb[4], double qyb[4],
+                                            bool use_heat = false) {
+    // ---- forward recompute
+    const double rho = q[0], mx = q[1], my = q[2], E = q[3];
+    const double rinv = 1.0 / rho;
+    const double u = mx * rinv, v = my * rinv;
+    const double gz = P.gravity ? P.g * z : 0.0;
+    const double p = P.gm1 * (E - 0.5 * (mx * u + my * v) - rho * gz);
+    const double T = p * rinv * P.invR;
+    const double ux = (qx[1] - u * qx[0]) * rinv;
+    const double uy = (qy[1] - u * qy[0]) * rinv;
+    const double vx = (qx[2] - v * qx[0]) * rinv;
+    const double vy = (qy[2] - v * qy[0]) * rinv;
+    const double kin = 0.5 * (u * u + v * v);
+    double px = 0.0, py = 0.0;
+    if (!use_heat) {
+        px = P.gm1 * (qx[3] - (u * qx[1] + v * qx[2]) + kin * qx[0] - gz * qx[0]);
+        py = P.gm1 * (qy[3] - (u * qy[1] + v * qy[2]) + kin * qy[0] - gz * qy[0] - (P.gravity ? rho * P.g : 0.0));
+    }
+    const double div = ux + vy;
+    const double sxx = P.mu * ((2.0 / 3.0) * div - 2.0 * ux);
+    const double syy = P.mu * ((2.0 / 3.0) * div - 2.0 * vy);
+    const double sxy = -P.mu * (uy + vx);
+    const double Ep = E + p;
+    // ---- reverse
+    double mx_b = Fb[0] + Fb[1] * u + Gb[1] * v;
+    double my_b = Gb[0] + Fb[2] * u + Gb[2] * v;
+    double u_b = Fb[1] * mx + Fb[2] * my + Fb[3] * (Ep + sxx) + Gb[3] * sxy;
+    double v_b = Fb[3] * sxy + Gb[1] * mx + Gb[2] * my + Gb[3] * (Ep + syy);
+    double pp_b = Fb[1] + Gb[2];
+    double sxx_b = Fb[1] + Fb[3] * u;
+    double syy_b = Gb[2] + Gb[3] * v;
+    double sxy_b = Fb[2] + Fb[3] * v + Gb[1] + Gb[3] * u;
+    const double Ep_b = Fb[3] * u + Gb[3] * v;
+    const double Tx_b = -P.kappa * Fb[3];
+    const double Ty_b = -P.kappa * Gb[3];
+    double rho_b = P.gravity ? -P.g * Sb[2] : 0.0;
+    double E_b = Ep_b;
+    double p_b = Ep_b + pp_b;
+    double rinv_b = 0.0, T_b = 0.0, kin_b = 0.0;
+    // stresses
+    const double uy_b = -P.mu * sxy_b;
+    const double vx_b = -P.mu * sxy_b;
+    const double div_b = P.mu * (2.0 / 3.0) * (sxx_b + syy_b);
+    const double ux_b = -2.0 * P.mu * sxx_b + div_b;
+    const double vy_b = -2.0 * P.mu * syy_b + div_b;
+    // heat flux
+    if (!use_heat) {
+        const double a = rinv * P.invR;
+        const double px_b = Tx_b * a, py_b = Ty_b * a;
+        T_b += -P.R * a * (qx[0] * Tx_b + qy[0] * Ty_b);
+        qxb[0] += -P.R * T * a * Tx_b;
+        qyb[0] += -P.R * T * a * Ty_b;
+        rinv_b += P.invR * ((px - P.R * T * qx[0]) * Tx_b + (py - P.R * T * qy[0]) * Ty_b);
+        // px, py
+        qxb[3] += P.gm1 * px_b;
+        qyb[3] += P.gm1 * py_b;
+        u_b += -P.gm1 * (qx[1] * px_b + qy[1] * py_b);
+        v_b += -P.gm1 * (qx[2] * px_b + qy[2] * py_b);
+        qxb[1] += -P.gm1 * u * px_b;
+        qyb[1] += -P.gm1 * u * py_b;
+        qxb[2] += -P.gm1 * v * px_b;
+        qyb[2] += -P.gm1 * v * py_b;
+        kin_b += P.gm1 * (qx[0] * px_b + qy[0] * py_b);
+        qxb[0] += P.gm1 * (kin - gz) * px_b;
+        qyb[0] += P.gm1 * (kin - gz) * py_b;
+        if (P.gravity) rho_b += -P.gm1 * P.g * py_b;
+    }
+    u_b += u * kin_b;
+    v_b += v * kin_b;
+    // velocity gradients
+    qxb[1] += rinv * ux_b;
+    u_b += -qx[0] * rinv * ux_b;
+    qxb[0] += -u * rinv * ux_b;
+    rinv_b += (qx[1] - u * qx[0]) * ux_b;
+    qyb[1] += rinv * uy_b;
+    u_b += -qy[0] * rinv * uy_b;
+    qyb[0] += -u * rinv * uy_b;
+    rinv_b += (qy[1] - u * qy[0]) * uy_b;
+    qxb[2] += rinv * vx_b;
+    v_b += -qx[0] * rinv * vx_b;
+    qxb[0] += -v * rinv * vx_b;
+    rinv_b += (qx[2] - v * qx[0]) * vx_b;
+    qyb[2] += rinv * vy_b;
+    v_b += -qy[0] * rinv * vy_b;
+    qyb[0] += -v * rinv * vy_b;
+    rinv_b += (qy[2] - v * qy[0]) * vy_b;
+    // T = p rinv / R
+    p_b += rinv * P.invR * T_b;
+    rinv_b += p * P.invR * T_b;
+    // p = gm1 (E - (mx u + my v)/2 - rho gz)
+    E_b += P.gm1 * p_b;
+    const double kem_b = -0.5 * P.gm1 * p_b;
+    rho_b += -P.gm1 * gz * p_b;
+    mx_b += u * kem_b;
+    u_b += mx * kem_b;
+    my_b += v * kem_b;
+    v_b += my * kem_b;
+    // u = mx rinv, v = my rinv
+    mx_b += rinv * u_b;
+    rinv_b += mx * u_b;
+    my_b += rinv * v_b;
+    rinv_b += my * v_b;
+    rho_b += -rinv * rinv * rinv_b;
+    qb[0] += rho_b;
+    qb[1] += mx_b;
+    qb[2] += my_b;
+    qb[3] += E_b;
+}
+
+// Reverse of wave_speed: accumulate d s / d q * sb into qb.  |v.n| takes the
+// sign of v.n (0 at exactly 0).
+__device__ __forceinline__ void wave_speed_adj(const double q[4], double z, bool xdir, const Phys& P,
+                                               double sb, double qb[4]) {
+    const double rinv = 1.0 / q[0];
+    const double u = q[1] * rinv, v = q[2] * rinv;
+    const double gz = P.gravity ? P.g * z : 0.0;
+    const double p = P.gm1 * (q[3] - 0.5 * (q[1] * u + q[2] * v) - q[0] * gz);
+    const double c = sqrt(P.gamma * p * rinv);
+    const double eta = xdir ? P.eta_x : P.eta_y;
+    const double vn = xdir ? u : v;
+    const double sgn = vn > 0.0 ? 1.0 : (vn < 0.0 ? -1.0 : 0.0);
+    double u_b = xdir ? sgn * sb : 0.0;
+    double v_b = xdir ? 0.0 : sgn * sb;
+    const double c_b = sb;
+    double rinv_b = 2.0 * eta * P.lamv * sb;
+    const double p_b = P.gamma * rinv / (2.0 * c) * c_b;
+    rinv_b += P.gamma * p / (2.0 * c) * c_b;
+    qb[3] += P.gm1 * p_b;
+    const double kem_b = -0.5 * P.gm1 * p_b;
+    qb[0] += -P.gm1 * gz * p_b;
+    qb[1] += u * kem_b;
+    u_b += q[1] * kem_b;
+    qb[2] += v * kem_b;
+    v_b += q[2] * kem_b;
+    qb[1] += rinv * u_b;
+    rinv_b += q[1] * u_b;
+    qb[2] += rinv * v_b;
+    rinv_b += q[2] * v_b;
+    qb[0] += -rinv * rinv * rinv_b;
+}
+
+}  // namespace adg

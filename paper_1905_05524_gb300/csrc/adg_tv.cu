@@ -5,8 +5,8 @@
 // (potential temperature, Sec. 4.2) or rho at the nodes, derivatives by the
 // nodal derivative matrix.  Mean and population standard deviation over all
 // cells follow Chan, Golub and LeVeque's pairwise update (cited by the paper
-// for a parallel, stable evaluation): each thread accumulates a strided
-// subset with Welford's update, then partial (count, mean, M2) triples are
+// for a parallel, stable evaluation): contiguous chunks are reduced exactly
+// (two-pass) per block, then the partial (count, mean, M2) triples are
 // combined in a fixed binary tree, so the result is deterministic.
 #include <cuda_runtime.h>
 
@@ -65,27 +65,122 @@ k_tv_cells(const double* __restrict__ u, double* __restrict__ tv, int cells, int
     }
 }
 
-constexpr int kStatThreads = 1024;
+// Mixed-precision TV: the indicator field is formed from the FP64 state by
+// the FP64 perturbation split (rho' = rho - rhobar, E' = rhoE - Ebar) and then
+// in FP32.  For theta the potential-temperature perturbation is evaluated
+// without the 300 K offset,
+//     theta'/theta0 = (1 + p'/pbar)^(1-R/cp) / (1 + rho'/rhobar) - 1
+//                   = expm1((1 - R/cp) log1p(p'/pbar) - log1p(rho'/rhobar)),
+// (theta = p^(1-R/cp) p0^(R/cp) / (rho R) and theta0 is the same expression
+// at the background), so no FP32 value carries theta ~ 300 K.  For rho the
+// field is rho' and the background gradient d rhobar/dz is added.
+template <int N, int CPB>
+__global__ void __launch_bounds__(CPB*(N + 1) * (N + 1))
+k_tv_cells_mixed(const double* __restrict__ u, double* __restrict__ tv, int cells, int var,
+                 const BasisF B, const PhysF P, const MixedBg bg, float theta0, float one_m_kappa) {
+    constexpr int n = N + 1, n2 = n * n, SL = 4 * n2;
+    __shared__ float fs[CPB][n2];
+    __shared__ float red[CPB][n2];
+    const int cl = threadIdx.x / n2;
+    const int node = threadIdx.x - cl * n2;
+    const int j = node / n, i = node - j * n;
+    const int cell_raw = blockIdx.x * CPB + cl;
+    const bool active = cell_raw < cells;
+    const int cell = active ? cell_raw : cells - 1;
+    const int iy = cell / P.nx;
+    const int row = iy * n + j;
+    const double* uc = u + (size_t)cell * SL;
+    const float rp = (float)(uc[node] - bg.rb[row]);
+    float f;
+    if (var == ADG_TV_THETA) {
+        const float Ep = (float)(uc[3 * n2 + node] - bg.Eb[row]);
+        const float mx = (float)uc[n2 + node], my = (float)uc[2 * n2 + node];
+        const float rb = (float)bg.rb[row];
+        const float rho = rb + rp;
+        const float z = P.y0 + (iy + B.xi[j]) * P.hy;
+        const float pp = P.gm1 * (Ep - 0.5f * (mx * mx + my * my) / rho - P.g * z * rp);
+        f = theta0 * expm1f(one_m_kappa * log1pf(pp / bg.pb[row]) - log1pf(rp / rb));
+    } else {
+        f = rp;
+    }
+    fs[cl][node] = f;
+    __syncthreads();
+    float fx = 0.f, fy = 0.f;
+#pragma unroll
+    for (int p = 0; p < n; ++p) {
+        fx = fmaf(B.D[i][p], fs[cl][j * n + p], fx);
+        fy = fmaf(B.D[j][p], fs[cl][p * n + i], fy);
+    }
+    fx *= P.inv_hx;
+    fy *= P.inv_hy;
+    if (var != ADG_TV_THETA) fy += bg.dzr[row];
+    red[cl][node] = B.w[i] * B.w[j] * (fabsf(fx) + fabsf(fy));
+    __syncthreads();
+    if (node == 0 && active) {
+        double s = 0.0;
+        for (int a = 0; a < n2; ++a) s += (double)red[cl][a];
+        tv[cell] = (double)P.hx * (double)P.hy * s;
+    }
+}
 
-__global__ void __launch_bounds__(kStatThreads)
-k_tv_stats(const double* __restrict__ tv, int cells, double T_r, double T_c,
-           double* __restrict__ stats, int8_t* __restrict__ flags) {
-    __shared__ double sc[kStatThreads], smean[kStatThreads], sm2[kStatThreads];
+// Multi-block statistics.  Block b owns the contiguous chunk of cells
+// [b*chunk, min((b+1)*chunk, cells)); it forms the chunk's count, mean and M2
+// by an exact two-pass reduction in a fixed tree and writes the triple to
+// part[b] (scratch).  k_tv_final then combines the partial triples with Chan
+// et al.'s pairwise update in a fixed binary tree (deterministic) and writes
+// the flags.
+constexpr int kPartThreads = 256;
+
+__device__ __forceinline__ double block_sum_256(double v, double* sh) {
+    const int t = threadIdx.x;
+    sh[t] = v;
+    __syncthreads();
+    for (int s = kPartThreads / 2; s > 0; s >>= 1) {
+        if (t < s) sh[t] += sh[t + s];
+        __syncthreads();
+    }
+    const double r = sh[0];
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(kPartThreads)
+k_tv_partials(const double* __restrict__ tv, int cells, int chunk, double* __restrict__ part) {
+    __shared__ double sh[kPartThreads];
+    const int b = blockIdx.x;
+    const int lo = b * chunk;
+    const int hi = min(cells, lo + chunk);
+    double s = 0.0;
+    for (int c = lo + threadIdx.x; c < hi; c += kPartThreads) s += tv[c];
+    const double cnt = (double)max(0, hi - lo);
+    const double sum = block_sum_256(s, sh);
+    const double mean = cnt > 0.0 ? sum / cnt : 0.0;
+    double q = 0.0;
+    for (int c = lo + threadIdx.x; c < hi; c += kPartThreads) {
+        const double d = tv[c] - mean;
+        q += d * d;
+    }
+    const double m2 = block_sum_256(q, sh);
+    if (threadIdx.x == 0) {
+        part[3 * b + 0] = cnt;
+        part[3 * b + 1] = mean;
+        part[3 * b + 2] = m2;
+    }
+}
+
+constexpr int kMaxPartials = 1024;
+
+__global__ void __launch_bounds__(kMaxPartials)
+k_tv_final(const double* __restrict__ part, int nparts, const double* __restrict__ tv, int cells,
+           double T_r, double T_c, double* __restrict__ stats, int8_t* __restrict__ flags) {
+    __shared__ double sc[kMaxPartials], smean[kMaxPartials], sm2[kMaxPartials];
     __shared__ double mu_sig[2];
     const int t = threadIdx.x;
-    double cnt = 0.0, mean = 0.0, m2 = 0.0;
-    for (int c = t; c < cells; c += kStatThreads) {  // Welford on a strided subset
-        const double x = tv[c];
-        cnt += 1.0;
-        const double d = x - mean;
-        mean += d / cnt;
-        m2 += d * (x - mean);
-    }
-    sc[t] = cnt;
-    smean[t] = mean;
-    sm2[t] = m2;
+    sc[t] = t < nparts ? part[3 * t] : 0.0;
+    smean[t] = t < nparts ? part[3 * t + 1] : 0.0;
+    sm2[t] = t < nparts ? part[3 * t + 2] : 0.0;
     __syncthreads();
-    for (int stride = kStatThreads / 2; stride > 0; stride >>= 1) {  // Chan et al. pairwise combine
+    for (int stride = kMaxPartials / 2; stride > 0; stride >>= 1) {
         if (t < stride) {
             const double na = sc[t], nb = sc[t + stride];
             const double nn = na + nb;
@@ -99,24 +194,21 @@ k_tv_stats(const double* __restrict__ tv, int cells, double T_r, double T_c,
         __syncthreads();
     }
     if (t == 0) {
-        const double mu = smean[0];
-        const double sig = sc[0] > 0.0 ? sqrt(sm2[0] / sc[0]) : 0.0;
-        mu_sig[0] = mu;
-        mu_sig[1] = sig;
+        mu_sig[0] = smean[0];
+        mu_sig[1] = sc[0] > 0.0 ? sqrt(sm2[0] / sc[0]) : 0.0;
         if (stats) {
-            stats[0] = mu;
-            stats[1] = sig;
+            stats[0] = mu_sig[0];
+            stats[1] = mu_sig[1];
         }
     }
     __syncthreads();
     if (flags) {
         const double thr_r = mu_sig[0] + T_r * mu_sig[1];
         const double thr_c = mu_sig[0] + T_c * mu_sig[1];
-        for (int c = t; c < cells; c += kStatThreads) {
+        const bool flat = mu_sig[1] <= 1e-12 * fabs(mu_sig[0]);  // reading F1: keep all
+        for (int c = t; c < cells; c += kMaxPartials) {
             const double x = tv[c];
-            // sigma = 0 (up to rounding): every cell shares one TV; keep all
-            flags[c] = mu_sig[1] <= 1e-12 * fabs(mu_sig[0]) ? (int8_t)0
-                       : x >= thr_r ? (int8_t)1 : (x < thr_c ? (int8_t)-1 : (int8_t)0);
+            flags[c] = flat ? (int8_t)0 : x >= thr_r ? (int8_t)1 : (x < thr_c ? (int8_t)-1 : (int8_t)0);
         }
     }
 }
@@ -239,12 +331,6 @@ int launch_tv_cells(int N, const double* u, double* tv, int cells, int var, cons
     return (int)cudaErrorInvalidValue;
 }
 
-int launch_tv_stats(const double* tv, int cells, double T_r, double T_c, double* stats_dev,
-                    int8_t* flags, void* stream) {
-    k_tv_stats<<<1, kStatThreads, 0, (cudaStream_t)stream>>>(tv, cells, T_r, T_c, stats_dev, flags);
-    return (int)cudaGetLastError();
-}
-
 template <int N>
 static int init_n(double* u, int cells, int kind, double A, double a, double xc, double zc,
                   const Basis& B, const Phys& P, cudaStream_t s) {
@@ -292,6 +378,54 @@ int launch_max_speed(int N, const double* u, double* partial, int cells, const B
         case 7: return speed_n<7>(u, partial, cells, B, P, nblocks_out, s);
     }
     return (int)cudaErrorInvalidValue;
+}
+
+template <int N>
+static int tv_cells_mixed_n(const double* u, double* tv, int cells, int var, const BasisF& B,
+                            const PhysF& P, const MixedBg& bg, float theta0, float omk, cudaStream_t s) {
+    using C = TvCfg<N>;
+    const int blocks = (cells + C::cpb - 1) / C::cpb;
+    k_tv_cells_mixed<N, C::cpb><<<blocks, C::cpb * C::n * C::n, 0, s>>>(u, tv, cells, var, B, P, bg, theta0, omk);
+    return (int)cudaGetLastError();
+}
+
+int launch_tv_cells_mixed(int N, const double* u, double* tv, int cells, int var, const BasisF& B,
+                          const PhysF& P, const MixedBg& bg, double theta0, double Rcp, void* stream) {
+    cudaStream_t s = (cudaStream_t)stream;
+    const float t0 = (float)theta0, omk = (float)(1.0 - Rcp);
+    switch (N) {
+        case 1: return tv_cells_mixed_n<1>(u, tv, cells, var, B, P, bg, t0, omk, s);
+        case 2: return tv_cells_mixed_n<2>(u, tv, cells, var, B, P, bg, t0, omk, s);
+        case 3: return tv_cells_mixed_n<3>(u, tv, cells, var, B, P, bg, t0, omk, s);
+        case 4: return tv_cells_mixed_n<4>(u, tv, cells, var, B, P, bg, t0, omk, s);
+        case 5: return tv_cells_mixed_n<5>(u, tv, cells, var, B, P, bg, t0, omk, s);
+        case 6: return tv_cells_mixed_n<6>(u, tv, cells, var, B, P, bg, t0, omk, s);
+        case 7: return tv_cells_mixed_n<7>(u, tv, cells, var, B, P, bg, t0, omk, s);
+    }
+    return (int)cudaErrorInvalidValue;
+}
+
+int tv_stats_partials(int cells) {
+    const int chunk = tv_stats_chunk(cells);
+    return (cells + chunk - 1) / chunk;
+}
+
+int tv_stats_chunk(int cells) {
+    int chunk = 256;
+    while ((cells + chunk - 1) / chunk > kMaxPartials) chunk *= 2;
+    return chunk;
+}
+
+int launch_tv_stats_multi(const double* tv, int cells, double T_r, double T_c, double* part,
+                          double* stats_dev, int8_t* flags, void* stream) {
+    cudaStream_t s = (cudaStream_t)stream;
+    const int chunk = tv_stats_chunk(cells);
+    const int np = (cells + chunk - 1) / chunk;
+    k_tv_partials<<<np, kPartThreads, 0, s>>>(tv, cells, chunk, part);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return (int)e;
+    k_tv_final<<<1, kMaxPartials, 0, s>>>(part, np, tv, cells, T_r, T_c, stats_dev, flags);
+    return (int)cudaGetLastError();
 }
 
 int launch_check_finite(const double* u, size_t count, int* flag, void* stream) {

@@ -42,3 +42,9 @@ def instance_sizes(count, seed, lo=9, hi=81):
 def uniform_values(count, seed, lo, hi):
     rng = np.random.default_rng(seed)
     return rng.uniform(lo, hi, size=count)
+
+
+def normal_values(count, seed, scale):
+    """Gaussian values N(0, scale^2)."""
+    rng = np.random.default_rng(seed)
+    return rng.normal(0.0, scale, size=count)

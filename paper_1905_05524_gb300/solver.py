@@ -159,3 +159,37 @@ class Mesh:
 
     def check_finite(self, stream=None):
         L.check(self._lib.adg_check_finite(self.h, _stream_ptr(stream)))
+
+
+class Batch:
+    """Owns one adg_batch handle over a list of Mesh objects (kept alive here)."""
+
+    def __init__(self, meshes):
+        self.meshes = list(meshes)
+        self._lib = L.lib()
+        arr = (ctypes.c_void_p * len(self.meshes))(*[m.h.value for m in self.meshes])
+        h = ctypes.c_void_p()
+        L.check(self._lib.adg_batch_create(arr, len(self.meshes), ctypes.byref(h)))
+        self.h = h
+
+    def step(self, dts, nsteps=1, stream=None):
+        arr = (ctypes.c_double * len(self.meshes))(*[float(d) for d in dts])
+        L.check(self._lib.adg_batch_step(self.h, arr, int(nsteps), _stream_ptr(stream)))
+
+    def info(self):
+        buf = (ctypes.c_int * 9)()
+        L.check(self._lib.adg_batch_info(self.h, buf, 9))
+        keys = ["tiles_pred", "cpb_pred", "grid_pred", "tiles_corr", "cpb_corr", "grid_corr",
+                "tune_ns_0", "tune_ns_1", "tune_ns_2"]
+        return dict(zip(keys, list(buf)))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._lib.adg_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -90,3 +90,40 @@ def test_mixed_vs_oracle_manufactured():
     for v in range(4):
         r = (torch.linalg.vector_norm(a[:, v] - uo[:, v]) / torch.linalg.vector_norm(uo[:, v])).item()
         assert r < 1e-6, (v, r)
+
+
+def test_mixed_tv_indicator_vs_oracle():
+    """Mixed-path TV of theta (FP32 theta' from the FP64 perturbation split)
+    against the FP64 oracle on the two-bubble field: relative error per cell
+    <= 1e-5 where the TV carries signal; flags identical away from the
+    thresholds; mean and sigma within 1e-5."""
+    from oracle import indicator as oind
+    cfg = atmosphere_config(degree=5, nx=27, ny=27, precision=L.ADG_PREC_MIXED)
+    o = oracle_for(cfg)
+    from tests.oracle_bridge import two_bubble_field
+    u0 = two_bubble_field(o)
+    m = Mesh(cfg)
+    m.set_state(u0.cuda().contiguous())
+    T_r, T_c = 2.5, -0.5
+    tv, flags, (mean, std) = m.tv_indicator(L.ADG_TV_THETA, T_r, T_c)
+    tvo, flo, meano, stdo = oind.tv_indicator(o, u0, "theta", T_r, T_c)
+    tv = tv.cpu()
+    floor = 1e-6 * tvo.abs().max()
+    assert bool(((tv - tvo).abs() <= 1e-5 * tvo.abs() + floor).all()), (tv - tvo).abs().max()
+    assert abs(mean - meano) <= 1e-5 * abs(meano)
+    assert abs(std - stdo) <= 1e-5 * abs(stdo)
+    thr_r, thr_c = meano + T_r * stdo, meano + T_c * stdo
+    amb = ((tvo - thr_r).abs() <= 1e-4 * abs(thr_r)) | ((tvo - thr_c).abs() <= 1e-4 * abs(thr_c))
+    assert torch.equal(flags.cpu()[~amb], flo[~amb])
+
+
+def test_mixed_tv_rho_periodic():
+    from oracle import indicator as oind
+    cfg = steady_manufactured_config(degree=3, nx=9, ny=9, precision=L.ADG_PREC_MIXED)
+    o = oracle_for(cfg)
+    u0 = steady_field(o, cfg)
+    m = Mesh(cfg)
+    m.set_state(u0.cuda().contiguous())
+    tv, flags, (mean, std) = m.tv_indicator(L.ADG_TV_RHO, 1.5, -0.5)
+    tvo, flo, meano, stdo = oind.tv_indicator(o, u0, "rho", 1.5, -0.5)
+    assert torch.allclose(tv.cpu(), tvo, rtol=1e-5, atol=1e-6 * tvo.abs().max().item())
