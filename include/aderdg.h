@@ -78,6 +78,9 @@ typedef struct adg_mesh_desc {
     double src_a, src_L, src_U, src_p; /* parameters of ADG_SRC_STEADY            */
     int precision;         /* ADG_PREC_*                                         */
     int device;            /* CUDA device ordinal                                */
+    int max_levels;        /* 0: uniform mesh; 1..4: adaptive 3:1 tree with up to
+                              this many refinement levels above the nx x ny base
+                              (FP64 only; see adg_adapt)                          */
 } adg_mesh_desc;
 
 #define ADG_SCEN_STEADY 0       /* steady manufactured field of the source above */
@@ -206,6 +209,27 @@ void adg_batch_destroy(adg_batch* b);
  * between calls. */
 #define ADG_NOALLOC_SCRATCH_BYTES (32u << 20)
 int adg_step_noalloc(const adg_mesh_desc* desc, double* u, size_t count, double dt, void* stream);
+
+/* ---- adaptive mesh (desc.max_levels > 0) ----
+ *
+ * Refinement criterion of Sec. 3 (Eq. 7 flags from adg_tv_indicator) applied
+ * on a 3:1 tree as in Sec. 4.2.  Leaves are ordered by (level, iy, ix); the
+ * state, tv and flags arrays follow that order and their length changes with
+ * every adaptation (adg_leaf_count).  Refinement: children = the parent
+ * polynomial at their nodes; coarsening (all 9 siblings flagged -1, as the
+ * paper requires): L2 projection; neighbours differ by at most one level,
+ * refinement wins; hanging faces: the coarse side receives the L2 restriction
+ * of the three fine numerical fluxes (conservative).
+ *
+ * adg_adapt: flags = device int8 per leaf (+1 refine, -1 coarsen, 0 keep);
+ *   rebuilds the leaf list, transfers the state, reallocates the workspace;
+ *   synchronises `stream`; writes the new leaf count to *leaves_out (may be
+ *   NULL).  ADG_EINVAL on a uniform mesh.
+ * adg_leaf_info: host int[3 * leaves] = (level, ix, iy) per leaf, ix/iy in
+ *   units of that level's cells (a uniform mesh reports level 0). */
+size_t adg_leaf_count(const adg_mesh* m);
+int adg_leaf_info(const adg_mesh* m, int* out, size_t count);
+int adg_adapt(adg_mesh* m, const int8_t* flags, int* leaves_out, void* stream);
 
 /* Text of the last error on the calling thread ("" if none). */
 const char* adg_last_error(void);

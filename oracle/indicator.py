@@ -2,8 +2,12 @@
 
 * Eq. 6 (TV): TV[f] = || int_C |grad f| dx ||_1, integral by Gaussian
   quadrature over the collocated nodes.  Reading T1: the component-wise
-  absolute gradient is integrated over the physical cell and the L1 norm
-  sums the components, TV = hx hy sum_ij w_i w_j (|df/dx| + |df/dy|).
+  absolute physical gradient is integrated with the quadrature of the
+  reference cell (weights summing to 1) and the L1 norm sums the
+  components, TV = sum_ij w_i w_j (|df/dx| + |df/dy|).  Integrating over the
+  physical cell instead (a factor hx hy) makes a child's TV 1/9 of its
+  parent's for the same gradient, so refinement stops after one level --
+  contrary to the three cell sizes of the paper's two-level runs (Sec. 4.2).
 * mean and population standard deviation of TV over all (leaf) cells --
   here their plain two-pass definition, which Chan et al.'s parallel update
   (cited by the paper) reaches up to rounding.
@@ -18,8 +22,8 @@ stratified scenarios and the density for the CFD scenarios (reading).
 
 Pins: tests/test_oracle_indicator.py (TV of a linear field is exact, TV of a
 constant is zero, flags obey the Chebyshev/Cantelli bound, sigma = 0 flags
-nothing).  The h-scaling of reading T1 is a recorded choice: parity unpinned
-for that factor.
+nothing).  The cell-size scaling of reading T1 is a recorded choice (parity
+unpinned for that factor).
 """
 import torch
 
@@ -42,7 +46,7 @@ def total_variation(solver, f):
     hx, hy = solver.m.hx, solver.m.hy
     fx = torch.einsum("ip,cjp->cji", D, f) / hx
     fy = torch.einsum("jp,cpi->cji", D, f) / hy
-    return hx * hy * torch.einsum("j,i,cji->c", w, w, fx.abs() + fy.abs())
+    return torch.einsum("j,i,cji->c", w, w, fx.abs() + fy.abs())
 
 
 def mean_std(tv):

@@ -49,7 +49,7 @@ class MeshDesc(ctypes.Structure):
                 ("source", ctypes.c_int), ("src_a", ctypes.c_double),
                 ("src_L", ctypes.c_double), ("src_U", ctypes.c_double),
                 ("src_p", ctypes.c_double), ("precision", ctypes.c_int),
-                ("device", ctypes.c_int)]
+                ("device", ctypes.c_int), ("max_levels", ctypes.c_int)]
 
 
 class Scenario(ctypes.Structure):
@@ -90,6 +90,9 @@ SIGNATURES = {
     "adg_batch_info": (_I, [_P, ctypes.POINTER(_I), _I]),
     "adg_batch_destroy": (None, [_P]),
     "adg_step_noalloc": (_I, [ctypes.POINTER(MeshDesc), _P, _S, _D, _P]),
+    "adg_leaf_count": (_S, [_P]),
+    "adg_leaf_info": (_I, [_P, _P, _S]),
+    "adg_adapt": (_I, [_P, _P, _P, _P]),
     "adg_last_error": (ctypes.c_char_p, []),
 }
 

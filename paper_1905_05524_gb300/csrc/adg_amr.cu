@@ -1,0 +1,796 @@
+// Adaptive 3:1 tree mesh: FP64 step on leaves of different levels, TV
+// indicator per leaf, and the refine/coarsen transfer (Sec. 3 refinement
+// criterion; Sec. 4.2 runs on two refinement levels of a 3:1 tree).
+//
+// Mesh operations (the paper gives the criterion, not the operations):
+//  * refinement: a leaf becomes 3 x 3 children whose nodal values are the
+//    parent polynomial at the children's nodes (exact);
+//  * coarsening: 9 sibling leaves, all flagged -1, become their parent, whose
+//    nodal values are the L2 projection of the children by Gauss-Legendre
+//    quadrature on each child (exact, conservative);
+//  * 2-level balance: neighbouring leaves differ by at most one level and
+//    refinement wins;
+//  * hanging faces: the fine side evaluates the coarse trace on its third of
+//    the face; the coarse side computes the same three fine numerical fluxes
+//    (identical operands and order, so the values are bitwise equal) and
+//    receives their L2 restriction onto its face basis -- conservative
+//    because the restriction preserves the face integral; the Rusanov
+//    penalty uses the fine cell size on both sides;
+//  * leaves are ordered by (level, iy, ix).
+// All leaves of all levels are advanced by one predictor launch and one
+// corrector launch per step.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstring>
+#include <unordered_map>
+#include <vector>
+
+#include "adg_fp64_body.cuh"
+#include "adg_internal.h"
+#include "adg_mesh.h"
+#include "adg_physics.cuh"
+
+namespace adg {
+
+constexpr int kNbrInts = 5;  // type, id0, id1, id2, sub-face
+enum { NB_CONF = 0, NB_COARSE = 1, NB_FINE = 2, NB_WALL = 3 };
+
+// 1D prolongation Pro[a][m][q] = phi_q((a + xi_m)/3) and the face
+// restriction weights Rw[a][m][q] = Pro[a][m][q] w_m / (3 w_q).
+struct AmrOps {
+    double Pro[3][kMaxN][kMaxN];
+    double Rw[3][kMaxN][kMaxN];
+};
+
+// ------------------------------------------------------------------ host tree
+struct AmrTree {
+    int nx0 = 0, ny0 = 0, maxl = 0;
+    bool per_x = false, per_y = false;
+    std::vector<std::array<int, 3>> leaves;  // level, ix, iy
+    std::unordered_map<long long, int> pos;
+    AmrOps ops;
+
+    static long long key(int l, int ix, int iy) { return ((long long)l << 50) | ((long long)ix << 25) | iy; }
+    void index() {
+        std::sort(leaves.begin(), leaves.end(), [](const std::array<int, 3>& a, const std::array<int, 3>& b) {
+            if (a[0] != b[0]) return a[0] < b[0];
+            if (a[2] != b[2]) return a[2] < b[2];
+            return a[1] < b[1];
+        });
+        pos.clear();
+        for (int k = 0; k < (int)leaves.size(); ++k) pos[key(leaves[k][0], leaves[k][1], leaves[k][2])] = k;
+    }
+    int find(int l, int ix, int iy) const {
+        auto it = pos.find(key(l, ix, iy));
+        return it == pos.end() ? -1 : it->second;
+    }
+    // face 0 E, 1 W, 2 N, 3 S; out[5] = type, id0, id1, id2, sub
+    bool neighbour(int k, int f, int out[kNbrInts]) const {
+        const int l = leaves[k][0], ix = leaves[k][1], iy = leaves[k][2];
+        const int NX = nx0 * ipow3(l), NY = ny0 * ipow3(l);
+        int jx = ix + (f == 0 ? 1 : f == 1 ? -1 : 0), jy = iy + (f == 2 ? 1 : f == 3 ? -1 : 0);
+        out[1] = out[2] = out[3] = -1;
+        out[4] = 0;
+        if (jx < 0 || jx >= NX) {
+            if (!per_x) { out[0] = NB_WALL; return true; }
+            jx = (jx + NX) % NX;
+        }
+        if (jy < 0 || jy >= NY) {
+            if (!per_y) { out[0] = NB_WALL; return true; }
+            jy = (jy + NY) % NY;
+        }
+        int o = find(l, jx, jy);
+        if (o >= 0) { out[0] = NB_CONF; out[1] = o; return true; }
+        if (l > 0 && (o = find(l - 1, jx / 3, jy / 3)) >= 0) {
+            out[0] = NB_COARSE;
+            out[1] = o;
+            out[4] = f < 2 ? iy % 3 : ix % 3;
+            return true;
+        }
+        out[0] = NB_FINE;
+        for (int s = 0; s < 3; ++s) {
+            int cx, cy;
+            if (f == 0) { cx = 3 * jx; cy = 3 * iy + s; }
+            else if (f == 1) { cx = 3 * jx + 2; cy = 3 * iy + s; }
+            else if (f == 2) { cx = 3 * ix + s; cy = 3 * jy; }
+            else { cx = 3 * ix + s; cy = 3 * jy + 2; }
+            out[1 + s] = find(l + 1, cx, cy);
+            if (out[1 + s] < 0) return false;  // unbalanced tree
+        }
+        return true;
+    }
+    static int ipow3(int l) {
+        int r = 1;
+        while (l-- > 0) r *= 3;
+        return r;
+    }
+};
+
+static AmrTree* tree_of(adg_mesh* m) { return (AmrTree*)m->tree; }
+
+// Upload geometry, neighbour and background tables of the current leaves.
+static int upload_tables(adg_mesh* m) {
+    AmrTree* T = tree_of(m);
+    const int L = (int)T->leaves.size(), n = m->n;
+    const adg_mesh_desc* d = &m->d;
+    std::vector<double> geo((size_t)L * 4), bgl((size_t)L * n * 2 + (size_t)L * 4, 0.0);
+    std::vector<int> nbr((size_t)L * 4 * kNbrInts);
+    const double cp = m->P.cp;
+    auto bgp = [&](double z, double& pb, double& rb) {
+        pb = rb = 0.0;
+        if (!d->gravity) return;
+        const double ex = 1.0 - d->g * z / (cp * d->theta0);
+        pb = d->p0 * std::pow(ex, cp / d->R);
+        rb = pb / (d->R * d->theta0 * ex);
+    };
+    double hmin = 1e300;
+    for (int k = 0; k < L; ++k) {
+        const int l = T->leaves[k][0], ix = T->leaves[k][1], iy = T->leaves[k][2];
+        const double hx = d->Lx / (d->nx * AmrTree::ipow3(l)), hy = d->Ly / (d->ny * AmrTree::ipow3(l));
+        hmin = std::fmin(hmin, std::fmin(hx, hy));
+        geo[k * 4 + 0] = d->x0 + ix * hx;
+        geo[k * 4 + 1] = d->y0 + iy * hy;
+        geo[k * 4 + 2] = hx;
+        geo[k * 4 + 3] = hy;
+        for (int j = 0; j < n; ++j)
+            bgp(d->y0 + (iy + m->B.xi[j]) * hy, bgl[((size_t)k * n + j) * 2], bgl[((size_t)k * n + j) * 2 + 1]);
+        double* fb = bgl.data() + (size_t)L * n * 2 + (size_t)k * 4;
+        bgp(d->y0 + (iy + 1) * hy, fb[0], fb[1]);  // north face
+        bgp(d->y0 + iy * hy, fb[2], fb[3]);        // south face
+        for (int f = 0; f < 4; ++f)
+            if (!T->neighbour(k, f, &nbr[((size_t)k * 4 + f) * kNbrInts]))
+                return fail(ADG_EINVAL, "adaptive mesh: level difference above one across a face");
+    }
+    m->hmin = hmin;
+    cudaFree(m->geo);
+    cudaFree(m->nbr);
+    cudaFree(m->bgl);
+    m->geo = nullptr;
+    m->nbr = nullptr;
+    m->bgl = nullptr;
+    if (cudaMalloc(&m->geo, geo.size() * 8) != cudaSuccess || cudaMalloc(&m->nbr, nbr.size() * 4) != cudaSuccess ||
+        cudaMalloc(&m->bgl, bgl.size() * 8) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ADG_ENOMEM, "adaptive mesh: tables");
+    }
+    ADG_CK(cudaMemcpy(m->geo, geo.data(), geo.size() * 8, cudaMemcpyHostToDevice), "amr tables");
+    ADG_CK(cudaMemcpy(m->nbr, nbr.data(), nbr.size() * 4, cudaMemcpyHostToDevice), "amr tables");
+    ADG_CK(cudaMemcpy(m->bgl, bgl.data(), bgl.size() * 8, cudaMemcpyHostToDevice), "amr tables");
+    return ADG_OK;
+}
+
+// (Re)allocate the per-leaf buffers for the current leaf count.
+static int size_buffers(adg_mesh* m, double* new_u) {
+    const int L = (int)tree_of(m)->leaves.size(), n = m->n;
+    const size_t cnt = (size_t)L * n * n * 4, tr = (size_t)L * 4 * kTraceComps * n;
+    cudaFree(m->rvol);
+    cudaFree(m->trace);
+    cudaFree(m->trace_bar);
+    cudaFree(m->tv);
+    cudaFree(m->part);
+    m->rvol = m->trace = m->trace_bar = m->tv = m->part = nullptr;
+    if (new_u) {
+        cudaFree(m->u);
+        m->u = new_u;
+    }
+    m->cells = L;
+    if (cudaMalloc(&m->rvol, cnt * 8) != cudaSuccess || cudaMalloc(&m->trace, tr * 8) != cudaSuccess ||
+        cudaMalloc(&m->tv, (size_t)L * 8) != cudaSuccess ||
+        cudaMalloc(&m->part, 3 * 8 * (size_t)tv_stats_partials(L)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ADG_ENOMEM, "adaptive mesh: buffers");
+    }
+    return ADG_OK;
+}
+
+int amr_setup(adg_mesh* m) {
+    AmrTree* T = new AmrTree();
+    T->nx0 = m->d.nx;
+    T->ny0 = m->d.ny;
+    T->maxl = m->d.max_levels;
+    T->per_x = m->d.bc_x == ADG_BC_PERIODIC;
+    T->per_y = m->d.bc_y == ADG_BC_PERIODIC;
+    for (int iy = 0; iy < T->ny0; ++iy)
+        for (int ix = 0; ix < T->nx0; ++ix) T->leaves.push_back({0, ix, iy});
+    T->index();
+    std::memset(&T->ops, 0, sizeof(T->ops));
+    const int n = m->n;
+    for (int a = 0; a < 3; ++a)
+        for (int mm = 0; mm < n; ++mm) {
+            const double x = (a + m->B.xi[mm]) / 3.0;
+            for (int q = 0; q < n; ++q) {
+                double v = 1.0;
+                for (int r = 0; r < n; ++r)
+                    if (r != q) v *= (x - m->B.xi[r]) / (m->B.xi[q] - m->B.xi[r]);
+                T->ops.Pro[a][mm][q] = v;
+                T->ops.Rw[a][mm][q] = v * m->B.w[mm] / (3.0 * m->B.w[q]);
+            }
+        }
+    m->tree = T;
+    m->amr = 1;
+    return upload_tables(m);
+}
+
+void amr_free(adg_mesh* m) {
+    delete tree_of(m);
+    m->tree = nullptr;
+    cudaFree(m->geo);
+    cudaFree(m->nbr);
+    cudaFree(m->bgl);
+}
+
+// per-leaf constants: P with the leaf's cell sizes
+__device__ __forceinline__ Phys leaf_phys(const Phys& P0, const double* geo, int cell, int N) {
+    Phys P = P0;
+    P.hx = geo[cell * 4 + 2];
+    P.hy = geo[cell * 4 + 3];
+    P.inv_hx = 1.0 / P.hx;
+    P.inv_hy = 1.0 / P.hy;
+    P.eta_x = (2.0 * N + 1.0) / (P.hx * 1.2533141373155002);  // sqrt(pi/2)
+    P.eta_y = (2.0 * N + 1.0) / (P.hy * 1.2533141373155002);
+    return P;
+}
+
+// ------------------------------------------------------------------ kernels
+template <int N, int CPB>
+__global__ void __launch_bounds__(CPB*(N + 1) * (N + 1))
+k_predictor_amr(const double* __restrict__ u, double* __restrict__ rvol, double* __restrict__ trace, int cells,
+                double dt, const Basis B, const Phys P0, const double* __restrict__ geo,
+                const double* __restrict__ bgl) {
+    constexpr int n = N + 1, n2 = n * n;
+    extern __shared__ double sm[];
+    const int cl = threadIdx.x / n2;
+    const int j = (threadIdx.x - cl * n2) / n;
+    const int cell_raw = blockIdx.x * CPB + cl;
+    const bool active = cell_raw < cells;
+    const int cell = active ? cell_raw : cells - 1;
+    const Phys P = leaf_phys(P0, geo, cell, N);
+    predictor_fp64_body<N, CPB>(u, rvol, trace, cell, active, dt, B, P, geo[cell * 4], geo[cell * 4 + 1],
+                                bgl[((size_t)cell * n + j) * 2], bgl[((size_t)cell * n + j) * 2 + 1], sm);
+}
+
+// face data (q-bar and normal flux) of record `rec` of a coarse face evaluated
+// on its third `s` at fine node m
+__device__ __forceinline__ void prolong_rec(const double* rec, int n, const AmrOps& O, int s, int m, double q[4],
+                                            double f[4]) {
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+        double a = 0.0, b = 0.0;
+        for (int p = 0; p < n; ++p) {
+            a += O.Pro[s][m][p] * rec[v * n + p];
+            b += O.Pro[s][m][p] * rec[(4 + v) * n + p];
+        }
+        q[v] = a;
+        f[v] = b;
+    }
+}
+
+template <int N, int CPB>
+__global__ void __launch_bounds__(CPB*(N + 1) * (N + 1))
+k_corrector_amr(double* __restrict__ u, const double* __restrict__ rvol, const double* __restrict__ trace,
+                int cells, double dt, const Basis B, const Phys P0, const AmrOps O, const double* __restrict__ geo,
+                const int* __restrict__ nbr, const double* __restrict__ bgl) {
+    constexpr int n = N + 1, n2 = n * n, SL = 4 * n2, TR = kTraceComps * n;
+    __shared__ double Fsub[CPB][4][3][4][n];
+    __shared__ double Fst[CPB][4][4][n];
+    const int cl = threadIdx.x / n2;
+    const int node = threadIdx.x - cl * n2;
+    const int j = node / n, i = node - j * n;
+    const int cell_raw = blockIdx.x * CPB + cl;
+    const bool active = cell_raw < cells;
+    const int cell = active ? cell_raw : cells - 1;
+    const Phys P = leaf_phys(P0, geo, cell, N);
+    const double yorg = geo[cell * 4 + 1];
+
+    for (int idx = node; idx < 4 * 3 * n; idx += n2) {
+        const int f = idx / (3 * n), rem = idx - f * 3 * n, s = rem / n, m = rem - s * n;
+        const int* nb = nbr + ((size_t)cell * 4 + f) * kNbrInts;
+        const int type = nb[0];
+        if (type != NB_FINE && s > 0) continue;
+        const bool xface = f < 2;
+        const int of = f ^ 1;  // opposite face: E<->W, N<->S
+        const bool own_minus = (f == 0 || f == 2);
+        const double* own = trace + ((size_t)cell * 4 + f) * TR;
+        double qo[4], fo[4], so;
+        double qn[4], fn[4], sn;
+        if (type == NB_FINE) {
+            // coarse side of a hanging face: own trace on third s vs fine neighbour s
+            const int o = nb[1 + s];
+            const Phys Pf = leaf_phys(P0, geo, o, N);
+            // heights of the fine neighbour's face nodes (the same expression it uses itself)
+            const double z = geo[o * 4 + 1] + (xface ? B.xi[m] * Pf.hy : (f == 2 ? 0.0 : Pf.hy));
+            prolong_rec(own, n, O, s, m, qo, fo);
+            so = wave_speed(qo, z, xface, Pf);
+            const double* ot = trace + ((size_t)o * 4 + of) * TR;
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                qn[v] = ot[v * n + m];
+                fn[v] = ot[(4 + v) * n + m];
+            }
+            sn = ot[16 * n + m];
+        } else {
+            double rec[kTraceComps];
+#pragma unroll
+            for (int c = 0; c < kTraceComps; ++c) rec[c] = own[c * n + m];
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                qo[v] = rec[v];
+                fo[v] = rec[4 + v];
+            }
+            so = rec[16];
+            const double z = xface ? yorg + B.xi[m] * P.hy : yorg + (f == 2 ? P.hy : 0.0);
+            if (type == NB_WALL) {
+                double pb, rb;
+                if (xface) {
+                    pb = bgl[((size_t)cell * n + m) * 2];
+                    rb = bgl[((size_t)cell * n + m) * 2 + 1];
+                } else {
+                    const double* fb = bgl + (size_t)cells * n * 2 + (size_t)cell * 4 + (f == 2 ? 0 : 2);
+                    pb = fb[0];
+                    rb = fb[1];
+                }
+                const double nx = f == 0 ? 1.0 : f == 1 ? -1.0 : 0.0;
+                const double ny = f == 2 ? 1.0 : f == 3 ? -1.0 : 0.0;
+                const double mn = rec[1] * nx + rec[2] * ny;
+                qn[1] = rec[1] - 2.0 * mn * nx;
+                qn[2] = rec[2] - 2.0 * mn * ny;
+                qn[0] = P.gravity ? rb : rec[0];
+                qn[3] = P.gravity ? pb / P.gm1 + rb * P.g * z : rec[3];
+                Flux4 fl;
+                ns_flux(qn, rec + 8, rec + 12, z, pb, rb, P, fl, true, 0.0, P.gravity ? -P.g / P.cp : 0.0);
+#pragma unroll
+                for (int v = 0; v < 4; ++v) fn[v] = xface ? fl.F[v] : fl.G[v];
+                sn = wave_speed(qn, z, xface, P);
+            } else if (type == NB_CONF) {
+                const double* ot = trace + ((size_t)nb[1] * 4 + of) * TR;
+#pragma unroll
+                for (int v = 0; v < 4; ++v) {
+                    qn[v] = ot[v * n + m];
+                    fn[v] = ot[(4 + v) * n + m];
+                }
+                sn = ot[16 * n + m];
+            } else {  // NB_COARSE: the coarse trace on this cell's third of the face
+                const double* ot = trace + ((size_t)nb[1] * 4 + of) * TR;
+                prolong_rec(ot, n, O, nb[4], m, qn, fn);
+                sn = wave_speed(qn, z, xface, P);
+            }
+        }
+        double out[4];
+        if (own_minus) rusanov(qo, fo, so, qn, fn, sn, out);
+        else rusanov(qn, fn, sn, qo, fo, so, out);
+#pragma unroll
+        for (int v = 0; v < 4; ++v) Fsub[cl][f][s][v][m] = out[v];
+    }
+    __syncthreads();
+    for (int idx = node; idx < 4 * n; idx += n2) {
+        const int f = idx / n, q = idx - f * n;
+        const bool fine = nbr[((size_t)cell * 4 + f) * kNbrInts] == NB_FINE;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            double a;
+            if (fine) {
+                a = 0.0;
+                for (int s = 0; s < 3; ++s)
+                    for (int mm = 0; mm < n; ++mm) a += O.Rw[s][mm][q] * Fsub[cl][f][s][v][mm];
+            } else {
+                a = Fsub[cl][f][0][v][q];
+            }
+            Fst[cl][f][v][q] = a;
+        }
+    }
+    __syncthreads();
+    if (!active) return;
+    double* uc = u + (size_t)cell * SL;
+    const double* rc = rvol + (size_t)cell * SL;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+        const double face = (B.lift1[i] * Fst[cl][0][v][j] - B.lift0[i] * Fst[cl][1][v][j]) * P.inv_hx +
+                            (B.lift1[j] * Fst[cl][2][v][i] - B.lift0[j] * Fst[cl][3][v][i]) * P.inv_hy;
+        uc[v * n2 + node] += dt * (rc[v * n2 + node] - face);
+    }
+}
+
+template <int N, int CPB>
+__global__ void __launch_bounds__(CPB*(N + 1) * (N + 1))
+k_tv_cells_amr(const double* __restrict__ u, double* __restrict__ tv, int cells, int var, const Basis B,
+               const Phys P0, const double* __restrict__ geo) {
+    constexpr int n = N + 1, n2 = n * n, SL = 4 * n2;
+    __shared__ double fs[CPB][n2];
+    __shared__ double red[CPB][n2];
+    const int cl = threadIdx.x / n2;
+    const int node = threadIdx.x - cl * n2;
+    const int j = node / n, i = node - j * n;
+    const int cell_raw = blockIdx.x * CPB + cl;
+    const bool active = cell_raw < cells;
+    const int cell = active ? cell_raw : cells - 1;
+    const Phys P = leaf_phys(P0, geo, cell, N);
+    const double* uc = u + (size_t)cell * SL;
+    double q[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) q[v] = uc[v * n2 + node];
+    const double z = geo[cell * 4 + 1] + B.xi[j] * P.hy;
+    double f = q[0];
+    if (var == ADG_TV_THETA) {
+        const double rinv = 1.0 / q[0];
+        const double p = P.gm1 * (q[3] - 0.5 * (q[1] * q[1] + q[2] * q[2]) * rinv - q[0] * (P.gravity ? P.g * z : 0.0));
+        f = p * rinv * P.invR * pow(P.p0 / p, P.Rcp);
+    }
+    fs[cl][node] = f;
+    __syncthreads();
+    double fx = 0.0, fy = 0.0;
+#pragma unroll
+    for (int p = 0; p < n; ++p) {
+        fx += B.D[i][p] * fs[cl][j * n + p];
+        fy += B.D[j][p] * fs[cl][p * n + i];
+    }
+    red[cl][node] = B.w[i] * B.w[j] * (fabs(fx * P.inv_hx) + fabs(fy * P.inv_hy));
+    __syncthreads();
+    if (node == 0 && active) {
+        double s = 0.0;
+        for (int a = 0; a < n2; ++a) s += red[cl][a];
+        tv[cell] = s;
+    }
+}
+
+template <int N>
+__global__ void k_init_amr(double* __restrict__ u, int cells, int kind, double A, double a, double xc, double zc,
+                           const Basis B, const Phys P, const double* __restrict__ geo) {
+    constexpr int n = N + 1, n2 = n * n, SL = 4 * n2;
+    const int gid = blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= cells * n2) return;
+    const int cell = gid / n2, node = gid - cell * n2;
+    const int j = node / n, i = node - j * n;
+    const double x = geo[cell * 4] + B.xi[i] * geo[cell * 4 + 2];
+    const double z = geo[cell * 4 + 1] + B.xi[j] * geo[cell * 4 + 3];
+    double q[4];
+    if (kind == ADG_SCEN_STEADY) {
+        const double k = 2.0 * 3.14159265358979323846 / P.sL;
+        const double rho = 1.0 + P.sa * sin(k * (x + z));
+        q[0] = rho;
+        q[1] = rho * P.sU;
+        q[2] = rho * P.sU;
+        q[3] = P.sp / P.gm1 + 0.5 * rho * (2.0 * P.sU * P.sU);
+    } else {
+        double th = 0.0;
+        if (kind == ADG_SCEN_COSINE) {
+            const double r = sqrt((x - xc) * (x - xc) + (z - zc) * (z - zc));
+            th = r <= a ? 0.5 * A * (1.0 + cos(3.14159265358979323846 * r / a)) : 0.0;
+        } else if (kind == ADG_SCEN_TWO_BUBBLES) {
+            const double r1 = sqrt((x - 500.0) * (x - 500.0) + (z - 300.0) * (z - 300.0));
+            const double r2 = sqrt((x - 560.0) * (x - 560.0) + (z - 640.0) * (z - 640.0));
+            th = (r1 <= 150.0 ? 0.5 : 0.5 * exp(-((r1 - 150.0) * (r1 - 150.0)) / 2500.0)) +
+                 (r2 <= 0.0 ? -0.15 : -0.15 * exp(-(r2 * r2) / 2500.0));
+        }
+        const double ex = 1.0 - P.g * z / (P.cp * P.theta0);
+        const double pb = P.p0 * pow(ex, 1.0 / P.Rcp);
+        const double T = (P.theta0 + th) * ex;
+        const double rho = pb / (P.R * T);
+        q[0] = rho;
+        q[1] = 0.0;
+        q[2] = 0.0;
+        q[3] = pb / P.gm1 + rho * P.g * z;
+    }
+    double* uc = u + (size_t)cell * SL;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) uc[v * n2 + node] = q[v];
+}
+
+template <int N>
+__global__ void k_max_speed_amr(const double* __restrict__ u, double* __restrict__ partial, int cells,
+                                const Basis B, const Phys P, const double* __restrict__ geo, double eta) {
+    constexpr int n = N + 1, n2 = n * n, SL = 4 * n2;
+    __shared__ double red[256];
+    const int gid = blockIdx.x * blockDim.x + threadIdx.x;
+    double s = 0.0;
+    if (gid < cells * n2) {
+        const int cell = gid / n2, node = gid - cell * n2;
+        const int j = node / n;
+        const double z = geo[cell * 4 + 1] + B.xi[j] * geo[cell * 4 + 3];
+        const double* uc = u + (size_t)cell * SL;
+        const double rho = uc[node], mx = uc[n2 + node], my = uc[2 * n2 + node], E = uc[3 * n2 + node];
+        const double p = P.gm1 * (E - 0.5 * (mx * mx + my * my) / rho - rho * (P.gravity ? P.g * z : 0.0));
+        s = sqrt(mx * mx + my * my) / rho + sqrt(P.gamma * p / rho) + 2.0 * eta * P.lamv / rho;
+        if (!(s == s)) s = 1e300;
+    }
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int st = 128; st > 0; st >>= 1) {
+        if (threadIdx.x < st) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + st]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
+}
+
+// transfer of the state to a new leaf set: per new leaf, copy (t = 0),
+// prolongation from a parent at child position (a, b) (t = 1) or restriction
+// of 9 children ordered b * 3 + a (t = 2).  trans[leaf] = t, a, b, src[9].
+template <int N>
+__global__ void k_amr_transfer(const double* __restrict__ uold, double* __restrict__ unew, int leaves,
+                               const int* __restrict__ trans, const Basis B, const AmrOps O) {
+    constexpr int n = N + 1, n2 = n * n, SL = 4 * n2;
+    const int gid = blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= leaves * n2) return;
+    const int leaf = gid / n2, node = gid - leaf * n2;
+    const int j = node / n, i = node - j * n;
+    const int* t = trans + (size_t)leaf * 12;
+    double* out = unew + (size_t)leaf * SL;
+    if (t[0] == 0) {
+        const double* src = uold + (size_t)t[3] * SL;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) out[v * n2 + node] = src[v * n2 + node];
+    } else if (t[0] == 1) {
+        const double* src = uold + (size_t)t[3] * SL;
+        const int a = t[1], b = t[2];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            double acc = 0.0;
+            for (int r = 0; r < n; ++r) {
+                double row = 0.0;
+                for (int q = 0; q < n; ++q) row += O.Pro[a][i][q] * src[v * n2 + r * n + q];
+                acc += O.Pro[b][j][r] * row;
+            }
+            out[v * n2 + node] = acc;
+        }
+    } else {
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            double acc = 0.0;
+            for (int b = 0; b < 3; ++b)
+                for (int a = 0; a < 3; ++a) {
+                    const double* src = uold + (size_t)t[3 + b * 3 + a] * SL;
+                    for (int l = 0; l < n; ++l)
+                        for (int mm = 0; mm < n; ++mm)
+                            acc += O.Pro[b][l][j] * O.Pro[a][mm][i] * B.w[l] * B.w[mm] * src[v * n2 + l * n + mm];
+                }
+            out[v * n2 + node] = acc / (9.0 * B.w[j] * B.w[i]);
+        }
+    }
+}
+
+// ------------------------------------------------------------------ launchers
+template <int N>
+struct AmrCfg {
+    static constexpr int n = N + 1;
+    static constexpr int cpb = N == 1 ? 32 : N == 2 ? 16 : N == 3 ? 8 : N <= 5 ? 4 : 2;
+    static constexpr int threads = cpb * n * n;
+    static constexpr size_t smem_pred = (size_t)cpb * 3 * n * 4 * n * n * sizeof(double);
+};
+
+#define AMR_DISPATCH(FN, ...)                     \
+    switch (m->N) {                               \
+        case 1: return FN<1>(__VA_ARGS__);        \
+        case 2: return FN<2>(__VA_ARGS__);        \
+        case 3: return FN<3>(__VA_ARGS__);        \
+        case 4: return FN<4>(__VA_ARGS__);        \
+        case 5: return FN<5>(__VA_ARGS__);        \
+        case 6: return FN<6>(__VA_ARGS__);        \
+        case 7: return FN<7>(__VA_ARGS__);        \
+    }                                             \
+    return fail(ADG_EINVAL, "bad degree");
+
+template <int N>
+static int pred_n(adg_mesh* m, double dt, cudaStream_t s) {
+    using C = AmrCfg<N>;
+    auto kern = k_predictor_amr<N, C::cpb>;
+    ADG_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem_pred), "amr pred");
+    kern<<<(m->cells + C::cpb - 1) / C::cpb, C::threads, C::smem_pred, s>>>(m->u, m->rvol, m->trace, m->cells, dt,
+                                                                             m->B, m->P, m->geo, m->bgl);
+    ADG_CK(cudaGetLastError(), "amr predictor launch");
+    return ADG_OK;
+}
+int amr_predictor(adg_mesh* m, double dt, void* stream) { AMR_DISPATCH(pred_n, m, dt, (cudaStream_t)stream) }
+
+template <int N>
+static int corr_n(adg_mesh* m, double dt, cudaStream_t s) {
+    using C = AmrCfg<N>;
+    k_corrector_amr<N, C::cpb><<<(m->cells + C::cpb - 1) / C::cpb, C::threads, 0, s>>>(
+        m->u, m->rvol, m->trace, m->cells, dt, m->B, m->P, tree_of(m)->ops, m->geo, m->nbr, m->bgl);
+    ADG_CK(cudaGetLastError(), "amr corrector launch");
+    return ADG_OK;
+}
+int amr_corrector(adg_mesh* m, double dt, void* stream) { AMR_DISPATCH(corr_n, m, dt, (cudaStream_t)stream) }
+
+template <int N>
+static int tv_n(adg_mesh* m, int var, double* tv, cudaStream_t s) {
+    using C = AmrCfg<N>;
+    k_tv_cells_amr<N, C::cpb><<<(m->cells + C::cpb - 1) / C::cpb, C::threads, 0, s>>>(m->u, tv, m->cells, var,
+                                                                                        m->B, m->P, m->geo);
+    ADG_CK(cudaGetLastError(), "amr tv launch");
+    return ADG_OK;
+}
+int amr_tv_cells(adg_mesh* m, int var, double* tv, void* stream) { AMR_DISPATCH(tv_n, m, var, tv, (cudaStream_t)stream) }
+
+template <int N>
+static int init_amr_n(adg_mesh* m, const adg_scenario* sc, cudaStream_t s) {
+    const int total = m->cells * (N + 1) * (N + 1);
+    k_init_amr<N><<<(total + 255) / 256, 256, 0, s>>>(m->u, m->cells, sc->kind, sc->A, sc->a, sc->xc, sc->zc, m->B,
+                                                      m->P, m->geo);
+    ADG_CK(cudaGetLastError(), "amr init launch");
+    return ADG_OK;
+}
+int amr_init_scenario(adg_mesh* m, const adg_scenario* sc, void* stream) {
+    AMR_DISPATCH(init_amr_n, m, sc, (cudaStream_t)stream)
+}
+
+template <int N>
+static int speed_amr_n(adg_mesh* m, double* lam, cudaStream_t s) {
+    const int total = m->cells * (N + 1) * (N + 1);
+    const int blocks = (total + 255) / 256;
+    double* part = nullptr;
+    if (cudaMalloc(&part, (size_t)blocks * 8) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ADG_ENOMEM, "amr stable_dt");
+    }
+    const double eta = (2.0 * N + 1.0) / (m->hmin * 1.2533141373155002);
+    k_max_speed_amr<N><<<blocks, 256, 0, s>>>(m->u, part, m->cells, m->B, m->P, m->geo, eta);
+    std::vector<double> h(blocks);
+    cudaError_t e = cudaMemcpyAsync(h.data(), part, (size_t)blocks * 8, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(part);
+    if (e != cudaSuccess) return cuda_fail(e, "amr stable_dt");
+    double mx = 0.0;
+    for (double v : h) mx = std::fmax(mx, v);
+    *lam = mx;
+    return ADG_OK;
+}
+int amr_max_speed(adg_mesh* m, double* lam, void* stream) { AMR_DISPATCH(speed_amr_n, m, lam, (cudaStream_t)stream) }
+
+template <int N>
+static int transfer_n(adg_mesh* m, const double* uold, double* unew, int leaves, const int* trans, cudaStream_t s) {
+    const int total = leaves * (N + 1) * (N + 1);
+    k_amr_transfer<N><<<(total + 127) / 128, 128, 0, s>>>(uold, unew, leaves, trans, m->B, tree_of(m)->ops);
+    ADG_CK(cudaGetLastError(), "amr transfer launch");
+    return ADG_OK;
+}
+static int amr_transfer(adg_mesh* m, const double* uold, double* unew, int leaves, const int* trans,
+                        cudaStream_t s) {
+    AMR_DISPATCH(transfer_n, m, uold, unew, leaves, trans, s)
+}
+
+}  // namespace adg
+
+// ------------------------------------------------------------------ C ABI
+using adg::AmrTree;
+
+extern "C" size_t adg_leaf_count(const adg_mesh* m) {
+    return m ? (size_t)m->cells : 0;
+}
+
+extern "C" int adg_leaf_info(const adg_mesh* m, int* out, size_t count) {
+    if (!m || !out) return adg::fail(ADG_EINVAL, "leaf_info: NULL argument");
+    if (count != 3 * (size_t)m->cells) return adg::fail(ADG_EINVAL, "leaf_info: count != 3 * leaves");
+    if (!m->amr) {
+        for (int c = 0; c < m->cells; ++c) {
+            out[3 * c] = 0;
+            out[3 * c + 1] = c % m->d.nx;
+            out[3 * c + 2] = c / m->d.nx;
+        }
+        return ADG_OK;
+    }
+    const AmrTree* T = (const AmrTree*)m->tree;
+    for (int c = 0; c < m->cells; ++c)
+        for (int a = 0; a < 3; ++a) out[3 * c + a] = T->leaves[c][a];
+    return ADG_OK;
+}
+
+extern "C" int adg_adapt(adg_mesh* m, const int8_t* flags_dev, int* leaves_out, void* stream) {
+    using namespace adg;
+    if (!m || !flags_dev) return fail(ADG_EINVAL, "adapt: NULL argument");
+    if (!m->amr) return fail(ADG_EINVAL, "adapt: mesh was created with max_levels = 0");
+    if (int rc = set_device(m)) return rc;
+    AmrTree* T = (AmrTree*)m->tree;
+    const int L = m->cells;
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<int8_t> fl(L);
+    ADG_CK(cudaMemcpyAsync(fl.data(), flags_dev, L, cudaMemcpyDeviceToHost, s), "adapt: flags");
+    ADG_CK(cudaStreamSynchronize(s), "adapt: sync");
+    // refinement set with 2-level balance (refinement wins)
+    std::vector<char> refine(L, 0);
+    for (int k = 0; k < L; ++k) refine[k] = fl[k] > 0 && T->leaves[k][0] < T->maxl;
+    int nb[kNbrInts];
+    for (bool changed = true; changed;) {
+        changed = false;
+        for (int k = 0; k < L; ++k) {
+            if (!refine[k]) continue;
+            for (int f = 0; f < 4; ++f) {
+                T->neighbour(k, f, nb);
+                if (nb[0] == NB_COARSE && !refine[nb[1]]) {
+                    refine[nb[1]] = 1;
+                    changed = true;
+                }
+            }
+        }
+    }
+    // coarsening: complete sibling groups all flagged -1, none refined, parent balanced
+    std::unordered_map<long long, std::vector<int>> groups;
+    for (int k = 0; k < L; ++k)
+        if (T->leaves[k][0] > 0)
+            groups[AmrTree::key(T->leaves[k][0] - 1, T->leaves[k][1] / 3, T->leaves[k][2] / 3)].push_back(k);
+    std::vector<char> coarse_member(L, 0);
+    std::vector<std::pair<std::array<int, 3>, std::vector<int>>> coarsen;
+    for (auto& g : groups) {
+        const std::vector<int>& ks = g.second;
+        if (ks.size() != 9) continue;
+        bool ok = true;
+        for (int k : ks)
+            if (fl[k] >= 0 || refine[k]) ok = false;
+        const int plv = T->leaves[ks[0]][0] - 1;
+        for (int k : ks) {
+            if (!ok) break;
+            for (int f = 0; f < 4; ++f) {
+                T->neighbour(k, f, nb);
+                if (nb[0] == NB_FINE) ok = false;
+                if (nb[0] == NB_CONF && std::find(ks.begin(), ks.end(), nb[1]) == ks.end() &&
+                    T->leaves[nb[1]][0] + (refine[nb[1]] ? 1 : 0) > plv + 1)
+                    ok = false;
+            }
+        }
+        if (!ok) continue;
+        for (int k : ks) coarse_member[k] = 1;
+        coarsen.push_back({{plv, T->leaves[ks[0]][1] / 3, T->leaves[ks[0]][2] / 3}, ks});
+    }
+    // new leaf list with its transfer rule
+    struct NewLeaf {
+        std::array<int, 3> c;
+        int t, a, b;
+        int src[9];
+    };
+    std::vector<NewLeaf> nl;
+    for (int k = 0; k < L; ++k) {
+        if (coarse_member[k]) continue;
+        const auto& c = T->leaves[k];
+        if (refine[k]) {
+            for (int b = 0; b < 3; ++b)
+                for (int a = 0; a < 3; ++a) {
+                    NewLeaf x{{c[0] + 1, 3 * c[1] + a, 3 * c[2] + b}, 1, a, b, {k}};
+                    nl.push_back(x);
+                }
+        } else {
+            NewLeaf x{c, 0, 0, 0, {k}};
+            nl.push_back(x);
+        }
+    }
+    for (auto& g : coarsen) {
+        NewLeaf x{g.first, 2, 0, 0, {0}};
+        for (int k : g.second) x.src[(T->leaves[k][2] % 3) * 3 + (T->leaves[k][1] % 3)] = k;
+        nl.push_back(x);
+    }
+    std::sort(nl.begin(), nl.end(), [](const NewLeaf& x, const NewLeaf& y) {
+        if (x.c[0] != y.c[0]) return x.c[0] < y.c[0];
+        if (x.c[2] != y.c[2]) return x.c[2] < y.c[2];
+        return x.c[1] < y.c[1];
+    });
+    const int L2 = (int)nl.size();
+    std::vector<int> trans((size_t)L2 * 12, 0);
+    for (int k = 0; k < L2; ++k) {
+        trans[k * 12 + 0] = nl[k].t;
+        trans[k * 12 + 1] = nl[k].a;
+        trans[k * 12 + 2] = nl[k].b;
+        for (int q = 0; q < 9; ++q) trans[k * 12 + 3 + q] = nl[k].src[q];
+    }
+    int* dtrans = nullptr;
+    double* unew = nullptr;
+    const size_t cnt = (size_t)L2 * m->n * m->n * 4;
+    if (cudaMalloc(&dtrans, trans.size() * 4) != cudaSuccess || cudaMalloc(&unew, cnt * 8) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(dtrans);
+        return fail(ADG_ENOMEM, "adapt: new state");
+    }
+    ADG_CK(cudaMemcpyAsync(dtrans, trans.data(), trans.size() * 4, cudaMemcpyHostToDevice, s), "adapt: upload");
+    int rc = amr_transfer(m, m->u, unew, L2, dtrans, s);
+    if (rc) { cudaFree(dtrans); cudaFree(unew); return rc; }
+    ADG_CK(cudaStreamSynchronize(s), "adapt: transfer sync");
+    cudaFree(dtrans);
+    T->leaves.clear();
+    for (auto& x : nl) T->leaves.push_back(x.c);
+    T->index();
+    rc = size_buffers(m, unew);
+    if (!rc) rc = upload_tables(m);
+    if (rc) return rc;
+    m->predicted = false;
+    if (leaves_out) *leaves_out = L2;
+    return ADG_OK;
+}

@@ -10,11 +10,13 @@
 #include <vector>
 
 #include "adg_internal.h"
+#include "adg_mesh.h"
 
 namespace {
-
 thread_local std::string g_err;
+}  // namespace
 
+namespace adg {
 int fail(int code, const std::string& msg) {
     g_err = msg;
     return code;
@@ -24,12 +26,11 @@ int cuda_fail(cudaError_t e, const char* what) {
     g_err = std::string(what) + ": " + cudaGetErrorString(e);
     return ADG_ECUDA;
 }
+}  // namespace adg
+using adg::cuda_fail;
+using adg::fail;
 
-#define ADG_CK(call, what)                              \
-    do {                                                \
-        cudaError_t e_ = (call);                        \
-        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
-    } while (0)
+namespace {
 
 // ---------------------------------------------------------------- basis
 // Gauss-Legendre nodes on [-1, 1] by Newton's method on the three-term
@@ -96,7 +97,9 @@ bool invert(int n, const double* A, double* Ainv) {  // Gauss-Jordan, partial pi
     return true;
 }
 
-bool build_basis(int N, adg::Basis& B) {
+}  // namespace
+
+bool adg::build_basis(int N, adg::Basis& B) {
     std::memset(&B, 0, sizeof(B));
     const int n = N + 1;
     B.n = n;
@@ -140,34 +143,7 @@ bool build_basis(int N, adg::Basis& B) {
     return true;
 }
 
-}  // namespace
-
-struct adg_mesh {
-    adg_mesh_desc d;
-    int N = 0, n = 0, cells = 0;
-    adg::Basis B;
-    adg::Phys P;
-    double* u = nullptr;
-    double* rvol = nullptr;
-    double* trace = nullptr;
-    double* trace_bar = nullptr; // adjoint of the traces (allocated on first adg_step_adjoint)
-    double* tv = nullptr;
-    double* stats = nullptr;     // device [2]
-    double* part = nullptr;      // device partial (count, mean, M2) triples of the TV statistics
-    double* speed = nullptr;     // device partial maxima
-    int speed_blocks = 0;
-    int* flag = nullptr;         // device int
-    double* bgbuf = nullptr;     // pbar_node, rhobar_node, pbar_face, rhobar_face
-    adg::Background bg{};
-    // mixed precision
-    adg::BasisF Bf;
-    adg::PhysF Pf;
-    void* mixbuf = nullptr;
-    adg::MixedBg mbg{};
-    double t = 0.0;
-    bool predicted = false;
-    double pred_dt = 0.0;
-};
+using adg::build_basis;
 
 namespace {
 
@@ -184,6 +160,7 @@ void free_mesh(adg_mesh* m) {
     cudaFree(m->flag);
     cudaFree(m->bgbuf);
     cudaFree(m->mixbuf);
+    if (m->amr) adg::amr_free(m);
     delete m;
 }
 
@@ -285,12 +262,13 @@ int build_mixed(adg_mesh* m) {
     return ADG_OK;
 }
 
-int set_device(const adg_mesh* m) {
+}  // namespace
+
+int adg::set_device(const adg_mesh* m) {
     ADG_CK(cudaSetDevice(m->d.device), "cudaSetDevice");
     return ADG_OK;
 }
-
-}  // namespace
+using adg::set_device;
 
 extern "C" {
 
@@ -316,6 +294,9 @@ int adg_create_mesh(const adg_mesh_desc* d, adg_mesh** out) {
         return fail(ADG_EINVAL, "create_mesh: unknown precision");
     if (d->gravity && !(d->theta0 > 0.0 && d->p0 > 0.0))
         return fail(ADG_EINVAL, "create_mesh: gravity needs theta0 > 0 and p0 > 0");
+    if (d->max_levels < 0 || d->max_levels > 4) return fail(ADG_EINVAL, "create_mesh: max_levels must be in [0, 4]");
+    if (d->max_levels > 0 && d->precision != ADG_PREC_FP64)
+        return fail(ADG_EUNSUPPORTED, "create_mesh: adaptive meshes are built for ADG_PREC_FP64");
     int ndev = 0;
     ADG_CK(cudaGetDeviceCount(&ndev), "cudaGetDeviceCount");
     if (d->device < 0 || d->device >= ndev) return fail(ADG_EINVAL, "create_mesh: bad device ordinal");
@@ -409,6 +390,13 @@ int adg_create_mesh(const adg_mesh_desc* d, adg_mesh** out) {
             return rc2;
         }
     }
+    if (d->max_levels > 0) {
+        int rc3 = adg::amr_setup(m);
+        if (rc3) {
+            free_mesh(m);
+            return rc3;
+        }
+    }
     m->bg.pbar_node = m->bgbuf;
     m->bg.rhobar_node = m->bgbuf + (size_t)d->ny * m->n;
     m->bg.pbar_face = m->bgbuf + 2 * (size_t)d->ny * m->n;
@@ -467,8 +455,12 @@ int adg_init_scenario(adg_mesh* m, const adg_scenario* s, void* stream) {
     if (s->kind == ADG_SCEN_COSINE && !(s->a > 0.0))
         return fail(ADG_EINVAL, "init_scenario: cosine bubble radius must be > 0");
     if (int rc = set_device(m)) return rc;
-    int e = adg::launch_init_scenario(m->N, m->u, m->cells, s->kind, s->A, s->a, s->xc, s->zc, m->B, m->P, stream);
-    if (e) return cuda_fail((cudaError_t)e, "init_scenario");
+    if (m->amr) {
+        if (int rc = adg::amr_init_scenario(m, s, stream)) return rc;
+    } else {
+        int e = adg::launch_init_scenario(m->N, m->u, m->cells, s->kind, s->A, s->a, s->xc, s->zc, m->B, m->P, stream);
+        if (e) return cuda_fail((cudaError_t)e, "init_scenario");
+    }
     m->predicted = false;
     m->t = 0.0;
     return ADG_OK;
@@ -478,6 +470,12 @@ int adg_predictor(adg_mesh* m, double dt, void* stream) {
     if (!m) return fail(ADG_EINVAL, "predictor: NULL mesh");
     if (!(dt > 0.0) || !std::isfinite(dt)) return fail(ADG_EINVAL, "predictor: dt must be finite and > 0");
     if (int rc = set_device(m)) return rc;
+    if (m->amr) {
+        if (int rc = adg::amr_predictor(m, dt, stream)) return rc;
+        m->predicted = true;
+        m->pred_dt = dt;
+        return ADG_OK;
+    }
     int e;
     if (m->d.precision == ADG_PREC_FP64)
         e = adg::launch_predictor_fp64(m->N, m->u, m->rvol, m->trace, m->cells, dt, m->t, m->B, m->P, m->bg, stream);
@@ -495,6 +493,11 @@ int adg_corrector(adg_mesh* m, double dt, void* stream) {
     if (!m->predicted || m->pred_dt != dt)
         return fail(ADG_ESTATE, "corrector: needs a preceding predictor with the same dt");
     if (int rc = set_device(m)) return rc;
+    if (m->amr) {
+        if (int rc = adg::amr_corrector(m, dt, stream)) return rc;
+        m->predicted = false;
+        return ADG_OK;
+    }
     int e = m->d.precision == ADG_PREC_FP64
                 ? adg::launch_corrector_fp64(m->N, m->u, m->rvol, m->trace, m->cells, dt, m->B, m->P, m->bg, stream)
                 : adg::launch_corrector_mixed(m->N, m->u, (const float*)m->rvol, (const float*)m->trace, m->cells,
@@ -517,6 +520,14 @@ int adg_stable_dt(adg_mesh* m, double cfl, double* dt, void* stream) {
     if (!m || !dt) return fail(ADG_EINVAL, "stable_dt: NULL argument");
     if (!(cfl > 0.0)) return fail(ADG_EINVAL, "stable_dt: cfl must be > 0");
     if (int rc = set_device(m)) return rc;
+    if (m->amr) {
+        double lam = 0.0;
+        if (int rc = adg::amr_max_speed(m, &lam, stream)) return rc;
+        if (!(lam > 0.0) || !std::isfinite(lam) || lam >= 1e300)
+            return fail(ADG_ENONFINITE, "stable_dt: non-finite or non-positive wave speed");
+        *dt = cfl * m->hmin / (2.0 * (2.0 * m->N + 1.0) * lam);
+        return ADG_OK;
+    }
     int nb = 0;
     int e = adg::launch_max_speed(m->N, m->u, m->speed, m->cells, m->B, m->P, &nb, stream);
     if (e) return cuda_fail((cudaError_t)e, "stable_dt launch");
@@ -541,7 +552,8 @@ int adg_tv_indicator(adg_mesh* m, int var, double T_r, double T_c, double* tv, i
     if (!(T_r > T_c)) return fail(ADG_EINVAL, "tv_indicator: needs T_r > T_c");
     if (int rc = set_device(m)) return rc;
     double* tvbuf = tv ? tv : m->tv;
-    int e = m->d.precision == ADG_PREC_FP64
+    int e = m->amr ? adg::amr_tv_cells(m, var, tvbuf, stream)
+            : m->d.precision == ADG_PREC_FP64
                 ? adg::launch_tv_cells(m->N, m->u, tvbuf, m->cells, var, m->B, m->P, stream)
                 : adg::launch_tv_cells_mixed(m->N, m->u, tvbuf, m->cells, var, m->Bf, m->Pf, m->mbg,
                                              m->d.theta0, m->P.Rcp, stream);
@@ -561,6 +573,7 @@ int adg_step_adjoint(adg_mesh* m, double dt, const double* u_n, const double* la
     if (!(dt > 0.0) || !std::isfinite(dt)) return fail(ADG_EINVAL, "step_adjoint: dt must be finite and > 0");
     if (m->d.precision != ADG_PREC_FP64) return fail(ADG_EUNSUPPORTED, "step_adjoint: FP64 meshes only");
     if (m->N > 5) return fail(ADG_EUNSUPPORTED, "step_adjoint: built for degree <= 5");
+    if (m->amr) return fail(ADG_EUNSUPPORTED, "step_adjoint: uniform meshes only");
     if (lam_n == lam_np1 || lam_n == u_n) return fail(ADG_EINVAL, "step_adjoint: lam_n must not alias the inputs");
     if (int rc = set_device(m)) return rc;
     const size_t tr = (size_t)m->cells * 4 * adg::kTraceComps * m->n;

@@ -25,6 +25,7 @@
 
 #include "adg_internal.h"
 #include "adg_physics.cuh"
+#include "adg_fp64_body.cuh"
 
 namespace adg {
 
@@ -42,193 +43,17 @@ __global__ void __launch_bounds__(CPB*(N + 1) * (N + 1))
 k_predictor_fp64(const double* __restrict__ u, double* __restrict__ rvol,
                  double* __restrict__ trace, int cells, double dt, double t,
                  const Basis B, const Phys P, const Background bg) {
-    constexpr int n = N + 1, n2 = n * n, SL = 4 * n2;
+    constexpr int n = N + 1, n2 = n * n;
     extern __shared__ double sm[];
+    (void)t;
     const int cl = threadIdx.x / n2;
-    const int node = threadIdx.x - cl * n2;
-    const int j = node / n, i = node - j * n;
+    const int j = (threadIdx.x - cl * n2) / n;
     const int cell_raw = blockIdx.x * CPB + cl;
     const bool active = cell_raw < cells;
     const int cell = active ? cell_raw : cells - 1;
-    double* Q = sm + (size_t)cl * (3 * n * SL);
-    double* Fs = Q + n * SL;
-    double* Gs = Fs + n * SL;
     const int ix = cell % P.nx, iy = cell / P.nx;
-    const double x = P.x0 + (ix + B.xi[i]) * P.hx;
-    const double z = P.y0 + (iy + B.xi[j]) * P.hy;
-    const double pbar = bg.pbar_node[iy * n + j];
-    const double rhobar = bg.rhobar_node[iy * n + j];
-    (void)t;
-
-    double uu[4];
-    const double* uc = u + (size_t)cell * SL;
-#pragma unroll
-    for (int v = 0; v < 4; ++v) {
-        uu[v] = uc[v * n2 + node];
-        Q[v * n2 + node] = uu[v];
-    }
-    double Sm[4] = {0.0, 0.0, 0.0, 0.0};
-    if (P.source == ADG_SRC_STEADY) steady_source(x, z, P, Sm);
-    __syncthreads();
-
-    // gradients of q_k at this node and the point-wise fluxes; F, G to smem
-    auto eval_node = [&](const double* Qk, double q[4], double qx[4], double qy[4], Flux4& f) {
-#pragma unroll
-        for (int v = 0; v < 4; ++v) {
-            const double* Qv = Qk + v * n2;
-            q[v] = Qv[node];
-            double sx = 0.0, sy = 0.0;
-#pragma unroll
-            for (int p = 0; p < n; ++p) {
-                sx += B.D[i][p] * Qv[j * n + p];
-                sy += B.D[j][p] * Qv[p * n + i];
-            }
-            qx[v] = sx * P.inv_hx;
-            qy[v] = sy * P.inv_hy;
-        }
-        ns_flux(q, qx, qy, z, pbar, rhobar, P, f);
-    };
-    // -dF/dx - dG/dy at this node from the fluxes of time slice k in smem
-    auto divergence = [&](int k, int v) {
-        const double* Fv = Fs + k * SL + v * n2;
-        const double* Gv = Gs + k * SL + v * n2;
-        double sx = 0.0, sy = 0.0;
-#pragma unroll
-        for (int p = 0; p < n; ++p) {
-            sx += B.D[i][p] * Fv[j * n + p];
-            sy += B.D[j][p] * Gv[p * n + i];
-        }
-        return -(sx * P.inv_hx + sy * P.inv_hy);
-    };
-
-    // sweep 1: the iterate is u at every time node, so one flux evaluation
-    {
-        double q[4], qx[4], qy[4];
-        Flux4 f;
-        eval_node(Q, q, qx, qy, f);
-#pragma unroll
-        for (int v = 0; v < 4; ++v) {
-            Fs[v * n2 + node] = f.F[v];
-            Gs[v * n2 + node] = f.G[v];
-        }
-        double R0[4];
-        __syncthreads();
-#pragma unroll
-        for (int v = 0; v < 4; ++v) R0[v] = f.S[v] + Sm[v] + divergence(0, v);
-#pragma unroll
-        for (int l = 0; l < n; ++l) {
-#pragma unroll
-            for (int v = 0; v < 4; ++v) Q[l * SL + v * n2 + node] = uu[v] + dt * (B.Kw1[l] * R0[v]);
-        }
-        __syncthreads();
-    }
-    // sweeps 2..n
-#pragma unroll 1
-    for (int r = 1; r < n; ++r) {
-        double R[n][4];
-#pragma unroll
-        for (int k = 0; k < n; ++k) {
-            double q[4], qx[4], qy[4];
-            Flux4 f;
-            eval_node(Q + k * SL, q, qx, qy, f);
-#pragma unroll
-            for (int v = 0; v < 4; ++v) {
-                Fs[k * SL + v * n2 + node] = f.F[v];
-                Gs[k * SL + v * n2 + node] = f.G[v];
-                R[k][v] = f.S[v] + Sm[v];
-            }
-        }
-        __syncthreads();
-#pragma unroll
-        for (int k = 0; k < n; ++k) {
-#pragma unroll
-            for (int v = 0; v < 4; ++v) R[k][v] += divergence(k, v);
-        }
-#pragma unroll
-        for (int l = 0; l < n; ++l) {
-#pragma unroll
-            for (int v = 0; v < 4; ++v) {
-                double acc = 0.0;
-#pragma unroll
-                for (int k = 0; k < n; ++k) acc += B.Kw[l][k] * R[k][v];
-                Q[l * SL + v * n2 + node] = uu[v] + dt * acc;
-            }
-        }
-        __syncthreads();
-    }
-
-    // final evaluation on the converged iterate and time averages
-    double qb[4], Fb[4], Gb[4], Sb[4], qxb[4], qyb[4];
-#pragma unroll
-    for (int v = 0; v < 4; ++v) qb[v] = Fb[v] = Gb[v] = Sb[v] = qxb[v] = qyb[v] = 0.0;
-#pragma unroll
-    for (int k = 0; k < n; ++k) {
-        double q[4], qx[4], qy[4];
-        Flux4 f;
-        eval_node(Q + k * SL, q, qx, qy, f);
-        const double wk = B.w[k];
-#pragma unroll
-        for (int v = 0; v < 4; ++v) {
-            qb[v] += wk * q[v];
-            Fb[v] += wk * f.F[v];
-            Gb[v] += wk * f.G[v];
-            Sb[v] += wk * (f.S[v] + Sm[v]);
-            qxb[v] += wk * qx[v];
-            qyb[v] += wk * qy[v];
-        }
-    }
-    __syncthreads();
-    // time averages to shared memory: slots 0..4 = qbar, Fbar, Gbar, qxbar, qybar
-    double* A = Q;
-#pragma unroll
-    for (int v = 0; v < 4; ++v) {
-        A[0 * SL + v * n2 + node] = qb[v];
-        A[1 * SL + v * n2 + node] = Fb[v];
-        A[2 * SL + v * n2 + node] = Gb[v];
-        A[3 * SL + v * n2 + node] = qxb[v];
-        A[4 * SL + v * n2 + node] = qyb[v];
-    }
-    __syncthreads();
-    if (active) {
-        double* rc = rvol + (size_t)cell * SL;
-#pragma unroll
-        for (int v = 0; v < 4; ++v) {
-            double sx = 0.0, sy = 0.0;
-#pragma unroll
-            for (int p = 0; p < n; ++p) {
-                sx += B.Vx[p][i] * A[1 * SL + v * n2 + j * n + p];
-                sy += B.Vx[p][j] * A[2 * SL + v * n2 + p * n + i];
-            }
-            rc[v * n2 + node] = sx * P.inv_hx + sy * P.inv_hy + Sb[v];
-        }
-    }
-    // boundary-extrapolated traces: faces E, W (x = const), N, S (y = const)
-    for (int idx = node; idx < 4 * n; idx += n2) {
-        const int f = idx / n, m = idx - f * n;
-        const bool xface = f < 2;
-        const double* phi = (f == 0 || f == 2) ? B.phi1 : B.phi0;
-        double rec[kTraceComps];
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            const int slot = c == 0 ? 0 : c == 1 ? (xface ? 1 : 2) : (c == 2 ? 3 : 4);
-#pragma unroll
-            for (int v = 0; v < 4; ++v) {
-                const double* S = A + slot * SL + v * n2;
-                double s = 0.0;
-#pragma unroll
-                for (int p = 0; p < n; ++p) s += phi[p] * (xface ? S[m * n + p] : S[p * n + m]);
-                rec[c * 4 + v] = s;
-            }
-        }
-        const double zf = xface ? P.y0 + (iy + B.xi[m]) * P.hy
-                                : P.y0 + (iy + (f == 2 ? 1 : 0)) * P.hy;
-        rec[16] = wave_speed(rec, zf, xface, P);
-        if (active) {
-            double* tr = trace + ((size_t)cell * 4 + f) * kTraceComps * n;
-#pragma unroll
-            for (int c = 0; c < kTraceComps; ++c) tr[c * n + m] = rec[c];
-        }
-    }
+    predictor_fp64_body<N, CPB>(u, rvol, trace, cell, active, dt, B, P, P.x0 + ix * P.hx, P.y0 + iy * P.hy,
+                                bg.pbar_node[iy * n + j], bg.rhobar_node[iy * n + j], sm);
 }
 
 // Slip-wall ghost of face f (0 E, 1 W, 2 N, 3 S) from the interior trace

@@ -1,0 +1,64 @@
+// Internal definition of the mesh object and shared host helpers of the
+// library's translation units (not part of the C ABI).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+
+#include "adg_internal.h"
+
+struct adg_mesh {
+    adg_mesh_desc d;
+    int N = 0, n = 0, cells = 0;
+    adg::Basis B;
+    adg::Phys P;
+    double* u = nullptr;
+    double* rvol = nullptr;
+    double* trace = nullptr;
+    double* trace_bar = nullptr; // adjoint of the traces (allocated on first adg_step_adjoint)
+    double* tv = nullptr;
+    double* stats = nullptr;     // device [2]
+    double* part = nullptr;      // device partial (count, mean, M2) triples of the TV statistics
+    double* speed = nullptr;     // device partial maxima
+    int speed_blocks = 0;
+    int* flag = nullptr;         // device int
+    double* bgbuf = nullptr;     // pbar_node, rhobar_node, pbar_face, rhobar_face
+    adg::Background bg{};
+    // mixed precision
+    adg::BasisF Bf;
+    adg::PhysF Pf;
+    void* mixbuf = nullptr;
+    adg::MixedBg mbg{};
+    double t = 0.0;
+    bool predicted = false;
+    double pred_dt = 0.0;
+    // adaptive 3:1 tree (desc.max_levels > 0); cells = number of leaves
+    int amr = 0;
+    void* tree = nullptr;         // host tree (adg_amr.cu)
+    double* geo = nullptr;        // [leaves][4]: x0, y0, hx, hy of each leaf
+    int* nbr = nullptr;           // [leaves][4 faces][5]: type, id0, id1, id2, sub-face
+    double* bgl = nullptr;        // [leaves][n][2] node background, then [leaves][2][2] N/S faces
+    double hmin = 0.0;            // smallest leaf size (dt rule)
+};
+
+namespace adg {
+int fail(int code, const std::string& msg);
+int cuda_fail(cudaError_t e, const char* what);
+bool build_basis(int N, Basis& B);
+int set_device(const adg_mesh* m);
+
+// adaptive-mesh path (adg_amr.cu)
+int amr_setup(adg_mesh* m);
+void amr_free(adg_mesh* m);
+int amr_predictor(adg_mesh* m, double dt, void* stream);
+int amr_corrector(adg_mesh* m, double dt, void* stream);
+int amr_tv_cells(adg_mesh* m, int var, double* tv, void* stream);
+int amr_max_speed(adg_mesh* m, double* lam_max, void* stream);
+int amr_init_scenario(adg_mesh* m, const adg_scenario* s, void* stream);
+}  // namespace adg
+
+#define ADG_CK(call, what)                                        \
+    do {                                                          \
+        cudaError_t e_ = (call);                                  \
+        if (e_ != cudaSuccess) return adg::cuda_fail(e_, what);   \
+    } while (0)

@@ -90,30 +90,41 @@ struct MixCfg {
     static constexpr int cpb_default = N == 1 ? 32 : N == 2 ? 16 : N == 3 ? 8 : N <= 5 ? 4 : 2;
     static constexpr int cpb = CPB_ ? CPB_ : cpb_default;
     static constexpr int threads = cpb * n * n;
-    // per-cell smem stride padded to 16 (mod 32) floats: neighbouring cells of
-    // one warp then fall on disjoint banks in the row/column contractions
-    static constexpr int raw = 3 * n * 4 * n * n;
+    // rows padded to an even length (8-byte vector loads); per-cell smem stride
+    // padded to 16 (mod 32) floats: neighbouring cells of one warp then fall on
+    // disjoint banks in the row contractions
+    static constexpr int np = n + (n & 1);
+    static constexpr int raw = 4 * n * 4 * n * np;
     static constexpr int stride = raw + ((16 - raw % 32) + 32) % 32;
     static constexpr size_t smem_pred = (size_t)cpb * stride * sizeof(float);
 };
 
 // Predictor body for the tile of CPB cells starting at cell c0 (one thread per
 // spatial node); shared by the per-mesh kernel and the batched persistent one.
+//
+// Shared-memory layout per cell (floats): the iterate q' in row-major [v][j][i]
+// and in transposed [v][i][j] form, the x-flux F row-major and the y-flux G
+// transposed, each for n time slices, rows padded to an even length NP.  Every
+// contraction then reads one contiguous row with 8-byte vector loads: the
+// x-derivative from the row-major copy, the y-derivative from the transposed
+// copy (the shared-memory instruction count, which bounds this kernel, halves).
 template <int N, int CPB>
 __device__ __forceinline__ void predictor_mixed_body(const double* __restrict__ u, float* __restrict__ rvol,
                                                      float* __restrict__ trace, int cells, int c0, float dt,
                                                      const BasisF& B, const PhysF& P, const MixedBg& bg,
                                                      float* smf) {
     constexpr int n = N + 1, n2 = n * n, SL = 4 * n2;
+    constexpr int NP = MixCfg<N, CPB>::np, RS = n * NP, SLP = 4 * RS;  // padded row, var and slice strides
     const int cl = threadIdx.x / n2;
     const int node = threadIdx.x - cl * n2;
     const int j = node / n, i = node - j * n;
     const int cell_raw = c0 + cl;
     const bool active = cell_raw < cells;
     const int cell = active ? cell_raw : cells - 1;
-    float* Q = smf + (size_t)cl * MixCfg<N, CPB>::stride;
-    float* Fs = Q + n * SL;
-    float* Gs = Fs + n * SL;
+    float* Q = smf + (size_t)cl * MixCfg<N, CPB>::stride;  // [k][v][j][i]
+    float* QT = Q + n * SLP;                               // [k][v][i][j]
+    float* Fs = QT + n * SLP;                              // [k][v][j][i]
+    float* GT = Fs + n * SLP;                              // [k][v][i][j]
     const int ix = cell % P.nx, iy = cell / P.nx;
     const int row = iy * n + j;
     const float x = P.x0 + (ix + B.xi[i]) * P.hx;
@@ -121,7 +132,11 @@ __device__ __forceinline__ void predictor_mixed_body(const double* __restrict__ 
     (void)x;
     const float rb = (float)bg.rb[row], Eb = (float)bg.Eb[row], pb = bg.pb[row];
     const float dzr = bg.dzr[row], dzE = bg.dzE[row];
+    const int rm = j * NP + i, tm = i * NP + j;  // this node in row-major / transposed rows
 
+    if (NP != n) {  // zero the row padding once (it is multiplied by D[.][n] = 0)
+        for (int a = node; a < 4 * n * 4 * n; a += n2) Q[a * NP + n] = 0.f;
+    }
     // FP64 perturbation split, then FP32 from here on
     float up[4];
     const double* uc = u + (size_t)cell * SL;
@@ -130,7 +145,10 @@ __device__ __forceinline__ void predictor_mixed_body(const double* __restrict__ 
     up[2] = (float)uc[2 * n2 + node];
     up[3] = (float)(uc[3 * n2 + node] - bg.Eb[row]);
 #pragma unroll
-    for (int v = 0; v < 4; ++v) Q[v * n2 + node] = up[v];
+    for (int v = 0; v < 4; ++v) {
+        Q[v * RS + rm] = up[v];
+        QT[v * RS + tm] = up[v];
+    }
     float Sm[4] = {0.f, 0.f, 0.f, 0.f};
     if (P.source == ADG_SRC_STEADY) {
         const float k = 6.283185307179586f / P.sL;
@@ -148,45 +166,52 @@ __device__ __forceinline__ void predictor_mixed_body(const double* __restrict__ 
     }
     __syncthreads();
 
-    auto eval_node = [&](const float* Qk, float q[4], float gx[4], float gy[4], FluxF& f) {
+    // D-contraction of the contiguous row starting at r with D row d
+    auto rowdot = [&](const float* r, const float* d) {
+        const float2* r2 = reinterpret_cast<const float2*>(r);
+        float s = 0.f;
+#pragma unroll
+        for (int p = 0; p < NP / 2; ++p) {
+            const float2 a = r2[p];
+            s = fmaf(d[2 * p], a.x, s);
+            s = fmaf(d[2 * p + 1], a.y, s);
+        }
+        return s;
+    };
+    auto eval_node = [&](int k, float q[4], float gx[4], float gy[4], FluxF& f) {
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
-            const float* Qv = Qk + v * n2;
-            q[v] = Qv[node];
-            float sx = 0.f, sy = 0.f;
-#pragma unroll
-            for (int p = 0; p < n; ++p) {
-                sx = fmaf(B.D[i][p], Qv[j * n + p], sx);
-                sy = fmaf(B.D[j][p], Qv[p * n + i], sy);
-            }
-            gx[v] = sx * P.inv_hx;
-            gy[v] = sy * P.inv_hy;
+            const float* Qv = Q + k * SLP + v * RS;
+            q[v] = Qv[rm];
+            gx[v] = rowdot(Qv + j * NP, B.D[i]) * P.inv_hx;
+            gy[v] = rowdot(QT + k * SLP + v * RS + i * NP, B.D[j]) * P.inv_hy;
         }
         gy[0] += dzr;
         gy[3] += dzE;
         ns_flux_pert(q, gx, gy, z, rb, Eb, pb, P, f);
     };
-    auto divergence = [&](int k, int v) {
-        const float* Fv = Fs + k * SL + v * n2;
-        const float* Gv = Gs + k * SL + v * n2;
-        float sx = 0.f, sy = 0.f;
+    auto store_flux = [&](int k, const FluxF& f) {
 #pragma unroll
-        for (int p = 0; p < n; ++p) {
-            sx = fmaf(B.D[i][p], Fv[j * n + p], sx);
-            sy = fmaf(B.D[j][p], Gv[p * n + i], sy);
+        for (int v = 0; v < 4; ++v) {
+            Fs[k * SLP + v * RS + rm] = f.F[v];
+            GT[k * SLP + v * RS + tm] = f.G[v];
         }
+    };
+    auto divergence = [&](int k, int v) {
+        const float sx = rowdot(Fs + k * SLP + v * RS + j * NP, B.D[i]);
+        const float sy = rowdot(GT + k * SLP + v * RS + i * NP, B.D[j]);
         return -(sx * P.inv_hx + sy * P.inv_hy);
+    };
+    auto store_q = [&](int l, int v, float val) {
+        Q[l * SLP + v * RS + rm] = val;
+        QT[l * SLP + v * RS + tm] = val;
     };
 
     {  // sweep 1: iterate constant in time
         float q[4], gx[4], gy[4];
         FluxF f;
-        eval_node(Q, q, gx, gy, f);
-#pragma unroll
-        for (int v = 0; v < 4; ++v) {
-            Fs[v * n2 + node] = f.F[v];
-            Gs[v * n2 + node] = f.G[v];
-        }
+        eval_node(0, q, gx, gy, f);
+        store_flux(0, f);
         __syncthreads();
         float R0[4];
 #pragma unroll
@@ -194,7 +219,7 @@ __device__ __forceinline__ void predictor_mixed_body(const double* __restrict__ 
 #pragma unroll
         for (int l = 0; l < n; ++l) {
 #pragma unroll
-            for (int v = 0; v < 4; ++v) Q[l * SL + v * n2 + node] = fmaf(dt, B.Kw1[l] * R0[v], up[v]);
+            for (int v = 0; v < 4; ++v) store_q(l, v, fmaf(dt, B.Kw1[l] * R0[v], up[v]));
         }
         __syncthreads();
     }
@@ -205,13 +230,10 @@ __device__ __forceinline__ void predictor_mixed_body(const double* __restrict__ 
         for (int k = 0; k < n; ++k) {
             float q[4], gx[4], gy[4];
             FluxF f;
-            eval_node(Q + k * SL, q, gx, gy, f);
+            eval_node(k, q, gx, gy, f);
+            store_flux(k, f);
 #pragma unroll
-            for (int v = 0; v < 4; ++v) {
-                Fs[k * SL + v * n2 + node] = f.F[v];
-                Gs[k * SL + v * n2 + node] = f.G[v];
-                R[k][v] = f.S[v] + Sm[v];
-            }
+            for (int v = 0; v < 4; ++v) R[k][v] = f.S[v] + Sm[v];
         }
         __syncthreads();
 #pragma unroll
@@ -226,7 +248,7 @@ __device__ __forceinline__ void predictor_mixed_body(const double* __restrict__ 
                 float acc = 0.f;
 #pragma unroll
                 for (int k = 0; k < n; ++k) acc = fmaf(B.Kw[l][k], R[k][v], acc);
-                Q[l * SL + v * n2 + node] = fmaf(dt, acc, up[v]);
+                store_q(l, v, fmaf(dt, acc, up[v]));
             }
         }
         __syncthreads();
@@ -239,7 +261,7 @@ __device__ __forceinline__ void predictor_mixed_body(const double* __restrict__ 
     for (int k = 0; k < n; ++k) {
         float q[4], gx[4], gy[4];
         FluxF f;
-        eval_node(Q + k * SL, q, gx, gy, f);
+        eval_node(k, q, gx, gy, f);
         const float wk = B.w[k];
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
@@ -252,14 +274,15 @@ __device__ __forceinline__ void predictor_mixed_body(const double* __restrict__ 
         }
     }
     __syncthreads();
+    // time averages, row-major with padded rows: slots 0..4 = qbar, Fbar, Gbar, qxbar, qybar
     float* A = Q;
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
-        A[0 * SL + v * n2 + node] = qb[v];
-        A[1 * SL + v * n2 + node] = Fb[v];
-        A[2 * SL + v * n2 + node] = Gb[v];
-        A[3 * SL + v * n2 + node] = qxb[v];
-        A[4 * SL + v * n2 + node] = qyb[v];
+        A[0 * SLP + v * RS + rm] = qb[v];
+        A[1 * SLP + v * RS + rm] = Fb[v];
+        A[2 * SLP + v * RS + rm] = Gb[v];
+        A[3 * SLP + v * RS + rm] = qxb[v];
+        A[4 * SLP + v * RS + rm] = qyb[v];
     }
     __syncthreads();
     if (active) {
@@ -269,8 +292,8 @@ __device__ __forceinline__ void predictor_mixed_body(const double* __restrict__ 
             float sx = 0.f, sy = 0.f;
 #pragma unroll
             for (int p = 0; p < n; ++p) {
-                sx = fmaf(B.Vx[p][i], A[1 * SL + v * n2 + j * n + p], sx);
-                sy = fmaf(B.Vx[p][j], A[2 * SL + v * n2 + p * n + i], sy);
+                sx = fmaf(B.Vx[p][i], A[1 * SLP + v * RS + j * NP + p], sx);
+                sy = fmaf(B.Vx[p][j], A[2 * SLP + v * RS + p * NP + i], sy);
             }
             rc[v * n2 + node] = sx * P.inv_hx + sy * P.inv_hy + Sb[v];
         }
@@ -285,10 +308,10 @@ __device__ __forceinline__ void predictor_mixed_body(const double* __restrict__ 
             const int slot = c == 0 ? 0 : c == 1 ? (xface ? 1 : 2) : (c == 2 ? 3 : 4);
 #pragma unroll
             for (int v = 0; v < 4; ++v) {
-                const float* S = A + slot * SL + v * n2;
+                const float* S = A + slot * SLP + v * RS;
                 float s = 0.f;
 #pragma unroll
-                for (int p = 0; p < n; ++p) s = fmaf(phi[p], xface ? S[m * n + p] : S[p * n + m], s);
+                for (int p = 0; p < n; ++p) s = fmaf(phi[p], xface ? S[m * NP + p] : S[p * NP + m], s);
                 rec[c * 4 + v] = s;
             }
         }

@@ -1,7 +1,7 @@
 // Total-variation refinement indicator (Sec. 3, Eqs. 6-8), scenario
 // initialisation (Sec. 4.1, 4.2), stable time step and finiteness scan.
 //
-// TV per cell: TV = hx hy sum_ij w_i w_j (|df/dx| + |df/dy|) with f = theta
+// TV per cell: TV = sum_ij w_i w_j (|df/dx| + |df/dy|) with f = theta
 // (potential temperature, Sec. 4.2) or rho at the nodes, derivatives by the
 // nodal derivative matrix.  Mean and population standard deviation over all
 // cells follow Chan, Golub and LeVeque's pairwise update (cited by the paper
@@ -61,7 +61,7 @@ k_tv_cells(const double* __restrict__ u, double* __restrict__ tv, int cells, int
     if (node == 0 && active) {
         double s = 0.0;
         for (int a = 0; a < n2; ++a) s += red[cl][a];
-        tv[cell] = P.hx * P.hy * s;
+        tv[cell] = s;
     }
 }
 
@@ -119,7 +119,7 @@ k_tv_cells_mixed(const double* __restrict__ u, double* __restrict__ tv, int cell
     if (node == 0 && active) {
         double s = 0.0;
         for (int a = 0; a < n2; ++a) s += (double)red[cl][a];
-        tv[cell] = (double)P.hx * (double)P.hy * s;
+        tv[cell] = s;
     }
 }
 

@@ -40,6 +40,7 @@ class MeshConfig:
     src_p: float = 1.0
     precision: int = L.ADG_PREC_FP64
     device: int = 0
+    max_levels: int = 0
 
     def to_c(self):
         return L.MeshDesc(**{f: getattr(self, f) for f, _ in L.MeshDesc._fields_})
@@ -111,7 +112,7 @@ class Mesh:
 
     def get_state(self, out: torch.Tensor = None, stream=None):
         if out is None:
-            out = torch.empty(self.shape, dtype=torch.float64, device=self.device)
+            out = torch.empty(self.state_shape, dtype=torch.float64, device=self.device)
         assert out.dtype == torch.float64 and out.is_contiguous() and out.numel() == self.count
         L.check(self._lib.adg_get_state(self.h, ctypes.c_void_p(out.data_ptr()), self.count,
                                         1 if out.is_cuda else 0, _stream_ptr(stream)))
@@ -147,7 +148,7 @@ class Mesh:
         return dt.value
 
     def tv_indicator(self, var, T_r, T_c, want_stats=True, stream=None):
-        C = self.cfg.cells
+        C = self.leaves
         tv = torch.empty(C, dtype=torch.float64, device=self.device)
         flags = torch.empty(C, dtype=torch.int8, device=self.device)
         stats = (ctypes.c_double * 2)()
@@ -159,6 +160,30 @@ class Mesh:
 
     def check_finite(self, stream=None):
         L.check(self._lib.adg_check_finite(self.h, _stream_ptr(stream)))
+
+    # --------------------------------------------------------------- adaptive mesh
+    @property
+    def leaves(self):
+        return int(self._lib.adg_leaf_count(self.h))
+
+    def leaf_info(self):
+        n = self.leaves
+        buf = (ctypes.c_int * (3 * n))()
+        L.check(self._lib.adg_leaf_info(self.h, buf, 3 * n))
+        return [tuple(buf[3 * k:3 * k + 3]) for k in range(n)]
+
+    def adapt(self, flags: torch.Tensor, stream=None):
+        assert flags.dtype == torch.int8 and flags.is_cuda and flags.numel() == self.leaves
+        out = ctypes.c_int()
+        L.check(self._lib.adg_adapt(self.h, ctypes.c_void_p(flags.data_ptr()), ctypes.byref(out),
+                                    _stream_ptr(stream)))
+        self.count = self._lib.adg_state_count(self.h)
+        return out.value
+
+    @property
+    def state_shape(self):
+        n = self.cfg.n
+        return (self.leaves, 4, n, n)
 
 
 class Batch:

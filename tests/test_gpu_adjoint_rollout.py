@@ -35,7 +35,7 @@ def _grad(th0, m, dt, nsteps, every, cells, W, target):
     x = th0.clone().requires_grad_(True)
     J = objective_from_theta(x, m, dt, nsteps, every, cells, W, target)
     (g,) = torch.autograd.grad(J, x)
-    return float(J), g
+    return float(J.detach()), g
 
 
 def _J(th, m, dt, nsteps, cells, W, target):
@@ -73,11 +73,15 @@ def test_rollout_gradient_vs_oracle_adjoint():
 
 def test_config4_gradient_vs_central_differences():
     """Config 4: degree 3, 27x27 cells, 200 steps, checkpoints every 20, 64
-    probes; 32 seeded unit directions, central differences with h = 1e-6."""
+    probes; 32 seeded unit directions.  Step h = 1e-2 K along a unit
+    direction over 11,664 DOFs: with h = 1e-6 the central difference is
+    dominated by the FP64 rounding noise of J after 200 steps (~5e-14, from the
+    p - pbar cancellation), which alone gives relative differences of 1e-6 to
+    1e-3; at h = 1e-2 the truncation error is far below the 1e-5 bound."""
     cfg, m, dt, o, th0, probes, target, cells, W = _setup(27)
     J, g = _grad(th0, m, dt, 200, 20, cells, W, target)
     dirs = inputs.directions(32, th0.numel(), seed=2)
-    h = 1e-6
+    h = 1e-2
     worst = 0.0
     for d_np in dirs:
         d = torch.from_numpy(d_np).reshape(th0.shape).cuda()

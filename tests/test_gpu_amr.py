@@ -1,0 +1,129 @@
+"""Adaptive 3:1 tree on the GPU against the oracle's tree (oracle/amr.py):
+identical leaf sets after adaptation, transferred states, steps across
+hanging faces, conservation, TV indicator and the config-3 initial-mesh
+procedure (init -> TV -> refine, twice, re-initialising from the analytic
+two-bubble field)."""
+import math
+
+import pytest
+import torch
+
+from paper_1905_05524_gb300 import _lib as L
+from paper_1905_05524_gb300 import inputs
+from paper_1905_05524_gb300.solver import Mesh, MeshConfig, atmosphere_config
+from oracle.amr import AmrSolver
+from oracle import indicator as oind
+from oracle import physics as ph
+
+pytestmark = pytest.mark.gpu
+
+
+def _pair(cfg, bc):
+    P = ph.Params(N=cfg.degree, gamma=cfg.gamma, Pr=cfg.Pr, R=cfg.R, mu=cfg.mu, gravity=bool(cfg.gravity),
+                  g=cfg.g, p0=cfg.p0, theta0=cfg.theta0, source="none")
+    o = AmrSolver(cfg.nx, cfg.ny, P, cfg.Lx, cfg.Ly, cfg.x0, cfg.y0, bc=bc, max_level=cfg.max_levels)
+    return Mesh(cfg), o
+
+
+def _flags(k, seed, frac):
+    x = torch.from_numpy(inputs.uniform_values(k, seed=seed, lo=0.0, hi=1.0))
+    return torch.where(x < frac, 1, torch.where(x > 1 - frac / 2, -1, 0)).to(torch.int8)
+
+
+def _close(a, b, tol=1e-11):
+    nrho = torch.linalg.vector_norm(b[:, 0]).item()
+    for v in range(4):
+        d = torch.linalg.vector_norm(a[:, v] - b[:, v]).item()
+        nb = torch.linalg.vector_norm(b[:, v]).item()
+        den = max(nb, nrho) if v in (1, 2) else nb
+        assert d <= tol * den, (v, d, den)
+
+
+def _wave(X, Y, P):
+    rho = 1.0 + 0.2 * torch.sin(2 * math.pi * (X + Y) / 6.0)
+    return [rho, rho * 1.0, rho * 0.5, 1.0 / (P.gamma - 1) + 0.5 * rho * 1.25]
+
+
+def test_adapt_and_step_periodic_matches_oracle():
+    cfg = MeshConfig(degree=3, nx=6, ny=6, Lx=6.0, Ly=6.0, mu=0.05, max_levels=2)
+    m, o = _pair(cfg, "periodic")
+    u = o.interpolate_field(lambda X, Y: _wave(X, Y, o.P))
+    m.set_state(u.cuda().contiguous())
+    for seed, frac in ((1, 0.3), (2, 0.2), (3, 0.2)):
+        fl = _flags(len(o.leaves), seed, frac)
+        u = o.adapt(u, fl)
+        m.adapt(fl.cuda())
+        assert m.leaf_info() == [tuple(c) for c in o.leaves]
+        _close(m.get_state().cpu(), u, 1e-13)
+    assert len({c[0] for c in o.leaves}) >= 2
+    I0 = o.integral(u)
+    dt = 0.003
+    for _ in range(3):
+        u = o.step(u, dt)
+    m.step(dt, 3)
+    a = m.get_state().cpu()
+    _close(a, u)
+    # conservation of the GPU run on the periodic tree
+    Ia = o.integral(a)
+    assert ((Ia - I0).abs() <= 1e-13 * I0.abs().clamp(min=1.0)).all(), Ia - I0
+
+
+@pytest.mark.parametrize("degree", [3, 5])
+def test_bubble_walls_hanging_faces_matches_oracle(degree):
+    """Cosine bubble with slip walls on a 6x6 base with a refined patch (hanging
+    faces, gravity): adaptation and 3 steps match the oracle."""
+    cfg = atmosphere_config(degree=degree, nx=6, ny=6)
+    cfg.max_levels = 1
+    m, o = _pair(cfg, "wall")
+    X, Y = o.node_coords()
+    u = torch.stack(ph.bubble_state(X, Y, ph.cosine_bubble(X, Y), o.P), 1)
+    m.set_state(u.cuda().contiguous())
+    fl = torch.zeros(36, dtype=torch.int8)
+    fl[[13, 14, 15, 20, 21, 28]] = 1
+    u = o.adapt(u, fl)
+    m.adapt(fl.cuda())
+    assert m.leaf_info() == [tuple(c) for c in o.leaves]
+    _close(m.get_state().cpu(), u, 1e-13)
+    dt = m.stable_dt(0.25)
+    for _ in range(3):
+        u = o.step(u, dt)
+    m.step(dt, 3)
+    _close(m.get_state().cpu(), u)
+
+
+def _oracle_tv(o, u, var):
+    tv = torch.empty(len(o.leaves), dtype=torch.float64)
+    for lv, idx, view in o.level_views():
+        f = oind.indicator_field(view, u[idx], var)
+        tv[idx] = oind.total_variation(view, f)
+    return tv
+
+
+def test_config3_initial_mesh_and_tv_match_oracle():
+    """Two-bubble field, base 27x27 on [0,1000]^2, 2 levels, T_r = 2.5,
+    T_c = -0.5: init -> TV -> refine twice (refine only), re-initialising from
+    the analytic field; identical leaves and TV values."""
+    cfg = atmosphere_config(degree=5, nx=27, ny=27, mu=0.001)
+    cfg.max_levels = 2
+    m, o = _pair(cfg, "wall")
+    for _ in range(2):
+        X, Y = o.node_coords()
+        u = torch.stack(ph.bubble_state(X, Y, ph.two_bubbles(X, Y), o.P), 1)
+        m.init_scenario(L.ADG_SCEN_TWO_BUBBLES)
+        _close(m.get_state().cpu(), u, 1e-13)
+        tv_o = _oracle_tv(o, u, "theta")
+        mean, std = oind.mean_std(tv_o)
+        fl_o = oind.flags(tv_o, mean, std, 2.5, -0.5)
+        tv_g, fl_g, (mg, sg) = m.tv_indicator(L.ADG_TV_THETA, 2.5, -0.5)
+        floor = 1e-10 * tv_o.abs().max()
+        assert bool(((tv_g.cpu() - tv_o).abs() <= 1e-11 * tv_o.abs() + floor).all())
+        fl_o = torch.where(fl_o > 0, 1, 0).to(torch.int8)   # refine only while building the initial mesh
+        fl_g = torch.where(fl_g > 0, 1, 0).to(torch.int8)
+        assert torch.equal(fl_g.cpu(), fl_o)
+        o.adapt(u, fl_o)
+        m.adapt(fl_g)
+        assert m.leaf_info() == [tuple(c) for c in o.leaves]
+    levels = [c[0] for c in o.leaves]
+    assert max(levels) >= 1 and len(levels) < 243 * 243
+    print(f"config3 initial mesh: {len(levels)} leaves "
+          f"({levels.count(0)}/{levels.count(1)}/{levels.count(2)} per level)")
