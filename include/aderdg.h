@@ -48,6 +48,12 @@ extern "C" {
 /* ---- options ---- */
 #define ADG_BC_PERIODIC 0
 #define ADG_BC_WALL 1       /* slip wall with background ghost (Sec. 4.2, Eq. 10) */
+/* bc_y only, FP64 uniform meshes: the mesh is one horizontal strip of a
+ * larger domain split across ranks; the marked sides take the neighbour
+ * strip's face traces from halo buffers (adg_set_halo_traces) */
+#define ADG_BC_EXCHANGE 2       /* south and north faces exchange            */
+#define ADG_BC_WALL_EXCHANGE 3  /* south slip wall, north face exchanges     */
+#define ADG_BC_EXCHANGE_WALL 4  /* south face exchanges, north slip wall     */
 
 #define ADG_SRC_NONE 0
 #define ADG_SRC_STEADY 1    /* steady manufactured source rho = 1 + a sin(2pi(x+y)/L) */
@@ -153,6 +159,27 @@ int adg_tv_indicator(adg_mesh* m, int var, double T_r, double T_c,
  * FP64 meshes with degree <= 5 (ADG_EUNSUPPORTED otherwise). */
 int adg_step_adjoint(adg_mesh* m, double dt, const double* u_n, const double* lam_np1, double* lam_n,
                      void* stream);
+
+/* Strip decomposition (bc_y = ADG_BC_EXCHANGE*): the one exchange of an
+ * ADER-DG step (Sec. 1: the scheme communicates once per step) is the face
+ * trace of the cells along a strip edge.  After adg_predictor,
+ * adg_get_boundary_traces copies the south-face traces of the first row and
+ * the north-face traces of the last row to device arrays of nx*17*(N+1)
+ * doubles each ([ix][component][node]; either pointer may be NULL).  The
+ * caller sends them to the ranks below and above; adg_set_halo_traces
+ * installs the traces received from the strip below (its north traces) and
+ * above (its south traces) before adg_corrector.  ADG_EINVAL if bc_y has no
+ * exchange side. */
+int adg_get_boundary_traces(adg_mesh* m, double* south, double* north, void* stream);
+int adg_set_halo_traces(adg_mesh* m, const double* south, const double* north, void* stream);
+
+/* Refinement flags for given statistics: flags[c] from tv[c] against the
+ * mean and population deviation of `count` values with sum of squared
+ * deviations M2 (Eq. 7; used when the statistics are combined across ranks
+ * with Chan's update).  tv, flags: device arrays of the mesh's cells.
+ * Synchronises `stream`. */
+int adg_tv_flags(adg_mesh* m, const double* tv, double count, double mean, double M2, double T_r, double T_c,
+                 int8_t* flags, void* stream);
 
 /* Scan the state for NaN/Inf: ADG_ENONFINITE if any.  Synchronises `stream`. */
 int adg_check_finite(adg_mesh* m, void* stream);

@@ -47,7 +47,8 @@ class Mesh:
     Lx: float = 10.0
     Ly: float = 10.0
     bc_x: str = "periodic"   # "periodic" | "wall"
-    bc_y: str = "periodic"
+    bc_y: str = "periodic"   # also "halo", "wall_halo", "halo_wall": strip of a larger mesh
+                             # (south/north side takes the neighbour strip's traces)
 
     @property
     def hx(self):
@@ -188,8 +189,10 @@ class Solver:
         s = torch.maximum(sL, sR)[:, None]
         return 0.5 * (fL + fR) - 0.5 * s * (qR - qL)
 
-    def face_fluxes(self, tr):
-        """F*_E, F*_W (x-fluxes along j) and G*_N, G*_S (y-fluxes along i)."""
+    def face_fluxes(self, tr, halo=None):
+        """F*_E, F*_W (x-fluxes along j) and G*_N, G*_S (y-fluxes along i).
+        halo = {"S": (q, f), "N": (q, f)} with [nx, 4, n] face data of the
+        strips below and above (strip decomposition, bc_y "halo*")."""
         m = self.m
         nxc, nyc = m.nx, m.ny
         C = m.cells
@@ -222,26 +225,35 @@ class Solver:
         Gy = self.riemann(qL, fL, qR, fR, zN, zN, (0.0, 1.0), m.hy)
         GN = Gy.clone()
         GS = Gy[idx.roll(1, dims=0).reshape(-1)].clone()
-        if m.bc_y == "wall":
-            iy = torch.arange(C) // nxc
-            top = iy == nyc - 1
-            bot = iy == 0
+        iy = torch.arange(C) // nxc
+        top = iy == nyc - 1
+        bot = iy == 0
+        north = {"wall": "wall", "halo": "halo", "wall_halo": "halo", "halo_wall": "wall"}.get(m.bc_y)
+        south = {"wall": "wall", "halo": "halo", "wall_halo": "wall", "halo_wall": "halo"}.get(m.bc_y)
+        if north == "wall":
             gq, gf = self._ghost(tr["N"], (0.0, 1.0), zN)
             GN_w = self.riemann(tr["N"]["q"], tr["N"]["f"], gq, gf, zN, zN, (0.0, 1.0), m.hy)
             GN[top] = GN_w[top]
+        if south == "wall":
             gq, gf = self._ghost(tr["S"], (0.0, -1.0), zS)
             GS_w = self.riemann(gq, gf, tr["S"]["q"], tr["S"]["f"], zS, zS, (0.0, 1.0), m.hy)
             GS[bot] = GS_w[bot]
+        if north == "halo":
+            hq, hf = halo["N"]
+            GN[top] = self.riemann(tr["N"]["q"][top], tr["N"]["f"][top], hq, hf, zN[top], zN[top], (0.0, 1.0), m.hy)
+        if south == "halo":
+            hq, hf = halo["S"]
+            GS[bot] = self.riemann(hq, hf, tr["S"]["q"][bot], tr["S"]["f"][bot], zS[bot], zS[bot], (0.0, 1.0), m.hy)
         return FE, FW, GN, GS
 
     # ------------------------------------------------------------ corrector
-    def corrector(self, u, dt, tavg):
+    def corrector(self, u, dt, tavg, halo=None):
         """u^{n+1} = u + dt (volume - face + Sbar), weak form with GL collocation."""
         b = self.b
         m = self.m
         w, D, p0, p1 = b.w, b.D, b.phi0, b.phi1
         tr = self.face_traces(tavg)
-        FE, FW, GN, GS = self.face_fluxes(tr)
+        FE, FW, GN, GS = self.face_fluxes(tr, halo)
         # volume: (1/hx) sum_p (w_p/w_i) D[p,i] Fbar[p,j] + (1/hy) sum_p (w_p/w_j) D[p,j] Gbar[i,p]
         Vx = (w[:, None] * D) / w[None, :]   # Vx[p, i] = w_p D[p,i] / w_i
         vol = (torch.einsum("pi,cvjp->cvji", Vx, tavg["Fbar"]) / m.hx

@@ -21,6 +21,9 @@ ADG_EUNSUPPORTED = 7
 
 ADG_BC_PERIODIC = 0
 ADG_BC_WALL = 1
+ADG_BC_EXCHANGE = 2
+ADG_BC_WALL_EXCHANGE = 3
+ADG_BC_EXCHANGE_WALL = 4
 ADG_SRC_NONE = 0
 ADG_SRC_STEADY = 1
 ADG_PREC_FP64 = 0
@@ -85,6 +88,9 @@ SIGNATURES = {
     "adg_tv_indicator": (_I, [_P, _I, _D, _D, _P, _P, _P, _P]),
     "adg_check_finite": (_I, [_P, _P]),
     "adg_step_adjoint": (_I, [_P, _D, _P, _P, _P, _P]),
+    "adg_get_boundary_traces": (_I, [_P, _P, _P, _P]),
+    "adg_set_halo_traces": (_I, [_P, _P, _P, _P]),
+    "adg_tv_flags": (_I, [_P, _P, _D, _D, _D, _D, _D, _P, _P]),
     "adg_batch_create": (_I, [ctypes.POINTER(_P), _I, ctypes.POINTER(_P)]),
     "adg_batch_step": (_I, [_P, ctypes.POINTER(_D), _I, _P]),
     "adg_batch_info": (_I, [_P, ctypes.POINTER(_I), _I]),

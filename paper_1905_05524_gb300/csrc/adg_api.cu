@@ -160,6 +160,7 @@ void free_mesh(adg_mesh* m) {
     cudaFree(m->flag);
     cudaFree(m->bgbuf);
     cudaFree(m->mixbuf);
+    cudaFree(m->halo);
     if (m->amr) adg::amr_free(m);
     delete m;
 }
@@ -282,8 +283,11 @@ int adg_create_mesh(const adg_mesh_desc* d, adg_mesh** out) {
     if (d->nx < 1 || d->ny < 1) return fail(ADG_EINVAL, "create_mesh: nx, ny must be >= 1");
     if ((long long)d->nx * d->ny > (1LL << 26)) return fail(ADG_EINVAL, "create_mesh: too many cells");
     if (!(d->Lx > 0.0) || !(d->Ly > 0.0)) return fail(ADG_EINVAL, "create_mesh: Lx, Ly must be > 0");
-    if (d->bc_x < 0 || d->bc_x > 1 || d->bc_y < 0 || d->bc_y > 1)
+    if (d->bc_x < 0 || d->bc_x > 1 || d->bc_y < 0 || d->bc_y > 4)
         return fail(ADG_EINVAL, "create_mesh: unknown boundary condition");
+    const bool exch = d->bc_y >= ADG_BC_EXCHANGE;
+    if (exch && (d->precision != ADG_PREC_FP64 || d->max_levels != 0))
+        return fail(ADG_EUNSUPPORTED, "create_mesh: strip exchange is built for uniform FP64 meshes");
     if (!(d->gamma > 1.0) || !(d->R > 0.0) || !(d->Pr > 0.0) || !(d->mu >= 0.0))
         return fail(ADG_EINVAL, "create_mesh: invalid gas constants");
     if (d->source != ADG_SRC_NONE && d->source != ADG_SRC_STEADY)
@@ -396,6 +400,16 @@ int adg_create_mesh(const adg_mesh_desc* d, adg_mesh** out) {
             free_mesh(m);
             return rc3;
         }
+    }
+    if (d->bc_y >= ADG_BC_EXCHANGE) {
+        const size_t hb = 2 * (size_t)d->nx * adg::kTraceComps * m->n * 8;
+        if (cudaMalloc(&m->halo, hb) != cudaSuccess || cudaMemset(m->halo, 0, hb) != cudaSuccess) {
+            cudaGetLastError();
+            free_mesh(m);
+            return fail(ADG_ENOMEM, "create_mesh: halo buffers");
+        }
+        m->bg.halo_s = m->halo;
+        m->bg.halo_n = m->halo + (size_t)d->nx * adg::kTraceComps * m->n;
     }
     m->bg.pbar_node = m->bgbuf;
     m->bg.rhobar_node = m->bgbuf + (size_t)d->ny * m->n;
@@ -574,6 +588,7 @@ int adg_step_adjoint(adg_mesh* m, double dt, const double* u_n, const double* la
     if (m->d.precision != ADG_PREC_FP64) return fail(ADG_EUNSUPPORTED, "step_adjoint: FP64 meshes only");
     if (m->N > 5) return fail(ADG_EUNSUPPORTED, "step_adjoint: built for degree <= 5");
     if (m->amr) return fail(ADG_EUNSUPPORTED, "step_adjoint: uniform meshes only");
+    if (m->d.bc_y >= ADG_BC_EXCHANGE) return fail(ADG_EUNSUPPORTED, "step_adjoint: strip exchange not supported");
     if (lam_n == lam_np1 || lam_n == u_n) return fail(ADG_EINVAL, "step_adjoint: lam_n must not alias the inputs");
     if (int rc = set_device(m)) return rc;
     const size_t tr = (size_t)m->cells * 4 * adg::kTraceComps * m->n;
@@ -588,6 +603,50 @@ int adg_step_adjoint(adg_mesh* m, double dt, const double* u_n, const double* la
     e = adg::launch_step_adjoint_fp64(m->N, u_n, lam_np1, lam_n, m->trace, m->trace_bar, m->cells, dt, m->B, m->P,
                                       m->bg, stream);
     if (e) return cuda_fail((cudaError_t)e, "step_adjoint: adjoint kernels");
+    return ADG_OK;
+}
+
+int adg_get_boundary_traces(adg_mesh* m, double* south, double* north, void* stream) {
+    if (!m) return fail(ADG_EINVAL, "get_boundary_traces: NULL mesh");
+    if (m->d.bc_y < ADG_BC_EXCHANGE) return fail(ADG_EINVAL, "get_boundary_traces: bc_y has no exchange side");
+    if (!m->predicted) return fail(ADG_ESTATE, "get_boundary_traces: call adg_predictor first");
+    if (int rc = set_device(m)) return rc;
+    const size_t TR = (size_t)adg::kTraceComps * m->n, nx = m->d.nx;
+    cudaStream_t s = (cudaStream_t)stream;
+    // record of face f of cell c starts at (c * 4 + f) * TR: strided gather of one row
+    if (south)
+        ADG_CK(cudaMemcpy2DAsync(south, TR * 8, m->trace + 3 * TR, 4 * TR * 8, TR * 8, nx, cudaMemcpyDeviceToDevice, s),
+               "get_boundary_traces: south");
+    if (north)
+        ADG_CK(cudaMemcpy2DAsync(north, TR * 8, m->trace + ((size_t)(m->d.ny - 1) * nx * 4 + 2) * TR, 4 * TR * 8,
+                                 TR * 8, nx, cudaMemcpyDeviceToDevice, s),
+               "get_boundary_traces: north");
+    return ADG_OK;
+}
+
+int adg_set_halo_traces(adg_mesh* m, const double* south, const double* north, void* stream) {
+    if (!m) return fail(ADG_EINVAL, "set_halo_traces: NULL mesh");
+    if (m->d.bc_y < ADG_BC_EXCHANGE) return fail(ADG_EINVAL, "set_halo_traces: bc_y has no exchange side");
+    if (int rc = set_device(m)) return rc;
+    const size_t bytes = (size_t)m->d.nx * adg::kTraceComps * m->n * 8;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (south) ADG_CK(cudaMemcpyAsync(m->halo, south, bytes, cudaMemcpyDeviceToDevice, s), "set_halo_traces: south");
+    if (north)
+        ADG_CK(cudaMemcpyAsync(m->halo + bytes / 8, north, bytes, cudaMemcpyDeviceToDevice, s), "set_halo_traces: north");
+    return ADG_OK;
+}
+
+int adg_tv_flags(adg_mesh* m, const double* tv, double count, double mean, double M2, double T_r, double T_c,
+                 int8_t* flags, void* stream) {
+    if (!m || !tv || !flags) return fail(ADG_EINVAL, "tv_flags: NULL argument");
+    if (!(count > 0.0) || !(M2 >= 0.0) || !(T_r > T_c)) return fail(ADG_EINVAL, "tv_flags: bad statistics");
+    if (int rc = set_device(m)) return rc;
+    const double trip[3] = {count, mean, M2};
+    ADG_CK(cudaMemcpyAsync(m->part, trip, sizeof(trip), cudaMemcpyHostToDevice, (cudaStream_t)stream), "tv_flags");
+    int e = adg::launch_tv_flags_given(tv, m->cells, m->part, T_r, T_c, flags, stream);
+    if (e) return cuda_fail((cudaError_t)e, "tv_flags launch");
+    // the host triple must outlive the copy
+    ADG_CK(cudaStreamSynchronize((cudaStream_t)stream), "tv_flags sync");
     return ADG_OK;
 }
 

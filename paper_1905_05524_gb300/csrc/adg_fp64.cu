@@ -102,8 +102,12 @@ k_corrector_fp64(double* __restrict__ u, const double* __restrict__ rvol,
     for (int idx = node; idx < 4 * n; idx += n2) {
         const int f = idx / n, m = idx - f * n;
         const bool xface = f < 2;
+        const bool top = f == 2 && iy == P.ny - 1, bot = f == 3 && iy == 0;
         const bool wall = xface ? (P.bc_x == ADG_BC_WALL && ((f == 0 && ix == P.nx - 1) || (f == 1 && ix == 0)))
-                                : (P.bc_y == ADG_BC_WALL && ((f == 2 && iy == P.ny - 1) || (f == 3 && iy == 0)));
+                                : ((P.bc_y == ADG_BC_WALL && (top || bot)) ||
+                                   (P.bc_y == ADG_BC_WALL_EXCHANGE && bot) || (P.bc_y == ADG_BC_EXCHANGE_WALL && top));
+        const bool halo = !xface && ((P.bc_y == ADG_BC_EXCHANGE && (top || bot)) ||
+                                     (P.bc_y == ADG_BC_WALL_EXCHANGE && top) || (P.bc_y == ADG_BC_EXCHANGE_WALL && bot));
         const double* own = trace + ((size_t)cell * 4 + f) * TR;
         double rec[kTraceComps];
 #pragma unroll
@@ -131,7 +135,8 @@ k_corrector_fp64(double* __restrict__ u, const double* __restrict__ rvol,
             else if (f == 1) { nb = iy * P.nx + (ix == 0 ? P.nx - 1 : ix - 1); nf = 0; }
             else if (f == 2) { nb = (iy + 1 == P.ny ? 0 : iy + 1) * P.nx + ix; nf = 3; }
             else { nb = (iy == 0 ? P.ny - 1 : iy - 1) * P.nx + ix; nf = 2; }
-            const double* ot = trace + ((size_t)nb * 4 + nf) * TR;
+            const double* ot = halo ? (f == 2 ? bg.halo_n : bg.halo_s) + (size_t)ix * TR
+                                    : trace + ((size_t)nb * 4 + nf) * TR;
 #pragma unroll
             for (int v = 0; v < 4; ++v) {
                 qn[v] = ot[v * n + m];

@@ -45,6 +45,8 @@ struct Background {
     const double* rhobar_node;  // [ny][n]
     const double* pbar_face;    // [ny+1]   at face heights y0 + f hy
     const double* rhobar_face;  // [ny+1]
+    const double* halo_s = nullptr;  // strip decomposition: north traces of the strip below [nx][17][n]
+    const double* halo_n = nullptr;  // south traces of the strip above
 };
 
 // Trace record per face node: q-bar(4), normal flux(4), qx-bar(4), qy-bar(4), s(1)
@@ -120,6 +122,8 @@ int launch_tv_cells_mixed(int N, const double* u, double* tv, int cells, int var
 // multi-block deterministic statistics: `part` is scratch of 3 * tv_stats_partials(cells) doubles
 int tv_stats_chunk(int cells);
 int tv_stats_partials(int cells);
+int launch_tv_flags_given(const double* tv, int cells, const double* part1, double T_r, double T_c,
+                          int8_t* flags, void* stream);
 int launch_tv_stats_multi(const double* tv, int cells, double T_r, double T_c, double* part,
                           double* stats_dev, int8_t* flags, void* stream);
 int launch_max_speed(int N, const double* u, double* partial, int cells, const Basis& B,

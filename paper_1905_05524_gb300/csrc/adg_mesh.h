@@ -39,6 +39,7 @@ struct adg_mesh {
     int* nbr = nullptr;           // [leaves][4 faces][5]: type, id0, id1, id2, sub-face
     double* bgl = nullptr;        // [leaves][n][2] node background, then [leaves][2][2] N/S faces
     double hmin = 0.0;            // smallest leaf size (dt rule)
+    double* halo = nullptr;       // strip decomposition: [2][nx][17][n] south, north halo traces
 };
 
 namespace adg {

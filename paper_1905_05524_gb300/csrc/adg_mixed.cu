@@ -20,6 +20,7 @@
 // Without gravity the background is zero and q' is the full state.
 #include <cuda_runtime.h>
 
+#include "adg_convert.cuh"
 #include "adg_internal.h"
 
 namespace adg {
@@ -130,7 +131,8 @@ __device__ __forceinline__ void predictor_mixed_body(const double* __restrict__ 
     const float x = P.x0 + (ix + B.xi[i]) * P.hx;
     const float z = P.y0 + (iy + B.xi[j]) * P.hy;
     (void)x;
-    const float rb = (float)bg.rb[row], Eb = (float)bg.Eb[row], pb = bg.pb[row];
+    const double rb64 = bg.rb[row], Eb64 = bg.Eb[row];
+    const float rb = f64_to_f32(rb64), Eb = f64_to_f32(Eb64), pb = bg.pb[row];
     const float dzr = bg.dzr[row], dzE = bg.dzE[row];
     const int rm = j * NP + i, tm = i * NP + j;  // this node in row-major / transposed rows
 
@@ -140,10 +142,10 @@ __device__ __forceinline__ void predictor_mixed_body(const double* __restrict__ 
     // FP64 perturbation split, then FP32 from here on
     float up[4];
     const double* uc = u + (size_t)cell * SL;
-    up[0] = (float)(uc[node] - bg.rb[row]);
-    up[1] = (float)uc[n2 + node];
-    up[2] = (float)uc[2 * n2 + node];
-    up[3] = (float)(uc[3 * n2 + node] - bg.Eb[row]);
+    up[0] = f64_to_f32(uc[node] - rb64);
+    up[1] = f64_to_f32(uc[n2 + node]);
+    up[2] = f64_to_f32(uc[2 * n2 + node]);
+    up[3] = f64_to_f32(uc[3 * n2 + node] - Eb64);
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
         Q[v * RS + rm] = up[v];
@@ -318,7 +320,7 @@ __device__ __forceinline__ void predictor_mixed_body(const double* __restrict__ 
         // background at the face node: nodal values on x-faces, extrapolated on y-faces
         float rbf, pbf;
         if (xface) {
-            rbf = (float)bg.rb[iy * n + m];
+            rbf = f64_to_f32(bg.rb[iy * n + m]);
             pbf = bg.pb[iy * n + m];
         } else {
             const float* fb = bg.face + ((size_t)iy * 2 + (f == 2 ? 0 : 1)) * kFaceBg;
@@ -411,8 +413,8 @@ __device__ __forceinline__ void corrector_mixed_body(double* __restrict__ u, con
             float z, rb, Eb, pb;
             if (xface) {
                 z = P.y0 + (iy + B.xi[m]) * P.hy;
-                rb = (float)bg.rb[iy * n + m];
-                Eb = (float)bg.Eb[iy * n + m];
+                rb = f64_to_f32(bg.rb[iy * n + m]);
+                Eb = f64_to_f32(bg.Eb[iy * n + m]);
                 pb = bg.pb[iy * n + m];
             } else {
                 z = P.y0 + (iy + (f == 2 ? 1 : 0)) * P.hy;
@@ -451,7 +453,7 @@ __device__ __forceinline__ void corrector_mixed_body(double* __restrict__ u, con
         const float face = (B.lift1[i] * Fst[cl][0][v][j] - B.lift0[i] * Fst[cl][1][v][j]) * P.inv_hx +
                            (B.lift1[j] * Fst[cl][2][v][i] - B.lift0[j] * Fst[cl][3][v][i]) * P.inv_hy;
         const float du = rc[v * n2 + node] - face;
-        uc[v * n2 + node] = fma(dt, (double)du, uc[v * n2 + node]);  // FP64 accumulation
+        uc[v * n2 + node] = fma(dt, f32_to_f64(du), uc[v * n2 + node]);  // FP64 accumulation
     }
 }
 

@@ -10,6 +10,7 @@
 // combined in a fixed binary tree, so the result is deterministic.
 #include <cuda_runtime.h>
 
+#include "adg_convert.cuh"
 #include "adg_internal.h"
 #include "adg_physics.cuh"
 
@@ -90,12 +91,13 @@ k_tv_cells_mixed(const double* __restrict__ u, double* __restrict__ tv, int cell
     const int iy = cell / P.nx;
     const int row = iy * n + j;
     const double* uc = u + (size_t)cell * SL;
-    const float rp = (float)(uc[node] - bg.rb[row]);
+    const double rb64 = bg.rb[row];
+    const float rp = f64_to_f32(uc[node] - rb64);
     float f;
     if (var == ADG_TV_THETA) {
-        const float Ep = (float)(uc[3 * n2 + node] - bg.Eb[row]);
-        const float mx = (float)uc[n2 + node], my = (float)uc[2 * n2 + node];
-        const float rb = (float)bg.rb[row];
+        const float Ep = f64_to_f32(uc[3 * n2 + node] - bg.Eb[row]);
+        const float mx = f64_to_f32(uc[n2 + node]), my = f64_to_f32(uc[2 * n2 + node]);
+        const float rb = f64_to_f32(rb64);
         const float rho = rb + rp;
         const float z = P.y0 + (iy + B.xi[j]) * P.hy;
         const float pp = P.gm1 * (Ep - 0.5f * (mx * mx + my * my) / rho - P.g * z * rp);
@@ -117,16 +119,16 @@ k_tv_cells_mixed(const double* __restrict__ u, double* __restrict__ tv, int cell
     red[cl][node] = B.w[i] * B.w[j] * (fabsf(fx) + fabsf(fy));
     __syncthreads();
     if (node == 0 && active) {
-        double s = 0.0;
-        for (int a = 0; a < n2; ++a) s += (double)red[cl][a];
-        tv[cell] = s;
+        float s = 0.f;  // FP32 sum of n^2 positive terms: relative error ~n^2 * 6e-8
+        for (int a = 0; a < n2; ++a) s += red[cl][a];
+        tv[cell] = f32_to_f64(s);
     }
 }
 
 // Multi-block statistics.  Block b owns the contiguous chunk of cells
 // [b*chunk, min((b+1)*chunk, cells)); it forms the chunk's count, mean and M2
 // by an exact two-pass reduction in a fixed tree and writes the triple to
-// part[b] (scratch).  k_tv_final then combines the partial triples with Chan
+// part[b] (scratch).  k_tv_flags then combines the partial triples with Chan
 // et al.'s pairwise update in a fixed binary tree (deterministic) and writes
 // the flags.
 constexpr int kPartThreads = 256;
@@ -170,46 +172,51 @@ k_tv_partials(const double* __restrict__ tv, int cells, int chunk, double* __res
 
 constexpr int kMaxPartials = 1024;
 
-__global__ void __launch_bounds__(kMaxPartials)
-k_tv_final(const double* __restrict__ part, int nparts, const double* __restrict__ tv, int cells,
+// Every block combines all partial triples in the same fixed binary tree
+// (so every block obtains bitwise the same mean and sigma), block 0 writes
+// them out, and each block flags its own chunk of cells.  Spreading the FP64
+// flag comparisons over many SMs matters on a part with 2 FP64 FMA per clock
+// per SM.
+__global__ void __launch_bounds__(kPartThreads)
+k_tv_flags(const double* __restrict__ part, int nparts, const double* __restrict__ tv, int cells, int chunk,
            double T_r, double T_c, double* __restrict__ stats, int8_t* __restrict__ flags) {
     __shared__ double sc[kMaxPartials], smean[kMaxPartials], sm2[kMaxPartials];
-    __shared__ double mu_sig[2];
     const int t = threadIdx.x;
-    sc[t] = t < nparts ? part[3 * t] : 0.0;
-    smean[t] = t < nparts ? part[3 * t + 1] : 0.0;
-    sm2[t] = t < nparts ? part[3 * t + 2] : 0.0;
+    for (int a = t; a < kMaxPartials; a += kPartThreads) {
+        sc[a] = a < nparts ? part[3 * a] : 0.0;
+        smean[a] = a < nparts ? part[3 * a + 1] : 0.0;
+        sm2[a] = a < nparts ? part[3 * a + 2] : 0.0;
+    }
     __syncthreads();
-    for (int stride = kMaxPartials / 2; stride > 0; stride >>= 1) {
-        if (t < stride) {
-            const double na = sc[t], nb = sc[t + stride];
+    int top = 1;
+    while (top < nparts) top <<= 1;
+    for (int stride = top / 2; stride > 0; stride >>= 1) {
+        for (int a = t; a < stride; a += kPartThreads) {
+            const double na = sc[a], nb = sc[a + stride];
             const double nn = na + nb;
             if (nb > 0.0) {
-                const double d = smean[t + stride] - smean[t];
-                smean[t] = smean[t] + d * (nb / nn);
-                sm2[t] = sm2[t] + sm2[t + stride] + d * d * (na * nb / nn);
-                sc[t] = nn;
+                const double d = smean[a + stride] - smean[a];
+                smean[a] = smean[a] + d * (nb / nn);
+                sm2[a] = sm2[a] + sm2[a + stride] + d * d * (na * nb / nn);
+                sc[a] = nn;
             }
         }
         __syncthreads();
     }
-    if (t == 0) {
-        mu_sig[0] = smean[0];
-        mu_sig[1] = sc[0] > 0.0 ? sqrt(sm2[0] / sc[0]) : 0.0;
-        if (stats) {
-            stats[0] = mu_sig[0];
-            stats[1] = mu_sig[1];
-        }
+    const double mu = smean[0];
+    const double sig = sc[0] > 0.0 ? sqrt(sm2[0] / sc[0]) : 0.0;
+    if (blockIdx.x == 0 && t == 0 && stats) {
+        stats[0] = mu;
+        stats[1] = sig;
     }
-    __syncthreads();
-    if (flags) {
-        const double thr_r = mu_sig[0] + T_r * mu_sig[1];
-        const double thr_c = mu_sig[0] + T_c * mu_sig[1];
-        const bool flat = mu_sig[1] <= 1e-12 * fabs(mu_sig[0]);  // reading F1: keep all
-        for (int c = t; c < cells; c += kMaxPartials) {
-            const double x = tv[c];
-            flags[c] = flat ? (int8_t)0 : x >= thr_r ? (int8_t)1 : (x < thr_c ? (int8_t)-1 : (int8_t)0);
-        }
+    if (!flags) return;
+    const double thr_r = mu + T_r * sig;
+    const double thr_c = mu + T_c * sig;
+    const bool flat = sig <= 1e-12 * fabs(mu);  // reading F1: keep all
+    const int lo = blockIdx.x * chunk, hi = min(cells, lo + chunk);
+    for (int c = lo + t; c < hi; c += kPartThreads) {
+        const double x = tv[c];
+        flags[c] = flat ? (int8_t)0 : x >= thr_r ? (int8_t)1 : (x < thr_c ? (int8_t)-1 : (int8_t)0);
     }
 }
 
@@ -424,7 +431,15 @@ int launch_tv_stats_multi(const double* tv, int cells, double T_r, double T_c, d
     k_tv_partials<<<np, kPartThreads, 0, s>>>(tv, cells, chunk, part);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return (int)e;
-    k_tv_final<<<1, kMaxPartials, 0, s>>>(part, np, tv, cells, T_r, T_c, stats_dev, flags);
+    k_tv_flags<<<np, kPartThreads, 0, s>>>(part, np, tv, cells, chunk, T_r, T_c, stats_dev, flags);
+    return (int)cudaGetLastError();
+}
+
+int launch_tv_flags_given(const double* tv, int cells, const double* part1, double T_r, double T_c,
+                          int8_t* flags, void* stream) {
+    const int chunk = tv_stats_chunk(cells);
+    const int nb = (cells + chunk - 1) / chunk;
+    k_tv_flags<<<nb, kPartThreads, 0, (cudaStream_t)stream>>>(part1, 1, tv, cells, chunk, T_r, T_c, nullptr, flags);
     return (int)cudaGetLastError();
 }
 
