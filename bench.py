@@ -83,7 +83,7 @@ def predictor_flops_per_cell(n):
 # DRAM bytes (read + write) of one predictor launch on this workload, from one
 # ncu capture of the kernel as it stands (profiles/k_predictor_*_warm_bubble_n5_81x81.md);
 # set to None whenever the kernel changes after the capture.
-PREDICTOR_TRAFFIC = {"fp64": None, "mixed": None}
+PREDICTOR_TRAFFIC = {"fp64": 7810304 + 1280, "mixed": 7645952 + 0}
 
 
 def measure_fma_peaks():
@@ -343,6 +343,104 @@ def run_batch(dev, nsteps=20, instances=64):
             "l2": "state (%.0f MB) exceeds L2" % (dof * 8 / 1e6) if dof * 8 > 129e6 else "not flushed"}
 
 
+def prolong_to_level(u, leaves, degree, target_level, nx0, ny0):
+    """Nodal values of every leaf evaluated at the nodes of the uniform mesh
+    of `target_level` (numpy; measurement only).  Returns [ny, nx, 4, n, n]."""
+    import numpy as np
+    n = degree + 1
+    xi, _ = np.polynomial.legendre.leggauss(n)
+    xi = 0.5 * (xi + 1.0)
+
+    def lag(x):
+        return np.array([[np.prod([(xx - xi[m]) / (xi[a] - xi[m]) for m in range(n) if m != a])
+                          for a in range(n)] for xx in x])
+    NX, NY = nx0 * 3 ** target_level, ny0 * 3 ** target_level
+    out = np.zeros((NY, NX, 4, n, n))
+    for k, (lv, ix, iy) in enumerate(leaves):
+        f = 3 ** (target_level - lv)
+        for b in range(f):
+            Ly = lag((b + xi) / f)
+            for a in range(f):
+                Lx = lag((a + xi) / f)
+                out[iy * f + b, ix * f + a] = np.einsum("jr,iq,vrq->vji", Ly, Lx, u[k])
+    return out
+
+
+def run_amr(args, dev):
+    """Config 3: two-bubble convection on a 3:1 tree, degree 5, 27x27 base, two
+    refinement levels (to 243x243), mu = 0.001, T_r = 2.5, T_c = -0.5, regrid
+    every 10 steps; all leaves of all levels advanced by one predictor and one
+    corrector launch per step (FP64).  Compared with the uniform 243x243 run."""
+    import numpy as np
+    import torch
+    from paper_1905_05524_gb300 import _lib as L
+    from paper_1905_05524_gb300.solver import Mesh, atmosphere_config
+    cfg = atmosphere_config(degree=DEGREE, nx=27, ny=27, mu=0.001, device=dev.index)
+    cfg.max_levels = 2
+    m = Mesh(cfg)
+    for _ in range(2):   # initial mesh: init -> TV -> refine, twice
+        m.init_scenario(L.ADG_SCEN_TWO_BUBBLES)
+        _, fl, _ = m.tv_indicator(L.ADG_TV_THETA, 2.5, -0.5)
+        m.adapt(torch.where(fl > 0, 1, 0).to(torch.int8))
+    m.init_scenario(L.ADG_SCEN_TWO_BUBBLES)
+    dt = m.stable_dt(CFL)
+    steps, every = args.amr_steps, 10
+    dof_updates = 0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    t_steps = 0.0
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    leaf_hist = []
+    for s0 in range(0, steps, every):
+        k = min(every, steps - s0)
+        ev0.record()
+        m.step(dt, k)
+        ev1.record()
+        ev1.synchronize()
+        t_steps += ev0.elapsed_time(ev1) * 1e-3
+        dof_updates += m.leaves * (DEGREE + 1) ** 2 * 4 * k
+        leaf_hist.append(m.leaves)
+        _, fl, _ = m.tv_indicator(L.ADG_TV_THETA, 2.5, -0.5)
+        m.adapt(fl)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    leaves = m.leaf_info()
+    ua = m.get_state().cpu().numpy()
+    # uniform fine reference (same dt)
+    cfu = atmosphere_config(degree=DEGREE, nx=243, ny=243, mu=0.001, device=dev.index)
+    mu_ = Mesh(cfu)
+    mu_.init_scenario(L.ADG_SCEN_TWO_BUBBLES)
+    ev0.record()
+    mu_.step(dt, steps)
+    ev1.record()
+    ev1.synchronize()
+    t_uni = ev0.elapsed_time(ev1) * 1e-3
+    uu = mu_.get_state().cpu().numpy().reshape(243, 243, 4, DEGREE + 1, DEGREE + 1)
+    fine = prolong_to_level(ua, leaves, DEGREE, 2, 27, 27)
+    tha = theta_prime_np(fine.reshape(-1, 4, DEGREE + 1, DEGREE + 1), cfu)
+    thu = theta_prime_np(uu.reshape(-1, 4, DEGREE + 1, DEGREE + 1), cfu)
+    n = DEGREE + 1
+    _, w = np.polynomial.legendre.leggauss(n)
+    w = 0.5 * w
+    area = (1000.0 / 243) ** 2
+    W = (w[:, None] * w[None, :])[None] * area
+    l2d = float(np.sqrt((W * (tha - thu) ** 2).sum()))
+    l2t = float(np.sqrt((W * (thu + cfu.theta0) ** 2).sum()))
+    levels = [c[0] for c in leaves]
+    return {
+        "metric": METRIC + " (config 3: two-bubble AMR)", "value": dof_updates / t_steps, "unit": UNIT,
+        "dtype": "f64", "steps": steps, "regrid_every": every,
+        "value_including_regrid": dof_updates / wall,
+        "leaves_final": len(leaves), "leaves_per_level": [levels.count(l) for l in range(3)],
+        "leaves_mean": float(np.mean(leaf_hist)),
+        "uniform_243x243": {"value": 243 * 243 * n * n * 4 * steps / t_uni, "unit": UNIT, "seconds": t_uni},
+        "amr_vs_uniform_theta": {"l2_difference": l2d, "relative_to_l2_theta": l2d / l2t,
+                                 "paper_reference": "L2 1.87, relative 2.6e-6 (order 6, 9x9 base, Sec. 4.2)"},
+        "config": {"workload": "two bubbles (Eq. 14), degree 5, 27x27 base, max 2 levels, mu=0.001, CFL 0.25 "
+                               "on the initial mesh, T_r=2.5, T_c=-0.5, regrid every 10 steps"},
+    }
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -353,6 +451,10 @@ def run_ours(args):
         dist.init_process_group("nccl")
     dev = torch.device("cuda", local if ws > 1 else 0)
     torch.cuda.set_device(dev)
+    if args.workload == "amr":
+        if rank == 0:
+            print(json.dumps(run_amr(args, dev)), flush=True)
+        return 0
     n = DEGREE + 1
     cells = NX * NY
     dof = cells * n * n * 4
@@ -446,6 +548,9 @@ def main():
     ap.add_argument("--no-compare", action="store_true", help="skip the FP64 comparison form")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-instance batched form")
     ap.add_argument("--batch-steps", type=int, default=20)
+    ap.add_argument("--workload", default="bubble", choices=["bubble", "amr"],
+                    help="amr: the two-bubble adaptive-mesh run of config 3 (separate JSON line)")
+    ap.add_argument("--amr-steps", type=int, default=1000)
     ap.add_argument("--cpu-steps", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-peaks", action="store_true", help="skip the FMA peak probe (profiling runs)")
