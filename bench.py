@@ -406,8 +406,10 @@ def run_amr(args, dev):
     wall = time.perf_counter() - t0
     leaves = m.leaf_info()
     ua = m.get_state().cpu().numpy()
-    # uniform fine reference (same dt)
-    cfu = atmosphere_config(degree=DEGREE, nx=243, ny=243, mu=0.001, device=dev.index)
+    # uniform reference at the finest level present (same dt, same smallest cell)
+    lmax = max(c[0] for c in leaves)
+    side = 27 * 3 ** lmax
+    cfu = atmosphere_config(degree=DEGREE, nx=side, ny=side, mu=0.001, device=dev.index)
     mu_ = Mesh(cfu)
     mu_.init_scenario(L.ADG_SCEN_TWO_BUBBLES)
     ev0.record()
@@ -415,14 +417,14 @@ def run_amr(args, dev):
     ev1.record()
     ev1.synchronize()
     t_uni = ev0.elapsed_time(ev1) * 1e-3
-    uu = mu_.get_state().cpu().numpy().reshape(243, 243, 4, DEGREE + 1, DEGREE + 1)
-    fine = prolong_to_level(ua, leaves, DEGREE, 2, 27, 27)
+    uu = mu_.get_state().cpu().numpy().reshape(side, side, 4, DEGREE + 1, DEGREE + 1)
+    fine = prolong_to_level(ua, leaves, DEGREE, lmax, 27, 27)
     tha = theta_prime_np(fine.reshape(-1, 4, DEGREE + 1, DEGREE + 1), cfu)
     thu = theta_prime_np(uu.reshape(-1, 4, DEGREE + 1, DEGREE + 1), cfu)
     n = DEGREE + 1
     _, w = np.polynomial.legendre.leggauss(n)
     w = 0.5 * w
-    area = (1000.0 / 243) ** 2
+    area = (1000.0 / side) ** 2
     W = (w[:, None] * w[None, :])[None] * area
     l2d = float(np.sqrt((W * (tha - thu) ** 2).sum()))
     l2t = float(np.sqrt((W * (thu + cfu.theta0) ** 2).sum()))
@@ -433,12 +435,94 @@ def run_amr(args, dev):
         "value_including_regrid": dof_updates / wall,
         "leaves_final": len(leaves), "leaves_per_level": [levels.count(l) for l in range(3)],
         "leaves_mean": float(np.mean(leaf_hist)),
-        "uniform_243x243": {"value": 243 * 243 * n * n * 4 * steps / t_uni, "unit": UNIT, "seconds": t_uni},
+        "uniform_reference": {"cells": side * side, "value": side * side * n * n * 4 * steps / t_uni, "unit": UNIT,
+                              "seconds": t_uni},
+        "uniform_equivalent_value": side * side * n * n * 4 * steps / t_steps,
         "amr_vs_uniform_theta": {"l2_difference": l2d, "relative_to_l2_theta": l2d / l2t,
                                  "paper_reference": "L2 1.87, relative 2.6e-6 (order 6, 9x9 base, Sec. 4.2)"},
         "config": {"workload": "two bubbles (Eq. 14), degree 5, 27x27 base, max 2 levels, mu=0.001, CFL 0.25 "
                                "on the initial mesh, T_r=2.5, T_c=-0.5, regrid every 10 steps"},
     }
+
+
+def run_sweep(args, dev):
+    """Config 5 (first part): periodic steady manufactured problem on 243x243
+    cells at degrees 2..7, FP64 and mixed, `sweep_steps` steps each
+    (predictor + corrector), CUDA-event timed; the state exceeds L2 from
+    degree 4 on (smaller ones are flushed before each step)."""
+    import torch
+    from paper_1905_05524_gb300 import _lib as L
+    from paper_1905_05524_gb300.solver import Mesh, steady_manufactured_config
+    out = []
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    for N in range(2, 8):
+        row = {"degree": N}
+        for prec_name, prec in (("fp64", L.ADG_PREC_FP64), ("mixed", L.ADG_PREC_MIXED)):
+            cfg = steady_manufactured_config(degree=N, nx=243, ny=243, precision=prec, device=dev.index)
+            cfg.Lx = cfg.Ly = 10.0
+            m = Mesh(cfg)
+            m.init_scenario(L.ADG_SCEN_STEADY)
+            dt = m.stable_dt(0.5)
+            m.step(dt, 2)
+            tot = 0.0
+            steps = args.sweep_steps if prec_name == "mixed" else max(2, args.sweep_steps // 5)
+            for _ in range(steps):
+                flush.fill_(1.0)
+                ev[0].record()
+                m.step(dt)
+                ev[1].record()
+                ev[1].synchronize()
+                tot += ev[0].elapsed_time(ev[1])
+            dof = 243 * 243 * (N + 1) ** 2 * 4
+            row[prec_name] = {"value": dof * steps / (tot * 1e-3), "ms_per_step": tot / steps, "steps": steps}
+            m.close()
+        row["mixed_over_fp64"] = row["mixed"]["value"] / row["fp64"]["value"]
+        out.append(row)
+    return {"metric": METRIC + " (config 5: degree sweep, 243x243 periodic)", "unit": UNIT,
+            "step": "predictor + corrector", "sweep": out}
+
+
+def run_adjoint(args, dev):
+    """Config 4: gradient of the probe misfit through 200 FP64 steps (degree 3,
+    27x27) with checkpoints every 20: forward + checkpointed backward."""
+    import torch
+    from paper_1905_05524_gb300 import _lib as L
+    from paper_1905_05524_gb300 import inputs
+    from paper_1905_05524_gb300.adjoint import objective_from_theta, probe_operator, node_heights
+    from paper_1905_05524_gb300.solver import Mesh, atmosphere_config
+    cfg = atmosphere_config(degree=3, nx=27, ny=27, device=dev.index)
+    m = Mesh(cfg)
+    m.init_scenario(L.ADG_SCEN_COSINE, A=0.5, a=250.0, xc=500.0, zc=350.0)
+    dt = m.stable_dt(CFL)
+    import numpy as np
+    n = 4
+    xi, _ = np.polynomial.legendre.leggauss(n)
+    xi = torch.tensor(0.5 * (xi + 1.0), dtype=torch.float64, device=dev)
+    ix = torch.arange(729, device=dev) % 27
+    X = (ix[:, None].double() + xi[None, :]) * (1000.0 / 27)
+    X = X[:, None, :].expand(-1, n, n)
+    Z = node_heights(cfg, dev)
+    r = torch.sqrt((X - 500.0) ** 2 + (Z - 350.0) ** 2)
+    th0 = torch.where(r <= 250.0, 0.25 * (1 + torch.cos(np.pi * r / 250.0)), torch.zeros_like(r))
+    cells, W = probe_operator(cfg, inputs.probes(64, seed=1), dev)
+    target = torch.from_numpy(inputs.normal_values(64, seed=0, scale=0.1)).to(dev)
+    x = th0.clone().requires_grad_(True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    J = objective_from_theta(x, m, dt, 200, 20, cells, W, target)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    (g,) = torch.autograd.grad(J, x)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    dof = 729 * n * n * 4
+    return {"metric": METRIC + " (config 4: adjoint)", "unit": UNIT, "dtype": "f64",
+            "forward_seconds": t1 - t0, "backward_seconds": t2 - t1,
+            "forward_value": dof * 200 / (t1 - t0), "gradient_value": dof * 200 / (t2 - t0),
+            "J": float(J.detach()), "grad_norm": float(g.norm()),
+            "note": "gradient_value counts the 200 forward steps once over forward + checkpointed "
+                    "backward (recompute of 180 states + 200 adjoint steps); Python launch overhead included"}
 
 
 def run_ours(args):
@@ -451,9 +535,10 @@ def run_ours(args):
         dist.init_process_group("nccl")
     dev = torch.device("cuda", local if ws > 1 else 0)
     torch.cuda.set_device(dev)
-    if args.workload == "amr":
+    if args.workload != "bubble":
         if rank == 0:
-            print(json.dumps(run_amr(args, dev)), flush=True)
+            fn = {"amr": run_amr, "sweep": run_sweep, "adjoint": run_adjoint}[args.workload]
+            print(json.dumps(fn(args, dev)), flush=True)
         return 0
     n = DEGREE + 1
     cells = NX * NY
@@ -548,8 +633,10 @@ def main():
     ap.add_argument("--no-compare", action="store_true", help="skip the FP64 comparison form")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-instance batched form")
     ap.add_argument("--batch-steps", type=int, default=20)
-    ap.add_argument("--workload", default="bubble", choices=["bubble", "amr"],
-                    help="amr: the two-bubble adaptive-mesh run of config 3 (separate JSON line)")
+    ap.add_argument("--workload", default="bubble", choices=["bubble", "amr", "sweep", "adjoint"],
+                    help="extra workloads, each printing its own JSON line: amr (config 3), "
+                         "sweep (config 5 degree sweep), adjoint (config 4 gradient)")
+    ap.add_argument("--sweep-steps", type=int, default=20)
     ap.add_argument("--amr-steps", type=int, default=1000)
     ap.add_argument("--cpu-steps", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
