@@ -200,9 +200,10 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
         "steps": steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec / steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic (analytic initial state)", "config": workload_config("fp64 CPU oracle"),
+        "data": "synthetic (analytic initial state)", "config": workload_config(args.precision),
         "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": f"{steps} full steps of the 81x81 degree-5 workload on the host cores"},
+                         "sample": f"{steps} full steps (FP64 oracle, predictor+corrector+TV) of the "
+                                   f"81x81 degree-5 workload on the host cores"},
         "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
