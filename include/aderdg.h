@@ -115,6 +115,10 @@ size_t adg_state_count(const adg_mesh* m);
 int adg_set_state(adg_mesh* m, const double* u, size_t count, int on_device, void* stream);
 int adg_get_state(adg_mesh* m, double* u, size_t count, int on_device, void* stream);
 
+/* Borrowed device pointer to the mesh's state (layout above, adg_state_count
+ * doubles); valid until adg_destroy_mesh or adg_adapt.  NULL for a NULL mesh. */
+double* adg_state_ptr(adg_mesh* m);
+
 /* Simulation time carried by the mesh (advanced by adg_step). */
 int adg_set_time(adg_mesh* m, double t);
 double adg_get_time(const adg_mesh* m);

@@ -78,6 +78,7 @@ SIGNATURES = {
     "adg_state_count": (_S, [_P]),
     "adg_set_state": (_I, [_P, _P, _S, _I, _P]),
     "adg_get_state": (_I, [_P, _P, _S, _I, _P]),
+    "adg_state_ptr": (_P, [_P]),
     "adg_set_time": (_I, [_P, _D]),
     "adg_get_time": (_D, [_P]),
     "adg_init_scenario": (_I, [_P, ctypes.POINTER(Scenario), _P]),

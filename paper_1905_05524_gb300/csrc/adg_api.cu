@@ -450,6 +450,8 @@ int adg_get_state(adg_mesh* m, double* u, size_t count, int on_device, void* str
     return ADG_OK;
 }
 
+double* adg_state_ptr(adg_mesh* m) { return m ? m->u : nullptr; }
+
 int adg_set_time(adg_mesh* m, double t) {
     if (!m) return fail(ADG_EINVAL, "set_time: NULL mesh");
     m->t = t;

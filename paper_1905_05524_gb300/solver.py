@@ -70,6 +70,13 @@ def atmosphere_config(degree=5, nx=81, ny=81, mu=0.01, precision=L.ADG_PREC_FP64
                       precision=precision, device=device)
 
 
+def _device_view(ptr, numel, device):
+    """A float64 tensor aliasing `numel` doubles of device memory at `ptr`."""
+    class _Iface:
+        __cuda_array_interface__ = {"shape": (numel,), "typestr": "<f8", "data": (ptr, False), "version": 3}
+    return torch.as_tensor(_Iface(), device=device)
+
+
 def _stream_ptr(stream=None):
     s = stream if stream is not None else torch.cuda.current_stream()
     return ctypes.c_void_p(s.cuda_stream)
@@ -117,6 +124,14 @@ class Mesh:
         L.check(self._lib.adg_get_state(self.h, ctypes.c_void_p(out.data_ptr()), self.count,
                                         1 if out.is_cuda else 0, _stream_ptr(stream)))
         return out
+
+    def state_view(self):
+        """Zero-copy torch view of the mesh's device state (borrowed: valid until
+        close() or adapt())."""
+        ptr = self._lib.adg_state_ptr(self.h)
+        n = self.cfg.n
+        size = self.leaves * 4 * n * n
+        return _device_view(ptr, size, self.device).view(self.state_shape)
 
     @property
     def time(self):

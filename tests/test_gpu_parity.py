@@ -273,3 +273,13 @@ def test_check_finite():
     with pytest.raises(L.AdgError) as e:
         m.check_finite()
     assert e.value.code == L.ADG_ENONFINITE
+
+
+def test_state_ptr_view_aliases_state():
+    cfg = steady_manufactured_config(degree=2, nx=3, ny=3)
+    m = Mesh(cfg)
+    m.init_scenario(L.ADG_SCEN_STEADY)
+    view = m.state_view()
+    assert torch.equal(view, m.get_state())
+    m.step(0.01)
+    assert torch.equal(view, m.get_state())
