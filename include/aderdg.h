@@ -57,6 +57,8 @@ extern "C" {
 
 #define ADG_SRC_NONE 0
 #define ADG_SRC_STEADY 1    /* steady manufactured source rho = 1 + a sin(2pi(x+y)/L) */
+#define ADG_SRC_PAPER 2     /* the paper's time-dependent manufactured solution (Sec. 4.1,
+                               Eq. 8) with phi = 2pi/L (x+y) - 2pi t; FP64 uniform meshes */
 
 #define ADG_PREC_FP64 0     /* every operation in FP64                          */
 #define ADG_PREC_MIXED 1    /* FP32 predictor on perturbation variables; FP64
@@ -93,6 +95,7 @@ typedef struct adg_mesh_desc {
 #define ADG_SCEN_COSINE 1       /* cosine bubble theta' (Eq. 15, r/a reading)    */
 #define ADG_SCEN_TWO_BUBBLES 2  /* Gaussian-tail warm + cold bubbles (Eqs. 12, 14) */
 #define ADG_SCEN_BACKGROUND 3   /* unperturbed hydrostatic atmosphere (Eq. 6)     */
+#define ADG_SCEN_PAPER 4        /* the Eq. 8 field at the mesh's time             */
 
 typedef struct adg_scenario {
     int kind;              /* ADG_SCEN_*                                         */

@@ -26,6 +26,7 @@ ADG_BC_WALL_EXCHANGE = 3
 ADG_BC_EXCHANGE_WALL = 4
 ADG_SRC_NONE = 0
 ADG_SRC_STEADY = 1
+ADG_SRC_PAPER = 2
 ADG_PREC_FP64 = 0
 ADG_PREC_MIXED = 1
 ADG_TV_RHO = 0
@@ -34,6 +35,7 @@ ADG_SCEN_STEADY = 0
 ADG_SCEN_COSINE = 1
 ADG_SCEN_TWO_BUBBLES = 2
 ADG_SCEN_BACKGROUND = 3
+ADG_SCEN_PAPER = 4
 ADG_NOALLOC_SCRATCH_BYTES = 32 << 20
 
 STATUS_NAMES = {1: "ADG_EINVAL", 2: "ADG_ENOMEM", 3: "ADG_ECUDA", 4: "ADG_ENONFINITE",

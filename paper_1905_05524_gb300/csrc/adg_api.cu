@@ -290,10 +290,13 @@ int adg_create_mesh(const adg_mesh_desc* d, adg_mesh** out) {
         return fail(ADG_EUNSUPPORTED, "create_mesh: strip exchange is built for uniform FP64 meshes");
     if (!(d->gamma > 1.0) || !(d->R > 0.0) || !(d->Pr > 0.0) || !(d->mu >= 0.0))
         return fail(ADG_EINVAL, "create_mesh: invalid gas constants");
-    if (d->source != ADG_SRC_NONE && d->source != ADG_SRC_STEADY)
+    if (d->source != ADG_SRC_NONE && d->source != ADG_SRC_STEADY && d->source != ADG_SRC_PAPER)
         return fail(ADG_EINVAL, "create_mesh: unknown source");
-    if (d->source == ADG_SRC_STEADY && !(d->src_L > 0.0))
-        return fail(ADG_EINVAL, "create_mesh: steady source needs src_L > 0");
+    if (d->source != ADG_SRC_NONE && !(d->src_L > 0.0))
+        return fail(ADG_EINVAL, "create_mesh: a manufactured source needs src_L > 0");
+    if (d->source == ADG_SRC_PAPER && (d->precision != ADG_PREC_FP64 || d->max_levels != 0 || d->gravity))
+        return fail(ADG_EUNSUPPORTED, "create_mesh: the time-dependent source is built for uniform FP64 meshes "
+                                      "without gravity");
     if (d->precision != ADG_PREC_FP64 && d->precision != ADG_PREC_MIXED)
         return fail(ADG_EINVAL, "create_mesh: unknown precision");
     if (d->gravity && !(d->theta0 > 0.0 && d->p0 > 0.0))
@@ -462,12 +465,15 @@ double adg_get_time(const adg_mesh* m) { return m ? m->t : 0.0; }
 
 int adg_init_scenario(adg_mesh* m, const adg_scenario* s, void* stream) {
     if (!m || !s) return fail(ADG_EINVAL, "init_scenario: NULL argument");
-    if (s->kind < ADG_SCEN_STEADY || s->kind > ADG_SCEN_BACKGROUND)
+    if (s->kind < ADG_SCEN_STEADY || s->kind > ADG_SCEN_PAPER)
         return fail(ADG_EINVAL, "init_scenario: unknown scenario");
-    if (s->kind != ADG_SCEN_STEADY && !m->d.gravity)
+    const bool manufactured = s->kind == ADG_SCEN_STEADY || s->kind == ADG_SCEN_PAPER;
+    if (!manufactured && !m->d.gravity)
         return fail(ADG_EINVAL, "init_scenario: bubble scenarios need gravity");
     if (s->kind == ADG_SCEN_STEADY && m->d.source != ADG_SRC_STEADY)
         return fail(ADG_EINVAL, "init_scenario: steady field needs the steady source");
+    if (s->kind == ADG_SCEN_PAPER && m->d.source != ADG_SRC_PAPER)
+        return fail(ADG_EINVAL, "init_scenario: the Eq. 8 field needs the time-dependent source");
     if (s->kind == ADG_SCEN_COSINE && !(s->a > 0.0))
         return fail(ADG_EINVAL, "init_scenario: cosine bubble radius must be > 0");
     if (int rc = set_device(m)) return rc;
@@ -591,6 +597,8 @@ int adg_step_adjoint(adg_mesh* m, double dt, const double* u_n, const double* la
     if (m->N > 5) return fail(ADG_EUNSUPPORTED, "step_adjoint: built for degree <= 5");
     if (m->amr) return fail(ADG_EUNSUPPORTED, "step_adjoint: uniform meshes only");
     if (m->d.bc_y >= ADG_BC_EXCHANGE) return fail(ADG_EUNSUPPORTED, "step_adjoint: strip exchange not supported");
+    if (m->d.source == ADG_SRC_PAPER)
+        return fail(ADG_EUNSUPPORTED, "step_adjoint: time-dependent source not supported");
     if (lam_n == lam_np1 || lam_n == u_n) return fail(ADG_EINVAL, "step_adjoint: lam_n must not alias the inputs");
     if (int rc = set_device(m)) return rc;
     const size_t tr = (size_t)m->cells * 4 * adg::kTraceComps * m->n;

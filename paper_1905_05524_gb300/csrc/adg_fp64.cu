@@ -38,22 +38,22 @@ struct Fp64Cfg {
     static constexpr size_t smem_pred = (size_t)cpb * 3 * n * 4 * n * n * sizeof(double);
 };
 
-template <int N, int CPB>
+template <int N, int CPB, bool TSRC>
 __global__ void __launch_bounds__(CPB*(N + 1) * (N + 1))
 k_predictor_fp64(const double* __restrict__ u, double* __restrict__ rvol,
                  double* __restrict__ trace, int cells, double dt, double t,
                  const Basis B, const Phys P, const Background bg) {
     constexpr int n = N + 1, n2 = n * n;
     extern __shared__ double sm[];
-    (void)t;
     const int cl = threadIdx.x / n2;
     const int j = (threadIdx.x - cl * n2) / n;
     const int cell_raw = blockIdx.x * CPB + cl;
     const bool active = cell_raw < cells;
     const int cell = active ? cell_raw : cells - 1;
     const int ix = cell % P.nx, iy = cell / P.nx;
-    predictor_fp64_body<N, CPB>(u, rvol, trace, cell, active, dt, B, P, P.x0 + ix * P.hx, P.y0 + iy * P.hy,
-                                bg.pbar_node[iy * n + j], bg.rhobar_node[iy * n + j], sm);
+    predictor_fp64_body<N, CPB, TSRC>(u, rvol, trace, cell, active, dt, B, P, P.x0 + ix * P.hx,
+                                      P.y0 + iy * P.hy, bg.pbar_node[iy * n + j], bg.rhobar_node[iy * n + j],
+                                      sm, t);
 }
 
 // Slip-wall ghost of face f (0 E, 1 W, 2 N, 3 S) from the interior trace
@@ -167,7 +167,7 @@ static int launch_pred(const double* u, double* rvol, double* trace, int cells, 
                        double t, const Basis& B, const Phys& P, const Background& bg,
                        cudaStream_t s) {
     using C = Fp64Cfg<N>;
-    auto kern = k_predictor_fp64<N, C::cpb>;
+    auto kern = P.source == ADG_SRC_PAPER ? k_predictor_fp64<N, C::cpb, true> : k_predictor_fp64<N, C::cpb, false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)C::smem_pred);
     if (e != cudaSuccess) return (int)e;

@@ -9,12 +9,15 @@ namespace adg {
 // Predictor body for one cell per group of n^2 threads (CPB groups per
 // block).  The cell's geometry arrives as its lower-left corner (xorg, yorg),
 // the cell sizes in P (hx, hy and the penalty eta_x, eta_y) and the
-// background pressure/density at this thread's node height.
-template <int N, int CPB>
+// background pressure/density at this thread's node height.  TSRC selects
+// the time-dependent manufactured source (evaluated at t + xi_k dt for time
+// node k); it is a separate instantiation so that the source-free kernel's
+// register allocation is not shaped by the source's arithmetic.
+template <int N, int CPB, bool TSRC = false>
 __device__ __forceinline__ void predictor_fp64_body(const double* __restrict__ u, double* __restrict__ rvol,
                                                     double* __restrict__ trace, int cell, bool active, double dt,
                                                     const Basis& B, const Phys& P, double xorg, double yorg,
-                                                    double pbar, double rhobar, double* sm) {
+                                                    double pbar, double rhobar, double* sm, double t = 0.0) {
     constexpr int n = N + 1, n2 = n * n, SL = 4 * n2;
     const int cl = threadIdx.x / n2;
     const int node = threadIdx.x - cl * n2;
@@ -34,6 +37,14 @@ __device__ __forceinline__ void predictor_fp64_body(const double* __restrict__ u
     }
     double Sm[4] = {0.0, 0.0, 0.0, 0.0};
     if (P.source == ADG_SRC_STEADY) steady_source(x, z, P, Sm);
+    auto src_k = [&](int k, double S[4]) {
+        if constexpr (TSRC) {
+            paper_source(x, z, t + B.xi[k] * dt, P, S);
+        } else {
+#pragma unroll
+            for (int v = 0; v < 4; ++v) S[v] = Sm[v];
+        }
+    };
     __syncthreads();
 
     // gradients of q_k at this node and the point-wise fluxes; F, G to smem
@@ -80,10 +91,30 @@ __device__ __forceinline__ void predictor_fp64_body(const double* __restrict__ u
         __syncthreads();
 #pragma unroll
         for (int v = 0; v < 4; ++v) R0[v] = f.S[v] + Sm[v] + divergence(0, v);
+        if constexpr (!TSRC) {
 #pragma unroll
-        for (int l = 0; l < n; ++l) {
+            for (int l = 0; l < n; ++l) {
 #pragma unroll
-            for (int v = 0; v < 4; ++v) Q[l * SL + v * n2 + node] = uu[v] + dt * (B.Kw1[l] * R0[v]);
+                for (int v = 0; v < 4; ++v) Q[l * SL + v * n2 + node] = uu[v] + dt * (B.Kw1[l] * R0[v]);
+            }
+        } else {  // the residual differs between time nodes by the source only
+            double acc[n][4];
+#pragma unroll
+            for (int l = 0; l < n; ++l)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[l][v] = B.Kw1[l] * R0[v];
+            for (int k = 0; k < n; ++k) {
+                double S[4];
+                src_k(k, S);
+#pragma unroll
+                for (int l = 0; l < n; ++l)
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) acc[l][v] += B.Kw[l][k] * S[v];
+            }
+#pragma unroll
+            for (int l = 0; l < n; ++l)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) Q[l * SL + v * n2 + node] = uu[v] + dt * acc[l][v];
         }
         __syncthreads();
     }
@@ -96,11 +127,13 @@ __device__ __forceinline__ void predictor_fp64_body(const double* __restrict__ u
             double q[4], qx[4], qy[4];
             Flux4 f;
             eval_node(Q + k * SL, q, qx, qy, f);
+            double Sk[4];
+            src_k(k, Sk);
 #pragma unroll
             for (int v = 0; v < 4; ++v) {
                 Fs[k * SL + v * n2 + node] = f.F[v];
                 Gs[k * SL + v * n2 + node] = f.G[v];
-                R[k][v] = f.S[v] + Sm[v];
+                R[k][v] = f.S[v] + Sk[v];
             }
         }
         __syncthreads();
@@ -132,12 +165,14 @@ __device__ __forceinline__ void predictor_fp64_body(const double* __restrict__ u
         Flux4 f;
         eval_node(Q + k * SL, q, qx, qy, f);
         const double wk = B.w[k];
+        double Sk[4];
+        src_k(k, Sk);
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
             qb[v] += wk * q[v];
             Fb[v] += wk * f.F[v];
             Gb[v] += wk * f.G[v];
-            Sb[v] += wk * (f.S[v] + Sm[v]);
+            Sb[v] += wk * (f.S[v] + Sk[v]);
             qxb[v] += wk * qx[v];
             qyb[v] += wk * qy[v];
         }

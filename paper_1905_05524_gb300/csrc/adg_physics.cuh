@@ -264,3 +264,85 @@ __device__ __forceinline__ void wave_speed_adj(const double q[4], double z, bool
 }
 
 }  // namespace adg
+
+namespace adg {
+
+// ---------------------------------------------------------------------------
+// The paper's manufactured solution (Sec. 4.1, Eq. 8) as a source term:
+// p = cos(phi)/10 + 1/gamma, rho = sin(phi)/2 + 1, v = (1,1) sin(phi)/4 with
+// phi = k (x + y) - 2 pi t, k = 2 pi / L (pi/5 on the paper's [0,10]^2).  All
+// fields depend on phi only, so dF/dx = k dF/dphi, dQ/dt = -2 pi dQ/dphi, and
+// S = dQ/dt + dF/dx + dG/dy is evaluated exactly by running the point-wise
+// flux on first-order dual numbers (value, d/dphi) -- forward-mode
+// differentiation of the same flux formula (gravity off).
+struct Dd {
+    double v, d;
+};
+__device__ __forceinline__ Dd operator+(Dd a, Dd b) { return {a.v + b.v, a.d + b.d}; }
+__device__ __forceinline__ Dd operator-(Dd a, Dd b) { return {a.v - b.v, a.d - b.d}; }
+__device__ __forceinline__ Dd operator-(Dd a) { return {-a.v, -a.d}; }
+__device__ __forceinline__ Dd operator*(Dd a, Dd b) { return {a.v * b.v, a.d * b.v + a.v * b.d}; }
+__device__ __forceinline__ Dd operator*(double s, Dd a) { return {s * a.v, s * a.d}; }
+__device__ __forceinline__ Dd operator/(Dd a, Dd b) { return {a.v / b.v, (a.d * b.v - a.v * b.d) / (b.v * b.v)}; }
+
+__device__ __forceinline__ void ns_flux_dual(const Dd q[4], const Dd qx[4], const Dd qy[4], const Phys& P, Dd F[4],
+                                             Dd G[4]) {
+    const Dd rho = q[0], mx = q[1], my = q[2], E = q[3];
+    const Dd u = mx / rho, v = my / rho;
+    const Dd p = P.gm1 * (E - 0.5 * (mx * u + my * v));
+    const Dd T = p / (P.R * rho);
+    const Dd ux = (qx[1] - u * qx[0]) / rho, uy = (qy[1] - u * qy[0]) / rho;
+    const Dd vx = (qx[2] - v * qx[0]) / rho, vy = (qy[2] - v * qy[0]) / rho;
+    const Dd kin = 0.5 * (u * u + v * v);
+    const Dd px = P.gm1 * (qx[3] - (u * qx[1] + v * qx[2]) + kin * qx[0]);
+    const Dd py = P.gm1 * (qy[3] - (u * qy[1] + v * qy[2]) + kin * qy[0]);
+    const Dd Tx = (px - P.R * (T * qx[0])) / (P.R * rho);
+    const Dd Ty = (py - P.R * (T * qy[0])) / (P.R * rho);
+    const Dd div = ux + vy;
+    const Dd sxx = P.mu * ((2.0 / 3.0) * div - 2.0 * ux);
+    const Dd syy = P.mu * ((2.0 / 3.0) * div - 2.0 * vy);
+    const Dd sxy = -P.mu * (uy + vx);
+    const Dd Ep = E + p;
+    F[0] = mx;
+    F[1] = mx * u + p + sxx;
+    F[2] = my * u + sxy;
+    F[3] = u * Ep + u * sxx + v * sxy - P.kappa * Tx;
+    G[0] = my;
+    G[1] = mx * v + sxy;
+    G[2] = my * v + p + syy;
+    G[3] = v * Ep + u * sxy + v * syy - P.kappa * Ty;
+}
+
+// Q(phi) and its first two phi-derivatives for the manufactured field
+__device__ __forceinline__ void paper_field(double phi, const Phys& P, double Q[4], double Q1[4], double Q2[4]) {
+    double s, c;
+    sincos(phi, &s, &c);
+    const double r = 1.0 + 0.5 * s, r1 = 0.5 * c, r2 = -0.5 * s;
+    const double u = 0.25 * s, u1 = 0.25 * c, u2 = -0.25 * s;  // v = u
+    const double p = 0.1 * c + 1.0 / P.gamma, p1 = -0.1 * s, p2 = -0.1 * c;
+    const double m = r * u, m1 = r1 * u + r * u1, m2 = r2 * u + 2.0 * r1 * u1 + r * u2;
+    const double E = p / P.gm1 + r * u * u;
+    const double E1 = p1 / P.gm1 + r1 * u * u + 2.0 * r * u * u1;
+    const double E2 = p2 / P.gm1 + r2 * u * u + 4.0 * r1 * u * u1 + 2.0 * r * (u1 * u1 + u * u2);
+    Q[0] = r; Q[1] = m; Q[2] = m; Q[3] = E;
+    Q1[0] = r1; Q1[1] = m1; Q1[2] = m1; Q1[3] = E1;
+    Q2[0] = r2; Q2[1] = m2; Q2[2] = m2; Q2[3] = E2;
+}
+
+__device__ __forceinline__ void paper_source(double x, double y, double t, const Phys& P, double S[4]) {
+    const double k = 2.0 * 3.14159265358979323846 / P.sL;
+    const double phi = k * (x + y) - 2.0 * 3.14159265358979323846 * t;
+    double Q[4], Q1[4], Q2[4];
+    paper_field(phi, P, Q, Q1, Q2);
+    Dd q[4], g[4], F[4], G[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+        q[v] = {Q[v], Q1[v]};
+        g[v] = {k * Q1[v], k * Q2[v]};
+    }
+    ns_flux_dual(q, g, g, P, F, G);
+#pragma unroll
+    for (int v = 0; v < 4; ++v) S[v] = -2.0 * 3.14159265358979323846 * Q1[v] + k * (F[v].d + G[v].d);
+}
+
+}  // namespace adg

@@ -251,6 +251,14 @@ __global__ void k_init(double* __restrict__ u, int cells, int kind, double A, do
         q[1] = rho * P.sU;
         q[2] = rho * P.sU;
         q[3] = P.sp / P.gm1 + 0.5 * rho * (2.0 * P.sU * P.sU);
+    } else if (kind == ADG_SCEN_PAPER) {  // Eq. 8 at t = 0
+        double s, c;
+        sincos(2.0 * 3.14159265358979323846 / P.sL * (x + z), &s, &c);
+        const double rho = 1.0 + 0.5 * s, vel = 0.25 * s;
+        q[0] = rho;
+        q[1] = rho * vel;
+        q[2] = rho * vel;
+        q[3] = (0.1 * c + 1.0 / P.gamma) / P.gm1 + rho * vel * vel;
     } else {
         double th = 0.0;
         if (kind == ADG_SCEN_COSINE) th = cosine_bubble(x, z, A, a, xc, zc);

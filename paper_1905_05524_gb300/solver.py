@@ -61,6 +61,12 @@ def steady_manufactured_config(degree=3, nx=9, ny=9, precision=L.ADG_PREC_FP64, 
                       precision=precision, device=device)
 
 
+def paper_manufactured_config(degree=3, nx=9, ny=9, mu=0.1, device=0):
+    """Periodic [0,10]^2, gamma 1.4, Pr 0.7, c_v 1, with the time-dependent
+    manufactured solution of Sec. 4.1 (Eq. 8) and its source (FP64)."""
+    return MeshConfig(degree=degree, nx=nx, ny=ny, mu=mu, source=L.ADG_SRC_PAPER, device=device)
+
+
 def atmosphere_config(degree=5, nx=81, ny=81, mu=0.01, precision=L.ADG_PREC_FP64, device=0):
     """[0,1000]^2 m with slip walls, gamma 1.4, Pr 0.71, R 287.058, p0 1e5 Pa,
     g 9.81, theta0 300 K isentropic background (Sec. 4.2)."""

@@ -13,7 +13,7 @@ def oracle_for(cfg):
                  bc_x=bc[cfg.bc_x], bc_y=bc[cfg.bc_y])
     P = ph.Params(N=cfg.degree, gamma=cfg.gamma, Pr=cfg.Pr, R=cfg.R, mu=cfg.mu,
                   gravity=bool(cfg.gravity), g=cfg.g, p0=cfg.p0, theta0=cfg.theta0,
-                  source={0: "none", 1: "steady"}[cfg.source])
+                  source={0: "none", 1: "steady", 2: "paper"}[cfg.source])
     return OSolver(mesh, P)
 
 
@@ -22,6 +22,11 @@ def steady_field(solver, cfg):
     import functools
     fn = functools.partial(ph.steady_manufactured, a=cfg.src_a, L=cfg.src_L, U=cfg.src_U, p=cfg.src_p)
     return solver.interpolate(lambda x, y, t, P: fn(x, y, t, P))
+
+
+def paper_field(solver, t=0.0):
+    """Oracle nodal interpolation of the Eq. 8 field at time t."""
+    return solver.interpolate(ph.paper_manufactured, t)
 
 
 def cosine_field(solver, A=0.5, a=250.0, xc=500.0, zc=350.0):
