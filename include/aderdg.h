@@ -155,6 +155,15 @@ int adg_stable_dt(adg_mesh* m, double cfl, double* dt, void* stream);
 int adg_tv_indicator(adg_mesh* m, int var, double T_r, double T_c,
                      double* tv, int8_t* flags, double* stats, void* stream);
 
+/* One step followed by the TV indicator of the new state: the results of
+ * adg_step then adg_tv_indicator with the same arguments (bitwise), but on
+ * uniform meshes the corrector kernel evaluates the per-cell TV on the state
+ * it has just written, saving one pass over the state and one launch
+ * (Sec. 3: the indicator is evaluated after every step).  Adaptive meshes
+ * run the two calls in turn.  Errors: those of both calls. */
+int adg_step_tv(adg_mesh* m, double dt, int var, double T_r, double T_c, double* tv, int8_t* flags,
+                double* stats, void* stream);
+
 /* Discrete adjoint of one adg_step (predictor + corrector, FP64) at the
  * state u_n: lam_n = lam_np1 + (d step / d u)^T lam_np1, i.e. the gradient of
  * J(u^{n+1}) with respect to u^n given lam_np1 = dJ/du^{n+1} (the adjoint of

@@ -89,6 +89,7 @@ SIGNATURES = {
     "adg_step": (_I, [_P, _D, _P]),
     "adg_stable_dt": (_I, [_P, _D, ctypes.POINTER(_D), _P]),
     "adg_tv_indicator": (_I, [_P, _I, _D, _D, _P, _P, _P, _P]),
+    "adg_step_tv": (_I, [_P, _D, _I, _D, _D, _P, _P, _P, _P]),
     "adg_check_finite": (_I, [_P, _P]),
     "adg_step_adjoint": (_I, [_P, _D, _P, _P, _P, _P]),
     "adg_get_boundary_traces": (_I, [_P, _P, _P, _P]),

@@ -177,9 +177,10 @@ static int size_buffers(adg_mesh* m, double* new_u) {
         m->u = new_u;
     }
     m->cells = L;
+    m->tv_prep_cells = -1;  // fresh `part`: statistics tree weights not prepared
     if (cudaMalloc(&m->rvol, cnt * 8) != cudaSuccess || cudaMalloc(&m->trace, tr * 8) != cudaSuccess ||
         cudaMalloc(&m->tv, (size_t)L * 8) != cudaSuccess ||
-        cudaMalloc(&m->part, 3 * 8 * (size_t)tv_stats_partials(L)) != cudaSuccess) {
+        cudaMalloc(&m->part, 8 * tv_stats_scratch_doubles()) != cudaSuccess) {
         cudaGetLastError();
         return fail(ADG_ENOMEM, "adaptive mesh: buffers");
     }

@@ -360,12 +360,17 @@ int adg_create_mesh(const adg_mesh_desc* d, adg_mesh** out) {
     const size_t nbg = 2 * (size_t)d->ny * m->n + 2 * (size_t)(d->ny + 1);
     if (cudaMalloc(&m->u, cnt * 8) != cudaSuccess || cudaMalloc(&m->rvol, cnt * 8) != cudaSuccess ||
         cudaMalloc(&m->trace, tr * 8) != cudaSuccess || cudaMalloc(&m->tv, (size_t)m->cells * 8) != cudaSuccess ||
-        cudaMalloc(&m->stats, 2 * 8) != cudaSuccess || cudaMalloc(&m->speed, (size_t)nb * 8) != cudaSuccess ||
-        cudaMalloc(&m->part, 3 * 8 * (size_t)adg::tv_stats_partials(m->cells)) != cudaSuccess ||
+        cudaMalloc(&m->stats, 4 * 8) != cudaSuccess || cudaMalloc(&m->speed, (size_t)nb * 8) != cudaSuccess ||
+        cudaMalloc(&m->part, 8 * adg::tv_stats_scratch_doubles()) != cudaSuccess ||
         cudaMalloc(&m->flag, sizeof(int)) != cudaSuccess || cudaMalloc(&m->bgbuf, nbg * 8) != cudaSuccess) {
         cudaGetLastError();
         free_mesh(m);
         return fail(ADG_ENOMEM, "create_mesh: device allocation failed");
+    }
+    if (cudaMemset(m->stats, 0, 4 * 8) != cudaSuccess) {  // mean, sigma, statistics ticket
+        cudaGetLastError();
+        free_mesh(m);
+        return fail(ADG_ECUDA, "create_mesh: workspace initialisation failed");
     }
     // hydrostatic background tables (Eq. 6, isentropic reading): zero without gravity
     std::vector<double> h(nbg, 0.0);
@@ -510,24 +515,30 @@ int adg_predictor(adg_mesh* m, double dt, void* stream) {
     return ADG_OK;
 }
 
-int adg_corrector(adg_mesh* m, double dt, void* stream) {
+// corrector of a uniform or adaptive mesh; epi (uniform meshes only): the TV
+// indicator of the updated state in the same kernel
+static int corrector_impl(adg_mesh* m, double dt, void* stream, const adg::TvEpilogue* epi) {
     if (!m) return fail(ADG_EINVAL, "corrector: NULL mesh");
     if (!m->predicted || m->pred_dt != dt)
         return fail(ADG_ESTATE, "corrector: needs a preceding predictor with the same dt");
     if (int rc = set_device(m)) return rc;
     if (m->amr) {
+        if (epi) return fail(ADG_EUNSUPPORTED, "corrector: no TV epilogue on adaptive meshes");
         if (int rc = adg::amr_corrector(m, dt, stream)) return rc;
         m->predicted = false;
         return ADG_OK;
     }
     int e = m->d.precision == ADG_PREC_FP64
-                ? adg::launch_corrector_fp64(m->N, m->u, m->rvol, m->trace, m->cells, dt, m->B, m->P, m->bg, stream)
+                ? adg::launch_corrector_fp64(m->N, m->u, m->rvol, m->trace, m->cells, dt, m->B, m->P, m->bg, stream,
+                                             epi)
                 : adg::launch_corrector_mixed(m->N, m->u, (const float*)m->rvol, (const float*)m->trace, m->cells,
-                                              dt, m->Bf, m->Pf, m->mbg, stream);
+                                              dt, m->Bf, m->Pf, m->mbg, stream, epi);
     if (e) return cuda_fail((cudaError_t)e, "corrector launch");
     m->predicted = false;
     return ADG_OK;
 }
+
+int adg_corrector(adg_mesh* m, double dt, void* stream) { return corrector_impl(m, dt, stream, nullptr); }
 
 int adg_step(adg_mesh* m, double dt, void* stream) {
     int rc = adg_predictor(m, dt, stream);
@@ -565,13 +576,36 @@ int adg_stable_dt(adg_mesh* m, double cfl, double* dt, void* stream) {
     return ADG_OK;
 }
 
-int adg_tv_indicator(adg_mesh* m, int var, double T_r, double T_c, double* tv, int8_t* flags,
-                     double* stats, void* stream) {
-    if (!m) return fail(ADG_EINVAL, "tv_indicator: NULL mesh");
+static int tv_check(const adg_mesh* m, int var, double T_r, double T_c) {
     if (var != ADG_TV_RHO && var != ADG_TV_THETA) return fail(ADG_EINVAL, "tv_indicator: unknown variable");
     if (var == ADG_TV_THETA && !m->d.gravity)
         return fail(ADG_EINVAL, "tv_indicator: theta needs the atmosphere constants (gravity on)");
     if (!(T_r > T_c)) return fail(ADG_EINVAL, "tv_indicator: needs T_r > T_c");
+    return ADG_OK;
+}
+
+// statistics over the TV values in tvbuf, flags, optional host copy of (mean, sigma)
+static int tv_finish(adg_mesh* m, double* tvbuf, double T_r, double T_c, int8_t* flags, double* stats,
+                     void* stream) {
+    int e;
+    if (m->tv_prep_cells != m->cells) {
+        e = adg::tv_stats_prepare(m->cells, m->part, stream);
+        if (e) return cuda_fail((cudaError_t)e, "tv_indicator prepare");
+        m->tv_prep_cells = m->cells;
+    }
+    e = adg::launch_tv_stats_multi(tvbuf, m->cells, T_r, T_c, m->part, m->stats, flags, stream);
+    if (e) return cuda_fail((cudaError_t)e, "tv_indicator stats");
+    if (stats) {
+        ADG_CK(cudaMemcpyAsync(stats, m->stats, 16, cudaMemcpyDeviceToHost, (cudaStream_t)stream), "tv stats copy");
+        ADG_CK(cudaStreamSynchronize((cudaStream_t)stream), "tv stats sync");
+    }
+    return ADG_OK;
+}
+
+int adg_tv_indicator(adg_mesh* m, int var, double T_r, double T_c, double* tv, int8_t* flags,
+                     double* stats, void* stream) {
+    if (!m) return fail(ADG_EINVAL, "tv_indicator: NULL mesh");
+    if (int rc = tv_check(m, var, T_r, T_c)) return rc;
     if (int rc = set_device(m)) return rc;
     double* tvbuf = tv ? tv : m->tv;
     int e = m->amr ? adg::amr_tv_cells(m, var, tvbuf, stream)
@@ -580,13 +614,26 @@ int adg_tv_indicator(adg_mesh* m, int var, double T_r, double T_c, double* tv, i
                 : adg::launch_tv_cells_mixed(m->N, m->u, tvbuf, m->cells, var, m->Bf, m->Pf, m->mbg,
                                              m->d.theta0, m->P.Rcp, stream);
     if (e) return cuda_fail((cudaError_t)e, "tv_indicator cells");
-    e = adg::launch_tv_stats_multi(tvbuf, m->cells, T_r, T_c, m->part, m->stats, flags, stream);
-    if (e) return cuda_fail((cudaError_t)e, "tv_indicator stats");
-    if (stats) {
-        ADG_CK(cudaMemcpyAsync(stats, m->stats, 16, cudaMemcpyDeviceToHost, (cudaStream_t)stream), "tv stats copy");
-        ADG_CK(cudaStreamSynchronize((cudaStream_t)stream), "tv stats sync");
+    return tv_finish(m, tvbuf, T_r, T_c, flags, stats, stream);
+}
+
+int adg_step_tv(adg_mesh* m, double dt, int var, double T_r, double T_c, double* tv, int8_t* flags,
+                double* stats, void* stream) {
+    if (!m) return fail(ADG_EINVAL, "step_tv: NULL mesh");
+    if (int rc = tv_check(m, var, T_r, T_c)) return rc;
+    if (m->amr) {  // adaptive meshes: the two calls in turn
+        if (int rc = adg_step(m, dt, stream)) return rc;
+        return adg_tv_indicator(m, var, T_r, T_c, tv, flags, stats, stream);
     }
-    return ADG_OK;
+    if (int rc = adg_predictor(m, dt, stream)) return rc;
+    adg::TvEpilogue epi;
+    epi.tv = tv ? tv : m->tv;
+    epi.var = var;
+    epi.theta0 = m->d.theta0;
+    epi.Rcp = m->P.Rcp;
+    if (int rc = corrector_impl(m, dt, stream, &epi)) return rc;
+    m->t += dt;
+    return tv_finish(m, epi.tv, T_r, T_c, flags, stats, stream);
 }
 
 int adg_step_adjoint(adg_mesh* m, double dt, const double* u_n, const double* lam_np1, double* lam_n,
@@ -651,11 +698,11 @@ int adg_tv_flags(adg_mesh* m, const double* tv, double count, double mean, doubl
     if (!m || !tv || !flags) return fail(ADG_EINVAL, "tv_flags: NULL argument");
     if (!(count > 0.0) || !(M2 >= 0.0) || !(T_r > T_c)) return fail(ADG_EINVAL, "tv_flags: bad statistics");
     if (int rc = set_device(m)) return rc;
-    const double trip[3] = {count, mean, M2};
-    ADG_CK(cudaMemcpyAsync(m->part, trip, sizeof(trip), cudaMemcpyHostToDevice, (cudaStream_t)stream), "tv_flags");
+    const double ms[2] = {mean, std::sqrt(M2 / count)};  // population sigma, as the device forms it
+    ADG_CK(cudaMemcpyAsync(m->part, ms, sizeof(ms), cudaMemcpyHostToDevice, (cudaStream_t)stream), "tv_flags");
     int e = adg::launch_tv_flags_given(tv, m->cells, m->part, T_r, T_c, flags, stream);
     if (e) return cuda_fail((cudaError_t)e, "tv_flags launch");
-    // the host triple must outlive the copy
+    // the host pair must outlive the copy
     ADG_CK(cudaStreamSynchronize((cudaStream_t)stream), "tv_flags sync");
     return ADG_OK;
 }

@@ -26,6 +26,7 @@
 #include "adg_internal.h"
 #include "adg_physics.cuh"
 #include "adg_fp64_body.cuh"
+#include "adg_tv_cell.cuh"
 
 namespace adg {
 
@@ -84,11 +85,13 @@ __device__ __forceinline__ void wall_ghost(const double* rec, int f, double z, d
     sG = wave_speed(qG, z, xdir, P);
 }
 
-template <int N, int CPB>
+// With TV the TV indicator of the updated state follows in the same kernel
+// (tv_cell, bitwise what k_tv_cells computes).
+template <int N, int CPB, bool TV>
 __global__ void __launch_bounds__(CPB*(N + 1) * (N + 1))
 k_corrector_fp64(double* __restrict__ u, const double* __restrict__ rvol,
                  const double* __restrict__ trace, int cells, double dt, const Basis B,
-                 const Phys P, const Background bg) {
+                 const Phys P, const Background bg, const TvEpilogue epi) {
     constexpr int n = N + 1, n2 = n * n, SL = 4 * n2, TR = kTraceComps * n;
     __shared__ double Fst[CPB][4][4][n];
     const int cl = threadIdx.x / n2;
@@ -151,14 +154,25 @@ k_corrector_fp64(double* __restrict__ u, const double* __restrict__ rvol,
         for (int v = 0; v < 4; ++v) Fst[cl][f][v][m] = out[v];
     }
     __syncthreads();
-    if (!active) return;
     double* uc = u + (size_t)cell * SL;
     const double* rc = rvol + (size_t)cell * SL;
+    double unew[4];
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
         const double face = (B.lift1[i] * Fst[cl][0][v][j] - B.lift0[i] * Fst[cl][1][v][j]) * P.inv_hx +
                             (B.lift1[j] * Fst[cl][2][v][i] - B.lift0[j] * Fst[cl][3][v][i]) * P.inv_hy;
-        uc[v * n2 + node] += dt * (rc[v * n2 + node] - face);
+        if (active) {  // padding threads touch no state
+            unew[v] = uc[v * n2 + node] + dt * (rc[v * n2 + node] - face);
+            uc[v * n2 + node] = unew[v];
+        } else {
+            unew[v] = 1.0;
+        }
+    }
+    if constexpr (TV) {
+        __shared__ double fs[CPB][n2], red[CPB][n2];
+        const double z = P.y0 + (iy + B.xi[j]) * P.hy;
+        const double f = epi.var == ADG_TV_THETA ? theta_of(unew, z, P) : unew[0];
+        tv_cell<N, double>(f, 0.0, node, i, j, B, P.inv_hx, P.inv_hy, fs[cl], red[cl], active, epi.tv + cell);
     }
 }
 
@@ -178,10 +192,15 @@ static int launch_pred(const double* u, double* rvol, double* trace, int cells, 
 
 template <int N>
 static int launch_corr(double* u, const double* rvol, const double* trace, int cells, double dt,
-                       const Basis& B, const Phys& P, const Background& bg, cudaStream_t s) {
+                       const Basis& B, const Phys& P, const Background& bg, const TvEpilogue* epi,
+                       cudaStream_t s) {
     using C = Fp64Cfg<N>;
     const int blocks = (cells + C::cpb - 1) / C::cpb;
-    k_corrector_fp64<N, C::cpb><<<blocks, C::threads, 0, s>>>(u, rvol, trace, cells, dt, B, P, bg);
+    if (epi)
+        k_corrector_fp64<N, C::cpb, true><<<blocks, C::threads, 0, s>>>(u, rvol, trace, cells, dt, B, P, bg, *epi);
+    else
+        k_corrector_fp64<N, C::cpb, false>
+            <<<blocks, C::threads, 0, s>>>(u, rvol, trace, cells, dt, B, P, bg, TvEpilogue{});
     return (int)cudaGetLastError();
 }
 
@@ -203,16 +222,16 @@ int launch_predictor_fp64(int N, const double* u, double* rvol, double* trace, i
 
 int launch_corrector_fp64(int N, double* u, const double* rvol, const double* trace, int cells,
                           double dt, const Basis& B, const Phys& P, const Background& bg,
-                          void* stream) {
+                          void* stream, const TvEpilogue* epi) {
     cudaStream_t s = (cudaStream_t)stream;
     switch (N) {
-        case 1: return launch_corr<1>(u, rvol, trace, cells, dt, B, P, bg, s);
-        case 2: return launch_corr<2>(u, rvol, trace, cells, dt, B, P, bg, s);
-        case 3: return launch_corr<3>(u, rvol, trace, cells, dt, B, P, bg, s);
-        case 4: return launch_corr<4>(u, rvol, trace, cells, dt, B, P, bg, s);
-        case 5: return launch_corr<5>(u, rvol, trace, cells, dt, B, P, bg, s);
-        case 6: return launch_corr<6>(u, rvol, trace, cells, dt, B, P, bg, s);
-        case 7: return launch_corr<7>(u, rvol, trace, cells, dt, B, P, bg, s);
+        case 1: return launch_corr<1>(u, rvol, trace, cells, dt, B, P, bg, epi, s);
+        case 2: return launch_corr<2>(u, rvol, trace, cells, dt, B, P, bg, epi, s);
+        case 3: return launch_corr<3>(u, rvol, trace, cells, dt, B, P, bg, epi, s);
+        case 4: return launch_corr<4>(u, rvol, trace, cells, dt, B, P, bg, epi, s);
+        case 5: return launch_corr<5>(u, rvol, trace, cells, dt, B, P, bg, epi, s);
+        case 6: return launch_corr<6>(u, rvol, trace, cells, dt, B, P, bg, epi, s);
+        case 7: return launch_corr<7>(u, rvol, trace, cells, dt, B, P, bg, epi, s);
     }
     return (int)cudaErrorInvalidValue;
 }

@@ -97,16 +97,25 @@ constexpr int kBatchCandidates = 3;  // tile-size candidates the autotuner times
 
 // Kernel launchers (adg_fp64.cu, adg_mixed.cu, adg_tv.cu).  They return a
 // cudaError_t value as int.
+// TV indicator evaluated by the corrector on the state it has just updated
+// (the corrector launchers take nullptr for none).
+struct TvEpilogue {
+    double* tv = nullptr;            // [cells] output
+    int var = 0;                     // ADG_TV_THETA or ADG_TV_RHO
+    double theta0 = 0.0, Rcp = 0.0;  // background potential temperature, R/c_p
+};
+
 int launch_predictor_fp64(int N, const double* u, double* rvol, double* trace, int cells,
                           double dt, double t, const Basis& B, const Phys& P,
                           const Background& bg, void* stream);
 int launch_corrector_fp64(int N, double* u, const double* rvol, const double* trace, int cells,
                           double dt, const Basis& B, const Phys& P, const Background& bg,
-                          void* stream);
+                          void* stream, const TvEpilogue* epi = nullptr);
 int launch_predictor_mixed(int N, const double* u, float* rvol, float* trace, int cells, double dt,
                            const BasisF& B, const PhysF& P, const MixedBg& bg, void* stream);
 int launch_corrector_mixed(int N, double* u, const float* rvol, const float* trace, int cells,
-                           double dt, const BasisF& B, const PhysF& P, const MixedBg& bg, void* stream);
+                           double dt, const BasisF& B, const PhysF& P, const MixedBg& bg, void* stream,
+                           const TvEpilogue* epi = nullptr);
 // phase 0: predictor, 1: corrector.  tiles == nullptr: query -- returns the
 // cells per block and writes the persistent grid size to *blocks_out; otherwise
 // launches with the grid size in *blocks_out.
@@ -119,10 +128,16 @@ int launch_tv_cells(int N, const double* u, double* tv, int cells, int var, cons
                     const Phys& P, void* stream);
 int launch_tv_cells_mixed(int N, const double* u, double* tv, int cells, int var, const BasisF& B,
                           const PhysF& P, const MixedBg& bg, double theta0, double Rcp, void* stream);
-// multi-block deterministic statistics: `part` is scratch of 3 * tv_stats_partials(cells) doubles
+// multi-block deterministic statistics: `part` is scratch of 3 * tv_stats_partials(cells) doubles;
+// stats_dev is [mean, sigma, ticket] (the ticket slot zeroed at allocation)
 int tv_stats_chunk(int cells);
 int tv_stats_partials(int cells);
-int launch_tv_flags_given(const double* tv, int cells, const double* part1, double T_r, double T_c,
+size_t tv_stats_scratch_doubles();  // size of `part`, whatever the cell count
+// Chan weights of the statistics tree for `cells` cells into `part` (host
+// division, one copy; synchronises `stream`); needed once per cell count
+int tv_stats_prepare(int cells, double* part, void* stream);
+// flags from (mean, sigma) held in device memory at stats_dev
+int launch_tv_flags_given(const double* tv, int cells, const double* stats_dev, double T_r, double T_c,
                           int8_t* flags, void* stream);
 int launch_tv_stats_multi(const double* tv, int cells, double T_r, double T_c, double* part,
                           double* stats_dev, int8_t* flags, void* stream);

@@ -17,8 +17,9 @@ struct adg_mesh {
     double* trace = nullptr;
     double* trace_bar = nullptr; // adjoint of the traces (allocated on first adg_step_adjoint)
     double* tv = nullptr;
-    double* stats = nullptr;     // device [2]
-    double* part = nullptr;      // device partial (count, mean, M2) triples of the TV statistics
+    double* stats = nullptr;     // device [4]: mean, sigma, ticket of the one-launch statistics
+    double* part = nullptr;      // device partial (count, mean, M2) triples of the TV statistics + tree weights
+    int tv_prep_cells = -1;      // cell count the tree weights in `part` were prepared for
     double* speed = nullptr;     // device partial maxima
     int speed_blocks = 0;
     int* flag = nullptr;         // device int

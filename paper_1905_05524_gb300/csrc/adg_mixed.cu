@@ -22,6 +22,7 @@
 
 #include "adg_convert.cuh"
 #include "adg_internal.h"
+#include "adg_tv_cell.cuh"
 
 namespace adg {
 
@@ -85,6 +86,75 @@ __device__ __forceinline__ float wave_speed_f(float rho, float mx, float my, flo
     return vn + c + 2.f * (xdir ? P.eta_x : P.eta_y) * P.lamv * rinv;
 }
 
+// ---------------------------------------------------------------------------
+// Packed FP32x2 arithmetic (sm_100 and later): one instruction works on two
+// FP32 lanes, each rounded like its scalar counterpart.  The predictor runs
+// the point-wise flux on two time slices at once and pairs adjacent row
+// entries in its contractions, halving the FP32 instruction count there.
+__device__ __forceinline__ float2 bc2(float s) { return make_float2(s, s); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 fnma2(float2 a, float2 b, float2 c) {  // c - a b
+    return __ffma2_rn(make_float2(-a.x, -a.y), b, c);
+}
+// approximate reciprocal (hardware rcp, relative error ~2^-23); rho is O(1)
+// and never subnormal, so flushing subnormals changes nothing
+__device__ __forceinline__ float rcp_fast(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+struct FluxF2 {
+    float2 F[4], G[4], S2;  // S2: the only non-zero physical source, -g rho' (z-momentum)
+};
+
+// ns_flux_pert on a pair of time slices at one node (the interior form:
+// gradients of T from the state, no wall heat flux).
+__device__ __forceinline__ void ns_flux_pert2(const float2 qp[4], const float2 gx[4], const float2 gy[4],
+                                              float z, float rb, float Eb, float pb, const PhysF& P,
+                                              FluxF2& o) {
+    const float2 rho = add2(bc2(rb), qp[0]);
+    const float2 mx = qp[1], my = qp[2];
+    const float2 rinv = make_float2(rcp_fast(rho.x), rcp_fast(rho.y));
+    const float2 u = mul2(mx, rinv), v = mul2(my, rinv);
+    const float gz = P.g * z;
+    // p' = (gamma-1) (E' - (mx u + my v)/2 - g z rho')
+    const float2 m2 = fma2(my, v, mul2(mx, u));
+    const float2 pp = mul2(bc2(P.gm1), fma2(bc2(-gz), qp[0], fma2(bc2(-0.5f), m2, qp[3])));
+    const float2 p = add2(bc2(pb), pp);
+    const float2 E = add2(bc2(Eb), qp[3]);
+    const float2 T = mul2(mul2(p, rinv), bc2(P.invR));
+    const float2 ux = mul2(fnma2(u, gx[0], gx[1]), rinv);
+    const float2 uy = mul2(fnma2(u, gy[0], gy[1]), rinv);
+    const float2 vx = mul2(fnma2(v, gx[0], gx[2]), rinv);
+    const float2 vy = mul2(fnma2(v, gy[0], gy[2]), rinv);
+    // kin - g z, the common factor of the density gradient in grad p
+    const float2 kg = fma2(bc2(0.5f), fma2(v, v, mul2(u, u)), bc2(-gz));
+    const float2 px = mul2(bc2(P.gm1), fma2(kg, gx[0], fnma2(v, gx[2], fnma2(u, gx[1], gx[3]))));
+    const float2 py = mul2(bc2(P.gm1),
+                           fnma2(rho, bc2(P.g), fma2(kg, gy[0], fnma2(v, gy[2], fnma2(u, gy[1], gy[3])))));
+    const float2 RT = mul2(bc2(P.R), T);
+    const float2 ri = mul2(rinv, bc2(P.invR));
+    const float2 Tx = mul2(fnma2(RT, gx[0], px), ri);
+    const float2 Ty = mul2(fnma2(RT, gy[0], py), ri);
+    const float2 div = add2(ux, vy);
+    const float2 sxx = mul2(bc2(P.mu), fma2(bc2(2.f / 3.f), div, mul2(bc2(-2.f), ux)));
+    const float2 syy = mul2(bc2(P.mu), fma2(bc2(2.f / 3.f), div, mul2(bc2(-2.f), vy)));
+    const float2 sxy = mul2(bc2(-P.mu), add2(uy, vx));
+    const float2 Ep = add2(E, p);
+    o.F[0] = mx;
+    o.F[1] = fma2(mx, u, add2(pp, sxx));
+    o.F[2] = fma2(my, u, sxy);
+    o.F[3] = fma2(bc2(-P.kappa), Tx, fma2(v, sxy, mul2(u, add2(Ep, sxx))));
+    o.G[0] = my;
+    o.G[1] = fma2(mx, v, sxy);
+    o.G[2] = fma2(my, v, add2(pp, syy));
+    o.G[3] = fma2(bc2(-P.kappa), Ty, fma2(u, sxy, mul2(v, add2(Ep, syy))));
+    o.S2 = mul2(bc2(-P.g), qp[0]);
+}
+
 template <int N, int CPB_ = 0>
 struct MixCfg {
     static constexpr int n = N + 1;
@@ -98,6 +168,10 @@ struct MixCfg {
     static constexpr int raw = 4 * n * 4 * n * np;
     static constexpr int stride = raw + ((16 - raw % 32) + 32) % 32;
     static constexpr size_t smem_pred = (size_t)cpb * stride * sizeof(float);
+    // minimum resident blocks asked of the register allocator (measured: at
+    // N = 5 the four blocks that shared memory admits beat three blocks
+    // without spills; elsewhere the allocator's own choice is best)
+    static constexpr int minb = (N == 5 && cpb == 4) ? 4 : 1;
 };
 
 // Predictor body for the tile of CPB cells starting at cell c0 (one thread per
@@ -168,29 +242,52 @@ __device__ __forceinline__ void predictor_mixed_body(const double* __restrict__ 
     }
     __syncthreads();
 
-    // D-contraction of the contiguous row starting at r with D row d
-    auto rowdot = [&](const float* r, const float* d) {
-        const float2* r2 = reinterpret_cast<const float2*>(r);
-        float s = 0.f;
+    // This node's rows of D, pre-scaled by 1/h, as packed pairs (the padded
+    // entry D[.][n] is zero).
+    constexpr int NH = NP / 2;
+    float2 dI[NH], dJ[NH];
 #pragma unroll
-        for (int p = 0; p < NP / 2; ++p) {
-            const float2 a = r2[p];
-            s = fmaf(d[2 * p], a.x, s);
-            s = fmaf(d[2 * p + 1], a.y, s);
-        }
-        return s;
+    for (int p = 0; p < NH; ++p) {
+        dI[p] = mul2(make_float2(B.D[i][2 * p], B.D[i][2 * p + 1]), bc2(P.inv_hx));
+        dJ[p] = mul2(make_float2(B.D[j][2 * p], B.D[j][2 * p + 1]), bc2(P.inv_hy));
+    }
+    // scaled D-contraction of the contiguous row starting at r: pairs of
+    // adjacent entries, then one horizontal add
+    auto rowdot = [&](const float* r, const float2(&d)[NH]) {
+        const float2* r2 = reinterpret_cast<const float2*>(r);
+        float2 s = mul2(d[0], r2[0]);
+#pragma unroll
+        for (int p = 1; p < NH; ++p) s = fma2(d[p], r2[p], s);
+        return s.x + s.y;
     };
+    // slice k alone (sweep 1: the iterate is constant in time)
     auto eval_node = [&](int k, float q[4], float gx[4], float gy[4], FluxF& f) {
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
             const float* Qv = Q + k * SLP + v * RS;
             q[v] = Qv[rm];
-            gx[v] = rowdot(Qv + j * NP, B.D[i]) * P.inv_hx;
-            gy[v] = rowdot(QT + k * SLP + v * RS + i * NP, B.D[j]) * P.inv_hy;
+            gx[v] = rowdot(Qv + j * NP, dI);
+            gy[v] = rowdot(QT + k * SLP + v * RS + i * NP, dJ);
         }
         gy[0] += dzr;
         gy[3] += dzE;
         ns_flux_pert(q, gx, gy, z, rb, Eb, pb, P, f);
+    };
+    // slices k0 and k1 together (k1 = k0 when n is odd and k0 is the last)
+    auto eval_pair = [&](int k0, int k1, float2 q[4], float2 gx[4], float2 gy[4], FluxF2& f) {
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const float* Q0 = Q + k0 * SLP + v * RS;
+            const float* Q1 = Q + k1 * SLP + v * RS;
+            const float* T0 = QT + k0 * SLP + v * RS + i * NP;
+            const float* T1 = QT + k1 * SLP + v * RS + i * NP;
+            q[v] = make_float2(Q0[rm], Q1[rm]);
+            gx[v] = make_float2(rowdot(Q0 + j * NP, dI), rowdot(Q1 + j * NP, dI));
+            gy[v] = make_float2(rowdot(T0, dJ), rowdot(T1, dJ));
+        }
+        gy[0] = add2(gy[0], bc2(dzr));
+        gy[3] = add2(gy[3], bc2(dzE));
+        ns_flux_pert2(q, gx, gy, z, rb, Eb, pb, P, f);
     };
     auto store_flux = [&](int k, const FluxF& f) {
 #pragma unroll
@@ -199,10 +296,20 @@ __device__ __forceinline__ void predictor_mixed_body(const double* __restrict__ 
             GT[k * SLP + v * RS + tm] = f.G[v];
         }
     };
+    auto store_flux_pair = [&](int k0, bool second, const FluxF2& f) {
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            Fs[k0 * SLP + v * RS + rm] = f.F[v].x;
+            GT[k0 * SLP + v * RS + tm] = f.G[v].x;
+            if (second) {
+                Fs[(k0 + 1) * SLP + v * RS + rm] = f.F[v].y;
+                GT[(k0 + 1) * SLP + v * RS + tm] = f.G[v].y;
+            }
+        }
+    };
+    // -dF/dx - dG/dy of slice k at this node
     auto divergence = [&](int k, int v) {
-        const float sx = rowdot(Fs + k * SLP + v * RS + j * NP, B.D[i]);
-        const float sy = rowdot(GT + k * SLP + v * RS + i * NP, B.D[j]);
-        return -(sx * P.inv_hx + sy * P.inv_hy);
+        return -(rowdot(Fs + k * SLP + v * RS + j * NP, dI) + rowdot(GT + k * SLP + v * RS + i * NP, dJ));
     };
     auto store_q = [&](int l, int v, float val) {
         Q[l * SLP + v * RS + rm] = val;
@@ -225,56 +332,78 @@ __device__ __forceinline__ void predictor_mixed_body(const double* __restrict__ 
         }
         __syncthreads();
     }
+    // sweeps 2..n on pairs of time slices; R2[h] holds slices 2h, 2h+1 (for
+    // odd n the last pair's second lane repeats slice n-1 and meets the zero
+    // padding of Kw and w)
+    constexpr int NPAIR = (n + 1) / 2;
 #pragma unroll 1
     for (int r = 1; r < n; ++r) {
-        float R[n][4];
+        float2 R2[NPAIR][4];
 #pragma unroll
-        for (int k = 0; k < n; ++k) {
-            float q[4], gx[4], gy[4];
-            FluxF f;
-            eval_node(k, q, gx, gy, f);
-            store_flux(k, f);
+        for (int h = 0; h < NPAIR; ++h) {
+            const int k0 = 2 * h, k1 = 2 * h + 1 < n ? 2 * h + 1 : 2 * h;
+            float2 q[4], gx[4], gy[4];
+            FluxF2 f;
+            eval_pair(k0, k1, q, gx, gy, f);
+            store_flux_pair(k0, 2 * h + 1 < n, f);
 #pragma unroll
-            for (int v = 0; v < 4; ++v) R[k][v] = f.S[v] + Sm[v];
+            for (int v = 0; v < 4; ++v) R2[h][v] = bc2(Sm[v]);
+            R2[h][2] = add2(R2[h][2], f.S2);
         }
         __syncthreads();
 #pragma unroll
-        for (int k = 0; k < n; ++k) {
+        for (int h = 0; h < NPAIR; ++h) {
+            const int k1 = 2 * h + 1 < n ? 2 * h + 1 : 2 * h;
 #pragma unroll
-            for (int v = 0; v < 4; ++v) R[k][v] += divergence(k, v);
+            for (int v = 0; v < 4; ++v)
+                R2[h][v] = add2(R2[h][v], make_float2(divergence(2 * h, v), divergence(k1, v)));
         }
 #pragma unroll
         for (int l = 0; l < n; ++l) {
 #pragma unroll
             for (int v = 0; v < 4; ++v) {
-                float acc = 0.f;
+                float2 acc = mul2(make_float2(B.Kw[l][0], B.Kw[l][1]), R2[0][v]);
 #pragma unroll
-                for (int k = 0; k < n; ++k) acc = fmaf(B.Kw[l][k], R[k][v], acc);
-                store_q(l, v, fmaf(dt, acc, up[v]));
+                for (int h = 1; h < NPAIR; ++h) acc = fma2(make_float2(B.Kw[l][2 * h], B.Kw[l][2 * h + 1]), R2[h][v], acc);
+                store_q(l, v, fmaf(dt, acc.x + acc.y, up[v]));
             }
         }
         __syncthreads();
     }
 
-    float qb[4], Fb[4], Gb[4], Sb[4], qxb[4], qyb[4];
+    // final evaluation on the converged iterate and the time averages
+    float2 qb2[4], Fb2[4], Gb2[4], qxb2[4], qyb2[4], Sz2;
 #pragma unroll
-    for (int v = 0; v < 4; ++v) qb[v] = Fb[v] = Gb[v] = Sb[v] = qxb[v] = qyb[v] = 0.f;
+    for (int v = 0; v < 4; ++v) qb2[v] = Fb2[v] = Gb2[v] = qxb2[v] = qyb2[v] = bc2(0.f);
+    Sz2 = bc2(0.f);
 #pragma unroll
-    for (int k = 0; k < n; ++k) {
-        float q[4], gx[4], gy[4];
-        FluxF f;
-        eval_node(k, q, gx, gy, f);
-        const float wk = B.w[k];
+    for (int h = 0; h < NPAIR; ++h) {
+        const int k0 = 2 * h, k1 = 2 * h + 1 < n ? 2 * h + 1 : 2 * h;
+        float2 q[4], gx[4], gy[4];
+        FluxF2 f;
+        eval_pair(k0, k1, q, gx, gy, f);
+        const float2 wk = make_float2(B.w[k0], B.w[2 * h + 1]);  // w[n] = 0 pads an odd n
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
-            qb[v] = fmaf(wk, q[v], qb[v]);
-            Fb[v] = fmaf(wk, f.F[v], Fb[v]);
-            Gb[v] = fmaf(wk, f.G[v], Gb[v]);
-            Sb[v] = fmaf(wk, f.S[v] + Sm[v], Sb[v]);
-            qxb[v] = fmaf(wk, gx[v], qxb[v]);
-            qyb[v] = fmaf(wk, gy[v], qyb[v]);  // full y-gradient (background included)
+            qb2[v] = fma2(wk, q[v], qb2[v]);
+            Fb2[v] = fma2(wk, f.F[v], Fb2[v]);
+            Gb2[v] = fma2(wk, f.G[v], Gb2[v]);
+            qxb2[v] = fma2(wk, gx[v], qxb2[v]);
+            qyb2[v] = fma2(wk, gy[v], qyb2[v]);  // full y-gradient (background included)
         }
+        Sz2 = fma2(wk, f.S2, Sz2);
     }
+    float qb[4], Fb[4], Gb[4], Sb[4], qxb[4], qyb[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+        qb[v] = qb2[v].x + qb2[v].y;
+        Fb[v] = Fb2[v].x + Fb2[v].y;
+        Gb[v] = Gb2[v].x + Gb2[v].y;
+        qxb[v] = qxb2[v].x + qxb2[v].y;
+        qyb[v] = qyb2[v].x + qyb2[v].y;
+        Sb[v] = Sm[v];  // the time weights sum to one
+    }
+    Sb[2] += Sz2.x + Sz2.y;
     __syncthreads();
     // time averages, row-major with padded rows: slots 0..4 = qbar, Fbar, Gbar, qxbar, qybar
     float* A = Q;
@@ -381,11 +510,13 @@ __device__ __forceinline__ void rusanov_f(const float qL[4], const float fL[4], 
     }
 }
 
-template <int N, int CPB>
+// Corrector body; with TV the TV indicator of the updated state follows in
+// the same kernel (tv_cell, bitwise what k_tv_cells_mixed computes).
+template <int N, int CPB, bool TV = false>
 __device__ __forceinline__ void corrector_mixed_body(double* __restrict__ u, const float* __restrict__ rvol,
                                                      const float* __restrict__ trace, int cells, int c0,
                                                      double dt, const BasisF& B, const PhysF& P,
-                                                     const MixedBg& bg) {
+                                                     const MixedBg& bg, const TvEpilogue& epi = TvEpilogue{}) {
     constexpr int n = N + 1, n2 = n * n, SL = 4 * n2, TR = kTraceComps * n;
     __shared__ float Fst[CPB][4][4][n];
     const int cl = threadIdx.x / n2;
@@ -445,32 +576,43 @@ __device__ __forceinline__ void corrector_mixed_body(double* __restrict__ u, con
         for (int v = 0; v < 4; ++v) Fst[cl][f][v][m] = out[v];
     }
     __syncthreads();
-    if (!active) return;
     double* uc = u + (size_t)cell * SL;
     const float* rc = rvol + (size_t)cell * SL;
+    double unew[4];
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
         const float face = (B.lift1[i] * Fst[cl][0][v][j] - B.lift0[i] * Fst[cl][1][v][j]) * P.inv_hx +
                            (B.lift1[j] * Fst[cl][2][v][i] - B.lift0[j] * Fst[cl][3][v][i]) * P.inv_hy;
         const float du = rc[v * n2 + node] - face;
-        uc[v * n2 + node] = fma(dt, f32_to_f64(du), uc[v * n2 + node]);  // FP64 accumulation
+        const double uo = active ? uc[v * n2 + node] : 0.0;  // padding threads touch no state
+        unew[v] = fma(dt, f32_to_f64(du), uo);                 // FP64 accumulation
+        if (active) uc[v * n2 + node] = unew[v];
+    }
+    if constexpr (TV) {
+        __shared__ float fs[CPB][n2], red[CPB][n2];
+        const int row = iy * n + j;
+        const float z = P.y0 + (iy + B.xi[j]) * P.hy;
+        const float f = tv_field_mixed(unew, epi.var, bg.rb[row], bg.Eb[row], bg.pb[row], z, P, (float)epi.theta0,
+                                       (float)(1.0 - epi.Rcp));
+        tv_cell<N, float>(f, epi.var == ADG_TV_THETA ? 0.f : bg.dzr[row], node, i, j, B, P.inv_hx, P.inv_hy,
+                          fs[cl], red[cl], active, epi.tv + cell);
     }
 }
 
 template <int N, int CPB>
-__global__ void __launch_bounds__(CPB*(N + 1) * (N + 1))
+__global__ void __launch_bounds__(CPB*(N + 1) * (N + 1), (MixCfg<N, CPB>::minb))
 k_predictor_mixed(const double* __restrict__ u, float* __restrict__ rvol, float* __restrict__ trace,
                   int cells, float dt, const BasisF B, const PhysF P, const MixedBg bg) {
     extern __shared__ float smf[];
     predictor_mixed_body<N, CPB>(u, rvol, trace, cells, blockIdx.x * CPB, dt, B, P, bg, smf);
 }
 
-template <int N, int CPB>
+template <int N, int CPB, bool TV>
 __global__ void __launch_bounds__(CPB*(N + 1) * (N + 1))
 k_corrector_mixed(double* __restrict__ u, const float* __restrict__ rvol,
                   const float* __restrict__ trace, int cells, double dt, const BasisF B,
-                  const PhysF P, const MixedBg bg) {
-    corrector_mixed_body<N, CPB>(u, rvol, trace, cells, blockIdx.x * CPB, dt, B, P, bg);
+                  const PhysF P, const MixedBg bg, const TvEpilogue epi) {
+    corrector_mixed_body<N, CPB, TV>(u, rvol, trace, cells, blockIdx.x * CPB, dt, B, P, bg, epi);
 }
 
 // Batched persistent kernels: a fixed grid walks a list of tiles (instance,
@@ -519,10 +661,15 @@ static int launch_pred_mixed(const double* u, float* rvol, float* trace, int cel
 
 template <int N>
 static int launch_corr_mixed(double* u, const float* rvol, const float* trace, int cells, double dt,
-                             const BasisF& B, const PhysF& P, const MixedBg& bg, cudaStream_t s) {
+                             const BasisF& B, const PhysF& P, const MixedBg& bg, const TvEpilogue* epi,
+                             cudaStream_t s) {
     using C = MixCfg<N>;
     const int blocks = (cells + C::cpb - 1) / C::cpb;
-    k_corrector_mixed<N, C::cpb><<<blocks, C::threads, 0, s>>>(u, rvol, trace, cells, dt, B, P, bg);
+    if (epi)
+        k_corrector_mixed<N, C::cpb, true><<<blocks, C::threads, 0, s>>>(u, rvol, trace, cells, dt, B, P, bg, *epi);
+    else
+        k_corrector_mixed<N, C::cpb, false>
+            <<<blocks, C::threads, 0, s>>>(u, rvol, trace, cells, dt, B, P, bg, TvEpilogue{});
     return (int)cudaGetLastError();
 }
 
@@ -543,16 +690,17 @@ int launch_predictor_mixed(int N, const double* u, float* rvol, float* trace, in
 }
 
 int launch_corrector_mixed(int N, double* u, const float* rvol, const float* trace, int cells,
-                           double dt, const BasisF& B, const PhysF& P, const MixedBg& bg, void* stream) {
+                           double dt, const BasisF& B, const PhysF& P, const MixedBg& bg, void* stream,
+                           const TvEpilogue* epi) {
     cudaStream_t s = (cudaStream_t)stream;
     switch (N) {
-        case 1: return launch_corr_mixed<1>(u, rvol, trace, cells, dt, B, P, bg, s);
-        case 2: return launch_corr_mixed<2>(u, rvol, trace, cells, dt, B, P, bg, s);
-        case 3: return launch_corr_mixed<3>(u, rvol, trace, cells, dt, B, P, bg, s);
-        case 4: return launch_corr_mixed<4>(u, rvol, trace, cells, dt, B, P, bg, s);
-        case 5: return launch_corr_mixed<5>(u, rvol, trace, cells, dt, B, P, bg, s);
-        case 6: return launch_corr_mixed<6>(u, rvol, trace, cells, dt, B, P, bg, s);
-        case 7: return launch_corr_mixed<7>(u, rvol, trace, cells, dt, B, P, bg, s);
+        case 1: return launch_corr_mixed<1>(u, rvol, trace, cells, dt, B, P, bg, epi, s);
+        case 2: return launch_corr_mixed<2>(u, rvol, trace, cells, dt, B, P, bg, epi, s);
+        case 3: return launch_corr_mixed<3>(u, rvol, trace, cells, dt, B, P, bg, epi, s);
+        case 4: return launch_corr_mixed<4>(u, rvol, trace, cells, dt, B, P, bg, epi, s);
+        case 5: return launch_corr_mixed<5>(u, rvol, trace, cells, dt, B, P, bg, epi, s);
+        case 6: return launch_corr_mixed<6>(u, rvol, trace, cells, dt, B, P, bg, epi, s);
+        case 7: return launch_corr_mixed<7>(u, rvol, trace, cells, dt, B, P, bg, epi, s);
     }
     return (int)cudaErrorInvalidValue;
 }

@@ -3,16 +3,21 @@
 //
 // TV per cell: TV = sum_ij w_i w_j (|df/dx| + |df/dy|) with f = theta
 // (potential temperature, Sec. 4.2) or rho at the nodes, derivatives by the
-// nodal derivative matrix.  Mean and population standard deviation over all
-// cells follow Chan, Golub and LeVeque's pairwise update (cited by the paper
-// for a parallel, stable evaluation): contiguous chunks are reduced exactly
-// (two-pass) per block, then the partial (count, mean, M2) triples are
-// combined in a fixed binary tree, so the result is deterministic.
+// nodal derivative matrix (adg_tv_cell.cuh).  Mean and population standard
+// deviation over all cells follow Chan, Golub and LeVeque's pairwise update
+// (cited by the paper for a parallel, stable evaluation): contiguous chunks
+// are reduced exactly (two-pass) per block, then the partial (count, mean,
+// M2) triples are combined in a fixed binary tree, so the result is
+// deterministic.
 #include <cuda_runtime.h>
+
+#include <algorithm>
+#include <vector>
 
 #include "adg_convert.cuh"
 #include "adg_internal.h"
 #include "adg_physics.cuh"
+#include "adg_tv_cell.cuh"
 
 namespace adg {
 
@@ -21,14 +26,6 @@ struct TvCfg {
     static constexpr int n = N + 1;
     static constexpr int cpb = N == 1 ? 32 : N == 2 ? 16 : N == 3 ? 8 : N <= 5 ? 4 : 2;
 };
-
-__device__ __forceinline__ double theta_of(const double q[4], double z, const Phys& P) {
-    const double rinv = 1.0 / q[0];
-    const double gz = P.gravity ? P.g * z : 0.0;
-    const double p = P.gm1 * (q[3] - 0.5 * (q[1] * q[1] + q[2] * q[2]) * rinv - q[0] * gz);
-    const double T = p * rinv * P.invR;
-    return T * pow(P.p0 / p, P.Rcp);
-}
 
 template <int N, int CPB>
 __global__ void __launch_bounds__(CPB*(N + 1) * (N + 1))
@@ -49,32 +46,12 @@ k_tv_cells(const double* __restrict__ u, double* __restrict__ tv, int cells, int
 #pragma unroll
     for (int v = 0; v < 4; ++v) q[v] = uc[v * n2 + node];
     const double z = P.y0 + (iy + B.xi[j]) * P.hy;
-    fs[cl][node] = var == ADG_TV_THETA ? theta_of(q, z, P) : q[0];
-    __syncthreads();
-    double fx = 0.0, fy = 0.0;
-#pragma unroll
-    for (int p = 0; p < n; ++p) {
-        fx += B.D[i][p] * fs[cl][j * n + p];
-        fy += B.D[j][p] * fs[cl][p * n + i];
-    }
-    red[cl][node] = B.w[i] * B.w[j] * (fabs(fx * P.inv_hx) + fabs(fy * P.inv_hy));
-    __syncthreads();
-    if (node == 0 && active) {
-        double s = 0.0;
-        for (int a = 0; a < n2; ++a) s += red[cl][a];
-        tv[cell] = s;
-    }
+    const double f = var == ADG_TV_THETA ? theta_of(q, z, P) : q[0];
+    tv_cell<N, double>(f, 0.0, node, i, j, B, P.inv_hx, P.inv_hy, fs[cl], red[cl], active, tv + cell);
 }
 
-// Mixed-precision TV: the indicator field is formed from the FP64 state by
-// the FP64 perturbation split (rho' = rho - rhobar, E' = rhoE - Ebar) and then
-// in FP32.  For theta the potential-temperature perturbation is evaluated
-// without the 300 K offset,
-//     theta'/theta0 = (1 + p'/pbar)^(1-R/cp) / (1 + rho'/rhobar) - 1
-//                   = expm1((1 - R/cp) log1p(p'/pbar) - log1p(rho'/rhobar)),
-// (theta = p^(1-R/cp) p0^(R/cp) / (rho R) and theta0 is the same expression
-// at the background), so no FP32 value carries theta ~ 300 K.  For rho the
-// field is rho' and the background gradient d rhobar/dz is added.
+// Mixed-precision TV: FP64 perturbation split, FP32 field and sums
+// (tv_field_mixed).
 template <int N, int CPB>
 __global__ void __launch_bounds__(CPB*(N + 1) * (N + 1))
 k_tv_cells_mixed(const double* __restrict__ u, double* __restrict__ tv, int cells, int var,
@@ -91,133 +68,126 @@ k_tv_cells_mixed(const double* __restrict__ u, double* __restrict__ tv, int cell
     const int iy = cell / P.nx;
     const int row = iy * n + j;
     const double* uc = u + (size_t)cell * SL;
-    const double rb64 = bg.rb[row];
-    const float rp = f64_to_f32(uc[node] - rb64);
-    float f;
-    if (var == ADG_TV_THETA) {
-        const float Ep = f64_to_f32(uc[3 * n2 + node] - bg.Eb[row]);
-        const float mx = f64_to_f32(uc[n2 + node]), my = f64_to_f32(uc[2 * n2 + node]);
-        const float rb = f64_to_f32(rb64);
-        const float rho = rb + rp;
-        const float z = P.y0 + (iy + B.xi[j]) * P.hy;
-        const float pp = P.gm1 * (Ep - 0.5f * (mx * mx + my * my) / rho - P.g * z * rp);
-        f = theta0 * expm1f(one_m_kappa * log1pf(pp / bg.pb[row]) - log1pf(rp / rb));
-    } else {
-        f = rp;
-    }
-    fs[cl][node] = f;
-    __syncthreads();
-    float fx = 0.f, fy = 0.f;
+    double q[4];
 #pragma unroll
-    for (int p = 0; p < n; ++p) {
-        fx = fmaf(B.D[i][p], fs[cl][j * n + p], fx);
-        fy = fmaf(B.D[j][p], fs[cl][p * n + i], fy);
-    }
-    fx *= P.inv_hx;
-    fy *= P.inv_hy;
-    if (var != ADG_TV_THETA) fy += bg.dzr[row];
-    red[cl][node] = B.w[i] * B.w[j] * (fabsf(fx) + fabsf(fy));
-    __syncthreads();
-    if (node == 0 && active) {
-        float s = 0.f;  // FP32 sum of n^2 positive terms: relative error ~n^2 * 6e-8
-        for (int a = 0; a < n2; ++a) s += red[cl][a];
-        tv[cell] = f32_to_f64(s);
-    }
+    for (int v = 0; v < 4; ++v) q[v] = uc[v * n2 + node];
+    const float z = P.y0 + (iy + B.xi[j]) * P.hy;
+    const float f = tv_field_mixed(q, var, bg.rb[row], bg.Eb[row], bg.pb[row], z, P, theta0, one_m_kappa);
+    tv_cell<N, float>(f, var == ADG_TV_THETA ? 0.f : bg.dzr[row], node, i, j, B, P.inv_hx, P.inv_hy, fs[cl],
+                      red[cl], active, tv + cell);
 }
 
-// Multi-block statistics.  Block b owns the contiguous chunk of cells
+// Statistics in one launch.  Block b owns the contiguous chunk of cells
 // [b*chunk, min((b+1)*chunk, cells)); it forms the chunk's count, mean and M2
-// by an exact two-pass reduction in a fixed tree and writes the triple to
-// part[b] (scratch).  k_tv_flags then combines the partial triples with Chan
-// et al.'s pairwise update in a fixed binary tree (deterministic) and writes
-// the flags.
+// by an exact two-pass reduction in a fixed order and publishes the triple.
+// The last block to finish (an atomic ticket taken after a fence; nothing
+// waits) combines the chunk triples with Chan et al.'s pairwise update in a
+// fixed binary tree -- the result does not depend on which block finishes
+// last -- writes mean and sigma and re-arms the ticket for the next launch.
+// The tree's shape depends only on the cell count, so its weights
+// n_b/(n_a+n_b) and n_a n_b/(n_a+n_b) are divided out once on the host
+// (`tv_stats_prepare`, the same IEEE quotients) and the device tree runs on
+// multiplies and adds: FP64 division is a long dependent chain on this part.
 constexpr int kPartThreads = 256;
+constexpr int kMaxPartials = 1024;
+constexpr int kFactorOffset = 3 * kMaxPartials;  // Chan weights after the triples in `part`
 
+// fixed-order block sum: warp shuffles, then the 8 warp sums by warp 0
 __device__ __forceinline__ double block_sum_256(double v, double* sh) {
-    const int t = threadIdx.x;
-    sh[t] = v;
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) sh[w] = v;
     __syncthreads();
-    for (int s = kPartThreads / 2; s > 0; s >>= 1) {
-        if (t < s) sh[t] += sh[t + s];
-        __syncthreads();
+    if (w == 0) {
+        v = lane < kPartThreads / 32 ? sh[lane] : 0.0;
+#pragma unroll
+        for (int o = 4; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) sh[8] = v;
     }
-    const double r = sh[0];
+    __syncthreads();
+    const double r = sh[8];
     __syncthreads();
     return r;
 }
 
 __global__ void __launch_bounds__(kPartThreads)
-k_tv_partials(const double* __restrict__ tv, int cells, int chunk, double* __restrict__ part) {
-    __shared__ double sh[kPartThreads];
-    const int b = blockIdx.x;
-    const int lo = b * chunk;
-    const int hi = min(cells, lo + chunk);
+k_tv_stats(const double* __restrict__ tv, int cells, int chunk, double* __restrict__ part,
+           double* __restrict__ stats, unsigned* __restrict__ ticket) {
+    __shared__ double sh[9];
+    __shared__ double smean[kMaxPartials], sm2[kMaxPartials];
+    __shared__ bool last;
+    const int t = threadIdx.x, b = blockIdx.x, nb = gridDim.x;
+    const int lo = b * chunk, hi = min(cells, lo + chunk);
     double s = 0.0;
-    for (int c = lo + threadIdx.x; c < hi; c += kPartThreads) s += tv[c];
-    const double cnt = (double)max(0, hi - lo);
+    for (int c = lo + t; c < hi; c += kPartThreads) s += tv[c];
     const double sum = block_sum_256(s, sh);
-    const double mean = cnt > 0.0 ? sum / cnt : 0.0;
+    if (t == 0) sh[0] = sum / (double)(hi - lo);  // every chunk holds >= 1 cell
+    __syncthreads();
+    const double mean = sh[0];
+    __syncthreads();
     double q = 0.0;
-    for (int c = lo + threadIdx.x; c < hi; c += kPartThreads) {
+    for (int c = lo + t; c < hi; c += kPartThreads) {
         const double d = tv[c] - mean;
         q += d * d;
     }
     const double m2 = block_sum_256(q, sh);
-    if (threadIdx.x == 0) {
-        part[3 * b + 0] = cnt;
+    if (t == 0) {
+        part[3 * b + 0] = (double)(hi - lo);
         part[3 * b + 1] = mean;
         part[3 * b + 2] = m2;
-    }
-}
-
-constexpr int kMaxPartials = 1024;
-
-// Every block combines all partial triples in the same fixed binary tree
-// (so every block obtains bitwise the same mean and sigma), block 0 writes
-// them out, and each block flags its own chunk of cells.  Spreading the FP64
-// flag comparisons over many SMs matters on a part with 2 FP64 FMA per clock
-// per SM.
-__global__ void __launch_bounds__(kPartThreads)
-k_tv_flags(const double* __restrict__ part, int nparts, const double* __restrict__ tv, int cells, int chunk,
-           double T_r, double T_c, double* __restrict__ stats, int8_t* __restrict__ flags) {
-    __shared__ double sc[kMaxPartials], smean[kMaxPartials], sm2[kMaxPartials];
-    const int t = threadIdx.x;
-    for (int a = t; a < kMaxPartials; a += kPartThreads) {
-        sc[a] = a < nparts ? part[3 * a] : 0.0;
-        smean[a] = a < nparts ? part[3 * a + 1] : 0.0;
-        sm2[a] = a < nparts ? part[3 * a + 2] : 0.0;
+        __threadfence();
+        last = atomicAdd(ticket, 1u) == (unsigned)(nb - 1);
     }
     __syncthreads();
+    if (!last) return;
+    __threadfence();
     int top = 1;
-    while (top < nparts) top <<= 1;
-    for (int stride = top / 2; stride > 0; stride >>= 1) {
+    while (top < nb) top <<= 1;
+    for (int a = t; a < top; a += kPartThreads) {
+        smean[a] = a < nb ? __ldcg(part + 3 * a + 1) : 0.0;
+        sm2[a] = a < nb ? __ldcg(part + 3 * a + 2) : 0.0;
+    }
+    __syncthreads();
+    const double* fac = part + kFactorOffset;
+    for (int stride = top / 2, off = 0; stride > 0; off += stride, stride >>= 1) {
         for (int a = t; a < stride; a += kPartThreads) {
-            const double na = sc[a], nb = sc[a + stride];
-            const double nn = na + nb;
-            if (nb > 0.0) {
-                const double d = smean[a + stride] - smean[a];
-                smean[a] = smean[a] + d * (nb / nn);
-                sm2[a] = sm2[a] + sm2[a + stride] + d * d * (na * nb / nn);
-                sc[a] = nn;
-            }
+            // weights are zero where the right-hand entry is empty padding
+            const double f1 = __ldcg(fac + 2 * (off + a)), f2 = __ldcg(fac + 2 * (off + a) + 1);
+            const double d = smean[a + stride] - smean[a];
+            smean[a] = smean[a] + d * f1;
+            sm2[a] = sm2[a] + sm2[a + stride] + d * d * f2;
         }
         __syncthreads();
     }
-    const double mu = smean[0];
-    const double sig = sc[0] > 0.0 ? sqrt(sm2[0] / sc[0]) : 0.0;
-    if (blockIdx.x == 0 && t == 0 && stats) {
-        stats[0] = mu;
-        stats[1] = sig;
+    if (t == 0) {
+        stats[0] = smean[0];
+        stats[1] = sqrt(sm2[0] / (double)cells);
+        *ticket = 0u;  // every block of this launch has taken its ticket
     }
-    if (!flags) return;
-    const double thr_r = mu + T_r * sig;
-    const double thr_c = mu + T_c * sig;
-    const bool flat = sig <= 1e-12 * fabs(mu);  // reading F1: keep all
-    const int lo = blockIdx.x * chunk, hi = min(cells, lo + chunk);
-    for (int c = lo + t; c < hi; c += kPartThreads) {
-        const double x = tv[c];
-        flags[c] = flat ? (int8_t)0 : x >= thr_r ? (int8_t)1 : (x < thr_c ? (int8_t)-1 : (int8_t)0);
-    }
+}
+
+// Flags from (mean, sigma) in device memory, one cell per thread: refine if
+// TV >= mean + T_r sigma, coarsen if TV < mean + T_c sigma, keep all when
+// sigma <= 1e-12 |mean| (reading F1).  The comparisons use the IEEE-754
+// order of non-negative doubles as 64-bit integers (TV >= 0): exact, and off
+// the narrow FP64 pipe.
+__global__ void __launch_bounds__(kPartThreads)
+k_tv_flag_cells(const double* __restrict__ tv, int cells, const double* __restrict__ stats, double T_r,
+                double T_c, int8_t* __restrict__ flags) {
+    const int c = blockIdx.x * kPartThreads + threadIdx.x;
+    if (c >= cells) return;
+    const double mu = stats[0], sig = stats[1];
+    // product and sum rounded separately (no contraction), as mean + T * sigma is usually written
+    const double thr_r = __dadd_rn(mu, __dmul_rn(T_r, sig)), thr_c = __dadd_rn(mu, __dmul_rn(T_c, sig));
+    // NaN statistics compare false both ways: no flags
+    const bool flat = sig <= 1e-12 * fabs(mu) || !(thr_r == thr_r) || !(thr_c == thr_c);
+    const long long bx = __double_as_longlong(tv[c]);
+    const bool nan = (bx & 0x7fffffffffffffffLL) > 0x7ff0000000000000LL;
+    // a threshold <= 0 lies at or below every TV
+    const bool ref = thr_r <= 0.0 || bx >= __double_as_longlong(thr_r);
+    const bool coa = thr_c > 0.0 && bx < __double_as_longlong(thr_c);
+    flags[c] = (flat || nan) ? (int8_t)0 : ref ? (int8_t)1 : (coa ? (int8_t)-1 : (int8_t)0);
 }
 
 // ---------------------------------------------------------------- scenarios
@@ -431,23 +401,49 @@ int tv_stats_chunk(int cells) {
     return chunk;
 }
 
+// Chan weights of the statistics tree for `cells` cells into part + kFactorOffset.
+int tv_stats_prepare(int cells, double* part, void* stream) {
+    const int chunk = tv_stats_chunk(cells);
+    const int nb = (cells + chunk - 1) / chunk;
+    int top = 1;
+    while (top < nb) top <<= 1;
+    std::vector<double> cnt(top, 0.0), fac(2 * (size_t)std::max(top - 1, 1), 0.0);
+    for (int b = 0; b < nb; ++b) cnt[b] = (double)std::min(chunk, cells - b * chunk);
+    for (int stride = top / 2, off = 0; stride > 0; off += stride, stride >>= 1) {
+        for (int a = 0; a < stride; ++a) {
+            const double na = cnt[a], nbb = cnt[a + stride], nn = na + nbb;
+            if (nbb > 0.0) {
+                fac[2 * (off + a)] = nbb / nn;
+                fac[2 * (off + a) + 1] = na * nbb / nn;
+                cnt[a] = nn;
+            }
+        }
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpyAsync(part + kFactorOffset, fac.data(), fac.size() * 8, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // the host table must outlive the copy
+    return (int)e;
+}
+
+size_t tv_stats_scratch_doubles() { return (size_t)kFactorOffset + 2 * (size_t)kMaxPartials; }
+
 int launch_tv_stats_multi(const double* tv, int cells, double T_r, double T_c, double* part,
                           double* stats_dev, int8_t* flags, void* stream) {
     cudaStream_t s = (cudaStream_t)stream;
     const int chunk = tv_stats_chunk(cells);
     const int np = (cells + chunk - 1) / chunk;
-    k_tv_partials<<<np, kPartThreads, 0, s>>>(tv, cells, chunk, part);
+    // stats_dev holds mean, sigma and (third slot) the ticket counter
+    k_tv_stats<<<np, kPartThreads, 0, s>>>(tv, cells, chunk, part, stats_dev,
+                                           reinterpret_cast<unsigned*>(stats_dev + 2));
     cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return (int)e;
-    k_tv_flags<<<np, kPartThreads, 0, s>>>(part, np, tv, cells, chunk, T_r, T_c, stats_dev, flags);
-    return (int)cudaGetLastError();
+    if (e != cudaSuccess || !flags) return (int)e;
+    return launch_tv_flags_given(tv, cells, stats_dev, T_r, T_c, flags, stream);
 }
 
-int launch_tv_flags_given(const double* tv, int cells, const double* part1, double T_r, double T_c,
+int launch_tv_flags_given(const double* tv, int cells, const double* stats_dev, double T_r, double T_c,
                           int8_t* flags, void* stream) {
-    const int chunk = tv_stats_chunk(cells);
-    const int nb = (cells + chunk - 1) / chunk;
-    k_tv_flags<<<nb, kPartThreads, 0, (cudaStream_t)stream>>>(part1, 1, tv, cells, chunk, T_r, T_c, nullptr, flags);
+    const int nb = (cells + kPartThreads - 1) / kPartThreads;
+    k_tv_flag_cells<<<nb, kPartThreads, 0, (cudaStream_t)stream>>>(tv, cells, stats_dev, T_r, T_c, flags);
     return (int)cudaGetLastError();
 }
 

@@ -1,0 +1,85 @@
+// Per-cell total variation (Sec. 3, Eq. 6), shared by the TV kernels
+// (adg_tv.cu) and the corrector epilogues that evaluate the indicator on the
+// freshly updated state (adg_fp64.cu, adg_mixed.cu), so both give bitwise the
+// same TV.  One thread per node, CPB cells per block.
+//
+//   TV = sum_ij w_i w_j (|df/dx| + |df/dy|),
+//
+// f the indicator field at the nodes (theta or rho), derivatives by the nodal
+// derivative matrix.
+#pragma once
+#include "adg_convert.cuh"
+#include "adg_internal.h"
+
+namespace adg {
+
+__device__ __forceinline__ double theta_of(const double q[4], double z, const Phys& P) {
+    const double rinv = 1.0 / q[0];
+    const double gz = P.gravity ? P.g * z : 0.0;
+    const double p = P.gm1 * (q[3] - 0.5 * (q[1] * q[1] + q[2] * q[2]) * rinv - q[0] * gz);
+    const double T = p * rinv * P.invR;
+    return T * pow(P.p0 / p, P.Rcp);
+}
+
+// Mixed-precision indicator field from the FP64 state at one node: the FP64
+// perturbation split (rho' = rho - rhobar, E' = rhoE - Ebar), then FP32.  For
+// theta the perturbation is evaluated without the 300 K offset,
+//     theta'/theta0 = (1 + p'/pbar)^(1-R/cp) / (1 + rho'/rhobar) - 1
+//                   = expm1((1 - R/cp) log1p(p'/pbar) - log1p(rho'/rhobar)),
+// (theta = p^(1-R/cp) p0^(R/cp) / (rho R), theta0 the same expression at the
+// background), so no FP32 value carries theta ~ 300 K.  For rho the field is
+// rho' (the caller adds d rhobar/dz to the y-derivative).
+__device__ __forceinline__ float tv_field_mixed(const double q[4], int var, double rb64, double Eb64, float pb,
+                                                float z, const PhysF& P, float theta0, float one_m_kappa) {
+    const float rp = f64_to_f32(q[0] - rb64);
+    if (var != ADG_TV_THETA) return rp;
+    const float Ep = f64_to_f32(q[3] - Eb64);
+    const float mx = f64_to_f32(q[1]), my = f64_to_f32(q[2]);
+    const float rb = f64_to_f32(rb64);
+    const float rho = rb + rp;
+    const float pp = P.gm1 * (Ep - __fdividef(0.5f * (mx * mx + my * my), rho) - P.g * z * rp);
+    return theta0 * expm1f(one_m_kappa * log1pf(__fdividef(pp, pb)) - log1pf(__fdividef(rp, rb)));
+}
+
+__device__ __forceinline__ double tv_abs(double x) { return fabs(x); }
+__device__ __forceinline__ float tv_abs(float x) { return fabsf(x); }
+__device__ __forceinline__ double tv_to_f64(double x) { return x; }
+__device__ __forceinline__ double tv_to_f64(float x) { return f32_to_f64(x); }
+
+// TV of this thread's cell from the field value f at its node.  fs, red: this
+// cell's two n^2 scratch rows in shared memory; fy_add is added to the
+// y-derivative (background gradient).  Every thread of the block must call
+// it (three barriers); node 0 of an active cell writes *out.  Sums run over
+// rows first (one thread per row), then over the row sums.
+template <int N, typename T, typename BT>
+__device__ __forceinline__ void tv_cell(T f, T fy_add, int node, int i, int j, const BT& B, T inv_hx, T inv_hy,
+                                        T* fs, T* red, bool active, double* out) {
+    constexpr int n = N + 1;
+    fs[node] = f;
+    __syncthreads();
+    T fx = T(0), fy = T(0);
+#pragma unroll
+    for (int p = 0; p < n; ++p) {
+        fx = fma(B.D[i][p], fs[j * n + p], fx);
+        fy = fma(B.D[j][p], fs[p * n + i], fy);
+    }
+    fx = fx * inv_hx;
+    fy = fy * inv_hy + fy_add;
+    red[node] = B.w[i] * B.w[j] * (tv_abs(fx) + tv_abs(fy));
+    __syncthreads();
+    if (i == 0) {
+        T s = T(0);
+#pragma unroll
+        for (int a = 0; a < n; ++a) s += red[j * n + a];
+        fs[j] = s;  // every thread has read fs before the barrier above
+    }
+    __syncthreads();
+    if (node == 0 && active) {
+        T s = T(0);
+#pragma unroll
+        for (int a = 0; a < n; ++a) s += fs[a];
+        *out = tv_to_f64(s);
+    }
+}
+
+}  // namespace adg

@@ -179,6 +179,17 @@ class Mesh:
             _stream_ptr(stream)))
         return tv, flags, (stats[0], stats[1])
 
+    def step_tv(self, dt, var, T_r, T_c, want_stats=True, stream=None):
+        """One step, then the TV indicator of the new state (adg_step_tv)."""
+        C = self.leaves
+        tv = torch.empty(C, dtype=torch.float64, device=self.device)
+        flags = torch.empty(C, dtype=torch.int8, device=self.device)
+        stats = (ctypes.c_double * 2)()
+        L.check(self._lib.adg_step_tv(
+            self.h, float(dt), int(var), float(T_r), float(T_c), ctypes.c_void_p(tv.data_ptr()),
+            ctypes.c_void_p(flags.data_ptr()), stats if want_stats else None, _stream_ptr(stream)))
+        return tv, flags, (stats[0], stats[1])
+
     def check_finite(self, stream=None):
         L.check(self._lib.adg_check_finite(self.h, _stream_ptr(stream)))
 
