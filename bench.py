@@ -83,7 +83,7 @@ def predictor_flops_per_cell(n):
 # DRAM bytes (read + write) of one predictor launch on this workload, from one
 # ncu capture of the kernel as it stands (profiles/k_predictor_*_warm_bubble_n5_81x81.md);
 # set to None whenever the kernel changes after the capture.
-PREDICTOR_TRAFFIC = {"fp64": 7810304 + 1280, "mixed": None}  # mixed: re-captured after the kernel change
+PREDICTOR_TRAFFIC = {"fp64": 7810304 + 1280, "mixed": 7634176 + 13568}
 
 
 def measure_fma_peaks():
@@ -302,13 +302,12 @@ def run_form(prec_name, steps, warmup, dev, ws):
     # end to end through the public API with host buffers (pinned)
     host_in = u_init.cpu().pin_memory()
     host_out = torch.empty_like(host_in).pin_memory()
-    stats = (ctypes.c_double * 2)()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(steps):
         L.check(lib.adg_set_state(m.h, ctypes.c_void_p(host_in.data_ptr()), m.count, 0, sp))
         L.check(lib.adg_step_tv(m.h, dt, L.ADG_TV_THETA, T_R, T_C, ctypes.c_void_p(tvbuf.data_ptr()),
-                                ctypes.c_void_p(flags.data_ptr()), stats, sp))
+                                ctypes.c_void_p(flags.data_ptr()), None, sp))
         L.check(lib.adg_get_state(m.h, ctypes.c_void_p(host_out.data_ptr()), m.count, 0, sp))
     torch.cuda.synchronize()
     e2e_sec = time.perf_counter() - t0
@@ -628,7 +627,7 @@ def run_ours(args):
             "gpu_launches": 4 * args.steps,
             "clocks": main["clocks"],
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": dof * 8,
-                    "d2h_bytes_per_step": dof * 8 + 16},
+                    "d2h_bytes_per_step": dof * 8},
             "roofline": roof,
             "cpu_baseline": cpu,
             "forms": forms,
