@@ -32,6 +32,7 @@
 #include "adg_internal.h"
 #include "adg_mesh.h"
 #include "adg_physics.cuh"
+#include "adg_tv_cell.cuh"
 
 namespace adg {
 
@@ -177,10 +178,10 @@ static int size_buffers(adg_mesh* m, double* new_u) {
         m->u = new_u;
     }
     m->cells = L;
-    m->tv_prep_cells = -1;  // fresh `part`: statistics tree weights not prepared
+    m->tv_prep_cells = -1;  // fresh `part`: combine weights not prepared
     if (cudaMalloc(&m->rvol, cnt * 8) != cudaSuccess || cudaMalloc(&m->trace, tr * 8) != cudaSuccess ||
         cudaMalloc(&m->tv, (size_t)L * 8) != cudaSuccess ||
-        cudaMalloc(&m->part, 8 * tv_stats_scratch_doubles()) != cudaSuccess) {
+        cudaMalloc(&m->part, 8 * tv_stats_scratch_doubles(m->N, L)) != cudaSuccess) {
         cudaGetLastError();
         return fail(ADG_ENOMEM, "adaptive mesh: buffers");
     }
@@ -396,8 +397,9 @@ k_corrector_amr(double* __restrict__ u, const double* __restrict__ rvol, const d
 
 template <int N, int CPB>
 __global__ void __launch_bounds__(CPB*(N + 1) * (N + 1))
-k_tv_cells_amr(const double* __restrict__ u, double* __restrict__ tv, int cells, int var, const Basis B,
-               const Phys P0, const double* __restrict__ geo) {
+k_tv_cells_amr(const double* __restrict__ u, double* __restrict__ tv, double* __restrict__ part, int cells,
+               int var, const Basis B, const Phys P0, const double* __restrict__ geo) {
+    static_assert(CPB == tv_cpb(N), "the TV statistics combine blocks of tv_cpb(N) cells");
     constexpr int n = N + 1, n2 = n * n, SL = 4 * n2;
     __shared__ double fs[CPB][n2];
     __shared__ double red[CPB][n2];
@@ -413,27 +415,10 @@ k_tv_cells_amr(const double* __restrict__ u, double* __restrict__ tv, int cells,
 #pragma unroll
     for (int v = 0; v < 4; ++v) q[v] = uc[v * n2 + node];
     const double z = geo[cell * 4 + 1] + B.xi[j] * P.hy;
-    double f = q[0];
-    if (var == ADG_TV_THETA) {
-        const double rinv = 1.0 / q[0];
-        const double p = P.gm1 * (q[3] - 0.5 * (q[1] * q[1] + q[2] * q[2]) * rinv - q[0] * (P.gravity ? P.g * z : 0.0));
-        f = p * rinv * P.invR * pow(P.p0 / p, P.Rcp);
-    }
-    fs[cl][node] = f;
-    __syncthreads();
-    double fx = 0.0, fy = 0.0;
-#pragma unroll
-    for (int p = 0; p < n; ++p) {
-        fx += B.D[i][p] * fs[cl][j * n + p];
-        fy += B.D[j][p] * fs[cl][p * n + i];
-    }
-    red[cl][node] = B.w[i] * B.w[j] * (fabs(fx * P.inv_hx) + fabs(fy * P.inv_hy));
-    __syncthreads();
-    if (node == 0 && active) {
-        double s = 0.0;
-        for (int a = 0; a < n2; ++a) s += red[cl][a];
-        tv[cell] = s;
-    }
+    const double f = var == ADG_TV_THETA ? theta_of(q, z, P) : q[0];
+    const double r = tv_cell<N, double>(f, 0.0, node, i, j, B, P.inv_hx, P.inv_hy, fs[cl], red[cl], active,
+                                        tv + cell);
+    tv_block_triple<CPB>(r, node == 0, cl, min(CPB, cells - (int)blockIdx.x * CPB), part);
 }
 
 template <int N>
@@ -595,14 +580,16 @@ static int corr_n(adg_mesh* m, double dt, cudaStream_t s) {
 int amr_corrector(adg_mesh* m, double dt, void* stream) { AMR_DISPATCH(corr_n, m, dt, (cudaStream_t)stream) }
 
 template <int N>
-static int tv_n(adg_mesh* m, int var, double* tv, cudaStream_t s) {
+static int tv_n(adg_mesh* m, int var, double* tv, double* part, cudaStream_t s) {
     using C = AmrCfg<N>;
-    k_tv_cells_amr<N, C::cpb><<<(m->cells + C::cpb - 1) / C::cpb, C::threads, 0, s>>>(m->u, tv, m->cells, var,
-                                                                                        m->B, m->P, m->geo);
+    k_tv_cells_amr<N, C::cpb><<<(m->cells + C::cpb - 1) / C::cpb, C::threads, 0, s>>>(m->u, tv, part, m->cells,
+                                                                                        var, m->B, m->P, m->geo);
     ADG_CK(cudaGetLastError(), "amr tv launch");
     return ADG_OK;
 }
-int amr_tv_cells(adg_mesh* m, int var, double* tv, void* stream) { AMR_DISPATCH(tv_n, m, var, tv, (cudaStream_t)stream) }
+int amr_tv_cells(adg_mesh* m, int var, double* tv, double* part, void* stream) {
+    AMR_DISPATCH(tv_n, m, var, tv, part, (cudaStream_t)stream)
+}
 
 template <int N>
 static int init_amr_n(adg_mesh* m, const adg_scenario* sc, cudaStream_t s) {

@@ -361,13 +361,13 @@ int adg_create_mesh(const adg_mesh_desc* d, adg_mesh** out) {
     if (cudaMalloc(&m->u, cnt * 8) != cudaSuccess || cudaMalloc(&m->rvol, cnt * 8) != cudaSuccess ||
         cudaMalloc(&m->trace, tr * 8) != cudaSuccess || cudaMalloc(&m->tv, (size_t)m->cells * 8) != cudaSuccess ||
         cudaMalloc(&m->stats, 4 * 8) != cudaSuccess || cudaMalloc(&m->speed, (size_t)nb * 8) != cudaSuccess ||
-        cudaMalloc(&m->part, 8 * adg::tv_stats_scratch_doubles()) != cudaSuccess ||
+        cudaMalloc(&m->part, 8 * adg::tv_stats_scratch_doubles(m->N, m->cells)) != cudaSuccess ||
         cudaMalloc(&m->flag, sizeof(int)) != cudaSuccess || cudaMalloc(&m->bgbuf, nbg * 8) != cudaSuccess) {
         cudaGetLastError();
         free_mesh(m);
         return fail(ADG_ENOMEM, "create_mesh: device allocation failed");
     }
-    if (cudaMemset(m->stats, 0, 4 * 8) != cudaSuccess) {  // mean, sigma, statistics ticket
+    if (cudaMemset(m->stats, 0, 4 * 8) != cudaSuccess) {  // mean, sigma and the given pair
         cudaGetLastError();
         free_mesh(m);
         return fail(ADG_ECUDA, "create_mesh: workspace initialisation failed");
@@ -584,17 +584,22 @@ static int tv_check(const adg_mesh* m, int var, double T_r, double T_c) {
     return ADG_OK;
 }
 
-// statistics over the TV values in tvbuf, flags, optional host copy of (mean, sigma)
-static int tv_finish(adg_mesh* m, double* tvbuf, double T_r, double T_c, int8_t* flags, double* stats,
-                     void* stream) {
-    int e;
+// combine weights of the statistics ready for the current cell count
+static int tv_prepare(adg_mesh* m, void* stream) {
     if (m->tv_prep_cells != m->cells) {
-        e = adg::tv_stats_prepare(m->cells, m->part, stream);
-        if (e) return cuda_fail((cudaError_t)e, "tv_indicator prepare");
+        int e = adg::tv_stats_prepare(m->N, m->cells, m->part, stream);
+        if (e) return cuda_fail((cudaError_t)e, "tv_indicator: statistics weights");
         m->tv_prep_cells = m->cells;
     }
-    e = adg::launch_tv_stats_multi(tvbuf, m->cells, T_r, T_c, m->part, m->stats, flags, stream);
-    if (e) return cuda_fail((cudaError_t)e, "tv_indicator stats");
+    return ADG_OK;
+}
+
+// statistics from the block triples in m->part, flags, optional host copy of (mean, sigma)
+static int tv_finish(adg_mesh* m, const double* tvbuf, double T_r, double T_c, int8_t* flags, double* stats,
+                     void* stream) {
+    const adg::TvStatsArgs st = adg::tv_stats_args(m->N, m->cells, m->part);
+    int e = adg::launch_tv_stats_flags(tvbuf, st, T_r, T_c, m->stats, flags, stream);
+    if (e) return cuda_fail((cudaError_t)e, "tv_indicator statistics");
     if (stats) {
         ADG_CK(cudaMemcpyAsync(stats, m->stats, 16, cudaMemcpyDeviceToHost, (cudaStream_t)stream), "tv stats copy");
         ADG_CK(cudaStreamSynchronize((cudaStream_t)stream), "tv stats sync");
@@ -607,13 +612,17 @@ int adg_tv_indicator(adg_mesh* m, int var, double T_r, double T_c, double* tv, i
     if (!m) return fail(ADG_EINVAL, "tv_indicator: NULL mesh");
     if (int rc = tv_check(m, var, T_r, T_c)) return rc;
     if (int rc = set_device(m)) return rc;
+    if (int rc = tv_prepare(m, stream)) return rc;
     double* tvbuf = tv ? tv : m->tv;
-    int e = m->amr ? adg::amr_tv_cells(m, var, tvbuf, stream)
-            : m->d.precision == ADG_PREC_FP64
-                ? adg::launch_tv_cells(m->N, m->u, tvbuf, m->cells, var, m->B, m->P, stream)
-                : adg::launch_tv_cells_mixed(m->N, m->u, tvbuf, m->cells, var, m->Bf, m->Pf, m->mbg,
-                                             m->d.theta0, m->P.Rcp, stream);
-    if (e) return cuda_fail((cudaError_t)e, "tv_indicator cells");
+    if (m->amr) {
+        if (int rc = adg::amr_tv_cells(m, var, tvbuf, m->part, stream)) return rc;
+    } else {
+        int e = m->d.precision == ADG_PREC_FP64
+                    ? adg::launch_tv_cells(m->N, m->u, tvbuf, m->part, m->cells, var, m->B, m->P, stream)
+                    : adg::launch_tv_cells_mixed(m->N, m->u, tvbuf, m->part, m->cells, var, m->Bf, m->Pf, m->mbg,
+                                                 m->d.theta0, m->P.Rcp, stream);
+        if (e) return cuda_fail((cudaError_t)e, "tv_indicator cells");
+    }
     return tv_finish(m, tvbuf, T_r, T_c, flags, stats, stream);
 }
 
@@ -625,9 +634,12 @@ int adg_step_tv(adg_mesh* m, double dt, int var, double T_r, double T_c, double*
         if (int rc = adg_step(m, dt, stream)) return rc;
         return adg_tv_indicator(m, var, T_r, T_c, tv, flags, stats, stream);
     }
+    if (int rc = set_device(m)) return rc;
+    if (int rc = tv_prepare(m, stream)) return rc;
     if (int rc = adg_predictor(m, dt, stream)) return rc;
     adg::TvEpilogue epi;
     epi.tv = tv ? tv : m->tv;
+    epi.part = m->part;
     epi.var = var;
     epi.theta0 = m->d.theta0;
     epi.Rcp = m->P.Rcp;
@@ -699,8 +711,9 @@ int adg_tv_flags(adg_mesh* m, const double* tv, double count, double mean, doubl
     if (!(count > 0.0) || !(M2 >= 0.0) || !(T_r > T_c)) return fail(ADG_EINVAL, "tv_flags: bad statistics");
     if (int rc = set_device(m)) return rc;
     const double ms[2] = {mean, std::sqrt(M2 / count)};  // population sigma, as the device forms it
-    ADG_CK(cudaMemcpyAsync(m->part, ms, sizeof(ms), cudaMemcpyHostToDevice, (cudaStream_t)stream), "tv_flags");
-    int e = adg::launch_tv_flags_given(tv, m->cells, m->part, T_r, T_c, flags, stream);
+    double* given = m->stats + 2;  // the two spare slots of the statistics buffer
+    ADG_CK(cudaMemcpyAsync(given, ms, sizeof(ms), cudaMemcpyHostToDevice, (cudaStream_t)stream), "tv_flags");
+    int e = adg::launch_tv_flags_given(tv, m->cells, given, T_r, T_c, flags, stream);
     if (e) return cuda_fail((cudaError_t)e, "tv_flags launch");
     // the host pair must outlive the copy
     ADG_CK(cudaStreamSynchronize((cudaStream_t)stream), "tv_flags sync");

@@ -172,7 +172,10 @@ k_corrector_fp64(double* __restrict__ u, const double* __restrict__ rvol,
         __shared__ double fs[CPB][n2], red[CPB][n2];
         const double z = P.y0 + (iy + B.xi[j]) * P.hy;
         const double f = epi.var == ADG_TV_THETA ? theta_of(unew, z, P) : unew[0];
-        tv_cell<N, double>(f, 0.0, node, i, j, B, P.inv_hx, P.inv_hy, fs[cl], red[cl], active, epi.tv + cell);
+        static_assert(CPB == tv_cpb(N), "the TV statistics combine blocks of tv_cpb(N) cells");
+        const double r =
+            tv_cell<N, double>(f, 0.0, node, i, j, B, P.inv_hx, P.inv_hy, fs[cl], red[cl], active, epi.tv + cell);
+        tv_block_triple<CPB>(r, node == 0, cl, min(CPB, cells - (int)blockIdx.x * CPB), epi.part);
     }
 }
 

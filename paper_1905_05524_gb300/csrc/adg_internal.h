@@ -97,10 +97,26 @@ constexpr int kBatchCandidates = 3;  // tile-size candidates the autotuner times
 
 // Kernel launchers (adg_fp64.cu, adg_mixed.cu, adg_tv.cu).  They return a
 // cudaError_t value as int.
+// Cells per block of every kernel that produces TV values (the TV kernels
+// and the correctors): each such block also publishes the (count, mean, M2)
+// triple of its cells, and the statistics combine these block triples.
+constexpr int tv_cpb(int N) { return N == 1 ? 32 : N == 2 ? 16 : N == 3 ? 8 : N <= 5 ? 4 : 2; }
+constexpr int kTvThreads = 256;  // threads per block of the statistics-and-flags kernel
+
+// Where the statistics kernel finds the block triples and the Chan weights
+// of its fixed combine order (tv_stats_prepare).
+struct TvStatsArgs {
+    const double* part = nullptr;   // [3 * nblk] block triples (count, mean, M2)
+    const double* wfold = nullptr;  // [2 * nblk] weights of the per-thread left folds
+    const double* wtree = nullptr;  // [2 * kTvThreads] weights of the tree over the threads
+    int nblk = 0, per = 0, cells = 0;
+};
+
 // TV indicator evaluated by the corrector on the state it has just updated
 // (the corrector launchers take nullptr for none).
 struct TvEpilogue {
     double* tv = nullptr;            // [cells] output
+    double* part = nullptr;          // [3 * tv_stats_blocks] block triples output
     int var = 0;                     // ADG_TV_THETA or ADG_TV_RHO
     double theta0 = 0.0, Rcp = 0.0;  // background potential temperature, R/c_p
 };
@@ -124,23 +140,26 @@ int launch_batch_mixed(int N, int cand, int phase, const MixedInst* insts, const
 int launch_step_adjoint_fp64(int N, const double* u, const double* lam, double* lam_out, const double* trace,
                              double* trace_bar, int cells, double dt, const Basis& B, const Phys& P,
                              const Background& bg, void* stream);
-int launch_tv_cells(int N, const double* u, double* tv, int cells, int var, const Basis& B,
+// TV per cell, plus the (count, mean, M2) triple of every block's cells into part
+int launch_tv_cells(int N, const double* u, double* tv, double* part, int cells, int var, const Basis& B,
                     const Phys& P, void* stream);
-int launch_tv_cells_mixed(int N, const double* u, double* tv, int cells, int var, const BasisF& B,
-                          const PhysF& P, const MixedBg& bg, double theta0, double Rcp, void* stream);
-// multi-block deterministic statistics: `part` is scratch of 3 * tv_stats_partials(cells) doubles;
-// stats_dev is [mean, sigma, ticket] (the ticket slot zeroed at allocation)
-int tv_stats_chunk(int cells);
-int tv_stats_partials(int cells);
-size_t tv_stats_scratch_doubles();  // size of `part`, whatever the cell count
-// Chan weights of the statistics tree for `cells` cells into `part` (host
-// division, one copy; synchronises `stream`); needed once per cell count
-int tv_stats_prepare(int cells, double* part, void* stream);
+int launch_tv_cells_mixed(int N, const double* u, double* tv, double* part, int cells, int var,
+                          const BasisF& B, const PhysF& P, const MixedBg& bg, double theta0, double Rcp,
+                          void* stream);
+// Statistics scratch `part`: [3 nblk] block triples | [2 nblk] fold weights |
+// [2 kTvThreads] tree weights, nblk = tv_stats_blocks(N, cells).
+int tv_stats_blocks(int N, int cells);
+size_t tv_stats_scratch_doubles(int N, int cells);
+// Chan weights of the combine order for (N, cells) into `part` (host
+// division, one copy; synchronises `stream`); needed once per cell count.
+int tv_stats_prepare(int N, int cells, double* part, void* stream);
+TvStatsArgs tv_stats_args(int N, int cells, const double* part);
+// mean and sigma from the block triples into stats_dev[0..1]; flags if not null
+int launch_tv_stats_flags(const double* tv, const TvStatsArgs& st, double T_r, double T_c, double* stats_dev,
+                          int8_t* flags, void* stream);
 // flags from (mean, sigma) held in device memory at stats_dev
 int launch_tv_flags_given(const double* tv, int cells, const double* stats_dev, double T_r, double T_c,
                           int8_t* flags, void* stream);
-int launch_tv_stats_multi(const double* tv, int cells, double T_r, double T_c, double* part,
-                          double* stats_dev, int8_t* flags, void* stream);
 int launch_max_speed(int N, const double* u, double* partial, int cells, const Basis& B,
                      const Phys& P, int* nblocks_out, void* stream);
 int launch_init_scenario(int N, double* u, int cells, int kind, double A, double a, double xc,

@@ -17,9 +17,9 @@ struct adg_mesh {
     double* trace = nullptr;
     double* trace_bar = nullptr; // adjoint of the traces (allocated on first adg_step_adjoint)
     double* tv = nullptr;
-    double* stats = nullptr;     // device [4]: mean, sigma, ticket of the one-launch statistics
-    double* part = nullptr;      // device partial (count, mean, M2) triples of the TV statistics + tree weights
-    int tv_prep_cells = -1;      // cell count the tree weights in `part` were prepared for
+    double* stats = nullptr;     // device [4]: mean, sigma; given mean, sigma (adg_tv_flags)
+    double* part = nullptr;      // device TV statistics scratch: block triples and combine weights
+    int tv_prep_cells = -1;      // cell count the combine weights in `part` were prepared for
     double* speed = nullptr;     // device partial maxima
     int speed_blocks = 0;
     int* flag = nullptr;         // device int
@@ -54,7 +54,7 @@ int amr_setup(adg_mesh* m);
 void amr_free(adg_mesh* m);
 int amr_predictor(adg_mesh* m, double dt, void* stream);
 int amr_corrector(adg_mesh* m, double dt, void* stream);
-int amr_tv_cells(adg_mesh* m, int var, double* tv, void* stream);
+int amr_tv_cells(adg_mesh* m, int var, double* tv, double* part, void* stream);
 int amr_max_speed(adg_mesh* m, double* lam_max, void* stream);
 int amr_init_scenario(adg_mesh* m, const adg_scenario* s, void* stream);
 }  // namespace adg

@@ -594,8 +594,10 @@ __device__ __forceinline__ void corrector_mixed_body(double* __restrict__ u, con
         const float z = P.y0 + (iy + B.xi[j]) * P.hy;
         const float f = tv_field_mixed(unew, epi.var, bg.rb[row], bg.Eb[row], bg.pb[row], z, P, (float)epi.theta0,
                                        (float)(1.0 - epi.Rcp));
-        tv_cell<N, float>(f, epi.var == ADG_TV_THETA ? 0.f : bg.dzr[row], node, i, j, B, P.inv_hx, P.inv_hy,
-                          fs[cl], red[cl], active, epi.tv + cell);
+        static_assert(CPB == tv_cpb(N), "the TV statistics combine blocks of tv_cpb(N) cells");
+        const double r = tv_cell<N, float>(f, epi.var == ADG_TV_THETA ? 0.f : bg.dzr[row], node, i, j, B,
+                                           P.inv_hx, P.inv_hy, fs[cl], red[cl], active, epi.tv + cell);
+        tv_block_triple<CPB>(r, node == 0, cl, min(CPB, cells - c0), epi.part);
     }
 }
 

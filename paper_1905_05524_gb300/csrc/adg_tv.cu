@@ -5,9 +5,9 @@
 // (potential temperature, Sec. 4.2) or rho at the nodes, derivatives by the
 // nodal derivative matrix (adg_tv_cell.cuh).  Mean and population standard
 // deviation over all cells follow Chan, Golub and LeVeque's pairwise update
-// (cited by the paper for a parallel, stable evaluation): contiguous chunks
-// are reduced exactly (two-pass) per block, then the partial (count, mean,
-// M2) triples are combined in a fixed binary tree, so the result is
+// (cited by the paper for a parallel, stable evaluation): every block that
+// produces TV values reduces its own cells exactly (two-pass), then the
+// block triples are combined in a fixed order, so the result is
 // deterministic.
 #include <cuda_runtime.h>
 
@@ -24,12 +24,12 @@ namespace adg {
 template <int N>
 struct TvCfg {
     static constexpr int n = N + 1;
-    static constexpr int cpb = N == 1 ? 32 : N == 2 ? 16 : N == 3 ? 8 : N <= 5 ? 4 : 2;
+    static constexpr int cpb = tv_cpb(N);
 };
 
 template <int N, int CPB>
 __global__ void __launch_bounds__(CPB*(N + 1) * (N + 1))
-k_tv_cells(const double* __restrict__ u, double* __restrict__ tv, int cells, int var,
+k_tv_cells(const double* __restrict__ u, double* __restrict__ tv, double* __restrict__ part, int cells, int var,
            const Basis B, const Phys P) {
     constexpr int n = N + 1, n2 = n * n, SL = 4 * n2;
     __shared__ double fs[CPB][n2];
@@ -47,15 +47,17 @@ k_tv_cells(const double* __restrict__ u, double* __restrict__ tv, int cells, int
     for (int v = 0; v < 4; ++v) q[v] = uc[v * n2 + node];
     const double z = P.y0 + (iy + B.xi[j]) * P.hy;
     const double f = var == ADG_TV_THETA ? theta_of(q, z, P) : q[0];
-    tv_cell<N, double>(f, 0.0, node, i, j, B, P.inv_hx, P.inv_hy, fs[cl], red[cl], active, tv + cell);
+    const double r = tv_cell<N, double>(f, 0.0, node, i, j, B, P.inv_hx, P.inv_hy, fs[cl], red[cl], active,
+                                        tv + cell);
+    tv_block_triple<CPB>(r, node == 0, cl, min(CPB, cells - (int)blockIdx.x * CPB), part);
 }
 
 // Mixed-precision TV: FP64 perturbation split, FP32 field and sums
 // (tv_field_mixed).
 template <int N, int CPB>
 __global__ void __launch_bounds__(CPB*(N + 1) * (N + 1))
-k_tv_cells_mixed(const double* __restrict__ u, double* __restrict__ tv, int cells, int var,
-                 const BasisF B, const PhysF P, const MixedBg bg, float theta0, float one_m_kappa) {
+k_tv_cells_mixed(const double* __restrict__ u, double* __restrict__ tv, double* __restrict__ part, int cells,
+                 int var, const BasisF B, const PhysF P, const MixedBg bg, float theta0, float one_m_kappa) {
     constexpr int n = N + 1, n2 = n * n, SL = 4 * n2;
     __shared__ float fs[CPB][n2];
     __shared__ float red[CPB][n2];
@@ -73,121 +75,86 @@ k_tv_cells_mixed(const double* __restrict__ u, double* __restrict__ tv, int cell
     for (int v = 0; v < 4; ++v) q[v] = uc[v * n2 + node];
     const float z = P.y0 + (iy + B.xi[j]) * P.hy;
     const float f = tv_field_mixed(q, var, bg.rb[row], bg.Eb[row], bg.pb[row], z, P, theta0, one_m_kappa);
-    tv_cell<N, float>(f, var == ADG_TV_THETA ? 0.f : bg.dzr[row], node, i, j, B, P.inv_hx, P.inv_hy, fs[cl],
-                      red[cl], active, tv + cell);
+    const double r = tv_cell<N, float>(f, var == ADG_TV_THETA ? 0.f : bg.dzr[row], node, i, j, B, P.inv_hx,
+                                       P.inv_hy, fs[cl], red[cl], active, tv + cell);
+    tv_block_triple<CPB>(r, node == 0, cl, min(CPB, cells - (int)blockIdx.x * CPB), part);
 }
 
-// Statistics in one launch.  Block b owns the contiguous chunk of cells
-// [b*chunk, min((b+1)*chunk, cells)); it forms the chunk's count, mean and M2
-// by an exact two-pass reduction in a fixed order and publishes the triple.
-// The last block to finish (an atomic ticket taken after a fence; nothing
-// waits) combines the chunk triples with Chan et al.'s pairwise update in a
-// fixed binary tree -- the result does not depend on which block finishes
-// last -- writes mean and sigma and re-arms the ticket for the next launch.
-// The tree's shape depends only on the cell count, so its weights
-// n_b/(n_a+n_b) and n_a n_b/(n_a+n_b) are divided out once on the host
-// (`tv_stats_prepare`, the same IEEE quotients) and the device tree runs on
-// multiplies and adds: FP64 division is a long dependent chain on this part.
-constexpr int kPartThreads = 256;
-constexpr int kMaxPartials = 1024;
-constexpr int kFactorOffset = 3 * kMaxPartials;  // Chan weights after the triples in `part`
+// Statistics of the TV values and the flags, one launch.  The TV-producing
+// kernels have left one exact (count, mean, M2) triple per block of cells.
+// Every block of this kernel combines all of them with Chan et al.'s
+// pairwise update in the same fixed order -- thread t folds triples
+// [t per, (t+1) per) left to right, then a binary tree joins the thread
+// results -- so every block holds bitwise the same mean and sigma without
+// waiting on any other block; then it flags its own cells.  The weights
+// n_b/(n_a+n_b) and n_a n_b/(n_a+n_b) of every combine depend only on the
+// cell count and come divided out by the host (tv_stats_prepare, the same
+// IEEE quotients): the device runs multiplies and adds, since FP64 division
+// is a long dependent chain on this part.
+constexpr int kPartThreads = kTvThreads;
 
-// fixed-order block sum: warp shuffles, then the 8 warp sums by warp 0
-__device__ __forceinline__ double block_sum_256(double v, double* sh) {
-    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if (lane == 0) sh[w] = v;
-    __syncthreads();
-    if (w == 0) {
-        v = lane < kPartThreads / 32 ? sh[lane] : 0.0;
-#pragma unroll
-        for (int o = 4; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-        if (lane == 0) sh[8] = v;
-    }
-    __syncthreads();
-    const double r = sh[8];
-    __syncthreads();
-    return r;
-}
-
-__global__ void __launch_bounds__(kPartThreads)
-k_tv_stats(const double* __restrict__ tv, int cells, int chunk, double* __restrict__ part,
-           double* __restrict__ stats, unsigned* __restrict__ ticket) {
-    __shared__ double sh[9];
-    __shared__ double smean[kMaxPartials], sm2[kMaxPartials];
-    __shared__ bool last;
-    const int t = threadIdx.x, b = blockIdx.x, nb = gridDim.x;
-    const int lo = b * chunk, hi = min(cells, lo + chunk);
-    double s = 0.0;
-    for (int c = lo + t; c < hi; c += kPartThreads) s += tv[c];
-    const double sum = block_sum_256(s, sh);
-    if (t == 0) sh[0] = sum / (double)(hi - lo);  // every chunk holds >= 1 cell
-    __syncthreads();
-    const double mean = sh[0];
-    __syncthreads();
-    double q = 0.0;
-    for (int c = lo + t; c < hi; c += kPartThreads) {
-        const double d = tv[c] - mean;
-        q += d * d;
-    }
-    const double m2 = block_sum_256(q, sh);
-    if (t == 0) {
-        part[3 * b + 0] = (double)(hi - lo);
-        part[3 * b + 1] = mean;
-        part[3 * b + 2] = m2;
-        __threadfence();
-        last = atomicAdd(ticket, 1u) == (unsigned)(nb - 1);
-    }
-    __syncthreads();
-    if (!last) return;
-    __threadfence();
-    int top = 1;
-    while (top < nb) top <<= 1;
-    for (int a = t; a < top; a += kPartThreads) {
-        smean[a] = a < nb ? __ldcg(part + 3 * a + 1) : 0.0;
-        sm2[a] = a < nb ? __ldcg(part + 3 * a + 2) : 0.0;
-    }
-    __syncthreads();
-    const double* fac = part + kFactorOffset;
-    for (int stride = top / 2, off = 0; stride > 0; off += stride, stride >>= 1) {
-        for (int a = t; a < stride; a += kPartThreads) {
-            // weights are zero where the right-hand entry is empty padding
-            const double f1 = __ldcg(fac + 2 * (off + a)), f2 = __ldcg(fac + 2 * (off + a) + 1);
-            const double d = smean[a + stride] - smean[a];
-            smean[a] = smean[a] + d * f1;
-            sm2[a] = sm2[a] + sm2[a + stride] + d * d * f2;
-        }
-        __syncthreads();
-    }
-    if (t == 0) {
-        stats[0] = smean[0];
-        stats[1] = sqrt(sm2[0] / (double)cells);
-        *ticket = 0u;  // every block of this launch has taken its ticket
-    }
-}
-
-// Flags from (mean, sigma) in device memory, one cell per thread: refine if
-// TV >= mean + T_r sigma, coarsen if TV < mean + T_c sigma, keep all when
-// sigma <= 1e-12 |mean| (reading F1).  The comparisons use the IEEE-754
+// Flag of one cell: refine if TV >= mean + T_r sigma, coarsen if
+// TV < mean + T_c sigma, keep all when sigma <= 1e-12 |mean| (reading F1).
+// The thresholds round product and sum separately (no contraction), as
+// mean + T * sigma is usually written; the comparisons use the IEEE-754
 // order of non-negative doubles as 64-bit integers (TV >= 0): exact, and off
-// the narrow FP64 pipe.
-__global__ void __launch_bounds__(kPartThreads)
-k_tv_flag_cells(const double* __restrict__ tv, int cells, const double* __restrict__ stats, double T_r,
-                double T_c, int8_t* __restrict__ flags) {
-    const int c = blockIdx.x * kPartThreads + threadIdx.x;
-    if (c >= cells) return;
-    const double mu = stats[0], sig = stats[1];
-    // product and sum rounded separately (no contraction), as mean + T * sigma is usually written
+// the narrow FP64 pipe.  NaN compares false both ways.
+__device__ __forceinline__ int8_t tv_flag_of(double x, double mu, double sig, double T_r, double T_c) {
     const double thr_r = __dadd_rn(mu, __dmul_rn(T_r, sig)), thr_c = __dadd_rn(mu, __dmul_rn(T_c, sig));
-    // NaN statistics compare false both ways: no flags
     const bool flat = sig <= 1e-12 * fabs(mu) || !(thr_r == thr_r) || !(thr_c == thr_c);
-    const long long bx = __double_as_longlong(tv[c]);
+    const long long bx = __double_as_longlong(x);
     const bool nan = (bx & 0x7fffffffffffffffLL) > 0x7ff0000000000000LL;
     // a threshold <= 0 lies at or below every TV
     const bool ref = thr_r <= 0.0 || bx >= __double_as_longlong(thr_r);
     const bool coa = thr_c > 0.0 && bx < __double_as_longlong(thr_c);
-    flags[c] = (flat || nan) ? (int8_t)0 : ref ? (int8_t)1 : (coa ? (int8_t)-1 : (int8_t)0);
+    return (flat || nan) ? (int8_t)0 : ref ? (int8_t)1 : (coa ? (int8_t)-1 : (int8_t)0);
+}
+
+__global__ void __launch_bounds__(kTvThreads)
+k_tv_stats_flags(const double* __restrict__ tv, const TvStatsArgs st, double T_r, double T_c,
+                 double* __restrict__ stats, int8_t* __restrict__ flags) {
+    __shared__ double tm[kTvThreads], t2[kTvThreads];
+    const int t = threadIdx.x;
+    double m = 0.0, m2 = 0.0;
+    const int k0 = t * st.per, k1 = min(k0 + st.per, st.nblk);
+    if (k0 < k1) {
+        m = st.part[3 * k0 + 1];
+        m2 = st.part[3 * k0 + 2];
+        for (int k = k0 + 1; k < k1; ++k) {
+            const double d = st.part[3 * k + 1] - m;
+            m = m + d * st.wfold[2 * k];
+            m2 = m2 + st.part[3 * k + 2] + d * d * st.wfold[2 * k + 1];
+        }
+    }
+    tm[t] = m;
+    t2[t] = m2;
+    __syncthreads();
+    for (int stride = kTvThreads / 2, off = 0; stride > 0; off += stride, stride >>= 1) {
+        if (t < stride) {
+            // weights are zero where the right-hand entry holds no cells
+            const double d = tm[t + stride] - tm[t];
+            tm[t] = tm[t] + d * st.wtree[2 * (off + t)];
+            t2[t] = t2[t] + t2[t + stride] + d * d * st.wtree[2 * (off + t) + 1];
+        }
+        __syncthreads();
+    }
+    const double mu = tm[0];
+    const double sig = sqrt(t2[0] / (double)st.cells);
+    if (blockIdx.x == 0 && t == 0 && stats) {
+        stats[0] = mu;
+        stats[1] = sig;
+    }
+    if (!flags) return;
+    for (int c = blockIdx.x * kTvThreads + t; c < st.cells; c += gridDim.x * kTvThreads)
+        flags[c] = tv_flag_of(tv[c], mu, sig, T_r, T_c);
+}
+
+// Flags from (mean, sigma) held in device memory, one cell per thread.
+__global__ void __launch_bounds__(kPartThreads)
+k_tv_flag_cells(const double* __restrict__ tv, int cells, const double* __restrict__ stats, double T_r,
+                double T_c, int8_t* __restrict__ flags) {
+    const int c = blockIdx.x * kPartThreads + threadIdx.x;
+    if (c < cells) flags[c] = tv_flag_of(tv[c], stats[0], stats[1], T_r, T_c);
 }
 
 // ---------------------------------------------------------------- scenarios
@@ -293,25 +260,25 @@ __global__ void k_check_finite(const double* __restrict__ u, size_t count, int* 
 
 // ------------------------------------------------------------------ launchers
 template <int N>
-static int tv_cells_n(const double* u, double* tv, int cells, int var, const Basis& B,
+static int tv_cells_n(const double* u, double* tv, double* part, int cells, int var, const Basis& B,
                       const Phys& P, cudaStream_t s) {
     using C = TvCfg<N>;
     const int blocks = (cells + C::cpb - 1) / C::cpb;
-    k_tv_cells<N, C::cpb><<<blocks, C::cpb * C::n * C::n, 0, s>>>(u, tv, cells, var, B, P);
+    k_tv_cells<N, C::cpb><<<blocks, C::cpb * C::n * C::n, 0, s>>>(u, tv, part, cells, var, B, P);
     return (int)cudaGetLastError();
 }
 
-int launch_tv_cells(int N, const double* u, double* tv, int cells, int var, const Basis& B,
+int launch_tv_cells(int N, const double* u, double* tv, double* part, int cells, int var, const Basis& B,
                     const Phys& P, void* stream) {
     cudaStream_t s = (cudaStream_t)stream;
     switch (N) {
-        case 1: return tv_cells_n<1>(u, tv, cells, var, B, P, s);
-        case 2: return tv_cells_n<2>(u, tv, cells, var, B, P, s);
-        case 3: return tv_cells_n<3>(u, tv, cells, var, B, P, s);
-        case 4: return tv_cells_n<4>(u, tv, cells, var, B, P, s);
-        case 5: return tv_cells_n<5>(u, tv, cells, var, B, P, s);
-        case 6: return tv_cells_n<6>(u, tv, cells, var, B, P, s);
-        case 7: return tv_cells_n<7>(u, tv, cells, var, B, P, s);
+        case 1: return tv_cells_n<1>(u, tv, part, cells, var, B, P, s);
+        case 2: return tv_cells_n<2>(u, tv, part, cells, var, B, P, s);
+        case 3: return tv_cells_n<3>(u, tv, part, cells, var, B, P, s);
+        case 4: return tv_cells_n<4>(u, tv, part, cells, var, B, P, s);
+        case 5: return tv_cells_n<5>(u, tv, part, cells, var, B, P, s);
+        case 6: return tv_cells_n<6>(u, tv, part, cells, var, B, P, s);
+        case 7: return tv_cells_n<7>(u, tv, part, cells, var, B, P, s);
     }
     return (int)cudaErrorInvalidValue;
 }
@@ -366,78 +333,102 @@ int launch_max_speed(int N, const double* u, double* partial, int cells, const B
 }
 
 template <int N>
-static int tv_cells_mixed_n(const double* u, double* tv, int cells, int var, const BasisF& B,
+static int tv_cells_mixed_n(const double* u, double* tv, double* part, int cells, int var, const BasisF& B,
                             const PhysF& P, const MixedBg& bg, float theta0, float omk, cudaStream_t s) {
     using C = TvCfg<N>;
     const int blocks = (cells + C::cpb - 1) / C::cpb;
-    k_tv_cells_mixed<N, C::cpb><<<blocks, C::cpb * C::n * C::n, 0, s>>>(u, tv, cells, var, B, P, bg, theta0, omk);
+    k_tv_cells_mixed<N, C::cpb>
+        <<<blocks, C::cpb * C::n * C::n, 0, s>>>(u, tv, part, cells, var, B, P, bg, theta0, omk);
     return (int)cudaGetLastError();
 }
 
-int launch_tv_cells_mixed(int N, const double* u, double* tv, int cells, int var, const BasisF& B,
-                          const PhysF& P, const MixedBg& bg, double theta0, double Rcp, void* stream) {
+int launch_tv_cells_mixed(int N, const double* u, double* tv, double* part, int cells, int var,
+                          const BasisF& B, const PhysF& P, const MixedBg& bg, double theta0, double Rcp,
+                          void* stream) {
     cudaStream_t s = (cudaStream_t)stream;
     const float t0 = (float)theta0, omk = (float)(1.0 - Rcp);
     switch (N) {
-        case 1: return tv_cells_mixed_n<1>(u, tv, cells, var, B, P, bg, t0, omk, s);
-        case 2: return tv_cells_mixed_n<2>(u, tv, cells, var, B, P, bg, t0, omk, s);
-        case 3: return tv_cells_mixed_n<3>(u, tv, cells, var, B, P, bg, t0, omk, s);
-        case 4: return tv_cells_mixed_n<4>(u, tv, cells, var, B, P, bg, t0, omk, s);
-        case 5: return tv_cells_mixed_n<5>(u, tv, cells, var, B, P, bg, t0, omk, s);
-        case 6: return tv_cells_mixed_n<6>(u, tv, cells, var, B, P, bg, t0, omk, s);
-        case 7: return tv_cells_mixed_n<7>(u, tv, cells, var, B, P, bg, t0, omk, s);
+        case 1: return tv_cells_mixed_n<1>(u, tv, part, cells, var, B, P, bg, t0, omk, s);
+        case 2: return tv_cells_mixed_n<2>(u, tv, part, cells, var, B, P, bg, t0, omk, s);
+        case 3: return tv_cells_mixed_n<3>(u, tv, part, cells, var, B, P, bg, t0, omk, s);
+        case 4: return tv_cells_mixed_n<4>(u, tv, part, cells, var, B, P, bg, t0, omk, s);
+        case 5: return tv_cells_mixed_n<5>(u, tv, part, cells, var, B, P, bg, t0, omk, s);
+        case 6: return tv_cells_mixed_n<6>(u, tv, part, cells, var, B, P, bg, t0, omk, s);
+        case 7: return tv_cells_mixed_n<7>(u, tv, part, cells, var, B, P, bg, t0, omk, s);
     }
     return (int)cudaErrorInvalidValue;
 }
 
-int tv_stats_partials(int cells) {
-    const int chunk = tv_stats_chunk(cells);
-    return (cells + chunk - 1) / chunk;
+// ---------------------------------------------------------- statistics setup
+int tv_stats_blocks(int N, int cells) { return (cells + tv_cpb(N) - 1) / tv_cpb(N); }
+
+size_t tv_stats_scratch_doubles(int N, int cells) {
+    return 5 * (size_t)tv_stats_blocks(N, cells) + 2 * (size_t)kTvThreads;
 }
 
-int tv_stats_chunk(int cells) {
-    int chunk = 256;
-    while ((cells + chunk - 1) / chunk > kMaxPartials) chunk *= 2;
-    return chunk;
+static int tv_fold_per(int nblk) { return (nblk + kTvThreads - 1) / kTvThreads; }
+
+TvStatsArgs tv_stats_args(int N, int cells, const double* part) {
+    TvStatsArgs a;
+    a.nblk = tv_stats_blocks(N, cells);
+    a.per = tv_fold_per(a.nblk);
+    a.cells = cells;
+    a.part = part;
+    a.wfold = part + 3 * (size_t)a.nblk;
+    a.wtree = part + 5 * (size_t)a.nblk;
+    return a;
 }
 
-// Chan weights of the statistics tree for `cells` cells into part + kFactorOffset.
-int tv_stats_prepare(int cells, double* part, void* stream) {
-    const int chunk = tv_stats_chunk(cells);
-    const int nb = (cells + chunk - 1) / chunk;
-    int top = 1;
-    while (top < nb) top <<= 1;
-    std::vector<double> cnt(top, 0.0), fac(2 * (size_t)std::max(top - 1, 1), 0.0);
-    for (int b = 0; b < nb; ++b) cnt[b] = (double)std::min(chunk, cells - b * chunk);
-    for (int stride = top / 2, off = 0; stride > 0; off += stride, stride >>= 1) {
+// Weights n_b/(n_a+n_b) and n_a n_b/(n_a+n_b) of every combine of
+// k_tv_stats_flags, from the block cell counts alone (IEEE division here).
+int tv_stats_prepare(int N, int cells, double* part, void* stream) {
+    const int cpb = tv_cpb(N), nblk = tv_stats_blocks(N, cells), per = tv_fold_per(nblk);
+    std::vector<double> w(2 * (size_t)nblk + 2 * (size_t)kTvThreads, 0.0);
+    double* wfold = w.data();
+    double* wtree = w.data() + 2 * (size_t)nblk;
+    std::vector<double> tcnt(kTvThreads, 0.0);
+    for (int t = 0; t < kTvThreads; ++t) {
+        const int k0 = t * per, k1 = std::min(k0 + per, nblk);
+        double na = 0.0;
+        for (int k = k0; k < k1; ++k) {
+            const double nb = (double)std::min(cpb, cells - k * cpb);
+            if (k > k0) {
+                wfold[2 * k] = nb / (na + nb);
+                wfold[2 * k + 1] = na * nb / (na + nb);
+            }
+            na += nb;
+        }
+        tcnt[t] = na;
+    }
+    for (int stride = kTvThreads / 2, off = 0; stride > 0; off += stride, stride >>= 1) {
         for (int a = 0; a < stride; ++a) {
-            const double na = cnt[a], nbb = cnt[a + stride], nn = na + nbb;
-            if (nbb > 0.0) {
-                fac[2 * (off + a)] = nbb / nn;
-                fac[2 * (off + a) + 1] = na * nbb / nn;
-                cnt[a] = nn;
+            const double na = tcnt[a], nb = tcnt[a + stride];
+            if (nb > 0.0) {
+                wtree[2 * (off + a)] = nb / (na + nb);
+                wtree[2 * (off + a) + 1] = na * nb / (na + nb);
+                tcnt[a] = na + nb;
             }
         }
     }
     cudaStream_t s = (cudaStream_t)stream;
-    cudaError_t e = cudaMemcpyAsync(part + kFactorOffset, fac.data(), fac.size() * 8, cudaMemcpyHostToDevice, s);
+    cudaError_t e = cudaMemcpyAsync(part + 3 * (size_t)nblk, w.data(), w.size() * 8, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // the host table must outlive the copy
     return (int)e;
 }
 
-size_t tv_stats_scratch_doubles() { return (size_t)kFactorOffset + 2 * (size_t)kMaxPartials; }
-
-int launch_tv_stats_multi(const double* tv, int cells, double T_r, double T_c, double* part,
-                          double* stats_dev, int8_t* flags, void* stream) {
-    cudaStream_t s = (cudaStream_t)stream;
-    const int chunk = tv_stats_chunk(cells);
-    const int np = (cells + chunk - 1) / chunk;
-    // stats_dev holds mean, sigma and (third slot) the ticket counter
-    k_tv_stats<<<np, kPartThreads, 0, s>>>(tv, cells, chunk, part, stats_dev,
-                                           reinterpret_cast<unsigned*>(stats_dev + 2));
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess || !flags) return (int)e;
-    return launch_tv_flags_given(tv, cells, stats_dev, T_r, T_c, flags, stream);
+int launch_tv_stats_flags(const double* tv, const TvStatsArgs& st, double T_r, double T_c, double* stats_dev,
+                          int8_t* flags, void* stream) {
+    // with flags: enough blocks for one cell per thread, at most one per SM
+    // (every block repeats the combine); without: a single block
+    int nb = 1;
+    if (flags) {
+        int dev = 0, sms = 1;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        nb = std::max(1, std::min((st.cells + kTvThreads - 1) / kTvThreads, sms));
+    }
+    k_tv_stats_flags<<<nb, kTvThreads, 0, (cudaStream_t)stream>>>(tv, st, T_r, T_c, stats_dev, flags);
+    return (int)cudaGetLastError();
 }
 
 int launch_tv_flags_given(const double* tv, int cells, const double* stats_dev, double T_r, double T_c,

@@ -49,11 +49,12 @@ __device__ __forceinline__ double tv_to_f64(float x) { return f32_to_f64(x); }
 // TV of this thread's cell from the field value f at its node.  fs, red: this
 // cell's two n^2 scratch rows in shared memory; fy_add is added to the
 // y-derivative (background gradient).  Every thread of the block must call
-// it (three barriers); node 0 of an active cell writes *out.  Sums run over
-// rows first (one thread per row), then over the row sums.
+// it (three barriers); node 0 of an active cell writes *out and gets the
+// value back (zero elsewhere).  Sums run over rows first (one thread per
+// row), then over the row sums.
 template <int N, typename T, typename BT>
-__device__ __forceinline__ void tv_cell(T f, T fy_add, int node, int i, int j, const BT& B, T inv_hx, T inv_hy,
-                                        T* fs, T* red, bool active, double* out) {
+__device__ __forceinline__ double tv_cell(T f, T fy_add, int node, int i, int j, const BT& B, T inv_hx, T inv_hy,
+                                          T* fs, T* red, bool active, double* out) {
     constexpr int n = N + 1;
     fs[node] = f;
     __syncthreads();
@@ -74,11 +75,41 @@ __device__ __forceinline__ void tv_cell(T f, T fy_add, int node, int i, int j, c
         fs[j] = s;  // every thread has read fs before the barrier above
     }
     __syncthreads();
+    double r = 0.0;
     if (node == 0 && active) {
         T s = T(0);
 #pragma unroll
         for (int a = 0; a < n; ++a) s += fs[a];
-        *out = tv_to_f64(s);
+        r = tv_to_f64(s);
+        *out = r;
+    }
+    return r;
+}
+
+// The (count, mean, M2) triple of this block's TV values into part[3 b ..]:
+// the first step of the statistics (Chan et al.'s pairwise combination
+// starts from exact per-block triples).  tvc: the cell's TV on node 0 (from
+// tv_cell); ncell: active cells of the block.  Exact two-pass over at most
+// CPB values by one thread; CPB is a power of two, so a full block's mean is
+// a multiplication.  Every thread of the block calls it (one barrier).
+template <int CPB>
+__device__ __forceinline__ void tv_block_triple(double tvc, bool node0, int cl, int ncell, double* part) {
+    __shared__ double ctv[CPB];
+    if (node0 && cl < ncell) ctv[cl] = tvc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int a = 0; a < ncell; ++a) s += ctv[a];
+        const double mean = ncell == CPB ? s * (1.0 / CPB) : s / (double)ncell;
+        double q = 0.0;
+        for (int a = 0; a < ncell; ++a) {
+            const double d = ctv[a] - mean;
+            q += d * d;
+        }
+        double* p = part + 3 * (size_t)blockIdx.x;
+        p[0] = (double)ncell;
+        p[1] = mean;
+        p[2] = q;
     }
 }
 

@@ -232,14 +232,20 @@ def test_hydrostatic_background_gpu_matches_oracle():
     assert (a[:, 1:3] - b[:, 1:3]).abs().max().item() < 1e-9
 
 
-@pytest.mark.parametrize("var,cfgname", [("theta", "bubble"), ("rho", "steady")])
+@pytest.mark.parametrize("var,cfgname", [("theta", "bubble"), ("rho", "steady"), ("theta", "bubble_large"),
+                                         ("rho", "steady_n1")])
 def test_tv_indicator_matches_oracle(var, cfgname):
-    if cfgname == "bubble":
-        cfg = atmosphere_config(degree=5, nx=27, ny=27)
+    # bubble_large: 1599 cells in 400 blocks of 4, so the statistics fold two
+    # block triples per thread and the last block holds 3 cells; steady_n1:
+    # blocks of 32 cells, the last holding 15
+    if cfgname in ("bubble", "bubble_large"):
+        cfg = atmosphere_config(degree=5, nx=27, ny=27) if cfgname == "bubble" else \
+            atmosphere_config(degree=5, nx=41, ny=39)
         o = oracle_for(cfg)
         u0 = two_bubble_field(o)
     else:
-        cfg = steady_manufactured_config(degree=3, nx=9, ny=9)
+        cfg = steady_manufactured_config(degree=3, nx=9, ny=9) if cfgname == "steady" else \
+            steady_manufactured_config(degree=1, nx=13, ny=11)
         o = oracle_for(cfg)
         u0 = steady_field(o, cfg)
     m = Mesh(cfg)
