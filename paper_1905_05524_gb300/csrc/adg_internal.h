@@ -102,13 +102,14 @@ constexpr int kBatchCandidates = 3;  // tile-size candidates the autotuner times
 // triple of its cells, and the statistics combine these block triples.
 constexpr int tv_cpb(int N) { return N == 1 ? 32 : N == 2 ? 16 : N == 3 ? 8 : N <= 5 ? 4 : 2; }
 constexpr int kTvThreads = 256;  // threads per block of the statistics-and-flags kernel
+constexpr int kTvLevels = 8;     // its combine tree: 5 levels within warps, 3 across the 8 warps
 
 // Where the statistics kernel finds the block triples and the Chan weights
 // of its fixed combine order (tv_stats_prepare).
 struct TvStatsArgs {
     const double* part = nullptr;   // [3 * nblk] block triples (count, mean, M2)
     const double* wfold = nullptr;  // [2 * nblk] weights of the per-thread left folds
-    const double* wtree = nullptr;  // [2 * kTvThreads] weights of the tree over the threads
+    const double* wtree = nullptr;  // [2 * kTvLevels * kTvThreads] weights of the tree over the threads
     int nblk = 0, per = 0, cells = 0;
 };
 
@@ -147,7 +148,7 @@ int launch_tv_cells_mixed(int N, const double* u, double* tv, double* part, int 
                           const BasisF& B, const PhysF& P, const MixedBg& bg, double theta0, double Rcp,
                           void* stream);
 // Statistics scratch `part`: [3 nblk] block triples | [2 nblk] fold weights |
-// [2 kTvThreads] tree weights, nblk = tv_stats_blocks(N, cells).
+// [2 kTvLevels kTvThreads] tree weights, nblk = tv_stats_blocks(N, cells).
 int tv_stats_blocks(int N, int cells);
 size_t tv_stats_scratch_doubles(int N, int cells);
 // Chan weights of the combine order for (N, cells) into `part` (host

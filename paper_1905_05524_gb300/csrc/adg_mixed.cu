@@ -621,7 +621,7 @@ k_corrector_mixed(double* __restrict__ u, const float* __restrict__ rvol,
 // first cell) of many independent meshes; tile t goes to block t mod grid,
 // so the schedule is static and the results do not depend on timing.
 template <int N, int CPB>
-__global__ void __launch_bounds__(CPB*(N + 1) * (N + 1))
+__global__ void __launch_bounds__(CPB*(N + 1) * (N + 1), (MixCfg<N, CPB>::minb))
 k_predictor_mixed_batch(const MixedInst* __restrict__ insts, const BatchTile* __restrict__ tiles,
                         int ntiles, const BasisF B) {
     extern __shared__ float smf[];

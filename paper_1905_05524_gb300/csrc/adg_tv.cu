@@ -85,7 +85,9 @@ k_tv_cells_mixed(const double* __restrict__ u, double* __restrict__ tv, double* 
 // Every block of this kernel combines all of them with Chan et al.'s
 // pairwise update in the same fixed order -- thread t folds triples
 // [t per, (t+1) per) left to right, then a binary tree joins the thread
-// results -- so every block holds bitwise the same mean and sigma without
+// results (warp shuffles within each warp, then across the warp results;
+// sigma once per block) -- so every block holds bitwise the same mean and
+// sigma without
 // waiting on any other block; then it flags its own cells.  The weights
 // n_b/(n_a+n_b) and n_a n_b/(n_a+n_b) of every combine depend only on the
 // cell count and come divided out by the host (tv_stats_prepare, the same
@@ -93,60 +95,119 @@ k_tv_cells_mixed(const double* __restrict__ u, double* __restrict__ tv, double* 
 // is a long dependent chain on this part.
 constexpr int kPartThreads = kTvThreads;
 
-// Flag of one cell: refine if TV >= mean + T_r sigma, coarsen if
+// Flag decision: refine if TV >= mean + T_r sigma, coarsen if
 // TV < mean + T_c sigma, keep all when sigma <= 1e-12 |mean| (reading F1).
 // The thresholds round product and sum separately (no contraction), as
-// mean + T * sigma is usually written; the comparisons use the IEEE-754
-// order of non-negative doubles as 64-bit integers (TV >= 0): exact, and off
-// the narrow FP64 pipe.  NaN compares false both ways.
-__device__ __forceinline__ int8_t tv_flag_of(double x, double mu, double sig, double T_r, double T_c) {
+// mean + T * sigma is usually written, and are formed once per block; the
+// per-cell comparisons use the IEEE-754 order of non-negative doubles as
+// 64-bit integers (TV >= 0): exact, and off the narrow FP64 pipe.  NaN
+// compares false both ways.
+struct TvThresholds {
+    long long br, bc;  // encodings of the thresholds
+    bool r_all, c_none, flat;
+};
+
+__device__ __forceinline__ TvThresholds tv_thresholds(double mu, double sig, double T_r, double T_c) {
     const double thr_r = __dadd_rn(mu, __dmul_rn(T_r, sig)), thr_c = __dadd_rn(mu, __dmul_rn(T_c, sig));
-    const bool flat = sig <= 1e-12 * fabs(mu) || !(thr_r == thr_r) || !(thr_c == thr_c);
+    TvThresholds h;
+    h.flat = sig <= 1e-12 * fabs(mu) || !(thr_r == thr_r) || !(thr_c == thr_c);
+    h.r_all = thr_r <= 0.0;   // a threshold <= 0 lies at or below every TV
+    h.c_none = thr_c <= 0.0;
+    h.br = __double_as_longlong(thr_r);
+    h.bc = __double_as_longlong(thr_c);
+    return h;
+}
+
+__device__ __forceinline__ int8_t tv_flag_of(double x, const TvThresholds& h) {
     const long long bx = __double_as_longlong(x);
     const bool nan = (bx & 0x7fffffffffffffffLL) > 0x7ff0000000000000LL;
-    // a threshold <= 0 lies at or below every TV
-    const bool ref = thr_r <= 0.0 || bx >= __double_as_longlong(thr_r);
-    const bool coa = thr_c > 0.0 && bx < __double_as_longlong(thr_c);
-    return (flat || nan) ? (int8_t)0 : ref ? (int8_t)1 : (coa ? (int8_t)-1 : (int8_t)0);
+    const bool ref = h.r_all || bx >= h.br;
+    const bool coa = !h.c_none && bx < h.bc;
+    return (h.flat || nan) ? (int8_t)0 : ref ? (int8_t)1 : (coa ? (int8_t)-1 : (int8_t)0);
 }
 
 __global__ void __launch_bounds__(kTvThreads)
 k_tv_stats_flags(const double* __restrict__ tv, const TvStatsArgs st, double T_r, double T_c,
                  double* __restrict__ stats, int8_t* __restrict__ flags) {
-    __shared__ double tm[kTvThreads], t2[kTvThreads];
-    const int t = threadIdx.x;
+    __shared__ double wm[kTvThreads / 32], w2[kTvThreads / 32];
+    __shared__ TvThresholds thr;
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    // this thread's tree weights, loaded ahead of the dependent chain
+    double f1[kTvLevels], f2[kTvLevels];
+#pragma unroll
+    for (int l = 0; l < kTvLevels; ++l) {
+        const int pos = l < 5 ? t : lane;
+        f1[l] = st.wtree[2 * (l * kTvThreads + pos)];
+        f2[l] = st.wtree[2 * (l * kTvThreads + pos) + 1];
+    }
+    // left fold of this thread's block triples, loads batched four at a time
     double m = 0.0, m2 = 0.0;
     const int k0 = t * st.per, k1 = min(k0 + st.per, st.nblk);
     if (k0 < k1) {
         m = st.part[3 * k0 + 1];
         m2 = st.part[3 * k0 + 2];
-        for (int k = k0 + 1; k < k1; ++k) {
-            const double d = st.part[3 * k + 1] - m;
-            m = m + d * st.wfold[2 * k];
-            m2 = m2 + st.part[3 * k + 2] + d * d * st.wfold[2 * k + 1];
+        for (int k = k0 + 1; k < k1; k += 4) {
+            double mb[4], m2b[4], g1[4], g2[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int kk = min(k + q, k1 - 1);
+                mb[q] = st.part[3 * kk + 1];
+                m2b[q] = st.part[3 * kk + 2];
+                g1[q] = st.wfold[2 * kk];
+                g2[q] = st.wfold[2 * kk + 1];
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (k + q < k1) {
+                    const double d = mb[q] - m;
+                    m = m + d * g1[q];
+                    m2 = m2 + m2b[q] + d * d * g2[q];
+                }
+            }
         }
     }
-    tm[t] = m;
-    t2[t] = m2;
+    // tree: strides 16..1 within each warp, then 4..1 across the warp results
+    // (weights are zero where the right-hand entry holds no cells)
+#pragma unroll
+    for (int l = 0, s = 16; s > 0; ++l, s >>= 1) {
+        const double mo = __shfl_down_sync(0xffffffffu, m, s), m2o = __shfl_down_sync(0xffffffffu, m2, s);
+        if (lane < s) {
+            const double d = mo - m;
+            m = m + d * f1[l];
+            m2 = m2 + m2o + d * d * f2[l];
+        }
+    }
+    if (lane == 0) {
+        wm[w] = m;
+        w2[w] = m2;
+    }
     __syncthreads();
-    for (int stride = kTvThreads / 2, off = 0; stride > 0; off += stride, stride >>= 1) {
-        if (t < stride) {
-            // weights are zero where the right-hand entry holds no cells
-            const double d = tm[t + stride] - tm[t];
-            tm[t] = tm[t] + d * st.wtree[2 * (off + t)];
-            t2[t] = t2[t] + t2[t + stride] + d * d * st.wtree[2 * (off + t) + 1];
+    if (w == 0) {
+        m = lane < kTvThreads / 32 ? wm[lane] : 0.0;
+        m2 = lane < kTvThreads / 32 ? w2[lane] : 0.0;
+#pragma unroll
+        for (int l = 5, s = kTvThreads / 64; s > 0; ++l, s >>= 1) {
+            const double mo = __shfl_down_sync(0xffffffffu, m, s), m2o = __shfl_down_sync(0xffffffffu, m2, s);
+            if (lane < s) {
+                const double d = mo - m;
+                m = m + d * f1[l];
+                m2 = m2 + m2o + d * d * f2[l];
+            }
         }
-        __syncthreads();
+        if (lane == 0) {
+            const double sig = sqrt(m2 / (double)st.cells);
+            if (blockIdx.x == 0 && stats) {
+                stats[0] = m;
+                stats[1] = sig;
+            }
+            thr = tv_thresholds(m, sig, T_r, T_c);
+        }
     }
-    const double mu = tm[0];
-    const double sig = sqrt(t2[0] / (double)st.cells);
-    if (blockIdx.x == 0 && t == 0 && stats) {
-        stats[0] = mu;
-        stats[1] = sig;
-    }
+    __syncthreads();
     if (!flags) return;
+    const TvThresholds h = thr;
     for (int c = blockIdx.x * kTvThreads + t; c < st.cells; c += gridDim.x * kTvThreads)
-        flags[c] = tv_flag_of(tv[c], mu, sig, T_r, T_c);
+        flags[c] = tv_flag_of(tv[c], h);
 }
 
 // Flags from (mean, sigma) held in device memory, one cell per thread.
@@ -154,7 +215,7 @@ __global__ void __launch_bounds__(kPartThreads)
 k_tv_flag_cells(const double* __restrict__ tv, int cells, const double* __restrict__ stats, double T_r,
                 double T_c, int8_t* __restrict__ flags) {
     const int c = blockIdx.x * kPartThreads + threadIdx.x;
-    if (c < cells) flags[c] = tv_flag_of(tv[c], stats[0], stats[1], T_r, T_c);
+    if (c < cells) flags[c] = tv_flag_of(tv[c], tv_thresholds(stats[0], stats[1], T_r, T_c));
 }
 
 // ---------------------------------------------------------------- scenarios
@@ -363,7 +424,7 @@ int launch_tv_cells_mixed(int N, const double* u, double* tv, double* part, int 
 int tv_stats_blocks(int N, int cells) { return (cells + tv_cpb(N) - 1) / tv_cpb(N); }
 
 size_t tv_stats_scratch_doubles(int N, int cells) {
-    return 5 * (size_t)tv_stats_blocks(N, cells) + 2 * (size_t)kTvThreads;
+    return 5 * (size_t)tv_stats_blocks(N, cells) + 2 * (size_t)kTvLevels * kTvThreads;
 }
 
 static int tv_fold_per(int nblk) { return (nblk + kTvThreads - 1) / kTvThreads; }
@@ -382,10 +443,15 @@ TvStatsArgs tv_stats_args(int N, int cells, const double* part) {
 // Weights n_b/(n_a+n_b) and n_a n_b/(n_a+n_b) of every combine of
 // k_tv_stats_flags, from the block cell counts alone (IEEE division here).
 int tv_stats_prepare(int N, int cells, double* part, void* stream) {
+    static_assert(kTvThreads == 256 && kTvLevels == 8, "tree shape: 8 warps of 32");
     const int cpb = tv_cpb(N), nblk = tv_stats_blocks(N, cells), per = tv_fold_per(nblk);
-    std::vector<double> w(2 * (size_t)nblk + 2 * (size_t)kTvThreads, 0.0);
+    std::vector<double> w(2 * (size_t)nblk + 2 * (size_t)kTvLevels * kTvThreads, 0.0);
     double* wfold = w.data();
     double* wtree = w.data() + 2 * (size_t)nblk;
+    auto put = [&](int level, int pos, double na, double nb) {
+        wtree[2 * ((size_t)level * kTvThreads + pos)] = nb / (na + nb);
+        wtree[2 * ((size_t)level * kTvThreads + pos) + 1] = na * nb / (na + nb);
+    };
     std::vector<double> tcnt(kTvThreads, 0.0);
     for (int t = 0; t < kTvThreads; ++t) {
         const int k0 = t * per, k1 = std::min(k0 + per, nblk);
@@ -400,19 +466,28 @@ int tv_stats_prepare(int N, int cells, double* part, void* stream) {
         }
         tcnt[t] = na;
     }
-    for (int stride = kTvThreads / 2, off = 0; stride > 0; off += stride, stride >>= 1) {
-        for (int a = 0; a < stride; ++a) {
-            const double na = tcnt[a], nb = tcnt[a + stride];
-            if (nb > 0.0) {
-                wtree[2 * (off + a)] = nb / (na + nb);
-                wtree[2 * (off + a) + 1] = na * nb / (na + nb);
-                tcnt[a] = na + nb;
+    // levels 0..4: lane l of each warp takes lane l + s, s = 16, 8, 4, 2, 1
+    for (int l = 0, s = 16; s > 0; ++l, s >>= 1)
+        for (int wp = 0; wp < kTvThreads / 32; ++wp)
+            for (int lane = 0; lane < s; ++lane) {
+                const int a = 32 * wp + lane, b = a + s;
+                if (tcnt[b] > 0.0) {
+                    put(l, a, tcnt[a], tcnt[b]);
+                    tcnt[a] += tcnt[b];
+                }
             }
-        }
-    }
-    cudaStream_t s = (cudaStream_t)stream;
-    cudaError_t e = cudaMemcpyAsync(part + 3 * (size_t)nblk, w.data(), w.size() * 8, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // the host table must outlive the copy
+    // levels 5..7: warp results, entry l takes entry l + s, s = 4, 2, 1
+    std::vector<double> wc(kTvThreads / 32);
+    for (int wp = 0; wp < kTvThreads / 32; ++wp) wc[wp] = tcnt[32 * wp];
+    for (int l = 5, s = kTvThreads / 64; s > 0; ++l, s >>= 1)
+        for (int a = 0; a < s; ++a)
+            if (wc[a + s] > 0.0) {
+                put(l, a, wc[a], wc[a + s]);
+                wc[a] += wc[a + s];
+            }
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpyAsync(part + 3 * (size_t)nblk, w.data(), w.size() * 8, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // the host table must outlive the copy
     return (int)e;
 }
 
