@@ -540,7 +540,7 @@ __global__ void k_amr_transfer(const double* __restrict__ uold, double* __restri
 template <int N>
 struct AmrCfg {
     static constexpr int n = N + 1;
-    static constexpr int cpb = N == 1 ? 32 : N == 2 ? 16 : N == 3 ? 8 : N <= 5 ? 4 : 2;
+    static constexpr int cpb = tv_cpb(N);
     static constexpr int threads = cpb * n * n;
     static constexpr size_t smem_pred = (size_t)cpb * 3 * n * 4 * n * n * sizeof(double);
 };

@@ -34,7 +34,7 @@ template <int N>
 struct Fp64Cfg {
     static constexpr int n = N + 1;
     // cells per block: enough threads per block for small degrees
-    static constexpr int cpb = N == 1 ? 32 : N == 2 ? 16 : N == 3 ? 8 : N <= 5 ? 4 : 2;
+    static constexpr int cpb = tv_cpb(N);
     static constexpr int threads = cpb * n * n;
     static constexpr size_t smem_pred = (size_t)cpb * 3 * n * 4 * n * n * sizeof(double);
 };

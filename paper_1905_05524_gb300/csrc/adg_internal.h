@@ -97,10 +97,12 @@ constexpr int kBatchCandidates = 3;  // tile-size candidates the autotuner times
 
 // Kernel launchers (adg_fp64.cu, adg_mixed.cu, adg_tv.cu).  They return a
 // cudaError_t value as int.
-// Cells per block of every kernel that produces TV values (the TV kernels
-// and the correctors): each such block also publishes the (count, mean, M2)
-// triple of its cells, and the statistics combine these block triples.
-constexpr int tv_cpb(int N) { return N == 1 ? 32 : N == 2 ? 16 : N == 3 ? 8 : N <= 5 ? 4 : 2; }
+// Cells per block of the per-cell kernels (predictors, correctors, TV): one
+// thread per node, whole warps as far as n^2 allows (N = 4: 5 cells = 125 of
+// 128 lanes).  Every block that produces TV values also publishes the
+// (count, mean, M2) triple of its cells, and the statistics combine these
+// block triples.
+constexpr int tv_cpb(int N) { return N == 1 ? 32 : N == 2 ? 16 : N == 3 ? 8 : N == 4 ? 5 : N == 5 ? 4 : 2; }
 constexpr int kTvThreads = 256;  // threads per block of the statistics-and-flags kernel
 constexpr int kTvLevels = 8;     // its combine tree: 5 levels within warps, 3 across the 8 warps
 

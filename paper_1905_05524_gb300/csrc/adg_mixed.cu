@@ -158,7 +158,7 @@ __device__ __forceinline__ void ns_flux_pert2(const float2 qp[4], const float2 g
 template <int N, int CPB_ = 0>
 struct MixCfg {
     static constexpr int n = N + 1;
-    static constexpr int cpb_default = N == 1 ? 32 : N == 2 ? 16 : N == 3 ? 8 : N <= 5 ? 4 : 2;
+    static constexpr int cpb_default = tv_cpb(N);
     static constexpr int cpb = CPB_ ? CPB_ : cpb_default;
     static constexpr int threads = cpb * n * n;
     // rows padded to an even length (8-byte vector loads); per-cell smem stride
@@ -170,8 +170,9 @@ struct MixCfg {
     static constexpr size_t smem_pred = (size_t)cpb * stride * sizeof(float);
     // minimum resident blocks asked of the register allocator (measured: at
     // N = 5 the four blocks that shared memory admits beat three blocks
-    // without spills; elsewhere the allocator's own choice is best)
-    static constexpr int minb = (N == 5 && cpb == 4) ? 4 : 1;
+    // without spills; N = 4 asks for the four its 128 registers allow;
+    // elsewhere the allocator's own choice is best)
+    static constexpr int minb = (N == 5 && cpb == 4) ? 4 : (N == 4 && cpb == 5) ? 4 : 1;
 };
 
 // Predictor body for the tile of CPB cells starting at cell c0 (one thread per

@@ -90,8 +90,8 @@ __device__ __forceinline__ double tv_cell(T f, T fy_add, int node, int i, int j,
 // the first step of the statistics (Chan et al.'s pairwise combination
 // starts from exact per-block triples).  tvc: the cell's TV on node 0 (from
 // tv_cell); ncell: active cells of the block.  Exact two-pass over at most
-// CPB values by one thread; CPB is a power of two, so a full block's mean is
-// a multiplication.  Every thread of the block calls it (one barrier).
+// CPB values by one thread (a full block's mean is a multiplication where
+// CPB is a power of two).  Every thread of the block calls it (one barrier).
 template <int CPB>
 __device__ __forceinline__ void tv_block_triple(double tvc, bool node0, int cl, int ncell, double* part) {
     __shared__ double ctv[CPB];
@@ -100,7 +100,7 @@ __device__ __forceinline__ void tv_block_triple(double tvc, bool node0, int cl, 
     if (threadIdx.x == 0) {
         double s = 0.0;
         for (int a = 0; a < ncell; ++a) s += ctv[a];
-        const double mean = ncell == CPB ? s * (1.0 / CPB) : s / (double)ncell;
+        const double mean = (ncell == CPB && (CPB & (CPB - 1)) == 0) ? s * (1.0 / CPB) : s / (double)ncell;
         double q = 0.0;
         for (int a = 0; a < ncell; ++a) {
             const double d = ctv[a] - mean;
