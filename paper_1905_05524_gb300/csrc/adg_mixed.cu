@@ -172,7 +172,7 @@ struct MixCfg {
     // N = 5 the four blocks that shared memory admits beat three blocks
     // without spills; N = 4 asks for the four its 128 registers allow;
     // elsewhere the allocator's own choice is best)
-    static constexpr int minb = (N == 5 && cpb == 4) ? 4 : (N == 4 && cpb == 5) ? 4 : 1;
+    static constexpr int minb = (N == 5 && cpb == 4) ? 4 : (N == 4 && cpb == 5) ? 4 : (N == 3 && cpb == 8) ? 5 : (N == 6 && cpb == 2) ? 4 : (N == 7 && cpb == 2) ? 3 : 1;
 };
 
 // Predictor body for the tile of CPB cells starting at cell c0 (one thread per
@@ -333,13 +333,14 @@ __device__ __forceinline__ void predictor_mixed_body(const double* __restrict__ 
         }
         __syncthreads();
     }
-    // sweeps 2..n on pairs of time slices; R2[h] holds slices 2h, 2h+1 (for
-    // odd n the last pair's second lane repeats slice n-1 and meets the zero
-    // padding of Kw and w)
+    // sweeps 2..n on pairs of time slices (for odd n the last pair's second
+    // lane repeats slice n-1 and meets the zero padding of Kw and w).  The
+    // residual is contracted in time one variable at a time, so only the
+    // z-momentum source of each slice pair stays live across the barrier.
     constexpr int NPAIR = (n + 1) / 2;
 #pragma unroll 1
     for (int r = 1; r < n; ++r) {
-        float2 R2[NPAIR][4];
+        float2 S2h[NPAIR];
 #pragma unroll
         for (int h = 0; h < NPAIR; ++h) {
             const int k0 = 2 * h, k1 = 2 * h + 1 < n ? 2 * h + 1 : 2 * h;
@@ -347,25 +348,24 @@ __device__ __forceinline__ void predictor_mixed_body(const double* __restrict__ 
             FluxF2 f;
             eval_pair(k0, k1, q, gx, gy, f);
             store_flux_pair(k0, 2 * h + 1 < n, f);
-#pragma unroll
-            for (int v = 0; v < 4; ++v) R2[h][v] = bc2(Sm[v]);
-            R2[h][2] = add2(R2[h][2], f.S2);
+            S2h[h] = f.S2;
         }
         __syncthreads();
 #pragma unroll
-        for (int h = 0; h < NPAIR; ++h) {
-            const int k1 = 2 * h + 1 < n ? 2 * h + 1 : 2 * h;
+        for (int v = 0; v < 4; ++v) {
+            float2 R2[NPAIR];  // slices 2h, 2h+1 of variable v
 #pragma unroll
-            for (int v = 0; v < 4; ++v)
-                R2[h][v] = add2(R2[h][v], make_float2(divergence(2 * h, v), divergence(k1, v)));
-        }
+            for (int h = 0; h < NPAIR; ++h) {
+                const int k1 = 2 * h + 1 < n ? 2 * h + 1 : 2 * h;
+                R2[h] = bc2(Sm[v]);
+                if (v == 2) R2[h] = add2(R2[h], S2h[h]);
+                R2[h] = add2(R2[h], make_float2(divergence(2 * h, v), divergence(k1, v)));
+            }
 #pragma unroll
-        for (int l = 0; l < n; ++l) {
+            for (int l = 0; l < n; ++l) {
+                float2 acc = mul2(make_float2(B.Kw[l][0], B.Kw[l][1]), R2[0]);
 #pragma unroll
-            for (int v = 0; v < 4; ++v) {
-                float2 acc = mul2(make_float2(B.Kw[l][0], B.Kw[l][1]), R2[0][v]);
-#pragma unroll
-                for (int h = 1; h < NPAIR; ++h) acc = fma2(make_float2(B.Kw[l][2 * h], B.Kw[l][2 * h + 1]), R2[h][v], acc);
+                for (int h = 1; h < NPAIR; ++h) acc = fma2(make_float2(B.Kw[l][2 * h], B.Kw[l][2 * h + 1]), R2[h], acc);
                 store_q(l, v, fmaf(dt, acc.x + acc.y, up[v]));
             }
         }
@@ -373,38 +373,31 @@ __device__ __forceinline__ void predictor_mixed_body(const double* __restrict__ 
     }
 
     // final evaluation on the converged iterate and the time averages
-    float2 qb2[4], Fb2[4], Gb2[4], qxb2[4], qyb2[4], Sz2;
+    // (scalar accumulators: half the registers of packed ones, at the
+    // register peak of the kernel)
+    float qb[4], Fb[4], Gb[4], Sb[4], qxb[4], qyb[4], Sz = 0.f;
 #pragma unroll
-    for (int v = 0; v < 4; ++v) qb2[v] = Fb2[v] = Gb2[v] = qxb2[v] = qyb2[v] = bc2(0.f);
-    Sz2 = bc2(0.f);
+    for (int v = 0; v < 4; ++v) qb[v] = Fb[v] = Gb[v] = qxb[v] = qyb[v] = 0.f;
 #pragma unroll
     for (int h = 0; h < NPAIR; ++h) {
         const int k0 = 2 * h, k1 = 2 * h + 1 < n ? 2 * h + 1 : 2 * h;
         float2 q[4], gx[4], gy[4];
         FluxF2 f;
         eval_pair(k0, k1, q, gx, gy, f);
-        const float2 wk = make_float2(B.w[k0], B.w[2 * h + 1]);  // w[n] = 0 pads an odd n
+        const float w0 = B.w[k0], w1 = B.w[2 * h + 1];  // w[n] = 0 pads an odd n
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
-            qb2[v] = fma2(wk, q[v], qb2[v]);
-            Fb2[v] = fma2(wk, f.F[v], Fb2[v]);
-            Gb2[v] = fma2(wk, f.G[v], Gb2[v]);
-            qxb2[v] = fma2(wk, gx[v], qxb2[v]);
-            qyb2[v] = fma2(wk, gy[v], qyb2[v]);  // full y-gradient (background included)
+            qb[v] = fmaf(w1, q[v].y, fmaf(w0, q[v].x, qb[v]));
+            Fb[v] = fmaf(w1, f.F[v].y, fmaf(w0, f.F[v].x, Fb[v]));
+            Gb[v] = fmaf(w1, f.G[v].y, fmaf(w0, f.G[v].x, Gb[v]));
+            qxb[v] = fmaf(w1, gx[v].y, fmaf(w0, gx[v].x, qxb[v]));
+            qyb[v] = fmaf(w1, gy[v].y, fmaf(w0, gy[v].x, qyb[v]));  // full y-gradient (background included)
         }
-        Sz2 = fma2(wk, f.S2, Sz2);
+        Sz = fmaf(w1, f.S2.y, fmaf(w0, f.S2.x, Sz));
     }
-    float qb[4], Fb[4], Gb[4], Sb[4], qxb[4], qyb[4];
 #pragma unroll
-    for (int v = 0; v < 4; ++v) {
-        qb[v] = qb2[v].x + qb2[v].y;
-        Fb[v] = Fb2[v].x + Fb2[v].y;
-        Gb[v] = Gb2[v].x + Gb2[v].y;
-        qxb[v] = qxb2[v].x + qxb2[v].y;
-        qyb[v] = qyb2[v].x + qyb2[v].y;
-        Sb[v] = Sm[v];  // the time weights sum to one
-    }
-    Sb[2] += Sz2.x + Sz2.y;
+    for (int v = 0; v < 4; ++v) Sb[v] = Sm[v];  // the time weights sum to one
+    Sb[2] += Sz;
     __syncthreads();
     // time averages, row-major with padded rows: slots 0..4 = qbar, Fbar, Gbar, qxbar, qybar
     float* A = Q;
