@@ -231,13 +231,46 @@ int build_mixed(adg_mesh* m) {
                     E += phi[j] * Eb[iy * n + j];
                 }
                 const double zf = d->y0 + (iy + (side == 0 ? 1 : 0)) * P.hy;
+                const double exf = 1.0 - d->g * zf / (P.cp * d->theta0);
+                const double pfx = d->p0 * std::pow(exf, P.cp / d->R);
+                const double rfx = pfx / (d->R * d->theta0 * exf);
+                const double Efx = pfx / P.gm1 + rfx * d->g * zf;
                 float* fb = face.data() + ((size_t)iy * 2 + side) * adg::kFaceBg;
                 fb[0] = (float)r;
                 fb[1] = (float)E;
                 fb[2] = (float)(P.gm1 * (E - r * d->g * zf));
+                fb[3] = (float)rfx;
+                fb[4] = (float)Efx;
+                fb[5] = (float)pfx;
+                fb[6] = (float)(rfx - r);  // wall faces keep these; interior ones are overwritten below
+                fb[7] = (float)(Efx - E);
             }
             (void)zn;
             (void)pn;
+        }
+        // faces between rows (and the wrap face of a periodic y): the upper
+        // row's extrapolated background minus the lower row's, in FP64, the
+        // same FP32 value on both sides of the face
+        auto extrap = [&](int iy, int side, double& r, double& E) {
+            const double* phi = side == 0 ? m->B.phi1 : m->B.phi0;
+            r = E = 0.0;
+            for (int j = 0; j < n; ++j) {
+                r += phi[j] * rb[iy * n + j];
+                E += phi[j] * Eb[iy * n + j];
+            }
+        };
+        const bool wall_y = d->bc_y == ADG_BC_WALL;
+        for (int iy = 0; iy < ny; ++iy) {
+            const int up = iy + 1 < ny ? iy + 1 : 0;
+            if (wall_y && iy + 1 == ny) continue;
+            double rl, El, ru, Eu;
+            extrap(iy, 0, rl, El);   // lower row, north face
+            extrap(up, 1, ru, Eu);   // upper row, south face
+            const float dr = (float)(ru - rl), dE = (float)(Eu - El);
+            float* fn = face.data() + ((size_t)iy * 2 + 0) * adg::kFaceBg;
+            float* fs = face.data() + ((size_t)up * 2 + 1) * adg::kFaceBg;
+            fn[6] = fs[6] = dr;
+            fn[7] = fs[7] = dE;
         }
     }
     const size_t bytes = nn * 8 * 2 + nn * 4 * 3 + face.size() * 4;

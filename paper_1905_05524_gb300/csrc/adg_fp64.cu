@@ -170,7 +170,7 @@ k_corrector_fp64(double* __restrict__ u, const double* __restrict__ rvol,
     }
     if constexpr (TV) {
         __shared__ double fs[CPB][n2], red[CPB][n2];
-        const double z = P.y0 + (iy + B.xi[j]) * P.hy;
+        const double z = tv_node_z(iy, j, B, P);
         const double f = epi.var == ADG_TV_THETA ? theta_of(unew, z, P) : unew[0];
         static_assert(CPB == tv_cpb(N), "the TV statistics combine blocks of tv_cpb(N) cells");
         const double r =

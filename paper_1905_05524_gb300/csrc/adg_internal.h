@@ -68,7 +68,14 @@ struct PhysF {
 
 // Background tables of the mixed path (zero without gravity).  Node tables
 // are indexed [iy * n + j]; face table [iy][0: north, 1: south][kFaceBg].
-constexpr int kFaceBg = 3;  // rhobar, Ebar, pbar at the face (extrapolated nodal background)
+// Per y-face of a row: [0..2] rhobar, Ebar, pbar of the extrapolated nodal
+// background (the base of the traces' perturbations); [3..5] the exact
+// background at the face height (the slip-wall ghost state); [6..7] formed
+// in FP64: on a wall face the exact minus the extrapolated rhobar and Ebar
+// (the ghost's perturbation against the trace's base), on any other face
+// the upper row's extrapolated rhobar, Ebar minus the lower row's (the two
+// cells' bases differ there).
+constexpr int kFaceBg = 8;
 struct MixedBg {
     const double* rb;   // rhobar at nodes (FP64, for the perturbation split)
     const double* Eb;   // Ebar = pbar/(gamma-1) + rhobar g z at nodes (FP64)

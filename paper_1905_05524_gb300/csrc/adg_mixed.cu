@@ -463,10 +463,14 @@ __device__ __forceinline__ void predictor_mixed_body(const double* __restrict__ 
     }
 }
 
-// Slip-wall ghost (Eq. 10 reading) in perturbation variables: rho' = rhoE' = 0
-// (the background), momentum reflected, interior gradients, background heat flux.
+// Slip-wall ghost (Eq. 10 reading): the background state at the face (rb, Eb,
+// pb), momentum reflected, interior gradients, background heat flux.  Its
+// flux and wave speed are evaluated on that base with zero perturbation --
+// the FP64 path's ghost exactly; for the Rusanov jump the ghost is returned
+// as a perturbation (dr, dE) against the base of the interior trace (the
+// extrapolated nodal background on y-faces, zero on x-faces).
 __device__ __forceinline__ void wall_ghost_f(const float* rec, int f, float z, float rb, float Eb,
-                                             float pb, float dzr, float dzE, const PhysF& P,
+                                             float pb, float dr, float dE, const PhysF& P,
                                              float qG[4], float fG[4], float& sG) {
     const float nx = f == 0 ? 1.f : f == 1 ? -1.f : 0.f;
     const float ny = f == 2 ? 1.f : f == 3 ? -1.f : 0.f;
@@ -481,8 +485,6 @@ __device__ __forceinline__ void wall_ghost_f(const float* rec, int f, float z, f
         gx[v] = rec[8 + v];
         gy[v] = rec[12 + v];
     }
-    (void)dzr;
-    (void)dzE;
     FluxF fl;
     ns_flux_pert(qG, gx, gy, z, rb, Eb, pb, P, fl, true, P.gravity ? -P.g / P.cp : 0.f);
     const bool xdir = f < 2;
@@ -492,15 +494,24 @@ __device__ __forceinline__ void wall_ghost_f(const float* rec, int f, float z, f
     const float rinv = __frcp_rn(rho);
     const float pp = P.gm1 * (qG[3] - 0.5f * (qG[1] * qG[1] + qG[2] * qG[2]) * rinv - P.g * z * qG[0]);
     sG = wave_speed_f(rho, qG[1], qG[2], pp, pb, xdir, P);
+    if (P.gravity) {
+        qG[0] = dr;
+        qG[3] = dE;
+    }
 }
 
+// Rusanov flux on perturbations.  dRL[v]: base of the right state minus base
+// of the left state (the two cells' extrapolated backgrounds differ on
+// y-faces), so the jump is that of the full states.  Explicit rounding: the
+// two cells of a face obtain bitwise the same flux.
 __device__ __forceinline__ void rusanov_f(const float qL[4], const float fL[4], float sL,
-                                          const float qR[4], const float fR[4], float sR, float out[4]) {
+                                          const float qR[4], const float fR[4], float sR, const float dRL[4],
+                                          float out[4]) {
     const float hs = __fmul_rn(-0.5f, fmaxf(sL, sR));
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
         const float avg = __fmul_rn(0.5f, __fadd_rn(fL[v], fR[v]));
-        out[v] = __fmaf_rn(hs, __fsub_rn(qR[v], qL[v]), avg);
+        out[v] = __fmaf_rn(hs, __fadd_rn(__fsub_rn(qR[v], qL[v]), dRL[v]), avg);
     }
 }
 
@@ -534,9 +545,10 @@ __device__ __forceinline__ void corrector_mixed_body(double* __restrict__ u, con
         float fo[4] = {rec[4], rec[5], rec[6], rec[7]};
         const float so = rec[16];
         float qn[4], fn[4], sn;
+        float dRL[4] = {0.f, 0.f, 0.f, 0.f};
         if (wall) {
-            float z, rb, Eb, pb;
-            if (xface) {
+            float z, rb, Eb, pb, dr = 0.f, dE = 0.f;
+            if (xface) {  // nodal heights: the traces' base is the exact background
                 z = P.y0 + (iy + B.xi[m]) * P.hy;
                 rb = f64_to_f32(bg.rb[iy * n + m]);
                 Eb = f64_to_f32(bg.Eb[iy * n + m]);
@@ -544,11 +556,13 @@ __device__ __forceinline__ void corrector_mixed_body(double* __restrict__ u, con
             } else {
                 z = P.y0 + (iy + (f == 2 ? 1 : 0)) * P.hy;
                 const float* fb = bg.face + ((size_t)iy * 2 + (f == 2 ? 0 : 1)) * kFaceBg;
-                rb = fb[0];
-                Eb = fb[1];
-                pb = fb[2];
+                rb = fb[3];
+                Eb = fb[4];
+                pb = fb[5];
+                dr = fb[6];
+                dE = fb[7];
             }
-            wall_ghost_f(rec, f, z, rb, Eb, pb, 0.f, 0.f, P, qn, fn, sn);
+            wall_ghost_f(rec, f, z, rb, Eb, pb, dr, dE, P, qn, fn, sn);
         } else {
             int nb, nf;
             if (f == 0) { nb = iy * P.nx + (ix + 1 == P.nx ? 0 : ix + 1); nf = 1; }
@@ -562,10 +576,15 @@ __device__ __forceinline__ void corrector_mixed_body(double* __restrict__ u, con
                 fn[v] = ot[(4 + v) * n + m];
             }
             sn = ot[16 * n + m];
+            if (!xface) {  // upper cell's base minus lower cell's base at this face
+                const float* fb = bg.face + ((size_t)iy * 2 + (f == 2 ? 0 : 1)) * kFaceBg;
+                dRL[0] = fb[6];
+                dRL[3] = fb[7];
+            }
         }
         float out[4];
-        if (f == 0 || f == 2) rusanov_f(qo, fo, so, qn, fn, sn, out);
-        else rusanov_f(qn, fn, sn, qo, fo, so, out);
+        if (f == 0 || f == 2) rusanov_f(qo, fo, so, qn, fn, sn, dRL, out);
+        else rusanov_f(qn, fn, sn, qo, fo, so, dRL, out);
 #pragma unroll
         for (int v = 0; v < 4; ++v) Fst[cl][f][v][m] = out[v];
     }
@@ -585,7 +604,7 @@ __device__ __forceinline__ void corrector_mixed_body(double* __restrict__ u, con
     if constexpr (TV) {
         __shared__ float fs[CPB][n2], red[CPB][n2];
         const int row = iy * n + j;
-        const float z = P.y0 + (iy + B.xi[j]) * P.hy;
+        const float z = tv_node_z(iy, j, B, P);
         const float f = tv_field_mixed(unew, epi.var, bg.rb[row], bg.Eb[row], bg.pb[row], z, P, (float)epi.theta0,
                                        (float)(1.0 - epi.Rcp));
         static_assert(CPB == tv_cpb(N), "the TV statistics combine blocks of tv_cpb(N) cells");

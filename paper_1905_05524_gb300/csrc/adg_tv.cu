@@ -45,7 +45,7 @@ k_tv_cells(const double* __restrict__ u, double* __restrict__ tv, double* __rest
     double q[4];
 #pragma unroll
     for (int v = 0; v < 4; ++v) q[v] = uc[v * n2 + node];
-    const double z = P.y0 + (iy + B.xi[j]) * P.hy;
+    const double z = tv_node_z(iy, j, B, P);
     const double f = var == ADG_TV_THETA ? theta_of(q, z, P) : q[0];
     const double r = tv_cell<N, double>(f, 0.0, node, i, j, B, P.inv_hx, P.inv_hy, fs[cl], red[cl], active,
                                         tv + cell);
@@ -73,7 +73,7 @@ k_tv_cells_mixed(const double* __restrict__ u, double* __restrict__ tv, double* 
     double q[4];
 #pragma unroll
     for (int v = 0; v < 4; ++v) q[v] = uc[v * n2 + node];
-    const float z = P.y0 + (iy + B.xi[j]) * P.hy;
+    const float z = tv_node_z(iy, j, B, P);
     const float f = tv_field_mixed(q, var, bg.rb[row], bg.Eb[row], bg.pb[row], z, P, theta0, one_m_kappa);
     const double r = tv_cell<N, float>(f, var == ADG_TV_THETA ? 0.f : bg.dzr[row], node, i, j, B, P.inv_hx,
                                        P.inv_hy, fs[cl], red[cl], active, tv + cell);
