@@ -495,6 +495,66 @@ def run_sweep(args, dev):
             "step": "predictor + corrector", "sweep": out}
 
 
+def run_cfd(args, dev):
+    """CFD scenarios of Sec. 4.1 on the FP64 path: the Taylor-Green vortex
+    (degree 5, 25x25 on [0, 2pi]^2, analytic boundaries, to t = 10) and the
+    lid-driven cavity (degree 3, 27x27 on [0, 1]^2, no-slip walls, lid 1 m/s,
+    mu = 0.01, to t = 10 s), CFL 0.5 on the initial state."""
+    import math
+    import numpy as np
+    import torch
+    from paper_1905_05524_gb300 import _lib as L
+    from paper_1905_05524_gb300.solver import Mesh, cavity_config, taylor_green_config
+    out = {"metric": METRIC + " (Sec. 4.1 CFD scenarios)", "unit": UNIT, "dtype": "f64"}
+    for name, cfg, kind, T in (("taylor_green", taylor_green_config(degree=5, nx=25, ny=25, device=dev.index),
+                                L.ADG_SCEN_TAYLOR_GREEN, 10.0),
+                               ("cavity", cavity_config(degree=3, nx=27, ny=27, device=dev.index),
+                                L.ADG_SCEN_CAVITY, 10.0)):
+        m = Mesh(cfg)
+        m.init_scenario(kind)
+        dt0 = m.stable_dt(0.5)
+        steps = math.ceil(T / dt0)
+        dt = T / steps
+        m.step(dt, 3)  # warm-up, then restart from the initial field
+        m.init_scenario(kind)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        m.step(dt, steps)
+        torch.cuda.synchronize()
+        sec = time.perf_counter() - t0
+        n = cfg.degree + 1
+        dof = cfg.nx * cfg.ny * n * n * 4
+        u = m.get_state().cpu().numpy()
+        res = {"degree": cfg.degree, "cells": cfg.nx * cfg.ny, "steps": steps, "dt": dt, "t_end": T,
+               "seconds": sec, "value": dof * steps / sec}
+        vel = u[:, 1:3] / u[:, 0:1]
+        if name == "taylor_green":
+            # incompressible reference velocity at t_end on the nodes (not an exact
+            # solution of the compressible equations: a qualitative check, as in the paper)
+            xi, _ = np.polynomial.legendre.leggauss(n)
+            xi = 0.5 * (xi + 1.0)
+            h = cfg.Lx / cfg.nx
+            ix = np.arange(cfg.nx * cfg.ny) % cfg.nx
+            iy = np.arange(cfg.nx * cfg.ny) // cfg.nx
+            X = (ix[:, None, None] + xi[None, None, :]) * h + 0.0 * xi[None, :, None]
+            Y = (iy[:, None, None] + xi[None, :, None]) * h + 0.0 * xi[None, None, :]
+            a = math.exp(-2.0 * cfg.mu * T)
+            ue = a * np.sin(X) * np.cos(Y)
+            ve = -a * np.cos(X) * np.sin(Y)
+            num = np.sqrt(((vel[:, 0] - ue) ** 2 + (vel[:, 1] - ve) ** 2).sum())
+            res["velocity_rel_l2_vs_incompressible"] = float(num / np.sqrt((ue ** 2 + ve ** 2).sum()))
+        else:
+            res["max_u"] = float(vel[:, 0].max())
+            res["min_u"] = float(vel[:, 0].min())
+            _, wq = np.polynomial.legendre.leggauss(n)
+            wq = 0.5 * wq
+            mass = float((u[:, 0] * wq[None, :, None] * wq[None, None, :]).sum())
+            res["mass_drift_rel"] = abs(mass - cfg.nx * cfg.ny) / (cfg.nx * cfg.ny)  # rho = 1 initially
+        out[name] = res
+        m.close()
+    return out
+
+
 def run_adjoint(args, dev):
     """Config 4: gradient of the probe misfit through 200 FP64 steps (degree 3,
     27x27) with checkpoints every 20: forward + checkpointed backward."""
@@ -551,7 +611,7 @@ def run_ours(args):
     torch.cuda.set_device(dev)
     if args.workload != "bubble":
         if rank == 0:
-            fn = {"amr": run_amr, "sweep": run_sweep, "adjoint": run_adjoint}[args.workload]
+            fn = {"amr": run_amr, "sweep": run_sweep, "adjoint": run_adjoint, "cfd": run_cfd}[args.workload]
             print(json.dumps(fn(args, dev)), flush=True)
         return 0
     n = DEGREE + 1
@@ -649,9 +709,10 @@ def main():
     ap.add_argument("--no-compare", action="store_true", help="skip the FP64 comparison form")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-instance batched form")
     ap.add_argument("--batch-steps", type=int, default=20)
-    ap.add_argument("--workload", default="bubble", choices=["bubble", "amr", "sweep", "adjoint"],
+    ap.add_argument("--workload", default="bubble", choices=["bubble", "amr", "sweep", "adjoint", "cfd"],
                     help="extra workloads, each printing its own JSON line: amr (config 3), "
-                         "sweep (config 5 degree sweep), adjoint (config 4 gradient)")
+                         "sweep (config 5 degree sweep), adjoint (config 4 gradient), "
+                         "cfd (Sec. 4.1 Taylor-Green vortex and lid-driven cavity)")
     ap.add_argument("--sweep-steps", type=int, default=20)
     ap.add_argument("--amr-steps", type=int, default=1000)
     ap.add_argument("--cpu-steps", type=int, default=8)

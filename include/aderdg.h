@@ -54,6 +54,15 @@ extern "C" {
 #define ADG_BC_EXCHANGE 2       /* south and north faces exchange            */
 #define ADG_BC_WALL_EXCHANGE 3  /* south slip wall, north face exchanges     */
 #define ADG_BC_EXCHANGE_WALL 4  /* south face exchanges, north slip wall     */
+/* FP64 uniform meshes without gravity (the CFD scenarios of Sec. 4.1): */
+#define ADG_BC_NOSLIP 5     /* no-slip wall: ghost density and pressure of the
+                               interior, velocity 2 v_wall - v, interior
+                               gradients, adiabatic; the north wall moves with
+                               x-velocity lid_u (lid-driven cavity)            */
+#define ADG_BC_ANALYTIC 6   /* the field bc_field imposed on the boundary: ghost
+                               = the field's state and flux at the face node,
+                               averaged over the step at the Gauss-Legendre
+                               time nodes (Taylor-Green vortex)                */
 
 #define ADG_SRC_NONE 0
 #define ADG_SRC_STEADY 1    /* steady manufactured source rho = 1 + a sin(2pi(x+y)/L) */
@@ -89,13 +98,23 @@ typedef struct adg_mesh_desc {
     int max_levels;        /* 0: uniform mesh; 1..4: adaptive 3:1 tree with up to
                               this many refinement levels above the nx x ny base
                               (FP64 only; see adg_adapt)                          */
+    double lid_u;          /* ADG_BC_NOSLIP: x-velocity of the north wall (the
+                              lid of the driven cavity, Sec. 4.1); others rest    */
+    int bc_field;          /* ADG_BC_ANALYTIC: the imposed field, ADG_FIELD_*     */
 } adg_mesh_desc;
+
+#define ADG_FIELD_NONE 0
+#define ADG_FIELD_TAYLOR_GREEN 1 /* Sec. 4.1: rho = 1, v = e^{-2 mu t} (sin x cos y,
+                                    -cos x sin y), p = e^{-4 mu t} (cos 2x + cos 2y)/4
+                                    + 100/gamma                                     */
 
 #define ADG_SCEN_STEADY 0       /* steady manufactured field of the source above */
 #define ADG_SCEN_COSINE 1       /* cosine bubble theta' (Eq. 15, r/a reading)    */
 #define ADG_SCEN_TWO_BUBBLES 2  /* Gaussian-tail warm + cold bubbles (Eqs. 12, 14) */
 #define ADG_SCEN_BACKGROUND 3   /* unperturbed hydrostatic atmosphere (Eq. 6)     */
 #define ADG_SCEN_PAPER 4        /* the Eq. 8 field at the mesh's time             */
+#define ADG_SCEN_TAYLOR_GREEN 5 /* the Taylor-Green field at t = 0 (Sec. 4.1)     */
+#define ADG_SCEN_CAVITY 6       /* fluid at rest, rho = 1, p = 100/gamma (Sec. 4.1) */
 
 typedef struct adg_scenario {
     int kind;              /* ADG_SCEN_*                                         */

@@ -18,7 +18,14 @@ R6  Rusanov speed s = |v.n| + c + 2 eta lambda_v on the extrapolated
     time-averaged face state, F* = (F_L + F_R)/2 - max(s_L, s_R)(q_R - q_L)/2;
 R8  slip wall: ghost rho and rhoE from the background, momentum reflected,
     ghost gradient = interior gradient, the ghost's heat flux replaced by the
-    background value -kappa dTbar/dz n_z (Eq. 10).
+    background value -kappa dTbar/dz n_z (Eq. 10);
+R12 no-slip wall moving tangentially with velocity v_w: ghost rho and p of
+    the interior, ghost velocity 2 v_w - v, ghost gradient = interior
+    gradient, adiabatic ghost heat flux (zero);
+R13 analytic (Dirichlet) boundary: the ghost is the analytic field at the
+    face node, averaged over the step at the Gauss-Legendre time nodes like
+    the interior traces: q-bar = sum_k w_k Q(t + xi_k dt), normal flux
+    sum_k w_k F(Q_k, grad Q_k) with the analytic gradient.
 
 Layout: u[c, v, j, i] with c = iy * nx + ix, v in (rho, rho u, rho v, rho E),
 j the y-node and i the x-node.  Space-time tensors carry a time index k in
@@ -46,9 +53,11 @@ class Mesh:
     y0: float = 0.0
     Lx: float = 10.0
     Ly: float = 10.0
-    bc_x: str = "periodic"   # "periodic" | "wall"
+    bc_x: str = "periodic"   # "periodic" | "wall" | "noslip" | "dirichlet"
     bc_y: str = "periodic"   # also "halo", "wall_halo", "halo_wall": strip of a larger mesh
                              # (south/north side takes the neighbour strip's traces)
+    lid_u: float = 0.0       # x-velocity of the north wall (no-slip)
+    dirichlet: object = None  # analytic field fn(x, y, t, P) of the "dirichlet" sides
 
     @property
     def hx(self):
@@ -83,6 +92,9 @@ class Solver:
         self.Yface_x = yc[:, None, :].expand(mesh.ny, mesh.nx, n).reshape(-1, n)  # y at nodes j
         self.y_south = (mesh.y0 + iy * mesh.hy)[:, None].expand(mesh.ny, mesh.nx).reshape(-1)
         self.y_north = self.y_south + mesh.hy
+        self.Xface_y = xc[None, :, :].expand(mesh.ny, mesh.nx, n).reshape(-1, n)  # x at nodes i
+        self.x_west = (mesh.x0 + ix * mesh.hx)[None, :].expand(mesh.ny, mesh.nx).reshape(-1)
+        self.x_east = self.x_west + mesh.hx
         # Lagrange weights folded into the time update: K1^{-1} diag(w)
         self.Kw = self.b.K1inv * self.b.w[None, :]
 
@@ -180,6 +192,48 @@ class Solver:
         f = torch.stack(F if nx != 0.0 else G, 1)  # the x- or y-flux
         return torch.stack(gq, 1), f
 
+    def _ghost_noslip(self, tr, nrm, wall_u):
+        """Ghost (q, normal flux) of a no-slip wall moving with velocity
+        (wall_u, 0) (reading R12)."""
+        P = self.P
+        nx, ny = nrm
+        rho, mx, my, E = tr["q"].unbind(1)
+        gmx = 2.0 * rho * wall_u - mx
+        gmy = -my
+        # same density and pressure: only the kinetic energy changes
+        gE = E - 0.5 * (mx * mx + my * my) / rho + 0.5 * (gmx * gmx + gmy * gmy) / rho
+        gq = [rho, gmx, gmy, gE]
+        zero = torch.zeros_like(rho)
+        F, G, _ = ph.fluxes(gq, tr["qx"].unbind(1), tr["qy"].unbind(1), 0.0 * rho, P,
+                            heat_override=(zero, zero))
+        f = torch.stack(F if nx != 0.0 else G, 1)
+        return torch.stack(gq, 1), f
+
+    def _ghost_dirichlet(self, x, y, nrm, t, dt):
+        """Ghost (q-bar, normal flux) from the analytic field at face nodes
+        (x, y), averaged over [t, t + dt] at the time nodes (reading R13)."""
+        P = self.P
+        nx, ny = nrm
+        b = self.b
+        qbar, fbar = 0.0, 0.0
+        for k in range(b.n):
+            Q, Qx, Qy = ph.field_with_gradient(self.m.dirichlet, x, y, t + float(b.xi[k]) * dt, P)
+            F, G, _ = ph.fluxes(Q, Qx, Qy, y, P)
+            qbar = qbar + float(b.w[k]) * torch.stack(Q, 1)
+            fbar = fbar + float(b.w[k]) * torch.stack(F if nx != 0.0 else G, 1)
+        return qbar, fbar
+
+    def _boundary(self, kind, side, tr, x, y, t, dt):
+        """Ghost (q, f) of a boundary of the given kind on side E, W, N or S."""
+        nrm = {"E": (1.0, 0.0), "W": (-1.0, 0.0), "N": (0.0, 1.0), "S": (0.0, -1.0)}[side]
+        if kind == "wall":
+            return self._ghost(tr, nrm, y)
+        if kind == "noslip":
+            return self._ghost_noslip(tr, nrm, self.m.lid_u if side == "N" else 0.0)
+        if kind == "dirichlet":
+            return self._ghost_dirichlet(x, y, nrm, t, dt)
+        raise ValueError(kind)
+
     def riemann(self, qL, fL, qR, fR, zL, zR, nrm, h):
         """Rusanov-type viscous flux at face nodes (x- or y-component)."""
         P = self.P
@@ -189,10 +243,11 @@ class Solver:
         s = torch.maximum(sL, sR)[:, None]
         return 0.5 * (fL + fR) - 0.5 * s * (qR - qL)
 
-    def face_fluxes(self, tr, halo=None):
+    def face_fluxes(self, tr, halo=None, t=0.0, dt=0.0):
         """F*_E, F*_W (x-fluxes along j) and G*_N, G*_S (y-fluxes along i).
         halo = {"S": (q, f), "N": (q, f)} with [nx, 4, n] face data of the
-        strips below and above (strip decomposition, bc_y "halo*")."""
+        strips below and above (strip decomposition, bc_y "halo*"); t, dt:
+        the step, for analytic boundary data."""
         m = self.m
         nxc, nyc = m.nx, m.ny
         C = m.cells
@@ -207,14 +262,16 @@ class Solver:
         Fx = self.riemann(qL, fL, qR, fR, zx, zx, (1.0, 0.0), m.hx)  # flux on c's east face
         FE = Fx.clone()
         FW = Fx[idx.roll(1, dims=1).reshape(-1)].clone()           # west face = east face of ix-1
-        if m.bc_x == "wall":
+        if m.bc_x in ("wall", "noslip", "dirichlet"):
             ix = torch.arange(C) % nxc
             last = ix == nxc - 1
             first = ix == 0
-            gq, gf = self._ghost(tr["E"], (1.0, 0.0), zx)
+            xe = self.x_east[:, None].expand(C, n)
+            xw = self.x_west[:, None].expand(C, n)
+            gq, gf = self._boundary(m.bc_x, "E", tr["E"], xe, zx, t, dt)
             FE_w = self.riemann(tr["E"]["q"], tr["E"]["f"], gq, gf, zx, zx, (1.0, 0.0), m.hx)
             FE[last] = FE_w[last]
-            gq, gf = self._ghost(tr["W"], (-1.0, 0.0), zx)
+            gq, gf = self._boundary(m.bc_x, "W", tr["W"], xw, zx, t, dt)
             FW_w = self.riemann(gq, gf, tr["W"]["q"], tr["W"]["f"], zx, zx, (1.0, 0.0), m.hx)
             FW[first] = FW_w[first]
         # ---- y-faces: face between c (below) and north[c] (above)
@@ -228,14 +285,16 @@ class Solver:
         iy = torch.arange(C) // nxc
         top = iy == nyc - 1
         bot = iy == 0
-        north = {"wall": "wall", "halo": "halo", "wall_halo": "halo", "halo_wall": "wall"}.get(m.bc_y)
-        south = {"wall": "wall", "halo": "halo", "wall_halo": "wall", "halo_wall": "halo"}.get(m.bc_y)
-        if north == "wall":
-            gq, gf = self._ghost(tr["N"], (0.0, 1.0), zN)
+        north = {"wall": "wall", "halo": "halo", "wall_halo": "halo", "halo_wall": "wall",
+                 "noslip": "noslip", "dirichlet": "dirichlet"}.get(m.bc_y)
+        south = {"wall": "wall", "halo": "halo", "wall_halo": "wall", "halo_wall": "halo",
+                 "noslip": "noslip", "dirichlet": "dirichlet"}.get(m.bc_y)
+        if north in ("wall", "noslip", "dirichlet"):
+            gq, gf = self._boundary(north, "N", tr["N"], self.Xface_y, zN, t, dt)
             GN_w = self.riemann(tr["N"]["q"], tr["N"]["f"], gq, gf, zN, zN, (0.0, 1.0), m.hy)
             GN[top] = GN_w[top]
-        if south == "wall":
-            gq, gf = self._ghost(tr["S"], (0.0, -1.0), zS)
+        if south in ("wall", "noslip", "dirichlet"):
+            gq, gf = self._boundary(south, "S", tr["S"], self.Xface_y, zS, t, dt)
             GS_w = self.riemann(gq, gf, tr["S"]["q"], tr["S"]["f"], zS, zS, (0.0, 1.0), m.hy)
             GS[bot] = GS_w[bot]
         if north == "halo":
@@ -247,13 +306,13 @@ class Solver:
         return FE, FW, GN, GS
 
     # ------------------------------------------------------------ corrector
-    def corrector(self, u, dt, tavg, halo=None):
+    def corrector(self, u, dt, tavg, halo=None, t=0.0):
         """u^{n+1} = u + dt (volume - face + Sbar), weak form with GL collocation."""
         b = self.b
         m = self.m
         w, D, p0, p1 = b.w, b.D, b.phi0, b.phi1
         tr = self.face_traces(tavg)
-        FE, FW, GN, GS = self.face_fluxes(tr, halo)
+        FE, FW, GN, GS = self.face_fluxes(tr, halo, t, dt)
         # volume: (1/hx) sum_p (w_p/w_i) D[p,i] Fbar[p,j] + (1/hy) sum_p (w_p/w_j) D[p,j] Gbar[i,p]
         Vx = (w[:, None] * D) / w[None, :]   # Vx[p, i] = w_p D[p,i] / w_i
         vol = (torch.einsum("pi,cvjp->cvji", Vx, tavg["Fbar"]) / m.hx
@@ -266,7 +325,7 @@ class Solver:
 
     def step(self, u, dt, t=0.0):
         _, tavg = self.predictor(u, dt, t)
-        return self.corrector(u, dt, tavg)
+        return self.corrector(u, dt, tavg, t=t)
 
     # ------------------------------------------------------------ utilities
     def interpolate(self, fn, t=0.0):

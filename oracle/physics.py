@@ -198,6 +198,36 @@ def paper_manufactured(x, y, t, P):
     return [rho, rho * u, rho * v, E]
 
 
+def taylor_green(x, y, t, P):
+    """The Taylor-Green vortex of Sec. 4.1 (incompressible form, imposed as
+    initial and boundary data): rho = 1, v = exp(-2 mu t) (sin x cos y,
+    -cos x sin y), p = exp(-4 mu t) (cos 2x + cos 2y) / 4 + 100/gamma."""
+    t = torch.as_tensor(t, dtype=DTYPE)
+    a = torch.exp(-2.0 * P.mu * t)
+    rho = 1.0 + 0.0 * x + 0.0 * y
+    u = a * torch.sin(x) * torch.cos(y)
+    v = -a * torch.cos(x) * torch.sin(y)
+    pr = torch.exp(-4.0 * P.mu * t) * 0.25 * (torch.cos(2.0 * x) + torch.cos(2.0 * y)) + 100.0 / P.gamma
+    E = pr / (P.gamma - 1.0) + 0.5 * rho * (u * u + v * v)
+    return [rho, rho * u, rho * v, E]
+
+
+def field_with_gradient(fn, x, y, t, P):
+    """Q, dQ/dx, dQ/dy of an analytic field fn(x, y, t, P) by automatic
+    differentiation (for Dirichlet boundary data)."""
+    shape = x.shape
+    x = x.reshape(-1).clone().requires_grad_(True)
+    y = y.reshape(-1).clone().requires_grad_(True)
+    with torch.enable_grad():
+        Q = fn(x, y, t, P)
+        qx, qy = [], []
+        for c in Q:
+            gx, gy = torch.autograd.grad(c.sum(), [x, y], allow_unused=True, retain_graph=True)
+            qx.append((torch.zeros_like(x) if gx is None else gx).detach().reshape(shape))
+            qy.append((torch.zeros_like(y) if gy is None else gy).detach().reshape(shape))
+    return [c.detach().reshape(shape) for c in Q], qx, qy
+
+
 def manufactured_field(P):
     return {"steady": steady_manufactured, "paper": paper_manufactured}[P.source]
 

@@ -24,6 +24,10 @@ ADG_BC_WALL = 1
 ADG_BC_EXCHANGE = 2
 ADG_BC_WALL_EXCHANGE = 3
 ADG_BC_EXCHANGE_WALL = 4
+ADG_BC_NOSLIP = 5
+ADG_BC_ANALYTIC = 6
+ADG_FIELD_NONE = 0
+ADG_FIELD_TAYLOR_GREEN = 1
 ADG_SRC_NONE = 0
 ADG_SRC_STEADY = 1
 ADG_SRC_PAPER = 2
@@ -36,6 +40,8 @@ ADG_SCEN_COSINE = 1
 ADG_SCEN_TWO_BUBBLES = 2
 ADG_SCEN_BACKGROUND = 3
 ADG_SCEN_PAPER = 4
+ADG_SCEN_TAYLOR_GREEN = 5
+ADG_SCEN_CAVITY = 6
 ADG_NOALLOC_SCRATCH_BYTES = 32 << 20
 
 STATUS_NAMES = {1: "ADG_EINVAL", 2: "ADG_ENOMEM", 3: "ADG_ECUDA", 4: "ADG_ENONFINITE",
@@ -54,7 +60,8 @@ class MeshDesc(ctypes.Structure):
                 ("source", ctypes.c_int), ("src_a", ctypes.c_double),
                 ("src_L", ctypes.c_double), ("src_U", ctypes.c_double),
                 ("src_p", ctypes.c_double), ("precision", ctypes.c_int),
-                ("device", ctypes.c_int), ("max_levels", ctypes.c_int)]
+                ("device", ctypes.c_int), ("max_levels", ctypes.c_int),
+                ("lid_u", ctypes.c_double), ("bc_field", ctypes.c_int)]
 
 
 class Scenario(ctypes.Structure):

@@ -316,9 +316,18 @@ int adg_create_mesh(const adg_mesh_desc* d, adg_mesh** out) {
     if (d->nx < 1 || d->ny < 1) return fail(ADG_EINVAL, "create_mesh: nx, ny must be >= 1");
     if ((long long)d->nx * d->ny > (1LL << 26)) return fail(ADG_EINVAL, "create_mesh: too many cells");
     if (!(d->Lx > 0.0) || !(d->Ly > 0.0)) return fail(ADG_EINVAL, "create_mesh: Lx, Ly must be > 0");
-    if (d->bc_x < 0 || d->bc_x > 1 || d->bc_y < 0 || d->bc_y > 4)
+    auto known_x = [](int b) { return b == ADG_BC_PERIODIC || b == ADG_BC_WALL || b == ADG_BC_NOSLIP ||
+                                      b == ADG_BC_ANALYTIC; };
+    if (!known_x(d->bc_x) || d->bc_y < 0 || d->bc_y > ADG_BC_ANALYTIC)
         return fail(ADG_EINVAL, "create_mesh: unknown boundary condition");
-    const bool exch = d->bc_y >= ADG_BC_EXCHANGE;
+    const bool cfd_bc = d->bc_x >= ADG_BC_NOSLIP || d->bc_y >= ADG_BC_NOSLIP;
+    if (cfd_bc && (d->precision != ADG_PREC_FP64 || d->max_levels != 0 || d->gravity))
+        return fail(ADG_EUNSUPPORTED, "create_mesh: no-slip and analytic boundaries are built for uniform FP64 "
+                                      "meshes without gravity");
+    if ((d->bc_x == ADG_BC_ANALYTIC || d->bc_y == ADG_BC_ANALYTIC) && d->bc_field != ADG_FIELD_TAYLOR_GREEN)
+        return fail(ADG_EINVAL, "create_mesh: analytic boundaries need bc_field = ADG_FIELD_TAYLOR_GREEN");
+    if (!std::isfinite(d->lid_u)) return fail(ADG_EINVAL, "create_mesh: lid_u must be finite");
+    const bool exch = d->bc_y >= ADG_BC_EXCHANGE && d->bc_y <= ADG_BC_EXCHANGE_WALL;
     if (exch && (d->precision != ADG_PREC_FP64 || d->max_levels != 0))
         return fail(ADG_EUNSUPPORTED, "create_mesh: strip exchange is built for uniform FP64 meshes");
     if (!(d->gamma > 1.0) || !(d->R > 0.0) || !(d->Pr > 0.0) || !(d->mu >= 0.0))
@@ -382,6 +391,8 @@ int adg_create_mesh(const adg_mesh_desc* d, adg_mesh** out) {
     P.ny = d->ny;
     P.bc_x = d->bc_x;
     P.bc_y = d->bc_y;
+    P.lid_u = d->lid_u;
+    P.bc_field = d->bc_field;
 
     int rc = set_device(m);
     if (rc) { delete m; return rc; }
@@ -442,7 +453,7 @@ int adg_create_mesh(const adg_mesh_desc* d, adg_mesh** out) {
             return rc3;
         }
     }
-    if (d->bc_y >= ADG_BC_EXCHANGE) {
+    if (d->bc_y >= ADG_BC_EXCHANGE && d->bc_y <= ADG_BC_EXCHANGE_WALL) {
         const size_t hb = 2 * (size_t)d->nx * adg::kTraceComps * m->n * 8;
         if (cudaMalloc(&m->halo, hb) != cudaSuccess || cudaMemset(m->halo, 0, hb) != cudaSuccess) {
             cudaGetLastError();
@@ -503,10 +514,13 @@ double adg_get_time(const adg_mesh* m) { return m ? m->t : 0.0; }
 
 int adg_init_scenario(adg_mesh* m, const adg_scenario* s, void* stream) {
     if (!m || !s) return fail(ADG_EINVAL, "init_scenario: NULL argument");
-    if (s->kind < ADG_SCEN_STEADY || s->kind > ADG_SCEN_PAPER)
+    if (s->kind < ADG_SCEN_STEADY || s->kind > ADG_SCEN_CAVITY)
         return fail(ADG_EINVAL, "init_scenario: unknown scenario");
-    const bool manufactured = s->kind == ADG_SCEN_STEADY || s->kind == ADG_SCEN_PAPER;
-    if (!manufactured && !m->d.gravity)
+    const bool no_gravity = s->kind == ADG_SCEN_STEADY || s->kind == ADG_SCEN_PAPER ||
+                              s->kind == ADG_SCEN_TAYLOR_GREEN || s->kind == ADG_SCEN_CAVITY;
+    if ((s->kind == ADG_SCEN_TAYLOR_GREEN || s->kind == ADG_SCEN_CAVITY) && m->d.gravity)
+        return fail(ADG_EINVAL, "init_scenario: the CFD scenarios run without gravity");
+    if (!no_gravity && !m->d.gravity)
         return fail(ADG_EINVAL, "init_scenario: bubble scenarios need gravity");
     if (s->kind == ADG_SCEN_STEADY && m->d.source != ADG_SRC_STEADY)
         return fail(ADG_EINVAL, "init_scenario: steady field needs the steady source");
@@ -563,7 +577,7 @@ static int corrector_impl(adg_mesh* m, double dt, void* stream, const adg::TvEpi
     }
     int e = m->d.precision == ADG_PREC_FP64
                 ? adg::launch_corrector_fp64(m->N, m->u, m->rvol, m->trace, m->cells, dt, m->B, m->P, m->bg, stream,
-                                             epi)
+                                             epi, m->t)
                 : adg::launch_corrector_mixed(m->N, m->u, (const float*)m->rvol, (const float*)m->trace, m->cells,
                                               dt, m->Bf, m->Pf, m->mbg, stream, epi);
     if (e) return cuda_fail((cudaError_t)e, "corrector launch");
@@ -688,7 +702,8 @@ int adg_step_adjoint(adg_mesh* m, double dt, const double* u_n, const double* la
     if (m->d.precision != ADG_PREC_FP64) return fail(ADG_EUNSUPPORTED, "step_adjoint: FP64 meshes only");
     if (m->N > 5) return fail(ADG_EUNSUPPORTED, "step_adjoint: built for degree <= 5");
     if (m->amr) return fail(ADG_EUNSUPPORTED, "step_adjoint: uniform meshes only");
-    if (m->d.bc_y >= ADG_BC_EXCHANGE) return fail(ADG_EUNSUPPORTED, "step_adjoint: strip exchange not supported");
+    if (m->d.bc_y >= ADG_BC_EXCHANGE || m->d.bc_x >= ADG_BC_NOSLIP)
+        return fail(ADG_EUNSUPPORTED, "step_adjoint: built for periodic and slip-wall boundaries");
     if (m->d.source == ADG_SRC_PAPER)
         return fail(ADG_EUNSUPPORTED, "step_adjoint: time-dependent source not supported");
     if (lam_n == lam_np1 || lam_n == u_n) return fail(ADG_EINVAL, "step_adjoint: lam_n must not alias the inputs");
@@ -710,7 +725,8 @@ int adg_step_adjoint(adg_mesh* m, double dt, const double* u_n, const double* la
 
 int adg_get_boundary_traces(adg_mesh* m, double* south, double* north, void* stream) {
     if (!m) return fail(ADG_EINVAL, "get_boundary_traces: NULL mesh");
-    if (m->d.bc_y < ADG_BC_EXCHANGE) return fail(ADG_EINVAL, "get_boundary_traces: bc_y has no exchange side");
+    if (m->d.bc_y < ADG_BC_EXCHANGE || m->d.bc_y > ADG_BC_EXCHANGE_WALL)
+        return fail(ADG_EINVAL, "get_boundary_traces: bc_y has no exchange side");
     if (!m->predicted) return fail(ADG_ESTATE, "get_boundary_traces: call adg_predictor first");
     if (int rc = set_device(m)) return rc;
     const size_t TR = (size_t)adg::kTraceComps * m->n, nx = m->d.nx;
@@ -728,7 +744,8 @@ int adg_get_boundary_traces(adg_mesh* m, double* south, double* north, void* str
 
 int adg_set_halo_traces(adg_mesh* m, const double* south, const double* north, void* stream) {
     if (!m) return fail(ADG_EINVAL, "set_halo_traces: NULL mesh");
-    if (m->d.bc_y < ADG_BC_EXCHANGE) return fail(ADG_EINVAL, "set_halo_traces: bc_y has no exchange side");
+    if (m->d.bc_y < ADG_BC_EXCHANGE || m->d.bc_y > ADG_BC_EXCHANGE_WALL)
+        return fail(ADG_EINVAL, "set_halo_traces: bc_y has no exchange side");
     if (int rc = set_device(m)) return rc;
     const size_t bytes = (size_t)m->d.nx * adg::kTraceComps * m->n * 8;
     cudaStream_t s = (cudaStream_t)stream;

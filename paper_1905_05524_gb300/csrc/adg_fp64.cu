@@ -85,13 +85,85 @@ __device__ __forceinline__ void wall_ghost(const double* rec, int f, double z, d
     sG = wave_speed(qG, z, xdir, P);
 }
 
+// No-slip wall (ADG_BC_NOSLIP): ghost density and pressure of the interior
+// trace, velocity 2 v_wall - v (v_wall = (lid_u, 0) on the north wall, zero
+// elsewhere), interior gradients, adiabatic (zero ghost heat flux).
+__device__ __forceinline__ void noslip_ghost(const double* rec, int f, double z, const Phys& P, double qG[4],
+                                             double fG[4], double& sG) {
+    const double rho = rec[0], mx = rec[1], my = rec[2];
+    const double wu = f == 2 ? P.lid_u : 0.0;
+    const double rinv = 1.0 / rho;
+    qG[0] = rho;
+    qG[1] = 2.0 * rho * wu - mx;
+    qG[2] = -my;
+    // same pressure: only the kinetic energy changes
+    qG[3] = rec[3] + 0.5 * ((qG[1] * qG[1] + qG[2] * qG[2]) - (mx * mx + my * my)) * rinv;
+    Flux4 fl;
+    ns_flux(qG, rec + 8, rec + 12, z, 0.0, 0.0, P, fl, true, 0.0, 0.0);
+    const bool xdir = f < 2;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) fG[v] = xdir ? fl.F[v] : fl.G[v];
+    sG = wave_speed(qG, z, xdir, P);
+}
+
+// The Taylor-Green field (Sec. 4.1) and its x- and y-derivatives at (x, y, t):
+// rho = 1, v = a (sin x cos y, -cos x sin y), p = b (cos 2x + cos 2y)/4 + 100/gamma,
+// a = exp(-2 mu t), b = exp(-4 mu t).
+__device__ __forceinline__ void taylor_green(double x, double y, double t, const Phys& P, double Q[4],
+                                             double Qx[4], double Qy[4]) {
+    const double a = exp(-2.0 * P.mu * t), b = exp(-4.0 * P.mu * t);
+    double sx, cx, sy, cy, s2x, c2x, s2y, c2y;
+    sincos(x, &sx, &cx);
+    sincos(y, &sy, &cy);
+    sincos(2.0 * x, &s2x, &c2x);
+    sincos(2.0 * y, &s2y, &c2y);
+    const double u = a * sx * cy, v = -a * cx * sy;
+    const double ux = a * cx * cy, uy = -a * sx * sy, vx = a * sx * sy, vy = -a * cx * cy;
+    const double p = 0.25 * b * (c2x + c2y) + 100.0 / P.gamma;
+    const double px = -0.5 * b * s2x, py = -0.5 * b * s2y;
+    Q[0] = 1.0;
+    Q[1] = u;
+    Q[2] = v;
+    Q[3] = p / P.gm1 + 0.5 * (u * u + v * v);
+    Qx[0] = 0.0;
+    Qx[1] = ux;
+    Qx[2] = vx;
+    Qx[3] = px / P.gm1 + u * ux + v * vx;
+    Qy[0] = 0.0;
+    Qy[1] = uy;
+    Qy[2] = vy;
+    Qy[3] = py / P.gm1 + u * uy + v * vy;
+}
+
+// Analytic boundary (ADG_BC_ANALYTIC): the ghost is the field's state and
+// normal flux at the face node (x, y), averaged over [t, t + dt] at the
+// Gauss-Legendre time nodes like the interior traces.
+__device__ __forceinline__ void analytic_ghost(double x, double y, int f, double t, double dt, const Basis& B,
+                                               const Phys& P, int n, double qG[4], double fG[4], double& sG) {
+    const bool xdir = f < 2;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) qG[v] = fG[v] = 0.0;
+    for (int k = 0; k < n; ++k) {
+        double Q[4], Qx[4], Qy[4];
+        taylor_green(x, y, t + B.xi[k] * dt, P, Q, Qx, Qy);
+        Flux4 fl;
+        ns_flux(Q, Qx, Qy, y, 0.0, 0.0, P, fl);
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            qG[v] += B.w[k] * Q[v];
+            fG[v] += B.w[k] * (xdir ? fl.F[v] : fl.G[v]);
+        }
+    }
+    sG = wave_speed(qG, y, xdir, P);
+}
+
 // With TV the TV indicator of the updated state follows in the same kernel
 // (tv_cell, bitwise what k_tv_cells computes).
 template <int N, int CPB, bool TV>
 __global__ void __launch_bounds__(CPB*(N + 1) * (N + 1))
 k_corrector_fp64(double* __restrict__ u, const double* __restrict__ rvol,
                  const double* __restrict__ trace, int cells, double dt, const Basis B,
-                 const Phys P, const Background bg, const TvEpilogue epi) {
+                 const Phys P, const Background bg, const TvEpilogue epi, double t) {
     constexpr int n = N + 1, n2 = n * n, SL = 4 * n2, TR = kTraceComps * n;
     __shared__ double Fst[CPB][4][4][n];
     const int cl = threadIdx.x / n2;
@@ -111,6 +183,11 @@ k_corrector_fp64(double* __restrict__ u, const double* __restrict__ rvol,
                                    (P.bc_y == ADG_BC_WALL_EXCHANGE && bot) || (P.bc_y == ADG_BC_EXCHANGE_WALL && top));
         const bool halo = !xface && ((P.bc_y == ADG_BC_EXCHANGE && (top || bot)) ||
                                      (P.bc_y == ADG_BC_WALL_EXCHANGE && top) || (P.bc_y == ADG_BC_EXCHANGE_WALL && bot));
+        // no-slip and analytic sides (Sec. 4.1 CFD scenarios)
+        const bool edge = xface ? ((f == 0 && ix == P.nx - 1) || (f == 1 && ix == 0)) : (top || bot);
+        const int side_bc = xface ? P.bc_x : P.bc_y;
+        const bool noslip = edge && side_bc == ADG_BC_NOSLIP;
+        const bool analytic = edge && side_bc == ADG_BC_ANALYTIC;
         const double* own = trace + ((size_t)cell * 4 + f) * TR;
         double rec[kTraceComps];
 #pragma unroll
@@ -132,6 +209,11 @@ k_corrector_fp64(double* __restrict__ u, const double* __restrict__ rvol,
                 rb = bg.rhobar_face[fi];
             }
             wall_ghost(rec, f, z, pb, rb, P, qn, fn, sn);
+        } else if (noslip || analytic) {
+            const double xf = xface ? P.x0 + (ix + (f == 0 ? 1 : 0)) * P.hx : P.x0 + (ix + B.xi[m]) * P.hx;
+            const double yf = xface ? P.y0 + (iy + B.xi[m]) * P.hy : P.y0 + (iy + (f == 2 ? 1 : 0)) * P.hy;
+            if (noslip) noslip_ghost(rec, f, yf, P, qn, fn, sn);
+            else analytic_ghost(xf, yf, f, t, dt, B, P, n, qn, fn, sn);
         } else {
             int nb, nf;
             if (f == 0) { nb = iy * P.nx + (ix + 1 == P.nx ? 0 : ix + 1); nf = 1; }
@@ -196,14 +278,15 @@ static int launch_pred(const double* u, double* rvol, double* trace, int cells, 
 template <int N>
 static int launch_corr(double* u, const double* rvol, const double* trace, int cells, double dt,
                        const Basis& B, const Phys& P, const Background& bg, const TvEpilogue* epi,
-                       cudaStream_t s) {
+                       double t, cudaStream_t s) {
     using C = Fp64Cfg<N>;
     const int blocks = (cells + C::cpb - 1) / C::cpb;
     if (epi)
-        k_corrector_fp64<N, C::cpb, true><<<blocks, C::threads, 0, s>>>(u, rvol, trace, cells, dt, B, P, bg, *epi);
+        k_corrector_fp64<N, C::cpb, true>
+            <<<blocks, C::threads, 0, s>>>(u, rvol, trace, cells, dt, B, P, bg, *epi, t);
     else
         k_corrector_fp64<N, C::cpb, false>
-            <<<blocks, C::threads, 0, s>>>(u, rvol, trace, cells, dt, B, P, bg, TvEpilogue{});
+            <<<blocks, C::threads, 0, s>>>(u, rvol, trace, cells, dt, B, P, bg, TvEpilogue{}, t);
     return (int)cudaGetLastError();
 }
 
@@ -225,16 +308,16 @@ int launch_predictor_fp64(int N, const double* u, double* rvol, double* trace, i
 
 int launch_corrector_fp64(int N, double* u, const double* rvol, const double* trace, int cells,
                           double dt, const Basis& B, const Phys& P, const Background& bg,
-                          void* stream, const TvEpilogue* epi) {
+                          void* stream, const TvEpilogue* epi, double t) {
     cudaStream_t s = (cudaStream_t)stream;
     switch (N) {
-        case 1: return launch_corr<1>(u, rvol, trace, cells, dt, B, P, bg, epi, s);
-        case 2: return launch_corr<2>(u, rvol, trace, cells, dt, B, P, bg, epi, s);
-        case 3: return launch_corr<3>(u, rvol, trace, cells, dt, B, P, bg, epi, s);
-        case 4: return launch_corr<4>(u, rvol, trace, cells, dt, B, P, bg, epi, s);
-        case 5: return launch_corr<5>(u, rvol, trace, cells, dt, B, P, bg, epi, s);
-        case 6: return launch_corr<6>(u, rvol, trace, cells, dt, B, P, bg, epi, s);
-        case 7: return launch_corr<7>(u, rvol, trace, cells, dt, B, P, bg, epi, s);
+        case 1: return launch_corr<1>(u, rvol, trace, cells, dt, B, P, bg, epi, t, s);
+        case 2: return launch_corr<2>(u, rvol, trace, cells, dt, B, P, bg, epi, t, s);
+        case 3: return launch_corr<3>(u, rvol, trace, cells, dt, B, P, bg, epi, t, s);
+        case 4: return launch_corr<4>(u, rvol, trace, cells, dt, B, P, bg, epi, t, s);
+        case 5: return launch_corr<5>(u, rvol, trace, cells, dt, B, P, bg, epi, t, s);
+        case 6: return launch_corr<6>(u, rvol, trace, cells, dt, B, P, bg, epi, t, s);
+        case 7: return launch_corr<7>(u, rvol, trace, cells, dt, B, P, bg, epi, t, s);
     }
     return (int)cudaErrorInvalidValue;
 }

@@ -37,6 +37,8 @@ struct Phys {
     int source;
     double sa, sL, sU, sp;    // steady manufactured source parameters
     int nx, ny, bc_x, bc_y;
+    double lid_u = 0.0;       // ADG_BC_NOSLIP: x-velocity of the north wall
+    int bc_field = 0;         // ADG_BC_ANALYTIC: ADG_FIELD_*
 };
 
 // Per-mesh device tables of the hydrostatic background (zero without gravity).
@@ -134,9 +136,10 @@ struct TvEpilogue {
 int launch_predictor_fp64(int N, const double* u, double* rvol, double* trace, int cells,
                           double dt, double t, const Basis& B, const Phys& P,
                           const Background& bg, void* stream);
+// t: time at the start of the step (analytic boundary data)
 int launch_corrector_fp64(int N, double* u, const double* rvol, const double* trace, int cells,
                           double dt, const Basis& B, const Phys& P, const Background& bg,
-                          void* stream, const TvEpilogue* epi = nullptr);
+                          void* stream, const TvEpilogue* epi = nullptr, double t = 0.0);
 int launch_predictor_mixed(int N, const double* u, float* rvol, float* trace, int cells, double dt,
                            const BasisF& B, const PhysF& P, const MixedBg& bg, void* stream);
 int launch_corrector_mixed(int N, double* u, const float* rvol, const float* trace, int cells,

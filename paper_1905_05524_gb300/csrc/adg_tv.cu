@@ -249,6 +249,17 @@ __global__ void k_init(double* __restrict__ u, int cells, int kind, double A, do
         q[1] = rho * P.sU;
         q[2] = rho * P.sU;
         q[3] = P.sp / P.gm1 + 0.5 * rho * (2.0 * P.sU * P.sU);
+    } else if (kind == ADG_SCEN_TAYLOR_GREEN || kind == ADG_SCEN_CAVITY) {  // Sec. 4.1 CFD scenarios
+        double u = 0.0, v = 0.0, p = 100.0 / P.gamma;
+        if (kind == ADG_SCEN_TAYLOR_GREEN) {
+            u = sin(x) * cos(z);
+            v = -cos(x) * sin(z);
+            p += 0.25 * (cos(2.0 * x) + cos(2.0 * z));
+        }
+        q[0] = 1.0;
+        q[1] = u;
+        q[2] = v;
+        q[3] = p / P.gm1 + 0.5 * (u * u + v * v);
     } else if (kind == ADG_SCEN_PAPER) {  // Eq. 8 at t = 0
         double s, c;
         sincos(2.0 * 3.14159265358979323846 / P.sL * (x + z), &s, &c);

@@ -41,6 +41,8 @@ class MeshConfig:
     precision: int = L.ADG_PREC_FP64
     device: int = 0
     max_levels: int = 0
+    lid_u: float = 0.0
+    bc_field: int = L.ADG_FIELD_NONE
 
     def to_c(self):
         return L.MeshDesc(**{f: getattr(self, f) for f, _ in L.MeshDesc._fields_})
@@ -65,6 +67,23 @@ def paper_manufactured_config(degree=3, nx=9, ny=9, mu=0.1, device=0):
     """Periodic [0,10]^2, gamma 1.4, Pr 0.7, c_v 1, with the time-dependent
     manufactured solution of Sec. 4.1 (Eq. 8) and its source (FP64)."""
     return MeshConfig(degree=degree, nx=nx, ny=ny, mu=mu, source=L.ADG_SRC_PAPER, device=device)
+
+
+def taylor_green_config(degree=4, nx=25, ny=25, device=0):
+    """Taylor-Green vortex (Sec. 4.1): [0, 2pi]^2, gamma 1.4, Pr 0.7, c_v 1,
+    mu = 0.1, the analytic field imposed on every boundary."""
+    two_pi = 2.0 * 3.141592653589793
+    return MeshConfig(degree=degree, nx=nx, ny=ny, Lx=two_pi, Ly=two_pi, mu=0.1,
+                      bc_x=L.ADG_BC_ANALYTIC, bc_y=L.ADG_BC_ANALYTIC, bc_field=L.ADG_FIELD_TAYLOR_GREEN,
+                      device=device)
+
+
+def cavity_config(degree=2, nx=27, ny=27, mu=0.01, lid_u=1.0, device=0):
+    """Lid-driven cavity (Sec. 4.1): [0, 1]^2 m with no-slip walls, the lid
+    (north wall) moving at lid_u; gamma 1.4, Pr 0.7, c_v 1; mu = 0.01
+    (Reynolds number 100 at rho = 1, the paper does not state mu)."""
+    return MeshConfig(degree=degree, nx=nx, ny=ny, Lx=1.0, Ly=1.0, mu=mu,
+                      bc_x=L.ADG_BC_NOSLIP, bc_y=L.ADG_BC_NOSLIP, lid_u=lid_u, device=device)
 
 
 def atmosphere_config(degree=5, nx=81, ny=81, mu=0.01, precision=L.ADG_PREC_FP64, device=0):

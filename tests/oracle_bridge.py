@@ -8,9 +8,10 @@ from oracle import physics as ph
 
 
 def oracle_for(cfg):
-    bc = {0: "periodic", 1: "wall"}
+    bc = {0: "periodic", 1: "wall", 5: "noslip", 6: "dirichlet"}
+    field = {0: None, 1: ph.taylor_green}[getattr(cfg, "bc_field", 0)]
     mesh = OMesh(nx=cfg.nx, ny=cfg.ny, x0=cfg.x0, y0=cfg.y0, Lx=cfg.Lx, Ly=cfg.Ly,
-                 bc_x=bc[cfg.bc_x], bc_y=bc[cfg.bc_y])
+                 bc_x=bc[cfg.bc_x], bc_y=bc[cfg.bc_y], lid_u=getattr(cfg, "lid_u", 0.0), dirichlet=field)
     P = ph.Params(N=cfg.degree, gamma=cfg.gamma, Pr=cfg.Pr, R=cfg.R, mu=cfg.mu,
                   gravity=bool(cfg.gravity), g=cfg.g, p0=cfg.p0, theta0=cfg.theta0,
                   source={0: "none", 1: "steady", 2: "paper"}[cfg.source])
@@ -27,6 +28,19 @@ def steady_field(solver, cfg):
 def paper_field(solver, t=0.0):
     """Oracle nodal interpolation of the Eq. 8 field at time t."""
     return solver.interpolate(ph.paper_manufactured, t)
+
+
+def taylor_green_field(solver, t=0.0):
+    """Oracle nodal interpolation of the Taylor-Green field at time t."""
+    return solver.interpolate(ph.taylor_green, t)
+
+
+def cavity_field(solver):
+    """Fluid at rest, rho = 1, p = 100/gamma."""
+    import torch
+    P = solver.P
+    one = torch.ones_like(solver.X)
+    return torch.stack([one, 0.0 * one, 0.0 * one, (100.0 / P.gamma) / (P.gamma - 1.0) * one], 1)
 
 
 def cosine_field(solver, A=0.5, a=250.0, xc=500.0, zc=350.0):
