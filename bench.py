@@ -23,7 +23,7 @@ independent replica (weak scaling, no data-path collective); the time is the
 max over ranks.
 
 --impl reference times the FP64 CPU oracle on the host cores on a bounded
-sample of the same workload (the tier's reference arm).
+sample of the same workload (the paper has no code to run as a reference).
 """
 import argparse
 import json
@@ -674,6 +674,12 @@ def run_ours(args):
             cpu = {"value": cval, "unit": UNIT, "cores": ccores, "kind": "oracle",
                    "sample": f"{args.cpu_steps} full steps (predictor+corrector+TV) of the same "
                              f"81x81 degree-5 workload, {csec:.1f} s"}
+            import torch as _t
+            nthreads = _t.get_num_threads()
+            v1, s1, _ = oracle_sample(1, threads=1)  # the same oracle on one core
+            _t.set_num_threads(nthreads)
+            cpu["value_1_core"] = v1
+            cpu["sample_1_core"] = f"1 full step of the same workload on 1 thread, {s1:.1f} s"
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
