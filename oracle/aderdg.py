@@ -5,8 +5,7 @@ an element-local space-time predictor followed by a corrector with one face
 exchange per step, and a Rusanov-type numerical flux adapted to viscous terms
 (Gassner et al. 2008, used with ADER-DG in Dumbser 2010; Sec. 3).  The paper
 does not print the scheme, so the steps below are the standard ADER-DG
-predictor/corrector written from the mathematics, with these readings (each
-listed in DESIGN.md):
+predictor/corrector written from the mathematics, with these readings:
 
 P1  the Picard iteration of the predictor runs a fixed n = N+1 sweeps;
 P2  after the last sweep grad q, F, G and S are evaluated once more on the
