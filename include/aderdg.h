@@ -293,6 +293,32 @@ size_t adg_leaf_count(const adg_mesh* m);
 int adg_leaf_info(const adg_mesh* m, int* out, size_t count);
 int adg_adapt(adg_mesh* m, const int8_t* flags, int* leaves_out, void* stream);
 
+/* ---- MUSCL-Hancock finite volumes (the paper's second scheme, Sec. 3) ----
+ *
+ * Unsplit MUSCL-Hancock on cell averages with the van Albada limiter, run
+ * without viscosity as in the colliding-bubbles run of Sec. 4.2 ("as we use
+ * limiting, we do not need any viscosity"): slopes of the perturbation from
+ * the hydrostatic background (the atmosphere at rest is kept exactly), a
+ * half-step evolution of the face states, Rusanov fluxes (s = |v.n| + c),
+ * the perturbation form of Eq. 7 and slip walls with background ghosts.
+ * FP64.  The descriptor supplies nx, ny, the box, bc_x / bc_y (periodic or
+ * ADG_BC_WALL), gamma, R, gravity, g, p0, theta0 and device; mu must be 0.
+ * State: double[4][ny][nx] cell averages of (rho, rho u, rho v, rho E).
+ * adg_fv_step: one step of fixed dt (two kernels: face states at the half
+ *   step, then fluxes and update).  adg_fv_stable_dt: cfl / (max(|u| + c)/hx
+ *   + max(|v| + c)/hy); synchronises `stream`.  adg_fv_init_scenario: cell
+ *   centre values of ADG_SCEN_COSINE, ADG_SCEN_TWO_BUBBLES or
+ *   ADG_SCEN_BACKGROUND (gravity on).  Errors as for adg_mesh. */
+typedef struct adg_fv adg_fv;
+int adg_fv_create(const adg_mesh_desc* desc, adg_fv** out);
+void adg_fv_destroy(adg_fv* f);
+size_t adg_fv_state_count(const adg_fv* f);
+int adg_fv_set_state(adg_fv* f, const double* u, size_t count, int on_device, void* stream);
+int adg_fv_get_state(adg_fv* f, double* u, size_t count, int on_device, void* stream);
+int adg_fv_init_scenario(adg_fv* f, const adg_scenario* s, void* stream);
+int adg_fv_step(adg_fv* f, double dt, void* stream);
+int adg_fv_stable_dt(adg_fv* f, double cfl, double* dt, void* stream);
+
 /* Text of the last error on the calling thread ("" if none). */
 const char* adg_last_error(void);
 

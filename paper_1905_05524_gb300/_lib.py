@@ -96,6 +96,14 @@ SIGNATURES = {
     "adg_step": (_I, [_P, _D, _P]),
     "adg_stable_dt": (_I, [_P, _D, ctypes.POINTER(_D), _P]),
     "adg_tv_indicator": (_I, [_P, _I, _D, _D, _P, _P, _P, _P]),
+    "adg_fv_create": (_I, [ctypes.POINTER(MeshDesc), ctypes.POINTER(_P)]),
+    "adg_fv_destroy": (None, [_P]),
+    "adg_fv_state_count": (_S, [_P]),
+    "adg_fv_set_state": (_I, [_P, _P, _S, _I, _P]),
+    "adg_fv_get_state": (_I, [_P, _P, _S, _I, _P]),
+    "adg_fv_init_scenario": (_I, [_P, _P, _P]),
+    "adg_fv_step": (_I, [_P, _D, _P]),
+    "adg_fv_stable_dt": (_I, [_P, _D, _P, _P]),
     "adg_step_tv": (_I, [_P, _D, _I, _D, _D, _P, _P, _P, _P]),
     "adg_check_finite": (_I, [_P, _P]),
     "adg_step_adjoint": (_I, [_P, _D, _P, _P, _P, _P]),

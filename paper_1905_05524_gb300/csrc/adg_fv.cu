@@ -1,0 +1,440 @@
+// MUSCL-Hancock finite-volume scheme with the van Albada limiter for the
+// inviscid equations of Sec. 2 (the paper's second scheme, Sec. 3; run
+// without viscosity on the colliding bubbles, Sec. 4.2).  Unsplit MUSCL-
+// Hancock on cell averages of (rho, rho u, rho v, rho E), FP64:
+//
+//  1. k_fv_half, one thread per cell: perturbations U' = U - Ubar(z_centre)
+//     of the hydrostatic background (zero without gravity), van Albada
+//     slopes a b (a + b) / (a^2 + b^2) of U' per direction (zero next to a
+//     wall in its direction), face states Ubar(z_face) + U' +- slope/2 (the
+//     background at rest is reproduced exactly at every face), their
+//     half-step evolution with the cell's own flux differences and the
+//     source -g rho' at the centre; writes the four face states and the
+//     half-step rho' of the cell.
+//  2. k_fv_update, one thread per cell: Rusanov fluxes (s = max |v.n| + c)
+//     on its four faces from its own and its neighbours' face states (a
+//     slip-wall ghost with the background rho, rhoE and reflected momentum
+//     on walls), then U -= dt/h (flux differences) and the source at the
+//     half-step mean.  Each face is computed by both its cells with the
+//     same operands in the same order, so both see bitwise the same flux.
+//
+// Momentum fluxes carry p' = p - pbar(z) at the height where they are
+// evaluated (Eq. 7).  State layout: u[v][iy][ix] (structure of arrays).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "adg_internal.h"
+#include "adg_mesh.h"
+
+struct adg_fv {
+    adg_mesh_desc d;
+    int cells = 0;
+    double hx = 0, hy = 0, gm1 = 0;
+    double* u = nullptr;       // [4][cells]
+    double* half = nullptr;    // [17][cells]: UE, UW, UN, US (4 each), rho' at the half step
+    double* bg = nullptr;      // [6][ny] centre rhobar, Ebar, pbar; [3][ny + 1] face rhobar, Ebar, pbar
+    double* part = nullptr;    // stable-dt block maxima
+    int part_blocks = 0;
+};
+
+namespace adg {
+namespace {
+
+struct FvPhys {
+    double gamma, gm1, g, hx, hy, x0, y0;
+    int nx, ny, cells, wall_x, wall_y, gravity;
+    const double* rbc;  // [ny] background at cell centres
+    const double* Ebc;
+    const double* pbc;
+    const double* rbf;  // [ny + 1] background at horizontal faces
+    const double* Ebf;
+    const double* pbf;
+};
+
+__device__ __forceinline__ double van_albada(double a, double b) {
+    const double ab = a * b;
+    return ab > 0.0 ? ab * (a + b) / (a * a + b * b) : 0.0;
+}
+
+// inviscid flux along x (xdir) or y with p' = p - pbar at height z
+__device__ __forceinline__ void euler_flux(const double q[4], double z, double pbar, bool xdir, const FvPhys& P,
+                                           double f[4]) {
+    const double rinv = 1.0 / q[0];
+    const double u = q[1] * rinv, v = q[2] * rinv;
+    const double gz = P.gravity ? P.g * z : 0.0;
+    const double p = P.gm1 * (q[3] - 0.5 * (q[1] * u + q[2] * v) - q[0] * gz);
+    const double vn = xdir ? u : v;
+    f[0] = xdir ? q[1] : q[2];
+    f[1] = q[1] * vn + (xdir ? p - pbar : 0.0);
+    f[2] = q[2] * vn + (xdir ? 0.0 : p - pbar);
+    f[3] = vn * (q[3] + p);
+}
+
+__device__ __forceinline__ double euler_speed(const double q[4], double z, bool xdir, const FvPhys& P) {
+    const double rinv = 1.0 / q[0];
+    const double u = q[1] * rinv, v = q[2] * rinv;
+    const double gz = P.gravity ? P.g * z : 0.0;
+    const double p = P.gm1 * (q[3] - 0.5 * (q[1] * u + q[2] * v) - q[0] * gz);
+    return fabs(xdir ? u : v) + sqrt(P.gamma * p * rinv);
+}
+
+// F* = (F_L + F_R)/2 - max(s_L, s_R)(q_R - q_L)/2 with explicit rounding
+__device__ __forceinline__ void rusanov_fv(const double qL[4], const double qR[4], double z, double pbar, bool xdir,
+                                           const FvPhys& P, double out[4]) {
+    double fL[4], fR[4];
+    euler_flux(qL, z, pbar, xdir, P, fL);
+    euler_flux(qR, z, pbar, xdir, P, fR);
+    const double hs = __dmul_rn(-0.5, fmax(euler_speed(qL, z, xdir, P), euler_speed(qR, z, xdir, P)));
+#pragma unroll
+    for (int v = 0; v < 4; ++v)
+        out[v] = __fma_rn(hs, __dsub_rn(qR[v], qL[v]), __dmul_rn(0.5, __dadd_rn(fL[v], fR[v])));
+}
+
+// slip-wall ghost of a face state (background rho, rhoE at height z with gravity)
+__device__ __forceinline__ void wall_ghost_fv(const double q[4], double nx, double ny, double rbf, double Ebf,
+                                              const FvPhys& P, double g[4]) {
+    const double mn = q[1] * nx + q[2] * ny;
+    g[0] = P.gravity ? rbf : q[0];
+    g[1] = q[1] - 2.0 * mn * nx;
+    g[2] = q[2] - 2.0 * mn * ny;
+    g[3] = P.gravity ? Ebf : q[3];
+}
+
+__global__ void __launch_bounds__(256) k_fv_half(const double* __restrict__ u, double* __restrict__ half,
+                                                 double dt, const FvPhys P) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= P.cells) return;
+    const int ix = c % P.nx, iy = c / P.nx;
+    const int e = iy * P.nx + (ix + 1 == P.nx ? 0 : ix + 1), w = iy * P.nx + (ix == 0 ? P.nx - 1 : ix - 1);
+    const int nn = (iy + 1 == P.ny ? 0 : iy + 1) * P.nx + ix, s = (iy == 0 ? P.ny - 1 : iy - 1) * P.nx + ix;
+    const int iyn = iy + 1 == P.ny ? 0 : iy + 1, iys = iy == 0 ? P.ny - 1 : iy - 1;
+    const bool flat_x = P.wall_x && (ix == 0 || ix == P.nx - 1);
+    const bool flat_y = P.wall_y && (iy == 0 || iy == P.ny - 1);
+    const double bc[4] = {P.rbc[iy], 0.0, 0.0, P.Ebc[iy]};
+    const double bn[4] = {P.rbc[iyn], 0.0, 0.0, P.Ebc[iyn]};
+    const double bs[4] = {P.rbc[iys], 0.0, 0.0, P.Ebc[iys]};
+    const double bfn[4] = {P.rbf[iy + 1], 0.0, 0.0, P.Ebf[iy + 1]};
+    const double bfs[4] = {P.rbf[iy], 0.0, 0.0, P.Ebf[iy]};
+    double UE[4], UW[4], UN[4], US[4], U[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+        const size_t o = (size_t)v * P.cells;
+        U[v] = u[o + c];
+        const double up = U[v] - bc[v];
+        const double sx = flat_x ? 0.0 : van_albada(up - (u[o + w] - bc[v]), (u[o + e] - bc[v]) - up);
+        const double sy = flat_y ? 0.0 : van_albada(up - (u[o + s] - bs[v]), (u[o + nn] - bn[v]) - up);
+        UE[v] = U[v] + 0.5 * sx;
+        UW[v] = U[v] - 0.5 * sx;
+        UN[v] = bfn[v] + up + 0.5 * sy;
+        US[v] = bfs[v] + up - 0.5 * sy;
+    }
+    const double zc = P.y0 + (iy + 0.5) * P.hy;
+    const double zn = P.y0 + (iy + 1) * P.hy, zs = P.y0 + iy * P.hy;
+    double fE[4], fW[4], gN[4], gS[4];
+    euler_flux(UE, zc, P.pbc[iy], true, P, fE);
+    euler_flux(UW, zc, P.pbc[iy], true, P, fW);
+    euler_flux(UN, zn, P.pbf[iy + 1], false, P, gN);
+    euler_flux(US, zs, P.pbf[iy], false, P, gS);
+    const double ax = 0.5 * dt / P.hx, ay = 0.5 * dt / P.hy;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+        double d = -ax * (fE[v] - fW[v]) - ay * (gN[v] - gS[v]);
+        if (v == 2 && P.gravity) d += 0.5 * dt * (-P.g * (U[0] - bc[0]));
+        half[(size_t)(0 + v) * P.cells + c] = UE[v] + d;
+        half[(size_t)(4 + v) * P.cells + c] = UW[v] + d;
+        half[(size_t)(8 + v) * P.cells + c] = UN[v] + d;
+        half[(size_t)(12 + v) * P.cells + c] = US[v] + d;
+        if (v == 0) half[(size_t)16 * P.cells + c] = (U[0] + d) - bc[0];  // rho' of the half-step mean
+    }
+}
+
+__global__ void __launch_bounds__(256) k_fv_update(double* __restrict__ u, const double* __restrict__ half,
+                                                   double dt, const FvPhys P) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= P.cells) return;
+    const int ix = c % P.nx, iy = c / P.nx;
+    const int e = iy * P.nx + (ix + 1 == P.nx ? 0 : ix + 1), w = iy * P.nx + (ix == 0 ? P.nx - 1 : ix - 1);
+    const int nn = (iy + 1 == P.ny ? 0 : iy + 1) * P.nx + ix, s = (iy == 0 ? P.ny - 1 : iy - 1) * P.nx + ix;
+    auto ld = [&](int slot, int cell, double q[4]) {
+#pragma unroll
+        for (int v = 0; v < 4; ++v) q[v] = half[(size_t)(slot + v) * P.cells + cell];
+    };
+    const double zc = P.y0 + (iy + 0.5) * P.hy;
+    const double zn = P.y0 + (iy + 1) * P.hy, zs = P.y0 + iy * P.hy;
+    double own[4], nb[4], FE[4], FW[4], GN[4], GS[4];
+    // east face: own E state (left), east neighbour's W state (right)
+    ld(0, c, own);
+    if (P.wall_x && ix == P.nx - 1) wall_ghost_fv(own, 1.0, 0.0, P.rbc[iy], P.Ebc[iy], P, nb);
+    else ld(4, e, nb);
+    rusanov_fv(own, nb, zc, P.pbc[iy], true, P, FE);
+    // west face: west neighbour's E state (left), own W state (right)
+    ld(4, c, own);
+    if (P.wall_x && ix == 0) wall_ghost_fv(own, -1.0, 0.0, P.rbc[iy], P.Ebc[iy], P, nb);
+    else ld(0, w, nb);
+    rusanov_fv(nb, own, zc, P.pbc[iy], true, P, FW);
+    // north face: own N state (below), north neighbour's S state (above)
+    ld(8, c, own);
+    if (P.wall_y && iy == P.ny - 1) wall_ghost_fv(own, 0.0, 1.0, P.rbf[iy + 1], P.Ebf[iy + 1], P, nb);
+    else ld(12, nn, nb);
+    rusanov_fv(own, nb, zn, P.pbf[iy + 1], false, P, GN);
+    // south face: south neighbour's N state (below), own S state (above)
+    ld(12, c, own);
+    if (P.wall_y && iy == 0) wall_ghost_fv(own, 0.0, -1.0, P.rbf[iy], P.Ebf[iy], P, nb);
+    else ld(8, s, nb);
+    rusanov_fv(nb, own, zs, P.pbf[iy], false, P, GS);
+    const double rp = half[(size_t)16 * P.cells + c];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+        const size_t o = (size_t)v * P.cells + c;
+        double du = -dt / P.hx * (FE[v] - FW[v]) - dt / P.hy * (GN[v] - GS[v]);
+        if (v == 2 && P.gravity) du += dt * (-P.g * rp);
+        u[o] += du;
+    }
+}
+
+// per-block maxima of (|u| + c) and (|v| + c) at cell centres
+__global__ void __launch_bounds__(256) k_fv_speed(const double* __restrict__ u, double* __restrict__ part,
+                                                  const FvPhys P) {
+    __shared__ double sx[256], sy[256];
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    double ax = 0.0, ay = 0.0;
+    if (c < P.cells) {
+        const int iy = c / P.nx;
+        double q[4];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) q[v] = u[(size_t)v * P.cells + c];
+        const double zc = P.y0 + (iy + 0.5) * P.hy;
+        ax = euler_speed(q, zc, true, P);
+        ay = euler_speed(q, zc, false, P);
+    }
+    sx[threadIdx.x] = ax;
+    sy[threadIdx.x] = ay;
+    __syncthreads();
+    for (int k = blockDim.x / 2; k > 0; k >>= 1) {
+        if ((int)threadIdx.x < k) {
+            sx[threadIdx.x] = fmax(sx[threadIdx.x], sx[threadIdx.x + k]);
+            sy[threadIdx.x] = fmax(sy[threadIdx.x], sy[threadIdx.x + k]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        part[2 * blockIdx.x] = sx[0];
+        part[2 * blockIdx.x + 1] = sy[0];
+    }
+}
+
+__device__ double fv_bubble(double x, double z, double A, double a, double s, double xc, double zc) {
+    const double r = sqrt((x - xc) * (x - xc) + (z - zc) * (z - zc));
+    return r <= a ? A : A * exp(-((r - a) * (r - a)) / (s * s));
+}
+
+// point values at cell centres: background atmosphere with theta' (Sec. 4.2)
+__global__ void k_fv_init(double* __restrict__ u, int kind, double A, double a, double xc, double zc,
+                          double R, double cp, double p0, double theta0, const FvPhys P) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= P.cells) return;
+    const int ix = c % P.nx, iy = c / P.nx;
+    const double x = P.x0 + (ix + 0.5) * P.hx, z = P.y0 + (iy + 0.5) * P.hy;
+    double th = 0.0;
+    if (kind == ADG_SCEN_COSINE) {
+        const double r = sqrt((x - xc) * (x - xc) + (z - zc) * (z - zc));
+        th = r <= a ? 0.5 * A * (1.0 + cos(3.14159265358979323846 * r / a)) : 0.0;
+    } else if (kind == ADG_SCEN_TWO_BUBBLES) {
+        th = fv_bubble(x, z, 0.5, 150.0, 50.0, 500.0, 300.0) + fv_bubble(x, z, -0.15, 0.0, 50.0, 560.0, 640.0);
+    }
+    const double ex = 1.0 - P.g * z / (cp * theta0);
+    const double pb = p0 * pow(ex, cp / R);
+    const double rho = pb / (R * (theta0 + th) * ex);
+    u[c] = rho;
+    u[(size_t)P.cells + c] = 0.0;
+    u[(size_t)2 * P.cells + c] = 0.0;
+    u[(size_t)3 * P.cells + c] = pb / P.gm1 + rho * P.g * z;
+}
+
+FvPhys fv_phys(const adg_fv* f) {
+    FvPhys P;
+    P.gamma = f->d.gamma;
+    P.gm1 = f->gm1;
+    P.g = f->d.gravity ? f->d.g : 0.0;
+    P.hx = f->hx;
+    P.hy = f->hy;
+    P.x0 = f->d.x0;
+    P.y0 = f->d.y0;
+    P.nx = f->d.nx;
+    P.ny = f->d.ny;
+    P.cells = f->cells;
+    P.wall_x = f->d.bc_x == ADG_BC_WALL;
+    P.wall_y = f->d.bc_y == ADG_BC_WALL;
+    P.gravity = f->d.gravity ? 1 : 0;
+    const int ny = f->d.ny;
+    P.rbc = f->bg;
+    P.Ebc = f->bg + ny;
+    P.pbc = f->bg + 2 * ny;
+    P.rbf = f->bg + 3 * ny;
+    P.Ebf = f->bg + 3 * ny + (ny + 1);
+    P.pbf = f->bg + 3 * ny + 2 * (ny + 1);
+    return P;
+}
+
+int fv_blocks(int cells) { return (cells + 255) / 256; }
+
+}  // namespace
+}  // namespace adg
+
+using adg::cuda_fail;
+using adg::fail;
+
+static int fv_device(const adg_fv* f) {
+    cudaError_t e = cudaSetDevice(f->d.device);
+    return e == cudaSuccess ? ADG_OK : cuda_fail(e, "fv: cudaSetDevice");
+}
+
+static void fv_free(adg_fv* f) {
+    if (!f) return;
+    cudaSetDevice(f->d.device);
+    cudaFree(f->u);
+    cudaFree(f->half);
+    cudaFree(f->bg);
+    cudaFree(f->part);
+    delete f;
+}
+
+extern "C" int adg_fv_create(const adg_mesh_desc* d, adg_fv** out) {
+    if (!d || !out) return fail(ADG_EINVAL, "fv_create: NULL argument");
+    *out = nullptr;
+    if (d->nx < 1 || d->ny < 1 || (long long)d->nx * d->ny > (1LL << 28))
+        return fail(ADG_EINVAL, "fv_create: bad mesh size");
+    if (!(d->Lx > 0.0) || !(d->Ly > 0.0)) return fail(ADG_EINVAL, "fv_create: Lx, Ly must be > 0");
+    if ((d->bc_x != ADG_BC_PERIODIC && d->bc_x != ADG_BC_WALL) || (d->bc_y != ADG_BC_PERIODIC && d->bc_y != ADG_BC_WALL))
+        return fail(ADG_EINVAL, "fv_create: boundaries are periodic or slip walls");
+    if (!(d->gamma > 1.0) || !(d->R > 0.0)) return fail(ADG_EINVAL, "fv_create: invalid gas constants");
+    if (d->mu != 0.0) return fail(ADG_EINVAL, "fv_create: the finite-volume scheme is inviscid (mu = 0)");
+    if (d->precision != ADG_PREC_FP64) return fail(ADG_EUNSUPPORTED, "fv_create: FP64 only");
+    if (d->gravity && !(d->theta0 > 0.0 && d->p0 > 0.0))
+        return fail(ADG_EINVAL, "fv_create: gravity needs theta0 > 0 and p0 > 0");
+    int ndev = 0;
+    ADG_CK(cudaGetDeviceCount(&ndev), "cudaGetDeviceCount");
+    if (d->device < 0 || d->device >= ndev) return fail(ADG_EINVAL, "fv_create: bad device ordinal");
+    adg_fv* f = new adg_fv();
+    f->d = *d;
+    f->cells = d->nx * d->ny;
+    f->hx = d->Lx / d->nx;
+    f->hy = d->Ly / d->ny;
+    f->gm1 = d->gamma - 1.0;
+    if (int rc = fv_device(f)) {
+        delete f;
+        return rc;
+    }
+    const int ny = d->ny;
+    f->part_blocks = adg::fv_blocks(f->cells);
+    const size_t nbg = 3 * (size_t)ny + 3 * (size_t)(ny + 1);
+    if (cudaMalloc(&f->u, (size_t)4 * f->cells * 8) != cudaSuccess ||
+        cudaMalloc(&f->half, (size_t)17 * f->cells * 8) != cudaSuccess || cudaMalloc(&f->bg, nbg * 8) != cudaSuccess ||
+        cudaMalloc(&f->part, (size_t)2 * f->part_blocks * 8) != cudaSuccess) {
+        cudaGetLastError();
+        fv_free(f);
+        return fail(ADG_ENOMEM, "fv_create: device allocation failed");
+    }
+    // isentropic background (Eq. 6 reading) at centres and faces; zero without gravity
+    std::vector<double> h(nbg, 0.0);
+    if (d->gravity) {
+        const double cp = d->gamma * d->R / (d->gamma - 1.0);
+        auto bgp = [&](double z, double& r, double& E, double& p) {
+            const double ex = 1.0 - d->g * z / (cp * d->theta0);
+            p = d->p0 * std::pow(ex, cp / d->R);
+            r = p / (d->R * d->theta0 * ex);
+            E = p / f->gm1 + r * d->g * z;
+        };
+        for (int iy = 0; iy < ny; ++iy) bgp(d->y0 + (iy + 0.5) * f->hy, h[iy], h[ny + iy], h[2 * ny + iy]);
+        for (int k = 0; k <= ny; ++k)
+            bgp(d->y0 + k * f->hy, h[3 * ny + k], h[3 * ny + (ny + 1) + k], h[3 * ny + 2 * (ny + 1) + k]);
+    }
+    if (cudaMemcpy(f->bg, h.data(), nbg * 8, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(f->u, 0, (size_t)4 * f->cells * 8) != cudaSuccess) {
+        cudaGetLastError();
+        fv_free(f);
+        return fail(ADG_ECUDA, "fv_create: initialisation failed");
+    }
+    *out = f;
+    return ADG_OK;
+}
+
+extern "C" void adg_fv_destroy(adg_fv* f) { fv_free(f); }
+
+extern "C" size_t adg_fv_state_count(const adg_fv* f) { return f ? (size_t)4 * f->cells : 0; }
+
+extern "C" int adg_fv_set_state(adg_fv* f, const double* u, size_t count, int on_device, void* stream) {
+    if (!f || !u) return fail(ADG_EINVAL, "fv_set_state: NULL argument");
+    if (count != (size_t)4 * f->cells) return fail(ADG_EINVAL, "fv_set_state: count must be 4 * cells");
+    if (int rc = fv_device(f)) return rc;
+    ADG_CK(cudaMemcpyAsync(f->u, u, count * 8, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                           (cudaStream_t)stream),
+           "fv_set_state");
+    if (!on_device) ADG_CK(cudaStreamSynchronize((cudaStream_t)stream), "fv_set_state sync");
+    return ADG_OK;
+}
+
+extern "C" int adg_fv_get_state(adg_fv* f, double* u, size_t count, int on_device, void* stream) {
+    if (!f || !u) return fail(ADG_EINVAL, "fv_get_state: NULL argument");
+    if (count != (size_t)4 * f->cells) return fail(ADG_EINVAL, "fv_get_state: count must be 4 * cells");
+    if (int rc = fv_device(f)) return rc;
+    ADG_CK(cudaMemcpyAsync(u, f->u, count * 8, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                           (cudaStream_t)stream),
+           "fv_get_state");
+    if (!on_device) ADG_CK(cudaStreamSynchronize((cudaStream_t)stream), "fv_get_state sync");
+    return ADG_OK;
+}
+
+extern "C" int adg_fv_init_scenario(adg_fv* f, const adg_scenario* s, void* stream) {
+    if (!f || !s) return fail(ADG_EINVAL, "fv_init_scenario: NULL argument");
+    if (s->kind != ADG_SCEN_COSINE && s->kind != ADG_SCEN_TWO_BUBBLES && s->kind != ADG_SCEN_BACKGROUND)
+        return fail(ADG_EINVAL, "fv_init_scenario: cosine bubble, two bubbles or background");
+    if (!f->d.gravity) return fail(ADG_EINVAL, "fv_init_scenario: bubble scenarios need gravity");
+    if (s->kind == ADG_SCEN_COSINE && !(s->a > 0.0)) return fail(ADG_EINVAL, "fv_init_scenario: radius must be > 0");
+    if (int rc = fv_device(f)) return rc;
+    const adg::FvPhys P = adg::fv_phys(f);
+    const double cp = f->d.gamma * f->d.R / f->gm1;
+    adg::k_fv_init<<<adg::fv_blocks(f->cells), 256, 0, (cudaStream_t)stream>>>(
+        f->u, s->kind, s->A, s->a, s->xc, s->zc, f->d.R, cp, f->d.p0, f->d.theta0, P);
+    ADG_CK(cudaGetLastError(), "fv_init_scenario launch");
+    return ADG_OK;
+}
+
+extern "C" int adg_fv_step(adg_fv* f, double dt, void* stream) {
+    if (!f) return fail(ADG_EINVAL, "fv_step: NULL argument");
+    if (!(dt > 0.0) || !std::isfinite(dt)) return fail(ADG_EINVAL, "fv_step: dt must be finite and > 0");
+    if (int rc = fv_device(f)) return rc;
+    const adg::FvPhys P = adg::fv_phys(f);
+    const int nb = adg::fv_blocks(f->cells);
+    cudaStream_t s = (cudaStream_t)stream;
+    adg::k_fv_half<<<nb, 256, 0, s>>>(f->u, f->half, dt, P);
+    ADG_CK(cudaGetLastError(), "fv_step half");
+    adg::k_fv_update<<<nb, 256, 0, s>>>(f->u, f->half, dt, P);
+    ADG_CK(cudaGetLastError(), "fv_step update");
+    return ADG_OK;
+}
+
+extern "C" int adg_fv_stable_dt(adg_fv* f, double cfl, double* dt, void* stream) {
+    if (!f || !dt) return fail(ADG_EINVAL, "fv_stable_dt: NULL argument");
+    if (!(cfl > 0.0)) return fail(ADG_EINVAL, "fv_stable_dt: cfl must be > 0");
+    if (int rc = fv_device(f)) return rc;
+    const adg::FvPhys P = adg::fv_phys(f);
+    cudaStream_t s = (cudaStream_t)stream;
+    adg::k_fv_speed<<<f->part_blocks, 256, 0, s>>>(f->u, f->part, P);
+    ADG_CK(cudaGetLastError(), "fv_stable_dt launch");
+    std::vector<double> h((size_t)2 * f->part_blocks);
+    ADG_CK(cudaMemcpyAsync(h.data(), f->part, h.size() * 8, cudaMemcpyDeviceToHost, s), "fv_stable_dt copy");
+    ADG_CK(cudaStreamSynchronize(s), "fv_stable_dt sync");
+    double sx = 0.0, sy = 0.0;
+    for (int b = 0; b < f->part_blocks; ++b) {
+        sx = std::max(sx, h[2 * b]);
+        sy = std::max(sy, h[2 * b + 1]);
+    }
+    if (!(sx > 0.0 || sy > 0.0) || !std::isfinite(sx) || !std::isfinite(sy))
+        return fail(ADG_ENONFINITE, "fv_stable_dt: non-finite or zero wave speed");
+    *dt = cfl / (sx / f->hx + sy / f->hy);
+    return ADG_OK;
+}

@@ -269,3 +269,64 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def fv_bubble_config(nx=630, ny=630, device=0):
+    """MUSCL-Hancock colliding bubbles (Sec. 4.2): [0,1000]^2 m, slip walls,
+    the atmosphere of Eq. 11 without viscosity (the paper: 7^2 patches of
+    90^2 finite volumes = 630^2 cells)."""
+    return MeshConfig(degree=1, nx=nx, ny=ny, Lx=1000.0, Ly=1000.0, bc_x=L.ADG_BC_WALL, bc_y=L.ADG_BC_WALL,
+                      gamma=1.4, Pr=0.71, R=287.058, mu=0.0, gravity=1, g=9.81, p0=1e5, theta0=300.0,
+                      device=device)
+
+
+class FvMesh:
+    """MUSCL-Hancock finite volumes (adg_fv_*): state tensor [4, ny, nx]."""
+
+    def __init__(self, cfg: MeshConfig):
+        self.cfg = cfg
+        self._lib = L.lib()
+        self.device = torch.device("cuda", cfg.device)
+        h = ctypes.c_void_p()
+        L.check(self._lib.adg_fv_create(ctypes.byref(cfg.to_c()), ctypes.byref(h)))
+        self.h = h
+        self.count = self._lib.adg_fv_state_count(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._lib.adg_fv_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def shape(self):
+        return (4, self.cfg.ny, self.cfg.nx)
+
+    def set_state(self, u: torch.Tensor, stream=None):
+        u = u.to(self.device, torch.float64).contiguous()
+        L.check(self._lib.adg_fv_set_state(self.h, ctypes.c_void_p(u.data_ptr()), self.count, 1, _stream_ptr(stream)))
+
+    def get_state(self, stream=None):
+        out = torch.empty(self.shape, dtype=torch.float64, device=self.device)
+        L.check(self._lib.adg_fv_get_state(self.h, ctypes.c_void_p(out.data_ptr()), self.count, 1,
+                                           _stream_ptr(stream)))
+        return out
+
+    def init_scenario(self, kind, A=0.5, a=250.0, xc=500.0, zc=350.0, stream=None):
+        sc = L.Scenario(kind=kind, A=A, a=a, xc=xc, zc=zc)
+        L.check(self._lib.adg_fv_init_scenario(self.h, ctypes.byref(sc), _stream_ptr(stream)))
+
+    def step(self, dt, nsteps=1, stream=None):
+        for _ in range(nsteps):
+            L.check(self._lib.adg_fv_step(self.h, float(dt), _stream_ptr(stream)))
+
+    def stable_dt(self, cfl, stream=None):
+        dt = ctypes.c_double()
+        L.check(self._lib.adg_fv_stable_dt(self.h, float(cfl), ctypes.byref(dt), _stream_ptr(stream)))
+        return dt.value
+
