@@ -558,44 +558,60 @@ def run_cfd(args, dev):
 def run_fv(args, dev):
     """MUSCL-Hancock finite volumes (Sec. 3, 4.2): the colliding bubbles on
     630 x 630 cells (the paper's 7^2 patches of 90^2 cells), slip walls, no
-    viscosity, FP64, CFL 0.5 on the initial state; L2 flushed before every
-    timed step."""
+    viscosity, CFL 0.5 on the initial state; L2 flushed before every timed
+    step.  The mixed-precision fused kernel is the headline; the FP64 two-
+    kernel form is timed beside it."""
     import torch
     from paper_1905_05524_gb300 import _lib as L
     from paper_1905_05524_gb300.solver import FvMesh, fv_bubble_config
-    cfg = fv_bubble_config(nx=630, ny=630, device=dev.index)
-    m = FvMesh(cfg)
-    m.init_scenario(L.ADG_SCEN_TWO_BUBBLES)
-    dt = m.stable_dt(0.5)
-    m.step(dt, 3)
+    mp = measured_peaks_file()
+    peak = (mp or {}).get("hbm_gbs", 6800.0)
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     steps = 50
-    total = 0.0
-    for _ in range(steps):
-        flush.fill_(1.0)
-        e0.record(stream)
-        m.step(dt)
-        e1.record(stream)
-        e1.synchronize()
-        total += e0.elapsed_time(e1)
-    cells = cfg.nx * cfg.ny
-    ms = total / steps
-    mp = measured_peaks_file()
-    # algorithmic bytes per cell: half-step kernel reads U (4) and writes 4 face
-    # states + rho' (17); update kernel reads them (17) and 4 neighbour states
-    # of 4 values (16), reads and writes U (4 + 4): 62 doubles
-    bytes_step = cells * 62 * 8
-    u = m.get_state().cpu()
-    return {"metric": METRIC + " (MUSCL-Hancock finite volumes)", "unit": UNIT, "dtype": "f64",
-            "config": {"workload": "colliding bubbles (Eq. 14), 630x630 finite volumes on [0,1000]^2 m, "
-                                   "slip walls, mu = 0, CFL 0.5", "cells": cells},
-            "value": cells * 4 * steps / (total * 1e-3), "cell_updates_per_s": cells * steps / (total * 1e-3),
-            "ms_per_step": ms, "dt": dt, "steps": steps,
-            "hbm": {"algorithmic_bytes_per_step": bytes_step, "achieved_gbs": bytes_step / (ms * 1e-3) / 1e9,
-                    "peak_gbs": (mp or {}).get("hbm_gbs", 6800.0)},
-            "finite": bool(torch.isfinite(u).all())}
+    res = {}
+    for name, prec in (("mixed", L.ADG_PREC_MIXED), ("fp64", L.ADG_PREC_FP64)):
+        cfg = fv_bubble_config(nx=630, ny=630, device=dev.index)
+        cfg.precision = prec
+        m = FvMesh(cfg)
+        m.init_scenario(L.ADG_SCEN_TWO_BUBBLES)
+        dt = m.stable_dt(0.5)
+        m.step(dt, 3)
+        total = 0.0
+        for _ in range(steps):
+            flush.fill_(1.0)
+            e0.record(stream)
+            m.step(dt)
+            e1.record(stream)
+            e1.synchronize()
+            total += e0.elapsed_time(e1)
+        cells = cfg.nx * cfg.ny
+        ms = total / steps
+        # algorithmic bytes per cell: FP64 -- half-step kernel reads U (4) and
+        # writes 4 face states + rho' (17); update kernel reads them (17) and
+        # 4 neighbour states of 4 values (16), reads and writes U (4 + 4): 62
+        # doubles; mixed (fused) -- reads and writes U: 8 doubles
+        bytes_step = cells * (8 if name == "mixed" else 62) * 8
+        u = m.get_state().cpu()
+        res[name] = {"value": cells * 4 * steps / (total * 1e-3), "cell_updates_per_s": cells * steps / (total * 1e-3),
+                     "ms_per_step": ms, "dt": dt, "steps": steps,
+                     "hbm": {"algorithmic_bytes_per_step": bytes_step,
+                             "achieved_gbs": bytes_step / (ms * 1e-3) / 1e9, "peak_gbs": peak},
+                     "finite": bool(torch.isfinite(u).all()), "state": u}
+        m.close()
+    a, b = res["mixed"].pop("state"), res["fp64"].pop("state")
+    # the two precisions after the same 53 steps: relative L2 of rho' and of rho u
+    d_rho = float(torch.linalg.vector_norm(a[0] - b[0]))
+    out = {"metric": METRIC + " (MUSCL-Hancock finite volumes)", "unit": UNIT, "dtype": "f64 state, f32 arithmetic",
+           "config": {"workload": "colliding bubbles (Eq. 14), 630x630 finite volumes on [0,1000]^2 m, "
+                                  "slip walls, mu = 0, CFL 0.5", "cells": 630 * 630}}
+    out.update(res["mixed"])
+    out["fp64"] = res["fp64"]
+    out["mixed_vs_fp64"] = {"rho_abs_l2": d_rho,
+                            "momentum_rel_l2": float(torch.linalg.vector_norm(a[1:3] - b[1:3]) /
+                                                     torch.linalg.vector_norm(b[1:3]))}
+    return out
 
 
 def run_adjoint(args, dev):

@@ -301,11 +301,16 @@ int adg_adapt(adg_mesh* m, const int8_t* flags, int* leaves_out, void* stream);
  * the hydrostatic background (the atmosphere at rest is kept exactly), a
  * half-step evolution of the face states, Rusanov fluxes (s = |v.n| + c),
  * the perturbation form of Eq. 7 and slip walls with background ghosts.
- * FP64.  The descriptor supplies nx, ny, the box, bc_x / bc_y (periodic or
- * ADG_BC_WALL), gamma, R, gravity, g, p0, theta0 and device; mu must be 0.
+ * The descriptor supplies nx, ny, the box, bc_x / bc_y (periodic or
+ * ADG_BC_WALL), gamma, R, gravity, g, p0, theta0, precision and device; mu
+ * must be 0.  precision ADG_PREC_FP64: FP64 throughout; ADG_PREC_MIXED: FP64
+ * state, FP32 arithmetic on perturbations of the background (with gravity it
+ * needs bc_y = ADG_BC_WALL, else ADG_EUNSUPPORTED).
  * State: double[4][ny][nx] cell averages of (rho, rho u, rho v, rho E).
- * adg_fv_step: one step of fixed dt (two kernels: face states at the half
- *   step, then fluxes and update).  adg_fv_stable_dt: cfl / (max(|u| + c)/hx
+ * adg_fv_step: one step of fixed dt (FP64: two kernels, face states at the
+ *   half step, then fluxes and update; mixed: one fused kernel writing the
+ *   second state buffer, which becomes the state, so a device pointer to the
+ *   state is not stable across steps).  adg_fv_stable_dt: cfl / (max(|u| + c)/hx
  *   + max(|v| + c)/hy); synchronises `stream`.  adg_fv_init_scenario: cell
  *   centre values of ADG_SCEN_COSINE, ADG_SCEN_TWO_BUBBLES or
  *   ADG_SCEN_BACKGROUND (gravity on).  Errors as for adg_mesh. */

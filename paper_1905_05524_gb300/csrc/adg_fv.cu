@@ -20,12 +20,17 @@
 //
 // Momentum fluxes carry p' = p - pbar(z) at the height where they are
 // evaluated (Eq. 7).  State layout: u[v][iy][ix] (structure of arrays).
+//
+// Mixed precision (k_fv_step_mixed): the same scheme as one fused kernel per
+// step on shared-memory tiles, FP32 arithmetic on perturbations of the
+// background, FP64 state and accumulation.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cmath>
 #include <vector>
 
+#include "adg_convert.cuh"
 #include "adg_internal.h"
 #include "adg_mesh.h"
 
@@ -38,6 +43,11 @@ struct adg_fv {
     double* bg = nullptr;      // [6][ny] centre rhobar, Ebar, pbar; [3][ny + 1] face rhobar, Ebar, pbar
     double* part = nullptr;    // stable-dt block maxima
     int part_blocks = 0;
+    // mixed precision: second state buffer (the fused step reads u, writes
+    // u2, then the two swap) and the FP32 background tables
+    double* u2 = nullptr;
+    float* bgf = nullptr;      // [ny] centre (rhobar, pbar, Ebar + pbar, g z), [ny + 1] faces
+                               // (rhobar, pbar, 0, g z), [ny] face minus centre Ebar + pbar (north, south)
 };
 
 namespace adg {
@@ -231,6 +241,223 @@ __device__ double fv_bubble(double x, double z, double A, double a, double s, do
     return r <= a ? A : A * exp(-((r - a) * (r - a)) / (s * s));
 }
 
+// ---------------------------------------------------------------------------
+// Mixed precision: one fused kernel per step on tiles of kFvTx x kFvTy cells.
+// The FP64 state is split once per loaded cell into FP32 perturbations of the
+// row's centre background (rho' = rho - rhobar, E' = rhoE - Ebar: two FP64
+// subtractions, integer-pipe conversions); everything after that is FP32:
+//   phase 1  perturbations of the tile plus a 2-cell halo into shared memory;
+//   phase 2  van Albada slopes, face states and their half-step evolution for
+//            the tile plus a 1-cell halo (face states stay perturbations: the
+//            x-faces of the row's centre background, the y-faces of the
+//            background at the face height, so both states of a face share
+//            one base and the Rusanov jump is a jump of perturbations);
+//   phase 3  one Rusanov flux per face of the tile (a face on a tile edge is
+//            computed by both tiles with the same operands and instructions);
+//   phase 4  du in FP32, accumulated in FP64: uo = u + du.
+// The flux of a perturbation state over the base (rhobar, pbar, g z) uses
+// rho = rhobar + rho' and p' = (gamma - 1)(E' - |m|^2/(2 rho) - g z rho').
+// The energy flux v.n (Hbar + h'), h' = E' + p', Hbar = Ebar + pbar, is kept
+// in two parts, v.n and v.n h', and Hbar enters only as products with
+// velocity differences: Hbar_c (v_E - v_W) for x-faces and, for y-faces,
+// Hbar_c (v_N - v_S) + dN v_N - dS v_S with dN, dS the face enthalpies minus
+// the centre one formed in FP64.  The sum Hbar + h' (h' is five orders of
+// magnitude smaller) and the face enthalpies themselves are never rounded
+// to FP32.  Reads u, writes uo (the state is double-buffered).
+constexpr int kFvTx = 32, kFvTy = 8, kFvThreads = kFvTx * kFvTy;
+constexpr int kFvPw = kFvTx + 4, kFvPh = kFvTy + 4;  // perturbation tile (halo 2)
+constexpr int kFvHw = kFvTx + 2, kFvHh = kFvTy + 2;  // half-step tile (halo 1)
+constexpr int kFvFx = (kFvTx + 1) * kFvTy;           // x-faces of a tile
+constexpr int kFvFy = kFvTx * (kFvTy + 1);           // y-faces of a tile
+constexpr int kFvShared = (kFvFx + kFvFy) > kFvPw * kFvPh ? (kFvFx + kFvFy) : kFvPw * kFvPh;
+
+struct FvMixed {
+    const double* rbc;  // [ny] centre rhobar (FP64, for the split)
+    const double* Ebc;  // [ny] centre Ebar
+    const float4* cb;   // [ny] centre (rhobar, pbar, Hbar, g z)
+    const float4* fb;   // [ny + 1] faces (rhobar, pbar, 0, g z)
+    const float2* dh;   // [ny] Hbar(north face) - Hbar_c, Hbar(south face) - Hbar_c
+    float gamma, gm1;
+    float hdtx, hdty, hdtg;  // dt/(2 hx), dt/(2 hy), dt g/2
+    float dtx, dty, dtg;     // dt/hx, dt/hy, dt g
+    int nx, ny, cells, wall_x, wall_y, gravity;
+};
+
+__device__ __forceinline__ int fv_wrap(int a, int n) {
+    const int r = a % n;
+    return r < 0 ? r + n : r;
+}
+
+// van Albada in FP32; differences below ~1e-15 (squares outside the normal
+// range, where the fast division is not defined) give a zero slope, an
+// absolute change below 1e-15
+__device__ __forceinline__ float va_f(float a, float b) {
+    const float ab = a * b;
+    const float den = a * a + b * b;
+    return (ab > 0.0f && den > 1e-30f) ? __fdividef(ab * (a + b), den) : 0.0f;
+}
+
+__device__ __forceinline__ float fv_rcp(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// flux of a perturbation state q over the base b = (rhobar, pbar, -, g z)
+// along x (xdir) or y, without the energy flux's Hbar part: f.w = v.n h';
+// vn = v.n (the factor of Hbar); returns the wave speed |v.n| + c
+__device__ __forceinline__ float fv_flux_f(const float4 q, const float4 b, bool xdir, const FvMixed& M, float4& f,
+                                           float& vn) {
+    const float rho = b.x + q.x;
+    const float rinv = fv_rcp(rho);
+    const float u = q.y * rinv, v = q.z * rinv;
+    const float pp = M.gm1 * (q.w - 0.5f * (q.y * u + q.z * v) - b.w * q.x);
+    vn = xdir ? u : v;
+    f.x = xdir ? q.y : q.z;
+    f.y = q.y * vn + (xdir ? pp : 0.0f);
+    f.z = q.z * vn + (xdir ? 0.0f : pp);
+    f.w = vn * (q.w + pp);
+    return fabsf(vn) + sqrtf(M.gamma * (b.y + pp) * rinv);
+}
+
+// Rusanov flux of two perturbation states over one base; the energy flux is
+// Hbar a + F.w with a = (v.n_L + v.n_R)/2
+__device__ __forceinline__ float4 fv_rusanov_f(const float4 qL, const float4 qR, const float4 b, bool xdir,
+                                               const FvMixed& M, float& a) {
+    float4 fL, fR;
+    float vL, vR;
+    const float sL = fv_flux_f(qL, b, xdir, M, fL, vL);
+    const float sR = fv_flux_f(qR, b, xdir, M, fR, vR);
+    const float hs = 0.5f * fmaxf(sL, sR);
+    a = 0.5f * (vL + vR);
+    return make_float4(0.5f * (fL.x + fR.x) - hs * (qR.x - qL.x), 0.5f * (fL.y + fR.y) - hs * (qR.y - qL.y),
+                       0.5f * (fL.z + fR.z) - hs * (qR.z - qL.z), 0.5f * (fL.w + fR.w) - hs * (qR.w - qL.w));
+}
+
+// slip-wall ghost of a perturbation face state: the background rho and rhoE
+// (zero perturbation) with gravity, the interior ones without; normal momentum
+// reflected
+__device__ __forceinline__ float4 fv_ghost_f(const float4 q, bool xwall, const FvMixed& M) {
+    return make_float4(M.gravity ? 0.0f : q.x, xwall ? -q.y : q.y, xwall ? q.z : -q.z, M.gravity ? 0.0f : q.w);
+}
+
+__device__ __forceinline__ float4 f4_add(float4 a, float4 b) { return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w); }
+__device__ __forceinline__ float4 f4_axpy(float s, float4 a, float4 b) {  // b + s a
+    return make_float4(fmaf(s, a.x, b.x), fmaf(s, a.y, b.y), fmaf(s, a.z, b.z), fmaf(s, a.w, b.w));
+}
+
+__global__ void __launch_bounds__(kFvThreads) k_fv_step_mixed(const double* __restrict__ u, double* __restrict__ uo,
+                                                              const FvMixed M) {
+    __shared__ float4 sp[kFvShared];               // phase 1-2: perturbations; phase 3-4: face fluxes
+    __shared__ float4 sh[4][kFvHh * kFvHw];        // half-step face states E, W, N, S
+    __shared__ float srp[kFvThreads];              // half-step rho' of the tile's cells
+    __shared__ float sa[kFvFx + kFvFy];            // face velocity factor of Hbar in the energy flux
+    const int tid = threadIdx.x;
+    const int x0 = blockIdx.x * kFvTx, y0 = blockIdx.y * kFvTy;
+    // phase 1: FP64 split of the tile plus a 2-cell halo (wrapped indices;
+    // wall-side halo values are never used)
+    for (int k = tid; k < kFvPw * kFvPh; k += kFvThreads) {
+        const int r = k / kFvPw, c = k - r * kFvPw;
+        const int gy = fv_wrap(y0 - 2 + r, M.ny), gx = fv_wrap(x0 - 2 + c, M.nx);
+        const size_t i = (size_t)gy * M.nx + gx;
+        const double rho = u[i], mx = u[(size_t)M.cells + i], my = u[(size_t)2 * M.cells + i];
+        const double E = u[(size_t)3 * M.cells + i];
+        sp[k] = make_float4(f64_to_f32(__dsub_rn(rho, M.rbc[gy])), f64_to_f32(mx), f64_to_f32(my),
+                            f64_to_f32(__dsub_rn(E, M.Ebc[gy])));
+    }
+    __syncthreads();
+    // phase 2: slopes, face states, half-step evolution (tile plus 1-cell halo,
+    // corners unused)
+    for (int k = tid; k < kFvHw * kFvHh; k += kFvThreads) {
+        const int r = k / kFvHw, c = k - r * kFvHw;
+        if ((r == 0 || r == kFvHh - 1) && (c == 0 || c == kFvHw - 1)) continue;
+        const int gy = fv_wrap(y0 - 1 + r, M.ny), gx = fv_wrap(x0 - 1 + c, M.nx);
+        const bool flat_x = M.wall_x && (gx == 0 || gx == M.nx - 1);
+        const bool flat_y = M.wall_y && (gy == 0 || gy == M.ny - 1);
+        const int p = (r + 1) * kFvPw + (c + 1);
+        const float4 up = sp[p], pw = sp[p - 1], pe = sp[p + 1], ps = sp[p - kFvPw], pn = sp[p + kFvPw];
+        float4 sx = make_float4(0.f, 0.f, 0.f, 0.f), sy = sx;
+        if (!flat_x)
+            sx = make_float4(va_f(up.x - pw.x, pe.x - up.x), va_f(up.y - pw.y, pe.y - up.y),
+                             va_f(up.z - pw.z, pe.z - up.z), va_f(up.w - pw.w, pe.w - up.w));
+        if (!flat_y)
+            sy = make_float4(va_f(up.x - ps.x, pn.x - up.x), va_f(up.y - ps.y, pn.y - up.y),
+                             va_f(up.z - ps.z, pn.z - up.z), va_f(up.w - ps.w, pn.w - up.w));
+        const float4 qE = f4_axpy(0.5f, sx, up), qW = f4_axpy(-0.5f, sx, up);
+        const float4 qN = f4_axpy(0.5f, sy, up), qS = f4_axpy(-0.5f, sy, up);
+        const float4 bc = M.cb[gy], bn = M.fb[gy + 1], bs = M.fb[gy];
+        const float2 dh = M.dh[gy];
+        float4 fE, fW, gN, gS;
+        float vE, vW, vN, vS;
+        fv_flux_f(qE, bc, true, M, fE, vE);
+        fv_flux_f(qW, bc, true, M, fW, vW);
+        fv_flux_f(qN, bn, false, M, gN, vN);
+        fv_flux_f(qS, bs, false, M, gS, vS);
+        const float hx = fmaf(bc.z, vE - vW, fE.w - fW.w);
+        const float hy = fmaf(bc.z, vN - vS, fmaf(dh.x, vN, fmaf(-dh.y, vS, gN.w - gS.w)));
+        float4 d;
+        d.x = -M.hdtx * (fE.x - fW.x) - M.hdty * (gN.x - gS.x);
+        d.y = -M.hdtx * (fE.y - fW.y) - M.hdty * (gN.y - gS.y);
+        d.z = -M.hdtx * (fE.z - fW.z) - M.hdty * (gN.z - gS.z) - M.hdtg * up.x;
+        d.w = -M.hdtx * hx - M.hdty * hy;
+        sh[0][k] = f4_add(qE, d);
+        sh[1][k] = f4_add(qW, d);
+        sh[2][k] = f4_add(qN, d);
+        sh[3][k] = f4_add(qS, d);
+        if (r >= 1 && r <= kFvTy && c >= 1 && c <= kFvTx) srp[(r - 1) * kFvTx + (c - 1)] = up.x + d.x;
+    }
+    __syncthreads();
+    // phase 3: Rusanov fluxes, x-faces [r][j] (west face of tile column j),
+    // then y-faces [k][c] (south face of tile row k)
+    float4* fxs = sp;
+    float4* fys = sp + kFvFx;
+    for (int k = tid; k < kFvFx + kFvFy; k += kFvThreads) {
+        if (k < kFvFx) {
+            const int r = k / (kFvTx + 1), j = k - r * (kFvTx + 1);
+            const int gy = y0 + r, gf = x0 + j;
+            if (gy >= M.ny || gf > M.nx) continue;
+            const int h = (r + 1) * kFvHw + j;  // half-tile cell left of the face
+            float4 qL = sh[0][h], qR = sh[1][h + 1];
+            if (M.wall_x && gf == 0) qL = fv_ghost_f(qR, true, M);
+            if (M.wall_x && gf == M.nx) qR = fv_ghost_f(qL, true, M);
+            fxs[k] = fv_rusanov_f(qL, qR, M.cb[gy], true, M, sa[k]);
+        } else {
+            const int kk = k - kFvFx;
+            const int r = kk / kFvTx, c = kk - r * kFvTx;
+            const int gf = y0 + r, gx = x0 + c;
+            if (gf > M.ny || gx >= M.nx) continue;
+            const int h = r * kFvHw + (c + 1);  // half-tile cell below the face
+            float4 qL = sh[2][h], qR = sh[3][h + kFvHw];
+            if (M.wall_y && gf == 0) qL = fv_ghost_f(qR, false, M);
+            if (M.wall_y && gf == M.ny) qR = fv_ghost_f(qL, false, M);
+            fys[kk] = fv_rusanov_f(qL, qR, M.fb[gf], false, M, sa[k]);
+        }
+    }
+    __syncthreads();
+    // phase 4: FP32 increment, FP64 accumulation
+    const int ty = tid / kFvTx, tx = tid - ty * kFvTx;
+    const int gy = y0 + ty, gx = x0 + tx;
+    if (gy >= M.ny || gx >= M.nx) return;
+    const float4 FW = fxs[ty * (kFvTx + 1) + tx], FE = fxs[ty * (kFvTx + 1) + tx + 1];
+    const float4 GS = fys[ty * kFvTx + tx], GN = fys[(ty + 1) * kFvTx + tx];
+    const float aW = sa[ty * (kFvTx + 1) + tx], aE = sa[ty * (kFvTx + 1) + tx + 1];
+    const float aS = sa[kFvFx + ty * kFvTx + tx], aN = sa[kFvFx + (ty + 1) * kFvTx + tx];
+    const float Hc = M.cb[gy].z;
+    const float2 dh = M.dh[gy];
+    const float rp = srp[tid];
+    const float du0 = -M.dtx * (FE.x - FW.x) - M.dty * (GN.x - GS.x);
+    const float du1 = -M.dtx * (FE.y - FW.y) - M.dty * (GN.y - GS.y);
+    const float du2 = -M.dtx * (FE.z - FW.z) - M.dty * (GN.z - GS.z) - M.dtg * rp;
+    const float ex = fmaf(Hc, aE - aW, FE.w - FW.w);
+    const float ey = fmaf(Hc, aN - aS, fmaf(dh.x, aN, fmaf(-dh.y, aS, GN.w - GS.w)));
+    const float du3 = -M.dtx * ex - M.dty * ey;
+    const size_t i = (size_t)gy * M.nx + gx;
+    uo[i] = __dadd_rn(u[i], f32_to_f64(du0));
+    uo[(size_t)M.cells + i] = __dadd_rn(u[(size_t)M.cells + i], f32_to_f64(du1));
+    uo[(size_t)2 * M.cells + i] = __dadd_rn(u[(size_t)2 * M.cells + i], f32_to_f64(du2));
+    uo[(size_t)3 * M.cells + i] = __dadd_rn(u[(size_t)3 * M.cells + i], f32_to_f64(du3));
+}
+
 // point values at cell centres: background atmosphere with theta' (Sec. 4.2)
 __global__ void k_fv_init(double* __restrict__ u, int kind, double A, double a, double xc, double zc,
                           double R, double cp, double p0, double theta0, const FvPhys P) {
@@ -279,6 +506,32 @@ FvPhys fv_phys(const adg_fv* f) {
     return P;
 }
 
+FvMixed fv_mixed(const adg_fv* f, double dt) {
+    FvMixed M;
+    const int ny = f->d.ny;
+    M.rbc = f->bg;
+    M.Ebc = f->bg + ny;
+    M.cb = reinterpret_cast<const float4*>(f->bgf);
+    M.fb = reinterpret_cast<const float4*>(f->bgf) + ny;
+    M.dh = reinterpret_cast<const float2*>(f->bgf + 4 * (size_t)ny + 4 * (size_t)(ny + 1));
+    const double g = f->d.gravity ? f->d.g : 0.0;
+    M.gamma = (float)f->d.gamma;
+    M.gm1 = (float)f->gm1;
+    M.hdtx = (float)(0.5 * dt / f->hx);
+    M.hdty = (float)(0.5 * dt / f->hy);
+    M.hdtg = (float)(0.5 * dt * g);
+    M.dtx = (float)(dt / f->hx);
+    M.dty = (float)(dt / f->hy);
+    M.dtg = (float)(dt * g);
+    M.nx = f->d.nx;
+    M.ny = ny;
+    M.cells = f->cells;
+    M.wall_x = f->d.bc_x == ADG_BC_WALL;
+    M.wall_y = f->d.bc_y == ADG_BC_WALL;
+    M.gravity = f->d.gravity ? 1 : 0;
+    return M;
+}
+
 int fv_blocks(int cells) { return (cells + 255) / 256; }
 
 }  // namespace
@@ -299,6 +552,8 @@ static void fv_free(adg_fv* f) {
     cudaFree(f->half);
     cudaFree(f->bg);
     cudaFree(f->part);
+    cudaFree(f->u2);
+    cudaFree(f->bgf);
     delete f;
 }
 
@@ -312,7 +567,10 @@ extern "C" int adg_fv_create(const adg_mesh_desc* d, adg_fv** out) {
         return fail(ADG_EINVAL, "fv_create: boundaries are periodic or slip walls");
     if (!(d->gamma > 1.0) || !(d->R > 0.0)) return fail(ADG_EINVAL, "fv_create: invalid gas constants");
     if (d->mu != 0.0) return fail(ADG_EINVAL, "fv_create: the finite-volume scheme is inviscid (mu = 0)");
-    if (d->precision != ADG_PREC_FP64) return fail(ADG_EUNSUPPORTED, "fv_create: FP64 only");
+    if (d->precision != ADG_PREC_FP64 && d->precision != ADG_PREC_MIXED)
+        return fail(ADG_EINVAL, "fv_create: precision must be FP64 or mixed");
+    if (d->precision == ADG_PREC_MIXED && d->gravity && d->bc_y == ADG_BC_PERIODIC)
+        return fail(ADG_EUNSUPPORTED, "fv_create: mixed precision with gravity needs walls in y");
     if (d->gravity && !(d->theta0 > 0.0 && d->p0 > 0.0))
         return fail(ADG_EINVAL, "fv_create: gravity needs theta0 > 0 and p0 > 0");
     int ndev = 0;
@@ -331,9 +589,15 @@ extern "C" int adg_fv_create(const adg_mesh_desc* d, adg_fv** out) {
     const int ny = d->ny;
     f->part_blocks = adg::fv_blocks(f->cells);
     const size_t nbg = 3 * (size_t)ny + 3 * (size_t)(ny + 1);
-    if (cudaMalloc(&f->u, (size_t)4 * f->cells * 8) != cudaSuccess ||
-        cudaMalloc(&f->half, (size_t)17 * f->cells * 8) != cudaSuccess || cudaMalloc(&f->bg, nbg * 8) != cudaSuccess ||
-        cudaMalloc(&f->part, (size_t)2 * f->part_blocks * 8) != cudaSuccess) {
+    const bool mixed = d->precision == ADG_PREC_MIXED;
+    const size_t nbgf = 4 * (size_t)ny + 4 * (size_t)(ny + 1) + 2 * (size_t)ny;
+    bool ok = cudaMalloc(&f->u, (size_t)4 * f->cells * 8) == cudaSuccess && cudaMalloc(&f->bg, nbg * 8) == cudaSuccess &&
+              cudaMalloc(&f->part, (size_t)2 * f->part_blocks * 8) == cudaSuccess;
+    if (ok && mixed)
+        ok = cudaMalloc(&f->u2, (size_t)4 * f->cells * 8) == cudaSuccess && cudaMalloc(&f->bgf, nbgf * 4) == cudaSuccess;
+    else if (ok)
+        ok = cudaMalloc(&f->half, (size_t)17 * f->cells * 8) == cudaSuccess;
+    if (!ok) {
         cudaGetLastError();
         fv_free(f);
         return fail(ADG_ENOMEM, "fv_create: device allocation failed");
@@ -352,7 +616,32 @@ extern "C" int adg_fv_create(const adg_mesh_desc* d, adg_fv** out) {
         for (int k = 0; k <= ny; ++k)
             bgp(d->y0 + k * f->hy, h[3 * ny + k], h[3 * ny + (ny + 1) + k], h[3 * ny + 2 * (ny + 1) + k]);
     }
+    // FP32 tables of the mixed path: (rhobar, pbar, Ebar + pbar, g z) at centres, then faces
+    std::vector<float> hf(nbgf, 0.0f);
+    if (mixed && d->gravity) {
+        for (int iy = 0; iy < ny; ++iy) {
+            hf[4 * iy + 0] = (float)h[iy];
+            hf[4 * iy + 1] = (float)h[2 * ny + iy];
+            hf[4 * iy + 2] = (float)(h[ny + iy] + h[2 * ny + iy]);
+            hf[4 * iy + 3] = (float)(d->g * (d->y0 + (iy + 0.5) * f->hy));
+        }
+        auto Hf = [&](int k) { return h[3 * ny + (ny + 1) + k] + h[3 * ny + 2 * (ny + 1) + k]; };
+        for (int k = 0; k <= ny; ++k) {
+            float* q = hf.data() + 4 * (size_t)ny + 4 * (size_t)k;
+            q[0] = (float)h[3 * ny + k];
+            q[1] = (float)h[3 * ny + 2 * (ny + 1) + k];
+            q[2] = 0.0f;
+            q[3] = (float)(d->g * (d->y0 + k * f->hy));
+        }
+        for (int iy = 0; iy < ny; ++iy) {
+            float* q = hf.data() + 4 * (size_t)ny + 4 * (size_t)(ny + 1) + 2 * (size_t)iy;
+            const double Hc = h[ny + iy] + h[2 * ny + iy];
+            q[0] = (float)(Hf(iy + 1) - Hc);
+            q[1] = (float)(Hf(iy) - Hc);
+        }
+    }
     if (cudaMemcpy(f->bg, h.data(), nbg * 8, cudaMemcpyHostToDevice) != cudaSuccess ||
+        (mixed && cudaMemcpy(f->bgf, hf.data(), nbgf * 4, cudaMemcpyHostToDevice) != cudaSuccess) ||
         cudaMemset(f->u, 0, (size_t)4 * f->cells * 8) != cudaSuccess) {
         cudaGetLastError();
         fv_free(f);
@@ -407,9 +696,17 @@ extern "C" int adg_fv_step(adg_fv* f, double dt, void* stream) {
     if (!f) return fail(ADG_EINVAL, "fv_step: NULL argument");
     if (!(dt > 0.0) || !std::isfinite(dt)) return fail(ADG_EINVAL, "fv_step: dt must be finite and > 0");
     if (int rc = fv_device(f)) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (f->d.precision == ADG_PREC_MIXED) {
+        const adg::FvMixed M = adg::fv_mixed(f, dt);
+        const dim3 grid((f->d.nx + adg::kFvTx - 1) / adg::kFvTx, (f->d.ny + adg::kFvTy - 1) / adg::kFvTy);
+        adg::k_fv_step_mixed<<<grid, adg::kFvThreads, 0, s>>>(f->u, f->u2, M);
+        ADG_CK(cudaGetLastError(), "fv_step mixed");
+        std::swap(f->u, f->u2);
+        return ADG_OK;
+    }
     const adg::FvPhys P = adg::fv_phys(f);
     const int nb = adg::fv_blocks(f->cells);
-    cudaStream_t s = (cudaStream_t)stream;
     adg::k_fv_half<<<nb, 256, 0, s>>>(f->u, f->half, dt, P);
     ADG_CK(cudaGetLastError(), "fv_step half");
     adg::k_fv_update<<<nb, 256, 0, s>>>(f->u, f->half, dt, P);
