@@ -270,6 +270,10 @@ constexpr int kFvHw = kFvTx + 2, kFvHh = kFvTy + 2;  // half-step tile (halo 1)
 constexpr int kFvFx = (kFvTx + 1) * kFvTy;           // x-faces of a tile
 constexpr int kFvFy = kFvTx * (kFvTy + 1);           // y-faces of a tile
 constexpr int kFvShared = (kFvFx + kFvFy) > kFvPw * kFvPh ? (kFvFx + kFvFy) : kFvPw * kFvPh;
+// dynamic shared memory: perturbations / face fluxes, four half-step face
+// states, half-step rho', face velocity factors
+constexpr size_t kFvSmemBytes =
+    sizeof(float4) * ((size_t)kFvShared + 4 * (size_t)kFvHh * kFvHw) + sizeof(float) * ((size_t)kFvThreads + kFvFx + kFvFy);
 
 struct FvMixed {
     const double* rbc;  // [ny] centre rhobar (FP64, for the split)
@@ -284,6 +288,7 @@ struct FvMixed {
 };
 
 __device__ __forceinline__ int fv_wrap(int a, int n) {
+    if ((unsigned)a < (unsigned)n) return a;
     const int r = a % n;
     return r < 0 ? r + n : r;
 }
@@ -302,6 +307,13 @@ __device__ __forceinline__ float fv_rcp(float x) {
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
     return r;
 }
+// hardware square root approximation (relative error ~2^-23): it only scales
+// the Rusanov dissipation
+__device__ __forceinline__ float fv_sqrt(float x) {
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
 
 // flux of a perturbation state q over the base b = (rhobar, pbar, -, g z)
 // along x (xdir) or y, without the energy flux's Hbar part: f.w = v.n h';
@@ -317,7 +329,7 @@ __device__ __forceinline__ float fv_flux_f(const float4 q, const float4 b, bool 
     f.y = q.y * vn + (xdir ? pp : 0.0f);
     f.z = q.z * vn + (xdir ? 0.0f : pp);
     f.w = vn * (q.w + pp);
-    return fabsf(vn) + sqrtf(M.gamma * (b.y + pp) * rinv);
+    return fabsf(vn) + fv_sqrt(M.gamma * (b.y + pp) * rinv);
 }
 
 // Rusanov flux of two perturbation states over one base; the energy flux is
@@ -348,10 +360,12 @@ __device__ __forceinline__ float4 f4_axpy(float s, float4 a, float4 b) {  // b +
 
 __global__ void __launch_bounds__(kFvThreads) k_fv_step_mixed(const double* __restrict__ u, double* __restrict__ uo,
                                                               const FvMixed M) {
-    __shared__ float4 sp[kFvShared];               // phase 1-2: perturbations; phase 3-4: face fluxes
-    __shared__ float4 sh[4][kFvHh * kFvHw];        // half-step face states E, W, N, S
-    __shared__ float srp[kFvThreads];              // half-step rho' of the tile's cells
-    __shared__ float sa[kFvFx + kFvFy];            // face velocity factor of Hbar in the energy flux
+    extern __shared__ float4 fv_smem[];
+    float4* sp = fv_smem;                                // phase 1-2: perturbations; phase 3-4: face fluxes
+    float4 (*sh)[kFvHh * kFvHw] = reinterpret_cast<float4 (*)[kFvHh * kFvHw]>(fv_smem + kFvShared);
+                                                         // half-step face states E, W, N, S
+    float* srp = reinterpret_cast<float*>(fv_smem + kFvShared + 4 * kFvHh * kFvHw);  // half-step rho'
+    float* sa = srp + kFvThreads;                        // face velocity factor of Hbar in the energy flux
     const int tid = threadIdx.x;
     const int x0 = blockIdx.x * kFvTx, y0 = blockIdx.y * kFvTy;
     // phase 1: FP64 split of the tile plus a 2-cell halo (wrapped indices;
@@ -590,6 +604,14 @@ extern "C" int adg_fv_create(const adg_mesh_desc* d, adg_fv** out) {
     f->part_blocks = adg::fv_blocks(f->cells);
     const size_t nbg = 3 * (size_t)ny + 3 * (size_t)(ny + 1);
     const bool mixed = d->precision == ADG_PREC_MIXED;
+    if (mixed) {
+        const cudaError_t e = cudaFuncSetAttribute(adg::k_fv_step_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)adg::kFvSmemBytes);
+        if (e != cudaSuccess) {
+            delete f;
+            return cuda_fail(e, "fv_create: shared memory attribute");
+        }
+    }
     const size_t nbgf = 4 * (size_t)ny + 4 * (size_t)(ny + 1) + 2 * (size_t)ny;
     bool ok = cudaMalloc(&f->u, (size_t)4 * f->cells * 8) == cudaSuccess && cudaMalloc(&f->bg, nbg * 8) == cudaSuccess &&
               cudaMalloc(&f->part, (size_t)2 * f->part_blocks * 8) == cudaSuccess;
@@ -700,7 +722,7 @@ extern "C" int adg_fv_step(adg_fv* f, double dt, void* stream) {
     if (f->d.precision == ADG_PREC_MIXED) {
         const adg::FvMixed M = adg::fv_mixed(f, dt);
         const dim3 grid((f->d.nx + adg::kFvTx - 1) / adg::kFvTx, (f->d.ny + adg::kFvTy - 1) / adg::kFvTy);
-        adg::k_fv_step_mixed<<<grid, adg::kFvThreads, 0, s>>>(f->u, f->u2, M);
+        adg::k_fv_step_mixed<<<grid, adg::kFvThreads, adg::kFvSmemBytes, s>>>(f->u, f->u2, M);
         ADG_CK(cudaGetLastError(), "fv_step mixed");
         std::swap(f->u, f->u2);
         return ADG_OK;
