@@ -614,6 +614,67 @@ def run_fv(args, dev):
     return out
 
 
+def run_3d(args, dev):
+    """3D scenarios on the FP64 path: the 3D cosine bubble of Sec. 4.2
+    (degree 2 = order 3, 40 m cells = 25^3 on [0,1000]^3 m, mu = 0.005, slip
+    walls; 50 timed steps at the bubble CFL, L2 flushed before each) and the
+    ABC flow of Sec. 4.1 (degree 2, 27^3 on [-pi, pi]^3, mu = 0.01, analytic
+    boundaries, to t = 0.1, error against the analytic field)."""
+    import math
+    import torch
+    from paper_1905_05524_gb300 import _lib as L
+    from paper_1905_05524_gb300.solver import Mesh3, abc_config, bubble3d_config
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    cfg = bubble3d_config(device=dev.index)
+    m = Mesh3(cfg)
+    m.init_scenario(L.ADG_SCEN_COSINE, A=0.5, a=250.0, xc=500.0, zc=350.0)
+    dt = m.stable_dt(CFL)
+    m.step(dt, 3)
+    steps, total = 50, 0.0
+    for _ in range(steps):
+        flush.fill_(1.0)
+        e0.record(stream)
+        m.step(dt)
+        e1.record(stream)
+        e1.synchronize()
+        total += e0.elapsed_time(e1)
+    n = cfg.degree + 1
+    dof = cfg.cells * n ** 3 * 5
+    u = m.get_state()
+    out = {"metric": METRIC + " (3D scenarios)", "unit": UNIT, "dtype": "f64",
+           "bubble3d": {"config": "3D cosine bubble (Sec. 4.2), degree 2, 25^3 cells of 40 m, mu = 0.005, slip walls",
+                        "value": dof * steps / (total * 1e-3), "ms_per_step": total / steps, "dt": dt,
+                        "steps": steps, "dofs": dof, "gpu_launches_per_step": 2,
+                        "finite": bool(torch.isfinite(u).all())}}
+    m.close()
+    cfg = abc_config(device=dev.index)
+    m = Mesh3(cfg)
+    m.init_scenario(L.ADG_SCEN_ABC)
+    T = 0.1
+    dt0 = m.stable_dt(0.5)
+    nsteps = math.ceil(T / dt0)
+    dt = T / nsteps
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    m.step(dt, nsteps)
+    torch.cuda.synchronize()
+    sec = time.perf_counter() - t0
+    ref = Mesh3(cfg)
+    ref.time = T
+    ref.init_scenario(L.ADG_SCEN_ABC)
+    a, b = m.get_state(), ref.get_state()
+    n = cfg.degree + 1
+    err = float(torch.linalg.vector_norm(a[:, 1:4] - b[:, 1:4]) / torch.linalg.vector_norm(b[:, 1:4]))
+    out["abc"] = {"config": "ABC flow (Sec. 4.1), degree 2, 27^3 cells, mu = 0.01, analytic boundaries, t = 0.1",
+                  "steps": nsteps, "dt": dt, "seconds": sec, "value": cfg.cells * n ** 3 * 5 * nsteps / sec,
+                  "velocity_rel_l2_vs_analytic": err}
+    m.close()
+    ref.close()
+    return out
+
+
 def run_adjoint(args, dev):
     """Config 4: gradient of the probe misfit through 200 FP64 steps (degree 3,
     27x27) with checkpoints every 20: forward + checkpointed backward."""
@@ -671,7 +732,7 @@ def run_ours(args):
     if args.workload != "bubble":
         if rank == 0:
             fn = {"amr": run_amr, "sweep": run_sweep, "adjoint": run_adjoint, "cfd": run_cfd,
-                  "fv": run_fv}[args.workload]
+                  "fv": run_fv, "3d": run_3d}[args.workload]
             print(json.dumps(fn(args, dev)), flush=True)
         return 0
     n = DEGREE + 1
@@ -775,11 +836,12 @@ def main():
     ap.add_argument("--no-compare", action="store_true", help="skip the FP64 comparison form")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-instance batched form")
     ap.add_argument("--batch-steps", type=int, default=20)
-    ap.add_argument("--workload", default="bubble", choices=["bubble", "amr", "sweep", "adjoint", "cfd", "fv"],
+    ap.add_argument("--workload", default="bubble", choices=["bubble", "amr", "sweep", "adjoint", "cfd", "fv", "3d"],
                     help="extra workloads, each printing its own JSON line: amr (config 3), "
                          "sweep (config 5 degree sweep), adjoint (config 4 gradient), "
                          "cfd (Sec. 4.1 Taylor-Green vortex and lid-driven cavity), "
-                         "fv (MUSCL-Hancock finite volumes, colliding bubbles)")
+                         "fv (MUSCL-Hancock finite volumes, colliding bubbles), "
+                         "3d (3D cosine bubble and ABC flow)")
     ap.add_argument("--sweep-steps", type=int, default=20)
     ap.add_argument("--amr-steps", type=int, default=1000)
     ap.add_argument("--cpu-steps", type=int, default=8)

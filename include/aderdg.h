@@ -324,6 +324,50 @@ int adg_fv_init_scenario(adg_fv* f, const adg_scenario* s, void* stream);
 int adg_fv_step(adg_fv* f, double dt, void* stream);
 int adg_fv_stable_dt(adg_fv* f, double cfl, double* dt, void* stream);
 
+/* ---- Three dimensions (the ABC flow of Sec. 4.1, the 3D cosine bubble of
+ * Sec. 4.2) ----
+ *
+ * The ADER-DG scheme above on a uniform nx x ny x nz mesh of degree N in
+ * FP64: n = N+1 Picard sweeps of the space-time predictor, time-averaged
+ * volume term and face traces, the Rusanov-type viscous flux and the FP64
+ * update (one predictor and one corrector kernel per step).  z is the
+ * vertical: gravity, the isentropic background (Eq. 6) and the perturbation
+ * form (Eq. 7) act along z.
+ *   desc   supplies degree (1..ADG_MAX_DEGREE_3D), nx, ny, x0, y0, Lx, Ly,
+ *          bc_x, bc_y, gamma, Pr, R, mu, gravity, g, p0, theta0, device and
+ *          bc_field; precision must be ADG_PREC_FP64, source ADG_SRC_NONE,
+ *          max_levels 0 (ADG_EUNSUPPORTED otherwise).
+ *   nz, z0, Lz, bc_z   the vertical cells, origin, extent and boundary.
+ * Boundaries per direction: periodic, ADG_BC_WALL (slip wall: background
+ * rho, rhoE with gravity, reflected momentum, interior gradient, the
+ * background heat flux of Eq. 10) or ADG_BC_ANALYTIC with bc_field
+ * ADG_FIELD_ABC (no gravity; the field's state and flux averaged over the
+ * step at the Gauss-Legendre time nodes).
+ * State: double[nz*ny*nx][5][n][n][n], cell c = (iz*ny + iy)*nx + ix,
+ * variables (rho, rho u, rho v, rho w, rho E), nodes [l (z)][j (y)][i (x)].
+ * adg3_step: nsteps steps of fixed dt, advancing the mesh time.
+ * adg3_stable_dt: cfl h_min / (3 (2N+1) max(|v| + c + 2 eta lambda_v));
+ *   synchronises `stream`.
+ * adg3_init_scenario: ADG_SCEN_COSINE (centre (xc, xc, zc): the paper sets
+ *   yc = xc), ADG_SCEN_BACKGROUND (gravity on) or ADG_SCEN_ABC (the ABC field
+ *   at the mesh time).  Errors as for adg_mesh. */
+#define ADG_MAX_DEGREE_3D 4
+#define ADG_FIELD_ABC 2         /* Sec. 4.1: rho = 1, v = e^{-mu t} (sin z + cos y,
+                                   sin x + cos z, sin y + cos x), p = -e^{-2 mu t}
+                                   (cos x sin y + sin x cos z + sin z cos y) + 100/gamma */
+#define ADG_SCEN_ABC 7          /* the ABC field (3D meshes)                      */
+typedef struct adg_mesh3 adg_mesh3;
+int adg3_create(const adg_mesh_desc* desc, int nz, double z0, double Lz, int bc_z, adg_mesh3** out);
+void adg3_destroy(adg_mesh3* m);
+size_t adg3_state_count(const adg_mesh3* m);
+int adg3_set_state(adg_mesh3* m, const double* u, size_t count, int on_device, void* stream);
+int adg3_get_state(adg_mesh3* m, double* u, size_t count, int on_device, void* stream);
+int adg3_set_time(adg_mesh3* m, double t);
+double adg3_get_time(const adg_mesh3* m);
+int adg3_init_scenario(adg_mesh3* m, const adg_scenario* s, void* stream);
+int adg3_step(adg_mesh3* m, double dt, int nsteps, void* stream);
+int adg3_stable_dt(adg_mesh3* m, double cfl, double* dt, void* stream);
+
 /* Text of the last error on the calling thread ("" if none). */
 const char* adg_last_error(void);
 

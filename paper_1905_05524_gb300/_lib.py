@@ -28,6 +28,7 @@ ADG_BC_NOSLIP = 5
 ADG_BC_ANALYTIC = 6
 ADG_FIELD_NONE = 0
 ADG_FIELD_TAYLOR_GREEN = 1
+ADG_FIELD_ABC = 2
 ADG_SRC_NONE = 0
 ADG_SRC_STEADY = 1
 ADG_SRC_PAPER = 2
@@ -42,6 +43,8 @@ ADG_SCEN_BACKGROUND = 3
 ADG_SCEN_PAPER = 4
 ADG_SCEN_TAYLOR_GREEN = 5
 ADG_SCEN_CAVITY = 6
+ADG_SCEN_ABC = 7
+ADG_MAX_DEGREE_3D = 4
 ADG_NOALLOC_SCRATCH_BYTES = 32 << 20
 
 STATUS_NAMES = {1: "ADG_EINVAL", 2: "ADG_ENOMEM", 3: "ADG_ECUDA", 4: "ADG_ENONFINITE",
@@ -104,6 +107,16 @@ SIGNATURES = {
     "adg_fv_init_scenario": (_I, [_P, _P, _P]),
     "adg_fv_step": (_I, [_P, _D, _P]),
     "adg_fv_stable_dt": (_I, [_P, _D, _P, _P]),
+    "adg3_create": (_I, [ctypes.POINTER(MeshDesc), _I, _D, _D, _I, ctypes.POINTER(_P)]),
+    "adg3_destroy": (None, [_P]),
+    "adg3_state_count": (_S, [_P]),
+    "adg3_set_state": (_I, [_P, _P, _S, _I, _P]),
+    "adg3_get_state": (_I, [_P, _P, _S, _I, _P]),
+    "adg3_set_time": (_I, [_P, _D]),
+    "adg3_get_time": (_D, [_P]),
+    "adg3_init_scenario": (_I, [_P, _P, _P]),
+    "adg3_step": (_I, [_P, _D, _I, _P]),
+    "adg3_stable_dt": (_I, [_P, _D, _P, _P]),
     "adg_step_tv": (_I, [_P, _D, _I, _D, _D, _P, _P, _P, _P]),
     "adg_check_finite": (_I, [_P, _P]),
     "adg_step_adjoint": (_I, [_P, _D, _P, _P, _P, _P]),

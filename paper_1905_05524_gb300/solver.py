@@ -330,3 +330,93 @@ class FvMesh:
         L.check(self._lib.adg_fv_stable_dt(self.h, float(cfl), ctypes.byref(dt), _stream_ptr(stream)))
         return dt.value
 
+
+
+@dataclass
+class Mesh3Config(MeshConfig):
+    """A 3D mesh: the 2D descriptor's x and y plus the vertical z (gravity,
+    background and perturbation split along z)."""
+    nz: int = 9
+    z0: float = 0.0
+    Lz: float = 10.0
+    bc_z: int = L.ADG_BC_PERIODIC
+
+    @property
+    def cells(self):
+        return self.nx * self.ny * self.nz
+
+
+def bubble3d_config(degree=2, n=25, mu=0.005, device=0):
+    """The 3D cosine bubble of Sec. 4.2: [0,1000]^3 m, 40 m cells (25^3),
+    order 3 (degree 2), mu = 0.005, slip walls, the atmosphere of Eq. 11."""
+    return Mesh3Config(degree=degree, nx=n, ny=n, Lx=1000.0, Ly=1000.0, bc_x=L.ADG_BC_WALL, bc_y=L.ADG_BC_WALL,
+                       gamma=1.4, Pr=0.71, R=287.058, mu=mu, gravity=1, g=9.81, p0=1e5, theta0=300.0,
+                       device=device, nz=n, z0=0.0, Lz=1000.0, bc_z=L.ADG_BC_WALL)
+
+
+def abc_config(degree=2, n=27, mu=0.01, device=0):
+    """The ABC flow of Sec. 4.1: [-pi, pi]^3, 27^3 cells, order 3 (degree 2),
+    mu = 0.01, analytic boundaries, gamma 1.4, Pr 0.7, c_v 1."""
+    return Mesh3Config(degree=degree, nx=n, ny=n, x0=-math.pi, y0=-math.pi, Lx=2 * math.pi, Ly=2 * math.pi,
+                       bc_x=L.ADG_BC_ANALYTIC, bc_y=L.ADG_BC_ANALYTIC, mu=mu, bc_field=L.ADG_FIELD_ABC,
+                       device=device, nz=n, z0=-math.pi, Lz=2 * math.pi, bc_z=L.ADG_BC_ANALYTIC)
+
+
+class Mesh3:
+    """A 3D FP64 mesh (adg3_*): state tensor [cells, 5, n, n, n]."""
+
+    def __init__(self, cfg: Mesh3Config):
+        self.cfg = cfg
+        self._lib = L.lib()
+        self.device = torch.device("cuda", cfg.device)
+        h = ctypes.c_void_p()
+        L.check(self._lib.adg3_create(ctypes.byref(cfg.to_c()), cfg.nz, float(cfg.z0), float(cfg.Lz), cfg.bc_z,
+                                      ctypes.byref(h)))
+        self.h = h
+        self.count = self._lib.adg3_state_count(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._lib.adg3_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def shape(self):
+        n = self.cfg.n
+        return (self.cfg.cells, 5, n, n, n)
+
+    @property
+    def time(self):
+        return self._lib.adg3_get_time(self.h)
+
+    @time.setter
+    def time(self, t):
+        L.check(self._lib.adg3_set_time(self.h, float(t)))
+
+    def set_state(self, u: torch.Tensor, stream=None):
+        u = u.to(self.device, torch.float64).contiguous()
+        L.check(self._lib.adg3_set_state(self.h, ctypes.c_void_p(u.data_ptr()), self.count, 1, _stream_ptr(stream)))
+
+    def get_state(self, stream=None):
+        out = torch.empty(self.shape, dtype=torch.float64, device=self.device)
+        L.check(self._lib.adg3_get_state(self.h, ctypes.c_void_p(out.data_ptr()), self.count, 1,
+                                         _stream_ptr(stream)))
+        return out
+
+    def init_scenario(self, kind, A=0.5, a=250.0, xc=500.0, zc=350.0, stream=None):
+        sc = L.Scenario(kind=kind, A=A, a=a, xc=xc, zc=zc)
+        L.check(self._lib.adg3_init_scenario(self.h, ctypes.byref(sc), _stream_ptr(stream)))
+
+    def step(self, dt, nsteps=1, stream=None):
+        L.check(self._lib.adg3_step(self.h, float(dt), int(nsteps), _stream_ptr(stream)))
+
+    def stable_dt(self, cfl, stream=None):
+        dt = ctypes.c_double()
+        L.check(self._lib.adg3_stable_dt(self.h, float(cfl), ctypes.byref(dt), _stream_ptr(stream)))
+        return dt.value
