@@ -327,16 +327,18 @@ int adg_fv_stable_dt(adg_fv* f, double cfl, double* dt, void* stream);
 /* ---- Three dimensions (the ABC flow of Sec. 4.1, the 3D cosine bubble of
  * Sec. 4.2) ----
  *
- * The ADER-DG scheme above on a uniform nx x ny x nz mesh of degree N in
- * FP64: n = N+1 Picard sweeps of the space-time predictor, time-averaged
+ * The ADER-DG scheme above on a uniform nx x ny x nz mesh of degree N:
+ * n = N+1 Picard sweeps of the space-time predictor, time-averaged
  * volume term and face traces, the Rusanov-type viscous flux and the FP64
  * update (one predictor and one corrector kernel per step).  z is the
  * vertical: gravity, the isentropic background (Eq. 6) and the perturbation
  * form (Eq. 7) act along z.
  *   desc   supplies degree (1..ADG_MAX_DEGREE_3D), nx, ny, x0, y0, Lx, Ly,
  *          bc_x, bc_y, gamma, Pr, R, mu, gravity, g, p0, theta0, device and
- *          bc_field; precision must be ADG_PREC_FP64, source ADG_SRC_NONE,
- *          max_levels 0 (ADG_EUNSUPPORTED otherwise).
+ *          bc_field; precision ADG_PREC_FP64 or ADG_PREC_MIXED (the predictor
+ *          in FP32 on perturbations of the background, the corrector and the
+ *          state in FP64); source ADG_SRC_NONE, max_levels 0
+ *          (ADG_EUNSUPPORTED otherwise).
  *   nz, z0, Lz, bc_z   the vertical cells, origin, extent and boundary.
  * Boundaries per direction: periodic, ADG_BC_WALL (slip wall: background
  * rho, rhoE with gravity, reflected momentum, interior gradient, the

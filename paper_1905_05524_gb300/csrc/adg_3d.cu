@@ -29,8 +29,10 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <type_traits>
 #include <vector>
 
+#include "adg_convert.cuh"
 #include "adg_internal.h"
 #include "adg_mesh.h"
 
@@ -351,13 +353,17 @@ k3_predictor(const double* __restrict__ u, double* __restrict__ rvol, double* __
     }
 }
 
-template <int N>
+// MX: the mixed-precision form -- Rusanov flux from the FP64 jump of the
+// face states converted to FP32, flux average and lifting in FP32, the
+// update in FP64 (ghost states stay FP64).
+template <int N, bool MX>
 __global__ void __launch_bounds__(Cfg3<N>::threads)
 k3_corrector(double* __restrict__ u, const double* __restrict__ rvol, const double* __restrict__ trace, int cells,
              double dt, double t, const Basis B, const Phys3 P, const Bg3 bg) {
     using C = Cfg3<N>;
+    using FT = typename std::conditional<MX, float, double>::type;
     constexpr int n = C::n, n2 = C::n2, n3 = C::n3, SL = 5 * n3, TR = kTr3 * n2;
-    __shared__ double Fst[C::cpb][6][5][n2];
+    __shared__ FT Fst[C::cpb][6][5][n2];
     const int cl = threadIdx.x / n3;
     const int node = threadIdx.x - cl * n3;
     const int l = node / n2, j = (node / n) % n, i = node % n;
@@ -447,22 +453,356 @@ k3_corrector(double* __restrict__ u, const double* __restrict__ rvol, const doub
             }
             sn = ot[25 * n2 + m];
         }
-        double out[5];
-        if (plus) rusanov5(qo, fo, so, qn, fn, sn, out);
-        else rusanov5(qn, fn, sn, qo, fo, so, out);
+        if constexpr (MX) {
+            const double* qL = plus ? qo : qn;
+            const double* qR = plus ? qn : qo;
+            const double* fL = plus ? fo : fn;
+            const double* fR = plus ? fn : fo;
+            const float hs = 0.5f * fmaxf(f64_to_f32(so), f64_to_f32(sn));
 #pragma unroll
-        for (int v = 0; v < 5; ++v) Fst[cl][f][v][m] = out[v];
+            for (int v = 0; v < 5; ++v)
+                Fst[cl][f][v][m] = 0.5f * (f64_to_f32(fL[v]) + f64_to_f32(fR[v])) -
+                                   hs * f64_to_f32(__dsub_rn(qR[v], qL[v]));
+        } else {
+            double out[5];
+            if (plus) rusanov5(qo, fo, so, qn, fn, sn, out);
+            else rusanov5(qn, fn, sn, qo, fo, so, out);
+#pragma unroll
+            for (int v = 0; v < 5; ++v) Fst[cl][f][v][m] = out[v];
+        }
     }
     __syncthreads();
     if (!active) return;
     double* uc = u + (size_t)cell * SL;
     const double* rc = rvol + (size_t)cell * SL;
+    FT l1[3], l0[3], ih[3];
+    {
+        const int id[3] = {i, j, l};
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            if constexpr (MX) {
+                l1[c] = f64_to_f32(B.lift1[id[c]]);
+                l0[c] = f64_to_f32(B.lift0[id[c]]);
+                ih[c] = f64_to_f32(P.inv_h[c]);
+            } else {
+                l1[c] = B.lift1[id[c]];
+                l0[c] = B.lift0[id[c]];
+                ih[c] = P.inv_h[c];
+            }
+        }
+    }
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
-        const double face = (B.lift1[i] * Fst[cl][0][v][l * n + j] - B.lift0[i] * Fst[cl][1][v][l * n + j]) * P.inv_h[0] +
-                            (B.lift1[j] * Fst[cl][2][v][l * n + i] - B.lift0[j] * Fst[cl][3][v][l * n + i]) * P.inv_h[1] +
-                            (B.lift1[l] * Fst[cl][4][v][j * n + i] - B.lift0[l] * Fst[cl][5][v][j * n + i]) * P.inv_h[2];
-        uc[v * n3 + node] += dt * (rc[v * n3 + node] - face);
+        const FT face = (l1[0] * Fst[cl][0][v][l * n + j] - l0[0] * Fst[cl][1][v][l * n + j]) * ih[0] +
+                        (l1[1] * Fst[cl][2][v][l * n + i] - l0[1] * Fst[cl][3][v][l * n + i]) * ih[1] +
+                        (l1[2] * Fst[cl][4][v][j * n + i] - l0[2] * Fst[cl][5][v][j * n + i]) * ih[2];
+        double fd;
+        if constexpr (MX) fd = f32_to_f64(face);
+        else fd = face;
+        uc[v * n3 + node] += dt * (rc[v * n3 + node] - fd);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Mixed precision predictor: the same Picard iteration in FP32 on
+// perturbation variables q' = (rho - rhobar, rho u, rho v, rho w, rhoE - Ebar)
+// (the split in FP64 at load), total gradients = perturbation gradient +
+// the FP64-formed derivative of the interpolated background.  With
+// p' = (gamma-1)(E' - |m|^2/(2 rho) - g z rho') exact algebra, no FP32 value
+// carries the background pressure through a difference.  Outputs keep the
+// FP64 formats of the FP64 predictor: rvol converted, traces rebuilt as the
+// FP64 base (the nodal background on x- and y-faces, its FP64 extrapolation
+// on z-faces) plus the FP32 perturbation, the Rusanov speed in FP64 -- so
+// the FP64 corrector runs unchanged.
+struct Phys3f {
+    float gamma, gm1, R, invR, mu, kappa, g, lamv;
+    float inv_h[3], eta[3];
+    int gravity;
+};
+
+struct Bg3m {
+    const double* rb;   // [nz][n] rhobar at nodes (FP64, for the split)
+    const double* Eb;   // [nz][n] Ebar = pbar/(gamma-1) + rhobar g z
+    const float* rbf;   // [nz][n] rhobar
+    const float* pbf;   // [nz][n] pbar
+    const float* Hbf;   // [nz][n] Ebar + pbar
+    const float* dzr;   // [nz][n] d rhobar/dz of the nodal interpolant
+    const float* dzE;   // [nz][n] d Ebar/dz
+    const double* ext;  // [nz][2: top, bottom][2: rhobar, Ebar] extrapolated to the z-faces
+    const double* zn;   // [nz][n] node heights
+    const float* zext;  // [nz][2: top, bottom][2: rhobar, pbar_eff] of the extrapolated z-face base,
+                        // pbar_eff = (gamma-1)(Ebar - rhobar g z_face) formed in FP64
+};
+
+__device__ __forceinline__ void ns_flux3f(const float q[5], const float g[3][5], float gz, float rb, float pb,
+                                          float Hb, const Phys3f& P, float f[3][5], float& src) {
+    const float rho = rb + q[0];
+    const float rinv = __frcp_rn(rho);
+    const float vel[3] = {q[1] * rinv, q[2] * rinv, q[3] * rinv};
+    const float kin = 0.5f * (vel[0] * vel[0] + vel[1] * vel[1] + vel[2] * vel[2]);
+    const float pp = P.gm1 * (q[4] - rho * kin - gz * q[0]);
+    const float T = (pb + pp) * rinv * P.invR;
+    float d[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) d[a][b] = (g[b][1 + a] - vel[a] * g[b][0]) * rinv;
+    const float div = d[0][0] + d[1][1] + d[2][2];
+    float dT[3];
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+        float s = g[b][4] - (vel[0] * g[b][1] + vel[1] * g[b][2] + vel[2] * g[b][3]) + kin * g[b][0] - gz * g[b][0];
+        if (b == 2) s -= rho * P.g;
+        dT[b] = (P.gm1 * s - P.R * T * g[b][0]) * rinv * P.invR;
+    }
+    float sig[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b)
+            sig[a][b] = P.mu * ((a == b ? (2.0f / 3.0f) * div : 0.0f) - (d[a][b] + d[b][a]));
+    const float h = Hb + (q[4] + pp);
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+        f[b][0] = q[1 + b];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) f[b][1 + a] = q[1 + a] * vel[b] + (a == b ? pp : 0.0f) + sig[a][b];
+        f[b][4] = vel[b] * h + vel[0] * sig[0][b] + vel[1] * sig[1][b] + vel[2] * sig[2][b] - P.kappa * dT[b];
+    }
+    src = P.gravity ? -P.g * q[0] : 0.0f;
+}
+
+template <int N>
+struct Cfg3m {
+    static constexpr size_t smem = (size_t)Cfg3<N>::cpb * Cfg3<N>::slots * 5 * Cfg3<N>::n3 * sizeof(float);
+};
+
+template <int N>
+__global__ void __launch_bounds__(Cfg3<N>::threads)
+k3_predictor_mixed(const double* __restrict__ u, double* __restrict__ rvol, double* __restrict__ trace, int cells,
+                   float dt, const BasisF B, const Phys3f P, const Phys3 P64, const Bg3m bg) {
+    using C = Cfg3<N>;
+    constexpr int n = C::n, n2 = C::n2, n3 = C::n3, SL = 5 * n3;
+    extern __shared__ float smf[];
+    const int cl = threadIdx.x / n3;
+    const int node = threadIdx.x - cl * n3;
+    const int l = node / n2, j = (node / n) % n, i = node % n;
+    const int cell_raw = blockIdx.x * C::cpb + cl;
+    const bool active = cell_raw < cells;
+    const int cell = active ? cell_raw : cells - 1;
+    const int iz = cell / (P64.nc[0] * P64.nc[1]);
+    float* Q = smf + (size_t)cl * C::slots * SL;
+    float* Fs = Q + n * SL;
+    const int nb = iz * n + l;
+    const float rb = bg.rbf[nb], pb = bg.pbf[nb], Hb = bg.Hbf[nb], dzr = bg.dzr[nb], dzE = bg.dzE[nb];
+    const float gz = (float)(P64.g * bg.zn[nb]);
+
+    float uu[5];
+    {
+        const double* uc = u + (size_t)cell * SL;
+        uu[0] = f64_to_f32(__dsub_rn(uc[node], bg.rb[nb]));
+        uu[1] = f64_to_f32(uc[n3 + node]);
+        uu[2] = f64_to_f32(uc[2 * n3 + node]);
+        uu[3] = f64_to_f32(uc[3 * n3 + node]);
+        uu[4] = f64_to_f32(__dsub_rn(uc[4 * n3 + node], bg.Eb[nb]));
+    }
+#pragma unroll
+    for (int v = 0; v < 5; ++v) Q[v * n3 + node] = uu[v];
+    __syncthreads();
+
+    auto eval = [&](const float* Qk, float q[5], float g[3][5], float f[3][5], float& src) {
+#pragma unroll
+        for (int v = 0; v < 5; ++v) {
+            const float* Qv = Qk + v * n3;
+            q[v] = Qv[node];
+            float sx = 0.0f, sy = 0.0f, sz = 0.0f;
+#pragma unroll
+            for (int p = 0; p < n; ++p) {
+                sx = fmaf(B.D[i][p], Qv[(l * n + j) * n + p], sx);
+                sy = fmaf(B.D[j][p], Qv[(l * n + p) * n + i], sy);
+                sz = fmaf(B.D[l][p], Qv[(p * n + j) * n + i], sz);
+            }
+            g[0][v] = sx * P.inv_h[0];
+            g[1][v] = sy * P.inv_h[1];
+            g[2][v] = sz * P.inv_h[2];
+        }
+        g[2][0] += dzr;
+        g[2][4] += dzE;
+        ns_flux3f(q, g, gz, rb, pb, Hb, P, f, src);
+    };
+    auto store = [&](const float f[3][5]) {
+#pragma unroll
+        for (int b = 0; b < 3; ++b)
+#pragma unroll
+            for (int v = 0; v < 5; ++v) Fs[(b * 5 + v) * n3 + node] = f[b][v];
+    };
+    auto divergence = [&](int v) {
+        const float* Fv = Fs + v * n3;
+        const float* Gv = Fs + (5 + v) * n3;
+        const float* Hv = Fs + (10 + v) * n3;
+        float sx = 0.0f, sy = 0.0f, sz = 0.0f;
+#pragma unroll
+        for (int p = 0; p < n; ++p) {
+            sx = fmaf(B.D[i][p], Fv[(l * n + j) * n + p], sx);
+            sy = fmaf(B.D[j][p], Gv[(l * n + p) * n + i], sy);
+            sz = fmaf(B.D[l][p], Hv[(p * n + j) * n + i], sz);
+        }
+        return -(sx * P.inv_h[0] + sy * P.inv_h[1] + sz * P.inv_h[2]);
+    };
+
+    {
+        float q[5], g[3][5], f[3][5], src;
+        eval(Q, q, g, f, src);
+        store(f);
+        __syncthreads();
+        float R0[5];
+#pragma unroll
+        for (int v = 0; v < 5; ++v) R0[v] = (v == 3 ? src : 0.0f) + divergence(v);
+#pragma unroll
+        for (int k = 0; k < n; ++k)
+#pragma unroll
+            for (int v = 0; v < 5; ++v) Q[k * SL + v * n3 + node] = uu[v] + dt * (B.Kw1[k] * R0[v]);
+        __syncthreads();
+    }
+#pragma unroll 1
+    for (int r = 1; r < n; ++r) {
+        float R[n][5];
+#pragma unroll
+        for (int k = 0; k < n; ++k) {
+            float q[5], g[3][5], f[3][5], src;
+            eval(Q + k * SL, q, g, f, src);
+            __syncthreads();
+            store(f);
+            __syncthreads();
+#pragma unroll
+            for (int v = 0; v < 5; ++v) R[k][v] = (v == 3 ? src : 0.0f) + divergence(v);
+        }
+#pragma unroll
+        for (int k = 0; k < n; ++k)
+#pragma unroll
+            for (int v = 0; v < 5; ++v) {
+                float acc = 0.0f;
+#pragma unroll
+                for (int m = 0; m < n; ++m) acc = fmaf(B.Kw[k][m], R[m][v], acc);
+                Q[k * SL + v * n3 + node] = uu[v] + dt * acc;
+            }
+        __syncthreads();
+    }
+
+    float qb[5], fb[3][5], gb[3][5], sb = 0.0f;
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+        qb[v] = 0.0f;
+#pragma unroll
+        for (int b = 0; b < 3; ++b) fb[b][v] = gb[b][v] = 0.0f;
+    }
+#pragma unroll
+    for (int k = 0; k < n; ++k) {
+        float q[5], g[3][5], f[3][5], src;
+        eval(Q + k * SL, q, g, f, src);
+        const float wk = B.w[k];
+        sb = fmaf(wk, src, sb);
+#pragma unroll
+        for (int v = 0; v < 5; ++v) {
+            qb[v] = fmaf(wk, q[v], qb[v]);
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                fb[b][v] = fmaf(wk, f[b][v], fb[b][v]);
+                gb[b][v] = fmaf(wk, g[b][v], gb[b][v]);
+            }
+        }
+    }
+    __syncthreads();
+    float* A = Q;
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+        A[v * n3 + node] = qb[v];
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            A[(1 + b) * SL + v * n3 + node] = fb[b][v];
+            A[(4 + b) * SL + v * n3 + node] = gb[b][v];
+        }
+    }
+    __syncthreads();
+    if (active) {
+        double* rc = rvol + (size_t)cell * SL;
+#pragma unroll
+        for (int v = 0; v < 5; ++v) {
+            const float* Fv = A + 1 * SL + v * n3;
+            const float* Gv = A + 2 * SL + v * n3;
+            const float* Hv = A + 3 * SL + v * n3;
+            float sx = 0.0f, sy = 0.0f, sz = 0.0f;
+#pragma unroll
+            for (int p = 0; p < n; ++p) {
+                sx = fmaf(B.Vx[p][i], Fv[(l * n + j) * n + p], sx);
+                sy = fmaf(B.Vx[p][j], Gv[(l * n + p) * n + i], sy);
+                sz = fmaf(B.Vx[p][l], Hv[(p * n + j) * n + i], sz);
+            }
+            rc[v * n3 + node] = f32_to_f64(sx * P.inv_h[0] + sy * P.inv_h[1] + sz * P.inv_h[2] + (v == 3 ? sb : 0.0f));
+        }
+    }
+    for (int idx = node; idx < 6 * n2; idx += n3) {
+        const int f = idx / n2, m = idx - f * n2;
+        const int a = m / n, b = m - a * n;
+        const int dir = f >> 1;
+        const float* phi = (f & 1) ? B.phi0 : B.phi1;
+        double rec[kTr3];
+#pragma unroll
+        for (int c = 0; c < 5; ++c) {
+            const int slot = c == 0 ? 0 : c == 1 ? 1 + dir : 2 + c;
+#pragma unroll
+            for (int v = 0; v < 5; ++v) {
+                const float* S = A + slot * SL + v * n3;
+                float s = 0.0f;
+#pragma unroll
+                for (int p = 0; p < n; ++p) {
+                    const int at = dir == 0 ? (a * n + b) * n + p : dir == 1 ? (a * n + p) * n + b : (p * n + a) * n + b;
+                    s = fmaf(phi[p], S[at], s);
+                }
+                rec[c * 5 + v] = f32_to_f64(s);
+            }
+        }
+        // FP64 base of the face node: the nodal background at the node's height
+        // on x- and y-faces, its extrapolation on z-faces
+        double brho, bE;
+        if (dir < 2) {
+            brho = bg.rb[iz * n + a];
+            bE = bg.Eb[iz * n + a];
+        } else {
+            const double* e = bg.ext + ((size_t)iz * 2 + (f & 1)) * 2;
+            brho = e[0];
+            bE = e[1];
+        }
+        // Rusanov speed in FP32 from the perturbation face state over its base
+        {
+            float rbf, pbf, zf;
+            if (dir < 2) {
+                rbf = bg.rbf[iz * n + a];
+                pbf = bg.pbf[iz * n + a];
+                zf = (float)bg.zn[iz * n + a];
+            } else {
+                const float* e = bg.zext + ((size_t)iz * 2 + (f & 1)) * 2;
+                rbf = e[0];
+                pbf = e[1];
+                zf = (float)(P64.org[2] + (iz + ((f & 1) ? 0 : 1)) * P64.h[2]);
+            }
+            const float qp0 = (float)rec[0], qp4 = (float)rec[4];
+            const float m0 = (float)rec[1], m1 = (float)rec[2], m2 = (float)rec[3];
+            const float rho = rbf + qp0;
+            const float rinv = __frcp_rn(rho);
+            const float pp = P.gm1 * (qp4 - 0.5f * (m0 * m0 + m1 * m1 + m2 * m2) * rinv - P.g * zf * qp0);
+            const float mn = dir == 0 ? m0 : dir == 1 ? m1 : m2;
+            const float sp = fabsf(mn) * rinv + sqrtf(P.gamma * (pbf + pp) * rinv) +
+                             2.0f * P.eta[dir] * P.lamv * rinv;
+            rec[25] = f32_to_f64(sp);
+        }
+        rec[0] += brho;
+        rec[4] += bE;
+        if (active) {
+            double* tr = trace + ((size_t)cell * 6 + f) * kTr3 * n2;
+#pragma unroll
+            for (int c = 0; c < kTr3; ++c) tr[c * n2 + m] = rec[c];
+        }
     }
 }
 
@@ -533,7 +873,7 @@ __global__ void __launch_bounds__(256) k3_speed(const double* __restrict__ u, in
 
 template <int N>
 int launch3(bool pred, double* u, double* rvol, double* trace, int cells, double dt, double t, const Basis& B,
-            const Phys3& P, const Bg3& bg, cudaStream_t s) {
+            const Phys3& P, const Bg3& bg, cudaStream_t s, bool mixed) {
     using C = Cfg3<N>;
     const int blocks = (cells + C::cpb - 1) / C::cpb;
     if (pred) {
@@ -541,18 +881,42 @@ int launch3(bool pred, double* u, double* rvol, double* trace, int cells, double
         if (e != cudaSuccess) return (int)e;
         k3_predictor<N><<<blocks, C::threads, C::smem, s>>>(u, rvol, trace, cells, dt, B, P, bg);
     } else {
-        k3_corrector<N><<<blocks, C::threads, 0, s>>>(u, rvol, trace, cells, dt, t, B, P, bg);
+        if (mixed) k3_corrector<N, true><<<blocks, C::threads, 0, s>>>(u, rvol, trace, cells, dt, t, B, P, bg);
+        else k3_corrector<N, false><<<blocks, C::threads, 0, s>>>(u, rvol, trace, cells, dt, t, B, P, bg);
     }
     return (int)cudaGetLastError();
 }
 
-int launch3_any(int N, bool pred, double* u, double* rvol, double* trace, int cells, double dt, double t,
-                const Basis& B, const Phys3& P, const Bg3& bg, cudaStream_t s) {
+template <int N>
+int launch3m(const double* u, double* rvol, double* trace, int cells, float dt, const BasisF& B, const Phys3f& P,
+             const Phys3& P64, const Bg3m& bg, cudaStream_t s) {
+    using C = Cfg3<N>;
+    const int blocks = (cells + C::cpb - 1) / C::cpb;
+    cudaError_t e = cudaFuncSetAttribute(k3_predictor_mixed<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)Cfg3m<N>::smem);
+    if (e != cudaSuccess) return (int)e;
+    k3_predictor_mixed<N><<<blocks, C::threads, Cfg3m<N>::smem, s>>>(u, rvol, trace, cells, dt, B, P, P64, bg);
+    return (int)cudaGetLastError();
+}
+
+int launch3m_any(int N, const double* u, double* rvol, double* trace, int cells, float dt, const BasisF& B,
+                 const Phys3f& P, const Phys3& P64, const Bg3m& bg, cudaStream_t s) {
     switch (N) {
-        case 1: return launch3<1>(pred, u, rvol, trace, cells, dt, t, B, P, bg, s);
-        case 2: return launch3<2>(pred, u, rvol, trace, cells, dt, t, B, P, bg, s);
-        case 3: return launch3<3>(pred, u, rvol, trace, cells, dt, t, B, P, bg, s);
-        case 4: return launch3<4>(pred, u, rvol, trace, cells, dt, t, B, P, bg, s);
+        case 1: return launch3m<1>(u, rvol, trace, cells, dt, B, P, P64, bg, s);
+        case 2: return launch3m<2>(u, rvol, trace, cells, dt, B, P, P64, bg, s);
+        case 3: return launch3m<3>(u, rvol, trace, cells, dt, B, P, P64, bg, s);
+        case 4: return launch3m<4>(u, rvol, trace, cells, dt, B, P, P64, bg, s);
+        default: return (int)cudaErrorInvalidValue;
+    }
+}
+
+int launch3_any(int N, bool pred, double* u, double* rvol, double* trace, int cells, double dt, double t,
+                const Basis& B, const Phys3& P, const Bg3& bg, cudaStream_t s, bool mixed = false) {
+    switch (N) {
+        case 1: return launch3<1>(pred, u, rvol, trace, cells, dt, t, B, P, bg, s, mixed);
+        case 2: return launch3<2>(pred, u, rvol, trace, cells, dt, t, B, P, bg, s, mixed);
+        case 3: return launch3<3>(pred, u, rvol, trace, cells, dt, t, B, P, bg, s, mixed);
+        case 4: return launch3<4>(pred, u, rvol, trace, cells, dt, t, B, P, bg, s, mixed);
         default: return (int)cudaErrorInvalidValue;
     }
 }
@@ -571,6 +935,11 @@ struct adg_mesh3 {
     double* bg = nullptr;     // pbar, rhobar at nodes [nz n] each, then at faces [nz + 1] each
     double* part = nullptr;   // stable-dt block maxima
     int part_blocks = 0;
+    // mixed precision: FP32 basis and constants, background tables
+    adg::BasisF Bf;
+    adg::Phys3f Pf;
+    double* mbg = nullptr;    // rhobar, Ebar, node height [nz n] each, then extrapolated z-face base [nz][2][2]
+    float* mbgf = nullptr;    // rhobar, pbar, Ebar + pbar, d rhobar/dz, d Ebar/dz [nz n] each
 };
 
 using adg::cuda_fail;
@@ -591,12 +960,121 @@ void free3(adg_mesh3* m) {
     cudaFree(m->trace);
     cudaFree(m->bg);
     cudaFree(m->part);
+    cudaFree(m->mbg);
+    cudaFree(m->mbgf);
     delete m;
 }
 
 adg::Bg3 bg3(const adg_mesh3* m) {
     const int nn = m->nz * m->n;
     return adg::Bg3{m->bg, m->bg + nn, m->bg + 2 * nn, m->bg + 2 * nn + (m->nz + 1)};
+}
+
+adg::Bg3m bg3m(const adg_mesh3* m) {
+    const size_t nn = (size_t)m->nz * m->n;
+    adg::Bg3m b;
+    b.rb = m->mbg;
+    b.Eb = m->mbg + nn;
+    b.zn = m->mbg + 2 * nn;
+    b.ext = m->mbg + 3 * nn;
+    b.rbf = m->mbgf;
+    b.pbf = m->mbgf + nn;
+    b.Hbf = m->mbgf + 2 * nn;
+    b.dzr = m->mbgf + 3 * nn;
+    b.dzE = m->mbgf + 4 * nn;
+    b.zext = m->mbgf + 5 * nn;
+    return b;
+}
+
+// FP32 basis and constants and the background tables of the mixed predictor
+int build_mixed3(adg_mesh3* m) {
+    const int n = m->n, nz = m->nz;
+    const adg::Basis& B = m->B;
+    adg::BasisF& b = m->Bf;
+    std::memset(&b, 0, sizeof(b));
+    for (int a = 0; a < n; ++a) {
+        b.xi[a] = (float)B.xi[a];
+        b.w[a] = (float)B.w[a];
+        b.phi0[a] = (float)B.phi0[a];
+        b.phi1[a] = (float)B.phi1[a];
+        b.Kw1[a] = (float)B.Kw1[a];
+        b.lift0[a] = (float)B.lift0[a];
+        b.lift1[a] = (float)B.lift1[a];
+        for (int c = 0; c < n; ++c) {
+            b.D[a][c] = (float)B.D[a][c];
+            b.Kw[a][c] = (float)B.Kw[a][c];
+            b.Vx[a][c] = (float)B.Vx[a][c];
+        }
+    }
+    const adg::Phys3& P = m->P;
+    adg::Phys3f& f = m->Pf;
+    std::memset(&f, 0, sizeof(f));
+    f.gamma = (float)P.gamma;
+    f.gm1 = (float)P.gm1;
+    f.R = (float)P.R;
+    f.invR = (float)P.invR;
+    f.mu = (float)P.mu;
+    f.kappa = (float)P.kappa;
+    f.g = (float)P.g;
+    f.lamv = (float)P.lamv;
+    for (int c = 0; c < 3; ++c) {
+        f.inv_h[c] = (float)P.inv_h[c];
+        f.eta[c] = (float)P.eta[c];
+    }
+    f.gravity = P.gravity;
+    const size_t nn = (size_t)nz * n;
+    std::vector<double> hd(3 * nn + 4 * (size_t)nz, 0.0);
+    std::vector<float> hf(5 * nn + 4 * (size_t)nz, 0.0f);
+    std::vector<double> rb(nn, 0.0), Eb(nn, 0.0), pb(nn, 0.0);
+    for (int iz = 0; iz < nz; ++iz)
+        for (int l = 0; l < n; ++l) {
+            const size_t k = (size_t)iz * n + l;
+            const double z = P.org[2] + (iz + B.xi[l]) * P.h[2];
+            hd[2 * nn + k] = z;
+            if (P.gravity) {
+                const double ex = 1.0 - P.g * z / (P.cp * P.theta0);
+                pb[k] = P.p0 * std::pow(ex, P.cp / P.R);
+                rb[k] = pb[k] / (P.R * P.theta0 * ex);
+                Eb[k] = pb[k] / P.gm1 + rb[k] * P.g * z;
+            }
+        }
+    for (int iz = 0; iz < nz; ++iz) {
+        for (int l = 0; l < n; ++l) {
+            const size_t k = (size_t)iz * n + l;
+            double dr = 0.0, dE = 0.0;
+            for (int p = 0; p < n; ++p) {
+                dr += B.D[l][p] * rb[(size_t)iz * n + p];
+                dE += B.D[l][p] * Eb[(size_t)iz * n + p];
+            }
+            hd[k] = rb[k];
+            hd[nn + k] = Eb[k];
+            hf[k] = (float)rb[k];
+            hf[nn + k] = (float)pb[k];
+            hf[2 * nn + k] = (float)(Eb[k] + pb[k]);
+            hf[3 * nn + k] = (float)(dr * P.inv_h[2]);
+            hf[4 * nn + k] = (float)(dE * P.inv_h[2]);
+        }
+        for (int face = 0; face < 2; ++face) {  // 0: top (phi(1)), 1: bottom (phi(0))
+            const double* phi = face == 0 ? B.phi1 : B.phi0;
+            double er = 0.0, eE = 0.0;
+            for (int p = 0; p < n; ++p) {
+                er += phi[p] * rb[(size_t)iz * n + p];
+                eE += phi[p] * Eb[(size_t)iz * n + p];
+            }
+            hd[3 * nn + ((size_t)iz * 2 + face) * 2] = er;
+            hd[3 * nn + ((size_t)iz * 2 + face) * 2 + 1] = eE;
+            const double zf = P.org[2] + (iz + (face == 0 ? 1 : 0)) * P.h[2];
+            hf[5 * nn + ((size_t)iz * 2 + face) * 2] = (float)er;
+            hf[5 * nn + ((size_t)iz * 2 + face) * 2 + 1] = (float)(P.gm1 * (eE - er * P.g * zf));
+        }
+    }
+    if (cudaMalloc(&m->mbg, hd.size() * 8) != cudaSuccess || cudaMalloc(&m->mbgf, hf.size() * 4) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ADG_ENOMEM, "adg3_create: mixed-precision tables");
+    }
+    ADG_CK(cudaMemcpy(m->mbg, hd.data(), hd.size() * 8, cudaMemcpyHostToDevice), "adg3_create: mixed tables");
+    ADG_CK(cudaMemcpy(m->mbgf, hf.data(), hf.size() * 4, cudaMemcpyHostToDevice), "adg3_create: mixed tables");
+    return ADG_OK;
 }
 
 bool bc3_ok(int bc) { return bc == ADG_BC_PERIODIC || bc == ADG_BC_WALL || bc == ADG_BC_ANALYTIC; }
@@ -615,8 +1093,9 @@ extern "C" int adg3_create(const adg_mesh_desc* d, int nz, double z0, double Lz,
         return fail(ADG_EINVAL, "adg3_create: boundaries are periodic, ADG_BC_WALL or ADG_BC_ANALYTIC");
     if (!(d->gamma > 1.0) || !(d->R > 0.0) || !(d->Pr > 0.0) || !(d->mu >= 0.0))
         return fail(ADG_EINVAL, "adg3_create: invalid gas constants");
-    if (d->precision != ADG_PREC_FP64 || d->source != ADG_SRC_NONE || d->max_levels != 0)
-        return fail(ADG_EUNSUPPORTED, "adg3_create: FP64, no manufactured source, uniform mesh only");
+    if ((d->precision != ADG_PREC_FP64 && d->precision != ADG_PREC_MIXED) || d->source != ADG_SRC_NONE ||
+        d->max_levels != 0)
+        return fail(ADG_EUNSUPPORTED, "adg3_create: FP64 or mixed, no manufactured source, uniform mesh only");
     const bool analytic = d->bc_x == ADG_BC_ANALYTIC || d->bc_y == ADG_BC_ANALYTIC || bc_z == ADG_BC_ANALYTIC;
     if (analytic && (d->bc_field != ADG_FIELD_ABC || d->gravity))
         return fail(ADG_EINVAL, "adg3_create: analytic boundaries take bc_field ADG_FIELD_ABC without gravity");
@@ -698,6 +1177,12 @@ extern "C" int adg3_create(const adg_mesh_desc* d, int nz, double z0, double Lz,
         free3(m);
         return fail(ADG_ECUDA, "adg3_create: initialisation failed");
     }
+    if (d->precision == ADG_PREC_MIXED) {
+        if (int rc = build_mixed3(m)) {
+            free3(m);
+            return rc;
+        }
+    }
     *out = m;
     return ADG_OK;
 }
@@ -761,9 +1246,13 @@ extern "C" int adg3_step(adg_mesh3* m, double dt, int nsteps, void* stream) {
     cudaStream_t s = (cudaStream_t)stream;
     const adg::Bg3 bg = bg3(m);
     for (int k = 0; k < nsteps; ++k) {
-        int e = adg::launch3_any(m->N, true, m->u, m->rvol, m->trace, m->cells, dt, m->t, m->B, m->P, bg, s);
+        int e = m->d.precision == ADG_PREC_MIXED
+                    ? adg::launch3m_any(m->N, m->u, m->rvol, m->trace, m->cells, (float)dt, m->Bf, m->Pf, m->P,
+                                        bg3m(m), s)
+                    : adg::launch3_any(m->N, true, m->u, m->rvol, m->trace, m->cells, dt, m->t, m->B, m->P, bg, s);
         if (e) return cuda_fail((cudaError_t)e, "adg3_step predictor");
-        e = adg::launch3_any(m->N, false, m->u, m->rvol, m->trace, m->cells, dt, m->t, m->B, m->P, bg, s);
+        e = adg::launch3_any(m->N, false, m->u, m->rvol, m->trace, m->cells, dt, m->t, m->B, m->P, bg, s,
+                             m->d.precision == ADG_PREC_MIXED);
         if (e) return cuda_fail((cudaError_t)e, "adg3_step corrector");
         m->t += dt;
     }

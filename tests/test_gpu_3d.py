@@ -2,7 +2,10 @@
 (oracle/aderdg3d.py): relative L2 per variable <= 1e-11 (momentum floored at
 |rho| * 1 m/s), as the 2D FP64 parity tests; every degree 1-4, ragged
 meshes, slip walls with gravity, periodic boxes, the ABC field's analytic
-boundaries, and the full 25^3 bubble mesh of the timed configuration."""
+boundaries, and the full 25^3 bubble mesh of the timed configuration.
+The mixed-precision form (FP32 predictor on perturbations, corrector with
+FP32 flux average and lifting, FP64 jumps and update)
+is held to the 2D mixed path's bound: theta' relative L2 <= 1e-6."""
 import math
 
 import pytest
@@ -162,7 +165,7 @@ def test_full_size_bubble_one_step_matches_oracle():
 
 
 def test_rejects_unsupported_options():
-    for kw in (dict(precision=L.ADG_PREC_MIXED), dict(degree=5), dict(max_levels=1), dict(source=L.ADG_SRC_STEADY)):
+    for kw in (dict(degree=5), dict(max_levels=1), dict(source=L.ADG_SRC_STEADY)):
         cfg = bubble3d_config(degree=2, n=3)
         for k, v in kw.items():
             setattr(cfg, k, v)
@@ -176,3 +179,65 @@ def test_rejects_unsupported_options():
     cfg.gravity = 1
     with pytest.raises(L.AdgError):
         Mesh3(cfg)
+
+
+# ---------------------------------------------------------------- mixed
+THETA_TOL = 1e-6   # the 2D mixed path's stated bound on theta'
+
+
+def rel_theta_err(o, a, b):
+    w = o.b.w
+    W = w[None, :, None, None] * w[None, None, :, None] * w[None, None, None, :]
+    ta = p3.theta(a.unbind(1), o.Z, o.P) - o.P.theta0
+    tb = p3.theta(b.unbind(1), o.Z, o.P) - o.P.theta0
+    return (torch.sqrt((W * (ta - tb) ** 2).sum()) / torch.sqrt((W * tb ** 2).sum())).item()
+
+
+def mixed(cfg):
+    cfg.precision = L.ADG_PREC_MIXED
+    return cfg
+
+
+@pytest.mark.parametrize("degree", [1, 2, 3, 4])
+def test_mixed_bubble_every_degree(degree):
+    """FP32 predictor on perturbations, FP64 corrector: ragged 3 x 4 x 5
+    walled mesh, the stirred bubble, 12 steps; theta' within THETA_TOL,
+    total rho within 1e-9, momentum (floored at |rho| 1 m/s) within 1e-6."""
+    cfg = mixed(bubble3d_config(degree=degree, n=3, mu=0.5))
+    cfg.ny, cfg.nz = 4, 5
+    o = oracle3(cfg)
+    a, b = run(cfg, stirred(o, 40 + degree), 12)
+    a = a.cpu()
+    err = rel_theta_err(o, a, b)
+    assert err <= THETA_TOL, (degree, err)
+    assert (torch.linalg.vector_norm(a[:, 0] - b[:, 0]) / torch.linalg.vector_norm(b[:, 0])).item() <= 1e-9
+    assert_close(a, b, 1e-6, f"mixed N={degree}")
+
+
+def test_mixed_full_size_bubble():
+    """The timed configuration in mixed precision: 25^3, degree 2, device
+    initialisation, 3 steps at the bubble CFL."""
+    cfg = mixed(bubble3d_config())
+    o = oracle3(cfg)
+    m = Mesh3(cfg)
+    m.init_scenario(L.ADG_SCEN_COSINE, A=0.5, a=250.0, xc=500.0, zc=350.0)
+    u = m.get_state().cpu()
+    dt = m.stable_dt(0.25)
+    m.step(dt, 3)
+    for _ in range(3):
+        u = o.step(u, dt)
+    a = m.get_state().cpu()
+    assert rel_theta_err(o, a, u) <= THETA_TOL
+    assert (torch.linalg.vector_norm(a[:, 0] - u[:, 0]) / torch.linalg.vector_norm(u[:, 0])).item() <= 1e-9
+
+
+def test_mixed_abc_full_state_fp32():
+    """No gravity: the FP32 predictor carries the whole state; relative L2
+    per variable at FP32 level (<= 1e-6) after 3 steps with analytic
+    boundaries."""
+    cfg = mixed(abc_config(degree=2, n=3))
+    cfg.nx = 4
+    o = oracle3(cfg)
+    u0 = o.interpolate(p3.abc_flow, 0.1)
+    a, b = run(cfg, u0, 3, t0=0.1)
+    assert_close(a, b, 1e-6, "mixed abc")
