@@ -110,7 +110,8 @@ __device__ __forceinline__ double wave_speed3(const double q[5], double z, int d
     const double rinv = 1.0 / q[0];
     const double gg = P.gravity ? P.g : 0.0;
     const double p = P.gm1 * (q[4] - 0.5 * (q[1] * q[1] + q[2] * q[2] + q[3] * q[3]) * rinv - q[0] * gg * z);
-    return fabs(q[1 + dir] * rinv) + sqrt(P.gamma * p * rinv) + 2.0 * P.eta[dir] * P.lamv * rinv;
+    const double mn = dir == 0 ? q[1] : dir == 1 ? q[2] : q[3];  // selects keep q in registers
+    return fabs(mn * rinv) + sqrt(P.gamma * p * rinv) + 2.0 * P.eta[dir] * P.lamv * rinv;
 }
 
 __device__ __forceinline__ void rusanov5(const double qL[5], const double fL[5], double sL, const double qR[5],
@@ -370,14 +371,19 @@ k3_corrector(double* __restrict__ u, const double* __restrict__ rvol, const doub
     const int cell_raw = blockIdx.x * C::cpb + cl;
     const bool active = cell_raw < cells;
     const int cell = active ? cell_raw : cells - 1;
-    const int ic[3] = {cell % P.nc[0], (cell / P.nc[0]) % P.nc[1], cell / (P.nc[0] * P.nc[1])};
+    const int ic0 = cell % P.nc[0], ic1 = (cell / P.nc[0]) % P.nc[1], ic2 = cell / (P.nc[0] * P.nc[1]);
 
     for (int idx = node; idx < 6 * n2; idx += n3) {
         const int f = idx / n2, m = idx - f * n2;
         const int a = m / n, b = m - a * n;
         const int dir = f >> 1;
         const bool plus = (f & 1) == 0;
-        const bool edge = plus ? ic[dir] == P.nc[dir] - 1 : ic[dir] == 0;
+        // selects instead of arrays indexed by the face's direction (keeps
+        // everything in registers)
+        const int icd = dir == 0 ? ic0 : dir == 1 ? ic1 : ic2;
+        const int ncd = dir == 0 ? P.nc[0] : dir == 1 ? P.nc[1] : P.nc[2];
+        const int bcd = dir == 0 ? P.bc[0] : dir == 1 ? P.bc[1] : P.bc[2];
+        const bool edge = plus ? icd == ncd - 1 : icd == 0;
         const double* own = trace + ((size_t)cell * 6 + f) * TR;
         double qo[5], fo[5], g[3][5];
 #pragma unroll
@@ -387,24 +393,26 @@ k3_corrector(double* __restrict__ u, const double* __restrict__ rvol, const doub
         }
         const double so = own[25 * n2 + m];
         double qn[5], fn[5], sn;
-        if (edge && P.bc[dir] == ADG_BC_WALL) {
+        if (edge && bcd == ADG_BC_WALL) {
             // slip wall: background rho, rhoE at the face node (interior ones
             // without gravity), reflected normal momentum, interior gradient,
             // background heat flux
             double z, pb, rb;
             if (dir < 2) {
-                z = P.org[2] + (ic[2] + B.xi[a]) * P.h[2];
-                pb = bg.pn[ic[2] * n + a];
-                rb = bg.rn[ic[2] * n + a];
+                z = P.org[2] + (ic2 + B.xi[a]) * P.h[2];
+                pb = bg.pn[ic2 * n + a];
+                rb = bg.rn[ic2 * n + a];
             } else {
-                const int fz = ic[2] + (plus ? 1 : 0);
+                const int fz = ic2 + (plus ? 1 : 0);
                 z = P.org[2] + fz * P.h[2];
                 pb = bg.pf[fz];
                 rb = bg.rf[fz];
             }
-#pragma unroll
-            for (int v = 0; v < 5; ++v) qn[v] = qo[v];
-            qn[1 + dir] = -qo[1 + dir];
+            qn[0] = qo[0];
+            qn[1] = dir == 0 ? -qo[1] : qo[1];
+            qn[2] = dir == 1 ? -qo[2] : qo[2];
+            qn[3] = dir == 2 ? -qo[3] : qo[3];
+            qn[4] = qo[4];
             if (P.gravity) {
                 qn[0] = rb;
                 qn[4] = pb / P.gm1 + rb * P.g * z;
@@ -416,17 +424,19 @@ k3_corrector(double* __restrict__ u, const double* __restrict__ rvol, const doub
             double ff[3][5], src;
             ns_flux3(qn, g, z, pb, rb, P, true, ff, src);
 #pragma unroll
-            for (int v = 0; v < 5; ++v) fn[v] = ff[dir][v];
+            for (int v = 0; v < 5; ++v) fn[v] = dir == 0 ? ff[0][v] : dir == 1 ? ff[1][v] : ff[2][v];
             sn = wave_speed3(qn, z, dir, P);
-        } else if (edge && P.bc[dir] == ADG_BC_ANALYTIC) {
+        } else if (edge && bcd == ADG_BC_ANALYTIC) {
             // the analytic field averaged over the step at the time nodes
             double xf[3];
+            const int icc[3] = {ic0, ic1, ic2};
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 // along the face: node a (x-, y-faces: z; z-faces: y) and b
                 const bool normal = c == dir;
                 const int node_c = c == 2 ? a : (c == 1 ? (dir == 2 ? a : (dir == 0 ? b : 0)) : b);
-                xf[c] = normal ? P.org[c] + (ic[c] + (plus ? 1 : 0)) * P.h[c] : P.org[c] + (ic[c] + B.xi[node_c]) * P.h[c];
+                xf[c] = normal ? P.org[c] + (icc[c] + (plus ? 1 : 0)) * P.h[c]
+                               : P.org[c] + (icc[c] + B.xi[node_c]) * P.h[c];
             }
 #pragma unroll
             for (int v = 0; v < 5; ++v) qn[v] = fn[v] = 0.0;
@@ -437,14 +447,14 @@ k3_corrector(double* __restrict__ u, const double* __restrict__ rvol, const doub
 #pragma unroll
                 for (int v = 0; v < 5; ++v) {
                     qn[v] += B.w[k] * q[v];
-                    fn[v] += B.w[k] * ff[dir][v];
+                    fn[v] += B.w[k] * (dir == 0 ? ff[0][v] : dir == 1 ? ff[1][v] : ff[2][v]);
                 }
             }
             sn = wave_speed3(qn, xf[2], dir, P);
         } else {
-            int nb[3] = {ic[0], ic[1], ic[2]};
-            nb[dir] = plus ? (ic[dir] + 1 == P.nc[dir] ? 0 : ic[dir] + 1) : (ic[dir] == 0 ? P.nc[dir] - 1 : ic[dir] - 1);
-            const int nc = (nb[2] * P.nc[1] + nb[1]) * P.nc[0] + nb[0];
+            const int nd = plus ? (icd + 1 == ncd ? 0 : icd + 1) : (icd == 0 ? ncd - 1 : icd - 1);
+            const int nb0 = dir == 0 ? nd : ic0, nb1 = dir == 1 ? nd : ic1, nb2 = dir == 2 ? nd : ic2;
+            const int nc = (nb2 * P.nc[1] + nb1) * P.nc[0] + nb0;
             const double* ot = trace + ((size_t)nc * 6 + (f ^ 1)) * TR;
 #pragma unroll
             for (int v = 0; v < 5; ++v) {
