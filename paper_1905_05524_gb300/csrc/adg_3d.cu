@@ -585,10 +585,15 @@ __device__ __forceinline__ void ns_flux3f(const float q[5], const float g[3][5],
 template <int N>
 struct Cfg3m {
     static constexpr size_t smem = (size_t)Cfg3<N>::cpb * Cfg3<N>::slots * 5 * Cfg3<N>::n3 * sizeof(float);
+    // resident blocks asked of the register allocator: measured on the 25^3
+    // bubble, degree 2 runs 12% faster at 4 blocks (72 registers, some
+    // spills) than at the unconstrained 111 registers; degree 3 gains 1% at
+    // 3 and loses at 4; degree 1 is indifferent
+    static constexpr int minb = N == 2 ? 4 : N == 3 ? 3 : 1;
 };
 
 template <int N>
-__global__ void __launch_bounds__(Cfg3<N>::threads)
+__global__ void __launch_bounds__(Cfg3<N>::threads, Cfg3m<N>::minb)
 k3_predictor_mixed(const double* __restrict__ u, double* __restrict__ rvol, double* __restrict__ trace, int cells,
                    float dt, const BasisF B, const Phys3f P, const Phys3 P64, const Bg3m bg) {
     using C = Cfg3<N>;
