@@ -17,8 +17,13 @@
  *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
  *     stream); all device work of a call is queued on it; only calls that
  *     return host data synchronise it;
- *   - `on_device` != 0 means the pointer is a device pointer on the mesh's
- *     device, 0 means host memory.
+ *   - `on_device` 1 means the pointer is a device pointer on the mesh's
+ *     device, 0 means host memory (a get_state into host memory synchronises
+ *     `stream`), ADG_COPY_HOST_ASYNC (2) means host memory copied
+ *     asynchronously on `stream` without synchronising: the caller keeps the
+ *     buffer alive and unchanged until the stream has passed the copy (page-
+ *     locked memory makes the copy truly asynchronous); other values are
+ *     ADG_EINVAL.
  *
  * State layout (set_state / get_state / adjoint vectors): double u[c][v][j][i]
  * with c = iy*nx + ix (row-major cells), v = rho, rho*u, rho*v, rho*E, and
@@ -77,6 +82,8 @@ extern "C" {
 #define ADG_TV_THETA 1      /* potential temperature theta = T (p0/p)^(R/cp)  */
 
 #define ADG_MAX_DEGREE 7
+
+#define ADG_COPY_HOST_ASYNC 2 /* on_device value: host memory, asynchronous copy */
 
 typedef struct adg_mesh adg_mesh;
 

@@ -45,6 +45,7 @@ ADG_SCEN_TAYLOR_GREEN = 5
 ADG_SCEN_CAVITY = 6
 ADG_SCEN_ABC = 7
 ADG_MAX_DEGREE_3D = 4
+ADG_COPY_HOST_ASYNC = 2
 ADG_NOALLOC_SCRATCH_BYTES = 32 << 20
 
 STATUS_NAMES = {1: "ADG_EINVAL", 2: "ADG_ENOMEM", 3: "ADG_ECUDA", 4: "ADG_ENONFINITE",

@@ -1211,22 +1211,24 @@ extern "C" size_t adg3_state_count(const adg_mesh3* m) {
 extern "C" int adg3_set_state(adg_mesh3* m, const double* u, size_t count, int on_device, void* stream) {
     if (!m || !u) return fail(ADG_EINVAL, "adg3_set_state: NULL argument");
     if (count != adg3_state_count(m)) return fail(ADG_EINVAL, "adg3_set_state: count mismatch");
+    if (on_device < 0 || on_device > ADG_COPY_HOST_ASYNC) return fail(ADG_EINVAL, "bad on_device");
     if (int rc = dev3(m)) return rc;
-    ADG_CK(cudaMemcpyAsync(m->u, u, count * 8, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+    ADG_CK(cudaMemcpyAsync(m->u, u, count * 8, on_device == 1 ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                            (cudaStream_t)stream),
            "adg3_set_state");
-    if (!on_device) ADG_CK(cudaStreamSynchronize((cudaStream_t)stream), "adg3_set_state sync");
+    if (on_device == 0) ADG_CK(cudaStreamSynchronize((cudaStream_t)stream), "adg3_set_state sync");
     return ADG_OK;
 }
 
 extern "C" int adg3_get_state(adg_mesh3* m, double* u, size_t count, int on_device, void* stream) {
     if (!m || !u) return fail(ADG_EINVAL, "adg3_get_state: NULL argument");
     if (count != adg3_state_count(m)) return fail(ADG_EINVAL, "adg3_get_state: count mismatch");
+    if (on_device < 0 || on_device > ADG_COPY_HOST_ASYNC) return fail(ADG_EINVAL, "bad on_device");
     if (int rc = dev3(m)) return rc;
-    ADG_CK(cudaMemcpyAsync(u, m->u, count * 8, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+    ADG_CK(cudaMemcpyAsync(u, m->u, count * 8, on_device == 1 ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                            (cudaStream_t)stream),
            "adg3_get_state");
-    if (!on_device) ADG_CK(cudaStreamSynchronize((cudaStream_t)stream), "adg3_get_state sync");
+    if (on_device == 0) ADG_CK(cudaStreamSynchronize((cudaStream_t)stream), "adg3_get_state sync");
     return ADG_OK;
 }
 

@@ -485,8 +485,9 @@ size_t adg_state_count(const adg_mesh* m) {
 int adg_set_state(adg_mesh* m, const double* u, size_t count, int on_device, void* stream) {
     if (!m || !u) return fail(ADG_EINVAL, "set_state: NULL argument");
     if (count != adg_state_count(m)) return fail(ADG_EINVAL, "set_state: count != cells*(N+1)^2*4");
+    if (on_device < 0 || on_device > ADG_COPY_HOST_ASYNC) return fail(ADG_EINVAL, "set_state: bad on_device");
     if (int rc = set_device(m)) return rc;
-    ADG_CK(cudaMemcpyAsync(m->u, u, count * 8, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+    ADG_CK(cudaMemcpyAsync(m->u, u, count * 8, on_device == 1 ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                            (cudaStream_t)stream), "set_state");
     m->predicted = false;
     return ADG_OK;
@@ -495,10 +496,11 @@ int adg_set_state(adg_mesh* m, const double* u, size_t count, int on_device, voi
 int adg_get_state(adg_mesh* m, double* u, size_t count, int on_device, void* stream) {
     if (!m || !u) return fail(ADG_EINVAL, "get_state: NULL argument");
     if (count != adg_state_count(m)) return fail(ADG_EINVAL, "get_state: count != cells*(N+1)^2*4");
+    if (on_device < 0 || on_device > ADG_COPY_HOST_ASYNC) return fail(ADG_EINVAL, "get_state: bad on_device");
     if (int rc = set_device(m)) return rc;
-    ADG_CK(cudaMemcpyAsync(u, m->u, count * 8, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+    ADG_CK(cudaMemcpyAsync(u, m->u, count * 8, on_device == 1 ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                            (cudaStream_t)stream), "get_state");
-    if (!on_device) ADG_CK(cudaStreamSynchronize((cudaStream_t)stream), "get_state sync");
+    if (on_device == 0) ADG_CK(cudaStreamSynchronize((cudaStream_t)stream), "get_state sync");
     return ADG_OK;
 }
 

@@ -680,22 +680,24 @@ extern "C" size_t adg_fv_state_count(const adg_fv* f) { return f ? (size_t)4 * f
 extern "C" int adg_fv_set_state(adg_fv* f, const double* u, size_t count, int on_device, void* stream) {
     if (!f || !u) return fail(ADG_EINVAL, "fv_set_state: NULL argument");
     if (count != (size_t)4 * f->cells) return fail(ADG_EINVAL, "fv_set_state: count must be 4 * cells");
+    if (on_device < 0 || on_device > ADG_COPY_HOST_ASYNC) return fail(ADG_EINVAL, "bad on_device");
     if (int rc = fv_device(f)) return rc;
-    ADG_CK(cudaMemcpyAsync(f->u, u, count * 8, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+    ADG_CK(cudaMemcpyAsync(f->u, u, count * 8, on_device == 1 ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                            (cudaStream_t)stream),
            "fv_set_state");
-    if (!on_device) ADG_CK(cudaStreamSynchronize((cudaStream_t)stream), "fv_set_state sync");
+    if (on_device == 0) ADG_CK(cudaStreamSynchronize((cudaStream_t)stream), "fv_set_state sync");
     return ADG_OK;
 }
 
 extern "C" int adg_fv_get_state(adg_fv* f, double* u, size_t count, int on_device, void* stream) {
     if (!f || !u) return fail(ADG_EINVAL, "fv_get_state: NULL argument");
     if (count != (size_t)4 * f->cells) return fail(ADG_EINVAL, "fv_get_state: count must be 4 * cells");
+    if (on_device < 0 || on_device > ADG_COPY_HOST_ASYNC) return fail(ADG_EINVAL, "bad on_device");
     if (int rc = fv_device(f)) return rc;
-    ADG_CK(cudaMemcpyAsync(u, f->u, count * 8, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+    ADG_CK(cudaMemcpyAsync(u, f->u, count * 8, on_device == 1 ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                            (cudaStream_t)stream),
            "fv_get_state");
-    if (!on_device) ADG_CK(cudaStreamSynchronize((cudaStream_t)stream), "fv_get_state sync");
+    if (on_device == 0) ADG_CK(cudaStreamSynchronize((cudaStream_t)stream), "fv_get_state sync");
     return ADG_OK;
 }
 
