@@ -323,14 +323,26 @@ k3_predictor(const double* __restrict__ u, double* __restrict__ rvol, double* __
         }
     }
     // boundary-extrapolated traces of faces E, W (x), N, S (y), T, B (z)
+    const int ic0 = cell % P.nc[0], ic1 = (cell / P.nc[0]) % P.nc[1];
     for (int idx = node; idx < 6 * n2; idx += n3) {
         const int f = idx / n2, m = idx - f * n2;
         const int a = m / n, b = m - a * n;
         const int dir = f >> 1;
         const double* phi = (f & 1) ? B.phi0 : B.phi1;
+        // the gradient components are read only by slip-wall ghosts: written
+        // for wall faces alone
+        const int icd = dir == 0 ? ic0 : dir == 1 ? ic1 : iz;
+        const int ncd = dir == 0 ? P.nc[0] : dir == 1 ? P.nc[1] : P.nc[2];
+        const int bcd = dir == 0 ? P.bc[0] : dir == 1 ? P.bc[1] : P.bc[2];
+        const bool wallface = bcd == ADG_BC_WALL && ((f & 1) ? icd == 0 : icd == ncd - 1);
         double rec[kTr3];
 #pragma unroll
         for (int c = 0; c < 5; ++c) {
+            if (c >= 2 && !wallface) {
+#pragma unroll
+                for (int v = 0; v < 5; ++v) rec[c * 5 + v] = 0.0;
+                continue;
+            }
             const int slot = c == 0 ? 0 : c == 1 ? 1 + dir : 2 + c;  // q, normal flux, qx, qy, qz
 #pragma unroll
             for (int v = 0; v < 5; ++v) {
@@ -349,7 +361,8 @@ k3_predictor(const double* __restrict__ u, double* __restrict__ rvol, double* __
         if (active) {
             double* tr = trace + ((size_t)cell * 6 + f) * kTr3 * n2;
 #pragma unroll
-            for (int c = 0; c < kTr3; ++c) tr[c * n2 + m] = rec[c];
+            for (int c = 0; c < kTr3; ++c)
+                if (c < 10 || c == 25 || wallface) tr[c * n2 + m] = rec[c];
         }
     }
 }
@@ -756,14 +769,26 @@ k3_predictor_mixed(const double* __restrict__ u, double* __restrict__ rvol, doub
             rc[v * n3 + node] = f32_to_f64(sx * P.inv_h[0] + sy * P.inv_h[1] + sz * P.inv_h[2] + (v == 3 ? sb : 0.0f));
         }
     }
+    const int ic0 = cell % P64.nc[0], ic1 = (cell / P64.nc[0]) % P64.nc[1];
     for (int idx = node; idx < 6 * n2; idx += n3) {
         const int f = idx / n2, m = idx - f * n2;
         const int a = m / n, b = m - a * n;
         const int dir = f >> 1;
         const float* phi = (f & 1) ? B.phi0 : B.phi1;
+        // the gradient components are read only by slip-wall ghosts: written
+        // for wall faces alone
+        const int icd = dir == 0 ? ic0 : dir == 1 ? ic1 : iz;
+        const int ncd = dir == 0 ? P64.nc[0] : dir == 1 ? P64.nc[1] : P64.nc[2];
+        const int bcd = dir == 0 ? P64.bc[0] : dir == 1 ? P64.bc[1] : P64.bc[2];
+        const bool wallface = bcd == ADG_BC_WALL && ((f & 1) ? icd == 0 : icd == ncd - 1);
         double rec[kTr3];
 #pragma unroll
         for (int c = 0; c < 5; ++c) {
+            if (c >= 2 && !wallface) {
+#pragma unroll
+                for (int v = 0; v < 5; ++v) rec[c * 5 + v] = 0.0;
+                continue;
+            }
             const int slot = c == 0 ? 0 : c == 1 ? 1 + dir : 2 + c;
 #pragma unroll
             for (int v = 0; v < 5; ++v) {
@@ -816,7 +841,8 @@ k3_predictor_mixed(const double* __restrict__ u, double* __restrict__ rvol, doub
         if (active) {
             double* tr = trace + ((size_t)cell * 6 + f) * kTr3 * n2;
 #pragma unroll
-            for (int c = 0; c < kTr3; ++c) tr[c * n2 + m] = rec[c];
+            for (int c = 0; c < kTr3; ++c)
+                if (c < 10 || c == 25 || wallface) tr[c * n2 + m] = rec[c];
         }
     }
 }
