@@ -241,3 +241,23 @@ def test_mixed_abc_full_state_fp32():
     u0 = o.interpolate(p3.abc_flow, 0.1)
     a, b = run(cfg, u0, 3, t0=0.1)
     assert_close(a, b, 1e-6, "mixed abc")
+
+
+@pytest.mark.parametrize("shape,bc", [((1, 1, 1), "periodic"), ((1, 2, 1), "wall"), ((2, 1, 3), "wall")])
+def test_degenerate_meshes_match_oracle(shape, bc):
+    """One cell per direction (a periodic cell is its own neighbour on every
+    face; a walled single cell has walls on both sides), FP64 and mixed."""
+    nx, ny, nz = shape
+    for prec in (L.ADG_PREC_FP64, L.ADG_PREC_MIXED):
+        if bc == "periodic":
+            cfg = Mesh3Config(degree=2, nx=nx, ny=ny, nz=nz, Lx=6.0, Ly=5.0, Lz=7.0, mu=0.1)
+        else:
+            cfg = bubble3d_config(degree=2, n=1, mu=0.5)
+            cfg.nx, cfg.ny, cfg.nz = nx, ny, nz
+        cfg.precision = prec
+        o = oracle3(cfg)
+        a, b = run(cfg, stirred(o, 50 + nx + 3 * ny + 7 * nz), 3)
+        if prec == L.ADG_PREC_FP64:
+            assert_close(a, b, TOL, f"{shape} {bc}")
+        else:
+            assert_close(a, b, 1e-6, f"{shape} {bc} mixed")
