@@ -367,13 +367,72 @@ k3_predictor(const double* __restrict__ u, double* __restrict__ rvol, double* __
     }
 }
 
+struct Phys3f {
+    float gamma, gm1, R, invR, mu, kappa, g, lamv, dTdz;
+    float inv_h[3], eta[3];
+    int gravity;
+};
+
+struct Bg3m {
+    const double* rb;   // [nz][n] rhobar at nodes (FP64, for the split)
+    const double* Eb;   // [nz][n] Ebar = pbar/(gamma-1) + rhobar g z
+    const float* rbf;   // [nz][n] rhobar
+    const float* pbf;   // [nz][n] pbar
+    const float* Hbf;   // [nz][n] Ebar + pbar
+    const float* dzr;   // [nz][n] d rhobar/dz of the nodal interpolant
+    const float* dzE;   // [nz][n] d Ebar/dz
+    const double* ext;  // [nz][2: top, bottom][2: rhobar, Ebar] extrapolated to the z-faces
+    const double* zn;   // [nz][n] node heights
+    const float* zext;  // [nz][2: top, bottom][2: rhobar, pbar_eff] of the extrapolated z-face base,
+                        // pbar_eff = (gamma-1)(Ebar - rhobar g z_face) formed in FP64
+};
+
+__device__ __forceinline__ void ns_flux3f(const float q[5], const float g[3][5], float gz, float rb, float pb,
+                                          float Hb, const Phys3f& P, float f[3][5], float& src,
+                                          bool heat_wall = false, float dTdz = 0.0f) {
+    const float rho = rb + q[0];
+    const float rinv = __frcp_rn(rho);
+    const float vel[3] = {q[1] * rinv, q[2] * rinv, q[3] * rinv};
+    const float kin = 0.5f * (vel[0] * vel[0] + vel[1] * vel[1] + vel[2] * vel[2]);
+    const float pp = P.gm1 * (q[4] - rho * kin - gz * q[0]);
+    const float T = (pb + pp) * rinv * P.invR;
+    float d[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) d[a][b] = (g[b][1 + a] - vel[a] * g[b][0]) * rinv;
+    const float div = d[0][0] + d[1][1] + d[2][2];
+    float dT[3];
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+        float s = g[b][4] - (vel[0] * g[b][1] + vel[1] * g[b][2] + vel[2] * g[b][3]) + kin * g[b][0] - gz * g[b][0];
+        if (b == 2) s -= rho * P.g;
+        dT[b] = heat_wall ? (b == 2 ? dTdz : 0.0f) : (P.gm1 * s - P.R * T * g[b][0]) * rinv * P.invR;
+    }
+    float sig[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b)
+            sig[a][b] = P.mu * ((a == b ? (2.0f / 3.0f) * div : 0.0f) - (d[a][b] + d[b][a]));
+    const float h = Hb + (q[4] + pp);
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+        f[b][0] = q[1 + b];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) f[b][1 + a] = q[1 + a] * vel[b] + (a == b ? pp : 0.0f) + sig[a][b];
+        f[b][4] = vel[b] * h + vel[0] * sig[0][b] + vel[1] * sig[1][b] + vel[2] * sig[2][b] - P.kappa * dT[b];
+    }
+    src = P.gravity ? -P.g * q[0] : 0.0f;
+}
+
 // MX: the mixed-precision form -- Rusanov flux from the FP64 jump of the
 // face states converted to FP32, flux average and lifting in FP32, the
 // update in FP64 (ghost states stay FP64).
 template <int N, bool MX>
 __global__ void __launch_bounds__(Cfg3<N>::threads)
 k3_corrector(double* __restrict__ u, const double* __restrict__ rvol, const double* __restrict__ trace, int cells,
-             double dt, double t, const Basis B, const Phys3 P, const Bg3 bg) {
+             double dt, double t, const Basis B, const Phys3 P, const Bg3 bg, const Phys3f Pf) {
     using C = Cfg3<N>;
     using FT = typename std::conditional<MX, float, double>::type;
     constexpr int n = C::n, n2 = C::n2, n3 = C::n3, SL = 5 * n3, TR = kTr3 * n2;
@@ -434,11 +493,47 @@ k3_corrector(double* __restrict__ u, const double* __restrict__ rvol, const doub
             for (int c = 0; c < 3; ++c)
 #pragma unroll
                 for (int v = 0; v < 5; ++v) g[c][v] = own[((2 + c) * 5 + v) * n2 + m];
-            double ff[3][5], src;
-            ns_flux3(qn, g, z, pb, rb, P, true, ff, src);
+            if constexpr (MX) {
+                // the ghost's flux and speed in FP32: with gravity the zero
+                // perturbation of rho and rhoE over the exact background at the
+                // face node (rhobar, pbar, Ebar + pbar), without it the ghost state
+                float qg[5], gf[3][5], ff[3][5], src;
+                float rbf = 0.0f, pbf = 0.0f, Hbf = 0.0f, gz = 0.0f;
+                if (P.gravity) {
+                    qg[0] = 0.0f;
+                    qg[4] = 0.0f;
+                    rbf = f64_to_f32(rb);
+                    pbf = f64_to_f32(pb);
+                    Hbf = f64_to_f32(qn[4] + pb);
+                    gz = f64_to_f32(P.g * z);
+                } else {
+                    qg[0] = f64_to_f32(qn[0]);
+                    qg[4] = f64_to_f32(qn[4]);
+                }
+                qg[1] = f64_to_f32(qn[1]);
+                qg[2] = f64_to_f32(qn[2]);
+                qg[3] = f64_to_f32(qn[3]);
 #pragma unroll
-            for (int v = 0; v < 5; ++v) fn[v] = dir == 0 ? ff[0][v] : dir == 1 ? ff[1][v] : ff[2][v];
-            sn = wave_speed3(qn, z, dir, P);
+                for (int c = 0; c < 3; ++c)
+#pragma unroll
+                    for (int v = 0; v < 5; ++v) gf[c][v] = f64_to_f32(g[c][v]);
+                ns_flux3f(qg, gf, gz, rbf, pbf, Hbf, Pf, ff, src, true, Pf.dTdz);
+#pragma unroll
+                for (int v = 0; v < 5; ++v) fn[v] = f32_to_f64(dir == 0 ? ff[0][v] : dir == 1 ? ff[1][v] : ff[2][v]);
+                const float rho = rbf + qg[0];
+                const float rinv = __frcp_rn(rho);
+                const float pp = Pf.gm1 * (qg[4] - 0.5f * (qg[1] * qg[1] + qg[2] * qg[2] + qg[3] * qg[3]) * rinv -
+                                           gz * qg[0]);
+                const float mn = dir == 0 ? qg[1] : dir == 1 ? qg[2] : qg[3];
+                sn = f32_to_f64(fabsf(mn) * rinv + sqrtf(Pf.gamma * (pbf + pp) * rinv) +
+                                2.0f * Pf.eta[dir] * Pf.lamv * rinv);
+            } else {
+                double ff[3][5], src;
+                ns_flux3(qn, g, z, pb, rb, P, true, ff, src);
+#pragma unroll
+                for (int v = 0; v < 5; ++v) fn[v] = dir == 0 ? ff[0][v] : dir == 1 ? ff[1][v] : ff[2][v];
+                sn = wave_speed3(qn, z, dir, P);
+            }
         } else if (edge && bcd == ADG_BC_ANALYTIC) {
             // the analytic field averaged over the step at the time nodes
             double xf[3];
@@ -537,64 +632,6 @@ k3_corrector(double* __restrict__ u, const double* __restrict__ rvol, const doub
 // FP64 base (the nodal background on x- and y-faces, its FP64 extrapolation
 // on z-faces) plus the FP32 perturbation, the Rusanov speed in FP64 -- so
 // the FP64 corrector runs unchanged.
-struct Phys3f {
-    float gamma, gm1, R, invR, mu, kappa, g, lamv;
-    float inv_h[3], eta[3];
-    int gravity;
-};
-
-struct Bg3m {
-    const double* rb;   // [nz][n] rhobar at nodes (FP64, for the split)
-    const double* Eb;   // [nz][n] Ebar = pbar/(gamma-1) + rhobar g z
-    const float* rbf;   // [nz][n] rhobar
-    const float* pbf;   // [nz][n] pbar
-    const float* Hbf;   // [nz][n] Ebar + pbar
-    const float* dzr;   // [nz][n] d rhobar/dz of the nodal interpolant
-    const float* dzE;   // [nz][n] d Ebar/dz
-    const double* ext;  // [nz][2: top, bottom][2: rhobar, Ebar] extrapolated to the z-faces
-    const double* zn;   // [nz][n] node heights
-    const float* zext;  // [nz][2: top, bottom][2: rhobar, pbar_eff] of the extrapolated z-face base,
-                        // pbar_eff = (gamma-1)(Ebar - rhobar g z_face) formed in FP64
-};
-
-__device__ __forceinline__ void ns_flux3f(const float q[5], const float g[3][5], float gz, float rb, float pb,
-                                          float Hb, const Phys3f& P, float f[3][5], float& src) {
-    const float rho = rb + q[0];
-    const float rinv = __frcp_rn(rho);
-    const float vel[3] = {q[1] * rinv, q[2] * rinv, q[3] * rinv};
-    const float kin = 0.5f * (vel[0] * vel[0] + vel[1] * vel[1] + vel[2] * vel[2]);
-    const float pp = P.gm1 * (q[4] - rho * kin - gz * q[0]);
-    const float T = (pb + pp) * rinv * P.invR;
-    float d[3][3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-#pragma unroll
-        for (int b = 0; b < 3; ++b) d[a][b] = (g[b][1 + a] - vel[a] * g[b][0]) * rinv;
-    const float div = d[0][0] + d[1][1] + d[2][2];
-    float dT[3];
-#pragma unroll
-    for (int b = 0; b < 3; ++b) {
-        float s = g[b][4] - (vel[0] * g[b][1] + vel[1] * g[b][2] + vel[2] * g[b][3]) + kin * g[b][0] - gz * g[b][0];
-        if (b == 2) s -= rho * P.g;
-        dT[b] = (P.gm1 * s - P.R * T * g[b][0]) * rinv * P.invR;
-    }
-    float sig[3][3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-#pragma unroll
-        for (int b = 0; b < 3; ++b)
-            sig[a][b] = P.mu * ((a == b ? (2.0f / 3.0f) * div : 0.0f) - (d[a][b] + d[b][a]));
-    const float h = Hb + (q[4] + pp);
-#pragma unroll
-    for (int b = 0; b < 3; ++b) {
-        f[b][0] = q[1 + b];
-#pragma unroll
-        for (int a = 0; a < 3; ++a) f[b][1 + a] = q[1 + a] * vel[b] + (a == b ? pp : 0.0f) + sig[a][b];
-        f[b][4] = vel[b] * h + vel[0] * sig[0][b] + vel[1] * sig[1][b] + vel[2] * sig[2][b] - P.kappa * dT[b];
-    }
-    src = P.gravity ? -P.g * q[0] : 0.0f;
-}
-
 template <int N>
 struct Cfg3m {
     static constexpr size_t smem = (size_t)Cfg3<N>::cpb * Cfg3<N>::slots * 5 * Cfg3<N>::n3 * sizeof(float);
@@ -914,7 +951,7 @@ __global__ void __launch_bounds__(256) k3_speed(const double* __restrict__ u, in
 
 template <int N>
 int launch3(bool pred, double* u, double* rvol, double* trace, int cells, double dt, double t, const Basis& B,
-            const Phys3& P, const Bg3& bg, cudaStream_t s, bool mixed) {
+            const Phys3& P, const Bg3& bg, cudaStream_t s, bool mixed, const Phys3f& Pf) {
     using C = Cfg3<N>;
     const int blocks = (cells + C::cpb - 1) / C::cpb;
     if (pred) {
@@ -922,8 +959,8 @@ int launch3(bool pred, double* u, double* rvol, double* trace, int cells, double
         if (e != cudaSuccess) return (int)e;
         k3_predictor<N><<<blocks, C::threads, C::smem, s>>>(u, rvol, trace, cells, dt, B, P, bg);
     } else {
-        if (mixed) k3_corrector<N, true><<<blocks, C::threads, 0, s>>>(u, rvol, trace, cells, dt, t, B, P, bg);
-        else k3_corrector<N, false><<<blocks, C::threads, 0, s>>>(u, rvol, trace, cells, dt, t, B, P, bg);
+        if (mixed) k3_corrector<N, true><<<blocks, C::threads, 0, s>>>(u, rvol, trace, cells, dt, t, B, P, bg, Pf);
+        else k3_corrector<N, false><<<blocks, C::threads, 0, s>>>(u, rvol, trace, cells, dt, t, B, P, bg, Pf);
     }
     return (int)cudaGetLastError();
 }
@@ -952,12 +989,12 @@ int launch3m_any(int N, const double* u, double* rvol, double* trace, int cells,
 }
 
 int launch3_any(int N, bool pred, double* u, double* rvol, double* trace, int cells, double dt, double t,
-                const Basis& B, const Phys3& P, const Bg3& bg, cudaStream_t s, bool mixed = false) {
+                const Basis& B, const Phys3& P, const Bg3& bg, cudaStream_t s, bool mixed, const Phys3f& Pf) {
     switch (N) {
-        case 1: return launch3<1>(pred, u, rvol, trace, cells, dt, t, B, P, bg, s, mixed);
-        case 2: return launch3<2>(pred, u, rvol, trace, cells, dt, t, B, P, bg, s, mixed);
-        case 3: return launch3<3>(pred, u, rvol, trace, cells, dt, t, B, P, bg, s, mixed);
-        case 4: return launch3<4>(pred, u, rvol, trace, cells, dt, t, B, P, bg, s, mixed);
+        case 1: return launch3<1>(pred, u, rvol, trace, cells, dt, t, B, P, bg, s, mixed, Pf);
+        case 2: return launch3<2>(pred, u, rvol, trace, cells, dt, t, B, P, bg, s, mixed, Pf);
+        case 3: return launch3<3>(pred, u, rvol, trace, cells, dt, t, B, P, bg, s, mixed, Pf);
+        case 4: return launch3<4>(pred, u, rvol, trace, cells, dt, t, B, P, bg, s, mixed, Pf);
         default: return (int)cudaErrorInvalidValue;
     }
 }
@@ -1058,6 +1095,7 @@ int build_mixed3(adg_mesh3* m) {
     f.kappa = (float)P.kappa;
     f.g = (float)P.g;
     f.lamv = (float)P.lamv;
+    f.dTdz = (float)P.dTdz;
     for (int c = 0; c < 3; ++c) {
         f.inv_h[c] = (float)P.inv_h[c];
         f.eta[c] = (float)P.eta[c];
@@ -1160,6 +1198,7 @@ extern "C" int adg3_create(const adg_mesh_desc* d, int nz, double z0, double Lz,
     }
     adg::Phys3& P = m->P;
     std::memset(&P, 0, sizeof(P));
+    std::memset(&m->Pf, 0, sizeof(m->Pf));
     P.gamma = d->gamma;
     P.gm1 = d->gamma - 1.0;
     P.R = d->R;
@@ -1292,10 +1331,11 @@ extern "C" int adg3_step(adg_mesh3* m, double dt, int nsteps, void* stream) {
         int e = m->d.precision == ADG_PREC_MIXED
                     ? adg::launch3m_any(m->N, m->u, m->rvol, m->trace, m->cells, (float)dt, m->Bf, m->Pf, m->P,
                                         bg3m(m), s)
-                    : adg::launch3_any(m->N, true, m->u, m->rvol, m->trace, m->cells, dt, m->t, m->B, m->P, bg, s);
+                    : adg::launch3_any(m->N, true, m->u, m->rvol, m->trace, m->cells, dt, m->t, m->B, m->P, bg, s,
+                                       false, m->Pf);
         if (e) return cuda_fail((cudaError_t)e, "adg3_step predictor");
         e = adg::launch3_any(m->N, false, m->u, m->rvol, m->trace, m->cells, dt, m->t, m->B, m->P, bg, s,
-                             m->d.precision == ADG_PREC_MIXED);
+                             m->d.precision == ADG_PREC_MIXED, m->Pf);
         if (e) return cuda_fail((cudaError_t)e, "adg3_step corrector");
         m->t += dt;
     }
