@@ -422,37 +422,47 @@ def run_amr(args, dev):
     import torch
     from paper_1905_05524_gb300 import _lib as L
     from paper_1905_05524_gb300.solver import Mesh, atmosphere_config
-    cfg = atmosphere_config(degree=DEGREE, nx=27, ny=27, mu=0.001, device=dev.index)
-    cfg.max_levels = 2
-    m = Mesh(cfg)
-    for _ in range(2):   # initial mesh: init -> TV -> refine, twice
+    def amr_run(prec):
+        cfg = atmosphere_config(degree=DEGREE, nx=27, ny=27, mu=0.001, device=dev.index, precision=prec)
+        cfg.max_levels = 2
+        m = Mesh(cfg)
+        for _ in range(2):   # initial mesh: init -> TV -> refine, twice
+            m.init_scenario(L.ADG_SCEN_TWO_BUBBLES)
+            _, fl, _ = m.tv_indicator(L.ADG_TV_THETA, 2.5, -0.5)
+            m.adapt(torch.where(fl > 0, 1, 0).to(torch.int8))
         m.init_scenario(L.ADG_SCEN_TWO_BUBBLES)
-        _, fl, _ = m.tv_indicator(L.ADG_TV_THETA, 2.5, -0.5)
-        m.adapt(torch.where(fl > 0, 1, 0).to(torch.int8))
-    m.init_scenario(L.ADG_SCEN_TWO_BUBBLES)
-    dt = m.stable_dt(CFL)
-    steps, every = args.amr_steps, 10
-    dof_updates = 0
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    t_steps = 0.0
+        dt = m.stable_dt(CFL)
+        steps, every = args.amr_steps, 10
+        dof_updates = 0
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        t_steps = 0.0
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        leaf_hist = []
+        for s0 in range(0, steps, every):
+            k = min(every, steps - s0)
+            ev0.record()
+            m.step(dt, k)
+            ev1.record()
+            ev1.synchronize()
+            t_steps += ev0.elapsed_time(ev1) * 1e-3
+            dof_updates += m.leaves * (DEGREE + 1) ** 2 * 4 * k
+            leaf_hist.append(m.leaves)
+            _, fl, _ = m.tv_indicator(L.ADG_TV_THETA, 2.5, -0.5)
+            m.adapt(fl)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        res = dict(dt=dt, steps=steps, every=every, dof_updates=dof_updates, t_steps=t_steps, wall=wall,
+                   leaves=m.leaf_info(), ua=m.get_state().cpu().numpy(), leaf_hist=leaf_hist)
+        m.close()
+        return res
+
+    r64 = amr_run(L.ADG_PREC_FP64)
+    rmx = amr_run(L.ADG_PREC_MIXED)
+    dt, steps, every = r64["dt"], r64["steps"], r64["every"]
+    dof_updates, t_steps, wall = r64["dof_updates"], r64["t_steps"], r64["wall"]
+    leaves, ua, leaf_hist = r64["leaves"], r64["ua"], r64["leaf_hist"]
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    leaf_hist = []
-    for s0 in range(0, steps, every):
-        k = min(every, steps - s0)
-        ev0.record()
-        m.step(dt, k)
-        ev1.record()
-        ev1.synchronize()
-        t_steps += ev0.elapsed_time(ev1) * 1e-3
-        dof_updates += m.leaves * (DEGREE + 1) ** 2 * 4 * k
-        leaf_hist.append(m.leaves)
-        _, fl, _ = m.tv_indicator(L.ADG_TV_THETA, 2.5, -0.5)
-        m.adapt(fl)
-    torch.cuda.synchronize()
-    wall = time.perf_counter() - t0
-    leaves = m.leaf_info()
-    ua = m.get_state().cpu().numpy()
     # uniform reference at the finest level present (same dt, same smallest cell)
     lmax = max(c[0] for c in leaves)
     side = 27 * 3 ** lmax
@@ -476,12 +486,21 @@ def run_amr(args, dev):
     l2d = float(np.sqrt((W * (tha - thu) ** 2).sum()))
     l2t = float(np.sqrt((W * (thu + cfu.theta0) ** 2).sum()))
     levels = [c[0] for c in leaves]
+    # the mixed run against the FP64 adaptive run, both prolonged to the finest level
+    thm = theta_prime_np(prolong_to_level(rmx["ua"], rmx["leaves"], DEGREE, lmax, 27, 27).reshape(
+        -1, 4, DEGREE + 1, DEGREE + 1), cfu)
+    mixed = {"value": rmx["dof_updates"] / rmx["t_steps"], "value_including_regrid": rmx["dof_updates"] / rmx["wall"],
+             "unit": UNIT, "leaves_final": len(rmx["leaves"]), "same_leaves_as_fp64": rmx["leaves"] == leaves,
+             "theta_prime_rel_l2_vs_fp64_amr": float(np.sqrt((W * (thm - tha) ** 2).sum()) /
+                                                       np.sqrt((W * tha ** 2).sum())),
+             "form": "FP32 predictor on perturbations, FP64 corrector with hanging faces, FP64 TV and adaptation"}
     return {
         "metric": METRIC + " (config 3: two-bubble AMR)", "value": dof_updates / t_steps, "unit": UNIT,
         "dtype": "f64", "steps": steps, "regrid_every": every,
         "value_including_regrid": dof_updates / wall,
         "leaves_final": len(leaves), "leaves_per_level": [levels.count(l) for l in range(3)],
         "leaves_mean": float(np.mean(leaf_hist)),
+        "mixed": mixed,
         "uniform_reference": {"cells": side * side, "value": side * side * n * n * 4 * steps / t_uni, "unit": UNIT,
                               "seconds": t_uni},
         "uniform_equivalent_value": side * side * n * n * 4 * steps / t_steps,

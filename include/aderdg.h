@@ -104,7 +104,9 @@ typedef struct adg_mesh_desc {
     int device;            /* CUDA device ordinal                                */
     int max_levels;        /* 0: uniform mesh; 1..4: adaptive 3:1 tree with up to
                               this many refinement levels above the nx x ny base
-                              (FP64 only; see adg_adapt)                          */
+                              (see adg_adapt); with ADG_PREC_MIXED the predictor
+                              runs in FP32 on perturbations and the corrector,
+                              hanging faces and TV in FP64                        */
     double lid_u;          /* ADG_BC_NOSLIP: x-velocity of the north wall (the
                               lid of the driven cavity, Sec. 4.1); others rest    */
     int bc_field;          /* ADG_BC_ANALYTIC: the imposed field, ADG_FIELD_*     */

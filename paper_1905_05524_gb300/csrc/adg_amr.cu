@@ -28,9 +28,11 @@
 #include <unordered_map>
 #include <vector>
 
+#include "adg_convert.cuh"
 #include "adg_fp64_body.cuh"
 #include "adg_internal.h"
 #include "adg_mesh.h"
+#include "adg_mixed_point.cuh"
 #include "adg_physics.cuh"
 #include "adg_tv_cell.cuh"
 
@@ -160,6 +162,62 @@ static int upload_tables(adg_mesh* m) {
     ADG_CK(cudaMemcpy(m->geo, geo.data(), geo.size() * 8, cudaMemcpyHostToDevice), "amr tables");
     ADG_CK(cudaMemcpy(m->nbr, nbr.data(), nbr.size() * 4, cudaMemcpyHostToDevice), "amr tables");
     ADG_CK(cudaMemcpy(m->bgl, bgl.data(), bgl.size() * 8, cudaMemcpyHostToDevice), "amr tables");
+    if (d->precision == ADG_PREC_MIXED) {
+        // the mixed predictor's per-leaf background: FP64 (rhobar, Ebar) per
+        // node row and extrapolated to the N, S faces; FP32 (pbar, d rhobar/dz,
+        // d Ebar/dz) per row and (rhobar, (gamma-1)(Ebar - rhobar g z)) of the
+        // extrapolated face base
+        std::vector<double> h64((size_t)L * n * 2 + (size_t)L * 4, 0.0);
+        std::vector<float> h32((size_t)L * n * 3 + (size_t)L * 4, 0.0f);
+        const double g = d->gravity ? d->g : 0.0, gm1 = d->gamma - 1.0;
+        std::vector<double> rb(n), Eb(n), pb(n);
+        for (int k = 0; k < L; ++k) {
+            const double y0 = geo[k * 4 + 1], hy = geo[k * 4 + 3];
+            for (int j = 0; j < n; ++j) {
+                const double z = y0 + m->B.xi[j] * hy;
+                bgp(z, pb[j], rb[j]);
+                Eb[j] = pb[j] / gm1 + rb[j] * g * z;
+            }
+            for (int j = 0; j < n; ++j) {
+                double dr = 0.0, dE = 0.0;
+                for (int p = 0; p < n; ++p) {
+                    dr += m->B.D[j][p] * rb[p];
+                    dE += m->B.D[j][p] * Eb[p];
+                }
+                const size_t r = (size_t)k * n + j;
+                h64[r * 2] = rb[j];
+                h64[r * 2 + 1] = Eb[j];
+                h32[r * 3] = (float)pb[j];
+                h32[r * 3 + 1] = (float)(dr / hy);
+                h32[r * 3 + 2] = (float)(dE / hy);
+            }
+            for (int side = 0; side < 2; ++side) {  // 0: north (phi(1)), 1: south (phi(0))
+                const double* phi = side == 0 ? m->B.phi1 : m->B.phi0;
+                double er = 0.0, eE = 0.0;
+                for (int p = 0; p < n; ++p) {
+                    er += phi[p] * rb[p];
+                    eE += phi[p] * Eb[p];
+                }
+                const double zf = y0 + (side == 0 ? hy : 0.0);
+                const size_t o64 = (size_t)L * n * 2 + ((size_t)k * 2 + side) * 2;
+                const size_t o32 = (size_t)L * n * 3 + ((size_t)k * 2 + side) * 2;
+                h64[o64] = er;
+                h64[o64 + 1] = eE;
+                h32[o32] = (float)er;
+                h32[o32 + 1] = (float)(gm1 * (eE - er * g * zf));
+            }
+        }
+        cudaFree(m->mbl64);
+        cudaFree(m->mblf);
+        m->mbl64 = nullptr;
+        m->mblf = nullptr;
+        if (cudaMalloc(&m->mbl64, h64.size() * 8) != cudaSuccess || cudaMalloc(&m->mblf, h32.size() * 4) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(ADG_ENOMEM, "adaptive mesh: mixed tables");
+        }
+        ADG_CK(cudaMemcpy(m->mbl64, h64.data(), h64.size() * 8, cudaMemcpyHostToDevice), "amr mixed tables");
+        ADG_CK(cudaMemcpy(m->mblf, h32.data(), h32.size() * 4, cudaMemcpyHostToDevice), "amr mixed tables");
+    }
     return ADG_OK;
 }
 
@@ -222,6 +280,10 @@ void amr_free(adg_mesh* m) {
     cudaFree(m->geo);
     cudaFree(m->nbr);
     cudaFree(m->bgl);
+    cudaFree(m->mbl64);
+    cudaFree(m->mblf);
+    m->mbl64 = nullptr;
+    m->mblf = nullptr;
 }
 
 // per-leaf constants: P with the leaf's cell sizes
@@ -252,6 +314,232 @@ k_predictor_amr(const double* __restrict__ u, double* __restrict__ rvol, double*
     const Phys P = leaf_phys(P0, geo, cell, N);
     predictor_fp64_body<N, CPB>(u, rvol, trace, cell, active, dt, B, P, geo[cell * 4], geo[cell * 4 + 1],
                                 bgl[((size_t)cell * n + j) * 2], bgl[((size_t)cell * n + j) * 2 + 1], sm);
+}
+
+// Mixed-precision predictor of the adaptive mesh: the Picard iteration of
+// k_predictor_amr in FP32 on perturbation variables (the split against the
+// leaf's nodal background in FP64 at load; gradients plus the FP64-formed
+// derivative of the interpolated background), writing the FP64 formats of
+// the FP64 predictor -- the volume residual converted, the traces rebuilt as
+// an FP64 base plus the FP32 perturbation (x-faces: the nodal background of
+// the node's row, which does not vary along x; y-faces: the FP64
+// extrapolation of the leaf's nodal background) with the Rusanov speed in
+// FP32 -- so the FP64 corrector with its hanging faces runs unchanged.
+// Per-leaf tables: mb64 [leaves][n][2] (rhobar, Ebar) then [leaves][2 N, S][2]
+// extrapolated (rhobar, Ebar); mbf [leaves][n][3] (pbar, d rhobar/dz,
+// d Ebar/dz) then [leaves][2 N, S][2] (extrapolated rhobar, (gamma-1)(Ebar -
+// rhobar g z_face)).
+template <int N, int CPB>
+__global__ void __launch_bounds__(CPB*(N + 1) * (N + 1))
+k_predictor_amr_mixed(const double* __restrict__ u, double* __restrict__ rvol, double* __restrict__ trace, int cells,
+                      float dt, const BasisF B, const PhysF P, const double* __restrict__ geo,
+                      const double* __restrict__ mb64, const float* __restrict__ mbf) {
+    constexpr int n = N + 1, n2 = n * n, SL = 4 * n2;
+    extern __shared__ float smf[];
+    const int cl = threadIdx.x / n2;
+    const int node = threadIdx.x - cl * n2;
+    const int j = node / n, i = node - j * n;
+    const int cell_raw = blockIdx.x * CPB + cl;
+    const bool active = cell_raw < cells;
+    const int cell = active ? cell_raw : cells - 1;
+    float* Q = smf + (size_t)cl * 3 * n * SL;  // [k][v][j][i]
+    float* Fs = Q + n * SL;
+    float* Gs = Fs + n * SL;
+    const double hx = geo[cell * 4 + 2], hy = geo[cell * 4 + 3], yorg = geo[cell * 4 + 1];
+    const float inv_hx = (float)(1.0 / hx), inv_hy = (float)(1.0 / hy);
+    const float z = (float)(yorg + (double)B.xi[j] * hy);
+    const size_t rowj = (size_t)cell * n + j;
+    const double rb64 = mb64[rowj * 2], Eb64 = mb64[rowj * 2 + 1];
+    const float rb = f64_to_f32(rb64), Eb = f64_to_f32(Eb64);
+    const float pb = mbf[rowj * 3], dzr = mbf[rowj * 3 + 1], dzE = mbf[rowj * 3 + 2];
+
+    float up[4];
+    {
+        const double* uc = u + (size_t)cell * SL;
+        up[0] = f64_to_f32(__dsub_rn(uc[node], rb64));
+        up[1] = f64_to_f32(uc[n2 + node]);
+        up[2] = f64_to_f32(uc[2 * n2 + node]);
+        up[3] = f64_to_f32(__dsub_rn(uc[3 * n2 + node], Eb64));
+    }
+#pragma unroll
+    for (int v = 0; v < 4; ++v) Q[v * n2 + node] = up[v];
+    __syncthreads();
+
+    auto eval = [&](const float* Qk, float q[4], float gx[4], float gy[4], FluxF& f) {
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const float* Qv = Qk + v * n2;
+            q[v] = Qv[node];
+            float sx = 0.f, sy = 0.f;
+#pragma unroll
+            for (int p = 0; p < n; ++p) {
+                sx = fmaf(B.D[i][p], Qv[j * n + p], sx);
+                sy = fmaf(B.D[j][p], Qv[p * n + i], sy);
+            }
+            gx[v] = sx * inv_hx;
+            gy[v] = sy * inv_hy;
+        }
+        gy[0] += dzr;
+        gy[3] += dzE;
+        ns_flux_pert(q, gx, gy, z, rb, Eb, pb, P, f);
+    };
+    auto divergence = [&](int k, int v) {
+        const float* Fv = Fs + k * SL + v * n2;
+        const float* Gv = Gs + k * SL + v * n2;
+        float sx = 0.f, sy = 0.f;
+#pragma unroll
+        for (int p = 0; p < n; ++p) {
+            sx = fmaf(B.D[i][p], Fv[j * n + p], sx);
+            sy = fmaf(B.D[j][p], Gv[p * n + i], sy);
+        }
+        return -(sx * inv_hx + sy * inv_hy);
+    };
+
+    {  // sweep 1: the iterate is constant in time
+        float q[4], gx[4], gy[4];
+        FluxF f;
+        eval(Q, q, gx, gy, f);
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            Fs[v * n2 + node] = f.F[v];
+            Gs[v * n2 + node] = f.G[v];
+        }
+        __syncthreads();
+        float R0[4];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) R0[v] = f.S[v] + divergence(0, v);
+#pragma unroll
+        for (int l = 0; l < n; ++l)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) Q[l * SL + v * n2 + node] = fmaf(dt, B.Kw1[l] * R0[v], up[v]);
+        __syncthreads();
+    }
+#pragma unroll 1
+    for (int r = 1; r < n; ++r) {
+        float R[n][4];
+#pragma unroll
+        for (int k = 0; k < n; ++k) {
+            float q[4], gx[4], gy[4];
+            FluxF f;
+            eval(Q + k * SL, q, gx, gy, f);
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                Fs[k * SL + v * n2 + node] = f.F[v];
+                Gs[k * SL + v * n2 + node] = f.G[v];
+                R[k][v] = f.S[v];
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < n; ++k)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) R[k][v] += divergence(k, v);
+#pragma unroll
+        for (int l = 0; l < n; ++l)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                float acc = 0.f;
+#pragma unroll
+                for (int k = 0; k < n; ++k) acc = fmaf(B.Kw[l][k], R[k][v], acc);
+                Q[l * SL + v * n2 + node] = fmaf(dt, acc, up[v]);
+            }
+        __syncthreads();
+    }
+
+    float qb[4], Fb[4], Gb[4], Sb[4], qxb[4], qyb[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) qb[v] = Fb[v] = Gb[v] = Sb[v] = qxb[v] = qyb[v] = 0.f;
+#pragma unroll
+    for (int k = 0; k < n; ++k) {
+        float q[4], gx[4], gy[4];
+        FluxF f;
+        eval(Q + k * SL, q, gx, gy, f);
+        const float wk = B.w[k];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            qb[v] = fmaf(wk, q[v], qb[v]);
+            Fb[v] = fmaf(wk, f.F[v], Fb[v]);
+            Gb[v] = fmaf(wk, f.G[v], Gb[v]);
+            Sb[v] = fmaf(wk, f.S[v], Sb[v]);
+            qxb[v] = fmaf(wk, gx[v], qxb[v]);
+            qyb[v] = fmaf(wk, gy[v], qyb[v]);  // full y-gradient (background included)
+        }
+    }
+    __syncthreads();
+    float* A = Q;  // slots 0..4: qbar', Fbar, Gbar, qxbar, qybar
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+        A[0 * SL + v * n2 + node] = qb[v];
+        A[1 * SL + v * n2 + node] = Fb[v];
+        A[2 * SL + v * n2 + node] = Gb[v];
+        A[3 * SL + v * n2 + node] = qxb[v];
+        A[4 * SL + v * n2 + node] = qyb[v];
+    }
+    __syncthreads();
+    if (active) {
+        double* rc = rvol + (size_t)cell * SL;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            float sx = 0.f, sy = 0.f;
+#pragma unroll
+            for (int p = 0; p < n; ++p) {
+                sx = fmaf(B.Vx[p][i], A[1 * SL + v * n2 + j * n + p], sx);
+                sy = fmaf(B.Vx[p][j], A[2 * SL + v * n2 + p * n + i], sy);
+            }
+            rc[v * n2 + node] = f32_to_f64(sx * inv_hx + sy * inv_hy + Sb[v]);
+        }
+    }
+    const float eta_x = (2.f * N + 1.f) / ((float)hx * 1.2533141f), eta_y = (2.f * N + 1.f) / ((float)hy * 1.2533141f);
+    for (int idx = node; idx < 4 * n; idx += n2) {
+        const int f = idx / n, m = idx - f * n;
+        const bool xface = f < 2;
+        const float* phi = (f == 0 || f == 2) ? B.phi1 : B.phi0;
+        float rec[kTraceComps];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int slot = c == 0 ? 0 : c == 1 ? (xface ? 1 : 2) : (c == 2 ? 3 : 4);
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                const float* S = A + slot * SL + v * n2;
+                float s = 0.f;
+#pragma unroll
+                for (int p = 0; p < n; ++p) s = fmaf(phi[p], xface ? S[m * n + p] : S[p * n + m], s);
+                rec[c * 4 + v] = s;
+            }
+        }
+        // FP64 base and FP32 speed base of the face node
+        double brho, bE;
+        float rbf, pbf, zf;
+        if (xface) {
+            const size_t rm = (size_t)cell * n + m;
+            brho = mb64[rm * 2];
+            bE = mb64[rm * 2 + 1];
+            rbf = f64_to_f32(brho);
+            pbf = mbf[rm * 3];
+            zf = (float)(yorg + (double)B.xi[m] * hy);
+        } else {
+            const size_t side = (size_t)cell * 2 + (f == 2 ? 0 : 1);
+            const size_t o64 = (size_t)cells * n * 2 + side * 2, o32 = (size_t)cells * n * 3 + side * 2;
+            brho = mb64[o64];
+            bE = mb64[o64 + 1];
+            rbf = mbf[o32];
+            pbf = mbf[o32 + 1];
+            zf = (float)(yorg + (f == 2 ? hy : 0.0));
+        }
+        const float rho = rbf + rec[0];
+        const float rinv = __frcp_rn(rho);
+        const float pp = P.gm1 * (rec[3] - 0.5f * (rec[1] * rec[1] + rec[2] * rec[2]) * rinv - P.g * zf * rec[0]);
+        const float sp = fabsf((xface ? rec[1] : rec[2]) * rinv) + sqrtf(P.gamma * (pbf + pp) * rinv) +
+                         2.f * (xface ? eta_x : eta_y) * P.lamv * rinv;
+        if (active) {
+            double* tr = trace + ((size_t)cell * 4 + f) * kTraceComps * n;
+#pragma unroll
+            for (int c = 0; c < 16; ++c) tr[c * n + m] = f32_to_f64(rec[c]);
+            tr[0 * n + m] = brho + f32_to_f64(rec[0]);
+            tr[3 * n + m] = bE + f32_to_f64(rec[3]);
+            tr[16 * n + m] = f32_to_f64(sp);
+        }
+    }
 }
 
 // face data (q-bar and normal flux) of record `rec` of a coarse face evaluated
@@ -560,6 +848,15 @@ struct AmrCfg {
 template <int N>
 static int pred_n(adg_mesh* m, double dt, cudaStream_t s) {
     using C = AmrCfg<N>;
+    if (m->d.precision == ADG_PREC_MIXED) {
+        auto km = k_predictor_amr_mixed<N, C::cpb>;
+        const size_t smem = (size_t)C::cpb * 3 * C::n * 4 * C::n * C::n * sizeof(float);
+        ADG_CK(cudaFuncSetAttribute(km, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem), "amr pred mixed");
+        km<<<(m->cells + C::cpb - 1) / C::cpb, C::threads, smem, s>>>(m->u, m->rvol, m->trace, m->cells, (float)dt,
+                                                                       m->Bf, m->Pf, m->geo, m->mbl64, m->mblf);
+        ADG_CK(cudaGetLastError(), "amr mixed predictor launch");
+        return ADG_OK;
+    }
     auto kern = k_predictor_amr<N, C::cpb>;
     ADG_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem_pred), "amr pred");
     kern<<<(m->cells + C::cpb - 1) / C::cpb, C::threads, C::smem_pred, s>>>(m->u, m->rvol, m->trace, m->cells, dt,

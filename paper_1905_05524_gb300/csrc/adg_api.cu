@@ -344,8 +344,6 @@ int adg_create_mesh(const adg_mesh_desc* d, adg_mesh** out) {
     if (d->gravity && !(d->theta0 > 0.0 && d->p0 > 0.0))
         return fail(ADG_EINVAL, "create_mesh: gravity needs theta0 > 0 and p0 > 0");
     if (d->max_levels < 0 || d->max_levels > 4) return fail(ADG_EINVAL, "create_mesh: max_levels must be in [0, 4]");
-    if (d->max_levels > 0 && d->precision != ADG_PREC_FP64)
-        return fail(ADG_EUNSUPPORTED, "create_mesh: adaptive meshes are built for ADG_PREC_FP64");
     int ndev = 0;
     ADG_CK(cudaGetDeviceCount(&ndev), "cudaGetDeviceCount");
     if (d->device < 0 || d->device >= ndev) return fail(ADG_EINVAL, "create_mesh: bad device ordinal");
@@ -1013,6 +1011,8 @@ extern "C" int adg_batch_create(adg_mesh* const* meshes, int k, adg_batch** out)
             return fail(ADG_EINVAL, "batch_create: meshes must share degree and device");
         if (meshes[a]->d.precision != ADG_PREC_MIXED)
             return fail(ADG_EUNSUPPORTED, "batch_create: batched launch is built for ADG_PREC_MIXED meshes");
+        if (meshes[a]->amr)
+            return fail(ADG_EUNSUPPORTED, "batch_create: batched launch is built for uniform meshes");
     }
     adg_batch* b = new adg_batch();
     b->device = meshes[0]->d.device;

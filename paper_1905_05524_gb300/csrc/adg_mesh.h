@@ -39,6 +39,8 @@ struct adg_mesh {
     double* geo = nullptr;        // [leaves][4]: x0, y0, hx, hy of each leaf
     int* nbr = nullptr;           // [leaves][4 faces][5]: type, id0, id1, id2, sub-face
     double* bgl = nullptr;        // [leaves][n][2] node background, then [leaves][2][2] N/S faces
+    double* mbl64 = nullptr;      // mixed precision: per-leaf FP64 background (adg_amr.cu upload_tables)
+    float* mblf = nullptr;        // mixed precision: per-leaf FP32 background
     double hmin = 0.0;            // smallest leaf size (dt rule)
     double* halo = nullptr;       // strip decomposition: [2][nx][17][n] south, north halo traces
 };

@@ -127,3 +127,107 @@ def test_config3_initial_mesh_and_tv_match_oracle():
     assert max(levels) >= 1 and len(levels) < 243 * 243
     print(f"config3 initial mesh: {len(levels)} leaves "
           f"({levels.count(0)}/{levels.count(1)}/{levels.count(2)} per level)")
+
+
+# ---------------------------------------------------------------- mixed precision
+THETA_TOL = 1e-6  # the mixed path's stated bound on theta' (relative L2)
+
+
+def _theta_err(o, a, b):
+    X, Y = o.node_coords()
+    ta = ph.theta(a.unbind(1), Y, o.P) - o.P.theta0
+    tb = ph.theta(b.unbind(1), Y, o.P) - o.P.theta0
+    return (torch.linalg.vector_norm(ta - tb) / torch.linalg.vector_norm(tb)).item()
+
+
+@pytest.mark.parametrize("degree", [1, 2, 3, 5, 7])
+def test_mixed_bubble_walls_hanging_faces_matches_oracle(degree):
+    """Mixed precision (FP32 predictor on perturbations, FP64 corrector) on
+    the refined-patch bubble mesh with hanging faces and gravity: 6 steps
+    against the FP64 oracle, theta' within THETA_TOL, total rho within
+    1e-9."""
+    cfg = atmosphere_config(degree=degree, nx=6, ny=6, precision=L.ADG_PREC_MIXED)
+    cfg.max_levels = 1
+    m, o = _pair(cfg, "wall")
+    X, Y = o.node_coords()
+    u = torch.stack(ph.bubble_state(X, Y, ph.cosine_bubble(X, Y), o.P), 1)
+    m.set_state(u.cuda().contiguous())
+    fl = torch.zeros(36, dtype=torch.int8)
+    fl[[13, 14, 15, 20, 21, 28]] = 1
+    u = o.adapt(u, fl)
+    m.adapt(fl.cuda())
+    assert m.leaf_info() == [tuple(c) for c in o.leaves]
+    dt = m.stable_dt(0.25)
+    for _ in range(6):
+        u = o.step(u, dt)
+    m.step(dt, 6)
+    a = m.get_state().cpu()
+    err = _theta_err(o, a, u)
+    assert err <= THETA_TOL, (degree, err)
+    assert (torch.linalg.vector_norm(a[:, 0] - u[:, 0]) / torch.linalg.vector_norm(u[:, 0])).item() <= 1e-9
+
+
+def test_mixed_adapt_step_periodic_matches_oracle():
+    """Periodic tree without gravity (the FP32 predictor carries the whole
+    state), three adaptations then 3 steps at the stable dt (CFL 0.25 on the
+    finest leaves; the FP64 test's fixed dt = 0.003 is ~16x above it there,
+    and its unstable modes amplify FP32 rounding from step to step):
+    FP32-level agreement (<= 1e-6 per variable) and conservation to 1e-8:
+    the face fluxes are FP64 and shared by both sides, but the volume
+    residual's cell integral, zero in exact arithmetic, carries the FP32
+    rounding of its terms (about 1e-9 relative over the 3 steps)."""
+    cfg = MeshConfig(degree=3, nx=6, ny=6, Lx=6.0, Ly=6.0, mu=0.05, max_levels=2, precision=L.ADG_PREC_MIXED)
+    m, o = _pair(cfg, "periodic")
+    u = o.interpolate_field(lambda X, Y: _wave(X, Y, o.P))
+    m.set_state(u.cuda().contiguous())
+    for seed, frac in ((1, 0.3), (2, 0.2), (3, 0.2)):
+        fl = _flags(len(o.leaves), seed, frac)
+        u = o.adapt(u, fl)
+        m.adapt(fl.cuda())
+        assert m.leaf_info() == [tuple(c) for c in o.leaves]
+    I0 = o.integral(u)
+    dt = m.stable_dt(0.25)
+    for _ in range(3):
+        u = o.step(u, dt)
+    m.step(dt, 3)
+    a = m.get_state().cpu()
+    _close(a, u, 1e-6)
+    Ia = o.integral(a)
+    assert ((Ia - I0).abs() <= 1e-8 * I0.abs().clamp(min=1.0)).all(), Ia - I0
+
+
+def test_mixed_config3_run_tracks_fp64():
+    """The config-3 procedure (two bubbles, 27x27 base, two levels, initial
+    mesh by init -> TV -> refine twice) with an FP64 and a mixed mesh in
+    lockstep -- both adapted with the FP64 mesh's flags -- then 10 steps, a
+    regrid, 10 steps: theta' of the mixed run within THETA_TOL of the FP64
+    run on the same leaves."""
+    ms = []
+    for prec in (L.ADG_PREC_FP64, L.ADG_PREC_MIXED):
+        cfg = atmosphere_config(degree=5, nx=27, ny=27, mu=0.001, precision=prec)
+        cfg.max_levels = 2
+        ms.append(Mesh(cfg))
+    for _ in range(2):
+        for m in ms:
+            m.init_scenario(L.ADG_SCEN_TWO_BUBBLES)
+        _, fl, _ = ms[0].tv_indicator(L.ADG_TV_THETA, 2.5, -0.5)
+        fl = torch.where(fl > 0, 1, 0).to(torch.int8)
+        for m in ms:
+            m.adapt(fl)
+    for m in ms:
+        m.init_scenario(L.ADG_SCEN_TWO_BUBBLES)
+    dt = ms[0].stable_dt(0.25)
+    for m in ms:
+        m.step(dt, 10)
+    _, fl, _ = ms[0].tv_indicator(L.ADG_TV_THETA, 2.5, -0.5)
+    for m in ms:
+        m.adapt(fl)
+        m.step(dt, 10)
+    assert ms[0].leaf_info() == ms[1].leaf_info()
+    assert len({c[0] for c in ms[0].leaf_info()}) >= 2
+    P = ph.atmosphere_params(5, mu=0.001)
+    o = AmrSolver(27, 27, P, 1000.0, 1000.0, bc="wall", max_level=2)
+    o.leaves = [tuple(c) for c in ms[0].leaf_info()]
+    o._index()
+    err = _theta_err(o, ms[1].get_state().cpu(), ms[0].get_state().cpu())
+    assert err <= THETA_TOL, err
