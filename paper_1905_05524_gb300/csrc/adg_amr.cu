@@ -148,16 +148,15 @@ static int upload_tables(adg_mesh* m) {
                 return fail(ADG_EINVAL, "adaptive mesh: level difference above one across a face");
     }
     m->hmin = hmin;
-    cudaFree(m->geo);
-    cudaFree(m->nbr);
-    cudaFree(m->bgl);
-    m->geo = nullptr;
-    m->nbr = nullptr;
-    m->bgl = nullptr;
-    if (cudaMalloc(&m->geo, geo.size() * 8) != cudaSuccess || cudaMalloc(&m->nbr, nbr.size() * 4) != cudaSuccess ||
-        cudaMalloc(&m->bgl, bgl.size() * 8) != cudaSuccess) {
-        cudaGetLastError();
-        return fail(ADG_ENOMEM, "adaptive mesh: tables");
+    // the tables live in buffers sized for leaf_cap leaves (grow-only, see
+    // ensure_capacity); the layouts are those of the current L leaves
+    const size_t C = (size_t)m->leaf_cap;
+    if (!m->geo) {
+        if (cudaMalloc(&m->geo, C * 4 * 8) != cudaSuccess || cudaMalloc(&m->nbr, C * 4 * kNbrInts * 4) != cudaSuccess ||
+            cudaMalloc(&m->bgl, (C * n * 2 + C * 4) * 8) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(ADG_ENOMEM, "adaptive mesh: tables");
+        }
     }
     ADG_CK(cudaMemcpy(m->geo, geo.data(), geo.size() * 8, cudaMemcpyHostToDevice), "amr tables");
     ADG_CK(cudaMemcpy(m->nbr, nbr.data(), nbr.size() * 4, cudaMemcpyHostToDevice), "amr tables");
@@ -207,13 +206,12 @@ static int upload_tables(adg_mesh* m) {
                 h32[o32 + 1] = (float)(gm1 * (eE - er * g * zf));
             }
         }
-        cudaFree(m->mbl64);
-        cudaFree(m->mblf);
-        m->mbl64 = nullptr;
-        m->mblf = nullptr;
-        if (cudaMalloc(&m->mbl64, h64.size() * 8) != cudaSuccess || cudaMalloc(&m->mblf, h32.size() * 4) != cudaSuccess) {
-            cudaGetLastError();
-            return fail(ADG_ENOMEM, "adaptive mesh: mixed tables");
+        if (!m->mbl64) {
+            if (cudaMalloc(&m->mbl64, (C * n * 2 + C * 4) * 8) != cudaSuccess ||
+                cudaMalloc(&m->mblf, (C * n * 3 + C * 4) * 4) != cudaSuccess) {
+                cudaGetLastError();
+                return fail(ADG_ENOMEM, "adaptive mesh: mixed tables");
+            }
         }
         ADG_CK(cudaMemcpy(m->mbl64, h64.data(), h64.size() * 8, cudaMemcpyHostToDevice), "amr mixed tables");
         ADG_CK(cudaMemcpy(m->mblf, h32.data(), h32.size() * 4, cudaMemcpyHostToDevice), "amr mixed tables");
@@ -221,29 +219,44 @@ static int upload_tables(adg_mesh* m) {
     return ADG_OK;
 }
 
-// (Re)allocate the per-leaf buffers for the current leaf count.
-static int size_buffers(adg_mesh* m, double* new_u) {
-    const int L = (int)tree_of(m)->leaves.size(), n = m->n;
-    const size_t cnt = (size_t)L * n * n * 4, tr = (size_t)L * 4 * kTraceComps * n;
+// Grow the per-leaf buffers and tables to hold at least L leaves (with a
+// quarter of headroom); they are never shrunk, so the adaptations of a run
+// reallocate only while the leaf count reaches new highs (cudaFree
+// synchronises the device).  The state m->u keeps its contents; every other
+// per-leaf buffer is rewritten before it is read.  Sets *grew.
+static int ensure_capacity(adg_mesh* m, int L, bool* grew) {
+    *grew = false;
+    if (L <= m->leaf_cap) return ADG_OK;
+    const int cap = L + L / 4 + 16, n = m->n;
+    const size_t C = (size_t)cap, cnt = C * n * n * 4, tr = C * 4 * kTraceComps * n;
+    double* keep_u = m->u;
     cudaFree(m->rvol);
     cudaFree(m->trace);
     cudaFree(m->trace_bar);
     cudaFree(m->tv);
     cudaFree(m->part);
-    m->rvol = m->trace = m->trace_bar = m->tv = m->part = nullptr;
-    if (new_u) {
-        cudaFree(m->u);
-        m->u = new_u;
-    }
-    m->cells = L;
-    m->tv_prep_cells = -1;  // fresh `part`: combine weights not prepared
+    cudaFree(m->u_spare);
+    cudaFree(m->dtrans);
+    cudaFree(m->geo);
+    cudaFree(m->nbr);
+    cudaFree(m->bgl);
+    cudaFree(m->mbl64);
+    cudaFree(m->mblf);
+    m->rvol = m->trace = m->trace_bar = m->tv = m->part = m->u_spare = m->geo = m->bgl = m->mbl64 = nullptr;
+    m->nbr = m->dtrans = nullptr;
+    m->mblf = nullptr;
+    m->u = keep_u;
+    m->leaf_cap = cap;
+    m->tv_prep_cells = -1;
     if (cudaMalloc(&m->rvol, cnt * 8) != cudaSuccess || cudaMalloc(&m->trace, tr * 8) != cudaSuccess ||
-        cudaMalloc(&m->tv, (size_t)L * 8) != cudaSuccess ||
-        cudaMalloc(&m->part, 8 * tv_stats_scratch_doubles(m->N, L)) != cudaSuccess) {
+        cudaMalloc(&m->tv, C * 8) != cudaSuccess ||
+        cudaMalloc(&m->part, 8 * tv_stats_scratch_doubles(m->N, cap)) != cudaSuccess ||
+        cudaMalloc(&m->u_spare, cnt * 8) != cudaSuccess || cudaMalloc(&m->dtrans, C * 12 * 4) != cudaSuccess) {
         cudaGetLastError();
         return fail(ADG_ENOMEM, "adaptive mesh: buffers");
     }
-    return ADG_OK;
+    *grew = true;
+    return ADG_OK;  // the tables are allocated by the next upload_tables
 }
 
 int amr_setup(adg_mesh* m) {
@@ -271,6 +284,15 @@ int amr_setup(adg_mesh* m) {
         }
     m->tree = T;
     m->amr = 1;
+    // the base mesh's buffers (u, rvol, trace, tv, part) were sized by
+    // create_mesh for nx * ny leaves
+    m->leaf_cap = (int)T->leaves.size();
+    const size_t cnt = (size_t)m->leaf_cap * n * n * 4;
+    if (cudaMalloc(&m->u_spare, cnt * 8) != cudaSuccess ||
+        cudaMalloc(&m->dtrans, (size_t)m->leaf_cap * 12 * 4) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ADG_ENOMEM, "adaptive mesh: buffers");
+    }
     return upload_tables(m);
 }
 
@@ -282,8 +304,12 @@ void amr_free(adg_mesh* m) {
     cudaFree(m->bgl);
     cudaFree(m->mbl64);
     cudaFree(m->mblf);
+    cudaFree(m->u_spare);
+    cudaFree(m->dtrans);
     m->mbl64 = nullptr;
     m->mblf = nullptr;
+    m->u_spare = nullptr;
+    m->dtrans = nullptr;
 }
 
 // per-leaf constants: P with the leaf's cell sizes
@@ -1056,24 +1082,27 @@ extern "C" int adg_adapt(adg_mesh* m, const int8_t* flags_dev, int* leaves_out, 
         trans[k * 12 + 2] = nl[k].b;
         for (int q = 0; q < 9; ++q) trans[k * 12 + 3 + q] = nl[k].src[q];
     }
-    int* dtrans = nullptr;
-    double* unew = nullptr;
-    const size_t cnt = (size_t)L2 * m->n * m->n * 4;
-    if (cudaMalloc(&dtrans, trans.size() * 4) != cudaSuccess || cudaMalloc(&unew, cnt * 8) != cudaSuccess) {
-        cudaGetLastError();
-        cudaFree(dtrans);
-        return fail(ADG_ENOMEM, "adapt: new state");
-    }
-    ADG_CK(cudaMemcpyAsync(dtrans, trans.data(), trans.size() * 4, cudaMemcpyHostToDevice, s), "adapt: upload");
-    int rc = amr_transfer(m, m->u, unew, L2, dtrans, s);
-    if (rc) { cudaFree(dtrans); cudaFree(unew); return rc; }
+    bool grew = false;
+    if (int rc0 = ensure_capacity(m, L2, &grew)) return rc0;
+    ADG_CK(cudaMemcpyAsync(m->dtrans, trans.data(), trans.size() * 4, cudaMemcpyHostToDevice, s), "adapt: upload");
+    int rc = amr_transfer(m, m->u, m->u_spare, L2, m->dtrans, s);
+    if (rc) return rc;
     ADG_CK(cudaStreamSynchronize(s), "adapt: transfer sync");
-    cudaFree(dtrans);
+    std::swap(m->u, m->u_spare);
+    if (grew) {  // the spare (the old state) still has the old capacity
+        cudaFree(m->u_spare);
+        m->u_spare = nullptr;
+        if (cudaMalloc(&m->u_spare, (size_t)m->leaf_cap * m->n * m->n * 4 * 8) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(ADG_ENOMEM, "adapt: spare state");
+        }
+    }
     T->leaves.clear();
     for (auto& x : nl) T->leaves.push_back(x.c);
     T->index();
-    rc = size_buffers(m, unew);
-    if (!rc) rc = upload_tables(m);
+    m->cells = L2;
+    m->tv_prep_cells = -1;  // the statistics' combine weights depend on the leaf count
+    rc = upload_tables(m);
     if (rc) return rc;
     m->predicted = false;
     if (leaves_out) *leaves_out = L2;

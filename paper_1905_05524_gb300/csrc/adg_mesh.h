@@ -41,6 +41,9 @@ struct adg_mesh {
     double* bgl = nullptr;        // [leaves][n][2] node background, then [leaves][2][2] N/S faces
     double* mbl64 = nullptr;      // mixed precision: per-leaf FP64 background (adg_amr.cu upload_tables)
     float* mblf = nullptr;        // mixed precision: per-leaf FP32 background
+    int leaf_cap = 0;             // leaves the per-leaf buffers and tables hold (grow-only)
+    double* u_spare = nullptr;    // second state buffer: adaptation writes the new state here, then swaps
+    int* dtrans = nullptr;        // [leaf_cap][12] transfer rules of an adaptation
     double hmin = 0.0;            // smallest leaf size (dt rule)
     double* halo = nullptr;       // strip decomposition: [2][nx][17][n] south, north halo traces
 };
