@@ -37,4 +37,14 @@ __device__ __forceinline__ double f32_to_f64(float f) {
     return __hiloint2double((int)hi, (int)lo);
 }
 
+// Programmatic dependent launch (sm_90 and later).  A kernel launched with
+// the programmatic-serialization attribute may be scheduled while the
+// previous kernel of its stream is still finishing; pdl_wait() blocks until
+// that kernel has completed and its memory operations are visible, so every
+// read of its outputs must follow it.  pdl_trigger() tells the scheduler that
+// this block no longer needs to delay the dependent kernel.  Both are no-ops
+// for kernels launched without the attribute.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 }  // namespace adg

@@ -561,6 +561,7 @@ k_predictor_mixed(const double* __restrict__ u, float* __restrict__ rvol, float*
                   int cells, float dt, const BasisF B, const PhysF P, const MixedBg bg) {
     extern __shared__ float smf[];
     predictor_mixed_body<N, CPB>(u, rvol, trace, cells, blockIdx.x * CPB, dt, B, P, bg, smf);
+    pdl_trigger();  // the corrector (launched programmatically) may be scheduled
 }
 
 template <int N, int CPB, bool TV>
@@ -568,7 +569,9 @@ __global__ void __launch_bounds__(CPB*(N + 1) * (N + 1))
 k_corrector_mixed(double* __restrict__ u, const float* __restrict__ rvol,
                   const float* __restrict__ trace, int cells, double dt, const BasisF B,
                   const PhysF P, const MixedBg bg, const TvEpilogue epi) {
+    pdl_wait();  // the predictor's residual and traces are complete and visible
     corrector_mixed_body<N, CPB, TV>(u, rvol, trace, cells, blockIdx.x * CPB, dt, B, P, bg, epi);
+    pdl_trigger();
 }
 
 // Batched persistent kernels: a fixed grid walks a list of tiles (instance,
@@ -621,12 +624,25 @@ static int launch_corr_mixed(double* u, const float* rvol, const float* trace, i
                              cudaStream_t s) {
     using C = MixCfg<N>;
     const int blocks = (cells + C::cpb - 1) / C::cpb;
+    // programmatic launch: scheduled while the predictor drains, waits for it
+    // in pdl_wait() before reading its outputs
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(blocks);
+    cfg.blockDim = dim3(C::threads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t e;
     if (epi)
-        k_corrector_mixed<N, C::cpb, true><<<blocks, C::threads, 0, s>>>(u, rvol, trace, cells, dt, B, P, bg, *epi);
+        e = cudaLaunchKernelEx(&cfg, k_corrector_mixed<N, C::cpb, true>, u, rvol, trace, cells, dt, B, P, bg, *epi);
     else
-        k_corrector_mixed<N, C::cpb, false>
-            <<<blocks, C::threads, 0, s>>>(u, rvol, trace, cells, dt, B, P, bg, TvEpilogue{});
-    return (int)cudaGetLastError();
+        e = cudaLaunchKernelEx(&cfg, k_corrector_mixed<N, C::cpb, false>, u, rvol, trace, cells, dt, B, P, bg,
+                               TvEpilogue{});
+    return e != cudaSuccess ? (int)e : (int)cudaGetLastError();
 }
 
 int launch_predictor_mixed(int N, const double* u, float* rvol, float* trace, int cells, double dt,

@@ -140,6 +140,9 @@ k_tv_stats_flags(const double* __restrict__ tv, const TvStatsArgs st, double T_r
         f1[l] = st.wtree[2 * (l * kTvThreads + pos)];
         f2[l] = st.wtree[2 * (l * kTvThreads + pos) + 1];
     }
+    // the tree weights above come from the host-side preparation; the block
+    // triples below from the kernel before this one (programmatic launch)
+    pdl_wait();
     // left fold of this thread's block triples, loads batched four at a time
     double m = 0.0, m2 = 0.0;
     const int k0 = t * st.per, k1 = min(k0 + st.per, st.nblk);
@@ -513,8 +516,20 @@ int launch_tv_stats_flags(const double* tv, const TvStatsArgs& st, double T_r, d
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         nb = std::max(1, std::min((st.cells + kTvThreads - 1) / kTvThreads, sms));
     }
-    k_tv_stats_flags<<<nb, kTvThreads, 0, (cudaStream_t)stream>>>(tv, st, T_r, T_c, stats_dev, flags);
-    return (int)cudaGetLastError();
+    // programmatic launch: scheduled while the TV-producing kernel drains,
+    // waits for it in pdl_wait() before reading the TV values and triples
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(nb);
+    cfg.blockDim = dim3(kTvThreads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = (cudaStream_t)stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, k_tv_stats_flags, tv, st, T_r, T_c, stats_dev, flags);
+    return e != cudaSuccess ? (int)e : (int)cudaGetLastError();
 }
 
 int launch_tv_flags_given(const double* tv, int cells, const double* stats_dev, double T_r, double T_c,
