@@ -874,7 +874,8 @@ def run_ours(args):
                           "tv_indicator": main["tv"] / args.steps,
                           "note": "separate calls (adg_predictor, adg_corrector, adg_tv_indicator); the timed "
                                   "step is adg_step_tv, whose corrector also evaluates the per-cell TV"},
-            "gpu_launches": 4 * args.steps,
+            # adg_step_tv: predictor, corrector with the TV epilogue, statistics and flags
+            "gpu_launches": 3 * args.steps,
             "clocks": main["clocks"],
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": dof * 8,
                     "d2h_bytes_per_step": dof * 8,
