@@ -53,7 +53,13 @@ struct AmrTree {
     int nx0 = 0, ny0 = 0, maxl = 0;
     bool per_x = false, per_y = false;
     std::vector<std::array<int, 3>> leaves;  // level, ix, iy
-    std::unordered_map<long long, int> pos;
+    // leaf index of every (level, ix, iy) cell, one dense grid per level
+    // (-1: not a leaf); index() resets only the previous leaves' entries
+    std::vector<std::vector<int>> grid;
+    std::vector<std::array<int, 3>> indexed;
+    // per (level, iy) row: the background tables of upload_tables (they depend
+    // on the height only), computed once
+    std::unordered_map<long long, std::vector<double>> rows;
     AmrOps ops;
 
     static long long key(int l, int ix, int iy) { return ((long long)l << 50) | ((long long)ix << 25) | iy; }
@@ -63,12 +69,22 @@ struct AmrTree {
             if (a[2] != b[2]) return a[2] < b[2];
             return a[1] < b[1];
         });
-        pos.clear();
-        for (int k = 0; k < (int)leaves.size(); ++k) pos[key(leaves[k][0], leaves[k][1], leaves[k][2])] = k;
+        if ((int)grid.size() < maxl + 1) grid.resize(maxl + 1);
+        for (const auto& c : indexed) grid[c[0]][(size_t)c[2] * (nx0 * ipow3(c[0])) + c[1]] = -1;
+        for (int k = 0; k < (int)leaves.size(); ++k) {
+            const auto& c = leaves[k];
+            std::vector<int>& g = grid[c[0]];
+            const size_t NX = (size_t)nx0 * ipow3(c[0]), NY = (size_t)ny0 * ipow3(c[0]);
+            if (g.empty()) g.assign(NX * NY, -1);
+            g[(size_t)c[2] * NX + c[1]] = k;
+        }
+        indexed = leaves;
     }
     int find(int l, int ix, int iy) const {
-        auto it = pos.find(key(l, ix, iy));
-        return it == pos.end() ? -1 : it->second;
+        if (l < 0 || l >= (int)grid.size() || grid[l].empty()) return -1;
+        const int NX = nx0 * ipow3(l), NY = ny0 * ipow3(l);
+        if (ix < 0 || ix >= NX || iy < 0 || iy >= NY) return -1;
+        return grid[l][(size_t)iy * NX + ix];
     }
     // face 0 E, 1 W, 2 N, 3 S; out[5] = type, id0, id1, id2, sub
     bool neighbour(int k, int f, int out[kNbrInts]) const {
@@ -115,19 +131,74 @@ struct AmrTree {
 static AmrTree* tree_of(adg_mesh* m) { return (AmrTree*)m->tree; }
 
 // Upload geometry, neighbour and background tables of the current leaves.
+// The background depends on the height only, so each (level, iy) row's
+// values are computed once and cached in the tree.  Row layout (doubles):
+// [n][2] node (pbar, rhobar); [4] faces (pbar, rhobar) north, south; for the
+// mixed predictor [n][2] node (rhobar, Ebar), [2][2] (rhobar, Ebar) of the
+// nodal background extrapolated to the north, south faces, [n][3] node
+// (pbar, d rhobar/dz, d Ebar/dz), [2][2] extrapolated (rhobar, (gamma-1)
+// (Ebar - rhobar g z_face)).
 static int upload_tables(adg_mesh* m) {
     AmrTree* T = tree_of(m);
     const int L = (int)T->leaves.size(), n = m->n;
     const adg_mesh_desc* d = &m->d;
+    const bool mixed = d->precision == ADG_PREC_MIXED;
     std::vector<double> geo((size_t)L * 4), bgl((size_t)L * n * 2 + (size_t)L * 4, 0.0);
     std::vector<int> nbr((size_t)L * 4 * kNbrInts);
-    const double cp = m->P.cp;
+    std::vector<double> h64(mixed ? (size_t)L * n * 2 + (size_t)L * 4 : 0, 0.0);
+    std::vector<float> h32(mixed ? (size_t)L * n * 3 + (size_t)L * 4 : 0, 0.0f);
+    const double cp = m->P.cp, g = d->gravity ? d->g : 0.0, gm1 = d->gamma - 1.0;
     auto bgp = [&](double z, double& pb, double& rb) {
         pb = rb = 0.0;
         if (!d->gravity) return;
         const double ex = 1.0 - d->g * z / (cp * d->theta0);
         pb = d->p0 * std::pow(ex, cp / d->R);
         rb = pb / (d->R * d->theta0 * ex);
+    };
+    const size_t o_face = (size_t)n * 2, o_m64 = o_face + 4, o_ext = o_m64 + (size_t)n * 2, o_m32 = o_ext + 4,
+                 o_ext32 = o_m32 + (size_t)n * 3, row_len = o_ext32 + 4;
+    auto row_of = [&](int l, int iy, double hy) -> const std::vector<double>& {
+        std::vector<double>& r = T->rows[AmrTree::key(l, 0, iy)];
+        if (!r.empty()) return r;
+        r.assign(row_len, 0.0);
+        std::vector<double> rb(n), Eb(n), pb(n);
+        for (int j = 0; j < n; ++j) {
+            const double z = d->y0 + (iy + m->B.xi[j]) * hy;
+            bgp(z, r[(size_t)j * 2], r[(size_t)j * 2 + 1]);
+            // the mixed predictor's base at the same node height (its own
+            // formula for the height, as the leaf's origin plus xi hy)
+            const double zm = (d->y0 + iy * hy) + m->B.xi[j] * hy;
+            bgp(zm, pb[j], rb[j]);
+            Eb[j] = pb[j] / gm1 + rb[j] * g * zm;
+        }
+        bgp(d->y0 + (iy + 1) * hy, r[o_face], r[o_face + 1]);  // north face
+        bgp(d->y0 + iy * hy, r[o_face + 2], r[o_face + 3]);    // south face
+        for (int j = 0; j < n; ++j) {
+            double dr = 0.0, dE = 0.0;
+            for (int p = 0; p < n; ++p) {
+                dr += m->B.D[j][p] * rb[p];
+                dE += m->B.D[j][p] * Eb[p];
+            }
+            r[o_m64 + (size_t)j * 2] = rb[j];
+            r[o_m64 + (size_t)j * 2 + 1] = Eb[j];
+            r[o_m32 + (size_t)j * 3] = pb[j];
+            r[o_m32 + (size_t)j * 3 + 1] = dr / hy;
+            r[o_m32 + (size_t)j * 3 + 2] = dE / hy;
+        }
+        for (int side = 0; side < 2; ++side) {  // 0: north (phi(1)), 1: south (phi(0))
+            const double* phi = side == 0 ? m->B.phi1 : m->B.phi0;
+            double er = 0.0, eE = 0.0;
+            for (int p = 0; p < n; ++p) {
+                er += phi[p] * rb[p];
+                eE += phi[p] * Eb[p];
+            }
+            const double zf = (d->y0 + iy * hy) + (side == 0 ? hy : 0.0);
+            r[o_ext + side * 2] = er;
+            r[o_ext + side * 2 + 1] = eE;
+            r[o_ext32 + side * 2] = er;
+            r[o_ext32 + side * 2 + 1] = gm1 * (eE - er * g * zf);
+        }
+        return r;
     };
     double hmin = 1e300;
     for (int k = 0; k < L; ++k) {
@@ -138,11 +209,25 @@ static int upload_tables(adg_mesh* m) {
         geo[k * 4 + 1] = d->y0 + iy * hy;
         geo[k * 4 + 2] = hx;
         geo[k * 4 + 3] = hy;
-        for (int j = 0; j < n; ++j)
-            bgp(d->y0 + (iy + m->B.xi[j]) * hy, bgl[((size_t)k * n + j) * 2], bgl[((size_t)k * n + j) * 2 + 1]);
+        const std::vector<double>& r = row_of(l, iy, hy);
+        for (int j = 0; j < n; ++j) {
+            bgl[((size_t)k * n + j) * 2] = r[(size_t)j * 2];
+            bgl[((size_t)k * n + j) * 2 + 1] = r[(size_t)j * 2 + 1];
+        }
         double* fb = bgl.data() + (size_t)L * n * 2 + (size_t)k * 4;
-        bgp(d->y0 + (iy + 1) * hy, fb[0], fb[1]);  // north face
-        bgp(d->y0 + iy * hy, fb[2], fb[3]);        // south face
+        for (int q = 0; q < 4; ++q) fb[q] = r[o_face + q];
+        if (mixed) {
+            for (int j = 0; j < n; ++j) {
+                const size_t rr = (size_t)k * n + j;
+                h64[rr * 2] = r[o_m64 + (size_t)j * 2];
+                h64[rr * 2 + 1] = r[o_m64 + (size_t)j * 2 + 1];
+                for (int q = 0; q < 3; ++q) h32[rr * 3 + q] = (float)r[o_m32 + (size_t)j * 3 + q];
+            }
+            for (int q = 0; q < 4; ++q) {
+                h64[(size_t)L * n * 2 + (size_t)k * 4 + q] = r[o_ext + q];
+                h32[(size_t)L * n * 3 + (size_t)k * 4 + q] = (float)r[o_ext32 + q];
+            }
+        }
         for (int f = 0; f < 4; ++f)
             if (!T->neighbour(k, f, &nbr[((size_t)k * 4 + f) * kNbrInts]))
                 return fail(ADG_EINVAL, "adaptive mesh: level difference above one across a face");
@@ -161,51 +246,7 @@ static int upload_tables(adg_mesh* m) {
     ADG_CK(cudaMemcpy(m->geo, geo.data(), geo.size() * 8, cudaMemcpyHostToDevice), "amr tables");
     ADG_CK(cudaMemcpy(m->nbr, nbr.data(), nbr.size() * 4, cudaMemcpyHostToDevice), "amr tables");
     ADG_CK(cudaMemcpy(m->bgl, bgl.data(), bgl.size() * 8, cudaMemcpyHostToDevice), "amr tables");
-    if (d->precision == ADG_PREC_MIXED) {
-        // the mixed predictor's per-leaf background: FP64 (rhobar, Ebar) per
-        // node row and extrapolated to the N, S faces; FP32 (pbar, d rhobar/dz,
-        // d Ebar/dz) per row and (rhobar, (gamma-1)(Ebar - rhobar g z)) of the
-        // extrapolated face base
-        std::vector<double> h64((size_t)L * n * 2 + (size_t)L * 4, 0.0);
-        std::vector<float> h32((size_t)L * n * 3 + (size_t)L * 4, 0.0f);
-        const double g = d->gravity ? d->g : 0.0, gm1 = d->gamma - 1.0;
-        std::vector<double> rb(n), Eb(n), pb(n);
-        for (int k = 0; k < L; ++k) {
-            const double y0 = geo[k * 4 + 1], hy = geo[k * 4 + 3];
-            for (int j = 0; j < n; ++j) {
-                const double z = y0 + m->B.xi[j] * hy;
-                bgp(z, pb[j], rb[j]);
-                Eb[j] = pb[j] / gm1 + rb[j] * g * z;
-            }
-            for (int j = 0; j < n; ++j) {
-                double dr = 0.0, dE = 0.0;
-                for (int p = 0; p < n; ++p) {
-                    dr += m->B.D[j][p] * rb[p];
-                    dE += m->B.D[j][p] * Eb[p];
-                }
-                const size_t r = (size_t)k * n + j;
-                h64[r * 2] = rb[j];
-                h64[r * 2 + 1] = Eb[j];
-                h32[r * 3] = (float)pb[j];
-                h32[r * 3 + 1] = (float)(dr / hy);
-                h32[r * 3 + 2] = (float)(dE / hy);
-            }
-            for (int side = 0; side < 2; ++side) {  // 0: north (phi(1)), 1: south (phi(0))
-                const double* phi = side == 0 ? m->B.phi1 : m->B.phi0;
-                double er = 0.0, eE = 0.0;
-                for (int p = 0; p < n; ++p) {
-                    er += phi[p] * rb[p];
-                    eE += phi[p] * Eb[p];
-                }
-                const double zf = y0 + (side == 0 ? hy : 0.0);
-                const size_t o64 = (size_t)L * n * 2 + ((size_t)k * 2 + side) * 2;
-                const size_t o32 = (size_t)L * n * 3 + ((size_t)k * 2 + side) * 2;
-                h64[o64] = er;
-                h64[o64 + 1] = eE;
-                h32[o32] = (float)er;
-                h32[o32 + 1] = (float)(gm1 * (eE - er * g * zf));
-            }
-        }
+    if (mixed) {
         if (!m->mbl64) {
             if (cudaMalloc(&m->mbl64, (C * n * 2 + C * 4) * 8) != cudaSuccess ||
                 cudaMalloc(&m->mblf, (C * n * 3 + C * 4) * 4) != cudaSuccess) {
