@@ -711,6 +711,49 @@ def run_3d(args, dev):
     a, b = states["bubble3d_mixed"], states["bubble3d"]
     out["bubble3d_mixed"]["rho_rel_l2_vs_fp64_after_53_steps"] = float(
         torch.linalg.vector_norm(a[:, 0] - b[:, 0]) / torch.linalg.vector_norm(b[:, 0]))
+    if args.full_3d:
+        # the paper's 3D run: the cosine bubble to t = 400 s (mixed precision)
+        cfg = bubble3d_config(device=dev.index)
+        cfg.precision = L.ADG_PREC_MIXED
+        m = Mesh3(cfg)
+        m.init_scenario(L.ADG_SCEN_COSINE, A=0.5, a=250.0, xc=500.0, zc=350.0)
+        u0 = m.get_state()
+        n = cfg.degree + 1
+        import numpy as np
+        xi, w = np.polynomial.legendre.leggauss(n)
+        w = torch.tensor(0.5 * w, dtype=torch.float64, device=dev)
+        W = w[:, None, None] * w[None, :, None] * w[None, None, :]
+        mass0 = float((u0[:, 0] * W).sum())
+        dt = m.stable_dt(CFL)
+        T = 400.0
+        nsteps = math.ceil(T / dt)
+        dt = T / nsteps
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        chunk = 5000
+        for s0 in range(0, nsteps, chunk):
+            m.step(dt, min(chunk, nsteps - s0))
+        torch.cuda.synchronize()
+        sec = time.perf_counter() - t0
+        u = m.get_state()
+        # theta' at the nodes (FP64 on the device)
+        hz = 1000.0 / cfg.nz
+        iz = (torch.arange(cfg.cells, device=dev) // (cfg.nx * cfg.ny)).double()
+        zn = (iz[:, None] + torch.tensor(0.5 * (xi + 1.0), device=dev)[None, :]) * hz   # [c, l]
+        Z = zn[:, :, None, None].expand(-1, n, n, n)
+        rho, mx, my, mz, E = u.unbind(1)
+        p_ = (cfg.gamma - 1.0) * (E - 0.5 * (mx * mx + my * my + mz * mz) / rho - rho * cfg.g * Z)
+        cp = cfg.gamma * cfg.R / (cfg.gamma - 1.0)
+        th = p_ / (rho * cfg.R) * (cfg.p0 / p_) ** (cfg.R / cp) - cfg.theta0
+        k = int(torch.argmax(th.reshape(-1)))
+        out["bubble3d_mixed_full_run"] = {
+            "config": "3D cosine bubble to t = 400 s (Sec. 4.2), degree 2, 25^3 cells of 40 m, mu = 0.005, mixed",
+            "steps": nsteps, "dt": dt, "seconds": sec, "value": cfg.cells * n ** 3 * 5 * nsteps / sec,
+            "finite": bool(torch.isfinite(u).all()), "theta_prime_max": float(th.max()),
+            "theta_prime_min": float(th.min()), "z_of_theta_prime_max": float(Z.reshape(-1)[k]),
+            "max_speed": float((torch.sqrt(mx * mx + my * my + mz * mz) / rho).max()),
+            "mass_drift_rel": abs(float((u[:, 0] * W).sum()) - mass0) / mass0}
+        m.close()
     cfg = abc_config(device=dev.index)
     m = Mesh3(cfg)
     m.init_scenario(L.ADG_SCEN_ABC)
@@ -912,6 +955,8 @@ def main():
                          "fv (MUSCL-Hancock finite volumes, colliding bubbles), "
                          "3d (3D cosine bubble and ABC flow)")
     ap.add_argument("--sweep-steps", type=int, default=20)
+    ap.add_argument("--full-3d", action="store_true",
+                    help="with --workload 3d: also run the paper's 3D bubble to t = 400 s (mixed precision)")
     ap.add_argument("--amr-steps", type=int, default=1000)
     ap.add_argument("--cpu-steps", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
