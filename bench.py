@@ -846,14 +846,14 @@ def run_ours(args):
 
     main = run_form(args.precision, args.steps, args.warmup, dev, ws)
     t_ms = main["total"]
-    e2e_sec = main["e2e_sec"]
+    e2e_sec, e2e_serial_sec = main["e2e_sec"], main["e2e_serial_sec"]
     if ws > 1:
-        t = torch.tensor([t_ms, e2e_sec], device=dev, dtype=torch.float64)
+        t = torch.tensor([t_ms, e2e_sec, e2e_serial_sec], device=dev, dtype=torch.float64)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_ms, e2e_sec = float(t[0]), float(t[1])
+        t_ms, e2e_sec, e2e_serial_sec = float(t[0]), float(t[1]), float(t[2])
     value = dof * args.steps * ws / (t_ms * 1e-3)
     e2e_val = dof * args.steps * ws / e2e_sec
-    e2e_serial_val = dof * args.steps / main["e2e_serial_sec"]
+    e2e_serial_val = dof * args.steps * ws / e2e_serial_sec
 
     out = None
     if rank == 0:
