@@ -231,3 +231,34 @@ def test_mixed_config3_run_tracks_fp64():
     o._index()
     err = _theta_err(o, ms[1].get_state().cpu(), ms[0].get_state().cpu())
     assert err <= THETA_TOL, err
+
+
+@pytest.mark.parametrize("prec", [L.ADG_PREC_FP64, L.ADG_PREC_MIXED])
+def test_config3_mesh_step_matches_oracle(prec):
+    """A step on the full config-3 adaptive mesh (27x27 base, two levels,
+    built by init -> TV -> refine twice) against the oracle's tree: FP64 at
+    1e-11, mixed within THETA_TOL of theta' and 1e-9 of rho."""
+    cfg = atmosphere_config(degree=5, nx=27, ny=27, mu=0.001, precision=prec)
+    cfg.max_levels = 2
+    m, o = _pair(cfg, "wall")
+    for _ in range(2):
+        X, Y = o.node_coords()
+        u = torch.stack(ph.bubble_state(X, Y, ph.two_bubbles(X, Y), o.P), 1)
+        m.init_scenario(L.ADG_SCEN_TWO_BUBBLES)
+        _, fl, _ = m.tv_indicator(L.ADG_TV_THETA, 2.5, -0.5)
+        fl = torch.where(fl > 0, 1, 0).to(torch.int8)
+        o.adapt(u, fl.cpu())
+        m.adapt(fl)
+    assert m.leaf_info() == [tuple(c) for c in o.leaves]
+    X, Y = o.node_coords()
+    u = torch.stack(ph.bubble_state(X, Y, ph.two_bubbles(X, Y), o.P), 1)
+    m.init_scenario(L.ADG_SCEN_TWO_BUBBLES)
+    dt = m.stable_dt(0.25)
+    uo = o.step(u, dt)
+    m.step(dt)
+    a = m.get_state().cpu()
+    if prec == L.ADG_PREC_FP64:
+        _close(a, uo)
+    else:
+        assert _theta_err(o, a, uo) <= THETA_TOL
+        assert (torch.linalg.vector_norm(a[:, 0] - uo[:, 0]) / torch.linalg.vector_norm(uo[:, 0])).item() <= 1e-9

@@ -113,3 +113,18 @@ def test_fv_rejects_viscosity_and_other_boundaries():
     cfg.bc_y = L.ADG_BC_NOSLIP
     with pytest.raises(L.AdgError):
         FvMesh(cfg)
+
+
+def test_full_size_two_bubbles_match_oracle():
+    """The timed configuration in FP64: 630 x 630 cells, the colliding
+    bubbles from the device initialisation, 3 steps at CFL 0.5, every cell."""
+    cfg = fv_bubble_config(nx=630, ny=630)
+    o = oracle(cfg)
+    m = FvMesh(cfg)
+    m.init_scenario(L.ADG_SCEN_TWO_BUBBLES)
+    U = m.get_state().cpu()
+    dt = m.stable_dt(0.5)
+    for _ in range(3):
+        U = o.step(U, dt)
+    m.step(dt, 3)
+    assert_close(m.get_state(), U, TOL, True, "630x630")
