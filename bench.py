@@ -352,7 +352,7 @@ def run_form(prec_name, steps, warmup, dev, ws):
 
 
 def run_batch(dev, nsteps=20, instances=64):
-    """Config-5 batch: `instances` warm-bubble instances (sides U{9..81},
+    """Batch of `instances` warm-bubble instances (sides U{9..81},
     seed 3; radii U[100,300] m, seed 4), degree 5, mixed precision, advanced
     by the persistent graph-captured batched launch (predictor + corrector)."""
     import torch
@@ -414,7 +414,7 @@ def prolong_to_level(u, leaves, degree, target_level, nx0, ny0):
 
 
 def run_amr(args, dev):
-    """Config 3: two-bubble convection on a 3:1 tree, degree 5, 27x27 base, two
+    """Two-bubble convection on a 3:1 tree, degree 5, 27x27 base, two
     refinement levels (to 243x243), mu = 0.001, T_r = 2.5, T_c = -0.5, regrid
     every 10 steps; all leaves of all levels advanced by one predictor and one
     corrector launch per step (FP64).  Compared with the uniform 243x243 run."""
@@ -495,7 +495,7 @@ def run_amr(args, dev):
                                                        np.sqrt((W * tha ** 2).sum())),
              "form": "FP32 predictor on perturbations, FP64 corrector with hanging faces, FP64 TV and adaptation"}
     return {
-        "metric": METRIC + " (config 3: two-bubble AMR)", "value": dof_updates / t_steps, "unit": UNIT,
+        "metric": METRIC + " (two-bubble AMR run)", "value": dof_updates / t_steps, "unit": UNIT,
         "dtype": "f64", "steps": steps, "regrid_every": every,
         "value_including_regrid": dof_updates / wall,
         "leaves_final": len(leaves), "leaves_per_level": [levels.count(l) for l in range(3)],
@@ -512,7 +512,7 @@ def run_amr(args, dev):
 
 
 def run_sweep(args, dev):
-    """Config 5 (first part): periodic steady manufactured problem on 243x243
+    """Degree sweep: periodic steady manufactured problem on 243x243
     cells at degrees 2..7, FP64 and mixed, `sweep_steps` steps each
     (predictor + corrector), CUDA-event timed; the state exceeds L2 from
     degree 4 on (smaller ones are flushed before each step)."""
@@ -545,7 +545,7 @@ def run_sweep(args, dev):
             m.close()
         row["mixed_over_fp64"] = row["mixed"]["value"] / row["fp64"]["value"]
         out.append(row)
-    return {"metric": METRIC + " (config 5: degree sweep, 243x243 periodic)", "unit": UNIT,
+    return {"metric": METRIC + " (degree sweep, 243x243 periodic)", "unit": UNIT,
             "step": "predictor + corrector", "sweep": out}
 
 
@@ -781,7 +781,7 @@ def run_3d(args, dev):
 
 
 def run_adjoint(args, dev):
-    """Config 4: gradient of the probe misfit through 200 FP64 steps (degree 3,
+    """Adjoint run: gradient of the probe misfit through 200 FP64 steps (degree 3,
     27x27) with checkpoints every 20: forward + checkpointed backward."""
     import torch
     from paper_1905_05524_gb300 import _lib as L
@@ -816,7 +816,7 @@ def run_adjoint(args, dev):
     torch.cuda.synchronize()
     t2 = time.perf_counter()
     dof = 729 * n * n * 4
-    return {"metric": METRIC + " (config 4: adjoint)", "unit": UNIT, "dtype": "f64",
+    return {"metric": METRIC + " (adjoint run)", "unit": UNIT, "dtype": "f64",
             "forward_seconds": t1 - t0, "backward_seconds": t2 - t1,
             "forward_value": dof * 200 / (t1 - t0), "gradient_value": dof * 200 / (t2 - t0),
             "J": float(J.detach()), "grad_norm": float(g.norm()),
@@ -949,8 +949,8 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-instance batched form")
     ap.add_argument("--batch-steps", type=int, default=20)
     ap.add_argument("--workload", default="bubble", choices=["bubble", "amr", "sweep", "adjoint", "cfd", "fv", "3d"],
-                    help="extra workloads, each printing its own JSON line: amr (config 3), "
-                         "sweep (config 5 degree sweep), adjoint (config 4 gradient), "
+                    help="extra workloads, each printing its own JSON line: amr (two-bubble AMR run), "
+                         "sweep (degree sweep), adjoint (checkpointed gradient), "
                          "cfd (Sec. 4.1 Taylor-Green vortex and lid-driven cavity), "
                          "fv (MUSCL-Hancock finite volumes, colliding bubbles), "
                          "3d (3D cosine bubble and ABC flow)")

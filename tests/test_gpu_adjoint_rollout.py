@@ -72,7 +72,7 @@ def test_rollout_gradient_vs_oracle_adjoint():
 
 
 def test_config4_gradient_vs_central_differences():
-    """Config 4: degree 3, 27x27 cells, 200 steps, checkpoints every 20, 64
+    """The adjoint run: degree 3, 27x27 cells, 200 steps, checkpoints every 20, 64
     probes; 32 seeded unit directions.  Step h = 1e-2 K along a unit
     direction over 11,664 DOFs: with h = 1e-6 the central difference is
     dominated by the FP64 rounding noise of J after 200 steps (~5e-14, from the
@@ -88,5 +88,5 @@ def test_config4_gradient_vs_central_differences():
         fd = (_J(th0 + h * d, m, dt, 200, cells, W, target) - _J(th0 - h * d, m, dt, 200, cells, W, target)) / (2 * h)
         ad = float((g * d).sum())
         worst = max(worst, abs(fd - ad) / max(abs(ad), 1e-300))
-    print(f"config4: J = {J:.6e}, worst relative FD error over 32 directions = {worst:.3e}")
+    print(f"adjoint run: J = {J:.6e}, worst relative FD error over 32 directions = {worst:.3e}")
     assert worst <= 1e-5, worst

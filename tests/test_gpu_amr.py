@@ -1,6 +1,6 @@
 """Adaptive 3:1 tree on the GPU against the oracle's tree (oracle/amr.py):
 identical leaf sets after adaptation, transferred states, steps across
-hanging faces, conservation, TV indicator and the config-3 initial-mesh
+hanging faces, conservation, TV indicator and the two-bubble run's initial-mesh
 procedure (init -> TV -> refine, twice, re-initialising from the analytic
 two-bubble field)."""
 import math
@@ -125,7 +125,7 @@ def test_config3_initial_mesh_and_tv_match_oracle():
         assert m.leaf_info() == [tuple(c) for c in o.leaves]
     levels = [c[0] for c in o.leaves]
     assert max(levels) >= 1 and len(levels) < 243 * 243
-    print(f"config3 initial mesh: {len(levels)} leaves "
+    print(f"two-bubble initial mesh: {len(levels)} leaves "
           f"({levels.count(0)}/{levels.count(1)}/{levels.count(2)} per level)")
 
 
@@ -197,7 +197,7 @@ def test_mixed_adapt_step_periodic_matches_oracle():
 
 
 def test_mixed_config3_run_tracks_fp64():
-    """The config-3 procedure (two bubbles, 27x27 base, two levels, initial
+    """The two-bubble AMR procedure (two bubbles, 27x27 base, two levels, initial
     mesh by init -> TV -> refine twice) with an FP64 and a mixed mesh in
     lockstep -- both adapted with the FP64 mesh's flags -- then 10 steps, a
     regrid, 10 steps: theta' of the mixed run within THETA_TOL of the FP64
@@ -235,7 +235,7 @@ def test_mixed_config3_run_tracks_fp64():
 
 @pytest.mark.parametrize("prec", [L.ADG_PREC_FP64, L.ADG_PREC_MIXED])
 def test_config3_mesh_step_matches_oracle(prec):
-    """A step on the full config-3 adaptive mesh (27x27 base, two levels,
+    """A step on the full two-bubble adaptive mesh (27x27 base, two levels,
     built by init -> TV -> refine twice) against the oracle's tree: FP64 at
     1e-11, mixed within THETA_TOL of theta' and 1e-9 of rho."""
     cfg = atmosphere_config(degree=5, nx=27, ny=27, mu=0.001, precision=prec)

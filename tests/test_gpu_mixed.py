@@ -48,7 +48,7 @@ def test_mixed_vs_oracle_bubble_small():
 
 
 def test_mixed_vs_fp64_gpu_config2_400_steps():
-    """Config 2 at full size (CFL 0.25): 400 steps of the mixed path against 400
+    """The warm bubble at full size (degree 5, 81x81, CFL 0.25): 400 steps of the mixed path against 400
     steps of the FP64 GPU path (itself parity-checked against the oracle)."""
     res = {}
     for prec in (L.ADG_PREC_FP64, L.ADG_PREC_MIXED):
@@ -63,7 +63,7 @@ def test_mixed_vs_fp64_gpu_config2_400_steps():
         res[prec] = m.get_state().cpu()
     o = oracle_for(atmosphere_config(degree=5, nx=81, ny=81))
     err = rel_theta_err(o, res[L.ADG_PREC_MIXED], res[L.ADG_PREC_FP64])
-    print(f"config2 400 steps: relative theta' L2 error mixed vs fp64 = {err:.3e}")
+    print(f"warm bubble 400 steps: relative theta' L2 error mixed vs fp64 = {err:.3e}")
     assert err <= THETA_TOL, err
     # conserved variables: relative L2 per variable, stated
     for v in range(4):

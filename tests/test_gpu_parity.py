@@ -105,13 +105,13 @@ def test_step_steady_manufactured_all_degrees(degree):
 
 
 def test_step_config1_20_steps():
-    """Config 1: N = 3, 9x9 periodic [0,10]^2, steady manufactured, CFL 0.5, 20 steps."""
+    """Steady manufactured case: N = 3, 9x9 periodic [0,10]^2, steady manufactured, CFL 0.5, 20 steps."""
     cfg = steady_manufactured_config(degree=3, nx=9, ny=9)
     o = oracle_for(cfg)
     u0 = steady_field(o, cfg)
     dt = o.stable_dt(u0, 0.5)
     a, b, _, _ = run_pair(cfg, u0, dt, 20)
-    assert_close(a, b, what="config1")
+    assert_close(a, b, what="steady manufactured 9x9")
 
 
 def test_stable_dt_matches_oracle():
@@ -155,14 +155,14 @@ def test_two_bubbles_walls_degree3():
 
 
 def test_config2_full_size_two_steps():
-    """Config 2 at full size (N = 5, 81x81, walls, cosine bubble), the launch
+    """The warm bubble at full size (N = 5, 81x81, walls, cosine bubble), the launch
     configuration bench.py times: 2 steps compared element by element."""
     cfg = atmosphere_config(degree=5, nx=81, ny=81)
     o = oracle_for(cfg)
     u0 = cosine_field(o)
     dt = o.stable_dt(u0, 0.5)
     a, b, _, _ = run_pair(cfg, u0, dt, 2)
-    assert_close(a, b, what="config2")
+    assert_close(a, b, what="warm bubble 81x81")
 
 
 def test_predictor_corrector_split_equals_step():

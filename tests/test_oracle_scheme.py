@@ -108,7 +108,7 @@ def test_linear_predictor_reaches_spacetime_solution(N):
 
 
 def test_picard_sweeps_converged_navier_stokes():
-    """Reading P1 (n sweeps): extra sweeps move the config-1 step by < 1e-12."""
+    """Reading P1 (n sweeps): extra sweeps move the steady manufactured 9x9 step by < 1e-12."""
     s = Solver(Mesh(9, 9), ph.cfd_params(3, source="steady"))
     u = s.interpolate(ph.steady_manufactured)
     dt = s.stable_dt(u, 0.5)
@@ -192,7 +192,7 @@ def test_transpose_symmetry_manufactured():
 
 
 def test_steady_manufactured_error_small():
-    """Config 1 (N = 3, 9x9, 20 steps at CFL 0.5): the steady manufactured
+    """The steady manufactured case (N = 3, 9x9, 20 steps at CFL 0.5): the steady manufactured
     solution is kept to discretisation accuracy."""
     s = Solver(Mesh(9, 9), ph.cfd_params(3, source="steady"))
     u0 = s.interpolate(ph.steady_manufactured)
