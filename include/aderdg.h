@@ -319,7 +319,9 @@ int adg_adapt(adg_mesh* m, const int8_t* flags, int* leaves_out, void* stream);
  * adg_fv_step: one step of fixed dt (FP64: two kernels, face states at the
  *   half step, then fluxes and update; mixed: one fused kernel writing the
  *   second state buffer, which becomes the state, so a device pointer to the
- *   state is not stable across steps).  adg_fv_stable_dt: cfl / (max(|u| + c)/hx
+ *   state is not stable across steps, and the FP32 perturbations of the new
+ *   state for the next step; after adg_fv_set_state or adg_fv_init_scenario
+ *   one more kernel first splits the state).  adg_fv_stable_dt: cfl / (max(|u| + c)/hx
  *   + max(|v| + c)/hy); synchronises `stream`.  adg_fv_init_scenario: cell
  *   centre values of ADG_SCEN_COSINE, ADG_SCEN_TWO_BUBBLES or
  *   ADG_SCEN_BACKGROUND (gravity on).  Errors as for adg_mesh. */

@@ -46,6 +46,9 @@ struct adg_fv {
     // mixed precision: second state buffer (the fused step reads u, writes
     // u2, then the two swap) and the FP32 background tables
     double* u2 = nullptr;
+    float4* pert = nullptr;    // FP32 perturbations of u (kept current by the step; ping-pong with pert2)
+    float4* pert2 = nullptr;
+    bool pert_stale = true;    // u was changed outside the step
     float* bgf = nullptr;      // [ny] centre (rhobar, pbar, Ebar + pbar, g z), [ny + 1] faces
                                // (rhobar, pbar, 0, g z), [ny] face minus centre Ebar + pbar (north, south)
 };
@@ -359,7 +362,8 @@ __device__ __forceinline__ float4 f4_axpy(float s, float4 a, float4 b) {  // b +
 }
 
 __global__ void __launch_bounds__(kFvThreads) k_fv_step_mixed(const double* __restrict__ u, double* __restrict__ uo,
-                                                              const FvMixed M) {
+                                                              const float4* __restrict__ pin,
+                                                              float4* __restrict__ pout, const FvMixed M) {
     extern __shared__ float4 fv_smem[];
     float4* sp = fv_smem;                                // phase 1-2: perturbations; phase 3-4: face fluxes
     float4 (*sh)[kFvHh * kFvHw] = reinterpret_cast<float4 (*)[kFvHh * kFvHw]>(fv_smem + kFvShared);
@@ -368,16 +372,13 @@ __global__ void __launch_bounds__(kFvThreads) k_fv_step_mixed(const double* __re
     float* sa = srp + kFvThreads;                        // face velocity factor of Hbar in the energy flux
     const int tid = threadIdx.x;
     const int x0 = blockIdx.x * kFvTx, y0 = blockIdx.y * kFvTy;
-    // phase 1: FP64 split of the tile plus a 2-cell halo (wrapped indices;
-    // wall-side halo values are never used)
+    // phase 1: the FP32 perturbations of the tile plus a 2-cell halo (wrapped
+    // indices; wall-side halo values are never used), split from the FP64
+    // state by the previous step's phase 4 (or by k_fv_split)
     for (int k = tid; k < kFvPw * kFvPh; k += kFvThreads) {
         const int r = k / kFvPw, c = k - r * kFvPw;
         const int gy = fv_wrap(y0 - 2 + r, M.ny), gx = fv_wrap(x0 - 2 + c, M.nx);
-        const size_t i = (size_t)gy * M.nx + gx;
-        const double rho = u[i], mx = u[(size_t)M.cells + i], my = u[(size_t)2 * M.cells + i];
-        const double E = u[(size_t)3 * M.cells + i];
-        sp[k] = make_float4(f64_to_f32(__dsub_rn(rho, M.rbc[gy])), f64_to_f32(mx), f64_to_f32(my),
-                            f64_to_f32(__dsub_rn(E, M.Ebc[gy])));
+        sp[k] = pin[(size_t)gy * M.nx + gx];
     }
     __syncthreads();
     // phase 2: slopes, face states, half-step evolution (tile plus 1-cell halo,
@@ -466,10 +467,29 @@ __global__ void __launch_bounds__(kFvThreads) k_fv_step_mixed(const double* __re
     const float ey = fmaf(Hc, aN - aS, fmaf(dh.x, aN, fmaf(-dh.y, aS, GN.w - GS.w)));
     const float du3 = -M.dtx * ex - M.dty * ey;
     const size_t i = (size_t)gy * M.nx + gx;
-    uo[i] = __dadd_rn(u[i], f32_to_f64(du0));
-    uo[(size_t)M.cells + i] = __dadd_rn(u[(size_t)M.cells + i], f32_to_f64(du1));
-    uo[(size_t)2 * M.cells + i] = __dadd_rn(u[(size_t)2 * M.cells + i], f32_to_f64(du2));
-    uo[(size_t)3 * M.cells + i] = __dadd_rn(u[(size_t)3 * M.cells + i], f32_to_f64(du3));
+    const double r1 = __dadd_rn(u[i], f32_to_f64(du0));
+    const double m1 = __dadd_rn(u[(size_t)M.cells + i], f32_to_f64(du1));
+    const double n1 = __dadd_rn(u[(size_t)2 * M.cells + i], f32_to_f64(du2));
+    const double E1 = __dadd_rn(u[(size_t)3 * M.cells + i], f32_to_f64(du3));
+    uo[i] = r1;
+    uo[(size_t)M.cells + i] = m1;
+    uo[(size_t)2 * M.cells + i] = n1;
+    uo[(size_t)3 * M.cells + i] = E1;
+    // the next step's FP32 perturbations (the same split phase 1 would make)
+    pout[i] = make_float4(f64_to_f32(__dsub_rn(r1, M.rbc[gy])), f64_to_f32(m1), f64_to_f32(n1),
+                          f64_to_f32(__dsub_rn(E1, M.Ebc[gy])));
+}
+
+// FP32 perturbations of the whole FP64 state (after the state is set or
+// initialised; the step keeps them current afterwards)
+__global__ void __launch_bounds__(256) k_fv_split(const double* __restrict__ u, float4* __restrict__ p,
+                                                  const FvMixed M) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= M.cells) return;
+    const int gy = c / M.nx;
+    p[c] = make_float4(f64_to_f32(__dsub_rn(u[c], M.rbc[gy])), f64_to_f32(u[(size_t)M.cells + c]),
+                       f64_to_f32(u[(size_t)2 * M.cells + c]),
+                       f64_to_f32(__dsub_rn(u[(size_t)3 * M.cells + c], M.Ebc[gy])));
 }
 
 // point values at cell centres: background atmosphere with theta' (Sec. 4.2)
@@ -567,6 +587,8 @@ static void fv_free(adg_fv* f) {
     cudaFree(f->bg);
     cudaFree(f->part);
     cudaFree(f->u2);
+    cudaFree(f->pert);
+    cudaFree(f->pert2);
     cudaFree(f->bgf);
     delete f;
 }
@@ -616,7 +638,9 @@ extern "C" int adg_fv_create(const adg_mesh_desc* d, adg_fv** out) {
     bool ok = cudaMalloc(&f->u, (size_t)4 * f->cells * 8) == cudaSuccess && cudaMalloc(&f->bg, nbg * 8) == cudaSuccess &&
               cudaMalloc(&f->part, (size_t)2 * f->part_blocks * 8) == cudaSuccess;
     if (ok && mixed)
-        ok = cudaMalloc(&f->u2, (size_t)4 * f->cells * 8) == cudaSuccess && cudaMalloc(&f->bgf, nbgf * 4) == cudaSuccess;
+        ok = cudaMalloc(&f->u2, (size_t)4 * f->cells * 8) == cudaSuccess && cudaMalloc(&f->bgf, nbgf * 4) == cudaSuccess &&
+             cudaMalloc(&f->pert, (size_t)f->cells * 16) == cudaSuccess &&
+             cudaMalloc(&f->pert2, (size_t)f->cells * 16) == cudaSuccess;
     else if (ok)
         ok = cudaMalloc(&f->half, (size_t)17 * f->cells * 8) == cudaSuccess;
     if (!ok) {
@@ -686,6 +710,7 @@ extern "C" int adg_fv_set_state(adg_fv* f, const double* u, size_t count, int on
                            (cudaStream_t)stream),
            "fv_set_state");
     if (on_device == 0) ADG_CK(cudaStreamSynchronize((cudaStream_t)stream), "fv_set_state sync");
+    f->pert_stale = true;
     return ADG_OK;
 }
 
@@ -713,6 +738,7 @@ extern "C" int adg_fv_init_scenario(adg_fv* f, const adg_scenario* s, void* stre
     adg::k_fv_init<<<adg::fv_blocks(f->cells), 256, 0, (cudaStream_t)stream>>>(
         f->u, s->kind, s->A, s->a, s->xc, s->zc, f->d.R, cp, f->d.p0, f->d.theta0, P);
     ADG_CK(cudaGetLastError(), "fv_init_scenario launch");
+    f->pert_stale = true;
     return ADG_OK;
 }
 
@@ -723,10 +749,16 @@ extern "C" int adg_fv_step(adg_fv* f, double dt, void* stream) {
     cudaStream_t s = (cudaStream_t)stream;
     if (f->d.precision == ADG_PREC_MIXED) {
         const adg::FvMixed M = adg::fv_mixed(f, dt);
+        if (f->pert_stale) {
+            adg::k_fv_split<<<adg::fv_blocks(f->cells), 256, 0, s>>>(f->u, f->pert, M);
+            ADG_CK(cudaGetLastError(), "fv_step split");
+            f->pert_stale = false;
+        }
         const dim3 grid((f->d.nx + adg::kFvTx - 1) / adg::kFvTx, (f->d.ny + adg::kFvTy - 1) / adg::kFvTy);
-        adg::k_fv_step_mixed<<<grid, adg::kFvThreads, adg::kFvSmemBytes, s>>>(f->u, f->u2, M);
+        adg::k_fv_step_mixed<<<grid, adg::kFvThreads, adg::kFvSmemBytes, s>>>(f->u, f->u2, f->pert, f->pert2, M);
         ADG_CK(cudaGetLastError(), "fv_step mixed");
         std::swap(f->u, f->u2);
+        std::swap(f->pert, f->pert2);
         return ADG_OK;
     }
     const adg::FvPhys P = adg::fv_phys(f);
