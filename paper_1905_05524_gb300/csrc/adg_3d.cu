@@ -364,7 +364,7 @@ k3_predictor(const double* __restrict__ u, double* __restrict__ rvol, double* __
             for (int c = 0; c < kTr3; ++c)
                 if (c < 10 || c == 25 || wallface) tr[c * n2 + m] = rec[c];
         }
-    }
+    }    pdl_trigger();
 }
 
 struct Phys3f {
@@ -444,6 +444,7 @@ k3_corrector(double* __restrict__ u, const double* __restrict__ rvol, const doub
     const bool active = cell_raw < cells;
     const int cell = active ? cell_raw : cells - 1;
     const int ic0 = cell % P.nc[0], ic1 = (cell / P.nc[0]) % P.nc[1], ic2 = cell / (P.nc[0] * P.nc[1]);
+    pdl_wait();  // programmatic launch: the predictor's residual and traces are complete and visible
 
     for (int idx = node; idx < 6 * n2; idx += n3) {
         const int f = idx / n2, m = idx - f * n2;
@@ -915,7 +916,7 @@ k3_predictor_mixed(const double* __restrict__ u, double* __restrict__ rvol, doub
             for (int c = 0; c < kTr3; ++c)
                 if (c < 10 || c == 25 || wallface) tr[c * n2 + m] = rec[c];
         }
-    }
+    }    pdl_trigger();
 }
 
 // nodal values of a scenario: the 3D cosine bubble or the background
@@ -993,8 +994,20 @@ int launch3(bool pred, double* u, double* rvol, double* trace, int cells, double
         if (e != cudaSuccess) return (int)e;
         k3_predictor<N><<<blocks, C::threads, C::smem, s>>>(u, rvol, trace, cells, dt, B, P, bg);
     } else {
-        if (mixed) k3_corrector<N, true><<<blocks, C::threads, 0, s>>>(u, rvol, trace, cells, dt, t, B, P, bg, Pf);
-        else k3_corrector<N, false><<<blocks, C::threads, 0, s>>>(u, rvol, trace, cells, dt, t, B, P, bg, Pf);
+        // programmatic launch: scheduled while the predictor drains
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(blocks);
+        cfg.blockDim = dim3(C::threads);
+        cfg.dynamicSmemBytes = 0;
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        const cudaError_t e = mixed ? cudaLaunchKernelEx(&cfg, k3_corrector<N, true>, u, rvol, trace, cells, dt, t, B, P, bg, Pf)
+                                    : cudaLaunchKernelEx(&cfg, k3_corrector<N, false>, u, rvol, trace, cells, dt, t, B, P, bg, Pf);
+        if (e != cudaSuccess) return (int)e;
     }
     return (int)cudaGetLastError();
 }
