@@ -30,6 +30,7 @@ import json
 import os
 import statistics
 import subprocess
+import threading
 import sys
 import time
 
@@ -119,35 +120,67 @@ def measured_peaks_file():
 
 # ------------------------------------------------------------------ clocks
 class ClockSampler:
+    """nvidia-smi clock/throttle samples every 20 ms, read on a thread with
+    their arrival times; `begin()`/`end()` mark the timed region and `stop()`
+    reduces the samples that arrived inside it (the nearest one when the
+    region is shorter than the interval)."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    INTERVAL_MS = 20
 
     def __init__(self, gpu_index):
         self.gpu = gpu_index
         self.proc = None
+        self.lines = []          # (monotonic arrival time, csv line)
+        self.t0 = self.t1 = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append((time.monotonic(), line))
 
     def start(self):
+        """Start sampling; returns once the first sample has arrived (at most 5 s)."""
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", str(self.INTERVAL_MS)],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
+            return
+        self.reader = threading.Thread(target=self._read, daemon=True)
+        self.reader.start()
+        deadline = time.monotonic() + 5.0
+        while not self.lines and time.monotonic() < deadline and self.proc.poll() is None:
+            time.sleep(0.005)
+
+    def begin(self):
+        self.t0 = time.monotonic()
+
+    def end(self):
+        self.t1 = time.monotonic()
 
     def stop(self):
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        time.sleep(2 * self.INTERVAL_MS * 1e-3)   # let the sample after the region arrive
         self.proc.terminate()
         try:
-            out, _ = self.proc.communicate(timeout=5)
+            self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
-            out, _ = self.proc.communicate()
+            self.proc.wait()
+        self.reader.join(timeout=5)
+        t0 = self.t0 if self.t0 is not None else -float("inf")
+        t1 = self.t1 if self.t1 is not None else float("inf")
+        inside = [ln for (t, ln) in self.lines if t0 <= t <= t1]
+        if not inside and self.lines:
+            mid = 0.5 * (t0 + t1) if self.t0 is not None and self.t1 is not None else self.lines[-1][0]
+            inside = [min(self.lines, key=lambda x: abs(x[0] - mid))[1]]
         sm, smax, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in out.strip().splitlines():
+        for line in inside:
             parts = [p.strip() for p in line.split(",")]
             if len(parts) < 9:
                 continue
@@ -160,7 +193,8 @@ class ClockSampler:
                 if val.lower().startswith("active"):
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm),
+                "interval_ms": self.INTERVAL_MS}
 
 
 # ------------------------------------------------------------------ oracle arm
@@ -276,10 +310,11 @@ def run_form(prec_name, steps, warmup, dev, ws):
     m.set_state(u_init)          # timed steps start from the initial state
     torch.cuda.synchronize()
     clocks = ClockSampler(dev.index)
+    clocks.start()
     if ws > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    clocks.start()
+    clocks.begin()
     total = pred = corr = tvt = 0.0
     for _ in range(steps):
         flush.fill_(1.0)  # evict L2 between timed steps
@@ -287,6 +322,7 @@ def run_form(prec_name, steps, warmup, dev, ws):
         ev[3].synchronize()
         total += ev[0].elapsed_time(ev[3])
     torch.cuda.synchronize()
+    clocks.end()
     if ws > 1:
         torch.distributed.barrier()
     clk = clocks.stop()
@@ -941,7 +977,7 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
