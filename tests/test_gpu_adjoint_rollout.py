@@ -71,7 +71,7 @@ def test_rollout_gradient_vs_oracle_adjoint():
     assert r <= 1e-9, r
 
 
-def test_config4_gradient_vs_central_differences():
+def test_adjoint_run_27x27_gradient_vs_central_differences():
     """The adjoint run: degree 3, 27x27 cells, 200 steps, checkpoints every 20, 64
     probes; 32 seeded unit directions.  Step h = 1e-2 K along a unit
     direction over 11,664 DOFs: with h = 1e-6 the central difference is

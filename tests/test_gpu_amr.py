@@ -99,7 +99,7 @@ def _oracle_tv(o, u, var):
     return tv
 
 
-def test_config3_initial_mesh_and_tv_match_oracle():
+def test_two_bubble_initial_mesh_and_tv_match_oracle():
     """Two-bubble field, base 27x27 on [0,1000]^2, 2 levels, T_r = 2.5,
     T_c = -0.5: init -> TV -> refine twice (refine only), re-initialising from
     the analytic field; identical leaves and TV values."""
@@ -196,7 +196,7 @@ def test_mixed_adapt_step_periodic_matches_oracle():
     assert ((Ia - I0).abs() <= 1e-8 * I0.abs().clamp(min=1.0)).all(), Ia - I0
 
 
-def test_mixed_config3_run_tracks_fp64():
+def test_mixed_two_bubble_run_tracks_fp64():
     """The two-bubble AMR procedure (two bubbles, 27x27 base, two levels, initial
     mesh by init -> TV -> refine twice) with an FP64 and a mixed mesh in
     lockstep -- both adapted with the FP64 mesh's flags -- then 10 steps, a
@@ -234,7 +234,7 @@ def test_mixed_config3_run_tracks_fp64():
 
 
 @pytest.mark.parametrize("prec", [L.ADG_PREC_FP64, L.ADG_PREC_MIXED])
-def test_config3_mesh_step_matches_oracle(prec):
+def test_two_bubble_mesh_step_matches_oracle(prec):
     """A step on the full two-bubble adaptive mesh (27x27 base, two levels,
     built by init -> TV -> refine twice) against the oracle's tree: FP64 at
     1e-11, mixed within THETA_TOL of theta' and 1e-9 of rho."""

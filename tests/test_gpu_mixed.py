@@ -47,7 +47,7 @@ def test_mixed_vs_oracle_bubble_small():
     assert err <= THETA_TOL, err
 
 
-def test_mixed_vs_fp64_gpu_config2_400_steps():
+def test_mixed_vs_fp64_gpu_warm_bubble_81x81_400_steps():
     """The warm bubble at full size (degree 5, 81x81, CFL 0.25): 400 steps of the mixed path against 400
     steps of the FP64 GPU path (itself parity-checked against the oracle)."""
     res = {}

@@ -104,7 +104,7 @@ def test_step_steady_manufactured_all_degrees(degree):
     assert_close(a, b, what=f"N={degree}")
 
 
-def test_step_config1_20_steps():
+def test_step_steady_manufactured_9x9_20_steps():
     """Steady manufactured case: N = 3, 9x9 periodic [0,10]^2, steady manufactured, CFL 0.5, 20 steps."""
     cfg = steady_manufactured_config(degree=3, nx=9, ny=9)
     o = oracle_for(cfg)
@@ -154,7 +154,7 @@ def test_two_bubbles_walls_degree3():
     assert_close(a, b, what="two bubbles")
 
 
-def test_config2_full_size_two_steps():
+def test_warm_bubble_81x81_full_size_two_steps():
     """The warm bubble at full size (N = 5, 81x81, walls, cosine bubble), the launch
     configuration bench.py times: 2 steps compared element by element."""
     cfg = atmosphere_config(degree=5, nx=81, ny=81)
