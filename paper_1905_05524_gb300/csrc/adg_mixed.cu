@@ -106,7 +106,7 @@ struct MixCfg {
     // padded to 16 (mod 32) floats: neighbouring cells of one warp then fall on
     // disjoint banks in the row contractions
     static constexpr int np = n + (n & 1);
-    static constexpr int raw = 4 * n * 4 * n * np;
+    static constexpr int raw = 3 * n * 4 * n * np;
     static constexpr int stride = raw + ((16 - raw % 32) + 32) % 32;
     static constexpr size_t smem_pred = (size_t)cpb * stride * sizeof(float);
     // minimum resident blocks asked of the register allocator (measured: at
@@ -119,12 +119,14 @@ struct MixCfg {
 // Predictor body for the tile of CPB cells starting at cell c0 (one thread per
 // spatial node); shared by the per-mesh kernel and the batched persistent one.
 //
-// Shared-memory layout per cell (floats): the iterate q' in row-major [v][j][i]
-// and in transposed [v][i][j] form, the x-flux F row-major and the y-flux G
-// transposed, each for n time slices, rows padded to an even length NP.  Every
-// contraction then reads one contiguous row with 8-byte vector loads: the
-// x-derivative from the row-major copy, the y-derivative from the transposed
-// copy (the shared-memory instruction count, which bounds this kernel, halves).
+// Shared-memory layout per cell (floats): the iterate q' and the fluxes F and G,
+// each row-major [k][v][j][i] for n time slices, rows padded to an even length
+// NP.  x-contractions read one contiguous row with 8-byte vector loads,
+// y-contractions a column with 4-byte loads (the lanes of one column read the
+// same word: a broadcast, one wavefront per load, the same shared-memory data
+// rate as vector loads of a transposed copy).  Shared-memory wavefronts bound
+// this kernel; keeping no transposed copies saves their bank-conflicting
+// stores and a quarter of the footprint.
 template <int N, int CPB>
 __device__ __forceinline__ void predictor_mixed_body(const double* __restrict__ u, float* __restrict__ rvol,
                                                      float* __restrict__ trace, int cells, int c0, float dt,
@@ -139,9 +141,8 @@ __device__ __forceinline__ void predictor_mixed_body(const double* __restrict__ 
     const bool active = cell_raw < cells;
     const int cell = active ? cell_raw : cells - 1;
     float* Q = smf + (size_t)cl * MixCfg<N, CPB>::stride;  // [k][v][j][i]
-    float* QT = Q + n * SLP;                               // [k][v][i][j]
-    float* Fs = QT + n * SLP;                              // [k][v][j][i]
-    float* GT = Fs + n * SLP;                              // [k][v][i][j]
+    float* Fs = Q + n * SLP;                               // [k][v][j][i]
+    float* Gs = Fs + n * SLP;                              // [k][v][j][i]
     const int ix = cell % P.nx, iy = cell / P.nx;
     const int row = iy * n + j;
     const float x = P.x0 + (ix + B.xi[i]) * P.hx;
@@ -150,10 +151,10 @@ __device__ __forceinline__ void predictor_mixed_body(const double* __restrict__ 
     const double rb64 = bg.rb[row], Eb64 = bg.Eb[row];
     const float rb = f64_to_f32(rb64), Eb = f64_to_f32(Eb64), pb = bg.pb[row];
     const float dzr = bg.dzr[row], dzE = bg.dzE[row];
-    const int rm = j * NP + i, tm = i * NP + j;  // this node in row-major / transposed rows
+    const int rm = j * NP + i;  // this node in the row-major slices
 
     if (NP != n) {  // zero the row padding once (it is multiplied by D[.][n] = 0)
-        for (int a = node; a < 4 * n * 4 * n; a += n2) Q[a * NP + n] = 0.f;
+        for (int a = node; a < 3 * n * 4 * n; a += n2) Q[a * NP + n] = 0.f;
     }
     // FP64 perturbation split, then FP32 from here on
     float up[4];
@@ -163,10 +164,7 @@ __device__ __forceinline__ void predictor_mixed_body(const double* __restrict__ 
     up[2] = f64_to_f32(uc[2 * n2 + node]);
     up[3] = f64_to_f32(uc[3 * n2 + node] - Eb64);
 #pragma unroll
-    for (int v = 0; v < 4; ++v) {
-        Q[v * RS + rm] = up[v];
-        QT[v * RS + tm] = up[v];
-    }
+    for (int v = 0; v < 4; ++v) Q[v * RS + rm] = up[v];
     float Sm[4] = {0.f, 0.f, 0.f, 0.f};
     if (P.source == ADG_SRC_STEADY) {
         const float k = 6.283185307179586f / P.sL;
@@ -202,6 +200,16 @@ __device__ __forceinline__ void predictor_mixed_body(const double* __restrict__ 
         for (int p = 1; p < NH; ++p) s = fma2(d[p], r2[p], s);
         return s.x + s.y;
     };
+    // the same for the column starting at c (entries NP apart): pairs of
+    // scalar loads, the odd last entry alone
+    auto coldot = [&](const float* c, const float2(&d)[NH]) {
+        float2 s = mul2(d[0], make_float2(c[0], c[NP]));
+#pragma unroll
+        for (int p = 1; p < n / 2; ++p) s = fma2(d[p], make_float2(c[2 * p * NP], c[(2 * p + 1) * NP]), s);
+        float r = s.x + s.y;
+        if (n & 1) r = fmaf(d[NH - 1].x, c[(n - 1) * NP], r);
+        return r;
+    };
     // slice k alone (sweep 1: the iterate is constant in time)
     auto eval_node = [&](int k, float q[4], float gx[4], float gy[4], FluxF& f) {
 #pragma unroll
@@ -209,7 +217,7 @@ __device__ __forceinline__ void predictor_mixed_body(const double* __restrict__ 
             const float* Qv = Q + k * SLP + v * RS;
             q[v] = Qv[rm];
             gx[v] = rowdot(Qv + j * NP, dI);
-            gy[v] = rowdot(QT + k * SLP + v * RS + i * NP, dJ);
+            gy[v] = coldot(Qv + i, dJ);
         }
         gy[0] += dzr;
         gy[3] += dzE;
@@ -221,11 +229,9 @@ __device__ __forceinline__ void predictor_mixed_body(const double* __restrict__ 
         for (int v = 0; v < 4; ++v) {
             const float* Q0 = Q + k0 * SLP + v * RS;
             const float* Q1 = Q + k1 * SLP + v * RS;
-            const float* T0 = QT + k0 * SLP + v * RS + i * NP;
-            const float* T1 = QT + k1 * SLP + v * RS + i * NP;
             q[v] = make_float2(Q0[rm], Q1[rm]);
             gx[v] = make_float2(rowdot(Q0 + j * NP, dI), rowdot(Q1 + j * NP, dI));
-            gy[v] = make_float2(rowdot(T0, dJ), rowdot(T1, dJ));
+            gy[v] = make_float2(coldot(Q0 + i, dJ), coldot(Q1 + i, dJ));
         }
         gy[0] = add2(gy[0], bc2(dzr));
         gy[3] = add2(gy[3], bc2(dzE));
@@ -235,28 +241,25 @@ __device__ __forceinline__ void predictor_mixed_body(const double* __restrict__ 
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
             Fs[k * SLP + v * RS + rm] = f.F[v];
-            GT[k * SLP + v * RS + tm] = f.G[v];
+            Gs[k * SLP + v * RS + rm] = f.G[v];
         }
     };
     auto store_flux_pair = [&](int k0, bool second, const FluxF2& f) {
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
             Fs[k0 * SLP + v * RS + rm] = f.F[v].x;
-            GT[k0 * SLP + v * RS + tm] = f.G[v].x;
+            Gs[k0 * SLP + v * RS + rm] = f.G[v].x;
             if (second) {
                 Fs[(k0 + 1) * SLP + v * RS + rm] = f.F[v].y;
-                GT[(k0 + 1) * SLP + v * RS + tm] = f.G[v].y;
+                Gs[(k0 + 1) * SLP + v * RS + rm] = f.G[v].y;
             }
         }
     };
     // -dF/dx - dG/dy of slice k at this node
     auto divergence = [&](int k, int v) {
-        return -(rowdot(Fs + k * SLP + v * RS + j * NP, dI) + rowdot(GT + k * SLP + v * RS + i * NP, dJ));
+        return -(rowdot(Fs + k * SLP + v * RS + j * NP, dI) + coldot(Gs + k * SLP + v * RS + i, dJ));
     };
-    auto store_q = [&](int l, int v, float val) {
-        Q[l * SLP + v * RS + rm] = val;
-        QT[l * SLP + v * RS + tm] = val;
-    };
+    auto store_q = [&](int l, int v, float val) { Q[l * SLP + v * RS + rm] = val; };
 
     {  // sweep 1: iterate constant in time
         float q[4], gx[4], gy[4];
