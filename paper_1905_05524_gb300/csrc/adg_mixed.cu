@@ -106,7 +106,8 @@ struct MixCfg {
     // padded to 16 (mod 32) floats: neighbouring cells of one warp then fall on
     // disjoint banks in the row contractions
     static constexpr int np = n + (n & 1);
-    static constexpr int raw = 3 * n * 4 * n * np;
+    static constexpr int npair = (n + 1) / 2;
+    static constexpr int raw = 3 * npair * 4 * n * n * 2;
     static constexpr int stride = raw + ((16 - raw % 32) + 32) % 32;
     static constexpr size_t smem_pred = (size_t)cpb * stride * sizeof(float);
     // minimum resident blocks asked of the register allocator (measured: at
@@ -119,14 +120,14 @@ struct MixCfg {
 // Predictor body for the tile of CPB cells starting at cell c0 (one thread per
 // spatial node); shared by the per-mesh kernel and the batched persistent one.
 //
-// Shared-memory layout per cell (floats): the iterate q' and the fluxes F and G,
-// each row-major [k][v][j][i] for n time slices, rows padded to an even length
-// NP.  x-contractions read one contiguous row with 8-byte vector loads,
-// y-contractions a column with 4-byte loads (the lanes of one column read the
-// same word: a broadcast, one wavefront per load, the same shared-memory data
-// rate as vector loads of a transposed copy).  Shared-memory wavefronts bound
-// this kernel; keeping no transposed copies saves their bank-conflicting
-// stores and a quarter of the footprint.
+// Shared-memory layout per cell: the iterate q' and the fluxes F and G, each
+// row-major [h][v][j][i] of float2 holding time slices (2h, 2h+1) -- the
+// pairs the packed FP32x2 flux evaluation works on.  One 8-byte load then
+// serves both slices of a contraction term: x-contractions walk a row (the
+// lanes of one row read the same entry, a broadcast), y-contractions a column
+// (the lanes of one column likewise), with no transposed copies.  For odd n
+// the last pair's second slice repeats slice n-1 and meets the zero padding
+// of Kw and w.  The shared-memory data path bounds this kernel.
 template <int N, int CPB>
 __device__ __forceinline__ void predictor_mixed_body(const double* __restrict__ u, float* __restrict__ rvol,
                                                      float* __restrict__ trace, int cells, int c0, float dt,
@@ -140,9 +141,10 @@ __device__ __forceinline__ void predictor_mixed_body(const double* __restrict__ 
     const int cell_raw = c0 + cl;
     const bool active = cell_raw < cells;
     const int cell = active ? cell_raw : cells - 1;
-    float* Q = smf + (size_t)cl * MixCfg<N, CPB>::stride;  // [k][v][j][i]
-    float* Fs = Q + n * SLP;                               // [k][v][j][i]
-    float* Gs = Fs + n * SLP;                              // [k][v][j][i]
+    constexpr int NPAIR = MixCfg<N, CPB>::npair, PS = 4 * n2;  // slice pairs, pair stride (float2)
+    float2* Q2 = reinterpret_cast<float2*>(smf + (size_t)cl * MixCfg<N, CPB>::stride);  // [h][v][j][i]
+    float2* F2 = Q2 + NPAIR * PS;                                                       // [h][v][j][i]
+    float2* G2 = F2 + NPAIR * PS;                                                       // [h][v][j][i]
     const int ix = cell % P.nx, iy = cell / P.nx;
     const int row = iy * n + j;
     const float x = P.x0 + (ix + B.xi[i]) * P.hx;
@@ -151,11 +153,6 @@ __device__ __forceinline__ void predictor_mixed_body(const double* __restrict__ 
     const double rb64 = bg.rb[row], Eb64 = bg.Eb[row];
     const float rb = f64_to_f32(rb64), Eb = f64_to_f32(Eb64), pb = bg.pb[row];
     const float dzr = bg.dzr[row], dzE = bg.dzE[row];
-    const int rm = j * NP + i;  // this node in the row-major slices
-
-    if (NP != n) {  // zero the row padding once (it is multiplied by D[.][n] = 0)
-        for (int a = node; a < 3 * n * 4 * n; a += n2) Q[a * NP + n] = 0.f;
-    }
     // FP64 perturbation split, then FP32 from here on
     float up[4];
     const double* uc = u + (size_t)cell * SL;
@@ -164,7 +161,7 @@ __device__ __forceinline__ void predictor_mixed_body(const double* __restrict__ 
     up[2] = f64_to_f32(uc[2 * n2 + node]);
     up[3] = f64_to_f32(uc[3 * n2 + node] - Eb64);
 #pragma unroll
-    for (int v = 0; v < 4; ++v) Q[v * RS + rm] = up[v];
+    for (int v = 0; v < 4; ++v) Q2[v * n2 + node] = make_float2(up[v], up[v]);
     float Sm[4] = {0.f, 0.f, 0.f, 0.f};
     if (P.source == ADG_SRC_STEADY) {
         const float k = 6.283185307179586f / P.sL;
@@ -182,116 +179,87 @@ __device__ __forceinline__ void predictor_mixed_body(const double* __restrict__ 
     }
     __syncthreads();
 
-    // This node's rows of D, pre-scaled by 1/h, as packed pairs (the padded
-    // entry D[.][n] is zero).
-    constexpr int NH = NP / 2;
-    float2 dI[NH], dJ[NH];
+    // This node's rows of D, pre-scaled by 1/h
+    float dI[n], dJ[n];
 #pragma unroll
-    for (int p = 0; p < NH; ++p) {
-        dI[p] = mul2(make_float2(B.D[i][2 * p], B.D[i][2 * p + 1]), bc2(P.inv_hx));
-        dJ[p] = mul2(make_float2(B.D[j][2 * p], B.D[j][2 * p + 1]), bc2(P.inv_hy));
+    for (int p = 0; p < n; ++p) {
+        dI[p] = B.D[i][p] * P.inv_hx;
+        dJ[p] = B.D[j][p] * P.inv_hy;
     }
-    // scaled D-contraction of the contiguous row starting at r: pairs of
-    // adjacent entries, then one horizontal add
-    auto rowdot = [&](const float* r, const float2(&d)[NH]) {
-        const float2* r2 = reinterpret_cast<const float2*>(r);
-        float2 s = mul2(d[0], r2[0]);
+    // scaled D-contraction along the row (x) or the column (y) through this
+    // node of one slice pair and variable
+    auto xdot = [&](const float2* S) {
+        const float2* r = S + j * n;
+        float2 s = mul2(bc2(dI[0]), r[0]);
 #pragma unroll
-        for (int p = 1; p < NH; ++p) s = fma2(d[p], r2[p], s);
-        return s.x + s.y;
+        for (int p = 1; p < n; ++p) s = fma2(bc2(dI[p]), r[p], s);
+        return s;
     };
-    // the same for the column starting at c (entries NP apart): pairs of
-    // scalar loads, the odd last entry alone
-    auto coldot = [&](const float* c, const float2(&d)[NH]) {
-        float2 s = mul2(d[0], make_float2(c[0], c[NP]));
+    auto ydot = [&](const float2* S) {
+        const float2* c = S + i;
+        float2 s = mul2(bc2(dJ[0]), c[0]);
 #pragma unroll
-        for (int p = 1; p < n / 2; ++p) s = fma2(d[p], make_float2(c[2 * p * NP], c[(2 * p + 1) * NP]), s);
-        float r = s.x + s.y;
-        if (n & 1) r = fmaf(d[NH - 1].x, c[(n - 1) * NP], r);
-        return r;
+        for (int p = 1; p < n; ++p) s = fma2(bc2(dJ[p]), c[p * n], s);
+        return s;
     };
-    // slice k alone (sweep 1: the iterate is constant in time)
-    auto eval_node = [&](int k, float q[4], float gx[4], float gy[4], FluxF& f) {
+    // both slices of pair h at this node
+    auto eval_pair = [&](int h, float2 q[4], float2 gx[4], float2 gy[4], FluxF2& f) {
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
-            const float* Qv = Q + k * SLP + v * RS;
-            q[v] = Qv[rm];
-            gx[v] = rowdot(Qv + j * NP, dI);
-            gy[v] = coldot(Qv + i, dJ);
-        }
-        gy[0] += dzr;
-        gy[3] += dzE;
-        ns_flux_pert(q, gx, gy, z, rb, Eb, pb, P, f);
-    };
-    // slices k0 and k1 together (k1 = k0 when n is odd and k0 is the last)
-    auto eval_pair = [&](int k0, int k1, float2 q[4], float2 gx[4], float2 gy[4], FluxF2& f) {
-#pragma unroll
-        for (int v = 0; v < 4; ++v) {
-            const float* Q0 = Q + k0 * SLP + v * RS;
-            const float* Q1 = Q + k1 * SLP + v * RS;
-            q[v] = make_float2(Q0[rm], Q1[rm]);
-            gx[v] = make_float2(rowdot(Q0 + j * NP, dI), rowdot(Q1 + j * NP, dI));
-            gy[v] = make_float2(coldot(Q0 + i, dJ), coldot(Q1 + i, dJ));
+            const float2* S = Q2 + h * PS + v * n2;
+            q[v] = S[node];
+            gx[v] = xdot(S);
+            gy[v] = ydot(S);
         }
         gy[0] = add2(gy[0], bc2(dzr));
         gy[3] = add2(gy[3], bc2(dzE));
         ns_flux_pert2(q, gx, gy, z, rb, Eb, pb, P, f);
     };
-    auto store_flux = [&](int k, const FluxF& f) {
+    auto store_flux_pair = [&](int h, const FluxF2& f) {
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
-            Fs[k * SLP + v * RS + rm] = f.F[v];
-            Gs[k * SLP + v * RS + rm] = f.G[v];
+            F2[h * PS + v * n2 + node] = f.F[v];
+            G2[h * PS + v * n2 + node] = f.G[v];
         }
     };
-    auto store_flux_pair = [&](int k0, bool second, const FluxF2& f) {
-#pragma unroll
-        for (int v = 0; v < 4; ++v) {
-            Fs[k0 * SLP + v * RS + rm] = f.F[v].x;
-            Gs[k0 * SLP + v * RS + rm] = f.G[v].x;
-            if (second) {
-                Fs[(k0 + 1) * SLP + v * RS + rm] = f.F[v].y;
-                Gs[(k0 + 1) * SLP + v * RS + rm] = f.G[v].y;
-            }
-        }
+    // dF/dx + dG/dy of slice pair h at this node
+    auto divergence = [&](int h, int v) { return add2(xdot(F2 + h * PS + v * n2), ydot(G2 + h * PS + v * n2)); };
+    // slices 2g, 2g+1 of variable v (for odd n the slot past the last slice
+    // repeats it)
+    auto store_q_pair = [&](int g, int v, float a, float b) {
+        Q2[g * PS + v * n2 + node] = make_float2(a, 2 * g + 1 < n ? b : a);
     };
-    // -dF/dx - dG/dy of slice k at this node
-    auto divergence = [&](int k, int v) {
-        return -(rowdot(Fs + k * SLP + v * RS + j * NP, dI) + coldot(Gs + k * SLP + v * RS + i, dJ));
-    };
-    auto store_q = [&](int l, int v, float val) { Q[l * SLP + v * RS + rm] = val; };
 
-    {  // sweep 1: iterate constant in time
-        float q[4], gx[4], gy[4];
-        FluxF f;
-        eval_node(0, q, gx, gy, f);
-        store_flux(0, f);
+    {  // sweep 1: iterate constant in time (both slices of pair 0 hold it)
+        float2 q[4], gx[4], gy[4];
+        FluxF2 f;
+        eval_pair(0, q, gx, gy, f);
+        store_flux_pair(0, f);
         __syncthreads();
         float R0[4];
 #pragma unroll
-        for (int v = 0; v < 4; ++v) R0[v] = f.S[v] + Sm[v] + divergence(0, v);
+        for (int v = 0; v < 4; ++v) R0[v] = (v == 2 ? f.S2.x : 0.f) + Sm[v] - divergence(0, v).x;
 #pragma unroll
-        for (int l = 0; l < n; ++l) {
+        for (int g = 0; g < NPAIR; ++g) {
+            const int l1 = 2 * g + 1 < n ? 2 * g + 1 : 2 * g;
 #pragma unroll
-            for (int v = 0; v < 4; ++v) store_q(l, v, fmaf(dt, B.Kw1[l] * R0[v], up[v]));
+            for (int v = 0; v < 4; ++v)
+                store_q_pair(g, v, fmaf(dt, B.Kw1[2 * g] * R0[v], up[v]), fmaf(dt, B.Kw1[l1] * R0[v], up[v]));
         }
         __syncthreads();
     }
-    // sweeps 2..n on pairs of time slices (for odd n the last pair's second
-    // lane repeats slice n-1 and meets the zero padding of Kw and w).  The
-    // residual is contracted in time one variable at a time, so only the
-    // z-momentum source of each slice pair stays live across the barrier.
-    constexpr int NPAIR = (n + 1) / 2;
+    // sweeps 2..n on the slice pairs; the residual is contracted in time one
+    // variable at a time, so only the z-momentum source of each pair stays
+    // live across the barrier
 #pragma unroll 1
     for (int r = 1; r < n; ++r) {
         float2 S2h[NPAIR];
 #pragma unroll
         for (int h = 0; h < NPAIR; ++h) {
-            const int k0 = 2 * h, k1 = 2 * h + 1 < n ? 2 * h + 1 : 2 * h;
             float2 q[4], gx[4], gy[4];
             FluxF2 f;
-            eval_pair(k0, k1, q, gx, gy, f);
-            store_flux_pair(k0, 2 * h + 1 < n, f);
+            eval_pair(h, q, gx, gy, f);
+            store_flux_pair(h, f);
             S2h[h] = f.S2;
         }
         __syncthreads();
@@ -300,17 +268,21 @@ __device__ __forceinline__ void predictor_mixed_body(const double* __restrict__ 
             float2 R2[NPAIR];  // slices 2h, 2h+1 of variable v
 #pragma unroll
             for (int h = 0; h < NPAIR; ++h) {
-                const int k1 = 2 * h + 1 < n ? 2 * h + 1 : 2 * h;
                 R2[h] = bc2(Sm[v]);
                 if (v == 2) R2[h] = add2(R2[h], S2h[h]);
-                R2[h] = add2(R2[h], make_float2(divergence(2 * h, v), divergence(k1, v)));
+                R2[h] = fma2(bc2(-1.f), divergence(h, v), R2[h]);
             }
 #pragma unroll
-            for (int l = 0; l < n; ++l) {
-                float2 acc = mul2(make_float2(B.Kw[l][0], B.Kw[l][1]), R2[0]);
+            for (int g = 0; g < NPAIR; ++g) {
+                const int l0 = 2 * g, l1 = 2 * g + 1 < n ? 2 * g + 1 : 2 * g;
+                float2 a0 = mul2(make_float2(B.Kw[l0][0], B.Kw[l0][1]), R2[0]);
+                float2 a1 = mul2(make_float2(B.Kw[l1][0], B.Kw[l1][1]), R2[0]);
 #pragma unroll
-                for (int h = 1; h < NPAIR; ++h) acc = fma2(make_float2(B.Kw[l][2 * h], B.Kw[l][2 * h + 1]), R2[h], acc);
-                store_q(l, v, fmaf(dt, acc.x + acc.y, up[v]));
+                for (int h = 1; h < NPAIR; ++h) {
+                    a0 = fma2(make_float2(B.Kw[l0][2 * h], B.Kw[l0][2 * h + 1]), R2[h], a0);
+                    a1 = fma2(make_float2(B.Kw[l1][2 * h], B.Kw[l1][2 * h + 1]), R2[h], a1);
+                }
+                store_q_pair(g, v, fmaf(dt, a0.x + a0.y, up[v]), fmaf(dt, a1.x + a1.y, up[v]));
             }
         }
         __syncthreads();
@@ -324,11 +296,10 @@ __device__ __forceinline__ void predictor_mixed_body(const double* __restrict__ 
     for (int v = 0; v < 4; ++v) qb[v] = Fb[v] = Gb[v] = qxb[v] = qyb[v] = 0.f;
 #pragma unroll
     for (int h = 0; h < NPAIR; ++h) {
-        const int k0 = 2 * h, k1 = 2 * h + 1 < n ? 2 * h + 1 : 2 * h;
         float2 q[4], gx[4], gy[4];
         FluxF2 f;
-        eval_pair(k0, k1, q, gx, gy, f);
-        const float w0 = B.w[k0], w1 = B.w[2 * h + 1];  // w[n] = 0 pads an odd n
+        eval_pair(h, q, gx, gy, f);
+        const float w0 = B.w[2 * h], w1 = B.w[2 * h + 1];  // w[n] = 0 pads an odd n
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
             qb[v] = fmaf(w1, q[v].y, fmaf(w0, q[v].x, qb[v]));
@@ -344,7 +315,8 @@ __device__ __forceinline__ void predictor_mixed_body(const double* __restrict__ 
     Sb[2] += Sz;
     __syncthreads();
     // time averages, row-major with padded rows: slots 0..4 = qbar, Fbar, Gbar, qxbar, qybar
-    float* A = Q;
+    float* A = reinterpret_cast<float*>(Q2);
+    const int rm = j * NP + i;
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
         A[0 * SLP + v * RS + rm] = qb[v];
