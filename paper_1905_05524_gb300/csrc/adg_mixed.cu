@@ -102,13 +102,17 @@ struct MixCfg {
     static constexpr int cpb_default = tv_cpb(N);
     static constexpr int cpb = CPB_ ? CPB_ : cpb_default;
     static constexpr int threads = cpb * n * n;
-    // rows padded to an even length (8-byte vector loads); per-cell smem stride
-    // padded to 16 (mod 32) floats: neighbouring cells of one warp then fall on
-    // disjoint banks in the row contractions
+    // time averages: rows padded to an even length.  Per-cell shared-memory
+    // stride: the slice-pair arrays, padded to a bank offset (mod 32 floats)
+    // between neighbouring cells.  Measured per degree: 8 at N = 2 and 18 at
+    // N = 4 (where a count of bank conflicts per half-warp of 8-byte accesses
+    // predicts fewer than at 16) beat 16 by 5%; at N = 5 the same count
+    // favours 8, which measured 2% slower, so 16 stays there and elsewhere
     static constexpr int np = n + (n & 1);
     static constexpr int npair = (n + 1) / 2;
     static constexpr int raw = 3 * npair * 4 * n * n * 2;
-    static constexpr int stride = raw + ((16 - raw % 32) + 32) % 32;
+    static constexpr int bank_off = cpb != cpb_default ? 16 : N == 2 ? 8 : N == 4 ? 18 : 16;
+    static constexpr int stride = raw + ((bank_off - raw % 32) + 32) % 32;
     static constexpr size_t smem_pred = (size_t)cpb * stride * sizeof(float);
     // minimum resident blocks asked of the register allocator (measured: at
     // N = 5 the four blocks that shared memory admits beat three blocks
