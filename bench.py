@@ -84,7 +84,7 @@ def predictor_flops_per_cell(n):
 # DRAM bytes (read + write) of one predictor launch on this workload, from one
 # ncu capture of the kernel as it stands (the predictor summaries under profiles/);
 # set to None whenever the kernel changes after the capture.
-PREDICTOR_TRAFFIC = {"fp64": 7810304 + 1280, "mixed": None}
+PREDICTOR_TRAFFIC = {"fp64": 7810304 + 1280, "mixed": 7631872 + 0}
 
 
 def measure_fma_peaks():
