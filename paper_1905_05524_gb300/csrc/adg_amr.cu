@@ -392,6 +392,17 @@ k_predictor_amr(const double* __restrict__ u, double* __restrict__ rvol, double*
 // the node's row, which does not vary along x; y-faces: the FP64
 // extrapolation of the leaf's nodal background) with the Rusanov speed in
 // FP32 -- so the FP64 corrector with its hanging faces runs unchanged.
+// Shared memory of the mixed adaptive predictor per leaf: q', F and G as
+// float2 pairs of time slices, padded to a bank offset of 16 (mod 32 floats)
+// between neighbouring leaves.
+template <int N>
+struct AmrMixCfg {
+    static constexpr int n = N + 1;
+    static constexpr int npair = (n + 1) / 2;
+    static constexpr int raw = 3 * npair * 4 * n * n * 2;
+    static constexpr int stride = raw + ((16 - raw % 32) + 32) % 32;
+};
+
 // Per-leaf tables: mb64 [leaves][n][2] (rhobar, Ebar) then [leaves][2 N, S][2]
 // extrapolated (rhobar, Ebar); mbf [leaves][n][3] (pbar, d rhobar/dz,
 // d Ebar/dz) then [leaves][2 N, S][2] (extrapolated rhobar, (gamma-1)(Ebar -
@@ -409,9 +420,10 @@ k_predictor_amr_mixed(const double* __restrict__ u, double* __restrict__ rvol, d
     const int cell_raw = blockIdx.x * CPB + cl;
     const bool active = cell_raw < cells;
     const int cell = active ? cell_raw : cells - 1;
-    float* Q = smf + (size_t)cl * 3 * n * SL;  // [k][v][j][i]
-    float* Fs = Q + n * SL;
-    float* Gs = Fs + n * SL;
+    constexpr int NPAIR = AmrMixCfg<N>::npair, PS = 4 * n2;  // slice pairs, pair stride (float2)
+    float2* Q2 = reinterpret_cast<float2*>(smf + (size_t)cl * AmrMixCfg<N>::stride);  // [h][v][j][i]
+    float2* F2 = Q2 + NPAIR * PS;                                                      // [h][v][j][i]
+    float2* G2 = F2 + NPAIR * PS;                                                      // [h][v][j][i]
     const double hx = geo[cell * 4 + 2], hy = geo[cell * 4 + 3], yorg = geo[cell * 4 + 1];
     const float inv_hx = (float)(1.0 / hx), inv_hy = (float)(1.0 / hy);
     const float z = (float)(yorg + (double)B.xi[j] * hy);
@@ -429,111 +441,130 @@ k_predictor_amr_mixed(const double* __restrict__ u, double* __restrict__ rvol, d
         up[3] = f64_to_f32(__dsub_rn(uc[3 * n2 + node], Eb64));
     }
 #pragma unroll
-    for (int v = 0; v < 4; ++v) Q[v * n2 + node] = up[v];
+    for (int v = 0; v < 4; ++v) Q2[v * n2 + node] = make_float2(up[v], up[v]);
     __syncthreads();
 
-    auto eval = [&](const float* Qk, float q[4], float gx[4], float gy[4], FluxF& f) {
+    // the uniform mixed predictor's slice-pair scheme (adg_mixed.cu) with this
+    // leaf's spacing and background
+    float dI[n], dJ[n];
+#pragma unroll
+    for (int p = 0; p < n; ++p) {
+        dI[p] = B.D[i][p] * inv_hx;
+        dJ[p] = B.D[j][p] * inv_hy;
+    }
+    auto xdot = [&](const float2* S) {
+        const float2* r = S + j * n;
+        float2 s = mul2(bc2(dI[0]), r[0]);
+#pragma unroll
+        for (int p = 1; p < n; ++p) s = fma2(bc2(dI[p]), r[p], s);
+        return s;
+    };
+    auto ydot = [&](const float2* S) {
+        const float2* c = S + i;
+        float2 s = mul2(bc2(dJ[0]), c[0]);
+#pragma unroll
+        for (int p = 1; p < n; ++p) s = fma2(bc2(dJ[p]), c[p * n], s);
+        return s;
+    };
+    auto eval_pair = [&](int h, float2 q[4], float2 gx[4], float2 gy[4], FluxF2& f) {
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
-            const float* Qv = Qk + v * n2;
-            q[v] = Qv[node];
-            float sx = 0.f, sy = 0.f;
-#pragma unroll
-            for (int p = 0; p < n; ++p) {
-                sx = fmaf(B.D[i][p], Qv[j * n + p], sx);
-                sy = fmaf(B.D[j][p], Qv[p * n + i], sy);
-            }
-            gx[v] = sx * inv_hx;
-            gy[v] = sy * inv_hy;
+            const float2* S = Q2 + h * PS + v * n2;
+            q[v] = S[node];
+            gx[v] = xdot(S);
+            gy[v] = ydot(S);
         }
-        gy[0] += dzr;
-        gy[3] += dzE;
-        ns_flux_pert(q, gx, gy, z, rb, Eb, pb, P, f);
+        gy[0] = add2(gy[0], bc2(dzr));
+        gy[3] = add2(gy[3], bc2(dzE));
+        ns_flux_pert2(q, gx, gy, z, rb, Eb, pb, P, f);
     };
-    auto divergence = [&](int k, int v) {
-        const float* Fv = Fs + k * SL + v * n2;
-        const float* Gv = Gs + k * SL + v * n2;
-        float sx = 0.f, sy = 0.f;
+    auto store_flux_pair = [&](int h, const FluxF2& f) {
 #pragma unroll
-        for (int p = 0; p < n; ++p) {
-            sx = fmaf(B.D[i][p], Fv[j * n + p], sx);
-            sy = fmaf(B.D[j][p], Gv[p * n + i], sy);
+        for (int v = 0; v < 4; ++v) {
+            F2[h * PS + v * n2 + node] = f.F[v];
+            G2[h * PS + v * n2 + node] = f.G[v];
         }
-        return -(sx * inv_hx + sy * inv_hy);
+    };
+    auto divergence = [&](int h, int v) { return add2(xdot(F2 + h * PS + v * n2), ydot(G2 + h * PS + v * n2)); };
+    auto store_q_pair = [&](int g, int v, float a, float b) {
+        Q2[g * PS + v * n2 + node] = make_float2(a, 2 * g + 1 < n ? b : a);
     };
 
-    {  // sweep 1: the iterate is constant in time
-        float q[4], gx[4], gy[4];
-        FluxF f;
-        eval(Q, q, gx, gy, f);
-#pragma unroll
-        for (int v = 0; v < 4; ++v) {
-            Fs[v * n2 + node] = f.F[v];
-            Gs[v * n2 + node] = f.G[v];
-        }
+    {  // sweep 1: iterate constant in time (both slices of pair 0 hold it)
+        float2 q[4], gx[4], gy[4];
+        FluxF2 f;
+        eval_pair(0, q, gx, gy, f);
+        store_flux_pair(0, f);
         __syncthreads();
         float R0[4];
 #pragma unroll
-        for (int v = 0; v < 4; ++v) R0[v] = f.S[v] + divergence(0, v);
+        for (int v = 0; v < 4; ++v) R0[v] = (v == 2 ? f.S2.x : 0.f) - divergence(0, v).x;
 #pragma unroll
-        for (int l = 0; l < n; ++l)
+        for (int g = 0; g < NPAIR; ++g) {
+            const int l1 = 2 * g + 1 < n ? 2 * g + 1 : 2 * g;
 #pragma unroll
-            for (int v = 0; v < 4; ++v) Q[l * SL + v * n2 + node] = fmaf(dt, B.Kw1[l] * R0[v], up[v]);
+            for (int v = 0; v < 4; ++v)
+                store_q_pair(g, v, fmaf(dt, B.Kw1[2 * g] * R0[v], up[v]), fmaf(dt, B.Kw1[l1] * R0[v], up[v]));
+        }
         __syncthreads();
     }
 #pragma unroll 1
     for (int r = 1; r < n; ++r) {
-        float R[n][4];
+        float2 S2h[NPAIR];
 #pragma unroll
-        for (int k = 0; k < n; ++k) {
-            float q[4], gx[4], gy[4];
-            FluxF f;
-            eval(Q + k * SL, q, gx, gy, f);
-#pragma unroll
-            for (int v = 0; v < 4; ++v) {
-                Fs[k * SL + v * n2 + node] = f.F[v];
-                Gs[k * SL + v * n2 + node] = f.G[v];
-                R[k][v] = f.S[v];
-            }
+        for (int h = 0; h < NPAIR; ++h) {
+            float2 q[4], gx[4], gy[4];
+            FluxF2 f;
+            eval_pair(h, q, gx, gy, f);
+            store_flux_pair(h, f);
+            S2h[h] = f.S2;
         }
         __syncthreads();
 #pragma unroll
-        for (int k = 0; k < n; ++k)
+        for (int v = 0; v < 4; ++v) {
+            float2 R2[NPAIR];  // slices 2h, 2h+1 of variable v
 #pragma unroll
-            for (int v = 0; v < 4; ++v) R[k][v] += divergence(k, v);
+            for (int h = 0; h < NPAIR; ++h) R2[h] = fma2(bc2(-1.f), divergence(h, v), v == 2 ? S2h[h] : bc2(0.f));
 #pragma unroll
-        for (int l = 0; l < n; ++l)
+            for (int g = 0; g < NPAIR; ++g) {
+                const int l0 = 2 * g, l1 = 2 * g + 1 < n ? 2 * g + 1 : 2 * g;
+                float2 a0 = mul2(make_float2(B.Kw[l0][0], B.Kw[l0][1]), R2[0]);
+                float2 a1 = mul2(make_float2(B.Kw[l1][0], B.Kw[l1][1]), R2[0]);
 #pragma unroll
-            for (int v = 0; v < 4; ++v) {
-                float acc = 0.f;
-#pragma unroll
-                for (int k = 0; k < n; ++k) acc = fmaf(B.Kw[l][k], R[k][v], acc);
-                Q[l * SL + v * n2 + node] = fmaf(dt, acc, up[v]);
+                for (int h = 1; h < NPAIR; ++h) {
+                    a0 = fma2(make_float2(B.Kw[l0][2 * h], B.Kw[l0][2 * h + 1]), R2[h], a0);
+                    a1 = fma2(make_float2(B.Kw[l1][2 * h], B.Kw[l1][2 * h + 1]), R2[h], a1);
+                }
+                store_q_pair(g, v, fmaf(dt, a0.x + a0.y, up[v]), fmaf(dt, a1.x + a1.y, up[v]));
             }
+        }
         __syncthreads();
     }
 
-    float qb[4], Fb[4], Gb[4], Sb[4], qxb[4], qyb[4];
+    float qb[4], Fb[4], Gb[4], Sb[4], qxb[4], qyb[4], Sz = 0.f;
 #pragma unroll
-    for (int v = 0; v < 4; ++v) qb[v] = Fb[v] = Gb[v] = Sb[v] = qxb[v] = qyb[v] = 0.f;
+    for (int v = 0; v < 4; ++v) qb[v] = Fb[v] = Gb[v] = qxb[v] = qyb[v] = 0.f;
 #pragma unroll
-    for (int k = 0; k < n; ++k) {
-        float q[4], gx[4], gy[4];
-        FluxF f;
-        eval(Q + k * SL, q, gx, gy, f);
-        const float wk = B.w[k];
+    for (int h = 0; h < NPAIR; ++h) {
+        float2 q[4], gx[4], gy[4];
+        FluxF2 f;
+        eval_pair(h, q, gx, gy, f);
+        const float w0 = B.w[2 * h], w1 = B.w[2 * h + 1];  // w[n] = 0 pads an odd n
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
-            qb[v] = fmaf(wk, q[v], qb[v]);
-            Fb[v] = fmaf(wk, f.F[v], Fb[v]);
-            Gb[v] = fmaf(wk, f.G[v], Gb[v]);
-            Sb[v] = fmaf(wk, f.S[v], Sb[v]);
-            qxb[v] = fmaf(wk, gx[v], qxb[v]);
-            qyb[v] = fmaf(wk, gy[v], qyb[v]);  // full y-gradient (background included)
+            qb[v] = fmaf(w1, q[v].y, fmaf(w0, q[v].x, qb[v]));
+            Fb[v] = fmaf(w1, f.F[v].y, fmaf(w0, f.F[v].x, Fb[v]));
+            Gb[v] = fmaf(w1, f.G[v].y, fmaf(w0, f.G[v].x, Gb[v]));
+            qxb[v] = fmaf(w1, gx[v].y, fmaf(w0, gx[v].x, qxb[v]));
+            qyb[v] = fmaf(w1, gy[v].y, fmaf(w0, gy[v].x, qyb[v]));  // full y-gradient (background included)
         }
+        Sz = fmaf(w1, f.S2.y, fmaf(w0, f.S2.x, Sz));
     }
+#pragma unroll
+    for (int v = 0; v < 4; ++v) Sb[v] = 0.f;
+    Sb[2] = Sz;
     __syncthreads();
-    float* A = Q;  // slots 0..4: qbar', Fbar, Gbar, qxbar, qybar
+    float* A = reinterpret_cast<float*>(Q2);  // slots 0..4: qbar', Fbar, Gbar, qxbar, qybar
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
         A[0 * SL + v * n2 + node] = qb[v];
@@ -917,7 +948,7 @@ static int pred_n(adg_mesh* m, double dt, cudaStream_t s) {
     using C = AmrCfg<N>;
     if (m->d.precision == ADG_PREC_MIXED) {
         auto km = k_predictor_amr_mixed<N, C::cpb>;
-        const size_t smem = (size_t)C::cpb * 3 * C::n * 4 * C::n * C::n * sizeof(float);
+        const size_t smem = (size_t)C::cpb * AmrMixCfg<N>::stride * sizeof(float);
         ADG_CK(cudaFuncSetAttribute(km, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem), "amr pred mixed");
         km<<<(m->cells + C::cpb - 1) / C::cpb, C::threads, smem, s>>>(m->u, m->rvol, m->trace, m->cells, (float)dt,
                                                                        m->Bf, m->Pf, m->geo, m->mbl64, m->mblf);

@@ -27,75 +27,6 @@
 
 namespace adg {
 
-// ---------------------------------------------------------------------------
-// Packed FP32x2 arithmetic (sm_100 and later): one instruction works on two
-// FP32 lanes, each rounded like its scalar counterpart.  The predictor runs
-// the point-wise flux on two time slices at once and pairs adjacent row
-// entries in its contractions, halving the FP32 instruction count there.
-__device__ __forceinline__ float2 bc2(float s) { return make_float2(s, s); }
-__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
-__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-__device__ __forceinline__ float2 fnma2(float2 a, float2 b, float2 c) {  // c - a b
-    return __ffma2_rn(make_float2(-a.x, -a.y), b, c);
-}
-// approximate reciprocal (hardware rcp, relative error ~2^-23); rho is O(1)
-// and never subnormal, so flushing subnormals changes nothing
-__device__ __forceinline__ float rcp_fast(float x) {
-    float r;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-    return r;
-}
-
-struct FluxF2 {
-    float2 F[4], G[4], S2;  // S2: the only non-zero physical source, -g rho' (z-momentum)
-};
-
-// ns_flux_pert on a pair of time slices at one node (the interior form:
-// gradients of T from the state, no wall heat flux).
-__device__ __forceinline__ void ns_flux_pert2(const float2 qp[4], const float2 gx[4], const float2 gy[4],
-                                              float z, float rb, float Eb, float pb, const PhysF& P,
-                                              FluxF2& o) {
-    const float2 rho = add2(bc2(rb), qp[0]);
-    const float2 mx = qp[1], my = qp[2];
-    const float2 rinv = make_float2(rcp_fast(rho.x), rcp_fast(rho.y));
-    const float2 u = mul2(mx, rinv), v = mul2(my, rinv);
-    const float gz = P.g * z;
-    // p' = (gamma-1) (E' - (mx u + my v)/2 - g z rho')
-    const float2 m2 = fma2(my, v, mul2(mx, u));
-    const float2 pp = mul2(bc2(P.gm1), fma2(bc2(-gz), qp[0], fma2(bc2(-0.5f), m2, qp[3])));
-    const float2 p = add2(bc2(pb), pp);
-    const float2 E = add2(bc2(Eb), qp[3]);
-    const float2 T = mul2(mul2(p, rinv), bc2(P.invR));
-    const float2 ux = mul2(fnma2(u, gx[0], gx[1]), rinv);
-    const float2 uy = mul2(fnma2(u, gy[0], gy[1]), rinv);
-    const float2 vx = mul2(fnma2(v, gx[0], gx[2]), rinv);
-    const float2 vy = mul2(fnma2(v, gy[0], gy[2]), rinv);
-    // kin - g z, the common factor of the density gradient in grad p
-    const float2 kg = fma2(bc2(0.5f), fma2(v, v, mul2(u, u)), bc2(-gz));
-    const float2 px = mul2(bc2(P.gm1), fma2(kg, gx[0], fnma2(v, gx[2], fnma2(u, gx[1], gx[3]))));
-    const float2 py = mul2(bc2(P.gm1),
-                           fnma2(rho, bc2(P.g), fma2(kg, gy[0], fnma2(v, gy[2], fnma2(u, gy[1], gy[3])))));
-    const float2 RT = mul2(bc2(P.R), T);
-    const float2 ri = mul2(rinv, bc2(P.invR));
-    const float2 Tx = mul2(fnma2(RT, gx[0], px), ri);
-    const float2 Ty = mul2(fnma2(RT, gy[0], py), ri);
-    const float2 div = add2(ux, vy);
-    const float2 sxx = mul2(bc2(P.mu), fma2(bc2(2.f / 3.f), div, mul2(bc2(-2.f), ux)));
-    const float2 syy = mul2(bc2(P.mu), fma2(bc2(2.f / 3.f), div, mul2(bc2(-2.f), vy)));
-    const float2 sxy = mul2(bc2(-P.mu), add2(uy, vx));
-    const float2 Ep = add2(E, p);
-    o.F[0] = mx;
-    o.F[1] = fma2(mx, u, add2(pp, sxx));
-    o.F[2] = fma2(my, u, sxy);
-    o.F[3] = fma2(bc2(-P.kappa), Tx, fma2(v, sxy, mul2(u, add2(Ep, sxx))));
-    o.G[0] = my;
-    o.G[1] = fma2(mx, v, sxy);
-    o.G[2] = fma2(my, v, add2(pp, syy));
-    o.G[3] = fma2(bc2(-P.kappa), Ty, fma2(u, sxy, mul2(v, add2(Ep, syy))));
-    o.S2 = mul2(bc2(-P.g), qp[0]);
-}
-
 template <int N, int CPB_ = 0>
 struct MixCfg {
     static constexpr int n = N + 1;
