@@ -251,6 +251,13 @@ typedef struct adg_batch adg_batch;
 int adg_batch_create(adg_mesh* const* meshes, int k, adg_batch** out);
 int adg_batch_step(adg_batch* b, const double* dt, int nsteps, void* stream);
 int adg_batch_info(const adg_batch* b, int* info, int n);
+/* Pins the predictor's tile-size candidate (0, 1 or 2: half, default and
+ * double the per-mesh cells per block) instead of the timed choice, e.g. to
+ * reproduce a run or to test every candidate.  Synchronises the device
+ * (the previous tile list may be in use by a launched step), rebuilds the
+ * tile list and drops the captured graph.  ADG_EINVAL for a NULL batch or a
+ * candidate outside 0..2. */
+int adg_batch_set_candidate(adg_batch* b, int cand);
 void adg_batch_destroy(adg_batch* b);
 
 /* ---- allocation-free step (the paper has no counterpart) ----

@@ -127,6 +127,7 @@ SIGNATURES = {
     "adg_batch_create": (_I, [ctypes.POINTER(_P), _I, ctypes.POINTER(_P)]),
     "adg_batch_step": (_I, [_P, ctypes.POINTER(_D), _I, _P]),
     "adg_batch_info": (_I, [_P, ctypes.POINTER(_I), _I]),
+    "adg_batch_set_candidate": (_I, [_P, _I]),
     "adg_batch_destroy": (None, [_P]),
     "adg_step_noalloc": (_I, [ctypes.POINTER(MeshDesc), _P, _S, _D, _P]),
     "adg_leaf_count": (_S, [_P]),

@@ -1107,6 +1107,18 @@ extern "C" int adg_batch_info(const adg_batch* b, int* info, int n) {
     return ADG_OK;
 }
 
+extern "C" int adg_batch_set_candidate(adg_batch* b, int cand) {
+    if (!b) return fail(ADG_EINVAL, "batch_set_candidate: NULL batch");
+    if (cand < 0 || cand >= adg::kBatchCandidates) return fail(ADG_EINVAL, "batch_set_candidate: candidate not in 0..2");
+    ADG_CK(cudaSetDevice(b->device), "batch_set_candidate: cudaSetDevice");
+    ADG_CK(cudaDeviceSynchronize(), "batch_set_candidate: synchronise");
+    if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
+    if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
+    b->graph_steps = 0;
+    b->cand_pred = cand;
+    return upload_tiles(b, cand, 0, &b->tiles_pred, &b->ntiles_pred, &b->cpb_pred, &b->blocks_pred);
+}
+
 extern "C" int adg_batch_step(adg_batch* b, const double* dt, int nsteps, void* stream) {
     if (!b || !dt) return fail(ADG_EINVAL, "batch_step: NULL argument");
     if (nsteps < 1) return fail(ADG_EINVAL, "batch_step: nsteps must be >= 1");

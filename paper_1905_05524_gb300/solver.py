@@ -252,6 +252,10 @@ class Batch:
         arr = (ctypes.c_double * len(self.meshes))(*[float(d) for d in dts])
         L.check(self._lib.adg_batch_step(self.h, arr, int(nsteps), _stream_ptr(stream)))
 
+    def set_candidate(self, cand):
+        """Pin the predictor's tile-size candidate (0, 1, 2) instead of the timed choice."""
+        L.check(self._lib.adg_batch_set_candidate(self.h, int(cand)))
+
     def info(self):
         buf = (ctypes.c_int * 9)()
         L.check(self._lib.adg_batch_info(self.h, buf, 9))

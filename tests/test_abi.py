@@ -116,3 +116,12 @@ def test_3d_and_fv_descriptors_rejected_without_gpu(built):
     assert lib.adg_fv_create(ctypes.byref(bad), ctypes.byref(h)) == _lib.ADG_EUNSUPPORTED
     assert lib.adg_fv_step(None, 0.1, None) == _lib.ADG_EINVAL
     lib.adg_fv_destroy(None)
+
+
+def test_batch_calls_rejected_without_gpu(built):
+    """Batch entry points validate their handle and candidate before touching a device."""
+    from paper_1905_05524_gb300 import _lib
+    lib = _lib.lib()
+    assert lib.adg_batch_set_candidate(None, 0) == _lib.ADG_EINVAL
+    assert lib.adg_batch_step(None, None, 1, None) == _lib.ADG_EINVAL
+    assert lib.adg_batch_info(None, None, 0) == _lib.ADG_EINVAL

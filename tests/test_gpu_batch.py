@@ -105,3 +105,27 @@ def test_batch_matches_individual_meshes_every_degree(degree):
     for ma, mb in zip(a, b):
         _same(ma.get_state(), mb.get_state(), 1e-9)
     batch.close()
+
+
+@pytest.mark.parametrize("degree", [2, 5, 7])
+@pytest.mark.parametrize("cand", [0, 1, 2])
+def test_batch_every_tile_candidate_matches_individual_meshes(degree, cand):
+    """Each predictor tile-size candidate pinned in turn (half, default and
+    double the per-mesh cells per block: separate instantiations of the
+    slice-pair predictor body with their own shared-memory strides), 2
+    batched steps against 2 per-mesh steps; 1e-9 relative as above (the
+    default candidate is the per-mesh kernel's own tile size)."""
+    a = [_bubble_mesh(s, 300.0, degree=degree) for s in (5, 8, 11)]
+    b = [_bubble_mesh(s, 300.0, degree=degree) for s in (5, 8, 11)]
+    dts = [m.stable_dt(0.25) for m in a]
+    batch = Batch(a)
+    batch.set_candidate(cand)
+    info = batch.info()
+    assert info["cpb_pred"] >= 1 and info["tiles_pred"] >= 1
+    batch.step(dts, nsteps=2)
+    for m, dt in zip(b, dts):
+        m.step(dt, 2)
+    torch.cuda.synchronize()
+    for ma, mb in zip(a, b):
+        _same(ma.get_state(), mb.get_state(), 1e-9)
+    batch.close()
