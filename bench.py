@@ -85,6 +85,10 @@ def predictor_flops_per_cell(n):
 # ncu capture of the kernel as it stands (the predictor summaries under profiles/);
 # set to None whenever the kernel changes after the capture.
 PREDICTOR_TRAFFIC = {"fp64": 7810304 + 1280, "mixed": 7631872 + 0}
+# The mixed predictor's shared-memory data-pipe utilisation from the same
+# capture (the FP64 predictor is bound by its FP64 pipe instead); None
+# whenever the kernel changes after the capture.
+PREDICTOR_SMEM_FRAC = {"fp64": None, "mixed": 0.813}
 
 
 def measure_fma_peaks():
@@ -930,6 +934,10 @@ def run_ours(args):
             "hbm_achieved_gbs": cells * n * n * 4 * 8 * 2 / (pred_avg * 1e-3) / 1e9,
             "hbm_peak_gbs": (mp or {}).get("hbm_gbs", 6800.0),
             "hbm_peak_source": "MEASURED_PEAKS.json" if mp else "fallback 6.8 TB/s",
+            "smem_data_pipe_frac": PREDICTOR_SMEM_FRAC.get(args.precision),
+            "smem_note": "the limiter of the predictor: fraction of the shared-memory wavefront rate "
+                         "(ncu l1tex__data_pipe_lsu_wavefronts_mem_shared.sum.pct_of_peak_sustained_elapsed, "
+                         "same capture as traffic); the FP32 pipe stays below it",
         }
         cpu = None
         if not args.no_cpu_baseline and ws == 1:
