@@ -118,33 +118,47 @@ def test_picard_sweeps_converged_navier_stokes():
     assert (a - b).abs().max().item() < 1e-12 * u.abs().max().item()
 
 
-@pytest.mark.parametrize("N,grids,T,min_order", [(1, (8, 16, 32), 0.25, 1.8), (2, (8, 16, 32), 0.5, 2.7)])
-def test_convergence_euler(N, grids, T, min_order):
-    """Order N+1 on an exact Euler solution (mu = 0)."""
+def _orders(N, mu, field, grids, T, source):
+    """L2 errors per variable at time T on nc x nc periodic meshes over [0,10]^2
+    and the observed orders between consecutive meshes."""
     errs = []
     for nc in grids:
-        P = ph.cfd_params(N, mu=0.0, source="none")
+        P = ph.cfd_params(N, mu=mu, source=source)
         s = Solver(Mesh(nc, nc), P)
-        u = run(s, s.interpolate(density_wave), T)
-        errs.append(s.l2_error(u, s.interpolate(density_wave, T))[0].item())
-    orders = [math.log2(errs[i] / errs[i + 1]) for i in range(len(errs) - 1)]
-    assert orders[-1] >= min_order, (errs, orders)
+        u = run(s, s.interpolate(field, 0.0), T)
+        errs.append(s.l2_error(u, s.interpolate(field, T)))
+    return errs, [torch.log2(errs[i] / errs[i + 1]) for i in range(len(errs) - 1)]
 
 
-@pytest.mark.parametrize("N,min_order", [(2, 2.0), (3, 2.5)])
+@pytest.mark.parametrize("N,grids,min_order", [(1, (8, 16, 32), 1.7), (2, (8, 16, 32), 2.7),
+                                               (3, (4, 8, 16), 3.7), (4, (4, 8, 16), 4.7)])
+def test_convergence_euler(N, grids, min_order):
+    """Order >= N + 0.7 on an exact Euler solution (mu = 0) at t = 0.5, degrees
+    1-4 (measured on the finest pair: 2.07, 2.95, 4.71, 4.76)."""
+    errs, orders = _orders(N, 0.0, density_wave, grids, 0.5, "none")
+    assert orders[-1].min().item() >= min_order, (errs, orders)
+
+
+@pytest.mark.parametrize("N,grids", [(2, (8, 16, 32)), (3, (8, 16, 32))])
+def test_convergence_paper_manufactured_inviscid(N, grids):
+    """The paper's manufactured field (Sec. 4.1, Eq. 8) with mu = 0 and its
+    source built by differentiation: order >= N + 0.7 in every variable at the
+    paper's t = 0.5 (measured 2.79 / 3.95 at worst)."""
+    errs, orders = _orders(N, 0.0, ph.paper_manufactured, grids, 0.5, "paper")
+    assert orders[-1].min().item() >= N + 0.7, (errs, orders)
+
+
+@pytest.mark.parametrize("N,min_order", [(1, 1.7), (2, 2.0), (3, 3.0), (4, 4.0)])
 def test_convergence_paper_manufactured(N, min_order):
-    """The paper's manufactured solution (Sec. 4.1, Eq. 8; mu = 0.1) with its
-    source built by differentiation: the error falls at high order.  With
-    the viscous Rusanov-type flux the measured order on these grids is
-    between N and N+1 (the paper notes diminishing returns too)."""
-    errs = []
-    for nc in (8, 16):
-        P = ph.cfd_params(N, mu=0.1, source="paper")
-        s = Solver(Mesh(nc, nc), P)
-        u = run(s, s.interpolate(ph.paper_manufactured, 0.0), 0.1)
-        errs.append(s.l2_error(u, s.interpolate(ph.paper_manufactured, 0.1))[0].item())
-    order = math.log2(errs[0] / errs[1])
-    assert order >= min_order, (errs, order)
+    """The paper's convergence study (Sec. 4.1, Eq. 8; mu = 0.1, t = 0.5) on
+    4^2, 8^2, 16^2 cells, degrees 1-4.  The viscous Rusanov-type flux (the
+    average of the two one-sided viscous fluxes plus the penalty 2 eta
+    lambda_v on the jump) has no adjoint-consistency term, and the measured
+    order of its L2 error sits between N and N + 1 (8 -> 16, worst variable:
+    2.18, 2.59, 3.26, 4.08; the inviscid runs above reach N + 1).  The pin is
+    order >= N (>= N + 0.7 at degree 1) in every variable."""
+    errs, orders = _orders(N, 0.1, ph.paper_manufactured, (4, 8, 16), 0.5, "paper")
+    assert orders[-1].min().item() >= min_order, (errs, orders)
 
 
 def test_hydrostatic_balance_preserved():
