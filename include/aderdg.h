@@ -270,7 +270,8 @@ void adg_batch_destroy(adg_batch* b);
  * synchronisation, or a plug-in whose host forbids allocator calls.
  *
  *   desc   mesh/physics description (as for adg_create_mesh); precision must
- *          be ADG_PREC_FP64 (ADG_EUNSUPPORTED otherwise)
+ *          be ADG_PREC_FP64 and max_levels 0 (ADG_EUNSUPPORTED otherwise);
+ *          at most 2^26 cells
  *   u      device pointer to the state (layout above), updated in place;
  *          count must equal nx*ny*(N+1)^2*4
  *   dt     time step (> 0)
@@ -279,12 +280,17 @@ void adg_batch_destroy(adg_batch* b);
  * fixed file-scope device array of ADG_NOALLOC_SCRATCH_BYTES that every GPU
  * loading the library holds until exit; meshes needing more scratch are
  * rejected with ADG_EINVAL and a message giving both sizes (at N = 5 about
- * 7,500 cells fit).  The first call on a device looks up the array's address
- * once; make that first call before any stream capture.  All calls share the
- * array, so calls whose work overlaps on the GPU (different streams, or
- * different threads on one device) race; serialise them.  Every scratch
- * entry is written before it is read within a call, so no state carries over
- * between calls. */
+ * 7,500 cells fit).  A call on a stream that is not capturing looks the
+ * array's device address up (again, so a device reset cannot leave a stale
+ * address); a call on a capturing stream reuses the address of the last
+ * uncaptured call on that device, so the first call on a device must come
+ * before any stream capture (ADG_ESTATE otherwise).  The work runs on
+ * desc->device; the caller's current device is restored before returning,
+ * and `stream` must belong to desc->device.  All calls share the array, so
+ * calls whose work overlaps on the GPU (different streams, or different
+ * threads on one device) race; serialise them.  Every scratch entry is
+ * written before it is read within a call, so no state carries over between
+ * calls. */
 #define ADG_NOALLOC_SCRATCH_BYTES (32u << 20)
 int adg_step_noalloc(const adg_mesh_desc* desc, double* u, size_t count, double dt, void* stream);
 

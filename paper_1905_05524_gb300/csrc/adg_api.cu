@@ -793,9 +793,12 @@ int adg_check_finite(adg_mesh* m, void* stream) {
 // start-up.  The scratch the predictor/corrector pair needs (background
 // tables, volume residual, face traces) lives in one file-scope device array
 // of fixed size; every GPU that loads this library holds it until exit.
-// The first call on a device looks up the array's device address once
-// (cudaGetSymbolAddress); make that first call before any stream capture.
-// All calls share the array: calls whose work overlaps on the GPU race.
+// Every call outside stream capture looks the array's device address up again
+// (cudaGetSymbolAddress, no synchronisation), so a device reset that reloads
+// the module cannot leave a stale address behind; a call on a capturing
+// stream uses the address of the last uncaptured call on that device, so the
+// first call on a device must come before any stream capture.  All calls
+// share the array: calls whose work overlaps on the GPU race.
 namespace {
 
 constexpr size_t kNoallocBytes = (size_t)32 << 20;  // ADG_NOALLOC_SCRATCH_BYTES
@@ -848,6 +851,8 @@ extern "C" int adg_step_noalloc(const adg_mesh_desc* d, double* u, size_t count,
     if (d->precision != ADG_PREC_FP64) return fail(ADG_EUNSUPPORTED, "step_noalloc: FP64 precision only");
     if (!(dt > 0.0) || !std::isfinite(dt)) return fail(ADG_EINVAL, "step_noalloc: dt must be finite and > 0");
     if (d->device < 0 || d->device >= kNoallocMaxDevices) return fail(ADG_EINVAL, "step_noalloc: bad device ordinal");
+    if (d->max_levels != 0) return fail(ADG_EUNSUPPORTED, "step_noalloc: uniform meshes only (max_levels must be 0)");
+    if ((long long)d->nx * d->ny > (1LL << 26)) return fail(ADG_EINVAL, "step_noalloc: more than 2^26 cells");
 
     const int N = d->degree, n = N + 1;
     const size_t cells = (size_t)d->nx * d->ny;
@@ -865,14 +870,25 @@ extern "C" int adg_step_noalloc(const adg_mesh_desc* d, double* u, size_t count,
         return fail(ADG_EINVAL, msg);
     }
 
+    // the caller's current device is restored on every return
+    int prev_dev = 0;
+    ADG_CK(cudaGetDevice(&prev_dev), "step_noalloc: cudaGetDevice");
+    struct DeviceRestore {
+        int dev;
+        ~DeviceRestore() { cudaSetDevice(dev); }
+    } restore{prev_dev};
     ADG_CK(cudaSetDevice(d->device), "step_noalloc: cudaSetDevice");
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    ADG_CK(cudaStreamIsCapturing((cudaStream_t)stream, &cap), "step_noalloc: cudaStreamIsCapturing");
     void* base = nullptr;
     {
         std::lock_guard<std::mutex> lock(g_noalloc_mu);
-        if (!g_noalloc_ptr[d->device]) {  // one-time set-up on this device
+        if (cap == cudaStreamCaptureStatusNone) {  // look the address up (again): valid after a device reset
             void* p = nullptr;
             ADG_CK(cudaGetSymbolAddress(&p, g_noalloc_scratch), "step_noalloc: cudaGetSymbolAddress");
             g_noalloc_ptr[d->device] = p;
+        } else if (!g_noalloc_ptr[d->device]) {
+            return fail(ADG_ESTATE, "step_noalloc: the first call on a device must come before stream capture");
         }
         base = g_noalloc_ptr[d->device];
     }

@@ -4,7 +4,8 @@
 // of the mixed-precision kernels; these versions use the integer pipes.
 //  * f64_to_f32: round to nearest, ties to even; results below the binary32
 //    normal range become +-0, above it +-inf (the solver's values are far from
-//    both ends).
+//    both ends); +-inf stays +-inf and NaN stays NaN (a quiet NaN of the same
+//    sign).
 //  * f32_to_f64: exact for normal numbers; subnormal inputs become +-0.
 #pragma once
 #include <cuda_runtime.h>
@@ -15,13 +16,15 @@ __device__ __forceinline__ float f64_to_f32(double d) {
     const unsigned int hi = (unsigned int)__double2hiint(d);
     const unsigned int lo = (unsigned int)__double2loint(d);
     const unsigned int sign = hi & 0x80000000u;
-    const int e = (int)((hi >> 20) & 0x7FFu) - 1023 + 127;
+    const unsigned int ein = (hi >> 20) & 0x7FFu;
+    const int e = (int)ein - 1023 + 127;
     const unsigned int m = ((hi & 0xFFFFFu) << 3) | (lo >> 29);   // top 23 of the 52 mantissa bits
     const unsigned int rest = lo & 0x1FFFFFFFu;                      // the 29 bits dropped
     unsigned int r = sign | ((unsigned int)e << 23) | m;
     r += (rest > 0x10000000u || (rest == 0x10000000u && (m & 1u))) ? 1u : 0u;  // carry may bump the exponent
     if (e <= 0) r = sign;
     if (e >= 255) r = sign | 0x7F800000u;
+    if (ein == 0x7FFu && ((hi & 0xFFFFFu) | lo) != 0u) r = sign | 0x7FC00000u;  // NaN input
     return __uint_as_float(r);
 }
 

@@ -48,26 +48,37 @@ def test_mixed_vs_oracle_bubble_small():
 
 
 def test_mixed_vs_fp64_gpu_warm_bubble_81x81_400_steps():
-    """The warm bubble at full size (degree 5, 81x81, CFL 0.25): 400 steps of the mixed path against 400
-    steps of the FP64 GPU path (itself parity-checked against the oracle)."""
+    """The warm bubble at full size (degree 5, 81x81, CFL 0.45 as timed by the
+    bench): 400 steps of the mixed path against 400 steps of the FP64 GPU path
+    (itself parity-checked against the oracle).  After 20 steps the horizontal
+    momentum is ~1e-2 of the vertical one, so its own relative difference is
+    large; against the momentum field as a whole the difference is at FP32
+    rounding (<= 1e-5), which is what the 20-step check states."""
     res = {}
     for prec in (L.ADG_PREC_FP64, L.ADG_PREC_MIXED):
         cfg = atmosphere_config(degree=5, nx=81, ny=81, precision=prec)
         m = Mesh(cfg)
         m.init_scenario(L.ADG_SCEN_COSINE, A=0.5, a=250.0, xc=500.0, zc=350.0)
         if prec == L.ADG_PREC_FP64:
-            dt = m.stable_dt(0.25)
-        for _ in range(8):
-            m.step(dt, 50)
+            dt = m.stable_dt(0.45)
+        m.step(dt, 20)
+        res[(prec, 20)] = m.get_state().cpu()
+        for _ in range(19):
+            m.step(dt, 20)
             m.check_finite()
-        res[prec] = m.get_state().cpu()
+        res[(prec, 400)] = m.get_state().cpu()
     o = oracle_for(atmosphere_config(degree=5, nx=81, ny=81))
-    err = rel_theta_err(o, res[L.ADG_PREC_MIXED], res[L.ADG_PREC_FP64])
+    a20, b20 = res[(L.ADG_PREC_MIXED, 20)], res[(L.ADG_PREC_FP64, 20)]
+    dmom = torch.linalg.vector_norm(a20[:, 1:3] - b20[:, 1:3]).item()
+    mom = torch.linalg.vector_norm(b20[:, 1:3]).item()
+    print(f"warm bubble 20 steps: momentum difference {dmom:.3e} of {mom:.3e} (relative {dmom / mom:.3e})")
+    assert dmom <= 1e-5 * mom, (dmom, mom)
+    err = rel_theta_err(o, res[(L.ADG_PREC_MIXED, 400)], res[(L.ADG_PREC_FP64, 400)])
     print(f"warm bubble 400 steps: relative theta' L2 error mixed vs fp64 = {err:.3e}")
     assert err <= THETA_TOL, err
     # conserved variables: relative L2 per variable, stated
     for v in range(4):
-        a, b = res[L.ADG_PREC_MIXED][:, v], res[L.ADG_PREC_FP64][:, v]
+        a, b = res[(L.ADG_PREC_MIXED, 400)][:, v], res[(L.ADG_PREC_FP64, 400)][:, v]
         r = (torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b)).item()
         print(f"  var {v}: rel L2 {r:.3e}")
         assert r < 1e-5

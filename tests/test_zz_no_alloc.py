@@ -16,19 +16,22 @@ import torch
 
 from paper_1905_05524_gb300 import _lib as L
 from paper_1905_05524_gb300.solver import Mesh, atmosphere_config, steady_manufactured_config
+from tests.tolerances import momentum_floor
 
 pytestmark = pytest.mark.gpu
 
 TOL = 1e-11
 
 
-def _close(a, b):
+def _close(a, b, floor):
+    """Per-variable L2 within TOL of the reference, plus the momentum
+    rounding floor of tests/tolerances.py for a fluid near rest over a
+    hydrostatic background."""
     for v in range(4):
         d = torch.linalg.vector_norm(a[:, v] - b[:, v]).item()
         nb = torch.linalg.vector_norm(b[:, v]).item()
-        nrho = torch.linalg.vector_norm(b[:, 0]).item()
-        den = max(nb, nrho) if v in (1, 2) else nb   # 1 m/s momentum floor (fluid near rest)
-        assert d <= TOL * den, (v, d, den)
+        bound = TOL * nb + (floor if v in (1, 2) else 0.0)
+        assert d <= bound, (v, d, bound)
 
 
 @pytest.mark.parametrize("cfg", [steady_manufactured_config(degree=3, nx=9, ny=9),
@@ -46,12 +49,12 @@ def test_noalloc_step_matches_mesh_step_twice(cfg):
     desc = cfg.to_c()
     stream = torch.cuda.current_stream()
     sp = ctypes.c_void_p(stream.cuda_stream)
-    for _ in range(2):                     # two calls in a row
+    for k in range(2):                     # two calls in a row
         ref.step(dt)
         L.check(lib.adg_step_noalloc(ctypes.byref(desc), ctypes.c_void_p(u.data_ptr()), u.numel(),
                                      float(dt), sp))
         torch.cuda.synchronize()
-        _close(u.cpu(), ref.get_state().cpu())
+        _close(u.cpu(), ref.get_state().cpu(), momentum_floor(cfg, dt, k + 1, u[:, 0].numel()))
     ref.close()
 
 
@@ -68,3 +71,13 @@ def test_noalloc_rejects_oversized_mesh_and_bad_count():
     small = steady_manufactured_config(degree=2, nx=3, ny=3).to_c()
     rc = lib.adg_step_noalloc(ctypes.byref(small), ctypes.c_void_p(u.data_ptr()), 5, 0.01, sp)
     assert rc == L.ADG_EINVAL
+    # an adaptive-mesh description is refused rather than stepped as a uniform mesh
+    amr = steady_manufactured_config(degree=2, nx=3, ny=3)
+    amr.max_levels = 1
+    rc = lib.adg_step_noalloc(ctypes.byref(amr.to_c()), ctypes.c_void_p(u.data_ptr()), 3 * 3 * 9 * 4, 0.01, sp)
+    assert rc == L.ADG_EUNSUPPORTED
+    # absurd sizes are refused before any size arithmetic can wrap
+    huge = steady_manufactured_config(degree=2, nx=1 << 20, ny=1 << 20).to_c()
+    rc = lib.adg_step_noalloc(ctypes.byref(huge), ctypes.c_void_p(u.data_ptr()), 36, 0.01, sp)
+    assert rc == L.ADG_EINVAL and b"2^26" in lib.adg_last_error()
+    assert torch.cuda.current_device() == 0
