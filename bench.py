@@ -856,30 +856,22 @@ def run_adjoint(args, dev):
     import torch
     from paper_1905_05524_gb300 import _lib as L
     from paper_1905_05524_gb300 import inputs
-    from paper_1905_05524_gb300.adjoint import objective_from_theta, probe_operator, node_heights
+    from paper_1905_05524_gb300.adjoint import objective_from_theta, state_to_theta
     from paper_1905_05524_gb300.solver import Mesh, atmosphere_config
     cfg = atmosphere_config(degree=3, nx=27, ny=27, device=dev.index)
     m = Mesh(cfg)
     m.init_scenario(L.ADG_SCEN_COSINE, A=0.5, a=250.0, xc=500.0, zc=350.0)
     dt = m.stable_dt(CFL_OTHER)
-    import numpy as np
     n = 4
-    xi, _ = np.polynomial.legendre.leggauss(n)
-    xi = torch.tensor(0.5 * (xi + 1.0), dtype=torch.float64, device=dev)
-    ix = torch.arange(729, device=dev) % 27
-    X = (ix[:, None].double() + xi[None, :]) * (1000.0 / 27)
-    X = X[:, None, :].expand(-1, n, n)
-    Z = node_heights(cfg, dev)
-    r = torch.sqrt((X - 500.0) ** 2 + (Z - 350.0) ** 2)
-    th0 = torch.where(r <= 250.0, 0.25 * (1 + torch.cos(np.pi * r / 250.0)), torch.zeros_like(r))
-    cells, W = probe_operator(cfg, inputs.probes(64, seed=1), dev)
+    th0 = state_to_theta(m.get_state(), m)          # nodal theta' of the cosine bubble
+    xy = torch.from_numpy(inputs.probes(64, seed=1)).to(dev)
     target = torch.from_numpy(inputs.normal_values(64, seed=0, scale=0.1)).to(dev)
     x = th0.clone().requires_grad_(True)
     # warm-up: first launches of every kernel on the path (module load, smem attributes)
-    (gw,) = torch.autograd.grad(objective_from_theta(x, m, dt, 4, 2, cells, W, target), x)
+    (gw,) = torch.autograd.grad(objective_from_theta(x, m, dt, 4, 2, xy, target), x)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    J = objective_from_theta(x, m, dt, 200, 20, cells, W, target)
+    J = objective_from_theta(x, m, dt, 200, 20, xy, target)
     torch.cuda.synchronize()
     t1 = time.perf_counter()
     (g,) = torch.autograd.grad(J, x)

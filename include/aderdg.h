@@ -204,6 +204,34 @@ int adg_step_tv(adg_mesh* m, double dt, int var, double T_r, double T_c, double*
 int adg_step_adjoint(adg_mesh* m, double dt, const double* u_n, const double* lam_np1, double* lam_n,
                      void* stream);
 
+/* ---- potential-temperature maps of the sensitivity problem (Sec. 4.2) ----
+ *
+ * Device arrays, uniform meshes (ADG_EUNSUPPORTED on adaptive ones), FP64,
+ * queued on `stream`.  theta' arrays are nodal [c][j][i] (cells*(N+1)^2
+ * doubles); states use the state layout above.
+ *
+ * adg_theta_to_state: the bubble initialisation of Sec. 4.2 (the reading
+ *   that fixes pressure at the isentropic background, temperature
+ *   (theta0 + theta') pi with the Exner function pi = 1 - g z/(cp theta0),
+ *   fluid at rest, rhoE = pbar/(gamma-1) + rho g z), node by node: with the
+ *   cosine theta' it is bitwise adg_init_scenario(ADG_SCEN_COSINE).  Needs
+ *   gravity (ADG_EINVAL otherwise).
+ * adg_theta_to_state_adjoint: lam_theta = (d u / d theta')^T lam_u at theta_p.
+ * adg_state_to_theta: theta' = T (p0/p)^(R/cp) - theta0 at the nodes.
+ * adg_probe_objective: J = sum_p (theta'(x_p) - target_p)^2, theta'
+ *   interpolated by the cell's nodal Lagrange basis at the probe points
+ *   probes_xy[2p], probes_xy[2p+1] (device, nprobes pairs; a point outside
+ *   the mesh uses the nearest cell), target device [nprobes].  Writes the
+ *   residuals theta'(x_p) - target_p to residual (device [nprobes]), J to
+ *   *J (device scalar) and, if dJ_du is not NULL, dJ/du (device, state
+ *   layout).  Sums run in a fixed order (bitwise reproducible). */
+int adg_theta_to_state(adg_mesh* m, const double* theta_p, double* u, void* stream);
+int adg_theta_to_state_adjoint(adg_mesh* m, const double* theta_p, const double* lam_u, double* lam_theta,
+                               void* stream);
+int adg_state_to_theta(adg_mesh* m, const double* u, double* theta_p, void* stream);
+int adg_probe_objective(adg_mesh* m, const double* u, int nprobes, const double* probes_xy, const double* target,
+                        double* residual, double* J, double* dJ_du, void* stream);
+
 /* Strip decomposition (bc_y = ADG_BC_EXCHANGE*): the one exchange of an
  * ADER-DG step (Sec. 1: the scheme communicates once per step) is the face
  * trace of the cells along a strip edge.  After adg_predictor,

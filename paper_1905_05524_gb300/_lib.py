@@ -121,6 +121,10 @@ SIGNATURES = {
     "adg_step_tv": (_I, [_P, _D, _I, _D, _D, _P, _P, _P, _P]),
     "adg_check_finite": (_I, [_P, _P]),
     "adg_step_adjoint": (_I, [_P, _D, _P, _P, _P, _P]),
+    "adg_theta_to_state": (_I, [_P, _P, _P, _P]),
+    "adg_theta_to_state_adjoint": (_I, [_P, _P, _P, _P, _P]),
+    "adg_state_to_theta": (_I, [_P, _P, _P, _P]),
+    "adg_probe_objective": (_I, [_P, _P, _I, _P, _P, _P, _P, _P, _P]),
     "adg_get_boundary_traces": (_I, [_P, _P, _P, _P]),
     "adg_set_halo_traces": (_I, [_P, _P, _P, _P]),
     "adg_tv_flags": (_I, [_P, _P, _D, _D, _D, _D, _D, _P, _P]),

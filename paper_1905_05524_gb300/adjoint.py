@@ -10,14 +10,12 @@ Around it, for the warm-bubble sensitivity problem: the map from nodal
 initial theta' to the conserved state (the bubble initialisation of
 Sec. 4.2: p = pbar, T = (theta0 + theta') pi, v = 0) and the probe objective
 J = sum_p (theta'(T, x_p) - target_p)^2 with theta' interpolated in the
-probe's cell by the nodal Lagrange basis.  These two are small element-wise
-set-up/read-out maps written with torch operations (autograd differentiates
-them); the stepping and its adjoint run in libaderdg.so.
+probe's cell by the nodal Lagrange basis.  Both maps and their adjoints run
+in libaderdg.so too (adg_theta_to_state, adg_theta_to_state_adjoint,
+adg_probe_objective); the autograd Functions below only pass device arrays.
 """
 import ctypes
-import math
 
-import numpy as np
 import torch
 
 from . import _lib as L
@@ -68,69 +66,77 @@ class Rollout(torch.autograd.Function):
 
 
 # ------------------------------------------------------------ bubble problem
-def _gl(n):
-    x, _ = np.polynomial.legendre.leggauss(n)
-    return 0.5 * (x + 1.0)
+class ThetaToState(torch.autograd.Function):
+    """u = state(theta') (adg_theta_to_state); backward: adg_theta_to_state_adjoint."""
+
+    @staticmethod
+    def forward(ctx, theta_p, mesh):
+        th = theta_p.detach().contiguous()
+        n = mesh.cfg.degree + 1
+        u = torch.empty(th.shape[0], 4, n, n, dtype=torch.float64, device=th.device)
+        L.check(mesh._lib.adg_theta_to_state(mesh.h, ctypes.c_void_p(th.data_ptr()), ctypes.c_void_p(u.data_ptr()),
+                                             _sp()))
+        ctx.mesh = mesh
+        ctx.save_for_backward(th)
+        return u
+
+    @staticmethod
+    def backward(ctx, lam_u):
+        (th,) = ctx.saved_tensors
+        lam_u = lam_u.contiguous()
+        out = torch.empty_like(th)
+        L.check(ctx.mesh._lib.adg_theta_to_state_adjoint(ctx.mesh.h, ctypes.c_void_p(th.data_ptr()),
+                                                         ctypes.c_void_p(lam_u.data_ptr()),
+                                                         ctypes.c_void_p(out.data_ptr()), _sp()))
+        return out, None
 
 
-def node_heights(cfg, device):
-    n = cfg.degree + 1
-    xi = torch.tensor(_gl(n), dtype=torch.float64, device=device)
-    iy = torch.arange(cfg.nx * cfg.ny, device=device) // cfg.nx
-    z = cfg.y0 + (iy[:, None].double() + xi[None, :]) * (cfg.Ly / cfg.ny)  # [c, j]
-    return z[:, :, None].expand(-1, n, n)
+class ProbeObjective(torch.autograd.Function):
+    """J(u) = sum_p (theta'(u; x_p) - target_p)^2 (adg_probe_objective, which
+    also returns dJ/du for the backward)."""
+
+    @staticmethod
+    def forward(ctx, u, mesh, probes_xy, target):
+        u = u.detach().contiguous()
+        xy = probes_xy.contiguous()
+        tg = target.contiguous()
+        resid = torch.empty_like(tg)
+        J = torch.empty((), dtype=torch.float64, device=u.device)
+        g = torch.empty_like(u)
+        L.check(mesh._lib.adg_probe_objective(mesh.h, ctypes.c_void_p(u.data_ptr()), int(tg.numel()),
+                                              ctypes.c_void_p(xy.data_ptr()), ctypes.c_void_p(tg.data_ptr()),
+                                              ctypes.c_void_p(resid.data_ptr()), ctypes.c_void_p(J.data_ptr()),
+                                              ctypes.c_void_p(g.data_ptr()), _sp()))
+        ctx.save_for_backward(g)
+        return J
+
+    @staticmethod
+    def backward(ctx, gJ):
+        (g,) = ctx.saved_tensors
+        return gJ * g, None, None, None
 
 
-def theta_to_state(theta_p, cfg):
-    """Conserved state of the isentropic background (theta0, p0, g) carrying
-    the temperature perturbation theta' at rest (theta_p: [c, j, i])."""
-    z = node_heights(cfg, theta_p.device)
-    cp = cfg.gamma * cfg.R / (cfg.gamma - 1.0)
-    ex = 1.0 - cfg.g * z / (cp * cfg.theta0)
-    pb = cfg.p0 * ex ** (cp / cfg.R)
-    rho = pb / (cfg.R * (cfg.theta0 + theta_p) * ex)
-    E = pb / (cfg.gamma - 1.0) + rho * cfg.g * z
-    zero = torch.zeros_like(rho)
-    return torch.stack([rho, zero, zero, E], 1).contiguous()
+def theta_to_state(theta_p, mesh):
+    """Conserved state of the isentropic background carrying theta' at rest."""
+    return ThetaToState.apply(theta_p, mesh)
 
 
-def state_to_theta(u, cfg):
-    """theta' = T (p0/p)^(R/cp) - theta0 at the nodes."""
-    z = node_heights(cfg, u.device)
-    cp = cfg.gamma * cfg.R / (cfg.gamma - 1.0)
-    rho, mx, my, E = u[:, 0], u[:, 1], u[:, 2], u[:, 3]
-    p = (cfg.gamma - 1.0) * (E - 0.5 * (mx * mx + my * my) / rho - rho * cfg.g * z)
-    T = p / (rho * cfg.R)
-    return T * (cfg.p0 / p) ** (cfg.R / cp) - cfg.theta0
+def state_to_theta(u, mesh):
+    """theta' = T (p0/p)^(R/cp) - theta0 at the nodes (adg_state_to_theta)."""
+    u = u.detach().contiguous()
+    n = mesh.cfg.degree + 1
+    th = torch.empty(u.shape[0], n, n, dtype=torch.float64, device=u.device)
+    L.check(mesh._lib.adg_state_to_theta(mesh.h, ctypes.c_void_p(u.data_ptr()), ctypes.c_void_p(th.data_ptr()),
+                                         _sp()))
+    return th
 
 
-def probe_operator(cfg, probes, device):
-    """(cell index, weights [P, n, n]) of Lagrange interpolation at probe points."""
-    n = cfg.degree + 1
-    xi = _gl(n)
-    hx, hy = cfg.Lx / cfg.nx, cfg.Ly / cfg.ny
-    cells, W = [], []
-    for (x, y) in probes:
-        ix = min(int((x - cfg.x0) / hx), cfg.nx - 1)
-        iy = min(int((y - cfg.y0) / hy), cfg.ny - 1)
-        sx = (x - cfg.x0) / hx - ix
-        sy = (y - cfg.y0) / hy - iy
-        lx = np.array([np.prod([(sx - xi[m]) / (xi[a] - xi[m]) for m in range(n) if m != a]) for a in range(n)])
-        ly = np.array([np.prod([(sy - xi[m]) / (xi[a] - xi[m]) for m in range(n) if m != a]) for a in range(n)])
-        cells.append(iy * cfg.nx + ix)
-        W.append(np.outer(ly, lx))  # [j, i]
-    return (torch.tensor(cells, device=device),
-            torch.tensor(np.array(W), dtype=torch.float64, device=device))
+def probe_objective(u, mesh, probes_xy, target):
+    return ProbeObjective.apply(u, mesh, probes_xy, target)
 
 
-def probe_objective(u, cfg, cells, W, target):
-    th = state_to_theta(u, cfg)                       # [c, j, i]
-    vals = (th[cells] * W).sum(dim=(1, 2))           # [P]
-    return ((vals - target) ** 2).sum()
-
-
-def objective_from_theta(theta0_p, mesh, dt, nsteps, ckpt_every, cells, W, target):
+def objective_from_theta(theta0_p, mesh, dt, nsteps, ckpt_every, probes_xy, target):
     """J(theta'_0) through the GPU rollout (differentiable)."""
-    u0 = theta_to_state(theta0_p, mesh.cfg)
+    u0 = theta_to_state(theta0_p, mesh)
     uT = Rollout.apply(u0, mesh, dt, nsteps, ckpt_every)
-    return probe_objective(uT, mesh.cfg, cells, W, target)
+    return probe_objective(uT, mesh, probes_xy, target)
