@@ -93,13 +93,13 @@ def predictor_flops_per_cell(n):
 # kernel edited after its capture reports null instead of a stale figure.
 PREDICTOR_SOURCES = {
     "fp64": ["adg_fp64.cu", "adg_fp64_body.cuh", "adg_physics.cuh", "adg_internal.h"],
-    "mixed": ["adg_mixed.cu", "adg_mixed_point.cuh", "adg_convert.cuh", "adg_internal.h"],
+    "mixed": ["adg_mixed.cu", "adg_mixed_body.cuh", "adg_mixed_point.cuh", "adg_convert.cuh", "adg_internal.h"],
 }
 PREDICTOR_COUNTERS = {
-    "fp64": {"sha256": "4d6445e1e6597b7ce537af6c3eae5ee8aeea792b5ab797d7acb67fc3dcd9671a",
+    "fp64": {"sha256": "20bd7fb29a7026a17d8e447cdce8b87c431994d217cfb9575ed713ac2b3801cd",
              "traffic": 7851520 + 0, "smem_frac": None},
-    "mixed": {"sha256": "a80949a04524c55ac3b87d65b4eecdca4aed1287b5821c5f7f88b43cb1a1f1e6",
-              "traffic": 7654400 + 0, "smem_frac": 0.735},
+    "mixed": {"sha256": "bbdb336d4198313cb0e30fc8ef147ec403b488932379a1b875f887d7a2a97842",
+              "traffic": 7654144 + 0, "smem_frac": 0.732},
 }
 
 
@@ -491,8 +491,8 @@ def run_amr(args, dev):
     import numpy as np
     import torch
     from paper_1905_05524_gb300 import _lib as L
-    from paper_1905_05524_gb300.solver import Mesh, atmosphere_config
-    def amr_run(prec):
+    from paper_1905_05524_gb300.solver import Batch, Mesh, atmosphere_config
+    def amr_run(prec, batched=False):
         cfg = atmosphere_config(degree=DEGREE, nx=27, ny=27, mu=0.001, device=dev.index, precision=prec)
         cfg.max_levels = 2
         m = Mesh(cfg)
@@ -509,10 +509,14 @@ def run_amr(args, dev):
         t_steps = 0.0
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         leaf_hist = []
+        batch = Batch([m]) if batched else None
         for s0 in range(0, steps, every):
             k = min(every, steps - s0)
             ev0.record()
-            m.step(dt, k)
+            if batch is not None:
+                batch.step([dt], nsteps=k)  # rebuilt and re-captured after each adaptation
+            else:
+                m.step(dt, k)
             ev1.record()
             ev1.synchronize()
             t_steps += ev0.elapsed_time(ev1) * 1e-3
@@ -524,11 +528,15 @@ def run_amr(args, dev):
         wall = time.perf_counter() - t0
         res = dict(dt=dt, steps=steps, every=every, dof_updates=dof_updates, t_steps=t_steps, wall=wall,
                    leaves=m.leaf_info(), ua=m.get_state().cpu().numpy(), leaf_hist=leaf_hist)
+        if batch is not None:
+            res["batch_info"] = batch.info()
+            batch.close()
         m.close()
         return res
 
     r64 = amr_run(L.ADG_PREC_FP64)
     rmx = amr_run(L.ADG_PREC_MIXED)
+    rbt = amr_run(L.ADG_PREC_MIXED, batched=True)
     dt, steps, every = r64["dt"], r64["steps"], r64["every"]
     dof_updates, t_steps, wall = r64["dof_updates"], r64["t_steps"], r64["wall"]
     leaves, ua, leaf_hist = r64["leaves"], r64["ua"], r64["leaf_hist"]
@@ -564,6 +572,14 @@ def run_amr(args, dev):
              "theta_prime_rel_l2_vs_fp64_amr": float(np.sqrt((W * (thm - tha) ** 2).sum()) /
                                                        np.sqrt((W * tha ** 2).sum())),
              "form": "FP32 predictor on perturbations, FP64 corrector with hanging faces, FP64 TV and adaptation"}
+    mixed_batched = {"value": rbt["dof_updates"] / rbt["t_steps"],
+                     "value_including_regrid": rbt["dof_updates"] / rbt["wall"], "unit": UNIT,
+                     "same_leaves_as_mixed": rbt["leaves"] == rmx["leaves"],
+                     "state_equal_to_mixed": bool(np.array_equal(rbt["ua"], rmx["ua"])),
+                     "batch": rbt.get("batch_info"),
+                     "form": "the same adaptive mixed instance stepped through adg_batch_step: every level's "
+                             "leaves in one persistent predictor and one persistent corrector launch per step, "
+                             "10-step CUDA graphs re-captured after each adaptation"}
     return {
         "metric": METRIC + " (two-bubble AMR run)", "value": dof_updates / t_steps, "unit": UNIT,
         "dtype": "f64", "steps": steps, "regrid_every": every,
@@ -571,6 +587,7 @@ def run_amr(args, dev):
         "leaves_final": len(leaves), "leaves_per_level": [levels.count(l) for l in range(3)],
         "leaves_mean": float(np.mean(leaf_hist)),
         "mixed": mixed,
+        "mixed_batched": mixed_batched,
         "uniform_reference": {"cells": side * side, "value": side * side * n * n * 4 * steps / t_uni, "unit": UNIT,
                               "seconds": t_uni},
         "uniform_equivalent_value": side * side * n * n * 4 * steps / t_steps,

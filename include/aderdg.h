@@ -263,18 +263,31 @@ int adg_check_finite(adg_mesh* m, void* stream);
  * per step one persistent predictor launch and one persistent corrector
  * launch walk a static list of tiles (instance, first cell) across all
  * instances; nsteps steps are captured once into a CUDA graph and replayed.
+ * Instances may be uniform or adaptive (desc.max_levels > 0, Sec. 3's
+ * dynamic AMR): the tiles of an adaptive instance cover its leaves of every
+ * level, which run the adaptive mixed predictor and the FP64 corrector with
+ * its hanging faces inside the same persistent launches.  After an
+ * adg_adapt of a member, the next adg_batch_step synchronises the device,
+ * rebuilds the instance tables and tile lists from the new leaves and
+ * captures the graph again.
  * adg_batch_create times the predictor's tile-size candidates on the batch
- * and keeps the fastest (cached per degree, SM count and size class).
+ * and keeps the fastest, cached per (degree, precision, SM count, size class,
+ * adaptive or not) in memory and in a JSON file: $ADG_TUNE_CACHE if set (an
+ * empty value keeps the cache in memory only), else tune_cache.json beside
+ * the library; an entry found there is used without timing.
  *
- *   meshes   k meshes of one degree and device, all ADG_PREC_MIXED
+ *   meshes   k distinct meshes of one degree and device, all ADG_PREC_MIXED
  *            (ADG_EUNSUPPORTED otherwise); they stay owned by the caller and
  *            must outlive the batch; their states are advanced in place
  *   dt       host array of k time steps (> 0), one per instance
  *   nsteps   steps per call (>= 1); each instance's time += nsteps * dt
  *   info     adg_batch_info fills up to n of: predictor tiles, cells per
  *            predictor tile, predictor grid, corrector tiles, cells per
- *            corrector tile, corrector grid, tuned time of candidates 0..2 (ns)
- * adg_batch_step synchronises `stream` only when the dt array changed. */
+ *            corrector tile, corrector grid, tuned time of candidates 0..2
+ *            (ns; 0 when the cache decided), chosen candidate, where the
+ *            choice came from (0 timed now, 2 cache), adaptive instances
+ * adg_batch_step synchronises `stream` only when the dt array changed or a
+ * member adapted. */
 typedef struct adg_batch adg_batch;
 int adg_batch_create(adg_mesh* const* meshes, int k, adg_batch** out);
 int adg_batch_step(adg_batch* b, const double* dt, int nsteps, void* stream);

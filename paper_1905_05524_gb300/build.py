@@ -68,7 +68,7 @@ def build(verbose=False, jobs=None):
             if verbose and out.strip():
                 print(out)
     if _stale(LIB, objs):
-        _run([nvcc, *ARCH, "-shared", "-o", LIB, *objs, "-lcudart"])
+        _run([nvcc, *ARCH, "-shared", "-o", LIB, *objs, "-lcudart", "-ldl"])
     return LIB
 
 

@@ -32,6 +32,7 @@
 #include "adg_fp64_body.cuh"
 #include "adg_internal.h"
 #include "adg_mesh.h"
+#include "adg_mixed_body.cuh"
 #include "adg_mixed_point.cuh"
 #include "adg_physics.cuh"
 #include "adg_tv_cell.cuh"
@@ -407,17 +408,20 @@ struct AmrMixCfg {
 // extrapolated (rhobar, Ebar); mbf [leaves][n][3] (pbar, d rhobar/dz,
 // d Ebar/dz) then [leaves][2 N, S][2] (extrapolated rhobar, (gamma-1)(Ebar -
 // rhobar g z_face)).
+// Body of the tile of CPB leaves starting at leaf c0; shared by the per-mesh
+// kernel and the batched persistent kernels.
 template <int N, int CPB>
-__global__ void __launch_bounds__(CPB*(N + 1) * (N + 1))
-k_predictor_amr_mixed(const double* __restrict__ u, double* __restrict__ rvol, double* __restrict__ trace, int cells,
-                      float dt, const BasisF B, const PhysF P, const double* __restrict__ geo,
-                      const double* __restrict__ mb64, const float* __restrict__ mbf) {
+__device__ __forceinline__ void predictor_amr_mixed_body(const double* __restrict__ u, double* __restrict__ rvol,
+                                                         double* __restrict__ trace, int cells, int c0, float dt,
+                                                         const BasisF& B, const PhysF& P,
+                                                         const double* __restrict__ geo,
+                                                         const double* __restrict__ mb64,
+                                                         const float* __restrict__ mbf, float* smf) {
     constexpr int n = N + 1, n2 = n * n, SL = 4 * n2;
-    extern __shared__ float smf[];
     const int cl = threadIdx.x / n2;
     const int node = threadIdx.x - cl * n2;
     const int j = node / n, i = node - j * n;
-    const int cell_raw = blockIdx.x * CPB + cl;
+    const int cell_raw = c0 + cl;
     const bool active = cell_raw < cells;
     const int cell = active ? cell_raw : cells - 1;
     constexpr int NPAIR = AmrMixCfg<N>::npair, PS = 4 * n2;  // slice pairs, pair stride (float2)
@@ -640,6 +644,15 @@ k_predictor_amr_mixed(const double* __restrict__ u, double* __restrict__ rvol, d
     }
 }
 
+template <int N, int CPB>
+__global__ void __launch_bounds__(CPB*(N + 1) * (N + 1))
+k_predictor_amr_mixed(const double* __restrict__ u, double* __restrict__ rvol, double* __restrict__ trace, int cells,
+                      float dt, const BasisF B, const PhysF P, const double* __restrict__ geo,
+                      const double* __restrict__ mb64, const float* __restrict__ mbf) {
+    extern __shared__ float smf[];
+    predictor_amr_mixed_body<N, CPB>(u, rvol, trace, cells, blockIdx.x * CPB, dt, B, P, geo, mb64, mbf, smf);
+}
+
 // face data (q-bar and normal flux) of record `rec` of a coarse face evaluated
 // on its third `s` at fine node m
 __device__ __forceinline__ void prolong_rec(const double* rec, int n, const AmrOps& O, int s, int m, double q[4],
@@ -657,17 +670,18 @@ __device__ __forceinline__ void prolong_rec(const double* rec, int n, const AmrO
 }
 
 template <int N, int CPB>
-__global__ void __launch_bounds__(CPB*(N + 1) * (N + 1))
-k_corrector_amr(double* __restrict__ u, const double* __restrict__ rvol, const double* __restrict__ trace,
-                int cells, double dt, const Basis B, const Phys P0, const AmrOps O, const double* __restrict__ geo,
-                const int* __restrict__ nbr, const double* __restrict__ bgl) {
+__device__ __forceinline__ void corrector_amr_body(double* __restrict__ u, const double* __restrict__ rvol,
+                                                   const double* __restrict__ trace, int cells, int c0, double dt,
+                                                   const Basis& B, const Phys& P0, const AmrOps& O,
+                                                   const double* __restrict__ geo, const int* __restrict__ nbr,
+                                                   const double* __restrict__ bgl) {
     constexpr int n = N + 1, n2 = n * n, SL = 4 * n2, TR = kTraceComps * n;
     __shared__ double Fsub[CPB][4][3][4][n];
     __shared__ double Fst[CPB][4][4][n];
     const int cl = threadIdx.x / n2;
     const int node = threadIdx.x - cl * n2;
     const int j = node / n, i = node - j * n;
-    const int cell_raw = blockIdx.x * CPB + cl;
+    const int cell_raw = c0 + cl;
     const bool active = cell_raw < cells;
     const int cell = active ? cell_raw : cells - 1;
     const Phys P = leaf_phys(P0, geo, cell, N);
@@ -779,6 +793,14 @@ k_corrector_amr(double* __restrict__ u, const double* __restrict__ rvol, const d
                             (B.lift1[j] * Fst[cl][2][v][i] - B.lift0[j] * Fst[cl][3][v][i]) * P.inv_hy;
         uc[v * n2 + node] += dt * (rc[v * n2 + node] - face);
     }
+}
+
+template <int N, int CPB>
+__global__ void __launch_bounds__(CPB*(N + 1) * (N + 1))
+k_corrector_amr(double* __restrict__ u, const double* __restrict__ rvol, const double* __restrict__ trace,
+                int cells, double dt, const Basis B, const Phys P0, const AmrOps O, const double* __restrict__ geo,
+                const int* __restrict__ nbr, const double* __restrict__ bgl) {
+    corrector_amr_body<N, CPB>(u, rvol, trace, cells, blockIdx.x * CPB, dt, B, P0, O, geo, nbr, bgl);
 }
 
 template <int N, int CPB>
@@ -1033,6 +1055,148 @@ static int amr_transfer(adg_mesh* m, const double* uold, double* unew, int leave
     AMR_DISPATCH(transfer_n, m, uold, unew, leaves, trans, s)
 }
 
+
+// ------------------------------------------------------------------ batches
+// Batched persistent kernels: a fixed grid walks a list of tiles of many
+// independent meshes -- uniform instances (tile.inst >= 0, the mixed
+// predictor and corrector bodies of adg_mixed_body.cuh) and adaptive ones
+// (tile.inst < 0, the leaves of every level: the mixed leaf predictor and the
+// FP64 corrector with its hanging faces).  Tile t goes to block t mod grid,
+// so the schedule is static and the results do not depend on timing.  Both
+// kinds run CPB cells (leaves) per block with one thread per node.
+template <int N, int CPB>
+struct BatchSmem {
+    static constexpr size_t uni = MixCfg<N, CPB>::smem_pred;
+    static constexpr size_t amr = (size_t)CPB * AmrMixCfg<N>::stride * sizeof(float);
+    static constexpr size_t bytes = uni > amr ? uni : amr;
+};
+
+template <int N, int CPB, bool AMR>
+__global__ void __launch_bounds__(CPB*(N + 1) * (N + 1), (AMR ? 1 : MixCfg<N, CPB>::minb))
+k_predictor_batch(const MixedInst* __restrict__ insts, const AmrInst* __restrict__ ainsts,
+                  const BatchTile* __restrict__ tiles, int ntiles, const BasisF B) {
+    extern __shared__ float smf[];
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const BatchTile tl = tiles[t];
+        if (!AMR || tl.inst >= 0) {
+            const MixedInst& I = insts[tl.inst];
+            const PhysF P = I.P;
+            const MixedBg bg = I.bg;
+            predictor_mixed_body<N, CPB>(I.u, I.rvol, I.trace, I.cells, tl.c0, I.dtf, B, P, bg, smf);
+        } else {
+            const AmrInst& I = ainsts[-tl.inst - 1];
+            const PhysF P = I.Pf;
+            predictor_amr_mixed_body<N, CPB>(I.u, I.rvol, I.trace, I.cells, tl.c0, I.dtf, B, P, I.geo, I.mb64,
+                                             I.mbf, smf);
+        }
+        __syncthreads();
+    }
+}
+
+template <int N, int CPB, bool AMR>
+__global__ void __launch_bounds__(CPB*(N + 1) * (N + 1))
+k_corrector_batch(const MixedInst* __restrict__ insts, const AmrInst* __restrict__ ainsts,
+                  const BatchTile* __restrict__ tiles, int ntiles, const BasisF Bf, const Basis B, const AmrOps O) {
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const BatchTile tl = tiles[t];
+        if (!AMR || tl.inst >= 0) {
+            const MixedInst& I = insts[tl.inst];
+            const PhysF P = I.P;
+            const MixedBg bg = I.bg;
+            corrector_mixed_body<N, CPB>(I.u, I.rvol, I.trace, I.cells, tl.c0, I.dt, Bf, P, bg);
+        } else {
+            const AmrInst& I = ainsts[-tl.inst - 1];
+            const Phys P = I.P;
+            corrector_amr_body<N, CPB>(I.u, I.rvol, I.trace, I.cells, tl.c0, I.dt, B, P, O, I.geo, I.nbr, I.bgl);
+        }
+        __syncthreads();
+    }
+}
+
+// Tile-size candidates per degree: half, default and double the default cells
+// per block (kept within 1024 threads and the shared-memory limit).
+template <int N, int K>
+struct BatchCand {
+    static constexpr int base = MixCfg<N>::cpb_default;
+    static constexpr int raw = K == 0 ? base / 2 : K == 1 ? base : base * 2;
+    static constexpr int cpb = raw < 1 ? 1 : ((raw * (N + 1) * (N + 1) > 1024) ? base : raw);
+};
+
+template <int N, int K, bool AMR>
+static int batch_nka(int phase, const MixedInst* insts, const AmrInst* ainsts, const BatchTile* tiles, int ntiles,
+                     const BasisF& Bf, const Basis& B, const AmrOps* O, int* cpb_out, int* blocks_io,
+                     cudaStream_t s) {
+    constexpr int CPB = BatchCand<N, K>::cpb;
+    constexpr int threads = CPB * (N + 1) * (N + 1);
+    constexpr size_t smem = AMR ? BatchSmem<N, CPB>::bytes : MixCfg<N, CPB>::smem_pred;
+    if (cpb_out) *cpb_out = CPB;
+    if (!tiles) {  // query: set the smem limit and size the persistent grid (not during capture)
+        int per_sm = 0, dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaError_t e;
+        if (phase == 0) {
+            e = cudaFuncSetAttribute(k_predictor_batch<N, CPB, AMR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem);
+            if (e == cudaSuccess)
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_predictor_batch<N, CPB, AMR>, threads,
+                                                                  smem);
+        } else {
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_corrector_batch<N, CPB, AMR>, threads, 0);
+        }
+        if (e != cudaSuccess) return (int)e;
+        if (blocks_io) *blocks_io = per_sm > 0 ? per_sm * sms : sms;
+        return 0;
+    }
+    const int blocks = *blocks_io;
+    if (phase == 0) {
+        k_predictor_batch<N, CPB, AMR><<<blocks, threads, smem, s>>>(insts, ainsts, tiles, ntiles, Bf);
+    } else {
+        AmrOps none;
+        if (!O) std::memset(&none, 0, sizeof(none));
+        k_corrector_batch<N, CPB, AMR><<<blocks, threads, 0, s>>>(insts, ainsts, tiles, ntiles, Bf, B, O ? *O : none);
+    }
+    return (int)cudaGetLastError();
+}
+
+template <int N>
+static int batch_n(int cand, int phase, const MixedInst* insts, const AmrInst* ainsts, const BatchTile* tiles,
+                   int ntiles, const BasisF& Bf, const Basis& B, const AmrOps* O, int* cpb_out, int* blocks_out,
+                   cudaStream_t s) {
+    const bool amr = ainsts != nullptr;
+#define ADG_BATCH_CASE(K)                                                                                    \
+    case K:                                                                                                  \
+        return amr ? batch_nka<N, K, true>(phase, insts, ainsts, tiles, ntiles, Bf, B, O, cpb_out, blocks_out, s) \
+                   : batch_nka<N, K, false>(phase, insts, ainsts, tiles, ntiles, Bf, B, O, cpb_out, blocks_out, s);
+    switch (cand) {
+        ADG_BATCH_CASE(0)
+        ADG_BATCH_CASE(1)
+        ADG_BATCH_CASE(2)
+    }
+#undef ADG_BATCH_CASE
+    return (int)cudaErrorInvalidValue;
+}
+
+int launch_batch_mixed(int N, int cand, int phase, const MixedInst* insts, const AmrInst* ainsts,
+                       const BatchTile* tiles, int ntiles, const BasisF& Bf, const Basis& B, const void* ops,
+                       int* cpb_out, int* blocks_out, void* stream) {
+    cudaStream_t s = (cudaStream_t)stream;
+    const AmrOps* O = (const AmrOps*)ops;
+    switch (N) {
+        case 1: return batch_n<1>(cand, phase, insts, ainsts, tiles, ntiles, Bf, B, O, cpb_out, blocks_out, s);
+        case 2: return batch_n<2>(cand, phase, insts, ainsts, tiles, ntiles, Bf, B, O, cpb_out, blocks_out, s);
+        case 3: return batch_n<3>(cand, phase, insts, ainsts, tiles, ntiles, Bf, B, O, cpb_out, blocks_out, s);
+        case 4: return batch_n<4>(cand, phase, insts, ainsts, tiles, ntiles, Bf, B, O, cpb_out, blocks_out, s);
+        case 5: return batch_n<5>(cand, phase, insts, ainsts, tiles, ntiles, Bf, B, O, cpb_out, blocks_out, s);
+        case 6: return batch_n<6>(cand, phase, insts, ainsts, tiles, ntiles, Bf, B, O, cpb_out, blocks_out, s);
+        case 7: return batch_n<7>(cand, phase, insts, ainsts, tiles, ntiles, Bf, B, O, cpb_out, blocks_out, s);
+    }
+    return (int)cudaErrorInvalidValue;
+}
+
+// the prolongation/restriction operators of an adaptive mesh (for batches)
+const void* amr_ops(const adg_mesh* m) { return m->tree ? &((const AmrTree*)m->tree)->ops : nullptr; }
+
 }  // namespace adg
 
 // ------------------------------------------------------------------ C ABI
@@ -1161,6 +1325,7 @@ extern "C" int adg_adapt(adg_mesh* m, const int8_t* flags_dev, int* leaves_out, 
     if (rc) return rc;
     ADG_CK(cudaStreamSynchronize(s), "adapt: transfer sync");
     std::swap(m->u, m->u_spare);
+    ++m->epoch;  // the state (and, if grown, every per-leaf buffer) moved: batches rebuild their tables
     if (grew) {  // the spare (the old state) still has the old capacity
         cudaFree(m->u_spare);
         m->u_spare = nullptr;

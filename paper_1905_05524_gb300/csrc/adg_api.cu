@@ -2,8 +2,12 @@
 // state transfer and the host side of every entry point in include/aderdg.h.
 #include <cuda_runtime.h>
 
+#include <dlfcn.h>
+
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -951,16 +955,23 @@ extern "C" int adg_step_noalloc(const adg_mesh_desc* d, double* u, size_t count,
 }
 
 // ---------------------------------------------------------------------------
-// Batched persistent step: many independent meshes (instances of different
-// sizes) advanced by one predictor and one corrector launch per step, each a
+// Batched persistent step: many independent mixed-precision meshes --
+// uniform instances of different sizes and adaptive ones with leaves of every
+// level -- advanced by one predictor and one corrector launch per step, each a
 // persistent grid walking a static tile list; nsteps steps are captured once
 // into a CUDA graph and replayed.  The tile size (cells per block) of the
-// predictor is chosen by timing the candidates on the batch itself.
+// predictor is chosen by timing the candidates on the batch itself, and the
+// choice is kept in a JSON cache keyed by degree, precision and SM count.
 struct adg_batch {
     int device = 0, N = 0, k = 0;
     std::vector<adg_mesh*> meshes;
+    std::vector<int> slot;                  // mesh -> index in its kind's table (uniform or adaptive)
+    std::vector<unsigned> epoch;            // mesh epochs the tables were built for
     std::vector<adg::MixedInst> host_insts;
+    std::vector<adg::AmrInst> host_ainsts;
     adg::MixedInst* insts = nullptr;
+    adg::AmrInst* ainsts = nullptr;
+    const void* ops = nullptr;              // prolongation/restriction of the adaptive instances
     adg::BatchTile* tiles_pred = nullptr;
     adg::BatchTile* tiles_corr = nullptr;
     int ntiles_pred = 0, ntiles_corr = 0;
@@ -973,36 +984,106 @@ struct adg_batch {
     cudaGraph_t graph = nullptr;
     int graph_steps = 0;
     double tune_ms[adg::kBatchCandidates] = {0, 0, 0};
+    int tune_source = 0;                    // 0: timed now, 1: in-process cache, 2: JSON cache file
 };
 
 namespace {
 
 std::mutex g_tune_mu;
 std::vector<std::pair<std::string, int>> g_tune_cache;  // key -> candidate
+bool g_tune_file_read = false;
 
-std::vector<adg::BatchTile> make_tiles(const std::vector<adg_mesh*>& ms, int cpb) {
+// The JSON tuner cache: $ADG_TUNE_CACHE if set (an empty value disables the
+// file), else tune_cache.json beside libaderdg.so.  One entry per line,
+//   {"key": "<degree, precision, SM count, problem-size bucket>", "candidate": c},
+// inside a JSON array; a missing or unreadable file is an empty cache.
+std::string tune_cache_path() {
+    if (const char* env = std::getenv("ADG_TUNE_CACHE")) return env;
+    Dl_info info;
+    if (dladdr((void*)&tune_cache_path, &info) && info.dli_fname) {
+        std::string f(info.dli_fname);
+        const size_t slash = f.rfind('/');
+        return (slash == std::string::npos ? std::string(".") : f.substr(0, slash)) + "/tune_cache.json";
+    }
+    return "";
+}
+
+void read_tune_file() {  // caller holds g_tune_mu
+    g_tune_file_read = true;
+    const std::string path = tune_cache_path();
+    if (path.empty()) return;
+    FILE* f = std::fopen(path.c_str(), "r");
+    if (!f) return;
+    char line[512];
+    while (std::fgets(line, sizeof(line), f)) {
+        const char* k = std::strstr(line, "\"key\": \"");
+        const char* c = std::strstr(line, "\"candidate\": ");
+        if (!k || !c) continue;
+        k += 8;
+        const char* e = std::strchr(k, '"');
+        int cand = -1;
+        if (!e || std::sscanf(c + 13, "%d", &cand) != 1 || cand < 0 || cand >= adg::kBatchCandidates) continue;
+        const std::string key(k, e - k);
+        bool have = false;
+        for (auto& kv : g_tune_cache) have = have || kv.first == key;
+        if (!have) g_tune_cache.push_back({key, cand});
+    }
+    std::fclose(f);
+}
+
+void write_tune_file() {  // caller holds g_tune_mu; best effort (a read-only location keeps the cache in memory)
+    const std::string path = tune_cache_path();
+    if (path.empty()) return;
+    const std::string tmp = path + ".tmp";
+    FILE* f = std::fopen(tmp.c_str(), "w");
+    if (!f) return;
+    std::fprintf(f, "[\n");
+    for (size_t i = 0; i < g_tune_cache.size(); ++i)
+        std::fprintf(f, "  {\"key\": \"%s\", \"candidate\": %d}%s\n", g_tune_cache[i].first.c_str(),
+                     g_tune_cache[i].second, i + 1 < g_tune_cache.size() ? "," : "");
+    std::fprintf(f, "]\n");
+    std::fclose(f);
+    std::rename(tmp.c_str(), path.c_str());
+}
+
+std::vector<adg::BatchTile> make_tiles(const adg_batch* b, int cpb) {
     std::vector<adg::BatchTile> t;
-    for (int a = 0; a < (int)ms.size(); ++a)
-        for (int c = 0; c < ms[a]->cells; c += cpb) t.push_back({a, c});
+    for (int a = 0; a < b->k; ++a) {
+        const adg_mesh* m = b->meshes[a];
+        const int id = m->amr ? -b->slot[a] - 1 : b->slot[a];
+        for (int c = 0; c < m->cells; c += cpb) t.push_back({id, c});
+    }
     return t;
+}
+
+void drop_graph(adg_batch* b) {
+    if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
+    if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
+    b->graph_steps = 0;
 }
 
 void free_batch(adg_batch* b) {
     if (!b) return;
-    if (b->exec) cudaGraphExecDestroy(b->exec);
-    if (b->graph) cudaGraphDestroy(b->graph);
+    drop_graph(b);
     if (b->cap) cudaStreamDestroy(b->cap);
     cudaFree(b->insts);
+    cudaFree(b->ainsts);
     cudaFree(b->tiles_pred);
     cudaFree(b->tiles_corr);
     delete b;
 }
 
+int launch_phase(adg_batch* b, int cand, int phase, const adg::BatchTile* tiles, int ntiles, int* cpb, int* blocks,
+                 cudaStream_t s) {
+    return adg::launch_batch_mixed(b->N, cand, phase, b->insts, b->host_ainsts.empty() ? nullptr : b->ainsts, tiles,
+                                   ntiles, b->meshes[0]->Bf, b->meshes[0]->B, b->ops, cpb, blocks, s);
+}
+
 int upload_tiles(adg_batch* b, int cand, int phase, adg::BatchTile** dst, int* ntiles, int* cpb, int* blocks) {
     int c = 0, bl = 0;
-    int e = adg::launch_batch_mixed(b->N, cand, phase, nullptr, nullptr, 0, b->meshes[0]->Bf, &c, &bl, nullptr);
+    int e = launch_phase(b, cand, phase, nullptr, 0, &c, &bl, nullptr);
     if (e) return cuda_fail((cudaError_t)e, "batch: query");
-    std::vector<adg::BatchTile> t = make_tiles(b->meshes, c);
+    std::vector<adg::BatchTile> t = make_tiles(b, c);
     cudaFree(*dst);
     *dst = nullptr;
     if (cudaMalloc(dst, t.size() * sizeof(adg::BatchTile)) != cudaSuccess) {
@@ -1013,6 +1094,69 @@ int upload_tiles(adg_batch* b, int cand, int phase, adg::BatchTile** dst, int* n
     *ntiles = (int)t.size();
     *cpb = c;
     *blocks = bl;
+    return ADG_OK;
+}
+
+// (Re)build the instance tables from the meshes' current buffers and leaf
+// counts (after an adaptation of a member the state moved and the leaf count
+// changed); dt values are kept.
+int build_instances(adg_batch* b) {
+    b->host_insts.clear();
+    b->host_ainsts.clear();
+    b->cells = 0;
+    for (int a = 0; a < b->k; ++a) {
+        adg_mesh* m = b->meshes[a];
+        const double dt = b->last_dt[a] > 0.0 ? b->last_dt[a] : 0.0;
+        if (m->amr) {
+            adg::AmrInst I;
+            I.u = m->u;
+            I.rvol = m->rvol;
+            I.trace = m->trace;
+            I.cells = m->cells;
+            I.dt = dt;
+            I.dtf = (float)dt;
+            I.Pf = m->Pf;
+            I.P = m->P;
+            I.geo = m->geo;
+            I.nbr = m->nbr;
+            I.bgl = m->bgl;
+            I.mb64 = m->mbl64;
+            I.mbf = m->mblf;
+            b->slot[a] = (int)b->host_ainsts.size();
+            b->host_ainsts.push_back(I);
+            b->ops = adg::amr_ops(m);
+        } else {
+            adg::MixedInst I;
+            I.u = m->u;
+            I.rvol = (float*)m->rvol;
+            I.trace = (float*)m->trace;
+            I.cells = m->cells;
+            I.dt = dt;
+            I.dtf = (float)dt;
+            I.P = m->Pf;
+            I.bg = m->mbg;
+            b->slot[a] = (int)b->host_insts.size();
+            b->host_insts.push_back(I);
+        }
+        b->epoch[a] = m->epoch;
+        b->cells += m->cells;
+    }
+    cudaFree(b->insts);
+    cudaFree(b->ainsts);
+    b->insts = nullptr;
+    b->ainsts = nullptr;
+    const size_t nu = std::max<size_t>(1, b->host_insts.size()), na = std::max<size_t>(1, b->host_ainsts.size());
+    if (cudaMalloc(&b->insts, nu * sizeof(adg::MixedInst)) != cudaSuccess ||
+        cudaMalloc(&b->ainsts, na * sizeof(adg::AmrInst)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ADG_ENOMEM, "batch: instance tables");
+    }
+    if (!b->host_insts.empty())
+        ADG_CK(cudaMemcpy(b->insts, b->host_insts.data(), b->host_insts.size() * sizeof(adg::MixedInst),
+                          cudaMemcpyHostToDevice), "batch: instance table");
+    if (!b->host_ainsts.empty())
+        ADG_CK(cudaMemcpy(b->ainsts, b->host_ainsts.data(), b->host_ainsts.size() * sizeof(adg::AmrInst),
+                          cudaMemcpyHostToDevice), "batch: adaptive instance table");
     return ADG_OK;
 }
 
@@ -1027,8 +1171,8 @@ extern "C" int adg_batch_create(adg_mesh* const* meshes, int k, adg_batch** out)
             return fail(ADG_EINVAL, "batch_create: meshes must share degree and device");
         if (meshes[a]->d.precision != ADG_PREC_MIXED)
             return fail(ADG_EUNSUPPORTED, "batch_create: batched launch is built for ADG_PREC_MIXED meshes");
-        if (meshes[a]->amr)
-            return fail(ADG_EUNSUPPORTED, "batch_create: batched launch is built for uniform meshes");
+        for (int c = 0; c < a; ++c)
+            if (meshes[c] == meshes[a]) return fail(ADG_EINVAL, "batch_create: a mesh appears twice");
     }
     adg_batch* b = new adg_batch();
     b->device = meshes[0]->d.device;
@@ -1036,28 +1180,11 @@ extern "C" int adg_batch_create(adg_mesh* const* meshes, int k, adg_batch** out)
     b->k = k;
     b->meshes.assign(meshes, meshes + k);
     b->last_dt.assign(k, -1.0);
+    b->slot.assign(k, 0);
+    b->epoch.assign(k, 0);
     if (int rc = set_device(meshes[0])) { delete b; return rc; }
-    b->host_insts.resize(k);
-    for (int a = 0; a < k; ++a) {
-        adg_mesh* m = meshes[a];
-        adg::MixedInst& I = b->host_insts[a];
-        I.u = m->u;
-        I.rvol = (float*)m->rvol;
-        I.trace = (float*)m->trace;
-        I.cells = m->cells;
-        I.dtf = 0.f;
-        I.dt = 0.0;
-        I.P = m->Pf;
-        I.bg = m->mbg;
-        b->cells += m->cells;
-    }
-    if (cudaMalloc(&b->insts, k * sizeof(adg::MixedInst)) != cudaSuccess) {
-        cudaGetLastError();
-        free_batch(b);
-        return fail(ADG_ENOMEM, "batch_create: instance table");
-    }
-    if (cudaMemcpy(b->insts, b->host_insts.data(), k * sizeof(adg::MixedInst), cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess) {
+    if (int rc = build_instances(b)) { free_batch(b); return rc; }
+    if (cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess) {
         cudaError_t e = cudaGetLastError();
         free_batch(b);
         return cuda_fail(e, "batch_create: setup");
@@ -1067,15 +1194,18 @@ extern "C" int adg_batch_create(adg_mesh* const* meshes, int k, adg_batch** out)
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
     int bucket = 0;
     for (long long c = b->cells; c > 1; c >>= 1) ++bucket;
-    char keybuf[96];
-    std::snprintf(keybuf, sizeof(keybuf), "mixed N=%d sms=%d cells~2^%d", b->N, sms, bucket);
+    char keybuf[128];
+    std::snprintf(keybuf, sizeof(keybuf), "degree=%d precision=mixed sms=%d cells~2^%d%s", b->N, sms, bucket,
+                  b->host_ainsts.empty() ? "" : " adaptive");
     const std::string key(keybuf);
     int best = -1;
     {
         std::lock_guard<std::mutex> lock(g_tune_mu);
+        if (!g_tune_file_read) read_tune_file();
         for (auto& kv : g_tune_cache)
             if (kv.first == key) best = kv.second;
     }
+    b->tune_source = best >= 0 ? 2 : 0;
     if (best < 0) {
         float best_ms = 1e30f;
         cudaEvent_t e0, e1;
@@ -1084,12 +1214,10 @@ extern "C" int adg_batch_create(adg_mesh* const* meshes, int k, adg_batch** out)
         for (int c = 0; c < adg::kBatchCandidates; ++c) {
             int rc = upload_tiles(b, c, 0, &b->tiles_pred, &b->ntiles_pred, &b->cpb_pred, &b->blocks_pred);
             if (rc) { cudaEventDestroy(e0); cudaEventDestroy(e1); free_batch(b); return rc; }
-            int e = adg::launch_batch_mixed(b->N, c, 0, b->insts, b->tiles_pred, b->ntiles_pred, meshes[0]->Bf,
-                                            nullptr, &b->blocks_pred, b->cap);  // warm-up
+            int e = launch_phase(b, c, 0, b->tiles_pred, b->ntiles_pred, nullptr, &b->blocks_pred, b->cap);  // warm-up
             cudaEventRecord(e0, b->cap);
             for (int r = 0; r < 3 && !e; ++r)
-                e = adg::launch_batch_mixed(b->N, c, 0, b->insts, b->tiles_pred, b->ntiles_pred, meshes[0]->Bf,
-                                            nullptr, &b->blocks_pred, b->cap);
+                e = launch_phase(b, c, 0, b->tiles_pred, b->ntiles_pred, nullptr, &b->blocks_pred, b->cap);
             cudaEventRecord(e1, b->cap);
             if (e || cudaEventSynchronize(e1) != cudaSuccess) {
                 cudaEventDestroy(e0);
@@ -1105,7 +1233,12 @@ extern "C" int adg_batch_create(adg_mesh* const* meshes, int k, adg_batch** out)
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
         std::lock_guard<std::mutex> lock(g_tune_mu);
-        g_tune_cache.push_back({key, best});
+        bool have = false;
+        for (auto& kv : g_tune_cache) have = have || kv.first == key;
+        if (!have) {
+            g_tune_cache.push_back({key, best});
+            write_tune_file();
+        }
     }
     b->cand_pred = best;
     int rc = upload_tiles(b, b->cand_pred, 0, &b->tiles_pred, &b->ntiles_pred, &b->cpb_pred, &b->blocks_pred);
@@ -1117,9 +1250,10 @@ extern "C" int adg_batch_create(adg_mesh* const* meshes, int k, adg_batch** out)
 
 extern "C" int adg_batch_info(const adg_batch* b, int* info, int n) {
     if (!b || !info || n < 1) return fail(ADG_EINVAL, "batch_info: NULL argument");
-    const int v[9] = {b->ntiles_pred, b->cpb_pred, b->blocks_pred, b->ntiles_corr, b->cpb_corr, b->blocks_corr,
-                      (int)(b->tune_ms[0] * 1000), (int)(b->tune_ms[1] * 1000), (int)(b->tune_ms[2] * 1000)};
-    for (int a = 0; a < n && a < 9; ++a) info[a] = v[a];
+    const int v[12] = {b->ntiles_pred, b->cpb_pred, b->blocks_pred, b->ntiles_corr, b->cpb_corr, b->blocks_corr,
+                       (int)(b->tune_ms[0] * 1000), (int)(b->tune_ms[1] * 1000), (int)(b->tune_ms[2] * 1000),
+                       b->cand_pred, b->tune_source, (int)b->host_ainsts.size()};
+    for (int a = 0; a < n && a < 12; ++a) info[a] = v[a];
     return ADG_OK;
 }
 
@@ -1128,9 +1262,7 @@ extern "C" int adg_batch_set_candidate(adg_batch* b, int cand) {
     if (cand < 0 || cand >= adg::kBatchCandidates) return fail(ADG_EINVAL, "batch_set_candidate: candidate not in 0..2");
     ADG_CK(cudaSetDevice(b->device), "batch_set_candidate: cudaSetDevice");
     ADG_CK(cudaDeviceSynchronize(), "batch_set_candidate: synchronise");
-    if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
-    if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
-    b->graph_steps = 0;
+    drop_graph(b);
     b->cand_pred = cand;
     return upload_tiles(b, cand, 0, &b->tiles_pred, &b->ntiles_pred, &b->cpb_pred, &b->blocks_pred);
 }
@@ -1142,31 +1274,49 @@ extern "C" int adg_batch_step(adg_batch* b, const double* dt, int nsteps, void* 
         if (!(dt[a] > 0.0) || !std::isfinite(dt[a])) return fail(ADG_EINVAL, "batch_step: dt must be finite and > 0");
     ADG_CK(cudaSetDevice(b->device), "batch_step: cudaSetDevice");
     cudaStream_t s = (cudaStream_t)stream;
+    bool moved = false;
+    for (int a = 0; a < b->k; ++a) moved = moved || b->epoch[a] != b->meshes[a]->epoch;
+    if (moved) {
+        // a member adapted: its state moved and its leaf count changed; rebuild the
+        // tables and tile lists and capture the graph again (the previous graph may
+        // still be running on another stream: wait for the device first)
+        ADG_CK(cudaDeviceSynchronize(), "batch_step: synchronise before rebuild");
+        drop_graph(b);
+        if (int rc = build_instances(b)) return rc;
+        int rc = upload_tiles(b, b->cand_pred, 0, &b->tiles_pred, &b->ntiles_pred, &b->cpb_pred, &b->blocks_pred);
+        if (!rc) rc = upload_tiles(b, b->cand_corr, 1, &b->tiles_corr, &b->ntiles_corr, &b->cpb_corr, &b->blocks_corr);
+        if (rc) return rc;
+    }
     bool changed = false;
     for (int a = 0; a < b->k; ++a)
         if (dt[a] != b->last_dt[a]) {
             changed = true;
             b->last_dt[a] = dt[a];
-            b->host_insts[a].dt = dt[a];
-            b->host_insts[a].dtf = (float)dt[a];
+            if (b->meshes[a]->amr) {
+                b->host_ainsts[b->slot[a]].dt = dt[a];
+                b->host_ainsts[b->slot[a]].dtf = (float)dt[a];
+            } else {
+                b->host_insts[b->slot[a]].dt = dt[a];
+                b->host_insts[b->slot[a]].dtf = (float)dt[a];
+            }
         }
     if (changed) {
-        ADG_CK(cudaMemcpyAsync(b->insts, b->host_insts.data(), b->k * sizeof(adg::MixedInst),
-                               cudaMemcpyHostToDevice, s), "batch_step: dt upload");
-        // the staging vector must stay valid until the copy has run
+        if (!b->host_insts.empty())
+            ADG_CK(cudaMemcpyAsync(b->insts, b->host_insts.data(), b->host_insts.size() * sizeof(adg::MixedInst),
+                                   cudaMemcpyHostToDevice, s), "batch_step: dt upload");
+        if (!b->host_ainsts.empty())
+            ADG_CK(cudaMemcpyAsync(b->ainsts, b->host_ainsts.data(), b->host_ainsts.size() * sizeof(adg::AmrInst),
+                                   cudaMemcpyHostToDevice, s), "batch_step: dt upload");
+        // the staging vectors must stay valid until the copies have run
         ADG_CK(cudaStreamSynchronize(s), "batch_step: dt upload sync");
     }
     if (!b->exec || b->graph_steps != nsteps) {
-        if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
-        if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
+        drop_graph(b);
         ADG_CK(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal), "batch_step: begin capture");
         int e = 0;
         for (int st = 0; st < nsteps && !e; ++st) {
-            e = adg::launch_batch_mixed(b->N, b->cand_pred, 0, b->insts, b->tiles_pred, b->ntiles_pred,
-                                        b->meshes[0]->Bf, nullptr, &b->blocks_pred, b->cap);
-            if (!e)
-                e = adg::launch_batch_mixed(b->N, b->cand_corr, 1, b->insts, b->tiles_corr, b->ntiles_corr,
-                                            b->meshes[0]->Bf, nullptr, &b->blocks_corr, b->cap);
+            e = launch_phase(b, b->cand_pred, 0, b->tiles_pred, b->ntiles_pred, nullptr, &b->blocks_pred, b->cap);
+            if (!e) e = launch_phase(b, b->cand_corr, 1, b->tiles_corr, b->ntiles_corr, nullptr, &b->blocks_corr, b->cap);
         }
         cudaGraph_t g = nullptr;
         cudaError_t ce = cudaStreamEndCapture(b->cap, &g);

@@ -99,6 +99,26 @@ struct MixedInst {
     PhysF P;
     MixedBg bg;
 };
+// Adaptive mixed-precision instance of a batch: the leaf predictor writes the
+// FP64 residual and traces that the FP64 corrector with its hanging faces
+// reads (adg_amr.cu); per-leaf geometry, neighbour and background tables.
+struct AmrInst {
+    double* u;
+    double* rvol;
+    double* trace;
+    int cells;
+    float dtf;
+    double dt;
+    PhysF Pf;
+    Phys P;
+    const double* geo;
+    const int* nbr;
+    const double* bgl;
+    const double* mb64;
+    const float* mbf;
+};
+// A tile of a batch: inst >= 0 names a uniform instance, inst < 0 the
+// adaptive instance -inst - 1; c0 is its first cell (leaf).
 struct BatchTile {
     int inst, c0;
 };
@@ -148,8 +168,13 @@ int launch_corrector_mixed(int N, double* u, const float* rvol, const float* tra
 // phase 0: predictor, 1: corrector.  tiles == nullptr: query -- returns the
 // cells per block and writes the persistent grid size to *blocks_out; otherwise
 // launches with the grid size in *blocks_out.
-int launch_batch_mixed(int N, int cand, int phase, const MixedInst* insts, const BatchTile* tiles,
-                       int ntiles, const BasisF& B, int* cpb_out, int* blocks_out, void* stream);
+// Batched persistent launch over uniform (insts) and adaptive (ainsts, may be
+// NULL) mixed-precision instances (adg_amr.cu).  B, ops: FP64 basis and the
+// adaptive mesh's prolongation/restriction operators (used when ainsts is
+// given).  With tiles == NULL: query the cells per block and persistent grid.
+int launch_batch_mixed(int N, int cand, int phase, const MixedInst* insts, const AmrInst* ainsts,
+                       const BatchTile* tiles, int ntiles, const BasisF& Bf, const Basis& B, const void* ops,
+                       int* cpb_out, int* blocks_out, void* stream);
 int launch_step_adjoint_fp64(int N, const double* u, const double* lam, double* lam_out, const double* trace,
                              double* trace_bar, int cells, double dt, const Basis& B, const Phys& P,
                              const Background& bg, void* stream);

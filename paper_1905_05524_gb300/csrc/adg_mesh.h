@@ -46,6 +46,7 @@ struct adg_mesh {
     int* dtrans = nullptr;        // [leaf_cap][12] transfer rules of an adaptation
     double hmin = 0.0;            // smallest leaf size (dt rule)
     double* halo = nullptr;       // strip decomposition: [2][nx][17][n] south, north halo traces
+    unsigned epoch = 0;           // changes whenever the state or workspace buffers move (adg_adapt)
 };
 
 namespace adg {
@@ -62,6 +63,7 @@ int amr_corrector(adg_mesh* m, double dt, void* stream);
 int amr_tv_cells(adg_mesh* m, int var, double* tv, double* part, void* stream);
 int amr_max_speed(adg_mesh* m, double* lam_max, void* stream);
 int amr_init_scenario(adg_mesh* m, const adg_scenario* s, void* stream);
+const void* amr_ops(const adg_mesh* m);
 }  // namespace adg
 
 #define ADG_CK(call, what)                                        \

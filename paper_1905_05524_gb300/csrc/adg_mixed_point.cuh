@@ -14,59 +14,100 @@ struct FluxF {
 };
 
 // Point-wise flux from perturbation variables qp (rho', m, m, E'), full
-// gradients (gx, gy), background (rb, Eb, pb) at height z.
+// gradients (gx, gy), background (rb, Eb, pb) at height z.  Explicit rounding
+// throughout: the slip-wall ghost that uses it is inlined into the per-mesh
+// and the batched correctors, which must agree bitwise.
 __device__ __forceinline__ void ns_flux_pert(const float qp[4], const float gx[4], const float gy[4],
                                              float z, float rb, float Eb, float pb, const PhysF& P,
                                              FluxF& o, bool use_heat = false, float hTy = 0.f) {
-    const float rho = rb + qp[0];
+    const float rho = __fadd_rn(rb, qp[0]);
     const float mx = qp[1], my = qp[2];
     const float rinv = __frcp_rn(rho);
-    const float u = mx * rinv, v = my * rinv;
-    const float gz = P.g * z;
-    const float pp = P.gm1 * (qp[3] - 0.5f * (mx * u + my * v) - gz * qp[0]);
-    const float p = pb + pp;
-    const float E = Eb + qp[3];
-    const float T = p * rinv * P.invR;
-    const float ux = (gx[1] - u * gx[0]) * rinv;
-    const float uy = (gy[1] - u * gy[0]) * rinv;
-    const float vx = (gx[2] - v * gx[0]) * rinv;
-    const float vy = (gy[2] - v * gy[0]) * rinv;
-    const float kin = 0.5f * (u * u + v * v);
+    const float u = __fmul_rn(mx, rinv), v = __fmul_rn(my, rinv);
+    const float gz = __fmul_rn(P.g, z);
+    const float m2 = __fmaf_rn(my, v, __fmul_rn(mx, u));
+    const float pp = __fmul_rn(P.gm1, __fmaf_rn(-gz, qp[0], __fmaf_rn(-0.5f, m2, qp[3])));
+    const float p = __fadd_rn(pb, pp);
+    const float E = __fadd_rn(Eb, qp[3]);
+    const float T = __fmul_rn(__fmul_rn(p, rinv), P.invR);
+    const float ux = __fmul_rn(__fmaf_rn(-u, gx[0], gx[1]), rinv);
+    const float uy = __fmul_rn(__fmaf_rn(-u, gy[0], gy[1]), rinv);
+    const float vx = __fmul_rn(__fmaf_rn(-v, gx[0], gx[2]), rinv);
+    const float vy = __fmul_rn(__fmaf_rn(-v, gy[0], gy[2]), rinv);
+    const float kg = __fmaf_rn(0.5f, __fmaf_rn(v, v, __fmul_rn(u, u)), -gz);  // kinetic energy per mass - g z
     float Tx, Ty;
     if (use_heat) {
         Tx = 0.f;
         Ty = hTy;
     } else {
-        const float px = P.gm1 * (gx[3] - (u * gx[1] + v * gx[2]) + kin * gx[0] - gz * gx[0]);
-        const float py = P.gm1 * (gy[3] - (u * gy[1] + v * gy[2]) + kin * gy[0] - gz * gy[0] - rho * P.g);
-        Tx = (px - P.R * T * gx[0]) * rinv * P.invR;
-        Ty = (py - P.R * T * gy[0]) * rinv * P.invR;
+        const float px = __fmul_rn(P.gm1, __fmaf_rn(kg, gx[0], __fmaf_rn(-v, gx[2], __fmaf_rn(-u, gx[1], gx[3]))));
+        const float py = __fmul_rn(P.gm1, __fmaf_rn(-rho, P.g, __fmaf_rn(kg, gy[0],
+                                                  __fmaf_rn(-v, gy[2], __fmaf_rn(-u, gy[1], gy[3])))));
+        const float RT = __fmul_rn(P.R, T), ri = __fmul_rn(rinv, P.invR);
+        Tx = __fmul_rn(__fmaf_rn(-RT, gx[0], px), ri);
+        Ty = __fmul_rn(__fmaf_rn(-RT, gy[0], py), ri);
     }
-    const float div = ux + vy;
-    const float sxx = P.mu * ((2.f / 3.f) * div - 2.f * ux);
-    const float syy = P.mu * ((2.f / 3.f) * div - 2.f * vy);
-    const float sxy = -P.mu * (uy + vx);
-    const float Ep = E + p;
+    const float div = __fadd_rn(ux, vy);
+    const float sxx = __fmul_rn(P.mu, __fmaf_rn(2.f / 3.f, div, __fmul_rn(-2.f, ux)));
+    const float syy = __fmul_rn(P.mu, __fmaf_rn(2.f / 3.f, div, __fmul_rn(-2.f, vy)));
+    const float sxy = __fmul_rn(-P.mu, __fadd_rn(uy, vx));
+    const float Ep = __fadd_rn(E, p);
     o.F[0] = mx;
-    o.F[1] = mx * u + pp + sxx;
-    o.F[2] = my * u + sxy;
-    o.F[3] = u * Ep + u * sxx + v * sxy - P.kappa * Tx;
+    o.F[1] = __fmaf_rn(mx, u, __fadd_rn(pp, sxx));
+    o.F[2] = __fmaf_rn(my, u, sxy);
+    o.F[3] = __fmaf_rn(-P.kappa, Tx, __fmaf_rn(v, sxy, __fmul_rn(u, __fadd_rn(Ep, sxx))));
     o.G[0] = my;
-    o.G[1] = mx * v + sxy;
-    o.G[2] = my * v + pp + syy;
-    o.G[3] = v * Ep + u * sxy + v * syy - P.kappa * Ty;
+    o.G[1] = __fmaf_rn(mx, v, sxy);
+    o.G[2] = __fmaf_rn(my, v, __fadd_rn(pp, syy));
+    o.G[3] = __fmaf_rn(-P.kappa, Ty, __fmaf_rn(u, sxy, __fmul_rn(v, __fadd_rn(Ep, syy))));
     o.S[0] = 0.f;
     o.S[1] = 0.f;
-    o.S[2] = -P.g * qp[0];
+    o.S[2] = __fmul_rn(-P.g, qp[0]);
     o.S[3] = 0.f;
 }
 
+// The scalar expressions below round explicitly (no contraction left to the
+// compiler): they are inlined into several kernels (the per-mesh and batched
+// predictors, node-per-thread and node-pair forms), which must agree bitwise.
 __device__ __forceinline__ float wave_speed_f(float rho, float mx, float my, float pp, float pb,
                                               bool xdir, const PhysF& P) {
     const float rinv = __frcp_rn(rho);
-    const float c = sqrtf(P.gamma * (pb + pp) * rinv);
-    const float vn = fabsf((xdir ? mx : my) * rinv);
-    return vn + c + 2.f * (xdir ? P.eta_x : P.eta_y) * P.lamv * rinv;
+    const float c = sqrtf(__fmul_rn(__fmul_rn(P.gamma, __fadd_rn(pb, pp)), rinv));
+    const float vn = fabsf(__fmul_rn(xdir ? mx : my, rinv));
+    return __fmaf_rn(__fmul_rn(__fmul_rn(2.f, xdir ? P.eta_x : P.eta_y), P.lamv), rinv, __fadd_rn(vn, c));
+}
+
+// coordinate o + (cell index + node) h of a node (or face: node = 0 or 1)
+__device__ __forceinline__ float node_coord_f(float o, int cell, float node, float h) {
+    return __fmaf_rn(__fadd_rn((float)cell, node), h, o);
+}
+
+// pressure perturbation of a trace record (rho', m_x, m_y, E') at height z
+__device__ __forceinline__ float trace_pp_f(const float* rec, float rinv, float z, const PhysF& P) {
+    const float m2 = __fmaf_rn(rec[1], rec[1], __fmul_rn(rec[2], rec[2]));
+    const float ke = __fmul_rn(__fmul_rn(0.5f, m2), rinv);
+    return __fmul_rn(P.gm1, __fsub_rn(__fsub_rn(rec[3], ke), __fmul_rn(__fmul_rn(P.g, z), rec[0])));
+}
+
+// the steady manufactured field's source (Sec. 4.1 workload: rho = 1 + a sin k(x+z),
+// u = v = U, p = const) at (x, z)
+__device__ __forceinline__ void steady_source_f(float x, float z, const PhysF& P, float Sm[4]) {
+    const float k = __fdiv_rn(6.283185307179586f, P.sL);
+    float sn, cs;
+    sincosf(__fmul_rn(k, __fadd_rn(x, z)), &sn, &cs);
+    const float a = P.sa, U = P.sU;
+    const float rho = __fmaf_rn(a, sn, 1.f);
+    const float c = __fmul_rn(__fmul_rn(__fmul_rn(__fmul_rn(2.f, U), a), k), cs);
+    const float r2 = __fmul_rn(rho, rho);
+    const float t1 = __fdiv_rn(__fmul_rn(__fmul_rn(__fmul_rn(a, k), k), sn), r2);
+    const float t2 = __fdiv_rn(__fmul_rn(__fmul_rn(__fmul_rn(__fmul_rn(__fmul_rn(2.f, a), a), k), k),
+                                         __fmul_rn(cs, cs)),
+                               __fmul_rn(r2, rho));
+    const float lapT = __fmul_rn(__fmul_rn(__fmul_rn(2.f, P.sp), P.invR), __fadd_rn(t1, t2));
+    Sm[0] = c;
+    Sm[1] = __fmul_rn(c, U);
+    Sm[2] = __fmul_rn(c, U);
+    Sm[3] = __fsub_rn(__fmul_rn(__fmul_rn(c, U), U), __fmul_rn(P.kappa, lapT));
 }
 
 // ---------------------------------------------------------------------------

@@ -257,10 +257,10 @@ class Batch:
         L.check(self._lib.adg_batch_set_candidate(self.h, int(cand)))
 
     def info(self):
-        buf = (ctypes.c_int * 9)()
-        L.check(self._lib.adg_batch_info(self.h, buf, 9))
+        buf = (ctypes.c_int * 12)()
+        L.check(self._lib.adg_batch_info(self.h, buf, 12))
         keys = ["tiles_pred", "cpb_pred", "grid_pred", "tiles_corr", "cpb_corr", "grid_corr",
-                "tune_ns_0", "tune_ns_1", "tune_ns_2"]
+                "tune_ns_0", "tune_ns_1", "tune_ns_2", "candidate", "tune_source", "adaptive_instances"]
         return dict(zip(keys, list(buf)))
 
     def close(self):

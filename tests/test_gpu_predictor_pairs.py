@@ -24,7 +24,7 @@ def _bubble(degree, side, stir=True):
     return m
 
 
-@pytest.mark.parametrize("degree,side", [(3, 13), (5, 9), (5, 14)])
+@pytest.mark.parametrize("degree,side", [(3, 13), (5, 9), (5, 13), (5, 14)])
 def test_node_pairs_bitwise_equal_node_per_thread(degree, side):
     a, b = _bubble(degree, side), _bubble(degree, side)
     dt = a.stable_dt(0.25)
