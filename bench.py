@@ -97,7 +97,7 @@ PREDICTOR_SOURCES = {
 }
 PREDICTOR_COUNTERS = {
     "fp64": {"sha256": "20bd7fb29a7026a17d8e447cdce8b87c431994d217cfb9575ed713ac2b3801cd",
-             "traffic": 7851520 + 0, "smem_frac": None},
+             "traffic": 7810304 + 256, "smem_frac": None},
     "mixed": {"sha256": "bbdb336d4198313cb0e30fc8ef147ec403b488932379a1b875f887d7a2a97842",
               "traffic": 7654144 + 0, "smem_frac": 0.732},
 }
@@ -304,7 +304,7 @@ def run_form(prec_name, steps, warmup, dev, ws):
     from paper_1905_05524_gb300 import _lib as L
     from paper_1905_05524_gb300.solver import Mesh, atmosphere_config
 
-    prec = L.ADG_PREC_FP64 if prec_name == "fp64" else L.ADG_PREC_MIXED
+    prec = {"fp64": L.ADG_PREC_FP64, "mixed": L.ADG_PREC_MIXED, "mixed_tf32": L.ADG_PREC_MIXED_TF32}[prec_name]
     cfg = atmosphere_config(degree=DEGREE, nx=NX, ny=NY, precision=prec, device=dev.index)
     m = Mesh(cfg)
     m.init_scenario(L.ADG_SCEN_COSINE, A=0.5, a=250.0, xc=500.0, zc=350.0)
@@ -955,6 +955,17 @@ def run_ours(args):
                              "phases_ms": {"predictor": ref["pred"] / args.steps,
                                            "corrector": ref["corr"] / args.steps,
                                            "tv_indicator": ref["tv"] / args.steps}}
+            tc = run_form("mixed_tf32", args.steps, min(args.warmup, 3), dev, 1)
+            th_t = theta_prime_np(tc["final"], tc["cfg"])
+            forms["mixed_tf32"] = {"value": dof * args.steps / (tc["total"] * 1e-3), "unit": UNIT,
+                                   "ms_per_step": tc["total"] / args.steps,
+                                   "phases_ms": {"predictor": tc["pred"] / args.steps,
+                                                 "corrector": tc["corr"] / args.steps,
+                                                 "tv_indicator": tc["tv"] / args.steps},
+                                   "theta_prime_rel_l2_vs_fp64": float(np.linalg.norm(th_t - th_d) /
+                                                                       np.linalg.norm(th_d)),
+                                   "form": "ADG_PREC_MIXED_TF32: the predictor's derivative contractions as "
+                                           "mma.sync TF32 MMAs with the three-term split"}
             forms["mixed_error_vs_fp64"] = {"theta_prime_rel_l2": err, "per_variable_rel_l2": var_err,
                                             "per_variable_abs_l2": var_abs,
                                             "momentum_rel_to_momentum_l2": [var_abs[1] / mom_norm,
@@ -973,7 +984,8 @@ def run_ours(args):
         achieved = flops_launch / (pred_avg * 1e-3) / 1e12
         traffic, smem_frac = predictor_counters(args.precision)
         roof = {
-            "kernel": "k_predictor_fp64<5,4>" if pipe == "fp64" else "k_predictor_mixed_x2<5,6>",
+            "kernel": {"fp64": "k_predictor_fp64<5,4>", "mixed": "k_predictor_mixed_x2<5,6>",
+                       "mixed_tf32": "k_predictor_mixed_tc<5,4>"}[args.precision],
             "bound": "alu", "pipe": f"{pipe} FMA (CUDA cores)",
             "achieved": achieved, "peak": pk, "unit": "TFLOP/s",
             "frac": (achieved / pk) if pk else None,
@@ -1039,7 +1051,7 @@ def main():
     ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
+    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed", "mixed_tf32"])
     ap.add_argument("--no-compare", action="store_true", help="skip the FP64 comparison form")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-instance batched form")
     ap.add_argument("--batch-steps", type=int, default=20)

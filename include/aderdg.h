@@ -77,6 +77,13 @@ extern "C" {
 #define ADG_PREC_FP64 0     /* every operation in FP64                          */
 #define ADG_PREC_MIXED 1    /* FP32 predictor on perturbation variables; FP64
                                background split, pressure recovery and update   */
+#define ADG_PREC_MIXED_TF32 2 /* ADG_PREC_MIXED with the predictor's derivative
+                               contractions as tensor-core MMAs (TF32 operands
+                               split in three terms, FP32 accumulation); uniform
+                               meshes of degree 3, 5, 7 (ADG_EUNSUPPORTED
+                               otherwise).  Measured slower than ADG_PREC_MIXED
+                               on this GPU; kept as the tensor-core form of the
+                               contractions.                                     */
 
 #define ADG_TV_RHO 0
 #define ADG_TV_THETA 1      /* potential temperature theta = T (p0/p)^(R/cp)  */

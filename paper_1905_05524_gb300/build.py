@@ -20,7 +20,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", INCLUDE]
 LIB_SOURCES = ["adg_api.cu", "adg_fp64.cu", "adg_mixed.cu", "adg_tv.cu", "adg_adjoint.cu", "adg_amr.cu", "adg_3d.cu",
-               "adg_fv.cu", "adg_objective.cu"]
+               "adg_fv.cu", "adg_objective.cu", "adg_mixed_tc.cu"]
 
 
 def _nvcc():
