@@ -23,9 +23,16 @@ A4  hanging faces (one coarse face against three fine faces): the fine side
     on both sides;
 A5  leaves are ordered by (level, iy, ix) after every adaptation.
 
+L1  local time stepping (step_lts, not in the paper): a leaf of level l steps
+    with dt 3^(L-l); at a hanging face the fine side sees the coarse
+    predictor's trace averaged over the third of the coarse step its own step
+    covers, and the coarse side receives the time average of the fine
+    numerical fluxes of its three sub-steps (restricted per spatial third).
+
 Pins: tests/test_oracle_amr.py (restrict(prolong(u)) = u, conservation of
 all integrals over steps with hanging faces and across adaptation, a mesh
-refined everywhere reproduces the uniform fine run, the balance rule).
+refined everywhere reproduces the uniform fine run, the balance rule);
+tests/test_oracle_lts.py (local time stepping).
 """
 import itertools
 
@@ -195,6 +202,112 @@ class AmrSolver:
                     / (hy * w[None, None, :, None]))
             out[idx] = u[idx] + dt * (vol - face + tavg["Sbar"][idx])
         return out
+
+    # -------------------------------------------------------------- local time stepping
+    def time_thirds(self):
+        """W[s][k]: average over the third s of the step of the nodal time
+        interpolant's basis function k, sum_m w_m phi_k((s + xi_m)/3) (n-point
+        Gauss-Legendre on the third, exact for the degree-N interpolant)."""
+        xi, w = self.b.xi, self.b.w
+        return torch.stack([torch.einsum("m,mk->k", w, lagrange_values(xi, (s + xi) / 3.0)) for s in range(3)])
+
+    def step_lts(self, u, dt, t=0.0):
+        """One cycle of local time stepping (reading L1): leaves of level l
+        advance by dt 3^(L-l), L the finest level present, in 3^(L-l0) steps
+        of the finest level (l0 the coarsest).  A level's step is its
+        predictor over its whole step, then three steps of the next finer
+        level, then its corrector.  Between levels: the finer side of a
+        hanging face takes the coarse predictor's trace averaged over the
+        third of the coarse step that its own step covers (the W weights of
+        time_thirds); the coarse side receives, per spatial third of the
+        face, the average of the three fine numerical fluxes of its three
+        sub-steps, then their L2 restriction -- conservative, because it is
+        the fine flux integral itself.  On a tree with one level this is the
+        global step.  Returns (state, cycle length)."""
+        levels = self.levels()
+        L, l0 = max(levels), min(levels)
+        self._lts_u = u.clone()
+        self._lts_sub = {}
+        self._lts_acc = {}
+        self._lts_W = self.time_thirds()
+        self._lts_level(l0, t, dt, L, 0)
+        u_new = self._lts_u
+        del self._lts_u, self._lts_sub, self._lts_acc, self._lts_W
+        return u_new, dt * 3 ** (L - l0)
+
+    def _lts_level(self, lv, t, dt, L, kstep):
+        b = self.b
+        n = b.n
+        dtl = dt * 3 ** (L - lv)
+        idx = [k for k, c in enumerate(self.leaves) if c[0] == lv]
+        loc = {k: a for a, k in enumerate(idx)}
+        view = _LevelView(self, lv, [self.leaves[k] for k in idx])
+        q, tavg = view.predictor(self._lts_u[idx], dtl, t)
+        tr = self.ref.face_traces(tavg)
+        finer = lv + 1 in self.levels()
+        if finer:
+            if self.P.source != "none":
+                Sman = torch.stack([view.manufactured(t + float(b.xi[k]) * dtl) for k in range(n)], 1)
+            else:
+                Sman = None
+            F, G, S, qx, qy = view.evaluate(q, Sman)
+            self._lts_sub[lv] = []
+            for s in range(3):
+                Ws = self._lts_W[s]
+                avg = lambda a: torch.einsum("k,ck...->c...", Ws, a)
+                self._lts_sub[lv].append(self.ref.face_traces(dict(qbar=avg(q), Fbar=avg(F), Gbar=avg(G),
+                                                                   qxbar=avg(qx), qybar=avg(qy))))
+            for k in idx:
+                for f in "EWNS":
+                    if self.neighbour(self.leaves[k], f)[0] == "fine":
+                        self._lts_acc[(k, f)] = [torch.zeros(1, 4, n, dtype=DTYPE) for _ in range(3)]
+            for ks in range(3):
+                self._lts_level(lv + 1, t + ks * dtl / 3.0, dt, L, ks)
+        # corrector of this level
+        nrm = {"E": (1.0, 0.0), "W": (1.0, 0.0), "N": (0.0, 1.0), "S": (0.0, 1.0)}
+        opp = {"E": "W", "W": "E", "N": "S", "S": "N"}
+        Fst = {f: torch.empty(len(idx), 4, n, dtype=DTYPE) for f in "EWNS"}
+        for a, k in enumerate(idx):
+            leaf = self.leaves[k]
+            hx, hy = self.h(lv)
+            for f in "EWNS":
+                xf = f in "EW"
+                hn = hx if xf else hy
+                own_minus = f in "EN"
+                z = self._face_z(leaf, f)
+                nb = self.neighbour(leaf, f)
+                own = {key: tr[f][key][a:a + 1] for key in ("q", "f", "qx", "qy")}
+                if nb[0] == "wall":
+                    normal = {"E": (1.0, 0.0), "W": (-1.0, 0.0), "N": (0.0, 1.0), "S": (0.0, -1.0)}[f]
+                    gq, gf = self.ref._ghost(own, normal, z)
+                    Fv = self._riemann(own["q"], own["f"], gq, gf, z, own_minus, nrm[f], hn)
+                elif nb[0] == "conf":
+                    o = loc[nb[1]]
+                    Fv = self._riemann(own["q"], own["f"], tr[opp[f]]["q"][o:o + 1], tr[opp[f]]["f"][o:o + 1],
+                                       z, own_minus, nrm[f], hn)
+                elif nb[0] == "coarse":
+                    o, sp = nb[1], nb[2]
+                    oidx = [kk for kk, c in enumerate(self.leaves) if c[0] == lv - 1].index(o)
+                    sub = self._lts_sub[lv - 1][kstep]
+                    cq = self._prolong_face(sub[opp[f]]["q"][oidx:oidx + 1], sp)
+                    cf = self._prolong_face(sub[opp[f]]["f"][oidx:oidx + 1], sp)
+                    Fv = self._riemann(own["q"], own["f"], cq, cf, z, own_minus, nrm[f], hn)
+                    acc = self._lts_acc[(o, opp[f])]
+                    acc[sp] = acc[sp] + Fv / 3.0
+                else:  # three finer neighbours: their three sub-step fluxes, averaged, restricted
+                    Fv = self._restrict_face(self._lts_acc[(k, f)])
+                Fst[f][a] = Fv[0]
+        w, p0, p1 = b.w, b.phi0, b.phi1
+        Vx = (w[:, None] * b.D) / w[None, :]
+        hx, hy = self.h(lv)
+        vol = (torch.einsum("pi,cvjp->cvji", Vx, tavg["Fbar"]) / hx
+               + torch.einsum("pj,cvpi->cvji", Vx, tavg["Gbar"]) / hy)
+        FE, FW, GN, GS = Fst["E"], Fst["W"], Fst["N"], Fst["S"]
+        face = ((p1[None, None, None, :] * FE[:, :, :, None] - p0[None, None, None, :] * FW[:, :, :, None])
+                / (hx * w[None, None, None, :])
+                + (p1[None, None, :, None] * GN[:, :, None, :] - p0[None, None, :, None] * GS[:, :, None, :])
+                / (hy * w[None, None, :, None]))
+        self._lts_u[idx] = self._lts_u[idx] + dtl * (vol - face + tavg["Sbar"])
 
     def _face_z(self, leaf, f):
         lv, ix, iy = leaf
