@@ -363,6 +363,24 @@ size_t adg_leaf_count(const adg_mesh* m);
 int adg_leaf_info(const adg_mesh* m, int* out, size_t count);
 int adg_adapt(adg_mesh* m, const int8_t* flags, int* leaves_out, void* stream);
 
+/* ---- local time stepping across the levels of an adaptive mesh ----
+ * (not in the paper, whose runs take one global dt from the finest cells)
+ *
+ * One cycle: the leaves of level l advance by dt * 3^(L-l), L the finest
+ * level present, so the cycle advances the mesh by dt * 3^(L-l0) (l0 the
+ * coarsest level), written to *cycle (host, may be NULL) and added to the
+ * mesh time.  A level's step is its predictor over its whole step, three
+ * steps of the next finer level, then its corrector.  At a hanging face the
+ * fine side takes the coarse predictor's trace averaged over the third of
+ * the coarse step its own step covers; the coarse side receives, per
+ * spatial third of the face, the average of the fine numerical fluxes of its
+ * three sub-steps (their L2 restriction, as for a global step) -- so the
+ * scheme stays conservative.  On a mesh with one level present it is
+ * adg_step.  dt is the finest level's step (from adg_stable_dt).  FP64
+ * adaptive meshes of degree >= 2 (ADG_EUNSUPPORTED otherwise; ADG_EINVAL on
+ * uniform meshes).  Queued on `stream`. */
+int adg_step_lts(adg_mesh* m, double dt, double* cycle, void* stream);
+
 /* ---- MUSCL-Hancock finite volumes (the paper's second scheme, Sec. 3) ----
  *
  * Unsplit MUSCL-Hancock on cell averages with the van Albada limiter, run

@@ -99,6 +99,7 @@ SIGNATURES = {
     "adg_predictor": (_I, [_P, _D, _P]),
     "adg_corrector": (_I, [_P, _D, _P]),
     "adg_step": (_I, [_P, _D, _P]),
+    "adg_step_lts": (_I, [_P, _D, ctypes.POINTER(_D), _P]),
     "adg_stable_dt": (_I, [_P, _D, ctypes.POINTER(_D), _P]),
     "adg_tv_indicator": (_I, [_P, _I, _D, _D, _P, _P, _P, _P]),
     "adg_fv_create": (_I, [ctypes.POINTER(MeshDesc), ctypes.POINTER(_P)]),

@@ -341,6 +341,10 @@ int amr_setup(adg_mesh* m) {
 void amr_free(adg_mesh* m) {
     delete tree_of(m);
     m->tree = nullptr;
+    cudaFree(m->lts_ttrace);
+    cudaFree(m->lts_acc);
+    m->lts_ttrace = m->lts_acc = nullptr;
+    m->lts_cap = 0;
     cudaFree(m->geo);
     cudaFree(m->nbr);
     cudaFree(m->bgl);
@@ -382,6 +386,26 @@ k_predictor_amr(const double* __restrict__ u, double* __restrict__ rvol, double*
     const Phys P = leaf_phys(P0, geo, cell, N);
     predictor_fp64_body<N, CPB>(u, rvol, trace, cell, active, dt, B, P, geo[cell * 4], geo[cell * 4 + 1],
                                 bgl[((size_t)cell * n + j) * 2], bgl[((size_t)cell * n + j) * 2 + 1], sm);
+}
+
+// Local time stepping: the FP64 predictor on the leaf range [first, end) (one
+// level) with dt of that level; REC adds the per-time-node face traces.
+template <int N, int CPB, bool REC>
+__global__ void __launch_bounds__(CPB*(N + 1) * (N + 1))
+k_predictor_amr_lts(const double* __restrict__ u, double* __restrict__ rvol, double* __restrict__ trace, int first,
+                    int end, double dt, const Basis B, const Phys P0, const double* __restrict__ geo,
+                    const double* __restrict__ bgl, double* __restrict__ ttrace) {
+    constexpr int n = N + 1, n2 = n * n;
+    extern __shared__ double sm[];
+    const int cl = threadIdx.x / n2;
+    const int j = (threadIdx.x - cl * n2) / n;
+    const int cell_raw = first + blockIdx.x * CPB + cl;
+    const bool active = cell_raw < end;
+    const int cell = active ? cell_raw : end - 1;
+    const Phys P = leaf_phys(P0, geo, cell, N);
+    predictor_fp64_body<N, CPB, false, REC>(u, rvol, trace, cell, active, dt, B, P, geo[cell * 4], geo[cell * 4 + 1],
+                                            bgl[((size_t)cell * n + j) * 2], bgl[((size_t)cell * n + j) * 2 + 1],
+                                            sm, 0.0, ttrace);
 }
 
 // Mixed-precision predictor of the adaptive mesh: the Picard iteration of
@@ -669,12 +693,26 @@ __device__ __forceinline__ void prolong_rec(const double* rec, int n, const AmrO
     }
 }
 
-template <int N, int CPB>
+// Local-time-stepping arguments of a corrector launch on one level: W, the
+// weights of the time average over the part of a coarser neighbour's step
+// that this level's step covers (third kstep); ttrace, the per-time-node
+// traces of the coarser level; acc[leaf][face][third][v][n], per spatial
+// third of a coarse face, the time average of the fine numerical fluxes of
+// the coarse leaf's sub-steps (the fine leaves add theirs; the coarse leaf
+// reads them instead of computing fine fluxes).
+struct LtsArgs {
+    double W[kMaxN];
+    const double* ttrace;
+    double* acc;
+    int total;  // leaves of the mesh (the background table's face part follows all leaves' node part)
+};
+
+template <int N, int CPB, bool LTS = false>
 __device__ __forceinline__ void corrector_amr_body(double* __restrict__ u, const double* __restrict__ rvol,
                                                    const double* __restrict__ trace, int cells, int c0, double dt,
                                                    const Basis& B, const Phys& P0, const AmrOps& O,
                                                    const double* __restrict__ geo, const int* __restrict__ nbr,
-                                                   const double* __restrict__ bgl) {
+                                                   const double* __restrict__ bgl, const LtsArgs* lts = nullptr) {
     constexpr int n = N + 1, n2 = n * n, SL = 4 * n2, TR = kTraceComps * n;
     __shared__ double Fsub[CPB][4][3][4][n];
     __shared__ double Fst[CPB][4][4][n];
@@ -698,6 +736,13 @@ __device__ __forceinline__ void corrector_amr_body(double* __restrict__ u, const
         const double* own = trace + ((size_t)cell * 4 + f) * TR;
         double qo[4], fo[4], so;
         double qn[4], fn[4], sn;
+        if (LTS && type == NB_FINE) {
+            // coarse side under local time stepping: the fine leaves' fluxes, averaged over their sub-steps
+            const double* a = lts->acc + ((((size_t)cell * 4 + f) * 3 + s) * 4) * n;
+#pragma unroll
+            for (int v = 0; v < 4; ++v) Fsub[cl][f][s][v][m] = a[v * n + m];
+            continue;
+        }
         if (type == NB_FINE) {
             // coarse side of a hanging face: own trace on third s vs fine neighbour s
             const int o = nb[1 + s];
@@ -730,7 +775,8 @@ __device__ __forceinline__ void corrector_amr_body(double* __restrict__ u, const
                     pb = bgl[((size_t)cell * n + m) * 2];
                     rb = bgl[((size_t)cell * n + m) * 2 + 1];
                 } else {
-                    const double* fb = bgl + (size_t)cells * n * 2 + (size_t)cell * 4 + (f == 2 ? 0 : 2);
+                    const double* fb = bgl + (size_t)(LTS ? lts->total : cells) * n * 2 + (size_t)cell * 4 +
+                                       (f == 2 ? 0 : 2);
                     pb = fb[0];
                     rb = fb[1];
                 }
@@ -754,6 +800,15 @@ __device__ __forceinline__ void corrector_amr_body(double* __restrict__ u, const
                     fn[v] = ot[(4 + v) * n + m];
                 }
                 sn = ot[16 * n + m];
+            } else if (LTS) {  // NB_COARSE under local time stepping: the coarse trace averaged over this step
+                double rec[8 * n];
+                for (int c = 0; c < 8 * n; ++c) rec[c] = 0.0;
+                for (int k = 0; k < n; ++k) {
+                    const double* tk = lts->ttrace + ((((size_t)nb[1] * n + k) * 4 + of) * 16) * n;
+                    for (int c = 0; c < 8 * n; ++c) rec[c] += lts->W[k] * tk[c];
+                }
+                prolong_rec(rec, n, O, nb[4], m, qn, fn);
+                sn = wave_speed(qn, z, xface, P);
             } else {  // NB_COARSE: the coarse trace on this cell's third of the face
                 const double* ot = trace + ((size_t)nb[1] * 4 + of) * TR;
                 prolong_rec(ot, n, O, nb[4], m, qn, fn);
@@ -763,6 +818,11 @@ __device__ __forceinline__ void corrector_amr_body(double* __restrict__ u, const
         double out[4];
         if (own_minus) rusanov(qo, fo, so, qn, fn, sn, out);
         else rusanov(qn, fn, sn, qo, fo, so, out);
+        if (LTS && type == NB_COARSE && active) {  // this sub-step's share of the coarse leaf's face flux
+            double* a = lts->acc + ((((size_t)nb[1] * 4 + of) * 3 + nb[4]) * 4) * n;
+#pragma unroll
+            for (int v = 0; v < 4; ++v) a[v * n + m] += out[v] * (1.0 / 3.0);
+        }
 #pragma unroll
         for (int v = 0; v < 4; ++v) Fsub[cl][f][s][v][m] = out[v];
     }
@@ -801,6 +861,15 @@ k_corrector_amr(double* __restrict__ u, const double* __restrict__ rvol, const d
                 int cells, double dt, const Basis B, const Phys P0, const AmrOps O, const double* __restrict__ geo,
                 const int* __restrict__ nbr, const double* __restrict__ bgl) {
     corrector_amr_body<N, CPB>(u, rvol, trace, cells, blockIdx.x * CPB, dt, B, P0, O, geo, nbr, bgl);
+}
+
+template <int N, int CPB>
+__global__ void __launch_bounds__(CPB*(N + 1) * (N + 1))
+k_corrector_amr_lts(double* __restrict__ u, const double* __restrict__ rvol, const double* __restrict__ trace,
+                    int first, int end, double dt, const Basis B, const Phys P0, const AmrOps O,
+                    const double* __restrict__ geo, const int* __restrict__ nbr, const double* __restrict__ bgl,
+                    const LtsArgs L) {
+    corrector_amr_body<N, CPB, true>(u, rvol, trace, end, first + blockIdx.x * CPB, dt, B, P0, O, geo, nbr, bgl, &L);
 }
 
 template <int N, int CPB>
@@ -1042,6 +1111,134 @@ static int speed_amr_n(adg_mesh* m, double* lam, cudaStream_t s) {
     return ADG_OK;
 }
 int amr_max_speed(adg_mesh* m, double* lam, void* stream) { AMR_DISPATCH(speed_amr_n, m, lam, (cudaStream_t)stream) }
+
+// ------------------------------------------------------------ local time stepping
+// One cycle (reading L1): level l steps with dt 3^(L-l); a level's step is its
+// predictor (with per-time-node traces when a finer level exists), three
+// steps of the next finer level, then its corrector.  Leaves are ordered by
+// level, so a level is a contiguous range of leaves.
+struct LtsRun {
+    adg_mesh* m;
+    cudaStream_t s;
+    int L;
+    std::vector<int> off;  // off[l] .. off[l + 1]: leaves of level l
+    double dt;             // step of the finest level
+    double W[3][kMaxN];    // time-average weights of the thirds of a step
+};
+
+template <int N>
+static int lts_level_n(LtsRun& R, int l, double t, int kstep) {
+    using C = AmrCfg<N>;
+    adg_mesh* m = R.m;
+    const int first = R.off[l], end = R.off[l + 1];
+    const double dtl = R.dt * std::pow(3.0, R.L - l);
+    const bool finer = l < R.L;
+    (void)t;
+    if (end > first) {
+        const int blocks = (end - first + C::cpb - 1) / C::cpb;
+        if (finer) {
+            auto k = k_predictor_amr_lts<N, C::cpb, true>;
+            ADG_CK(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem_pred), "lts pred");
+            k<<<blocks, C::threads, C::smem_pred, R.s>>>(m->u, m->rvol, m->trace, first, end, dtl, m->B, m->P, m->geo,
+                                                          m->bgl, m->lts_ttrace);
+        } else {
+            auto k = k_predictor_amr_lts<N, C::cpb, false>;
+            ADG_CK(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem_pred), "lts pred");
+            k<<<blocks, C::threads, C::smem_pred, R.s>>>(m->u, m->rvol, m->trace, first, end, dtl, m->B, m->P, m->geo,
+                                                          m->bgl, nullptr);
+        }
+        ADG_CK(cudaGetLastError(), "lts predictor launch");
+    }
+    if (finer) {
+        const size_t per_leaf = (size_t)4 * 3 * 4 * m->n;
+        if (end > first)
+            ADG_CK(cudaMemsetAsync(m->lts_acc + (size_t)first * per_leaf, 0, (size_t)(end - first) * per_leaf * 8, R.s),
+                   "lts: clear flux sums");
+        for (int ks = 0; ks < 3; ++ks)
+            if (int rc = lts_level_n<N>(R, l + 1, t + ks * dtl / 3.0, ks)) return rc;
+    }
+    if (end > first) {
+        LtsArgs A;
+        std::memset(&A, 0, sizeof(A));
+        for (int k = 0; k < m->n; ++k) A.W[k] = R.W[kstep][k];
+        A.ttrace = m->lts_ttrace;
+        A.acc = m->lts_acc;
+        A.total = m->cells;
+        const int blocks = (end - first + C::cpb - 1) / C::cpb;
+        k_corrector_amr_lts<N, C::cpb><<<blocks, C::threads, 0, R.s>>>(m->u, m->rvol, m->trace, first, end, dtl, m->B,
+                                                                        m->P, tree_of(m)->ops, m->geo, m->nbr, m->bgl, A);
+        ADG_CK(cudaGetLastError(), "lts corrector launch");
+    }
+    return ADG_OK;
+}
+
+template <int N>
+static int lts_cycle_n(LtsRun& R, int l0, double t) {
+    if constexpr (N < 2) {
+        (void)R;
+        (void)l0;
+        (void)t;
+        return fail(ADG_EUNSUPPORTED, "step_lts: degree >= 2");
+    } else {
+        return lts_level_n<N>(R, l0, t, 0);
+    }
+}
+
+int amr_step_lts(adg_mesh* m, double dt, double* cycle, void* stream) {
+    AmrTree* T = tree_of(m);
+    LtsRun R;
+    R.m = m;
+    R.s = (cudaStream_t)stream;
+    R.dt = dt;
+    int l0 = 1 << 30, L = 0;
+    for (const auto& c : T->leaves) {
+        l0 = std::min(l0, c[0]);
+        L = std::max(L, c[0]);
+    }
+    R.L = L;
+    R.off.assign(L + 2, 0);
+    for (const auto& c : T->leaves) R.off[c[0] + 1]++;
+    for (int l = 0; l <= L; ++l) R.off[l + 1] += R.off[l];
+    // W[s][k] = sum_q w_q phi_k((s + xi_q)/3): the average over the third s of the step
+    const int n = m->n;
+    for (int s3 = 0; s3 < 3; ++s3)
+        for (int k = 0; k < n; ++k) {
+            double a = 0.0;
+            for (int q = 0; q < n; ++q) {
+                const double x = (s3 + m->B.xi[q]) / 3.0;
+                double phi = 1.0;
+                for (int r = 0; r < n; ++r)
+                    if (r != k) phi *= (x - m->B.xi[r]) / (m->B.xi[k] - m->B.xi[r]);
+                a += m->B.w[q] * phi;
+            }
+            R.W[s3][k] = a;
+        }
+    // per-time-node traces and flux sums, grow-only with the leaf capacity
+    if (m->lts_cap < m->leaf_cap) {
+        cudaFree(m->lts_ttrace);
+        cudaFree(m->lts_acc);
+        m->lts_ttrace = m->lts_acc = nullptr;
+        const size_t C = (size_t)m->leaf_cap;
+        if (cudaMalloc(&m->lts_ttrace, C * n * 4 * 16 * n * 8) != cudaSuccess ||
+            cudaMalloc(&m->lts_acc, C * 4 * 3 * 4 * n * 8) != cudaSuccess) {
+            cudaGetLastError();
+            m->lts_cap = 0;
+            return fail(ADG_ENOMEM, "step_lts: buffers");
+        }
+        m->lts_cap = m->leaf_cap;
+    }
+    if (cycle) *cycle = dt * std::pow(3.0, L - l0);
+    switch (m->N) {
+        case 1: return lts_cycle_n<1>(R, l0, m->t);
+        case 2: return lts_cycle_n<2>(R, l0, m->t);
+        case 3: return lts_cycle_n<3>(R, l0, m->t);
+        case 4: return lts_cycle_n<4>(R, l0, m->t);
+        case 5: return lts_cycle_n<5>(R, l0, m->t);
+        case 6: return lts_cycle_n<6>(R, l0, m->t);
+        case 7: return lts_cycle_n<7>(R, l0, m->t);
+    }
+    return fail(ADG_EINVAL, "bad degree");
+}
 
 template <int N>
 static int transfer_n(adg_mesh* m, const double* uold, double* unew, int leaves, const int* trans, cudaStream_t s) {

@@ -546,6 +546,21 @@ int adg_init_scenario(adg_mesh* m, const adg_scenario* s, void* stream) {
     return ADG_OK;
 }
 
+int adg_step_lts(adg_mesh* m, double dt, double* cycle, void* stream) {
+    if (!m) return fail(ADG_EINVAL, "step_lts: NULL mesh");
+    if (!m->amr) return fail(ADG_EINVAL, "step_lts: adaptive meshes only (max_levels > 0)");
+    if (m->d.precision != ADG_PREC_FP64) return fail(ADG_EUNSUPPORTED, "step_lts: FP64 meshes only");
+    if (m->N < 2) return fail(ADG_EUNSUPPORTED, "step_lts: degree >= 2");
+    if (!(dt > 0.0) || !std::isfinite(dt)) return fail(ADG_EINVAL, "step_lts: dt must be finite and > 0");
+    if (int rc = set_device(m)) return rc;
+    double c = 0.0;
+    if (int rc = adg::amr_step_lts(m, dt, &c, stream)) return rc;
+    m->t += c;
+    m->predicted = false;
+    if (cycle) *cycle = c;
+    return ADG_OK;
+}
+
 int adg_predictor(adg_mesh* m, double dt, void* stream) {
     if (!m) return fail(ADG_EINVAL, "predictor: NULL mesh");
     if (!(dt > 0.0) || !std::isfinite(dt)) return fail(ADG_EINVAL, "predictor: dt must be finite and > 0");

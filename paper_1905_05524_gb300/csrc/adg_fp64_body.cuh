@@ -13,12 +13,19 @@ namespace adg {
 // the time-dependent manufactured source (evaluated at t + xi_k dt for time
 // node k); it is a separate instantiation so that the source-free kernel's
 // register allocation is not shaped by the source's arithmetic.
-template <int N, int CPB, bool TSRC = false>
+//
+// REC (local time stepping, adg_amr.cu): also write the face traces of every
+// time node k of the final iterate, ttrace[cell][k][face][16][n] (q, normal
+// flux, q_x, q_y extrapolated to the face), from which a finer neighbour
+// forms the trace averaged over its own part of this cell's step.
+template <int N, int CPB, bool TSRC = false, bool REC = false>
 __device__ __forceinline__ void predictor_fp64_body(const double* __restrict__ u, double* __restrict__ rvol,
                                                     double* __restrict__ trace, int cell, bool active, double dt,
                                                     const Basis& B, const Phys& P, double xorg, double yorg,
-                                                    double pbar, double rhobar, double* sm, double t = 0.0) {
+                                                    double pbar, double rhobar, double* sm, double t = 0.0,
+                                                    double* __restrict__ ttrace = nullptr) {
     constexpr int n = N + 1, n2 = n * n, SL = 4 * n2;
+    static_assert(!REC || n >= 3, "the per-time-node traces use the flux area (2 n SL >= 5 SL)");
     const int cl = threadIdx.x / n2;
     const int node = threadIdx.x - cl * n2;
     const int j = node / n, i = node - j * n;
@@ -164,6 +171,38 @@ __device__ __forceinline__ void predictor_fp64_body(const double* __restrict__ u
         double q[4], qx[4], qy[4];
         Flux4 f;
         eval_node(Q + k * SL, q, qx, qy, f);
+        if constexpr (REC) {
+            // slots 0..4 = q, F, G, q_x, q_y of time node k in the free flux area (5 SL <= 2 n SL)
+            double* T = Fs;
+            __syncthreads();  // the previous time node's extrapolation has read T
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                T[0 * SL + v * n2 + node] = q[v];
+                T[1 * SL + v * n2 + node] = f.F[v];
+                T[2 * SL + v * n2 + node] = f.G[v];
+                T[3 * SL + v * n2 + node] = qx[v];
+                T[4 * SL + v * n2 + node] = qy[v];
+            }
+            __syncthreads();
+            for (int idx = node; idx < 4 * n; idx += n2) {
+                const int fc = idx / n, m = idx - fc * n;
+                const bool xface = fc < 2;
+                const double* phi = (fc == 0 || fc == 2) ? B.phi1 : B.phi0;
+                double* tt = ttrace + ((((size_t)cell * n + k) * 4 + fc) * 16) * n;
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const int slot = c == 0 ? 0 : c == 1 ? (xface ? 1 : 2) : (c == 2 ? 3 : 4);
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) {
+                        const double* S = T + slot * SL + v * n2;
+                        double sv = 0.0;
+#pragma unroll
+                        for (int p = 0; p < n; ++p) sv += phi[p] * (xface ? S[m * n + p] : S[p * n + m]);
+                        if (active) tt[(c * 4 + v) * n + m] = sv;
+                    }
+                }
+            }
+        }
         const double wk = B.w[k];
         double Sk[4];
         src_k(k, Sk);

@@ -47,6 +47,10 @@ struct adg_mesh {
     double hmin = 0.0;            // smallest leaf size (dt rule)
     double* halo = nullptr;       // strip decomposition: [2][nx][17][n] south, north halo traces
     unsigned epoch = 0;           // changes whenever the state or workspace buffers move (adg_adapt)
+    // local time stepping (adg_step_lts): per-time-node traces and fine-flux sums, grow-only
+    double* lts_ttrace = nullptr;
+    double* lts_acc = nullptr;
+    int lts_cap = 0;
 };
 
 namespace adg {
@@ -64,6 +68,7 @@ int amr_tv_cells(adg_mesh* m, int var, double* tv, double* part, void* stream);
 int amr_max_speed(adg_mesh* m, double* lam_max, void* stream);
 int amr_init_scenario(adg_mesh* m, const adg_scenario* s, void* stream);
 const void* amr_ops(const adg_mesh* m);
+int amr_step_lts(adg_mesh* m, double dt, double* cycle, void* stream);
 }  // namespace adg
 
 #define ADG_CK(call, what)                                        \

@@ -182,6 +182,13 @@ class Mesh:
         for _ in range(nsteps):
             L.check(self._lib.adg_step(self.h, float(dt), sp))
 
+    def step_lts(self, dt, stream=None):
+        """One local-time-stepping cycle of an adaptive FP64 mesh (adg_step_lts);
+        returns the cycle length."""
+        c = ctypes.c_double()
+        L.check(self._lib.adg_step_lts(self.h, float(dt), ctypes.byref(c), _stream_ptr(stream)))
+        return c.value
+
     def stable_dt(self, cfl, stream=None):
         dt = ctypes.c_double()
         L.check(self._lib.adg_stable_dt(self.h, float(cfl), ctypes.byref(dt), _stream_ptr(stream)))
