@@ -492,7 +492,7 @@ def run_amr(args, dev):
     import torch
     from paper_1905_05524_gb300 import _lib as L
     from paper_1905_05524_gb300.solver import Batch, Mesh, atmosphere_config
-    def amr_run(prec, batched=False):
+    def amr_run(prec, batched=False, lts=False):
         cfg = atmosphere_config(degree=DEGREE, nx=27, ny=27, mu=0.001, device=dev.index, precision=prec)
         cfg.max_levels = 2
         m = Mesh(cfg)
@@ -510,24 +510,39 @@ def run_amr(args, dev):
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         leaf_hist = []
         batch = Batch([m]) if batched else None
-        for s0 in range(0, steps, every):
+        t_sim, s0 = 0.0, 0
+        while s0 < steps:
             k = min(every, steps - s0)
             ev0.record()
-            if batch is not None:
+            if lts:
+                # local time stepping: cycles of the finest step dt until k fine steps of time have passed
+                levels = [c[0] for c in m.leaf_info()]
+                l0 = min(levels)
+                done = 0
+                while done < k:
+                    c = m.step_lts(dt)
+                    r = int(round(c / dt))
+                    done += r
+                    dof_updates += sum(3 ** (lv - l0) for lv in levels) * (DEGREE + 1) ** 2 * 4
+                k = done
+            elif batch is not None:
                 batch.step([dt], nsteps=k)  # rebuilt and re-captured after each adaptation
             else:
                 m.step(dt, k)
             ev1.record()
             ev1.synchronize()
             t_steps += ev0.elapsed_time(ev1) * 1e-3
-            dof_updates += m.leaves * (DEGREE + 1) ** 2 * 4 * k
+            if not lts:
+                dof_updates += m.leaves * (DEGREE + 1) ** 2 * 4 * k
+            s0 += k
+            t_sim += k * dt
             leaf_hist.append(m.leaves)
             _, fl, _ = m.tv_indicator(L.ADG_TV_THETA, 2.5, -0.5)
             m.adapt(fl)
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
         res = dict(dt=dt, steps=steps, every=every, dof_updates=dof_updates, t_steps=t_steps, wall=wall,
-                   leaves=m.leaf_info(), ua=m.get_state().cpu().numpy(), leaf_hist=leaf_hist)
+                   leaves=m.leaf_info(), ua=m.get_state().cpu().numpy(), leaf_hist=leaf_hist, t_sim=t_sim)
         if batch is not None:
             res["batch_info"] = batch.info()
             batch.close()
@@ -537,6 +552,7 @@ def run_amr(args, dev):
     r64 = amr_run(L.ADG_PREC_FP64)
     rmx = amr_run(L.ADG_PREC_MIXED)
     rbt = amr_run(L.ADG_PREC_MIXED, batched=True)
+    rlt = amr_run(L.ADG_PREC_FP64, lts=True)
     dt, steps, every = r64["dt"], r64["steps"], r64["every"]
     dof_updates, t_steps, wall = r64["dof_updates"], r64["t_steps"], r64["wall"]
     leaves, ua, leaf_hist = r64["leaves"], r64["ua"], r64["leaf_hist"]
@@ -588,6 +604,19 @@ def run_amr(args, dev):
         "leaves_mean": float(np.mean(leaf_hist)),
         "mixed": mixed,
         "mixed_batched": mixed_batched,
+        "fp64_local_time_stepping": {
+            "value": rlt["dof_updates"] / rlt["t_steps"], "unit": UNIT,
+            "simulated_seconds": rlt["t_sim"], "seconds": rlt["t_steps"],
+            "simulated_per_wall_second": rlt["t_sim"] / rlt["t_steps"],
+            "global_dt_simulated_per_wall_second": r64["t_sim"] / r64["t_steps"],
+            "speedup_in_simulated_time": (rlt["t_sim"] / rlt["t_steps"]) / (r64["t_sim"] / r64["t_steps"]),
+            "dof_updates": rlt["dof_updates"], "global_dt_dof_updates": r64["dof_updates"],
+            "leaves_final": len(rlt["leaves"]),
+            "theta_prime_rel_l2_vs_global_dt": float(np.sqrt((W * (theta_prime_np(prolong_to_level(
+                rlt["ua"], rlt["leaves"], DEGREE, lmax, 27, 27).reshape(-1, 4, DEGREE + 1, DEGREE + 1), cfu)
+                - tha) ** 2).sum()) / np.sqrt((W * tha ** 2).sum())) if rlt["leaves"] == leaves else None,
+            "form": "adg_step_lts: coarse leaves step 3x longer than the level below (the same physical time "
+                    "as the global-dt FP64 run; regrid after every cycle group of >= 10 fine steps)"},
         "uniform_reference": {"cells": side * side, "value": side * side * n * n * 4 * steps / t_uni, "unit": UNIT,
                               "seconds": t_uni},
         "uniform_equivalent_value": side * side * n * n * 4 * steps / t_steps,
@@ -609,7 +638,7 @@ def run_sweep(args, dev):
     out = []
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-    for N in range(2, 8):
+    for N in [int(d) for d in args.sweep_degrees.split(",")]:
         row = {"degree": N}
         for prec_name, prec in (("fp64", L.ADG_PREC_FP64), ("mixed", L.ADG_PREC_MIXED)):
             cfg = steady_manufactured_config(degree=N, nx=243, ny=243, precision=prec, device=dev.index)
@@ -1062,6 +1091,7 @@ def main():
                          "fv (MUSCL-Hancock finite volumes, colliding bubbles), "
                          "3d (3D cosine bubble and ABC flow)")
     ap.add_argument("--sweep-steps", type=int, default=20)
+    ap.add_argument("--sweep-degrees", default="2,3,4,5,6,7", help="degrees of the sweep workload")
     ap.add_argument("--full-3d", action="store_true",
                     help="with --workload 3d: also run the paper's 3D bubble to t = 400 s (mixed precision)")
     ap.add_argument("--amr-steps", type=int, default=1000)
