@@ -421,19 +421,21 @@ def run_form(prec_name, steps, warmup, dev, ws):
                 e2e_serial_sec=e2e_serial_sec, e2e_ok=e2e_ok, cfg=cfg, dt=dt)
 
 
-def run_batch(dev, nsteps=20, instances=64):
+def run_batch(dev, nsteps=20, instances=64, fp64=False):
     """Batch of `instances` warm-bubble instances (sides U{9..81},
-    seed 3; radii U[100,300] m, seed 4), degree 5, mixed precision, advanced
-    by the persistent graph-captured batched launch (predictor + corrector)."""
+    seed 3; radii U[100,300] m, seed 4), degree 5, mixed precision (FP64 with
+    fp64=True), advanced by the persistent graph-captured batched launch
+    (predictor + corrector)."""
     import torch
     from paper_1905_05524_gb300 import _lib as L
     from paper_1905_05524_gb300 import inputs
     from paper_1905_05524_gb300.solver import Batch, Mesh, atmosphere_config
     sides = inputs.instance_sizes(instances, seed=3, lo=9, hi=81)
     radii = inputs.uniform_values(instances, seed=4, lo=100.0, hi=300.0)
+    prec = L.ADG_PREC_FP64 if fp64 else L.ADG_PREC_MIXED
     ms = []
     for s_, r_ in zip(sides, radii):
-        m = Mesh(atmosphere_config(degree=DEGREE, nx=int(s_), ny=int(s_), precision=L.ADG_PREC_MIXED,
+        m = Mesh(atmosphere_config(degree=DEGREE, nx=int(s_), ny=int(s_), precision=prec,
                                    device=dev.index))
         m.init_scenario(L.ADG_SCEN_COSINE, A=0.5, a=float(r_), xc=500.0, zc=350.0)
         ms.append(m)
@@ -455,6 +457,7 @@ def run_batch(dev, nsteps=20, instances=64):
     for m in ms:
         m.close()
     return {"value": dof * nsteps / (ms_total * 1e-3), "unit": UNIT, "instances": instances,
+            "precision": "fp64" if fp64 else "mixed",
             "cells": cells, "steps": nsteps, "ms_per_step": ms_total / nsteps,
             "step": "predictor + corrector (persistent launches, CUDA graph)", "tiles": info,
             "l2": "state (%.0f MB) exceeds L2" % (dof * 8 / 1e6) if dof * 8 > 129e6 else "not flushed"}
@@ -1004,6 +1007,7 @@ def run_ours(args):
                                             "steps": args.steps, "stated_bound": 1e-6}
         if not args.no_batch and args.precision == "mixed":
             forms["mixed_batched_64_instances"] = run_batch(dev, nsteps=args.batch_steps)
+            forms["fp64_batched_64_instances"] = run_batch(dev, nsteps=max(1, args.batch_steps // 4), fp64=True)
         peaks = {} if args.no_peaks else measure_fma_peaks()
         mp = measured_peaks_file()
         flops_launch = predictor_flops_per_cell(n) * cells

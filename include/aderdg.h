@@ -283,9 +283,17 @@ int adg_check_finite(adg_mesh* m, void* stream);
  * empty value keeps the cache in memory only), else tune_cache.json beside
  * the library; an entry found there is used without timing.
  *
- *   meshes   k distinct meshes of one degree and device, all ADG_PREC_MIXED
- *            (ADG_EUNSUPPORTED otherwise); they stay owned by the caller and
- *            must outlive the batch; their states are advanced in place
+ * A batch of ADG_PREC_FP64 members runs the per-mesh FP64 predictor and
+ * corrector bodies in the persistent launches, with one tile size (the
+ * per-mesh cells per block) and no timing; its members are uniform meshes
+ * without the time-dependent source (ADG_SRC_PAPER), analytic sides or strip
+ * exchange, since the graph replays fixed arguments (ADG_EUNSUPPORTED).
+ *
+ *   meshes   k distinct meshes of one degree, device and precision, all
+ *            ADG_PREC_MIXED or all ADG_PREC_FP64 (ADG_EINVAL for a mix,
+ *            ADG_EUNSUPPORTED for ADG_PREC_MIXED_TF32); they stay owned by
+ *            the caller and must outlive the batch; their states are
+ *            advanced in place
  *   dt       host array of k time steps (> 0), one per instance
  *   nsteps   steps per call (>= 1); each instance's time += nsteps * dt
  *   info     adg_batch_info fills up to n of: predictor tiles, cells per
@@ -304,7 +312,7 @@ int adg_batch_info(const adg_batch* b, int* info, int n);
  * reproduce a run or to test every candidate.  Synchronises the device
  * (the previous tile list may be in use by a launched step), rebuilds the
  * tile list and drops the captured graph.  ADG_EINVAL for a NULL batch or a
- * candidate outside 0..2. */
+ * candidate outside 0..2; ADG_EUNSUPPORTED for an FP64 batch. */
 int adg_batch_set_candidate(adg_batch* b, int cand);
 void adg_batch_destroy(adg_batch* b);
 

@@ -984,12 +984,15 @@ extern "C" int adg_step_noalloc(const adg_mesh_desc* d, double* u, size_t count,
 // choice is kept in a JSON cache keyed by degree, precision and SM count.
 struct adg_batch {
     int device = 0, N = 0, k = 0;
+    int precision = ADG_PREC_MIXED;         // of every member
     std::vector<adg_mesh*> meshes;
     std::vector<int> slot;                  // mesh -> index in its kind's table (uniform or adaptive)
     std::vector<unsigned> epoch;            // mesh epochs the tables were built for
     std::vector<adg::MixedInst> host_insts;
     std::vector<adg::AmrInst> host_ainsts;
+    std::vector<adg::Fp64Inst> host_finsts;
     adg::MixedInst* insts = nullptr;
+    adg::Fp64Inst* finsts = nullptr;
     adg::AmrInst* ainsts = nullptr;
     const void* ops = nullptr;              // prolongation/restriction of the adaptive instances
     adg::BatchTile* tiles_pred = nullptr;
@@ -1088,6 +1091,7 @@ void free_batch(adg_batch* b) {
     if (b->cap) cudaStreamDestroy(b->cap);
     cudaFree(b->insts);
     cudaFree(b->ainsts);
+    cudaFree(b->finsts);
     cudaFree(b->tiles_pred);
     cudaFree(b->tiles_corr);
     delete b;
@@ -1095,6 +1099,8 @@ void free_batch(adg_batch* b) {
 
 int launch_phase(adg_batch* b, int cand, int phase, const adg::BatchTile* tiles, int ntiles, int* cpb, int* blocks,
                  cudaStream_t s) {
+    if (b->precision == ADG_PREC_FP64)
+        return adg::launch_batch_fp64(b->N, phase, b->finsts, tiles, ntiles, b->meshes[0]->B, cpb, blocks, s);
     return adg::launch_batch_mixed(b->N, cand, phase, b->insts, b->host_ainsts.empty() ? nullptr : b->ainsts, tiles,
                                    ntiles, b->meshes[0]->Bf, b->meshes[0]->B, b->ops, cpb, blocks, s);
 }
@@ -1123,11 +1129,23 @@ int upload_tiles(adg_batch* b, int cand, int phase, adg::BatchTile** dst, int* n
 int build_instances(adg_batch* b) {
     b->host_insts.clear();
     b->host_ainsts.clear();
+    b->host_finsts.clear();
     b->cells = 0;
     for (int a = 0; a < b->k; ++a) {
         adg_mesh* m = b->meshes[a];
         const double dt = b->last_dt[a] > 0.0 ? b->last_dt[a] : 0.0;
-        if (m->amr) {
+        if (b->precision == ADG_PREC_FP64) {
+            adg::Fp64Inst I;
+            I.u = m->u;
+            I.rvol = m->rvol;
+            I.trace = m->trace;
+            I.cells = m->cells;
+            I.dt = dt;
+            I.P = m->P;
+            I.bg = m->bg;
+            b->slot[a] = (int)b->host_finsts.size();
+            b->host_finsts.push_back(I);
+        } else if (m->amr) {
             adg::AmrInst I;
             I.u = m->u;
             I.rvol = m->rvol;
@@ -1163,11 +1181,15 @@ int build_instances(adg_batch* b) {
     }
     cudaFree(b->insts);
     cudaFree(b->ainsts);
+    cudaFree(b->finsts);
     b->insts = nullptr;
     b->ainsts = nullptr;
+    b->finsts = nullptr;
     const size_t nu = std::max<size_t>(1, b->host_insts.size()), na = std::max<size_t>(1, b->host_ainsts.size());
+    const size_t nf = std::max<size_t>(1, b->host_finsts.size());
     if (cudaMalloc(&b->insts, nu * sizeof(adg::MixedInst)) != cudaSuccess ||
-        cudaMalloc(&b->ainsts, na * sizeof(adg::AmrInst)) != cudaSuccess) {
+        cudaMalloc(&b->ainsts, na * sizeof(adg::AmrInst)) != cudaSuccess ||
+        cudaMalloc(&b->finsts, nf * sizeof(adg::Fp64Inst)) != cudaSuccess) {
         cudaGetLastError();
         return fail(ADG_ENOMEM, "batch: instance tables");
     }
@@ -1177,6 +1199,9 @@ int build_instances(adg_batch* b) {
     if (!b->host_ainsts.empty())
         ADG_CK(cudaMemcpy(b->ainsts, b->host_ainsts.data(), b->host_ainsts.size() * sizeof(adg::AmrInst),
                           cudaMemcpyHostToDevice), "batch: adaptive instance table");
+    if (!b->host_finsts.empty())
+        ADG_CK(cudaMemcpy(b->finsts, b->host_finsts.data(), b->host_finsts.size() * sizeof(adg::Fp64Inst),
+                          cudaMemcpyHostToDevice), "batch: FP64 instance table");
     return ADG_OK;
 }
 
@@ -1189,13 +1214,26 @@ extern "C" int adg_batch_create(adg_mesh* const* meshes, int k, adg_batch** out)
         if (!meshes[a]) return fail(ADG_EINVAL, "batch_create: NULL mesh");
         if (meshes[a]->N != meshes[0]->N || meshes[a]->d.device != meshes[0]->d.device)
             return fail(ADG_EINVAL, "batch_create: meshes must share degree and device");
-        if (meshes[a]->d.precision != ADG_PREC_MIXED)
-            return fail(ADG_EUNSUPPORTED, "batch_create: batched launch is built for ADG_PREC_MIXED meshes");
+        const adg_mesh* m = meshes[a];
+        if (m->d.precision != meshes[0]->d.precision)
+            return fail(ADG_EINVAL, "batch_create: meshes must share the precision");
+        if (m->d.precision == ADG_PREC_FP64) {
+            // uniform FP64 members: the graph replays fixed arguments, so no
+            // time-dependent source or boundary data, and no strip exchange
+            if (m->amr) return fail(ADG_EUNSUPPORTED, "batch_create: FP64 members must be uniform meshes");
+            if (m->d.source == ADG_SRC_PAPER || m->d.bc_x == ADG_BC_ANALYTIC || m->d.bc_y == ADG_BC_ANALYTIC)
+                return fail(ADG_EUNSUPPORTED, "batch_create: no time-dependent source or boundary in a batch");
+            if (m->bg.halo_s || m->bg.halo_n)
+                return fail(ADG_EUNSUPPORTED, "batch_create: strip-exchange meshes cannot be batched");
+        } else if (m->d.precision != ADG_PREC_MIXED) {
+            return fail(ADG_EUNSUPPORTED, "batch_create: batched launch is built for ADG_PREC_MIXED and FP64 meshes");
+        }
         for (int c = 0; c < a; ++c)
             if (meshes[c] == meshes[a]) return fail(ADG_EINVAL, "batch_create: a mesh appears twice");
     }
     adg_batch* b = new adg_batch();
     b->device = meshes[0]->d.device;
+    b->precision = meshes[0]->d.precision;
     b->N = meshes[0]->N;
     b->k = k;
     b->meshes.assign(meshes, meshes + k);
@@ -1208,6 +1246,14 @@ extern "C" int adg_batch_create(adg_mesh* const* meshes, int k, adg_batch** out)
         cudaError_t e = cudaGetLastError();
         free_batch(b);
         return cuda_fail(e, "batch_create: setup");
+    }
+    if (b->precision == ADG_PREC_FP64) {  // one tile size (the per-mesh cells per block)
+        b->cand_pred = b->cand_corr = 0;
+        int rc = upload_tiles(b, 0, 0, &b->tiles_pred, &b->ntiles_pred, &b->cpb_pred, &b->blocks_pred);
+        if (!rc) rc = upload_tiles(b, 0, 1, &b->tiles_corr, &b->ntiles_corr, &b->cpb_corr, &b->blocks_corr);
+        if (rc) { free_batch(b); return rc; }
+        *out = b;
+        return ADG_OK;
     }
     // autotune the predictor tile size (the predictor only reads the state)
     int sms = 0;
@@ -1280,6 +1326,8 @@ extern "C" int adg_batch_info(const adg_batch* b, int* info, int n) {
 extern "C" int adg_batch_set_candidate(adg_batch* b, int cand) {
     if (!b) return fail(ADG_EINVAL, "batch_set_candidate: NULL batch");
     if (cand < 0 || cand >= adg::kBatchCandidates) return fail(ADG_EINVAL, "batch_set_candidate: candidate not in 0..2");
+    if (b->precision == ADG_PREC_FP64)
+        return fail(ADG_EUNSUPPORTED, "batch_set_candidate: FP64 batches have one tile size");
     ADG_CK(cudaSetDevice(b->device), "batch_set_candidate: cudaSetDevice");
     ADG_CK(cudaDeviceSynchronize(), "batch_set_candidate: synchronise");
     drop_graph(b);
@@ -1312,7 +1360,9 @@ extern "C" int adg_batch_step(adg_batch* b, const double* dt, int nsteps, void* 
         if (dt[a] != b->last_dt[a]) {
             changed = true;
             b->last_dt[a] = dt[a];
-            if (b->meshes[a]->amr) {
+            if (b->precision == ADG_PREC_FP64) {
+                b->host_finsts[b->slot[a]].dt = dt[a];
+            } else if (b->meshes[a]->amr) {
                 b->host_ainsts[b->slot[a]].dt = dt[a];
                 b->host_ainsts[b->slot[a]].dtf = (float)dt[a];
             } else {
@@ -1326,6 +1376,9 @@ extern "C" int adg_batch_step(adg_batch* b, const double* dt, int nsteps, void* 
                                    cudaMemcpyHostToDevice, s), "batch_step: dt upload");
         if (!b->host_ainsts.empty())
             ADG_CK(cudaMemcpyAsync(b->ainsts, b->host_ainsts.data(), b->host_ainsts.size() * sizeof(adg::AmrInst),
+                                   cudaMemcpyHostToDevice, s), "batch_step: dt upload");
+        if (!b->host_finsts.empty())
+            ADG_CK(cudaMemcpyAsync(b->finsts, b->host_finsts.data(), b->host_finsts.size() * sizeof(adg::Fp64Inst),
                                    cudaMemcpyHostToDevice, s), "batch_step: dt upload");
         // the staging vectors must stay valid until the copies have run
         ADG_CK(cudaStreamSynchronize(s), "batch_step: dt upload sync");

@@ -160,16 +160,16 @@ __device__ __forceinline__ void analytic_ghost(double x, double y, int f, double
 // With TV the TV indicator of the updated state follows in the same kernel
 // (tv_cell, bitwise what k_tv_cells computes).
 template <int N, int CPB, bool TV>
-__global__ void __launch_bounds__(CPB*(N + 1) * (N + 1))
-k_corrector_fp64(double* __restrict__ u, const double* __restrict__ rvol,
-                 const double* __restrict__ trace, int cells, double dt, const Basis B,
-                 const Phys P, const Background bg, const TvEpilogue epi, double t) {
+__device__ __forceinline__ void corrector_fp64_body(double* __restrict__ u, const double* __restrict__ rvol,
+                                                    const double* __restrict__ trace, int cells, int c0, double dt,
+                                                    const Basis& B, const Phys& P, const Background& bg,
+                                                    const TvEpilogue& epi, double t) {
     constexpr int n = N + 1, n2 = n * n, SL = 4 * n2, TR = kTraceComps * n;
     __shared__ double Fst[CPB][4][4][n];
     const int cl = threadIdx.x / n2;
     const int node = threadIdx.x - cl * n2;
     const int j = node / n, i = node - j * n;
-    const int cell_raw = blockIdx.x * CPB + cl;
+    const int cell_raw = c0 + cl;
     const bool active = cell_raw < cells;
     const int cell = active ? cell_raw : cells - 1;
     const int ix = cell % P.nx, iy = cell / P.nx;
@@ -257,8 +257,100 @@ k_corrector_fp64(double* __restrict__ u, const double* __restrict__ rvol,
         static_assert(CPB == tv_cpb(N), "the TV statistics combine blocks of tv_cpb(N) cells");
         const double r =
             tv_cell<N, double>(f, 0.0, node, i, j, B, P.inv_hx, P.inv_hy, fs[cl], red[cl], active, epi.tv + cell);
-        tv_block_triple<CPB>(r, node == 0, cl, min(CPB, cells - (int)blockIdx.x * CPB), epi.part);
+        tv_block_triple<CPB>(r, node == 0, cl, min(CPB, cells - c0), epi.part);
     }
+}
+
+template <int N, int CPB, bool TV>
+__global__ void __launch_bounds__(CPB*(N + 1) * (N + 1))
+k_corrector_fp64(double* __restrict__ u, const double* __restrict__ rvol,
+                 const double* __restrict__ trace, int cells, double dt, const Basis B,
+                 const Phys P, const Background bg, const TvEpilogue epi, double t) {
+    corrector_fp64_body<N, CPB, TV>(u, rvol, trace, cells, blockIdx.x * CPB, dt, B, P, bg, epi, t);
+}
+
+// Batched persistent FP64 kernels over uniform instances (tile = instance,
+// first cell; tile t goes to block t mod grid): the per-mesh bodies.
+template <int N, int CPB>
+__global__ void __launch_bounds__(CPB*(N + 1) * (N + 1))
+k_predictor_batch_fp64(const Fp64Inst* __restrict__ insts, const BatchTile* __restrict__ tiles, int ntiles,
+                       const Basis B) {
+    constexpr int n = N + 1, n2 = n * n;
+    extern __shared__ double sm[];
+    const int cl = threadIdx.x / n2;
+    const int j = (threadIdx.x - cl * n2) / n;
+    for (int tt = blockIdx.x; tt < ntiles; tt += gridDim.x) {
+        const BatchTile tl = tiles[tt];
+        const Fp64Inst& I = insts[tl.inst];
+        const Phys P = I.P;
+        const int cell_raw = tl.c0 + cl;
+        const bool active = cell_raw < I.cells;
+        const int cell = active ? cell_raw : I.cells - 1;
+        const int ix = cell % P.nx, iy = cell / P.nx;
+        predictor_fp64_body<N, CPB>(I.u, I.rvol, I.trace, cell, active, I.dt, B, P, P.x0 + ix * P.hx,
+                                    P.y0 + iy * P.hy, I.bg.pbar_node[iy * n + j], I.bg.rhobar_node[iy * n + j], sm);
+        __syncthreads();
+    }
+}
+
+template <int N, int CPB>
+__global__ void __launch_bounds__(CPB*(N + 1) * (N + 1))
+k_corrector_batch_fp64(const Fp64Inst* __restrict__ insts, const BatchTile* __restrict__ tiles, int ntiles,
+                       const Basis B) {
+    for (int tt = blockIdx.x; tt < ntiles; tt += gridDim.x) {
+        const BatchTile tl = tiles[tt];
+        const Fp64Inst& I = insts[tl.inst];
+        const Phys P = I.P;
+        const Background bg = I.bg;
+        corrector_fp64_body<N, CPB, false>(I.u, I.rvol, I.trace, I.cells, tl.c0, I.dt, B, P, bg, TvEpilogue{}, 0.0);
+        __syncthreads();
+    }
+}
+
+template <int N>
+static int batch_fp64_n(int phase, const Fp64Inst* insts, const BatchTile* tiles, int ntiles, const Basis& B,
+                        int* cpb_out, int* blocks_io, cudaStream_t s) {
+    using C = Fp64Cfg<N>;
+    if (cpb_out) *cpb_out = C::cpb;
+    if (!tiles) {  // query: smem limit and persistent grid (not during capture)
+        int per_sm = 0, dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaError_t e;
+        if (phase == 0) {
+            e = cudaFuncSetAttribute(k_predictor_batch_fp64<N, C::cpb>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)C::smem_pred);
+            if (e == cudaSuccess)
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_predictor_batch_fp64<N, C::cpb>,
+                                                                  C::threads, C::smem_pred);
+        } else {
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_corrector_batch_fp64<N, C::cpb>, C::threads,
+                                                              0);
+        }
+        if (e != cudaSuccess) return (int)e;
+        if (blocks_io) *blocks_io = per_sm > 0 ? per_sm * sms : sms;
+        return 0;
+    }
+    if (phase == 0)
+        k_predictor_batch_fp64<N, C::cpb><<<*blocks_io, C::threads, C::smem_pred, s>>>(insts, tiles, ntiles, B);
+    else
+        k_corrector_batch_fp64<N, C::cpb><<<*blocks_io, C::threads, 0, s>>>(insts, tiles, ntiles, B);
+    return (int)cudaGetLastError();
+}
+
+int launch_batch_fp64(int N, int phase, const Fp64Inst* insts, const BatchTile* tiles, int ntiles, const Basis& B,
+                      int* cpb_out, int* blocks_out, void* stream) {
+    cudaStream_t s = (cudaStream_t)stream;
+    switch (N) {
+        case 1: return batch_fp64_n<1>(phase, insts, tiles, ntiles, B, cpb_out, blocks_out, s);
+        case 2: return batch_fp64_n<2>(phase, insts, tiles, ntiles, B, cpb_out, blocks_out, s);
+        case 3: return batch_fp64_n<3>(phase, insts, tiles, ntiles, B, cpb_out, blocks_out, s);
+        case 4: return batch_fp64_n<4>(phase, insts, tiles, ntiles, B, cpb_out, blocks_out, s);
+        case 5: return batch_fp64_n<5>(phase, insts, tiles, ntiles, B, cpb_out, blocks_out, s);
+        case 6: return batch_fp64_n<6>(phase, insts, tiles, ntiles, B, cpb_out, blocks_out, s);
+        case 7: return batch_fp64_n<7>(phase, insts, tiles, ntiles, B, cpb_out, blocks_out, s);
+    }
+    return (int)cudaErrorInvalidValue;
 }
 
 template <int N>

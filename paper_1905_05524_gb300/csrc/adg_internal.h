@@ -117,6 +117,16 @@ struct AmrInst {
     const double* mb64;
     const float* mbf;
 };
+// Uniform FP64 instance of a batch (the per-mesh FP64 bodies of adg_fp64.cu).
+struct Fp64Inst {
+    double* u;
+    double* rvol;
+    double* trace;
+    int cells;
+    double dt;
+    Phys P;
+    Background bg;
+};
 // A tile of a batch: inst >= 0 names a uniform instance, inst < 0 the
 // adaptive instance -inst - 1; c0 is its first cell (leaf).
 struct BatchTile {
@@ -173,6 +183,10 @@ int launch_corrector_mixed(int N, double* u, const float* rvol, const float* tra
 // phase 0: predictor, 1: corrector.  tiles == nullptr: query -- returns the
 // cells per block and writes the persistent grid size to *blocks_out; otherwise
 // launches with the grid size in *blocks_out.
+// Batched persistent launch over uniform FP64 instances (adg_fp64.cu); with
+// tiles == NULL: query the cells per block and persistent grid.
+int launch_batch_fp64(int N, int phase, const Fp64Inst* insts, const BatchTile* tiles, int ntiles, const Basis& B,
+                      int* cpb_out, int* blocks_out, void* stream);
 // Batched persistent launch over uniform (insts) and adaptive (ainsts, may be
 // NULL) mixed-precision instances (adg_amr.cu).  B, ops: FP64 basis and the
 // adaptive mesh's prolongation/restriction operators (used when ainsts is

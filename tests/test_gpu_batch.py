@@ -75,15 +75,15 @@ def test_batch_vs_oracle_theta():
     batch.close()
 
 
-def test_batch_rejects_mixed_degrees_and_fp64():
+def test_batch_rejects_mixed_degrees_and_precisions():
     m1 = _bubble_mesh(9, 200.0, degree=3)
     m2 = _bubble_mesh(9, 200.0, degree=4)
     with pytest.raises(L.AdgError):
         Batch([m1, m2])
     m3 = _bubble_mesh(9, 200.0, prec=L.ADG_PREC_FP64, degree=3)
     with pytest.raises(L.AdgError) as e:
-        Batch([m3])
-    assert e.value.code == L.ADG_EUNSUPPORTED
+        Batch([m1, m3])
+    assert e.value.code == L.ADG_EINVAL
 
 
 @pytest.mark.parametrize("degree", [1, 2, 4, 6, 7])
