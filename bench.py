@@ -1016,7 +1016,7 @@ def run_ours(args):
         achieved = flops_launch / (pred_avg * 1e-3) / 1e12
         traffic, smem_frac = predictor_counters(args.precision)
         roof = {
-            "kernel": {"fp64": "k_predictor_fp64<5,4>", "mixed": "k_predictor_mixed_x2<5,6>",
+            "kernel": {"fp64": "k_predictor_fp64<5,4>", "mixed": "k_predictor_mixed_x2<5,7>",
                        "mixed_tf32": "k_predictor_mixed_tc<5,4>"}[args.precision],
             "bound": "alu", "pipe": f"{pipe} FMA (CUDA cores)",
             "achieved": achieved, "peak": pk, "unit": "TFLOP/s",

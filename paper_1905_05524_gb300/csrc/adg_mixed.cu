@@ -47,9 +47,10 @@ struct MixCfg2 {
     static constexpr int n = N + 1;
     static_assert(n % 2 == 0, "node pairs need an even number of nodes per row");
     static constexpr int tpc = n * n / 2;  // threads per cell
-    // measured at N = 5 on the 81x81 warm bubble: 6 cells (0.111 ms) against 4, 8, 10 (0.132, 0.123,
-    // 0.113 ms); three resident blocks of 108 threads
-    static constexpr int cpb_default = N == 3 ? 16 : N == 5 ? 6 : 4;
+    // measured at N = 5: 7 cells per block (126 threads, three resident blocks) took 101.7 us on the
+    // 81x81 warm bubble against 105.2 (6 cells), 102.5 (5), and 0.791 against 0.834 ms per step on
+    // the 243x243 sweep mesh; 4, 8, 10 cells were slower still (0.132, 0.123, 0.113 ms)
+    static constexpr int cpb_default = N == 3 ? 16 : N == 5 ? 7 : 4;
     static constexpr int cpb = CPB_ ? CPB_ : cpb_default;
     static constexpr int threads = cpb * tpc;
     static constexpr int npair = n / 2;
@@ -393,6 +394,17 @@ k_corrector_mixed(double* __restrict__ u, const float* __restrict__ rvol,
     pdl_trigger();
 }
 
+// Cells per block of the per-mesh node-per-thread predictor launch; the
+// corrector and the TV statistics keep tv_cpb(N).  At N = 6 (49 threads a
+// cell) two cells fill 98 threads, a fourth warp of two lanes that issues
+// every instruction for them; five cells (245 threads in eight warps, two
+// resident blocks at 128 registers) ran the 243x243 step in 2.38 against
+// 2.53 ms (three cells: 2.61, ten: 2.55).
+template <int N>
+constexpr int pred_cpb() {
+    return N == 6 ? 5 : MixCfg<N>::cpb_default;
+}
+
 template <int N>
 static int launch_pred_mixed(const double* u, float* rvol, float* trace, int cells, float dt,
                              const BasisF& B, const PhysF& P, const MixedBg& bg, cudaStream_t s) {
@@ -405,7 +417,7 @@ static int launch_pred_mixed(const double* u, float* rvol, float* trace, int cel
         kern<<<blocks, C2::threads, C2::smem_pred, s>>>(u, rvol, trace, cells, dt, B, P, bg);
         return (int)cudaGetLastError();
     }
-    using C = MixCfg<N>;
+    using C = MixCfg<N, pred_cpb<N>()>;
     auto kern = k_predictor_mixed<N, C::cpb>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem_pred);
     if (e != cudaSuccess) return (int)e;

@@ -38,7 +38,7 @@ struct MixCfg {
     // registers) than at the allocator's 124; N = 7 1% faster at four
     // blocks (128 registers, 8 bytes spilled) than at three; N = 6 at six
     // blocks spills 120 bytes; elsewhere the allocator's own choice is best)
-    static constexpr int minb = (N == 5 && cpb == 4) ? 4 : (N == 4 && cpb == 5) ? 4 : (N == 3 && cpb == 8) ? 5 : (N == 2 && cpb == 16) ? 4 : (N == 6 && cpb == 2) ? 4 : (N == 7 && cpb == 2) ? 4 : 1;
+    static constexpr int minb = (N == 5 && cpb == 4) ? 4 : (N == 4 && cpb == 5) ? 4 : (N == 3 && cpb == 8) ? 5 : (N == 2 && cpb == 16) ? 4 : (N == 6 && cpb == 2) ? 4 : (N == 7 && cpb == 2) ? 4 : (N == 6 && cpb == 3) ? 3 : (N == 6 && cpb == 5) ? 2 : 1;
 };
 
 // Predictor body for the tile of CPB cells starting at cell c0 (one thread per
