@@ -93,7 +93,8 @@ def predictor_flops_per_cell(n):
 # kernel edited after its capture reports null instead of a stale figure.
 PREDICTOR_SOURCES = {
     "fp64": ["adg_fp64.cu", "adg_fp64_body.cuh", "adg_physics.cuh", "adg_internal.h"],
-    "mixed": ["adg_mixed.cu", "adg_mixed_body.cuh", "adg_mixed_point.cuh", "adg_convert.cuh", "adg_internal.h"],
+    "mixed": ["adg_mixed.cu", "adg_mixed_x2.cuh", "adg_mixed_body.cuh", "adg_mixed_point.cuh", "adg_convert.cuh",
+              "adg_internal.h"],
 }
 PREDICTOR_COUNTERS = {
     "fp64": {"sha256": "0aecd81cbffb578f57218c0279219adbac8fb37c25169339e18fab526ed547a9",

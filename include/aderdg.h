@@ -277,9 +277,12 @@ int adg_check_finite(adg_mesh* m, void* stream);
  * adg_adapt of a member, the next adg_batch_step synchronises the device,
  * rebuilds the instance tables and tile lists from the new leaves and
  * captures the graph again.
- * adg_batch_create times the predictor's tile-size candidates on the batch
+ * adg_batch_create times the predictor's candidates on the batch -- three
+ * tile sizes of the node-per-thread body and, for batches of uniform
+ * instances at degrees 3 and 5, the node-pair body (two nodes per thread) --
  * and keeps the fastest, cached per (degree, precision, SM count, size class,
- * adaptive or not) in memory and in a JSON file: $ADG_TUNE_CACHE if set (an
+ * number of candidates, adaptive or not) in memory and in a JSON file:
+ * $ADG_TUNE_CACHE if set (an
  * empty value keeps the cache in memory only), else tune_cache.json beside
  * the library; an entry found there is used without timing.
  *
@@ -300,19 +303,22 @@ int adg_check_finite(adg_mesh* m, void* stream);
  *            predictor tile, predictor grid, corrector tiles, cells per
  *            corrector tile, corrector grid, tuned time of candidates 0..2
  *            (ns; 0 when the cache decided), chosen candidate, where the
- *            choice came from (0 timed now, 2 cache), adaptive instances
+ *            choice came from (0 timed now, 2 cache), adaptive instances,
+ *            tuned time of candidate 3 (ns)
  * adg_batch_step synchronises `stream` only when the dt array changed or a
  * member adapted. */
 typedef struct adg_batch adg_batch;
 int adg_batch_create(adg_mesh* const* meshes, int k, adg_batch** out);
 int adg_batch_step(adg_batch* b, const double* dt, int nsteps, void* stream);
 int adg_batch_info(const adg_batch* b, int* info, int n);
-/* Pins the predictor's tile-size candidate (0, 1 or 2: half, default and
- * double the per-mesh cells per block) instead of the timed choice, e.g. to
+/* Pins the predictor's candidate (0, 1 or 2: half, default and double the
+ * per-mesh node-per-thread cells per block; 3: the node-pair body with its
+ * per-mesh cells per block at degrees 3 and 5 in a batch without adaptive
+ * instances, candidate 1 otherwise) instead of the timed choice, e.g. to
  * reproduce a run or to test every candidate.  Synchronises the device
  * (the previous tile list may be in use by a launched step), rebuilds the
  * tile list and drops the captured graph.  ADG_EINVAL for a NULL batch or a
- * candidate outside 0..2; ADG_EUNSUPPORTED for an FP64 batch. */
+ * candidate outside 0..3; ADG_EUNSUPPORTED for an FP64 batch. */
 int adg_batch_set_candidate(adg_batch* b, int cand);
 void adg_batch_destroy(adg_batch* b);
 

@@ -33,6 +33,7 @@
 #include "adg_internal.h"
 #include "adg_mesh.h"
 #include "adg_mixed_body.cuh"
+#include "adg_mixed_x2.cuh"
 #include "adg_mixed_point.cuh"
 #include "adg_physics.cuh"
 #include "adg_tv_cell.cuh"
@@ -1310,6 +1311,44 @@ k_corrector_batch(const MixedInst* __restrict__ insts, const AmrInst* __restrict
     }
 }
 
+// Node-pair predictor over the tiles of uniform instances (candidate 3 of a
+// batch without adaptive instances at N = 3, 5): the per-mesh node-pair body,
+// two nodes per thread, MixCfg2's cells per tile.
+template <int N, int CPB>
+__global__ void __launch_bounds__(CPB*(N + 1) * (N + 1) / 2, (MixCfg2<N, CPB>::minb))
+k_predictor_batch_x2(const MixedInst* __restrict__ insts, const BatchTile* __restrict__ tiles, int ntiles,
+                     const BasisF B) {
+    extern __shared__ float smf[];
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const BatchTile tl = tiles[t];
+        const MixedInst& I = insts[tl.inst];
+        const PhysF P = I.P;
+        const MixedBg bg = I.bg;
+        predictor_mixed_body_x2<N, CPB>(I.u, I.rvol, I.trace, I.cells, tl.c0, I.dtf, B, P, bg, smf);
+        __syncthreads();
+    }
+}
+
+template <int N>
+static int batch_x2(const MixedInst* insts, const BatchTile* tiles, int ntiles, const BasisF& Bf, int* cpb_out,
+                    int* blocks_io, cudaStream_t s) {
+    using C = MixCfg2<N>;
+    auto kern = k_predictor_batch_x2<N, C::cpb>;
+    if (cpb_out) *cpb_out = C::cpb;
+    if (!tiles) {  // query: set the smem limit and size the persistent grid (not during capture)
+        int per_sm = 0, dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem_pred);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, C::threads, C::smem_pred);
+        if (e != cudaSuccess) return (int)e;
+        if (blocks_io) *blocks_io = per_sm > 0 ? per_sm * sms : sms;
+        return 0;
+    }
+    kern<<<*blocks_io, C::threads, C::smem_pred, s>>>(insts, tiles, ntiles, Bf);
+    return (int)cudaGetLastError();
+}
+
 // Tile-size candidates per degree: half, default and double the default cells
 // per block (kept within 1024 threads and the shared-memory limit).
 template <int N, int K>
@@ -1369,6 +1408,11 @@ static int batch_n(int cand, int phase, const MixedInst* insts, const AmrInst* a
         ADG_BATCH_CASE(0)
         ADG_BATCH_CASE(1)
         ADG_BATCH_CASE(2)
+        case 3:  // the node-pair predictor where it exists, else candidate 1
+            if constexpr (N == 3 || N == 5)
+                if (!amr && phase == 0) return batch_x2<N>(insts, tiles, ntiles, Bf, cpb_out, blocks_out, s);
+            return amr ? batch_nka<N, 1, true>(phase, insts, ainsts, tiles, ntiles, Bf, B, O, cpb_out, blocks_out, s)
+                       : batch_nka<N, 1, false>(phase, insts, ainsts, tiles, ntiles, Bf, B, O, cpb_out, blocks_out, s);
     }
 #undef ADG_BATCH_CASE
     return (int)cudaErrorInvalidValue;

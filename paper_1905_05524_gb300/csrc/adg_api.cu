@@ -1006,7 +1006,7 @@ struct adg_batch {
     cudaGraphExec_t exec = nullptr;
     cudaGraph_t graph = nullptr;
     int graph_steps = 0;
-    double tune_ms[adg::kBatchCandidates] = {0, 0, 0};
+    double tune_ms[adg::kBatchCandidates] = {0, 0, 0, 0};
     int tune_source = 0;                    // 0: timed now, 1: in-process cache, 2: JSON cache file
 };
 
@@ -1261,7 +1261,8 @@ extern "C" int adg_batch_create(adg_mesh* const* meshes, int k, adg_batch** out)
     int bucket = 0;
     for (long long c = b->cells; c > 1; c >>= 1) ++bucket;
     char keybuf[128];
-    std::snprintf(keybuf, sizeof(keybuf), "degree=%d precision=mixed sms=%d cells~2^%d%s", b->N, sms, bucket,
+    std::snprintf(keybuf, sizeof(keybuf), "degree=%d precision=mixed sms=%d cells~2^%d candidates=%d%s", b->N, sms,
+                  bucket, adg::kBatchCandidates,
                   b->host_ainsts.empty() ? "" : " adaptive");
     const std::string key(keybuf);
     int best = -1;
@@ -1316,16 +1317,16 @@ extern "C" int adg_batch_create(adg_mesh* const* meshes, int k, adg_batch** out)
 
 extern "C" int adg_batch_info(const adg_batch* b, int* info, int n) {
     if (!b || !info || n < 1) return fail(ADG_EINVAL, "batch_info: NULL argument");
-    const int v[12] = {b->ntiles_pred, b->cpb_pred, b->blocks_pred, b->ntiles_corr, b->cpb_corr, b->blocks_corr,
+    const int v[13] = {b->ntiles_pred, b->cpb_pred, b->blocks_pred, b->ntiles_corr, b->cpb_corr, b->blocks_corr,
                        (int)(b->tune_ms[0] * 1000), (int)(b->tune_ms[1] * 1000), (int)(b->tune_ms[2] * 1000),
-                       b->cand_pred, b->tune_source, (int)b->host_ainsts.size()};
-    for (int a = 0; a < n && a < 12; ++a) info[a] = v[a];
+                       b->cand_pred, b->tune_source, (int)b->host_ainsts.size(), (int)(b->tune_ms[3] * 1000)};
+    for (int a = 0; a < n && a < 13; ++a) info[a] = v[a];
     return ADG_OK;
 }
 
 extern "C" int adg_batch_set_candidate(adg_batch* b, int cand) {
     if (!b) return fail(ADG_EINVAL, "batch_set_candidate: NULL batch");
-    if (cand < 0 || cand >= adg::kBatchCandidates) return fail(ADG_EINVAL, "batch_set_candidate: candidate not in 0..2");
+    if (cand < 0 || cand >= adg::kBatchCandidates) return fail(ADG_EINVAL, "batch_set_candidate: candidate not in 0..3");
     if (b->precision == ADG_PREC_FP64)
         return fail(ADG_EUNSUPPORTED, "batch_set_candidate: FP64 batches have one tile size");
     ADG_CK(cudaSetDevice(b->device), "batch_set_candidate: cudaSetDevice");

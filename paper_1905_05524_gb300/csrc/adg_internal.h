@@ -132,7 +132,7 @@ struct Fp64Inst {
 struct BatchTile {
     int inst, c0;
 };
-constexpr int kBatchCandidates = 3;  // tile-size candidates the autotuner times
+constexpr int kBatchCandidates = 4;  // predictor candidates the autotuner times (three tile sizes, node pairs)
 
 // Kernel launchers (adg_fp64.cu, adg_mixed.cu, adg_tv.cu).  They return a
 // cudaError_t value as int.

@@ -260,14 +260,15 @@ class Batch:
         L.check(self._lib.adg_batch_step(self.h, arr, int(nsteps), _stream_ptr(stream)))
 
     def set_candidate(self, cand):
-        """Pin the predictor's tile-size candidate (0, 1, 2) instead of the timed choice."""
+        """Pin the predictor's candidate (0, 1, 2: tile sizes; 3: node pairs) instead of the timed choice."""
         L.check(self._lib.adg_batch_set_candidate(self.h, int(cand)))
 
     def info(self):
-        buf = (ctypes.c_int * 12)()
-        L.check(self._lib.adg_batch_info(self.h, buf, 12))
+        buf = (ctypes.c_int * 13)()
+        L.check(self._lib.adg_batch_info(self.h, buf, 13))
         keys = ["tiles_pred", "cpb_pred", "grid_pred", "tiles_corr", "cpb_corr", "grid_corr",
-                "tune_ns_0", "tune_ns_1", "tune_ns_2", "candidate", "tune_source", "adaptive_instances"]
+                "tune_ns_0", "tune_ns_1", "tune_ns_2", "candidate", "tune_source", "adaptive_instances",
+                "tune_ns_3"]
         return dict(zip(keys, list(buf)))
 
     def close(self):

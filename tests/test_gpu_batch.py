@@ -107,14 +107,15 @@ def test_batch_matches_individual_meshes_every_degree(degree):
     batch.close()
 
 
-@pytest.mark.parametrize("degree", [2, 5, 7])
-@pytest.mark.parametrize("cand", [0, 1, 2])
+@pytest.mark.parametrize("degree", [2, 3, 5, 7])
+@pytest.mark.parametrize("cand", [0, 1, 2, 3])
 def test_batch_every_tile_candidate_matches_individual_meshes(degree, cand):
-    """Each predictor tile-size candidate pinned in turn (half, default and
-    double the per-mesh cells per block: separate instantiations of the
-    slice-pair predictor body with their own shared-memory strides), 2
-    batched steps against 2 per-mesh steps; 1e-9 relative as above (the
-    default candidate is the per-mesh kernel's own tile size)."""
+    """Each predictor candidate pinned in turn (half, default and double the
+    per-mesh cells per block: separate instantiations of the slice-pair
+    predictor body with their own shared-memory strides; 3: the node-pair
+    body at degrees 3 and 5, candidate 1 elsewhere), 2 batched steps against
+    2 per-mesh steps; 1e-9 relative as above (the default candidate is the
+    per-mesh kernel's own tile size)."""
     a = [_bubble_mesh(s, 300.0, degree=degree) for s in (5, 8, 11)]
     b = [_bubble_mesh(s, 300.0, degree=degree) for s in (5, 8, 11)]
     dts = [m.stable_dt(0.25) for m in a]

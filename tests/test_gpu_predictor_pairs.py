@@ -1,6 +1,7 @@
 """The node-pair mixed predictor (two nodes of a row per thread, degrees 3
 and 5, the per-mesh launch) against the node-per-thread predictor (the
-batched persistent launch runs that body): the same arithmetic in the same
+batched persistent launch's candidate 1 runs that body) and against the
+batched node-pair kernel (candidate 3): the same arithmetic in the same
 order on the same shared-memory layout, so the states agree bitwise (meshes
 of several blocks with a ragged last block included)."""
 import pytest
@@ -24,12 +25,14 @@ def _bubble(degree, side, stir=True):
     return m
 
 
+@pytest.mark.parametrize("cand", [1, 3])
 @pytest.mark.parametrize("degree,side", [(3, 13), (5, 9), (5, 13), (5, 14)])
-def test_node_pairs_bitwise_equal_node_per_thread(degree, side):
+def test_node_pairs_bitwise_equal_node_per_thread(degree, side, cand):
     a, b = _bubble(degree, side), _bubble(degree, side)
     dt = a.stable_dt(0.25)
     a.step(dt, 3)
     batch = Batch([b])
+    batch.set_candidate(cand)
     batch.step([dt], nsteps=3)
     torch.cuda.synchronize()
     ua, ub = a.get_state(), b.get_state()
@@ -40,8 +43,9 @@ def test_node_pairs_bitwise_equal_node_per_thread(degree, side):
     b.close()
 
 
+@pytest.mark.parametrize("cand", [1, 3])
 @pytest.mark.parametrize("degree", [3, 5])
-def test_node_pairs_steady_source_bitwise(degree):
+def test_node_pairs_steady_source_bitwise(degree, cand):
     """The steady manufactured source (x-dependent per node) on a periodic mesh."""
     cfg = steady_manufactured_config(degree=degree, nx=5, ny=4, precision=L.ADG_PREC_MIXED)
     a, b = Mesh(cfg), Mesh(cfg)
@@ -50,6 +54,7 @@ def test_node_pairs_steady_source_bitwise(degree):
     dt = a.stable_dt(0.5)
     a.step(dt, 2)
     batch = Batch([b])
+    batch.set_candidate(cand)
     batch.step([dt], nsteps=2)
     torch.cuda.synchronize()
     assert torch.equal(a.get_state(), b.get_state())
