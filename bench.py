@@ -97,10 +97,10 @@ PREDICTOR_SOURCES = {
               "adg_internal.h"],
 }
 PREDICTOR_COUNTERS = {
-    "fp64": {"sha256": "0aecd81cbffb578f57218c0279219adbac8fb37c25169339e18fab526ed547a9",
-             "traffic": 7809792 + 1536, "smem_frac": None},
-    "mixed": {"sha256": "f553fced84700eaead473c70bd967b7d1b485c4811fb2f5334d8c1c5d4b54ba4",
-              "traffic": 7654144 + 0, "smem_frac": 0.730},
+    "fp64": {"sha256": "c9f6a442974642ccc047dbe70c610235ec1d1ae192ca7c0b308ea7cc6c8653ad",
+             "traffic": 7810304 + 0, "smem_frac": None},
+    "mixed": {"sha256": "2d3858f9e0904f61954f84e6ca86cf88709abd3ab5ef76a36b2edfe793f3183e",
+              "traffic": 7654144 + 0, "smem_frac": 0.745},
 }
 
 def predictor_sources_sha256(precision):

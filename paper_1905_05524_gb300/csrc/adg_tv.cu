@@ -126,47 +126,78 @@ __device__ __forceinline__ int8_t tv_flag_of(double x, const TvThresholds& h) {
     return (h.flat || nan) ? (int8_t)0 : ref ? (int8_t)1 : (coa ? (int8_t)-1 : (int8_t)0);
 }
 
+// Chan et al.'s combine of (mean m, M2 m2) with (mb, m2b) under the
+// host-divided weights g1 = n_b/(n_a+n_b), g2 = n_a n_b/(n_a+n_b); every
+// operation rounds explicitly, so each code path below forms the same bits.
+__device__ __forceinline__ void chan_combine(double& m, double& m2, double mb, double m2b, double g1, double g2) {
+    const double d = __dsub_rn(mb, m);
+    m = __fma_rn(d, g1, m);
+    m2 = __fma_rn(__dmul_rn(d, d), g2, __dadd_rn(m2, m2b));
+}
+
+constexpr int kFoldMax = 8;  // folds up to this length load all their triples in one batch
+
 __global__ void __launch_bounds__(kTvThreads)
 k_tv_stats_flags(const double* __restrict__ tv, const TvStatsArgs st, double T_r, double T_c,
                  double* __restrict__ stats, int8_t* __restrict__ flags) {
     __shared__ double wm[kTvThreads / 32], w2[kTvThreads / 32];
     __shared__ TvThresholds thr;
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
-    // this thread's tree weights, loaded ahead of the dependent chain
-    double f1[kTvLevels], f2[kTvLevels];
+    const int k0 = t * st.per, k1 = min(k0 + st.per, st.nblk);
+    const bool batch = st.per <= kFoldMax;
+    // this thread's tree and fold weights (host-prepared), loaded ahead of
+    // the dependent chain and of the wait for the kernel before this one
+    double f1[kTvLevels], f2[kTvLevels], g1[kFoldMax], g2[kFoldMax];
 #pragma unroll
     for (int l = 0; l < kTvLevels; ++l) {
         const int pos = l < 5 ? t : lane;
         f1[l] = st.wtree[2 * (l * kTvThreads + pos)];
         f2[l] = st.wtree[2 * (l * kTvThreads + pos) + 1];
     }
-    // the tree weights above come from the host-side preparation; the block
-    // triples below from the kernel before this one (programmatic launch)
+#pragma unroll
+    for (int q = 1; q < kFoldMax; ++q) {
+        const bool in = batch && k0 + q < k1;
+        g1[q] = in ? st.wfold[2 * (k0 + q)] : 0.0;
+        g2[q] = in ? st.wfold[2 * (k0 + q) + 1] : 0.0;
+    }
+    // the block triples and the TV values come from the kernel before this
+    // one (programmatic launch)
     pdl_wait();
-    // left fold of this thread's block triples, loads batched four at a time
+    const int c_first = blockIdx.x * kTvThreads + t;
+    const double tv_first = (flags && c_first < st.cells) ? tv[c_first] : 0.0;
+    // left fold of this thread's block triples
     double m = 0.0, m2 = 0.0;
-    const int k0 = t * st.per, k1 = min(k0 + st.per, st.nblk);
-    if (k0 < k1) {
+    if (batch) {
+        double mb[kFoldMax], m2b[kFoldMax];
+#pragma unroll
+        for (int q = 0; q < kFoldMax; ++q) {
+            const bool in = k0 + q < k1;
+            mb[q] = in ? st.part[3 * (k0 + q) + 1] : 0.0;
+            m2b[q] = in ? st.part[3 * (k0 + q) + 2] : 0.0;
+        }
+        if (k0 < k1) {
+            m = mb[0];
+            m2 = m2b[0];
+        }
+#pragma unroll
+        for (int q = 1; q < kFoldMax; ++q)
+            if (k0 + q < k1) chan_combine(m, m2, mb[q], m2b[q], g1[q], g2[q]);
+    } else if (k0 < k1) {  // long folds: loads batched four at a time
         m = st.part[3 * k0 + 1];
         m2 = st.part[3 * k0 + 2];
         for (int k = k0 + 1; k < k1; k += 4) {
-            double mb[4], m2b[4], g1[4], g2[4];
+            double mb[4], m2b[4], h1[4], h2[4];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const int kk = min(k + q, k1 - 1);
                 mb[q] = st.part[3 * kk + 1];
                 m2b[q] = st.part[3 * kk + 2];
-                g1[q] = st.wfold[2 * kk];
-                g2[q] = st.wfold[2 * kk + 1];
+                h1[q] = st.wfold[2 * kk];
+                h2[q] = st.wfold[2 * kk + 1];
             }
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                if (k + q < k1) {
-                    const double d = mb[q] - m;
-                    m = m + d * g1[q];
-                    m2 = m2 + m2b[q] + d * d * g2[q];
-                }
-            }
+            for (int q = 0; q < 4; ++q)
+                if (k + q < k1) chan_combine(m, m2, mb[q], m2b[q], h1[q], h2[q]);
         }
     }
     // tree: strides 16..1 within each warp, then 4..1 across the warp results
@@ -174,11 +205,7 @@ k_tv_stats_flags(const double* __restrict__ tv, const TvStatsArgs st, double T_r
 #pragma unroll
     for (int l = 0, s = 16; s > 0; ++l, s >>= 1) {
         const double mo = __shfl_down_sync(0xffffffffu, m, s), m2o = __shfl_down_sync(0xffffffffu, m2, s);
-        if (lane < s) {
-            const double d = mo - m;
-            m = m + d * f1[l];
-            m2 = m2 + m2o + d * d * f2[l];
-        }
+        if (lane < s) chan_combine(m, m2, mo, m2o, f1[l], f2[l]);
     }
     if (lane == 0) {
         wm[w] = m;
@@ -191,11 +218,7 @@ k_tv_stats_flags(const double* __restrict__ tv, const TvStatsArgs st, double T_r
 #pragma unroll
         for (int l = 5, s = kTvThreads / 64; s > 0; ++l, s >>= 1) {
             const double mo = __shfl_down_sync(0xffffffffu, m, s), m2o = __shfl_down_sync(0xffffffffu, m2, s);
-            if (lane < s) {
-                const double d = mo - m;
-                m = m + d * f1[l];
-                m2 = m2 + m2o + d * d * f2[l];
-            }
+            if (lane < s) chan_combine(m, m2, mo, m2o, f1[l], f2[l]);
         }
         if (lane == 0) {
             const double sig = sqrt(m2 / (double)st.cells);
@@ -209,7 +232,8 @@ k_tv_stats_flags(const double* __restrict__ tv, const TvStatsArgs st, double T_r
     __syncthreads();
     if (!flags) return;
     const TvThresholds h = thr;
-    for (int c = blockIdx.x * kTvThreads + t; c < st.cells; c += gridDim.x * kTvThreads)
+    if (c_first < st.cells) flags[c_first] = tv_flag_of(tv_first, h);
+    for (int c = c_first + gridDim.x * kTvThreads; c < st.cells; c += gridDim.x * kTvThreads)
         flags[c] = tv_flag_of(tv[c], h);
 }
 
