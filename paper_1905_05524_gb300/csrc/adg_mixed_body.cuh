@@ -358,6 +358,25 @@ __device__ __forceinline__ void corrector_mixed_body(double* __restrict__ u, con
     const bool active = cell_raw < cells;
     const int cell = active ? cell_raw : cells - 1;
     const int ix = cell % P.nx, iy = cell / P.nx;
+    // this node's state and residual (and the background row of the TV
+    // field), loaded before the face fluxes so their latency overlaps them
+    double* uc = u + (size_t)cell * SL;
+    const float* rc = rvol + (size_t)cell * SL;
+    double uo[4];
+    float rv[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+        uo[v] = active ? uc[v * n2 + node] : 0.0;  // padding threads touch no state
+        rv[v] = rc[v * n2 + node];
+    }
+    double rb_row = 0.0, Eb_row = 0.0;
+    float pb_row = 0.f;
+    if constexpr (TV) {
+        const int row = iy * n + j;
+        rb_row = bg.rb[row];
+        Eb_row = bg.Eb[row];
+        pb_row = bg.pb[row];
+    }
 
     for (int idx = node; idx < 4 * n; idx += n2) {
         const int f = idx / n, m = idx - f * n;
@@ -416,8 +435,6 @@ __device__ __forceinline__ void corrector_mixed_body(double* __restrict__ u, con
         for (int v = 0; v < 4; ++v) Fst[cl][f][v][m] = out[v];
     }
     __syncthreads();
-    double* uc = u + (size_t)cell * SL;
-    const float* rc = rvol + (size_t)cell * SL;
     double unew[4];
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
@@ -425,16 +442,15 @@ __device__ __forceinline__ void corrector_mixed_body(double* __restrict__ u, con
         const float fx = __fsub_rn(__fmul_rn(B.lift1[i], Fst[cl][0][v][j]), __fmul_rn(B.lift0[i], Fst[cl][1][v][j]));
         const float fy = __fsub_rn(__fmul_rn(B.lift1[j], Fst[cl][2][v][i]), __fmul_rn(B.lift0[j], Fst[cl][3][v][i]));
         const float face = __fmaf_rn(fx, P.inv_hx, __fmul_rn(fy, P.inv_hy));
-        const float du = __fsub_rn(rc[v * n2 + node], face);
-        const double uo = active ? uc[v * n2 + node] : 0.0;  // padding threads touch no state
-        unew[v] = fma(dt, f32_to_f64(du), uo);                 // FP64 accumulation
+        const float du = __fsub_rn(rv[v], face);
+        unew[v] = fma(dt, f32_to_f64(du), uo[v]);  // FP64 accumulation
         if (active) uc[v * n2 + node] = unew[v];
     }
     if constexpr (TV) {
         __shared__ float fs[CPB][n2], red[CPB][n2];
         const int row = iy * n + j;
         const float z = tv_node_z(iy, j, B, P);
-        const float f = tv_field_mixed(unew, epi.var, bg.rb[row], bg.Eb[row], bg.pb[row], z, P, (float)epi.theta0,
+        const float f = tv_field_mixed(unew, epi.var, rb_row, Eb_row, pb_row, z, P, (float)epi.theta0,
                                        (float)(1.0 - epi.Rcp));
         static_assert(CPB == tv_cpb(N), "the TV statistics combine blocks of tv_cpb(N) cells");
         const double r = tv_cell<N, float>(f, epi.var == ADG_TV_THETA ? 0.f : bg.dzr[row], node, i, j, B,
