@@ -304,7 +304,8 @@ def run_form(prec_name, steps, warmup, dev, ws):
     from paper_1905_05524_gb300 import _lib as L
     from paper_1905_05524_gb300.solver import Mesh, atmosphere_config
 
-    prec = {"fp64": L.ADG_PREC_FP64, "mixed": L.ADG_PREC_MIXED, "mixed_tf32": L.ADG_PREC_MIXED_TF32}[prec_name]
+    prec = {"fp64": L.ADG_PREC_FP64, "mixed": L.ADG_PREC_MIXED, "mixed_tf32": L.ADG_PREC_MIXED_TF32,
+            "mixed_bf16x3": L.ADG_PREC_MIXED_BF16X3}[prec_name]
     cfg = atmosphere_config(degree=DEGREE, nx=NX, ny=NY, precision=prec, device=dev.index)
     m = Mesh(cfg)
     m.init_scenario(L.ADG_SCEN_COSINE, A=0.5, a=250.0, xc=500.0, zc=350.0)
@@ -987,17 +988,20 @@ def run_ours(args):
                              "phases_ms": {"predictor": ref["pred"] / args.steps,
                                            "corrector": ref["corr"] / args.steps,
                                            "tv_indicator": ref["tv"] / args.steps}}
-            tc = run_form("mixed_tf32", args.steps, min(args.warmup, 3), dev, 1)
-            th_t = theta_prime_np(tc["final"], tc["cfg"])
-            forms["mixed_tf32"] = {"value": dof * args.steps / (tc["total"] * 1e-3), "unit": UNIT,
-                                   "ms_per_step": tc["total"] / args.steps,
-                                   "phases_ms": {"predictor": tc["pred"] / args.steps,
-                                                 "corrector": tc["corr"] / args.steps,
-                                                 "tv_indicator": tc["tv"] / args.steps},
-                                   "theta_prime_rel_l2_vs_fp64": float(np.linalg.norm(th_t - th_d) /
-                                                                       np.linalg.norm(th_d)),
-                                   "form": "ADG_PREC_MIXED_TF32: the predictor's derivative contractions as "
-                                           "mma.sync TF32 MMAs with the three-term split"}
+            for tc_name, tc_form in (("mixed_tf32", "ADG_PREC_MIXED_TF32: the predictor's derivative "
+                                                    "contractions as mma.sync TF32 MMAs with the three-term split"),
+                                     ("mixed_bf16x3", "ADG_PREC_MIXED_BF16X3: the same contractions as mma.sync "
+                                                      "BF16 MMAs, operands split in three, six products")):
+                tc = run_form(tc_name, args.steps, min(args.warmup, 3), dev, 1)
+                th_t = theta_prime_np(tc["final"], tc["cfg"])
+                forms[tc_name] = {"value": dof * args.steps / (tc["total"] * 1e-3), "unit": UNIT,
+                                  "ms_per_step": tc["total"] / args.steps,
+                                  "phases_ms": {"predictor": tc["pred"] / args.steps,
+                                                "corrector": tc["corr"] / args.steps,
+                                                "tv_indicator": tc["tv"] / args.steps},
+                                  "theta_prime_rel_l2_vs_fp64": float(np.linalg.norm(th_t - th_d) /
+                                                                      np.linalg.norm(th_d)),
+                                  "form": tc_form}
             forms["mixed_error_vs_fp64"] = {"theta_prime_rel_l2": err, "per_variable_rel_l2": var_err,
                                             "per_variable_abs_l2": var_abs,
                                             "momentum_rel_to_momentum_l2": [var_abs[1] / mom_norm,
@@ -1018,7 +1022,8 @@ def run_ours(args):
         traffic, smem_frac = predictor_counters(args.precision)
         roof = {
             "kernel": {"fp64": "k_predictor_fp64<5,4>", "mixed": "k_predictor_mixed_x2<5,7>",
-                       "mixed_tf32": "k_predictor_mixed_tc<5,4>"}[args.precision],
+                       "mixed_tf32": "k_predictor_mixed_tc<5,4,0>",
+                       "mixed_bf16x3": "k_predictor_mixed_tc<5,4,1>"}[args.precision],
             "bound": "alu", "pipe": f"{pipe} FMA (CUDA cores)",
             "achieved": achieved, "peak": pk, "unit": "TFLOP/s",
             "frac": (achieved / pk) if pk else None,
@@ -1084,7 +1089,7 @@ def main():
     ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed", "mixed_tf32"])
+    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed", "mixed_tf32", "mixed_bf16x3"])
     ap.add_argument("--no-compare", action="store_true", help="skip the FP64 comparison form")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-instance batched form")
     ap.add_argument("--batch-steps", type=int, default=20)

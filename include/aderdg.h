@@ -84,6 +84,11 @@ extern "C" {
                                otherwise).  Measured slower than ADG_PREC_MIXED
                                on this GPU; kept as the tensor-core form of the
                                contractions.                                     */
+#define ADG_PREC_MIXED_BF16X3 3 /* as ADG_PREC_MIXED_TF32 with BF16 operands: each
+                               operand split exactly in three BF16 numbers, the
+                               six products down to 2^-16 accumulated in FP32 by
+                               three m16n8k16 MMAs (FP32 accuracy); the same
+                               meshes as ADG_PREC_MIXED_TF32.                    */
 
 #define ADG_TV_RHO 0
 #define ADG_TV_THETA 1      /* potential temperature theta = T (p0/p)^(R/cp)  */
@@ -282,9 +287,9 @@ int adg_check_finite(adg_mesh* m, void* stream);
  * instances at degrees 3 and 5, the node-pair body (two nodes per thread) --
  * and keeps the fastest, cached per (degree, precision, SM count, size class,
  * number of candidates, adaptive or not) in memory and in a JSON file:
- * $ADG_TUNE_CACHE if set (an
- * empty value keeps the cache in memory only), else tune_cache.json beside
- * the library; an entry found there is used without timing.
+ * $ADG_TUNE_CACHE if set (an empty value keeps the cache in memory only),
+ * else tune_cache.json beside the library; an entry found there is used
+ * without timing.
  *
  * A batch of ADG_PREC_FP64 members runs the per-mesh FP64 predictor and
  * corrector bodies in the persistent launches, with one tile size (the
@@ -294,7 +299,7 @@ int adg_check_finite(adg_mesh* m, void* stream);
  *
  *   meshes   k distinct meshes of one degree, device and precision, all
  *            ADG_PREC_MIXED or all ADG_PREC_FP64 (ADG_EINVAL for a mix,
- *            ADG_EUNSUPPORTED for ADG_PREC_MIXED_TF32); they stay owned by
+ *            ADG_EUNSUPPORTED for the tensor-core precisions); they stay owned by
  *            the caller and must outlive the batch; their states are
  *            advanced in place
  *   dt       host array of k time steps (> 0), one per instance

@@ -35,6 +35,7 @@ ADG_SRC_PAPER = 2
 ADG_PREC_FP64 = 0
 ADG_PREC_MIXED = 1
 ADG_PREC_MIXED_TF32 = 2
+ADG_PREC_MIXED_BF16X3 = 3
 ADG_TV_RHO = 0
 ADG_TV_THETA = 1
 ADG_SCEN_STEADY = 0

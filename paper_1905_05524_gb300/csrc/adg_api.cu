@@ -343,10 +343,13 @@ int adg_create_mesh(const adg_mesh_desc* d, adg_mesh** out) {
     if (d->source == ADG_SRC_PAPER && (d->precision != ADG_PREC_FP64 || d->max_levels != 0 || d->gravity))
         return fail(ADG_EUNSUPPORTED, "create_mesh: the time-dependent source is built for uniform FP64 meshes "
                                       "without gravity");
-    if (d->precision != ADG_PREC_FP64 && d->precision != ADG_PREC_MIXED && d->precision != ADG_PREC_MIXED_TF32)
+    if (d->precision != ADG_PREC_FP64 && d->precision != ADG_PREC_MIXED && d->precision != ADG_PREC_MIXED_TF32 &&
+        d->precision != ADG_PREC_MIXED_BF16X3)
         return fail(ADG_EINVAL, "create_mesh: unknown precision");
-    if (d->precision == ADG_PREC_MIXED_TF32 && (d->max_levels != 0 || !adg::tc_degree_supported(d->degree)))
-        return fail(ADG_EUNSUPPORTED, "create_mesh: ADG_PREC_MIXED_TF32 is built for uniform meshes of degree 3, 5, 7");
+    if ((d->precision == ADG_PREC_MIXED_TF32 || d->precision == ADG_PREC_MIXED_BF16X3) &&
+        (d->max_levels != 0 || !adg::tc_degree_supported(d->degree)))
+        return fail(ADG_EUNSUPPORTED, "create_mesh: the tensor-core precisions are built for uniform meshes of "
+                                      "degree 3, 5, 7");
     if (d->gravity && !(d->theta0 > 0.0 && d->p0 > 0.0))
         return fail(ADG_EINVAL, "create_mesh: gravity needs theta0 > 0 and p0 > 0");
     if (d->max_levels < 0 || d->max_levels > 4) return fail(ADG_EINVAL, "create_mesh: max_levels must be in [0, 4]");
@@ -574,9 +577,9 @@ int adg_predictor(adg_mesh* m, double dt, void* stream) {
     int e;
     if (m->d.precision == ADG_PREC_FP64)
         e = adg::launch_predictor_fp64(m->N, m->u, m->rvol, m->trace, m->cells, dt, m->t, m->B, m->P, m->bg, stream);
-    else if (m->d.precision == ADG_PREC_MIXED_TF32)
+    else if (m->d.precision == ADG_PREC_MIXED_TF32 || m->d.precision == ADG_PREC_MIXED_BF16X3)
         e = adg::launch_predictor_mixed_tc(m->N, m->u, (float*)m->rvol, (float*)m->trace, m->cells, dt, m->Bf,
-                                           m->Pf, m->mbg, stream);
+                                           m->Pf, m->mbg, m->d.precision == ADG_PREC_MIXED_BF16X3, stream);
     else
         e = adg::launch_predictor_mixed(m->N, m->u, (float*)m->rvol, (float*)m->trace, m->cells, dt, m->Bf,
                                         m->Pf, m->mbg, stream);

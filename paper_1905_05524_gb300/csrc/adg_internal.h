@@ -173,10 +173,10 @@ int launch_corrector_fp64(int N, double* u, const double* rvol, const double* tr
 int launch_predictor_mixed(int N, const double* u, float* rvol, float* trace, int cells, double dt,
                            const BasisF& B, const PhysF& P, const MixedBg& bg, void* stream);
 // the mixed predictor with its derivative contractions on the tensor cores
-// (mma.sync TF32 with the three-term split; adg_mixed_tc.cu), degrees 3, 5, 7
+// (mma.sync TF32 with the three-term split, or BF16 operands split in three; adg_mixed_tc.cu), degrees 3, 5, 7
 bool tc_degree_supported(int N);
 int launch_predictor_mixed_tc(int N, const double* u, float* rvol, float* trace, int cells, double dt,
-                              const BasisF& B, const PhysF& P, const MixedBg& bg, void* stream);
+                              const BasisF& B, const PhysF& P, const MixedBg& bg, bool bf16, void* stream);
 int launch_corrector_mixed(int N, double* u, const float* rvol, const float* trace, int cells,
                            double dt, const BasisF& B, const PhysF& P, const MixedBg& bg, void* stream,
                            const TvEpilogue* epi = nullptr);

@@ -12,6 +12,17 @@
 // three-term split; the dropped a_lo D_lo is 2^-22 of the product), so the
 // contractions keep FP32 accuracy.
 //
+// ADG_PREC_MIXED_BF16X3 runs the same contractions as mma.sync m16n8k16 with
+// BF16 operands: every operand is split exactly into three BF16 numbers
+// a = a_hi + a_mid + a_lo (each the top 8 significant bits of what remains),
+// likewise D, and the six products of order up to 2^-16 -- hi hi, mid hi,
+// hi mid, lo hi, mid mid, hi lo -- are accumulated in FP32 by three MMAs, the
+// K = 16 of each holding two of them side by side (K = n <= 8 per product):
+//   [a_hi | a_mid] x [D_hi ; D_hi],  [a_hi | a_lo] x [D_mid ; D_hi],
+//   [a_mid | a_hi] x [D_mid ; D_lo].
+// The dropped products are of order 2^-24, so the contractions keep FP32
+// accuracy as with the TF32 split.
+//
 // Shape: for one cell and direction the contraction is a (rows x n) by
 // (n x n) product, rows = (slice pair, variable, line, slice): 16-row tiles,
 // K = n padded to 8 (the padding columns of D are zero), N = n padded to 8.
@@ -48,6 +59,31 @@ struct TcCfg {
 
 __device__ __forceinline__ uint32_t tf32_hi(float a) { return __float_as_uint(a) & 0xffffe000u; }
 
+// Exact three-way BF16 split of a: the FP32 bit patterns of hi, mid, lo (the
+// low 16 bits zero, so the top 16 are the BF16 numbers), hi + mid + lo = a.
+__device__ __forceinline__ void bf16_split3(float a, uint32_t& h, uint32_t& m, uint32_t& l) {
+    h = __float_as_uint(a) & 0xffff0000u;
+    const float r1 = __fsub_rn(a, __uint_as_float(h));  // exact: the low 16 significant bits of a
+    m = __float_as_uint(r1) & 0xffff0000u;
+    const float r2 = __fsub_rn(r1, __uint_as_float(m));  // exact, at most 8 significant bits
+    l = __float_as_uint(r2) & 0xffff0000u;              // = r2
+}
+
+// two BF16 numbers (FP32 patterns with zero low halves) in one register, the
+// first in the low half
+__device__ __forceinline__ uint32_t bf16_pack(uint32_t lo_elem, uint32_t hi_elem) {
+    return (lo_elem >> 16) | hi_elem;
+}
+
+__device__ __forceinline__ void mma_bf16(float c[4], const uint32_t a0, const uint32_t a1, const uint32_t a2,
+                                         const uint32_t a3, const uint32_t b0, const uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
 __device__ __forceinline__ void mma_tf32(float c[4], const uint32_t a[4], const uint32_t b[2]) {
     asm volatile(
         "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
@@ -60,10 +96,12 @@ __device__ __forceinline__ void mma_tf32(float c[4], const uint32_t a[4], const 
 // of one cell: row r = 2 R + s (s the slice of the float2 pair), R = hv n +
 // line; x-direction: in(r, k) at ((hv n + line) n + k) 2 + s (line = j, k
 // along the row); y-direction: at ((hv n + k) n + line) 2 + s (line = i, k
-// along the column).  The output uses the same index map with k'.
-template <int n, bool YDIR>
+// along the column).  The output uses the same index map with k'.  bf: the
+// lane's B fragments -- TF32: hi {bf[0], bf[1]}, lo {bf[2], bf[3]} (rows k =
+// t, t + 4); BF16: hi, mid, lo pairs (rows k = 2t, 2t + 1) in bf[0..2].
+template <int n, bool YDIR, bool BF16>
 __device__ __forceinline__ void mma_tile(const float* __restrict__ S, float* __restrict__ Dst, int m0,
-                                         const uint32_t bh[2], const uint32_t bl[2], int lane) {
+                                         const uint32_t bf[4], int lane) {
     const int g = lane >> 2, t = lane & 3;
     auto idx = [](int r, int k) {
         const int R = r >> 1, s = r & 1;
@@ -71,21 +109,39 @@ __device__ __forceinline__ void mma_tile(const float* __restrict__ S, float* __r
         return YDIR ? ((hv * n + k) * n + line) * 2 + s : ((hv * n + line) * n + k) * 2 + s;
     };
     const int r0 = m0 + g, r1 = m0 + g + 8;
-    float a[4];
-    a[0] = S[idx(r0, t)];
-    a[1] = S[idx(r1, t)];
-    a[2] = t + 4 < n ? S[idx(r0, t + 4)] : 0.f;
-    a[3] = t + 4 < n ? S[idx(r1, t + 4)] : 0.f;
-    uint32_t ah[4], al[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        ah[q] = tf32_hi(a[q]);
-        al[q] = __float_as_uint(__fsub_rn(a[q], __uint_as_float(ah[q])));
-    }
     float c[4] = {0.f, 0.f, 0.f, 0.f};
-    mma_tf32(c, al, bh);
-    mma_tf32(c, ah, bl);
-    mma_tf32(c, ah, bh);
+    if constexpr (BF16) {
+        // A: row g (r0) and g + 8 (r1), columns k = 2t, 2t + 1 of each K half
+        const int ka = 2 * t, kb = 2 * t + 1;
+        const float a00 = ka < n ? S[idx(r0, ka)] : 0.f, a01 = kb < n ? S[idx(r0, kb)] : 0.f;
+        const float a10 = ka < n ? S[idx(r1, ka)] : 0.f, a11 = kb < n ? S[idx(r1, kb)] : 0.f;
+        uint32_t h00, m00, l00, h01, m01, l01, h10, m10, l10, h11, m11, l11;
+        bf16_split3(a00, h00, m00, l00);
+        bf16_split3(a01, h01, m01, l01);
+        bf16_split3(a10, h10, m10, l10);
+        bf16_split3(a11, h11, m11, l11);
+        const uint32_t H0 = bf16_pack(h00, h01), M0 = bf16_pack(m00, m01), L0 = bf16_pack(l00, l01);
+        const uint32_t H1 = bf16_pack(h10, h11), M1 = bf16_pack(m10, m11), L1 = bf16_pack(l10, l11);
+        mma_bf16(c, H0, H1, M0, M1, bf[0], bf[0]);  // a_hi D_hi + a_mid D_hi
+        mma_bf16(c, H0, H1, L0, L1, bf[1], bf[0]);  // a_hi D_mid + a_lo D_hi
+        mma_bf16(c, M0, M1, H0, H1, bf[1], bf[2]);  // a_mid D_mid + a_hi D_lo
+    } else {
+        float a[4];
+        a[0] = S[idx(r0, t)];
+        a[1] = S[idx(r1, t)];
+        a[2] = t + 4 < n ? S[idx(r0, t + 4)] : 0.f;
+        a[3] = t + 4 < n ? S[idx(r1, t + 4)] : 0.f;
+        uint32_t ah[4], al[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            ah[q] = tf32_hi(a[q]);
+            al[q] = __float_as_uint(__fsub_rn(a[q], __uint_as_float(ah[q])));
+        }
+        const uint32_t bh[2] = {bf[0], bf[1]}, bl[2] = {bf[2], bf[3]};
+        mma_tf32(c, al, bh);
+        mma_tf32(c, ah, bl);
+        mma_tf32(c, ah, bh);
+    }
     const int k0 = 2 * t, k1 = 2 * t + 1;
     if (k0 < n) {
         Dst[idx(r0, k0)] = c[0];
@@ -98,9 +154,8 @@ __device__ __forceinline__ void mma_tile(const float* __restrict__ S, float* __r
 }
 
 // all tiles of the block's cells for slice pairs [0, hcount): src -> dst along x or y
-template <int N, int CPB, bool YDIR>
-__device__ __forceinline__ void contract_all(float* smf, int src_off, int dst_off, int hcount, const uint32_t bh[2],
-                                             const uint32_t bl[2]) {
+template <int N, int CPB, bool YDIR, bool BF16>
+__device__ __forceinline__ void contract_all(float* smf, int src_off, int dst_off, int hcount, const uint32_t bf[4]) {
     using C = TcCfg<N>;
     constexpr int n = N + 1;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = C::threads / 32;
@@ -108,11 +163,11 @@ __device__ __forceinline__ void contract_all(float* smf, int src_off, int dst_of
     for (int tt = warp; tt < CPB * tiles_per_cell; tt += nwarps) {
         const int cl = tt / tiles_per_cell, m0 = (tt - cl * tiles_per_cell) * 16;
         float* base = smf + (size_t)cl * C::stride;
-        mma_tile<n, YDIR>(base + src_off, base + dst_off, m0, bh, bl, lane);
+        mma_tile<n, YDIR, BF16>(base + src_off, base + dst_off, m0, bf, lane);
     }
 }
 
-template <int N, int CPB>
+template <int N, int CPB, bool BF16>
 __global__ void __launch_bounds__(TcCfg<N>::threads)
 k_predictor_mixed_tc(const double* __restrict__ u, float* __restrict__ rvol, float* __restrict__ trace, int cells,
                      float dt, const BasisF B, const PhysF P, const MixedBg bg) {
@@ -143,19 +198,38 @@ k_predictor_mixed_tc(const double* __restrict__ u, float* __restrict__ rvol, flo
     const float rb = f64_to_f32(rb64), Eb = f64_to_f32(Eb64), pb = bg.pb[row];
     const float dzr = bg.dzr[row], dzE = bg.dzE[row];
 
-    // B fragments of the two contractions: b[k][k'] = D[k'][k] / h, split in TF32 hi + lo
-    uint32_t bxh[2], bxl[2], byh[2], byl[2];
+    // B fragments of the two contractions: b[k][k'] = D[k'][k] / h (column k' = g),
+    // split in TF32 hi + lo (rows k = t, t + 4) or in BF16 hi + mid + lo (rows k = 2t, 2t + 1)
+    uint32_t bx[4], by[4];
     {
         const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+        if constexpr (BF16) {
+            uint32_t xs[2][3], ys[2][3];
 #pragma unroll
-        for (int q = 0; q < 2; ++q) {
-            const int k = t + 4 * q;
-            const float dx = (g < n && k < n) ? __fmul_rn(B.D[g][k], P.inv_hx) : 0.f;
-            const float dy = (g < n && k < n) ? __fmul_rn(B.D[g][k], P.inv_hy) : 0.f;
-            bxh[q] = tf32_hi(dx);
-            bxl[q] = __float_as_uint(__fsub_rn(dx, __uint_as_float(bxh[q])));
-            byh[q] = tf32_hi(dy);
-            byl[q] = __float_as_uint(__fsub_rn(dy, __uint_as_float(byh[q])));
+            for (int q = 0; q < 2; ++q) {
+                const int k = 2 * t + q;
+                const float dx = (g < n && k < n) ? __fmul_rn(B.D[g][k], P.inv_hx) : 0.f;
+                const float dy = (g < n && k < n) ? __fmul_rn(B.D[g][k], P.inv_hy) : 0.f;
+                bf16_split3(dx, xs[q][0], xs[q][1], xs[q][2]);
+                bf16_split3(dy, ys[q][0], ys[q][1], ys[q][2]);
+            }
+#pragma unroll
+            for (int p = 0; p < 3; ++p) {
+                bx[p] = bf16_pack(xs[0][p], xs[1][p]);
+                by[p] = bf16_pack(ys[0][p], ys[1][p]);
+            }
+            bx[3] = by[3] = 0u;
+        } else {
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const int k = t + 4 * q;
+                const float dx = (g < n && k < n) ? __fmul_rn(B.D[g][k], P.inv_hx) : 0.f;
+                const float dy = (g < n && k < n) ? __fmul_rn(B.D[g][k], P.inv_hy) : 0.f;
+                bx[q] = tf32_hi(dx);
+                bx[2 + q] = __float_as_uint(__fsub_rn(dx, __uint_as_float(bx[q])));
+                by[q] = tf32_hi(dy);
+                by[2 + q] = __float_as_uint(__fsub_rn(dy, __uint_as_float(by[q])));
+            }
         }
     }
 
@@ -174,12 +248,12 @@ k_predictor_mixed_tc(const double* __restrict__ u, float* __restrict__ rvol, flo
     __syncthreads();
 
     auto gradients = [&](int hcount) {
-        contract_all<N, CPB, false>(smf, OQ, OX, hcount, bxh, bxl);
-        contract_all<N, CPB, true>(smf, OQ, OY, hcount, byh, byl);
+        contract_all<N, CPB, false, BF16>(smf, OQ, OX, hcount, bx);
+        contract_all<N, CPB, true, BF16>(smf, OQ, OY, hcount, by);
     };
     auto divergences = [&](int hcount) {
-        contract_all<N, CPB, false>(smf, OF, OX, hcount, bxh, bxl);
-        contract_all<N, CPB, true>(smf, OG, OY, hcount, byh, byl);
+        contract_all<N, CPB, false, BF16>(smf, OF, OX, hcount, bx);
+        contract_all<N, CPB, true, BF16>(smf, OG, OY, hcount, by);
     };
     // both slices of pair h at this node from the contraction outputs
     auto eval_pair = [&](int h, float2 q[4], float2 gx[4], float2 gy[4], FluxF2& f) {
@@ -370,9 +444,9 @@ k_predictor_mixed_tc(const double* __restrict__ u, float* __restrict__ rvol, flo
 
 template <int N>
 int launch_tc_n(const double* u, float* rvol, float* trace, int cells, float dt, const BasisF& B, const PhysF& P,
-                const MixedBg& bg, cudaStream_t s) {
+                const MixedBg& bg, bool bf16, cudaStream_t s) {
     using C = TcCfg<N>;
-    auto kern = k_predictor_mixed_tc<N, C::cpb>;
+    auto kern = bf16 ? k_predictor_mixed_tc<N, C::cpb, true> : k_predictor_mixed_tc<N, C::cpb, false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem);
     if (e != cudaSuccess) return (int)e;
     kern<<<(cells + C::cpb - 1) / C::cpb, C::threads, C::smem, s>>>(u, rvol, trace, cells, dt, B, P, bg);
@@ -384,13 +458,13 @@ int launch_tc_n(const double* u, float* rvol, float* trace, int cells, float dt,
 bool tc_degree_supported(int N) { return N == 3 || N == 5 || N == 7; }
 
 int launch_predictor_mixed_tc(int N, const double* u, float* rvol, float* trace, int cells, double dt,
-                              const BasisF& B, const PhysF& P, const MixedBg& bg, void* stream) {
+                              const BasisF& B, const PhysF& P, const MixedBg& bg, bool bf16, void* stream) {
     cudaStream_t s = (cudaStream_t)stream;
     const float dtf = (float)dt;
     switch (N) {
-        case 3: return launch_tc_n<3>(u, rvol, trace, cells, dtf, B, P, bg, s);
-        case 5: return launch_tc_n<5>(u, rvol, trace, cells, dtf, B, P, bg, s);
-        case 7: return launch_tc_n<7>(u, rvol, trace, cells, dtf, B, P, bg, s);
+        case 3: return launch_tc_n<3>(u, rvol, trace, cells, dtf, B, P, bg, bf16, s);
+        case 5: return launch_tc_n<5>(u, rvol, trace, cells, dtf, B, P, bg, bf16, s);
+        case 7: return launch_tc_n<7>(u, rvol, trace, cells, dtf, B, P, bg, bf16, s);
     }
     return (int)cudaErrorInvalidValue;
 }
