@@ -116,6 +116,24 @@ __device__ __forceinline__ void predictor_mixed_body_x2(const double* __restrict
             s1 = fma2(bc2(dI1[p + 1]), make_float2(a.z, a.w), fma2(bc2(dI1[p]), make_float2(a.x, a.y), s1));
         }
     };
+    // the same, also returning the pair's own values, which the row loads
+    // include (the load at p = i0), so the iterate needs no load of its own
+    auto xdot2_own = [&](const float2* S, float2& s0, float2& s1, float2& q0, float2& q1) {
+        const float2* r = S + j * n;
+        float4 a = ld4(r, 0);
+        float4 own = a;
+        s0 = fma2(bc2(dI0[1]), make_float2(a.z, a.w), mul2(bc2(dI0[0]), make_float2(a.x, a.y)));
+        s1 = fma2(bc2(dI1[1]), make_float2(a.z, a.w), mul2(bc2(dI1[0]), make_float2(a.x, a.y)));
+#pragma unroll
+        for (int p = 2; p < n; p += 2) {
+            a = ld4(r, p);
+            if (p == i0) own = a;
+            s0 = fma2(bc2(dI0[p + 1]), make_float2(a.z, a.w), fma2(bc2(dI0[p]), make_float2(a.x, a.y), s0));
+            s1 = fma2(bc2(dI1[p + 1]), make_float2(a.z, a.w), fma2(bc2(dI1[p]), make_float2(a.x, a.y), s1));
+        }
+        q0 = make_float2(own.x, own.y);
+        q1 = make_float2(own.z, own.w);
+    };
     // y-contractions of the column pair (2m, 2m+1): one 16-byte load per term of both nodes
     auto ydot2 = [&](const float2* S, float2& s0, float2& s1) {
         float4 a = ld4(S, i0);
@@ -134,10 +152,7 @@ __device__ __forceinline__ void predictor_mixed_body_x2(const double* __restrict
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
             const float2* S = Q2 + h * PS + v * n2;
-            const float4 qq = ld4(S, nd0);
-            q[0][v] = make_float2(qq.x, qq.y);
-            q[1][v] = make_float2(qq.z, qq.w);
-            xdot2(S, gx[0][v], gx[1][v]);
+            xdot2_own(S, gx[0][v], gx[1][v], q[0][v], q[1][v]);
             ydot2(S, gy[0][v], gy[1][v]);
         }
 #pragma unroll
@@ -250,10 +265,7 @@ __device__ __forceinline__ void predictor_mixed_body_x2(const double* __restrict
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
             const float2* S = Q2 + h * PS + v * n2;
-            const float4 qq = ld4(S, nd0);
-            q[0][v] = make_float2(qq.x, qq.y);
-            q[1][v] = make_float2(qq.z, qq.w);
-            xdot2(S, gx[0][v], gx[1][v]);
+            xdot2_own(S, gx[0][v], gx[1][v], q[0][v], q[1][v]);
             ydot2(S, gy[0][v], gy[1][v]);
         }
         const float w0 = B.w[2 * h], w1 = B.w[2 * h + 1];
