@@ -495,12 +495,25 @@ __device__ __forceinline__ void predictor_amr_mixed_body(const double* __restric
         for (int p = 1; p < n; ++p) s = fma2(bc2(dJ[p]), c[p * n], s);
         return s;
     };
+    // the x-contraction with this node's own value taken from the row load at p = i
+    auto xdot_own = [&](const float2* S, float2& own) {
+        const float2* r = S + j * n;
+        float2 a = r[0];
+        own = a;
+        float2 s = mul2(bc2(dI[0]), a);
+#pragma unroll
+        for (int p = 1; p < n; ++p) {
+            a = r[p];
+            if (p == i) own = a;
+            s = fma2(bc2(dI[p]), a, s);
+        }
+        return s;
+    };
     auto eval_pair = [&](int h, float2 q[4], float2 gx[4], float2 gy[4], FluxF2& f) {
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
             const float2* S = Q2 + h * PS + v * n2;
-            q[v] = S[node];
-            gx[v] = xdot(S);
+            gx[v] = xdot_own(S, q[v]);
             gy[v] = ydot(S);
         }
         gy[0] = add2(gy[0], bc2(dzr));

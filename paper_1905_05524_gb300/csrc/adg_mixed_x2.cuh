@@ -40,7 +40,10 @@ struct MixCfg2 {
     static constexpr int bank_off = 16;                                // floats, mod 32, between cells
     static constexpr int stride = raw + ((bank_off - raw % 32) + 32) % 32;  // a multiple of 4 floats
     static constexpr size_t smem_pred = (size_t)cpb * stride * sizeof(float);
-    static constexpr int minb = N == 5 ? 3 : 1;
+    // three resident blocks asked of the register allocator: at N = 3 taking the pair's
+    // own iterate from its row loads otherwise grows the kernel to 218 registers (two
+    // blocks, 0.175 ms per 243x243 step); capped it keeps 167 (0.157 ms)
+    static constexpr int minb = (N == 5 || N == 3) ? 3 : 1;
 };
 
 template <int N, int CPB>
