@@ -121,7 +121,8 @@ def test_rollout_gradient_vs_oracle_adjoint():
             u = o.step(u, dt)
         Jo = _oracle_J(o, cfg, u, probes, target)
         (go,) = torch.autograd.grad(Jo, x)
-    assert abs(J - float(Jo)) <= 1e-10 * abs(float(Jo))
+    Jo = float(Jo.detach())
+    assert abs(J - Jo) <= 1e-10 * abs(Jo)
     r = (torch.linalg.vector_norm(g.cpu() - go) / torch.linalg.vector_norm(go)).item()
     assert r <= 1e-9, r
 
