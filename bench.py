@@ -458,7 +458,14 @@ def run_batch(dev, nsteps=20, instances=64, fp64=False):
     b.close()
     for m in ms:
         m.close()
+    # the chosen predictor candidate's CUDA-event time from the autotuner (mixed batches)
+    t_ns = info.get("tune_ns_%d" % info["candidate"], 0) if not fp64 else 0
+    pred = None
+    if t_ns > 0:
+        pred = {"ms": t_ns * 1e-6, "tflops": predictor_flops_per_cell(DEGREE + 1) * cells / (t_ns * 1e-9) / 1e12,
+                "source": "the autotuner's CUDA-event time of the chosen candidate (3 launches)"}
     return {"value": dof * nsteps / (ms_total * 1e-3), "unit": UNIT, "instances": instances,
+            "predictor": pred,
             "precision": "fp64" if fp64 else "mixed",
             "cells": cells, "steps": nsteps, "ms_per_step": ms_total / nsteps,
             "step": "predictor + corrector (persistent launches, CUDA graph)", "tiles": info,
@@ -1015,6 +1022,9 @@ def run_ours(args):
             forms["fp64_batched_64_instances"] = run_batch(dev, nsteps=max(1, args.batch_steps // 4), fp64=True)
         peaks = {} if args.no_peaks else measure_fma_peaks()
         mp = measured_peaks_file()
+        bt = forms.get("mixed_batched_64_instances", {}).get("predictor")
+        if bt and peaks.get("fp32"):
+            bt["frac_of_fp32_fma_peak"] = bt["tflops"] / peaks["fp32"]
         flops_launch = predictor_flops_per_cell(n) * cells
         pred_avg = main["pred"] / args.steps
         pipe = "fp64" if args.precision == "fp64" else "fp32"
