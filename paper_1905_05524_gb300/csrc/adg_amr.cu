@@ -1048,15 +1048,26 @@ struct AmrCfg {
     }                                             \
     return fail(ADG_EINVAL, "bad degree");
 
+// Leaves per block of the per-mesh mixed adaptive predictor (the TV
+// statistics of adaptive meshes come from their own kernel, so this need not
+// be tv_cpb).  Measured at N = 5 on the two-bubble tree (1065 leaves, under
+// half a wave): 4 leaves 2.61e9, 2 leaves 2.60e9, 1 leaf 2.43e9 DOF-updates/s.
+template <int N>
+constexpr int amr_mixed_cpb() {
+    return AmrCfg<N>::cpb;
+}
+
 template <int N>
 static int pred_n(adg_mesh* m, double dt, cudaStream_t s) {
     using C = AmrCfg<N>;
     if (m->d.precision == ADG_PREC_MIXED) {
-        auto km = k_predictor_amr_mixed<N, C::cpb>;
-        const size_t smem = (size_t)C::cpb * AmrMixCfg<N>::stride * sizeof(float);
+        constexpr int CM = amr_mixed_cpb<N>();
+        auto km = k_predictor_amr_mixed<N, CM>;
+        const size_t smem = (size_t)CM * AmrMixCfg<N>::stride * sizeof(float);
         ADG_CK(cudaFuncSetAttribute(km, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem), "amr pred mixed");
-        km<<<(m->cells + C::cpb - 1) / C::cpb, C::threads, smem, s>>>(m->u, m->rvol, m->trace, m->cells, (float)dt,
-                                                                       m->Bf, m->Pf, m->geo, m->mbl64, m->mblf);
+        km<<<(m->cells + CM - 1) / CM, CM * (N + 1) * (N + 1), smem, s>>>(m->u, m->rvol, m->trace, m->cells,
+                                                                          (float)dt, m->Bf, m->Pf, m->geo, m->mbl64,
+                                                                          m->mblf);
         ADG_CK(cudaGetLastError(), "amr mixed predictor launch");
         return ADG_OK;
     }
