@@ -1321,8 +1321,8 @@ extern "C" int adg_batch_create(adg_mesh* const* meshes, int k, adg_batch** out)
 extern "C" int adg_batch_info(const adg_batch* b, int* info, int n) {
     if (!b || !info || n < 1) return fail(ADG_EINVAL, "batch_info: NULL argument");
     const int v[13] = {b->ntiles_pred, b->cpb_pred, b->blocks_pred, b->ntiles_corr, b->cpb_corr, b->blocks_corr,
-                       (int)(b->tune_ms[0] * 1000), (int)(b->tune_ms[1] * 1000), (int)(b->tune_ms[2] * 1000),
-                       b->cand_pred, b->tune_source, (int)b->host_ainsts.size(), (int)(b->tune_ms[3] * 1000)};
+                       (int)(b->tune_ms[0] * 1e6), (int)(b->tune_ms[1] * 1e6), (int)(b->tune_ms[2] * 1e6),
+                       b->cand_pred, b->tune_source, (int)b->host_ainsts.size(), (int)(b->tune_ms[3] * 1e6)};
     for (int a = 0; a < n && a < 13; ++a) info[a] = v[a];
     return ADG_OK;
 }
