@@ -79,16 +79,16 @@ extern "C" {
                                background split, pressure recovery and update   */
 #define ADG_PREC_MIXED_TF32 2 /* ADG_PREC_MIXED with the predictor's derivative
                                contractions as tensor-core MMAs (TF32 operands
-                               split in three terms, FP32 accumulation); uniform
+                               split in two, three products, FP32 accumulation); uniform
                                meshes of degree 3, 5, 7 (ADG_EUNSUPPORTED
                                otherwise).  Measured slower than ADG_PREC_MIXED
                                on this GPU; kept as the tensor-core form of the
                                contractions.                                     */
 #define ADG_PREC_MIXED_BF16X3 3 /* as ADG_PREC_MIXED_TF32 with BF16 operands: each
                                operand split exactly in three BF16 numbers, the
-                               six products down to 2^-16 accumulated in FP32 by
-                               three m16n8k16 MMAs (FP32 accuracy); the same
-                               meshes as ADG_PREC_MIXED_TF32.                    */
+                               six largest products accumulated in FP32 by three
+                               m16n8k16 MMAs (a product within about 2^-21 of
+                               exact); the same meshes as ADG_PREC_MIXED_TF32. */
 
 #define ADG_TV_RHO 0
 #define ADG_TV_THETA 1      /* potential temperature theta = T (p0/p)^(R/cp)  */

@@ -7,21 +7,25 @@
 // FP32 FMAs.
 //
 // Accuracy: every operand a is split into a_hi (its top 11 significant bits,
-// exactly a TF32 number) and a_lo = a - a_hi (exact in FP32), likewise D, and
-// each product is accumulated as a_lo D_hi + a_hi D_lo + a_hi D_hi (the
-// three-term split; the dropped a_lo D_lo is 2^-22 of the product), so the
-// contractions keep FP32 accuracy.
+// exactly a TF32 number) and a_lo = a - a_hi (exact in FP32, |a_lo| < 2^-10
+// |a|), likewise D, and each product is accumulated as a_lo D_hi + a_hi D_lo
+// + a_hi D_hi (the three-term split).  The dropped a_lo D_lo is below 2^-20
+// of the product, and the MMA reads a_lo and D_lo as TF32 (their top 11
+// bits), another 2^-21 each: a product is within about 2^-19 of exact in the
+// worst case, 2^-22 typically, against 2^-24 for one FP32 rounding.
 //
 // ADG_PREC_MIXED_BF16X3 runs the same contractions as mma.sync m16n8k16 with
 // BF16 operands: every operand is split exactly into three BF16 numbers
-// a = a_hi + a_mid + a_lo (each the top 8 significant bits of what remains),
-// likewise D, and the six products of order up to 2^-16 -- hi hi, mid hi,
-// hi mid, lo hi, mid mid, hi lo -- are accumulated in FP32 by three MMAs, the
-// K = 16 of each holding two of them side by side (K = n <= 8 per product):
+// a = a_hi + a_mid + a_lo (each the top 8 significant bits of what remains,
+// so |a_mid| < 2^-7 |a| and |a_lo| < 2^-14 |a|), likewise D, and the six
+// products of order 1 to 2^-14 -- hi hi, mid hi, hi mid, lo hi, mid mid,
+// hi lo -- are accumulated in FP32 by three MMAs, the K = 16 of each
+// holding two of them side by side (K = n <= 8 per product):
 //   [a_hi | a_mid] x [D_hi ; D_hi],  [a_hi | a_lo] x [D_mid ; D_hi],
 //   [a_mid | a_hi] x [D_mid ; D_lo].
-// The dropped products are of order 2^-24, so the contractions keep FP32
-// accuracy as with the TF32 split.
+// The dropped mid lo, lo mid and lo lo are below 2^-20 of the product: about
+// 2^-21 in the worst case, 2^-25 typically (tests/test_split_products.py
+// checks both splits and these orders on the host).
 //
 // Shape: for one cell and direction the contraction is a (rows x n) by
 // (n x n) product, rows = (slice pair, variable, line, slice): 16-row tiles,
